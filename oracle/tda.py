@@ -1,0 +1,265 @@
+"""TDA-risp CPU oracle in plain NumPy FP64 -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may use
+this module; the product path never imports it.  It shares no code with the
+CUDA library.  Every function follows the paper's definitions directly:
+
+  A_{ia,jb} = (e_a - e_i) d_ij d_ab + 2 (ia|jb) - c_x (ij|ab)     Sec. 2, Eq. TDA-risp
+  (pq|rs)   ~ sum_PQ (pq|P) (P|Q)^-1 (Q|rs)                       Sec. 2, Eq. RI
+  aux basis: one s and one p primitive per non-hydrogen atom for J,
+             the s primitive only for K, none on hydrogen          Sec. 3.2
+  K window:  occupied e_i > -W and virtual e_a < W (W = 40 eV),
+             K restricted to that block                           Sec. 3.2
+  T_ij^P = sum_Q (ij|Q) (Q|P)^-1,  T_ab^P = (ab|P),
+  K_mia  = sum_P sum_j T_ij^P sum_b T_ab^P X_mjb                  Sec. 3.2, Eq. K_mia ff.
+  range-separated exchange: every K integral and the K metric use
+  (alpha + beta erf(omega r))/r                                   Sec. 3.2, Eqs. RSH, K_mia_RSH
+  Davidson: standard block Davidson with restart that keeps the current
+  Ritz vectors and recomputes A V                                 Sec. 3.3
+
+The reading of (ab|Q) in the paper's T_ab definition (a dangling sum over Q)
+is T_ab^P = (ab|P), which makes sum_P T_ij^P T_ab^P the RI value of (ij|ab).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from . import ints
+
+HARTREE_TO_EV = 27.211386245988
+
+
+def aux_shells(Z, xyz, aux_exp, kind: str, include_h: bool = False) -> ints.AuxShells:
+    """Auxiliary shells of Sec. 3.2: 'J' gives s then p on every atom that
+    carries an auxiliary exponent (hydrogen excluded unless include_h), 'K'
+    gives the s shells only."""
+    cen, ls, ex = [], [], []
+    for a, z in enumerate(Z):
+        if aux_exp[a] <= 0.0 or (z == 1 and not include_h):
+            continue
+        cen.append(xyz[a])
+        ls.append(0)
+        ex.append(aux_exp[a])
+        if kind == "J":
+            cen.append(xyz[a])
+            ls.append(1)
+            ex.append(aux_exp[a])
+    return ints.AuxShells(np.asarray(cen).reshape(-1, 3), ls, ex)
+
+
+def window(eps, nocc, window_ev):
+    """Exchange window of Sec. 3.2: occupied orbitals with e > -W and virtual
+    orbitals with e < W (Hartree).  window_ev <= 0 keeps every orbital."""
+    eps = np.asarray(eps)
+    occ = np.arange(nocc)
+    vir = np.arange(len(eps) - nocc)
+    if window_ev <= 0:
+        return occ, vir
+    w = window_ev / HARTREE_TO_EV
+    return occ[eps[:nocc] > -w], vir[eps[nocc:] < w]
+
+
+@dataclasses.dataclass
+class Factors:
+    nocc: int
+    nvir: int
+    D: np.ndarray        # (nocc, nvir) e_a - e_i
+    Y: np.ndarray        # (NJ, nocc, nvir) (P|ia), Coulomb
+    GJ: np.ndarray       # (NJ, NJ) (P|Q), Coulomb
+    Tij: np.ndarray      # (NK, o', o') sum_Q (ij|Q)(Q|P)^-1 with the K operator
+    Tab: np.ndarray      # (NK, v', v') (ab|P) with the K operator
+    GK: np.ndarray       # (NK, NK) K-operator metric
+    occK: np.ndarray     # occupied window indices
+    virK: np.ndarray     # virtual window indices (relative to nocc)
+    cx: float
+
+
+def build(Z, xyz, shells, aux_exp, C, eps, nocc, cx, ka=1.0, kb=0.0, omega=0.0,
+          window_ev=40.0, include_h=False, chunk=16) -> Factors:
+    """Three-centre integrals, metrics and MO-basis tensors of Secs. 2 and 3.2.
+
+    The K operator is (ka + kb erf(omega r))/r; for a global hybrid ka=1, kb=0.
+    J always uses the Coulomb operator."""
+    C = np.asarray(C, dtype=np.float64)
+    eps = np.asarray(eps, dtype=np.float64)
+    nmo = C.shape[1]
+    nvir = nmo - nocc
+    Co, Cv = C[:, :nocc], C[:, nocc:]
+    occK, virK = window(eps, nocc, window_ev)
+    CoK, CvK = Co[:, occK], Cv[:, virK]
+    D = eps[nocc:][None, :] - eps[:nocc][:, None]
+
+    auxJ = aux_shells(Z, xyz, aux_exp, "J", include_h)
+    auxK = aux_shells(Z, xyz, aux_exp, "K", include_h)
+
+    def mo_blocks(aux, ka_, kb_, om_, pairs):
+        out = [[] for _ in pairs]
+        for s0 in range(0, len(aux.l), chunk):
+            sub = ints.AuxShells(aux.xyz[s0:s0 + chunk], aux.l[s0:s0 + chunk], aux.exps[s0:s0 + chunk])
+            I = ints.int3c(xyz, shells, sub, ka_, kb_, om_)
+            for k, (L, R) in enumerate(pairs):
+                out[k].append(np.einsum("mp,Pmn,nq->Ppq", L, I, R, optimize=True))
+        return [np.concatenate(o, axis=0) if o else np.zeros((0, L.shape[1], R.shape[1]))
+                for o, (L, R) in zip(out, pairs)]
+
+    (Y,) = mo_blocks(auxJ, 1.0, 0.0, 0.0, [(Co, Cv)])
+    GJ = ints.int2c(auxJ)
+    Iij, Iab = mo_blocks(auxK, ka, kb, omega, [(CoK, CoK), (CvK, CvK)])
+    GK = ints.int2c(auxK, ka, kb, omega)
+    NK = GK.shape[0]
+    if NK:
+        # T_ij^P = sum_Q (ij|Q) [(Q|P)^-1]
+        Tij = np.einsum("Qij,QP->Pij", Iij, np.linalg.inv(GK))
+    else:
+        Tij = Iij
+    return Factors(nocc=nocc, nvir=nvir, D=D, Y=Y, GJ=GJ, Tij=Tij, Tab=Iab, GK=GK,
+                   occK=occK, virK=virK, cx=float(cx))
+
+
+def coulomb_ri(f: Factors) -> np.ndarray:
+    """(ia|jb) = sum_PQ (ia|P) (P|Q)^-1 (Q|jb) as an (nov, nov) matrix."""
+    Y = f.Y.reshape(f.Y.shape[0], -1)
+    if Y.shape[0] == 0:
+        return np.zeros((Y.shape[1], Y.shape[1]))
+    return Y.T @ np.linalg.solve(f.GJ, Y)
+
+
+def exchange_ri(f: Factors) -> np.ndarray:
+    """(ij|ab) RI value on the window, embedded as an (nov, nov) matrix with
+    rows (i,a) and columns (j,b); zero outside the window."""
+    K = np.zeros((f.nocc, f.nvir, f.nocc, f.nvir))
+    if f.Tij.shape[0]:
+        blk = np.einsum("Pij,Pab->iajb", f.Tij, f.Tab, optimize=True)
+        K[np.ix_(f.occK, f.virK, f.occK, f.virK)] = blk
+    n = f.nocc * f.nvir
+    return K.reshape(n, n)
+
+
+def explicit_A(f: Factors) -> np.ndarray:
+    """Explicit TDA-risp matrix (Sec. 2, Eq. TDA-risp) for small problems."""
+    A = 2.0 * coulomb_ri(f) - f.cx * exchange_ri(f)
+    A[np.diag_indices_from(A)] += f.D.reshape(-1)
+    return A
+
+
+def matvec(f: Factors, X: np.ndarray) -> np.ndarray:
+    """A X for a block X[m][nocc][nvir] without forming A (Sec. 3.2 order for K)."""
+    X = np.asarray(X, dtype=np.float64).reshape(-1, f.nocc, f.nvir)
+    AX = f.D[None] * X
+    if f.Y.shape[0]:
+        Z = np.einsum("Pia,mia->Pm", f.Y, X, optimize=True)
+        Z = np.linalg.solve(f.GJ, Z)
+        AX += 2.0 * np.einsum("Pia,Pm->mia", f.Y, Z, optimize=True)
+    if f.Tij.shape[0] and len(f.occK) and len(f.virK):
+        Xw = X[:, f.occK][:, :, f.virK]
+        M = np.einsum("Pab,mjb->Pmja", f.Tab, Xw, optimize=True)
+        K = np.einsum("Pij,Pmja->mia", f.Tij, M, optimize=True)
+        AX[np.ix_(np.arange(X.shape[0]), f.occK, f.virK)] -= f.cx * K
+    return AX
+
+
+# --------------------------------------------------------------------------
+# Davidson (Sec. 3.3: standard procedure; restart keeps the Ritz vectors and
+# recomputes A V).  The paper leaves guess, preconditioner and norms open;
+# this oracle uses: unit-vector guess on the `block` smallest diagonal
+# entries (ties to the lower index), diagonal preconditioner with the
+# denominator floored at 1e-8 in magnitude, two passes of classical
+# Gram-Schmidt, new vectors dropped below norm 1e-8, convergence when every
+# one of the nstates residual 2-norms is below tol.
+
+@dataclasses.dataclass
+class DavidsonResult:
+    omega: np.ndarray
+    X: np.ndarray
+    resid: np.ndarray
+    niter: int
+    nmatvec: int
+    nrestart: int
+    converged: bool
+
+
+def _orth_new(V, T, drop=1e-8):
+    keep = []
+    for t in T:
+        t = t / np.linalg.norm(t)
+        for _ in range(2):
+            if V.shape[0]:
+                t = t - V.T @ (V @ t)
+            if keep:
+                Q = np.asarray(keep)
+                t = t - Q.T @ (Q @ t)
+        n = np.linalg.norm(t)
+        if n < drop:
+            continue
+        keep.append(t / n)
+    return np.asarray(keep).reshape(-1, V.shape[1])
+
+
+def davidson(apply_A, D, nstates, block=None, tol=1e-6, max_space=None, max_iter=200,
+             floor=1e-8) -> DavidsonResult:
+    D = np.asarray(D, dtype=np.float64).reshape(-1)
+    n = D.size
+    nstates = min(nstates, n)
+    block = min(n, block if block else 2 * nstates)
+    block = max(block, nstates)
+    max_space = max_space if max_space else 20 * nstates
+    max_space = max(max_space, block + nstates)
+    order = np.argsort(D, kind="stable")[:block]
+    V = np.zeros((block, n))
+    V[np.arange(block), order] = 1.0
+    W = apply_A(V)
+    nmv = block
+    nrestart = 0
+    theta = Xr = rn = None
+    for it in range(1, max_iter + 1):
+        H = V @ W.T
+        H = 0.5 * (H + H.T)
+        w, y = np.linalg.eigh(H)
+        theta = w[:nstates]
+        Y = y[:, :nstates]
+        Xr = Y.T @ V
+        R = Y.T @ W - theta[:, None] * Xr
+        rn = np.linalg.norm(R, axis=1)
+        if np.all(rn < tol):
+            return DavidsonResult(theta, Xr, rn, it, nmv, nrestart, True)
+        T = []
+        for k in np.nonzero(rn >= tol)[0]:
+            den = theta[k] - D
+            small = np.abs(den) < floor
+            den[small] = np.where(den[small] < 0, -floor, floor)
+            T.append(R[k] / den)
+        T = np.asarray(T)
+        if V.shape[0] + T.shape[0] > max_space:
+            V = _orth_new(np.zeros((0, n)), Xr)
+            W = apply_A(V)
+            nmv += V.shape[0]
+            nrestart += 1
+            continue
+        Tn = _orth_new(V, T)
+        if Tn.shape[0] == 0:
+            break
+        V = np.vstack([V, Tn])
+        W = np.vstack([W, apply_A(Tn)])
+        nmv += Tn.shape[0]
+    return DavidsonResult(theta, Xr, rn, it, nmv, nrestart, False)
+
+
+def solve(f: Factors, nstates, block=None, tol=1e-6, max_space=None, max_iter=200):
+    """Lowest nstates of the TDA-risp problem by the Davidson procedure above."""
+    nov = f.nocc * f.nvir
+
+    def apply_A(V):
+        return matvec(f, V.reshape(-1, f.nocc, f.nvir)).reshape(-1, nov)
+
+    return davidson(apply_A, f.D, nstates, block, tol, max_space, max_iter)
+
+
+def fix_sign(X):
+    """Sign convention: the largest-magnitude component of each vector is positive."""
+    X = np.array(X, dtype=np.float64, copy=True).reshape(X.shape[0], -1)
+    idx = np.argmax(np.abs(X), axis=1)
+    s = np.sign(X[np.arange(X.shape[0]), idx])
+    s[s == 0] = 1.0
+    return X * s[:, None]

@@ -1,0 +1,197 @@
+/*
+ * tdarisp.h -- C ABI of the GB300 TDA-risp library (libtdarisp.so).
+ *
+ * The library computes the Tamm-Dancoff TDA-risp excitation energies of
+ * arXiv 2603.29257 on one GPU:
+ *
+ *   A_{ia,jb} = (e_a - e_i) d_ij d_ab + 2 (ia|jb) - c_x (ij|ab)          Sec. 2, Eq. TDA-risp
+ *
+ * with both electron-repulsion terms factorised through the minimal
+ * auxiliary basis (Sec. 2, Eqs. RI and g(r)): one s and one p primitive per
+ * non-hydrogen atom for the Coulomb term, the s primitive only for the
+ * exchange term, no auxiliary functions on hydrogen (Sec. 3.2), exchange
+ * restricted to the orbital-energy window |e| < window_ev (Sec. 3.2), and
+ * range-separated exchange with the operator (alpha + beta erf(omega r))/r
+ * used both in the three-centre integrals and in the metric (Sec. 3.2, Eqs.
+ * RSH and K_mia_RSH).  Davidson diagonalisation follows Sec. 3.3.
+ *
+ * Conventions
+ *   - Units: bohr and Hartree.
+ *   - AO function: chi(r) = sum_k coef[k] * Y(r - A) * exp(-exp[k] |r - A|^2);
+ *     the coefficients are used as given (normalisation folded in).
+ *     Y = 1 (l=0); x, y, z (l=1); for l=2 the real solid harmonics in the
+ *     order xy, yz, (2zz - xx - yy)/(2 sqrt 3), xz, (xx - yy)/2.
+ *   - Auxiliary function on atom A with exponent c: exp(-c |r-A|^2) (s) and
+ *     x, y, z times it (p), unnormalised; order per atom: s, px, py, pz.
+ *   - Matrices are row-major.  Trial vectors are X[m][nocc][nvir] with the
+ *     virtual index fastest.
+ *   - Orbital energies must be in ascending order; the exchange window is
+ *     then the contiguous block occ [nocc - noccK, nocc) x vir [0, nvirK).
+ *
+ * Ownership: the caller owns every buffer it passes; the library copies what
+ * it keeps.  The context owns its device memory until tr_destroy.  A pointer
+ * flagged "on_device" must be a device pointer of the context's device.
+ *
+ * Errors: every call returns TR_OK (0) or a negative code; tr_last_error()
+ * describes the last failure.  No call aborts the process.  Calls on one
+ * context must not run concurrently from several host threads.
+ */
+#ifndef TDARISP_H
+#define TDARISP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TR_OK 0
+#define TR_EINVAL (-1)    /* invalid argument or call order */
+#define TR_ENOMEM (-2)    /* device or pinned host allocation failed / budget exceeded */
+#define TR_ECUDA (-3)     /* CUDA runtime error */
+#define TR_ENOCONV (-4)   /* Davidson hit max_iter; outputs hold the best estimates */
+#define TR_ENOTPD (-5)    /* an auxiliary metric is not positive definite */
+
+#define TR_FP64 0
+
+typedef struct tr_ctx tr_ctx;
+
+/* One contracted AO shell (l = 0, 1 or 2). */
+typedef struct {
+    int atom;            /* index into the molecule's atoms */
+    int l;               /* angular momentum */
+    int nprim;           /* 1..16 */
+    const double *exp;   /* nprim exponents */
+    const double *coef;  /* nprim literal coefficients */
+} tr_shell;
+
+typedef struct {
+    /* exchange term: coefficient cx and operator (k_alpha + k_beta erf(omega r))/r.
+       Global hybrid: k_alpha = 1, k_beta = 0, omega = 0.
+       Range-separated (Sec. 3.2, Eq. RSH): cx = 1, k_alpha = SR fraction,
+       k_alpha + k_beta = LR fraction, omega > 0. */
+    double cx, k_alpha, k_beta, omega;
+    double window_ev;    /* exchange window in eV (Sec. 3.2); <= 0 disables it */
+    int aux_on_h;        /* 0 (default): no auxiliary functions on hydrogen (Sec. 3.2) */
+    int nstates;         /* number of excited states */
+    int block;           /* initial trial vectors (0: 2 * nstates) */
+    int max_space;       /* subspace size that triggers a restart (0: 20 * nstates) */
+    int max_iter;        /* Davidson iterations (0: 200) */
+    double tol;          /* residual 2-norm threshold per state */
+    int precision;       /* TR_FP64 */
+    double screen;       /* primitive-pair screening threshold (0: 1e-22) */
+    size_t hbm_budget;   /* bytes of device memory the context may hold (0: 90% of free) */
+    size_t aux_chunk_bytes; /* scratch for AO integral chunks (0: 2 GiB) */
+} tr_options;
+
+typedef struct {
+    int nao, nmo, nocc, nvir;
+    int naux_j, naux_k;  /* auxiliary functions for J (s+p) and K (s) */
+    int occ_k0, nocc_k;  /* exchange window: occupied [occ_k0, occ_k0 + nocc_k) */
+    int nvir_k;          /*                  virtual  [0, nvir_k) (relative to nocc) */
+    int npair;           /* AO shell pairs kept by screening */
+    int ntotal_pair;     /* AO shell pairs before screening */
+} tr_dims;
+
+typedef struct {
+    int niter, nmatvec, nrestart, converged;
+    double t_matvec_ms, t_ortho_ms, t_eigh_ms, t_other_ms;
+} tr_solve_info;
+
+/* Per-kernel timing, recorded with CUDA events on the context stream when
+   profiling is enabled. */
+typedef struct {
+    char name[32];
+    long launches;
+    double total_ms;
+    double flops;        /* algorithmic flops of all recorded launches */
+    double bytes;        /* algorithmic bytes of all recorded launches */
+} tr_prof_entry;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int tr_version(void);
+
+/* Fill opt with the defaults named above (cx = 0.25 global hybrid, 40 eV window,
+   5 states, tol 1e-5). */
+void tr_options_default(tr_options *opt);
+
+/* Create a context on the current CUDA device.  cuda_stream: a cudaStream_t
+   (NULL = the legacy default stream); all work of the context is ordered on it.
+   Errors: TR_EINVAL (opt NULL or out NULL), TR_ECUDA. */
+int tr_create(tr_ctx **out, const tr_options *opt, void *cuda_stream);
+
+/* Release every device and host resource of ctx (NULL is accepted). */
+void tr_destroy(tr_ctx *ctx);
+
+/* Text of the last error of ctx (never NULL; "" if none). */
+const char *tr_last_error(const tr_ctx *ctx);
+
+/* Replace the options (takes effect at the next tr_build / tr_solve). */
+int tr_set_options(tr_ctx *ctx, const tr_options *opt);
+
+/* Molecule (Sec. 2: geometry, AO and auxiliary basis).
+   Z[natm] nuclear charges; xyz[natm*3] in bohr; aux_exp[natm] exponent of the
+   auxiliary s/p primitive of each atom (<= 0: none; hydrogen gets none unless
+   aux_on_h); shells[nshell] AO shells.  Host pointers; the library copies them.
+   Errors: TR_EINVAL for l outside 0..2, nprim outside 1..16, atom out of range. */
+int tr_set_molecule(tr_ctx *ctx, int natm, const int *Z, const double *xyz,
+                    const double *aux_exp, int nshell, const tr_shell *shells);
+
+/* MO coefficients C[nao][nmo] (row-major) and orbital energies eps[nmo]
+   (ascending, Hartree); the first nocc orbitals are occupied.  on_device != 0:
+   both pointers are device pointers.  Errors: TR_EINVAL (sizes, order). */
+int tr_set_orbitals(tr_ctx *ctx, int nao, int nmo, int nocc, const double *C,
+                    const double *eps, int on_device);
+
+/* Sizes derived from the molecule, orbitals and options. */
+int tr_get_dims(tr_ctx *ctx, tr_dims *out);
+
+/* Build the factorised response operator (Sec. 2 Eq. RI, Sec. 3.2):
+   the metrics (P|Q) and their Cholesky factors, the three-centre integrals
+   (P|mu nu) over screened AO pairs, the Coulomb tensor (P|ia) and the window
+   exchange tensors T_ij^P = sum_Q (ij|Q)(Q|P)^-1 and T_ab^P = (ab|P).
+   Errors: TR_EINVAL (call order), TR_ENOMEM, TR_ENOTPD, TR_ECUDA. */
+int tr_build(tr_ctx *ctx);
+
+/* Raw AO three-centre integrals for auxiliary functions [p0, p0+np) of set
+   which (0 = Coulomb set s+p, Coulomb operator; 1 = exchange set s, exchange
+   operator) into out_dev[np][nao][nao] (device, full square; pairs dropped by
+   screening are zero).  Valid after tr_set_molecule. */
+int tr_int3c(tr_ctx *ctx, int which, int p0, int np, double *out_dev);
+
+/* Auxiliary metric of set which into out_dev[n][n] (device). */
+int tr_int2c(tr_ctx *ctx, int which, double *out_dev);
+
+/* Copy a built tensor to out (host, or device if on_device):
+   0: (P|ia)      [naux_j][nocc][nvir]
+   1: T_ij^P      [naux_k][nocc_k][nocc_k]   (inverse K metric applied)
+   2: T_ab^P      [naux_k][nvir_k][nvir_k]
+   3: e_a - e_i   [nocc][nvir] */
+int tr_get_tensor(tr_ctx *ctx, int which, double *out, int on_device);
+
+/* AX = A X for m trial vectors X[m][nocc][nvir] -> AX[m][nocc][nvir].
+   on_device != 0: device pointers, the call is asynchronous on the context
+   stream; otherwise host pointers and the call returns when AX is written.
+   X and AX must not overlap.  Requires tr_build. */
+int tr_matvec(tr_ctx *ctx, int m, const double *X, double *AX, int on_device);
+
+/* Davidson solve for the lowest nstates (Sec. 3.3).  Outputs (host, or device
+   if on_device): omega[nstates] (Hartree, ascending); X[nstates][nocc][nvir]
+   (may be NULL; unit norm, largest-magnitude component positive);
+   resid[nstates] (may be NULL).  info may be NULL.  Returns TR_ENOCONV when
+   max_iter is reached (outputs filled with the current estimates). */
+int tr_solve(tr_ctx *ctx, double *omega, double *X, double *resid, int on_device,
+             tr_solve_info *info);
+
+/* Kernel timing: enable (1) / disable (0) and reset the counters. */
+int tr_profile(tr_ctx *ctx, int enable);
+/* Copy up to max entries; returns the number of entries (>= 0) or an error. */
+int tr_profile_get(tr_ctx *ctx, tr_prof_entry *out, int max);
+/* Number of kernels this context has launched since creation. */
+long tr_launch_count(const tr_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDARISP_H */

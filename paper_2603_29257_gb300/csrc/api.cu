@@ -1,0 +1,248 @@
+// C ABI of libtdarisp (declared in include/tdarisp.h).  Every entry point
+// converts internal exceptions into a status code and keeps the message in
+// the context.
+#include <cstring>
+
+#include "ctx.cuh"
+
+namespace {
+
+template <typename F>
+int guarded(tr_ctx *c, F &&f)
+{
+    if (!c) return TR_EINVAL;
+    try {
+        c->err.clear();
+        return f();
+    } catch (const tr::Error &e) {
+        c->err = e.what();
+        return e.code;
+    } catch (const std::exception &e) {
+        c->err = e.what();
+        return TR_ECUDA;
+    }
+}
+
+void fill_defaults(tr_options *o)
+{
+    std::memset(o, 0, sizeof *o);
+    o->cx = 0.25;
+    o->k_alpha = 1.0;
+    o->k_beta = 0.0;
+    o->omega = 0.0;
+    o->window_ev = 40.0;
+    o->aux_on_h = 0;
+    o->nstates = 5;
+    o->block = 0;
+    o->max_space = 0;
+    o->max_iter = 0;
+    o->tol = 1e-5;
+    o->precision = TR_FP64;
+    o->screen = 1e-22;
+    o->hbm_budget = 0;
+    o->aux_chunk_bytes = 0;
+}
+
+void normalise_options(tr_options *o)
+{
+    if (!(o->screen > 0.0)) o->screen = 1e-22;
+    if (o->aux_chunk_bytes == 0) o->aux_chunk_bytes = (size_t)2 << 30;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tr_version(void) { return 100; }
+
+void tr_options_default(tr_options *opt)
+{
+    if (opt) fill_defaults(opt);
+}
+
+int tr_create(tr_ctx **out, const tr_options *opt, void *cuda_stream)
+{
+    if (!out || !opt) return TR_EINVAL;
+    *out = nullptr;
+    tr_ctx *c = nullptr;
+    try {
+        c = new tr_ctx();
+    } catch (...) {
+        return TR_ENOMEM;
+    }
+    int rc = guarded(c, [&]() {
+        TR_REQUIRE(opt->precision == TR_FP64, TR_EINVAL, "create: unsupported precision");
+        c->opt = *opt;
+        normalise_options(&c->opt);
+        c->st = (cudaStream_t)cuda_stream;
+        TR_CUDA(cudaGetDevice(&c->device));
+        size_t fr = 0, tot = 0;
+        TR_CUDA(cudaMemGetInfo(&fr, &tot));
+        c->budget.limit = opt->hbm_budget ? opt->hbm_budget : (size_t)(0.9 * (double)fr);
+        return TR_OK;
+    });
+    if (rc != TR_OK) {
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return TR_OK;
+}
+
+void tr_destroy(tr_ctx *ctx) { delete ctx; }
+
+const char *tr_last_error(const tr_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int tr_set_options(tr_ctx *ctx, const tr_options *opt)
+{
+    return guarded(ctx, [&]() {
+        TR_REQUIRE(opt, TR_EINVAL, "set_options: null options");
+        TR_REQUIRE(opt->precision == TR_FP64, TR_EINVAL, "set_options: unsupported precision");
+        bool rebuild = opt->cx != ctx->opt.cx || opt->k_alpha != ctx->opt.k_alpha ||
+                       opt->k_beta != ctx->opt.k_beta || opt->omega != ctx->opt.omega ||
+                       opt->window_ev != ctx->opt.window_ev || opt->aux_on_h != ctx->opt.aux_on_h ||
+                       opt->screen != ctx->opt.screen;
+        size_t limit = ctx->budget.limit;
+        ctx->opt = *opt;
+        normalise_options(&ctx->opt);
+        if (opt->hbm_budget) ctx->budget.limit = opt->hbm_budget;
+        else ctx->budget.limit = limit;
+        if (rebuild) {
+            ctx->built = false;
+            if (ctx->have_mol) tr::refresh_molecule(ctx);
+            if (ctx->have_orb) tr::refresh_window(ctx);
+        }
+        return TR_OK;
+    });
+}
+
+int tr_set_molecule(tr_ctx *ctx, int natm, const int *Z, const double *xyz, const double *aux_exp,
+                    int nshell, const tr_shell *shells)
+{
+    return guarded(ctx, [&]() {
+        tr::set_molecule(ctx, natm, Z, xyz, aux_exp, nshell, shells);
+        return TR_OK;
+    });
+}
+
+int tr_set_orbitals(tr_ctx *ctx, int nao, int nmo, int nocc, const double *C, const double *eps, int on_device)
+{
+    return guarded(ctx, [&]() {
+        tr::set_orbitals(ctx, nao, nmo, nocc, C, eps, on_device);
+        return TR_OK;
+    });
+}
+
+int tr_get_dims(tr_ctx *ctx, tr_dims *out)
+{
+    return guarded(ctx, [&]() {
+        TR_REQUIRE(out, TR_EINVAL, "get_dims: null output");
+        std::memset(out, 0, sizeof *out);
+        out->nao = ctx->nao;
+        out->nmo = ctx->nmo;
+        out->nocc = ctx->nocc;
+        out->nvir = ctx->nvir;
+        out->naux_j = ctx->nJ;
+        out->naux_k = ctx->nK;
+        out->occ_k0 = ctx->o0;
+        out->nocc_k = ctx->oK;
+        out->nvir_k = ctx->vK;
+        out->npair = (int)ctx->pl.pairs.size();
+        out->ntotal_pair = ctx->pl.ntotal;
+        return TR_OK;
+    });
+}
+
+int tr_build(tr_ctx *ctx)
+{
+    return guarded(ctx, [&]() {
+        tr::build(ctx);
+        return TR_OK;
+    });
+}
+
+int tr_int3c(tr_ctx *ctx, int which, int p0, int np, double *out_dev)
+{
+    return guarded(ctx, [&]() {
+        TR_REQUIRE(out_dev || np == 0, TR_EINVAL, "int3c: null output");
+        tr::int3c_ao(ctx, which, p0, np, out_dev);
+        return TR_OK;
+    });
+}
+
+int tr_int2c(tr_ctx *ctx, int which, double *out_dev)
+{
+    return guarded(ctx, [&]() {
+        TR_REQUIRE(out_dev, TR_EINVAL, "int2c: null output");
+        tr::int2c_aux(ctx, which, out_dev);
+        return TR_OK;
+    });
+}
+
+int tr_get_tensor(tr_ctx *ctx, int which, double *out, int on_device)
+{
+    return guarded(ctx, [&]() {
+        TR_REQUIRE(out, TR_EINVAL, "get_tensor: null output");
+        tr::get_tensor(ctx, which, out, on_device);
+        return TR_OK;
+    });
+}
+
+int tr_matvec(tr_ctx *ctx, int m, const double *X, double *AX, int on_device)
+{
+    return guarded(ctx, [&]() {
+        TR_REQUIRE(m >= 0, TR_EINVAL, "matvec: m must be >= 0");
+        TR_REQUIRE(ctx->built, TR_EINVAL, "matvec: call tr_build first");
+        if (m == 0) return TR_OK;
+        TR_REQUIRE(X && AX, TR_EINVAL, "matvec: null pointer");
+        const size_t n = (size_t)m * ctx->nov;
+        if (on_device) {
+            TR_REQUIRE(X + n <= AX || AX + n <= X, TR_EINVAL, "matvec: X and AX overlap");
+            tr::matvec(ctx, m, X, AX);
+            return TR_OK;
+        }
+        tr::DevBuf<double> dx, dax;
+        dx.alloc(n, &ctx->budget, "matvec input");
+        dax.alloc(n, &ctx->budget, "matvec output");
+        TR_CUDA(cudaMemcpyAsync(dx.p, X, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
+        tr::matvec(ctx, m, dx.p, dax.p);
+        TR_CUDA(cudaMemcpyAsync(AX, dax.p, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->st));
+        TR_CUDA(cudaStreamSynchronize(ctx->st));
+        return TR_OK;
+    });
+}
+
+int tr_solve(tr_ctx *ctx, double *omega, double *X, double *resid, int on_device, tr_solve_info *info)
+{
+    return guarded(ctx, [&]() { return tr::solve(ctx, omega, X, resid, on_device, info); });
+}
+
+int tr_profile(tr_ctx *ctx, int enable)
+{
+    return guarded(ctx, [&]() {
+        ctx->prof.reset();
+        ctx->prof.enabled = enable != 0;
+        return TR_OK;
+    });
+}
+
+int tr_profile_get(tr_ctx *ctx, tr_prof_entry *out, int max)
+{
+    return guarded(ctx, [&]() {
+        ctx->prof.flush();
+        int n = (int)ctx->prof.names.size();
+        for (int i = 0; i < n && i < max && out; ++i) {
+            std::memset(&out[i], 0, sizeof out[i]);
+            std::strncpy(out[i].name, ctx->prof.names[i].c_str(), sizeof(out[i].name) - 1);
+            out[i].launches = ctx->prof.n[i];
+            out[i].total_ms = ctx->prof.ms[i];
+            out[i].flops = ctx->prof.fl[i];
+            out[i].bytes = ctx->prof.by[i];
+        }
+        return n;
+    });
+}
+
+long tr_launch_count(const tr_ctx *ctx) { return ctx ? ctx->prof.launches : 0; }
+
+}  // extern "C"

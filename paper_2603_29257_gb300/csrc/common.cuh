@@ -1,0 +1,184 @@
+// Shared host/device utilities of libtdarisp (error handling, device buffers,
+// kernel timing).  Internal header; the public interface is tdarisp.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "tdarisp.h"
+
+namespace tr {
+
+struct Error : std::runtime_error {
+    int code;
+    Error(int c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+#define TR_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            throw ::tr::Error(TR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define TR_REQUIRE(cond, code, msg)                     \
+    do {                                                \
+        if (!(cond)) throw ::tr::Error((code), (msg));  \
+    } while (0)
+
+// Kernel launch bookkeeping: every launch goes through Prof::begin/end so the
+// context can count launches and, when profiling is on, time each kernel
+// with CUDA events on the launching stream.
+struct ProfRecord {
+    int kind;
+    cudaEvent_t a, b;
+    double flops, bytes;
+};
+
+struct Prof {
+    bool enabled = false;
+    long launches = 0;
+    std::vector<std::string> names;
+    std::vector<ProfRecord> pending;
+    std::vector<cudaEvent_t> pool;
+    // accumulated per kind
+    std::vector<long> n;
+    std::vector<double> ms, fl, by;
+
+    int kind(const char *name) {
+        for (size_t i = 0; i < names.size(); ++i)
+            if (names[i] == name) return (int)i;
+        names.push_back(name);
+        n.push_back(0);
+        ms.push_back(0);
+        fl.push_back(0);
+        by.push_back(0);
+        return (int)names.size() - 1;
+    }
+    cudaEvent_t ev() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        TR_CUDA(cudaEventCreate(&e));
+        return e;
+    }
+    // returns a token to pass to end()
+    int begin(cudaStream_t st, const char *name, double flops = 0, double bytes = 0) {
+        launches += 1;
+        if (!enabled) return -1;
+        ProfRecord r;
+        r.kind = kind(name);
+        r.a = ev();
+        r.b = ev();
+        r.flops = flops;
+        r.bytes = bytes;
+        TR_CUDA(cudaEventRecord(r.a, st));
+        pending.push_back(r);
+        return (int)pending.size() - 1;
+    }
+    void end(cudaStream_t st, int tok) {
+        if (tok < 0) return;
+        TR_CUDA(cudaEventRecord(pending[tok].b, st));
+    }
+    // resolve pending events (synchronises on the last one)
+    void flush() {
+        for (auto &r : pending) {
+            TR_CUDA(cudaEventSynchronize(r.b));
+            float t = 0.f;
+            TR_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+            n[r.kind] += 1;
+            ms[r.kind] += t;
+            fl[r.kind] += r.flops;
+            by[r.kind] += r.bytes;
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        pending.clear();
+    }
+    void reset() {
+        flush();
+        names.clear();
+        n.clear();
+        ms.clear();
+        fl.clear();
+        by.clear();
+    }
+    ~Prof() {
+        for (auto &r : pending) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+// Launch helper: checks the launch and records it.
+#define TR_LAUNCH(prof, stream, name, flops, bytes, ...)          \
+    do {                                                          \
+        int tok_ = (prof).begin((stream), (name), (flops), (bytes)); \
+        __VA_ARGS__;                                              \
+        TR_CUDA(cudaGetLastError());                              \
+        (prof).end((stream), tok_);                               \
+    } while (0)
+
+// Device allocation accounting against a byte budget.
+struct Budget {
+    size_t limit = 0, used = 0, peak = 0;
+};
+
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    Budget *budget = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) {
+            cudaFree(p);
+            if (budget) budget->used -= n * sizeof(T);
+        }
+        p = nullptr;
+        n = 0;
+    }
+    void alloc(size_t count, Budget *b, const char *what) {
+        if (count == n && p) return;
+        release();
+        if (count == 0) return;
+        size_t bytes = count * sizeof(T);
+        if (b && b->limit && b->used + bytes > b->limit)
+            throw Error(TR_ENOMEM, std::string("device budget exceeded allocating ") + what);
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            throw Error(TR_ENOMEM, std::string("cudaMalloc failed for ") + what + ": " +
+                                       cudaGetErrorString(e));
+        }
+        n = count;
+        budget = b;
+        if (b) {
+            b->used += bytes;
+            if (b->used > b->peak) b->peak = b->used;
+        }
+    }
+    // grow-only allocation for scratch space
+    void reserve(size_t count, Budget *b, const char *what) {
+        if (count <= n && p) return;
+        alloc(count, b, what);
+    }
+};
+
+inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+}  // namespace tr

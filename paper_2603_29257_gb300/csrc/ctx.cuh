@@ -1,0 +1,86 @@
+// Context of libtdarisp (internal): molecule, orbitals, built tensors and
+// workspaces of one TDA-risp problem on one GPU.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "ints.cuh"
+#include "linalg.cuh"
+
+struct tr_ctx {
+    tr_options opt{};
+    cudaStream_t st = nullptr;
+    std::string err;
+    tr::Prof prof;
+    tr::Budget budget;
+    int device = 0;
+
+    // molecule (Sec. 2: geometry, AO basis, auxiliary exponents)
+    bool have_mol = false;
+    std::vector<int> Z;
+    std::vector<double> xyz, aux_exp;
+    std::vector<tr::ShellDev> shells_h;
+    std::vector<double> pexp_h, pcoef_h;
+    int nao = 0;
+    tr::PairList pl;
+    tr::DevBuf<tr::ShellDev> shells;
+    tr::DevBuf<double> pexp, pcoef, boys;
+    tr::DevBuf<int2> pairs;
+    // auxiliary functions (Sec. 3.2): J = s + p on non-H atoms, K = s on non-H atoms
+    std::vector<tr::AuxDev> auxJ_h, auxK_h;  // in output order
+    int nJ = 0, nK = 0;
+    tr::DevBuf<tr::AuxDev> aux_ws;           // per-chunk class-sorted copy
+
+    // orbitals
+    bool have_orb = false;
+    int nmo = 0, nocc = 0, nvir = 0;
+    long long nov = 0;
+    tr::DevBuf<double> C, eps;
+    std::vector<double> eps_h;
+    int o0 = 0, oK = 0, vK = 0;              // exchange window (Sec. 3.2)
+
+    // built operator
+    bool built = false;
+    tr::DevBuf<double> Y;      // (P|ia) [nJ][nocc][nvir], Coulomb
+    tr::DevBuf<double> GinvJ;  // (P|Q)^-1 [nJ][nJ]
+    tr::DevBuf<double> GinvK;  // K-operator metric inverse [nK][nK]
+    tr::DevBuf<double> T2;     // T_ij^P stored [i][P][j]
+    tr::DevBuf<double> Tab;    // T_ab^P = (ab|P) [nK][vK][vK]
+    tr::DevBuf<double> D;      // e_a - e_i [nocc][nvir]
+    bool k_active = false;
+
+    // workspaces
+    tr::DevBuf<double> ws_split, ws_Z, ws_Z2, ws_Xw, ws_M;
+    tr::DevBuf<int> flag;
+    int mblk = 32;
+
+    // Davidson state
+    tr::DevBuf<double> V, W, Hs, Hw, Yev, Yw, theta, Xr, R, T, Tt, Cs, Ss, Gc, rn, part;
+    tr::DevBuf<int> idx_dev;
+    int dav_cap = 0;
+
+    ~tr_ctx()
+    {
+        if (st) cudaStreamSynchronize(st);
+    }
+};
+
+namespace tr {
+
+void set_molecule(tr_ctx *c, int natm, const int *Z, const double *xyz, const double *aux_exp,
+                  int nshell, const tr_shell *shells);
+void set_orbitals(tr_ctx *c, int nao, int nmo, int nocc, const double *C, const double *eps,
+                  int on_device);
+void refresh_molecule(tr_ctx *c);
+void refresh_window(tr_ctx *c);
+void build(tr_ctx *c);
+void int3c_ao(tr_ctx *c, int which, int p0, int np, double *out);
+void int2c_aux(tr_ctx *c, int which, double *out);
+void get_tensor(tr_ctx *c, int which, double *out, int on_device);
+// AX = A X for m device vectors (asynchronous on c->st)
+void matvec(tr_ctx *c, int m, const double *X, double *AX);
+int solve(tr_ctx *c, double *omega, double *X, double *resid, int on_device, tr_solve_info *info);
+
+}  // namespace tr

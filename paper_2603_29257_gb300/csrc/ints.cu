@@ -1,0 +1,412 @@
+// Three- and two-centre Gaussian integrals by the McMurchie-Davidson scheme.
+//
+// For an AO primitive pair (a at A, b at B) the product of Cartesian factors
+// is expanded in Hermite Gaussians at P = (aA + bB)/p with coefficients
+// E^{ij}_t; the auxiliary primitive at C is a Hermite Gaussian of order 0
+// (s) or 1 (p, coefficient 1/(2c)); the Coulomb-type integral of two Hermite
+// Gaussians is 2 pi^{5/2}/(p c sqrt(p+c)) (-1)^{ket order} R_{tuv}(P - C)
+// with R^n_{000} = (-2 rho)^n G_n and the usual Hermite recursion.
+// For (ka + kb erf(omega r))/r:  G_n = ka F_n(T) + kb s^{n+1/2} F_n(s T),
+// s = omega^2/(omega^2 + rho), T = rho |P-C|^2  (attenuated Boys function).
+//
+// One thread computes one (AO shell pair, auxiliary function) block,
+// contracting over primitive pairs in registers, then transforms d shells
+// to the real solid harmonics xy, yz, (2zz-xx-yy)/(2 sqrt3), xz, (xx-yy)/2.
+#include "ints.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace tr {
+
+// ---------------------------------------------------------------- Boys table
+
+void boys_table(std::vector<double> &tab)
+{
+    tab.assign((size_t)BOYS_NPTS * BOYS_NCOL, 0.0);
+    const int nmax = BOYS_NCOL - 1;
+    for (int k = 0; k < BOYS_NPTS; ++k) {
+        long double T = (long double)k * (long double)BOYS_DT;
+        // F_nmax(T) = e^{-T} sum_j (2T)^j / prod_{i=0..j} (2 nmax + 2i + 1)
+        long double term = 1.0L / (2 * nmax + 1), sum = term;
+        for (int j = 1; j < 2000; ++j) {
+            term *= 2.0L * T / (long double)(2 * nmax + 2 * j + 1);
+            sum += term;
+            if (term <= sum * 1e-21L) break;
+        }
+        long double e = expl(-T);
+        long double f[BOYS_NCOL];
+        f[nmax] = e * sum;
+        for (int n = nmax - 1; n >= 0; --n) f[n] = (2.0L * T * f[n + 1] + e) / (long double)(2 * n + 1);
+        for (int n = 0; n <= nmax; ++n) tab[(size_t)k * BOYS_NCOL + n] = (double)f[n];
+    }
+}
+
+// ---------------------------------------------------------------- pair list
+
+PairList make_pairs(const std::vector<ShellDev> &sh, const std::vector<double> &pexp,
+                    const std::vector<double> &pcoef, double screen)
+{
+    PairList pl;
+    std::vector<int2> cls[6];
+    const int nsh = (int)sh.size();
+    pl.ntotal = 0;
+    for (int i = 0; i < nsh; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            pl.ntotal += 1;
+            int a = i, b = j;
+            if (sh[a].l < sh[b].l) std::swap(a, b);
+            const ShellDev &A = sh[a], &B = sh[b];
+            double dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
+            double r2 = dx * dx + dy * dy + dz * dz;
+            double poly = std::pow(1.0 + std::sqrt(r2), A.l + B.l);
+            bool keep = false;
+            for (int u = 0; u < A.nprim && !keep; ++u)
+                for (int v = 0; v < B.nprim && !keep; ++v) {
+                    double ea = pexp[A.pstart + u], eb = pexp[B.pstart + v];
+                    double p = ea + eb;
+                    double k = std::fabs(pcoef[A.pstart + u] * pcoef[B.pstart + v]) *
+                               std::exp(-ea * eb / p * r2) * std::pow(M_PI / p, 1.5) * poly;
+                    keep = k >= screen;
+                }
+            if (!keep) continue;
+            int c = A.l == 0 ? 0 : (A.l == 1 ? 1 + B.l : 3 + B.l);
+            cls[c].push_back(make_int2(a, b));
+        }
+    }
+    pl.off[0] = 0;
+    for (int c = 0; c < 6; ++c) {
+        // group by primitive counts to keep warps uniform
+        std::stable_sort(cls[c].begin(), cls[c].end(), [&](const int2 &x, const int2 &y) {
+            int kx = sh[x.x].nprim * 8 + sh[x.y].nprim, ky = sh[y.x].nprim * 8 + sh[y.y].nprim;
+            return kx < ky;
+        });
+        pl.pairs.insert(pl.pairs.end(), cls[c].begin(), cls[c].end());
+        pl.off[c + 1] = (int)pl.pairs.size();
+    }
+    return pl;
+}
+
+namespace {
+
+constexpr double PI_D = 3.14159265358979323846;
+constexpr double TWO_PI_52 = 34.98683665524972;  // 2 pi^{5/2}
+
+__host__ __device__ constexpr int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+
+// exponent of direction d in Cartesian component k of shell l
+// (l=1: x,y,z; l=2: xx,xy,xz,yy,yz,zz)
+__host__ __device__ constexpr int cexp(int l, int k, int d)
+{
+    return l == 0 ? 0
+         : l == 1 ? (k == d ? 1 : 0)
+         : (d == 0 ? (k == 0 ? 2 : (k == 1 || k == 2) ? 1 : 0)
+          : d == 1 ? (k == 3 ? 2 : (k == 1 || k == 4) ? 1 : 0)
+                   : (k == 5 ? 2 : (k == 2 || k == 4) ? 1 : 0));
+}
+
+template <int L>
+__device__ __forceinline__ void boys_eval(double T, const double *__restrict__ tab, double *F)
+{
+    if (T < BOYS_TMAX) {
+        int k = __double2int_rn(T * (1.0 / BOYS_DT));
+        double dT = k * BOYS_DT - T;
+        const double *f = tab + k * BOYS_NCOL + L;
+        // F_L(T) = sum_j F_{L+j}(T_k) (T_k - T)^j / j!
+        double s = __ldg(f + 6);
+#pragma unroll
+        for (int j = 5; j >= 0; --j) s = fma(s, dT * (1.0 / (j + 1)), __ldg(f + j));
+        F[L] = s;
+        if (L > 0) {
+            double e = exp(-T);
+#pragma unroll
+            for (int n = L - 1; n >= 0; --n) F[n] = fma(2.0 * T, F[n + 1], e) * (1.0 / (2 * n + 1));
+        }
+    } else {
+        double e = exp(-T);
+        F[0] = 0.5 * sqrt(PI_D / T);
+        double h = 0.5 / T;
+#pragma unroll
+        for (int n = 0; n < L; ++n) F[n + 1] = ((2 * n + 1) * F[n] - e) * h;
+    }
+}
+
+// R^n_000 = (-2 rho)^n G_n for the operator (ka + kb erf(omega r))/r
+template <int L>
+__device__ __forceinline__ void coulomb_aux(double rho, double T, double ka, double kb, double omega,
+                                            const double *__restrict__ tab, double *Rn)
+{
+    double F[L + 1];
+    double G[L + 1];
+#pragma unroll
+    for (int n = 0; n <= L; ++n) G[n] = 0.0;
+    if (ka != 0.0) {
+        boys_eval<L>(T, tab, F);
+#pragma unroll
+        for (int n = 0; n <= L; ++n) G[n] = ka * F[n];
+    }
+    if (kb != 0.0 && omega > 0.0) {
+        double s = omega * omega / (omega * omega + rho);
+        boys_eval<L>(s * T, tab, F);
+        double f = kb * sqrt(s);
+#pragma unroll
+        for (int n = 0; n <= L; ++n) {
+            G[n] = fma(f, F[n], G[n]);
+            f *= s;
+        }
+    }
+    double m = 1.0;
+#pragma unroll
+    for (int n = 0; n <= L; ++n) {
+        Rn[n] = m * G[n];
+        m *= -2.0 * rho;
+    }
+}
+
+// Hermite Coulomb integrals R_{tuv} (n = 0 level) for t+u+v <= L, in place.
+template <int L>
+__device__ __forceinline__ void hermite_R(double X, double Y, double Z, const double *Rn,
+                                          double (&R)[L + 1][L + 1][L + 1])
+{
+    R[0][0][0] = Rn[L];
+#pragma unroll
+    for (int n = L - 1; n >= 0; --n) {
+#pragma unroll
+        for (int s = L - n; s >= 1; --s) {
+#pragma unroll
+            for (int t = s; t >= 0; --t) {
+#pragma unroll
+                for (int u = s - t; u >= 0; --u) {
+                    const int v = s - t - u;
+                    if (t > 0)
+                        R[t][u][v] = (t > 1 ? (t - 1) * R[t > 1 ? t - 2 : 0][u][v] : 0.0) + X * R[t - 1][u][v];
+                    else if (u > 0)
+                        R[0][u][v] = (u > 1 ? (u - 1) * R[0][u > 1 ? u - 2 : 0][v] : 0.0) + Y * R[0][u - 1][v];
+                    else
+                        R[0][0][v] = (v > 1 ? (v - 1) * R[0][0][v > 1 ? v - 2 : 0] : 0.0) + Z * R[0][0][v - 1];
+                }
+            }
+        }
+        R[0][0][0] = Rn[n];
+    }
+}
+
+// Hermite expansion coefficients E^{ij}_t of one direction
+template <int LA, int LB>
+__device__ __forceinline__ void hermite_E(double PA, double PB, double inv2p,
+                                          double (&E)[LA + 1][LB + 1][LA + LB + 1])
+{
+#pragma unroll
+    for (int i = 0; i <= LA; ++i)
+#pragma unroll
+        for (int j = 0; j <= LB; ++j)
+#pragma unroll
+            for (int t = 0; t <= LA + LB; ++t) E[i][j][t] = 0.0;
+    E[0][0][0] = 1.0;
+#pragma unroll
+    for (int i = 0; i < LA; ++i)
+#pragma unroll
+        for (int t = 0; t <= i + 1; ++t)
+            E[i + 1][0][t] = (t > 0 ? inv2p * E[i][0][t > 0 ? t - 1 : 0] : 0.0) + PA * E[i][0][t] +
+                             (t + 1 <= i ? (t + 1) * E[i][0][t + 1 <= i ? t + 1 : 0] : 0.0);
+#pragma unroll
+    for (int j = 0; j < LB; ++j)
+#pragma unroll
+        for (int i = 0; i <= LA; ++i)
+#pragma unroll
+            for (int t = 0; t <= i + j + 1; ++t)
+                E[i][j + 1][t] = (t > 0 ? inv2p * E[i][j][t > 0 ? t - 1 : 0] : 0.0) + PB * E[i][j][t] +
+                                 (t + 1 <= i + j ? (t + 1) * E[i][j][t + 1 <= i + j ? t + 1 : 0] : 0.0);
+}
+
+// spherical transform of a d shell: row s, Cartesian k
+__device__ __forceinline__ double d_sph(int s, int k)
+{
+    const double r3 = 0.57735026918962576451;  // 1/sqrt(3)
+    switch (s) {
+        case 0: return k == 1 ? 1.0 : 0.0;
+        case 1: return k == 4 ? 1.0 : 0.0;
+        case 2: return k == 5 ? r3 : ((k == 0 || k == 3) ? -0.5 * r3 : 0.0);
+        case 3: return k == 2 ? 1.0 : 0.0;
+        default: return k == 0 ? 0.5 : (k == 3 ? -0.5 : 0.0);
+    }
+}
+
+template <int LA, int LB, int CD>
+__global__ void __launch_bounds__(128)
+    int3c_kernel(const ShellDev *__restrict__ sh, const double *__restrict__ pexp,
+                 const double *__restrict__ pcoef, const int2 *__restrict__ pairs, int npair,
+                 const AuxDev *__restrict__ aux, int nao, double *__restrict__ out, double ka,
+                 double kb, double omega, const double *__restrict__ boys, double screen)
+{
+    constexpr int LC = CD >= 0 ? 1 : 0;
+    constexpr int L = LA + LB + LC;
+    constexpr int NCA = ncart(LA), NCB = ncart(LB);
+    constexpr int DX = CD == 0, DY = CD == 1, DZ = CD == 2;
+    const int ip = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ip >= npair) return;
+    const AuxDev c = aux[blockIdx.y];
+    const int2 pr = pairs[ip];
+    const ShellDev A = sh[pr.x], B = sh[pr.y];
+
+    double acc[NCA][NCB];
+#pragma unroll
+    for (int i = 0; i < NCA; ++i)
+#pragma unroll
+        for (int j = 0; j < NCB; ++j) acc[i][j] = 0.0;
+
+    const double ABx = A.x - B.x, ABy = A.y - B.y, ABz = A.z - B.z;
+    const double AB2 = ABx * ABx + ABy * ABy + ABz * ABz;
+    double poly = 1.0;
+    {
+        double r = 1.0 + sqrt(AB2);
+#pragma unroll
+        for (int i = 0; i < LA + LB; ++i) poly *= r;
+    }
+    const double ce = c.e;
+
+    for (int ia = 0; ia < A.nprim; ++ia) {
+        const double a = pexp[A.pstart + ia], ca = pcoef[A.pstart + ia];
+        for (int ib = 0; ib < B.nprim; ++ib) {
+            const double b = pexp[B.pstart + ib], cb = pcoef[B.pstart + ib];
+            const double p = a + b, ip_ = 1.0 / p;
+            const double Kab = ca * cb * exp(-a * b * ip_ * AB2);
+            const double vol = PI_D * ip_ * sqrt(PI_D * ip_);
+            if (fabs(Kab) * vol * poly < screen) continue;
+            const double Px = (a * A.x + b * B.x) * ip_, Py = (a * A.y + b * B.y) * ip_,
+                         Pz = (a * A.z + b * B.z) * ip_;
+            double Ex[LA + 1][LB + 1][LA + LB + 1], Ey[LA + 1][LB + 1][LA + LB + 1],
+                Ez[LA + 1][LB + 1][LA + LB + 1];
+            hermite_E<LA, LB>(Px - A.x, Px - B.x, 0.5 * ip_, Ex);
+            hermite_E<LA, LB>(Py - A.y, Py - B.y, 0.5 * ip_, Ey);
+            hermite_E<LA, LB>(Pz - A.z, Pz - B.z, 0.5 * ip_, Ez);
+            const double rho = p * ce / (p + ce);
+            const double X = Px - c.x, Y = Py - c.y, Z = Pz - c.z;
+            double Rn[L + 1];
+            coulomb_aux<L>(rho, rho * (X * X + Y * Y + Z * Z), ka, kb, omega, boys, Rn);
+            double R[L + 1][L + 1][L + 1];
+            hermite_R<L>(X, Y, Z, Rn, R);
+            double pref = TWO_PI_52 / (p * ce * sqrt(p + ce)) * Kab;
+            if (LC) pref *= -0.5 / ce;
+#pragma unroll
+            for (int ka_ = 0; ka_ < NCA; ++ka_) {
+                constexpr int dummy = 0;
+                (void)dummy;
+#pragma unroll
+                for (int kb_ = 0; kb_ < NCB; ++kb_) {
+                    const int ax = cexp(LA, ka_, 0), ay = cexp(LA, ka_, 1), az = cexp(LA, ka_, 2);
+                    const int bx = cexp(LB, kb_, 0), by = cexp(LB, kb_, 1), bz = cexp(LB, kb_, 2);
+                    double s = 0.0;
+#pragma unroll
+                    for (int t = 0; t <= ax + bx; ++t)
+#pragma unroll
+                        for (int u = 0; u <= ay + by; ++u) {
+                            double su = 0.0;
+#pragma unroll
+                            for (int v = 0; v <= az + bz; ++v)
+                                su = fma(Ez[az][bz][v], R[t + DX][u + DY][v + DZ], su);
+                            s = fma(Ex[ax][bx][t] * Ey[ay][by][u], su, s);
+                        }
+                    acc[ka_][kb_] = fma(pref, s, acc[ka_][kb_]);
+                }
+            }
+        }
+    }
+
+    constexpr int NSA = 2 * LA + 1, NSB = 2 * LB + 1;
+    double* o = out + (long long)c.out * nao * nao;
+#pragma unroll
+    for (int sa = 0; sa < NSA; ++sa) {
+#pragma unroll
+        for (int sb = 0; sb < NSB; ++sb) {
+            double v = 0.0;
+#pragma unroll
+            for (int ka_ = 0; ka_ < NCA; ++ka_) {
+                const double wa = LA == 2 ? d_sph(sa, ka_) : (ka_ == sa ? 1.0 : 0.0);
+                if (wa == 0.0) continue;
+#pragma unroll
+                for (int kb_ = 0; kb_ < NCB; ++kb_) {
+                    const double wb = LB == 2 ? d_sph(sb, kb_) : (kb_ == sb ? 1.0 : 0.0);
+                    if (wb == 0.0) continue;
+                    v = fma(wa * wb, acc[ka_][kb_], v);
+                }
+            }
+            const int mu = A.ao + sa, nu = B.ao + sb;
+            o[(long long)mu * nao + nu] = v;
+            o[(long long)nu * nao + mu] = v;
+        }
+    }
+}
+
+template <int LA, int LB>
+void launch_pair_class(Prof &prof, cudaStream_t st, int cls, const ShellDev *sh, const double *pexp,
+                       const double *pcoef, const int2 *pairs, int npair, const AuxDev *aux,
+                       const int *aoff, int nao, double *out, double ka, double kb, double omega,
+                       const double *boys, double screen)
+{
+    static const char *names[6] = {"int3c_ss", "int3c_ps", "int3c_pp", "int3c_ds", "int3c_dp", "int3c_dd"};
+    for (int cd = -1; cd <= 2; ++cd) {
+        int n = aoff[cd + 2] - aoff[cd + 1];
+        if (n <= 0 || npair <= 0) continue;
+        dim3 grid(cdiv(npair, 128), n);
+        const AuxDev *a = aux + aoff[cd + 1];
+        double bytes = 8.0 * 2.0 * npair * n * (2 * LA + 1) * (2 * LB + 1);
+        int tok = prof.begin(st, names[cls], 0, bytes);
+        switch (cd) {
+            case -1: int3c_kernel<LA, LB, -1><<<grid, 128, 0, st>>>(sh, pexp, pcoef, pairs, npair, a, nao, out, ka, kb, omega, boys, screen); break;
+            case 0: int3c_kernel<LA, LB, 0><<<grid, 128, 0, st>>>(sh, pexp, pcoef, pairs, npair, a, nao, out, ka, kb, omega, boys, screen); break;
+            case 1: int3c_kernel<LA, LB, 1><<<grid, 128, 0, st>>>(sh, pexp, pcoef, pairs, npair, a, nao, out, ka, kb, omega, boys, screen); break;
+            default: int3c_kernel<LA, LB, 2><<<grid, 128, 0, st>>>(sh, pexp, pcoef, pairs, npair, a, nao, out, ka, kb, omega, boys, screen); break;
+        }
+        TR_CUDA(cudaGetLastError());
+        prof.end(st, tok);
+    }
+}
+
+__global__ void int2c_kernel(const AuxDev *__restrict__ aux, int n, double ka, double kb, double omega,
+                             const double *__restrict__ boys, double *__restrict__ out)
+{
+    const int i = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const AuxDev P = aux[i], Q = aux[j];
+    const double a = P.e, b = Q.e;
+    const double rho = a * b / (a + b);
+    const double d[3] = {P.x - Q.x, P.y - Q.y, P.z - Q.z};
+    double Rn[3];
+    coulomb_aux<2>(rho, rho * (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]), ka, kb, omega, boys, Rn);
+    double v;
+    if (P.comp < 0 && Q.comp < 0)
+        v = Rn[0];
+    else if (Q.comp < 0)
+        v = (0.5 / a) * d[P.comp] * Rn[1];
+    else if (P.comp < 0)
+        v = -(0.5 / b) * d[Q.comp] * Rn[1];
+    else
+        v = -(0.25 / (a * b)) * ((P.comp == Q.comp ? Rn[1] : 0.0) + d[P.comp] * d[Q.comp] * Rn[2]);
+    out[(long long)P.out * n + Q.out] = TWO_PI_52 / (a * b * sqrt(a + b)) * v;
+}
+
+}  // namespace
+
+void int3c(Prof &prof, cudaStream_t st, const ShellDev *sh, const double *pexp, const double *pcoef,
+           const int2 *pairs, const int *off, const AuxDev *aux, const int *aoff, int nao,
+           double *out, double ka, double kb, double omega, const double *boys, double screen)
+{
+    launch_pair_class<0, 0>(prof, st, 0, sh, pexp, pcoef, pairs + off[0], off[1] - off[0], aux, aoff, nao, out, ka, kb, omega, boys, screen);
+    launch_pair_class<1, 0>(prof, st, 1, sh, pexp, pcoef, pairs + off[1], off[2] - off[1], aux, aoff, nao, out, ka, kb, omega, boys, screen);
+    launch_pair_class<1, 1>(prof, st, 2, sh, pexp, pcoef, pairs + off[2], off[3] - off[2], aux, aoff, nao, out, ka, kb, omega, boys, screen);
+    launch_pair_class<2, 0>(prof, st, 3, sh, pexp, pcoef, pairs + off[3], off[4] - off[3], aux, aoff, nao, out, ka, kb, omega, boys, screen);
+    launch_pair_class<2, 1>(prof, st, 4, sh, pexp, pcoef, pairs + off[4], off[5] - off[4], aux, aoff, nao, out, ka, kb, omega, boys, screen);
+    launch_pair_class<2, 2>(prof, st, 5, sh, pexp, pcoef, pairs + off[5], off[6] - off[5], aux, aoff, nao, out, ka, kb, omega, boys, screen);
+}
+
+void int2c(Prof &prof, cudaStream_t st, const AuxDev *aux, int n, double ka, double kb, double omega,
+           const double *boys, double *out)
+{
+    if (n <= 0) return;
+    TR_LAUNCH(prof, st, "int2c", 0, 8.0 * n * n,
+              int2c_kernel<<<dim3(cdiv(n, 128), n), 128, 0, st>>>(aux, n, ka, kb, omega, boys, out));
+}
+
+}  // namespace tr

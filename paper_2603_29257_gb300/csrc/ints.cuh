@@ -1,0 +1,56 @@
+// Gaussian integral kernels of libtdarisp (internal): Boys table, three-
+// and two-centre two-electron integrals for the operator
+// (ka + kb erf(omega r))/r over spherical AO shells (l <= 2) and
+// uncontracted auxiliary s/p primitives.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace tr {
+
+struct ShellDev {
+    double x, y, z;
+    int l, nprim, pstart, ao;
+};
+
+// auxiliary function: comp = -1 for s, 0/1/2 for p_x/p_y/p_z; out = row index
+struct AuxDev {
+    double x, y, z, e;
+    int comp, out;
+};
+
+constexpr int BOYS_NPTS = 1281;          // T = 0 .. 40 step 1/32
+constexpr int BOYS_NCOL = 13;            // F_0 .. F_12
+constexpr double BOYS_DT = 1.0 / 32.0;
+constexpr double BOYS_TMAX = 40.0;
+
+// Host: tabulate F_n(T_k) for the device Taylor interpolation.
+void boys_table(std::vector<double> &tab);
+
+// AO shell pairs grouped by angular class (la, lb), la >= lb, in the order
+// (0,0) (1,0) (1,1) (2,0) (2,1) (2,2).  off[c] .. off[c+1] index pairs[].
+struct PairList {
+    std::vector<int2> pairs;
+    int off[7];
+    int ntotal;
+};
+
+// Host: screened pair list.  A primitive pair is kept when
+// |c_a c_b| exp(-ab/(a+b) |AB|^2) (pi/(a+b))^{3/2} (1 + |AB|)^{la+lb} >= screen.
+PairList make_pairs(const std::vector<ShellDev> &sh, const std::vector<double> &pexp,
+                    const std::vector<double> &pcoef, double screen);
+
+// out[f][mu][nu] (+= nothing: caller zeroes) for auxiliary functions aux[0..naux)
+// of which aux_class_off[c]..aux_class_off[c+1] have comp = c - 1.
+void int3c(Prof &prof, cudaStream_t st, const ShellDev *sh, const double *pexp, const double *pcoef,
+           const int2 *pairs, const int *pair_off, const AuxDev *aux, const int *aux_class_off,
+           int nao, double *out, double ka, double kb, double omega, const double *boys,
+           double screen);
+
+// out[i][j] = (P_i|Q_j) for auxiliary functions aux[0..n) with out index aux[i].out.
+void int2c(Prof &prof, cudaStream_t st, const AuxDev *aux, int n, double ka, double kb, double omega,
+           const double *boys, double *out);
+
+}  // namespace tr

@@ -1,0 +1,41 @@
+// FP64 dense linear algebra kernels of libtdarisp (internal).
+#pragma once
+
+#include "common.cuh"
+
+namespace tr {
+
+// Two-level batch description: batch b = b1 * n2 + b2, operand offset
+// b1 * s?1 + b2 * s?2 (elements).
+struct Batch {
+    int n1 = 1, n2 = 1;
+    long long sA1 = 0, sA2 = 0, sB1 = 0, sB2 = 0, sC1 = 0, sC2 = 0;
+    int count() const { return n1 * n2; }
+};
+
+// C = alpha * op(A) * op(B) + beta * C, op(A) M x K, op(B) K x N, row-major.
+//   ta = false: A[m*lda + k]; ta = true: A[k*lda + m]
+//   tb = false: B[k*ldb + n]; tb = true: B[n*ldb + k]
+// beta == 0 never reads C.  Splits K across CTAs when the output is small;
+// ws/ws_elems is scratch for the partial sums (may be null: no split).
+void dgemm(Prof &prof, cudaStream_t st, const char *name, bool ta, bool tb, int M, int N, int K,
+           double alpha, const double *A, long long lda, const double *B, long long ldb,
+           double beta, double *C, long long ldc, const Batch &bt, double *ws, size_t ws_elems);
+
+// Lower Cholesky factor in place (upper triangle untouched): G = L L^T.
+// flag (device int) is set to 1 + column on the first non-positive pivot.
+void cholesky(Prof &prof, cudaStream_t st, double *G, int n, int *flag);
+
+// Ginv = (L L^T)^-1 from the lower Cholesky factor L (n x n).
+void chol_inverse(Prof &prof, cudaStream_t st, const double *L, int n, double *Ginv, double *work);
+
+// Eigen-decomposition of a symmetric k x k matrix (ld = k, destroyed) by
+// parallel cyclic Jacobi in one thread block: w ascending, Y[j*k + r] = j-th
+// component of eigenvector r.  flag (device int) set to 1 if not converged.
+void jacobi_eigh(Prof &prof, cudaStream_t st, double *H, int k, double *w, double *Y,
+                 double *work, int *flag);
+
+// out[i] = sum over rows of a[r][i] for a[nrows][n] (deterministic).
+void sum_rows(Prof &prof, cudaStream_t st, const double *a, int nrows, int n, double *out);
+
+}  // namespace tr

@@ -1,0 +1,492 @@
+// TDA-risp operator on the GPU: molecule and orbital set-up, the build of
+// the factorised operator and the matrix-vector product.
+//
+//   A X = (e_a - e_i) X + 2 J - c_x K                                Sec. 2, Eq. TDA-risp
+//   J_mia = sum_P (P|ia) Zt_Pm,  Zt = (P|Q)^-1 Z,  Z_Qm = sum_jb (Q|jb) X_mjb
+//          (RI in the Coulomb metric, Sec. 2 Eq. RI; the paper's J engine
+//           applies (P|Q)^-1 to the small aux-by-state intermediate, Sec. 3.1)
+//   K_mia = sum_P sum_j T_ij^P M^P_mja,  M^P_mja = sum_b T_ab^P X_mjb,
+//          T_ij^P = sum_Q (ij|Q)(Q|P)^-1,  T_ab^P = (ab|P)             Sec. 3.2
+//   with i, j, a, b inside the exchange window and K zero outside it.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ctx.cuh"
+
+namespace tr {
+namespace {
+
+constexpr double HARTREE_EV = 27.211386245988;
+
+__global__ void diag_kernel(const double *__restrict__ D, const double *__restrict__ X,
+                            double *__restrict__ AX, long long nov, int m)
+{
+    long long tot = nov * m;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x)
+        AX[t] = D[t % nov] * X[t];
+}
+
+__global__ void gather_window(const double *__restrict__ X, double *__restrict__ Xw, int m, int nocc,
+                              int nvir, int o0, int oK, int vK)
+{
+    long long tot = (long long)m * oK * vK;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        int b = (int)(t % vK);
+        long long r = t / vK;
+        int j = (int)(r % oK);
+        int mm = (int)(r / oK);
+        Xw[t] = X[((long long)mm * nocc + o0 + j) * nvir + b];
+    }
+}
+
+__global__ void orbital_diff(const double *__restrict__ eps, int nocc, int nvir, double *__restrict__ D)
+{
+    long long tot = (long long)nocc * nvir;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        int a = (int)(t % nvir), i = (int)(t / nvir);
+        D[t] = eps[nocc + a] - eps[i];
+    }
+}
+
+// [P][i][j] <- [i][P][j]
+__global__ void unpermute_T2(const double *__restrict__ T2, int nK, int oK, double *__restrict__ out)
+{
+    long long tot = (long long)nK * oK * oK;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        int j = (int)(t % oK);
+        long long r = t / oK;
+        int i = (int)(r % oK);
+        int P = (int)(r / oK);
+        out[t] = T2[((long long)i * nK + P) * oK + j];
+    }
+}
+
+unsigned grid_for(long long n) { return (unsigned)std::max<long long>(1, std::min<long long>(cdiv(n, 256), 152 * 16)); }
+
+// class-sorted copy of auxiliary functions with out index in [p0, p0+np);
+// cls[0..4] offsets for comp -1, 0, 1, 2
+void aux_chunk(tr_ctx *c, const std::vector<AuxDev> &all, int p0, int np, int cls[5])
+{
+    std::vector<AuxDev> sorted;
+    cls[0] = 0;
+    for (int cd = -1; cd <= 2; ++cd) {
+        for (const AuxDev &a : all)
+            if (a.comp == cd && a.out >= p0 && a.out < p0 + np) {
+                AuxDev b = a;
+                b.out -= p0;
+                sorted.push_back(b);
+            }
+        cls[cd + 2] = (int)sorted.size();
+    }
+    c->aux_ws.reserve(std::max<size_t>(sorted.size(), 1), &c->budget, "aux list");
+    if (!sorted.empty())
+        TR_CUDA(cudaMemcpyAsync(c->aux_ws.p, sorted.data(), sizeof(AuxDev) * sorted.size(),
+                                cudaMemcpyHostToDevice, c->st));
+}
+
+void compute_int3c(tr_ctx *c, const std::vector<AuxDev> &all, int p0, int np, double *out,
+                   double ka, double kb, double omega)
+{
+    int cls[5];
+    aux_chunk(c, all, p0, np, cls);
+    TR_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * (size_t)np * c->nao * c->nao, c->st));
+    int3c(c->prof, c->st, c->shells.p, c->pexp.p, c->pcoef.p, c->pairs.p, c->pl.off, c->aux_ws.p,
+          cls, c->nao, out, ka, kb, omega, c->boys.p, c->opt.screen);
+    // the aux list lives in aux_ws until the kernels have read it
+    TR_CUDA(cudaStreamSynchronize(c->st));
+}
+
+void metric(tr_ctx *c, const std::vector<AuxDev> &all, double ka, double kb, double omega, double *G)
+{
+    int n = (int)all.size();
+    if (n == 0) return;
+    c->aux_ws.reserve(n, &c->budget, "aux list");
+    TR_CUDA(cudaMemcpyAsync(c->aux_ws.p, all.data(), sizeof(AuxDev) * n, cudaMemcpyHostToDevice, c->st));
+    int2c(c->prof, c->st, c->aux_ws.p, n, ka, kb, omega, c->boys.p, G);
+    TR_CUDA(cudaStreamSynchronize(c->st));
+}
+
+// Cholesky factor and inverse of a metric; throws TR_ENOTPD if not positive definite
+void metric_inverse(tr_ctx *c, double *G, int n, double *Ginv, const char *what)
+{
+    if (n == 0) return;
+    DevBuf<double> work;
+    work.alloc((size_t)n * n, &c->budget, "metric work");
+    TR_CUDA(cudaMemsetAsync(c->flag.p, 0, sizeof(int), c->st));
+    cholesky(c->prof, c->st, G, n, c->flag.p);
+    int h = 0;
+    TR_CUDA(cudaMemcpyAsync(&h, c->flag.p, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    TR_CUDA(cudaStreamSynchronize(c->st));
+    if (h) throw Error(TR_ENOTPD, std::string(what) + " metric is not positive definite (column " +
+                                      std::to_string(h - 1) + ")");
+    chol_inverse(c->prof, c->st, G, n, Ginv, work.p);
+    TR_CUDA(cudaStreamSynchronize(c->st));
+}
+
+}  // namespace
+
+
+void refresh_molecule(tr_ctx *c)
+{
+    const int natm = (int)c->Z.size();
+    // auxiliary functions (Sec. 3.2): J = s, px, py, pz and K = s on every atom that
+    // carries an exponent, hydrogen excluded unless aux_on_h
+    c->auxJ_h.clear();
+    c->auxK_h.clear();
+    for (int a = 0; a < natm; ++a) {
+        if (!(c->aux_exp[a] > 0.0)) continue;
+        if (c->Z[a] == 1 && !c->opt.aux_on_h) continue;
+        int j0 = (int)c->auxJ_h.size();
+        for (int comp = -1; comp <= 2; ++comp) {
+            AuxDev f;
+            f.x = c->xyz[3 * a];
+            f.y = c->xyz[3 * a + 1];
+            f.z = c->xyz[3 * a + 2];
+            f.e = c->aux_exp[a];
+            f.comp = comp;
+            f.out = j0 + comp + 1;
+            c->auxJ_h.push_back(f);
+            if (comp < 0) {
+                f.out = (int)c->auxK_h.size();
+                c->auxK_h.push_back(f);
+            }
+        }
+    }
+    c->nJ = (int)c->auxJ_h.size();
+    c->nK = (int)c->auxK_h.size();
+    c->pl = make_pairs(c->shells_h, c->pexp_h, c->pcoef_h, c->opt.screen);
+    c->shells.alloc(c->shells_h.size(), &c->budget, "shells");
+    c->pexp.alloc(c->pexp_h.size(), &c->budget, "primitives");
+    c->pcoef.alloc(c->pcoef_h.size(), &c->budget, "primitives");
+    c->pairs.alloc(std::max<size_t>(c->pl.pairs.size(), 1), &c->budget, "pairs");
+    TR_CUDA(cudaMemcpy(c->shells.p, c->shells_h.data(), sizeof(ShellDev) * c->shells_h.size(), cudaMemcpyHostToDevice));
+    TR_CUDA(cudaMemcpy(c->pexp.p, c->pexp_h.data(), sizeof(double) * c->pexp_h.size(), cudaMemcpyHostToDevice));
+    TR_CUDA(cudaMemcpy(c->pcoef.p, c->pcoef_h.data(), sizeof(double) * c->pcoef_h.size(), cudaMemcpyHostToDevice));
+    if (!c->pl.pairs.empty())
+        TR_CUDA(cudaMemcpy(c->pairs.p, c->pl.pairs.data(), sizeof(int2) * c->pl.pairs.size(), cudaMemcpyHostToDevice));
+}
+
+void refresh_window(tr_ctx *c)
+{
+    // exchange window (Sec. 3.2): occupied e > -W, virtual e < W, contiguous for sorted eps
+    const int nocc = c->nocc;
+    c->o0 = 0;
+    c->oK = nocc;
+    c->vK = c->nvir;
+    if (c->opt.window_ev > 0) {
+        double w = c->opt.window_ev / HARTREE_EV;
+        int o0 = 0;
+        while (o0 < nocc && !(c->eps_h[o0] > -w)) ++o0;
+        int vk = 0;
+        while (vk < c->nvir && c->eps_h[nocc + vk] < w) ++vk;
+        c->o0 = o0;
+        c->oK = nocc - o0;
+        c->vK = vk;
+    }
+}
+
+void set_molecule(tr_ctx *c, int natm, const int *Z, const double *xyz, const double *aux_exp,
+                  int nshell, const tr_shell *shells)
+{
+    TR_REQUIRE(natm > 0 && Z && xyz && aux_exp, TR_EINVAL, "set_molecule: empty molecule");
+    TR_REQUIRE(nshell > 0 && shells, TR_EINVAL, "set_molecule: no AO shells");
+    c->have_mol = false;
+    c->built = false;
+    c->Z.assign(Z, Z + natm);
+    c->xyz.assign(xyz, xyz + 3 * natm);
+    c->aux_exp.assign(aux_exp, aux_exp + natm);
+    for (int i = 0; i < 3 * natm; ++i) TR_REQUIRE(std::isfinite(xyz[i]), TR_EINVAL, "set_molecule: non-finite coordinate");
+    c->shells_h.clear();
+    c->pexp_h.clear();
+    c->pcoef_h.clear();
+    int ao = 0;
+    for (int s = 0; s < nshell; ++s) {
+        const tr_shell &sh = shells[s];
+        TR_REQUIRE(sh.l >= 0 && sh.l <= 2, TR_EINVAL, "set_molecule: shell l must be 0, 1 or 2");
+        TR_REQUIRE(sh.nprim >= 1 && sh.nprim <= 16, TR_EINVAL, "set_molecule: nprim must be 1..16");
+        TR_REQUIRE(sh.atom >= 0 && sh.atom < natm, TR_EINVAL, "set_molecule: shell atom out of range");
+        TR_REQUIRE(sh.exp && sh.coef, TR_EINVAL, "set_molecule: null primitive arrays");
+        ShellDev d;
+        d.x = xyz[3 * sh.atom];
+        d.y = xyz[3 * sh.atom + 1];
+        d.z = xyz[3 * sh.atom + 2];
+        d.l = sh.l;
+        d.nprim = sh.nprim;
+        d.pstart = (int)c->pexp_h.size();
+        d.ao = ao;
+        for (int k = 0; k < sh.nprim; ++k) {
+            TR_REQUIRE(sh.exp[k] > 0.0 && std::isfinite(sh.exp[k]) && std::isfinite(sh.coef[k]),
+                       TR_EINVAL, "set_molecule: invalid primitive");
+            c->pexp_h.push_back(sh.exp[k]);
+            c->pcoef_h.push_back(sh.coef[k]);
+        }
+        c->shells_h.push_back(d);
+        ao += 2 * sh.l + 1;
+    }
+    c->nao = ao;
+    refresh_molecule(c);
+    if (!c->boys.p) {
+        std::vector<double> tab;
+        boys_table(tab);
+        c->boys.alloc(tab.size(), &c->budget, "boys table");
+        TR_CUDA(cudaMemcpy(c->boys.p, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice));
+    }
+    if (!c->flag.p) c->flag.alloc(4, &c->budget, "flags");
+    c->have_mol = true;
+}
+
+void set_orbitals(tr_ctx *c, int nao, int nmo, int nocc, const double *C, const double *eps, int on_device)
+{
+    TR_REQUIRE(c->have_mol, TR_EINVAL, "set_orbitals: call tr_set_molecule first");
+    TR_REQUIRE(nao == c->nao, TR_EINVAL, "set_orbitals: nao does not match the AO basis");
+    TR_REQUIRE(nmo > 0 && nmo <= nao && nocc > 0 && nocc < nmo, TR_EINVAL, "set_orbitals: bad nmo/nocc");
+    TR_REQUIRE(C && eps, TR_EINVAL, "set_orbitals: null pointer");
+    c->have_orb = false;
+    c->built = false;
+    c->eps_h.resize(nmo);
+    if (on_device)
+        TR_CUDA(cudaMemcpy(c->eps_h.data(), eps, sizeof(double) * nmo, cudaMemcpyDeviceToHost));
+    else
+        std::memcpy(c->eps_h.data(), eps, sizeof(double) * nmo);
+    for (int i = 0; i < nmo; ++i) {
+        TR_REQUIRE(std::isfinite(c->eps_h[i]), TR_EINVAL, "set_orbitals: non-finite orbital energy");
+        if (i) TR_REQUIRE(c->eps_h[i] >= c->eps_h[i - 1], TR_EINVAL, "set_orbitals: eps must be ascending");
+    }
+    c->nmo = nmo;
+    c->nocc = nocc;
+    c->nvir = nmo - nocc;
+    c->nov = (long long)nocc * c->nvir;
+    c->C.alloc((size_t)nao * nmo, &c->budget, "MO coefficients");
+    c->eps.alloc(nmo, &c->budget, "orbital energies");
+    TR_CUDA(cudaMemcpyAsync(c->C.p, C, sizeof(double) * (size_t)nao * nmo,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
+    TR_CUDA(cudaMemcpyAsync(c->eps.p, c->eps_h.data(), sizeof(double) * nmo, cudaMemcpyHostToDevice, c->st));
+    TR_CUDA(cudaStreamSynchronize(c->st));
+    refresh_window(c);
+    c->have_orb = true;
+}
+
+void build(tr_ctx *c)
+{
+    TR_REQUIRE(c->have_mol && c->have_orb, TR_EINVAL, "build: molecule and orbitals required");
+    c->built = false;
+    const int nao = c->nao, nocc = c->nocc, nvir = c->nvir, nmo = c->nmo, nJ = c->nJ, nK = c->nK;
+    const long long nov = c->nov;
+    cudaStream_t st = c->st;
+    Prof &pf = c->prof;
+    c->ws_split.reserve((size_t)16 << 20, &c->budget, "split-K workspace");
+
+    // Coulomb metric and its inverse (Sec. 2, Eq. RI)
+    c->GinvJ.alloc((size_t)nJ * nJ, &c->budget, "J metric");
+    if (nJ) {
+        DevBuf<double> G;
+        G.alloc((size_t)nJ * nJ, &c->budget, "J metric");
+        metric(c, c->auxJ_h, 1.0, 0.0, 0.0, G.p);
+        metric_inverse(c, G.p, nJ, c->GinvJ.p, "Coulomb");
+    }
+    // (P|ia) = sum_mu nu C_mu i (P|mu nu) C_nu a, aux chunks of at most aux_chunk_bytes
+    c->Y.alloc((size_t)nJ * nov, &c->budget, "(P|ia)");
+    c->k_active = nK > 0 && c->oK > 0 && c->vK > 0 && c->opt.cx != 0.0;
+    const int hrows = std::max(nocc, std::max(c->oK, c->vK));
+    size_t per = (size_t)nao * nao + (size_t)hrows * nao;
+    int npc = (int)std::max<size_t>(1, c->opt.aux_chunk_bytes / (per * sizeof(double)));
+    npc = std::min(npc, std::max(nJ, nK));
+    npc = std::max(npc, 1);
+    {
+        DevBuf<double> I, H;
+        I.alloc((size_t)npc * nao * nao, &c->budget, "AO integral chunk");
+        H.alloc((size_t)npc * hrows * nao, &c->budget, "half-transform chunk");
+        for (int p0 = 0; p0 < nJ; p0 += npc) {
+            int np = std::min(npc, nJ - p0);
+            compute_int3c(c, c->auxJ_h, p0, np, I.p, 1.0, 0.0, 0.0);
+            Batch b1;
+            b1.n1 = np;
+            b1.sB1 = (long long)nao * nao;
+            b1.sC1 = (long long)nocc * nao;
+            dgemm(pf, st, "xform_J1", true, false, nocc, nao, nao, 1.0, c->C.p, nmo, I.p, nao, 0.0, H.p, nao,
+                  b1, nullptr, 0);
+            Batch b2;
+            b2.n1 = np;
+            b2.sA1 = (long long)nocc * nao;
+            b2.sC1 = nov;
+            dgemm(pf, st, "xform_J2", false, false, nocc, nvir, nao, 1.0, H.p, nao, c->C.p + nocc, nmo, 0.0,
+                  c->Y.p + (long long)p0 * nov, nvir, b2, nullptr, 0);
+        }
+        // exchange tensors on the window with the K operator (Sec. 3.2, Eqs. RSH, K_mia_RSH)
+        c->Tab.release();
+        c->T2.release();
+        c->GinvK.release();
+        if (c->k_active) {
+            const double ka = c->opt.k_alpha, kb = c->opt.k_beta, om = c->opt.omega;
+            const int oK = c->oK, vK = c->vK, o0 = c->o0;
+            DevBuf<double> G, Iij;
+            G.alloc((size_t)nK * nK, &c->budget, "K metric");
+            c->GinvK.alloc((size_t)nK * nK, &c->budget, "K metric");
+            metric(c, c->auxK_h, ka, kb, om, G.p);
+            metric_inverse(c, G.p, nK, c->GinvK.p, "exchange");
+            Iij.alloc((size_t)nK * oK * oK, &c->budget, "(ij|P)");
+            c->Tab.alloc((size_t)nK * vK * vK, &c->budget, "T_ab");
+            for (int p0 = 0; p0 < nK; p0 += npc) {
+                int np = std::min(npc, nK - p0);
+                compute_int3c(c, c->auxK_h, p0, np, I.p, ka, kb, om);
+                Batch h;
+                h.n1 = np;
+                h.sB1 = (long long)nao * nao;
+                h.sC1 = (long long)oK * nao;
+                dgemm(pf, st, "xform_K1", true, false, oK, nao, nao, 1.0, c->C.p + o0, nmo, I.p, nao, 0.0, H.p,
+                      nao, h, nullptr, 0);
+                Batch g;
+                g.n1 = np;
+                g.sA1 = (long long)oK * nao;
+                g.sC1 = (long long)oK * oK;
+                dgemm(pf, st, "xform_K2", false, false, oK, oK, nao, 1.0, H.p, nao, c->C.p + o0, nmo, 0.0,
+                      Iij.p + (long long)p0 * oK * oK, oK, g, nullptr, 0);
+                h.sC1 = (long long)vK * nao;
+                dgemm(pf, st, "xform_K1", true, false, vK, nao, nao, 1.0, c->C.p + nocc, nmo, I.p, nao, 0.0, H.p,
+                      nao, h, nullptr, 0);
+                g.sA1 = (long long)vK * nao;
+                g.sC1 = (long long)vK * vK;
+                dgemm(pf, st, "xform_K2", false, false, vK, vK, nao, 1.0, H.p, nao, c->C.p + nocc, nmo, 0.0,
+                      c->Tab.p + (long long)p0 * vK * vK, vK, g, nullptr, 0);
+            }
+            // T_ij^P = sum_Q (ij|Q) (Q|P)^-1, stored [i][P][j]
+            c->T2.alloc((size_t)oK * nK * oK, &c->budget, "T_ij");
+            Batch t;
+            t.n1 = oK;
+            t.sB1 = oK;
+            t.sC1 = (long long)nK * oK;
+            dgemm(pf, st, "apply_K_metric", false, false, nK, oK, nK, 1.0, c->GinvK.p, nK, Iij.p,
+                  (long long)oK * oK, 0.0, c->T2.p, oK, t, nullptr, 0);
+            TR_CUDA(cudaStreamSynchronize(st));
+        }
+        TR_CUDA(cudaStreamSynchronize(st));
+    }
+    c->D.alloc(std::max<long long>(nov, 1), &c->budget, "orbital differences");
+    TR_LAUNCH(pf, st, "orbital_diff", 0, 0, orbital_diff<<<grid_for(nov), 256, 0, st>>>(c->eps.p, nocc, nvir, c->D.p));
+    TR_CUDA(cudaStreamSynchronize(st));
+    c->built = true;
+}
+
+void int3c_ao(tr_ctx *c, int which, int p0, int np, double *out)
+{
+    TR_REQUIRE(c->have_mol, TR_EINVAL, "int3c: call tr_set_molecule first");
+    const std::vector<AuxDev> &all = which == 0 ? c->auxJ_h : c->auxK_h;
+    int n = which == 0 ? c->nJ : c->nK;
+    TR_REQUIRE(which == 0 || which == 1, TR_EINVAL, "int3c: which must be 0 or 1");
+    TR_REQUIRE(p0 >= 0 && np >= 0 && p0 + np <= n, TR_EINVAL, "int3c: aux range out of bounds");
+    if (np == 0) return;
+    if (which == 0)
+        compute_int3c(c, all, p0, np, out, 1.0, 0.0, 0.0);
+    else
+        compute_int3c(c, all, p0, np, out, c->opt.k_alpha, c->opt.k_beta, c->opt.omega);
+}
+
+void int2c_aux(tr_ctx *c, int which, double *out)
+{
+    TR_REQUIRE(c->have_mol, TR_EINVAL, "int2c: call tr_set_molecule first");
+    TR_REQUIRE(which == 0 || which == 1, TR_EINVAL, "int2c: which must be 0 or 1");
+    if (which == 0)
+        metric(c, c->auxJ_h, 1.0, 0.0, 0.0, out);
+    else
+        metric(c, c->auxK_h, c->opt.k_alpha, c->opt.k_beta, c->opt.omega, out);
+}
+
+void get_tensor(tr_ctx *c, int which, double *out, int on_device)
+{
+    TR_REQUIRE(c->built, TR_EINVAL, "get_tensor: call tr_build first");
+    const double *src = nullptr;
+    size_t n = 0;
+    DevBuf<double> tmp;
+    switch (which) {
+        case 0: src = c->Y.p; n = (size_t)c->nJ * c->nov; break;
+        case 1:
+            n = c->k_active ? (size_t)c->nK * c->oK * c->oK : 0;
+            if (n) {
+                tmp.alloc(n, &c->budget, "tensor copy");
+                TR_LAUNCH(c->prof, c->st, "unpermute", 0, 0,
+                          unpermute_T2<<<grid_for(n), 256, 0, c->st>>>(c->T2.p, c->nK, c->oK, tmp.p));
+                src = tmp.p;
+            }
+            break;
+        case 2: src = c->Tab.p; n = c->k_active ? (size_t)c->nK * c->vK * c->vK : 0; break;
+        case 3: src = c->D.p; n = (size_t)c->nov; break;
+        default: throw Error(TR_EINVAL, "get_tensor: unknown tensor");
+    }
+    if (n)
+        TR_CUDA(cudaMemcpyAsync(out, src, sizeof(double) * n,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
+    TR_CUDA(cudaStreamSynchronize(c->st));
+}
+
+void matvec(tr_ctx *c, int m, const double *X, double *AX)
+{
+    TR_REQUIRE(c->built, TR_EINVAL, "matvec: call tr_build first");
+    if (m <= 0) return;
+    cudaStream_t st = c->st;
+    Prof &pf = c->prof;
+    const int nocc = c->nocc, nvir = c->nvir, nJ = c->nJ, nK = c->nK;
+    const long long nov = c->nov;
+    const int mb = std::min(m, c->mblk);
+    c->ws_Z.reserve((size_t)std::max(nJ, 1) * mb, &c->budget, "J workspace");
+    c->ws_Z2.reserve((size_t)std::max(nJ, 1) * mb, &c->budget, "J workspace");
+    const int oK = c->oK, vK = c->vK, o0 = c->o0;
+    int npk = 0;
+    if (c->k_active) {
+        c->ws_Xw.reserve((size_t)mb * oK * vK, &c->budget, "K workspace");
+        size_t perP = (size_t)mb * oK * vK;
+        size_t cap = std::max<size_t>(perP, ((size_t)4 << 30) / sizeof(double));
+        npk = (int)std::min<size_t>(nK, std::max<size_t>(1, cap / perP));
+        npk = std::min(npk, 65535 / mb);
+        c->ws_M.reserve((size_t)npk * perP, &c->budget, "K workspace");
+    }
+    for (int m0 = 0; m0 < m; m0 += mb) {
+        const int mm = std::min(mb, m - m0);
+        const double *x = X + (long long)m0 * nov;
+        double *ax = AX + (long long)m0 * nov;
+        // diagonal (e_a - e_i) X
+        TR_LAUNCH(pf, st, "diag", 0, 24.0 * nov * mm,
+                  diag_kernel<<<grid_for(nov * mm), 256, 0, st>>>(c->D.p, x, ax, nov, mm));
+        if (nJ) {
+            // Z = (Q|jb) X ; Zt = (P|Q)^-1 Z ; AX += 2 (P|ia) Zt
+            dgemm(pf, st, "J_contract", false, true, nJ, mm, (int)nov, 1.0, c->Y.p, nov, x, nov, 0.0,
+                  c->ws_Z.p, mm, Batch(), c->ws_split.p, c->ws_split.n);
+            dgemm(pf, st, "J_metric", false, false, nJ, mm, nJ, 1.0, c->GinvJ.p, nJ, c->ws_Z.p, mm, 0.0,
+                  c->ws_Z2.p, mm, Batch(), nullptr, 0);
+            dgemm(pf, st, "J_expand", true, false, mm, (int)nov, nJ, 2.0, c->ws_Z2.p, mm, c->Y.p, nov, 1.0,
+                  ax, nov, Batch(), nullptr, 0);
+        }
+        if (c->k_active) {
+            long long tot = (long long)mm * oK * vK;
+            TR_LAUNCH(pf, st, "gather_window", 0, 16.0 * tot,
+                      gather_window<<<grid_for(tot), 256, 0, st>>>(x, c->ws_Xw.p, mm, nocc, nvir, o0, oK, vK));
+            for (int P0 = 0; P0 < nK; P0 += npk) {
+                const int np = std::min(npk, nK - P0);
+                // M^P_mja = sum_b X_mjb T_ab^P
+                Batch b1;
+                b1.n1 = mm;
+                b1.n2 = np;
+                b1.sA1 = (long long)oK * vK;
+                b1.sC1 = (long long)np * oK * vK;
+                b1.sB2 = (long long)vK * vK;
+                b1.sC2 = (long long)oK * vK;
+                dgemm(pf, st, "K_stage1", false, false, oK, vK, vK, 1.0, c->ws_Xw.p, vK,
+                      c->Tab.p + (long long)P0 * vK * vK, vK, 0.0, c->ws_M.p, vK, b1, nullptr, 0);
+                // AX_mia -= cx sum_(P,j) T_ij^P M^P_mja  (window rows/cols)
+                Batch b2;
+                b2.n1 = mm;
+                b2.sB1 = (long long)np * oK * vK;
+                b2.sC1 = nov;
+                dgemm(pf, st, "K_stage2", false, false, oK, vK, np * oK, -c->opt.cx,
+                      c->T2.p + (long long)P0 * oK, (long long)nK * oK, c->ws_M.p, vK, 1.0,
+                      ax + (long long)o0 * nvir, nvir, b2, nullptr, 0);
+            }
+        }
+    }
+}
+
+}  // namespace tr

@@ -102,8 +102,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_inputs():
+def make_inputs(case="full"):
     from paper_2603_29257_gb300 import synth
+    if case == "small":
+        # profiling case of the same shape: 100 atoms (50 heavy + 50 H), nao 950
+        return synth.make_molecule(seed=2, n_heavy=50, n_h=50)
     return synth.molecule_200()
 
 
@@ -123,7 +126,7 @@ def run_native(args):
     __graft_entry__.build()
     from paper_2603_29257_gb300 import tdarisp
 
-    mol = make_inputs()
+    mol = make_inputs(args.case)
     torch.zeros(1, device="cuda")
     stream = torch.cuda.current_stream()
     C_dev = torch.from_numpy(mol.C).cuda()
@@ -178,7 +181,7 @@ def run_native(args):
 
     # end to end through the C ABI with host buffers (H2D of C, eps; D2H of omega, X)
     e2e = None
-    if rank == 0 or world > 1:
+    if not args.no_e2e:
         def host_step():
             ctx.set_orbitals(mol.C, mol.eps, mol.nocc)
             ctx.build()
@@ -206,8 +209,14 @@ def run_native(args):
     name, p = dom
     achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12
     fp64_peak = FP64_PEAK_TFLOPS
+    traffic = None
+    if name == "K_stage1" and p["launches"]:
+        # DRAM bytes per launch: the measured/algorithmic ratio of the ncu capture of this
+        # kernel (profiles/k_stage1_fp64_100atom.md) times the algorithmic bytes per launch
+        traffic = K_STAGE1_TRAFFIC_RATIO * p["bytes"] / p["launches"]
     roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp64_peak, "traffic": None,
+            "frac": achieved / fp64_peak, "traffic": traffic, "traffic_unit": "bytes per launch",
+            "algorithmic_bytes_per_launch": p["bytes"] / max(p["launches"], 1),
             "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz",
             "launches": p["launches"], "avg_launch_ms": p["ms"] / max(p["launches"], 1)}
     kernels = {k: {"ms": round(v["ms"], 3), "launches": v["launches"],
@@ -220,7 +229,8 @@ def run_native(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "natoms": int(len(mol.Z)), "nao": d.nao, "nocc": d.nocc,
+        "config": {"workload": WORKLOAD if args.case == "full" else "profiling case: 100-atom molecule, same options",
+                   "natoms": int(len(mol.Z)), "nao": d.nao, "nocc": d.nocc,
                    "nvir": d.nvir, "naux_j": d.naux_j, "naux_k": d.naux_k, "nocc_k": d.nocc_k,
                    "nvir_k": d.nvir_k, "nstates": OPTS["nstates"], "block": OPTS["block"],
                    "tol": OPTS["tol"], "parallelism": "independent problems per GPU" if world > 1 else "1 GPU",
@@ -244,6 +254,10 @@ def run_native(args):
 # The per-SM rate of 2 DFMA per clock comes from a register-only FMA loop on
 # GB300 (1186 GFLOP/s at 1987 MHz) and agrees with the nominal 1.25 TFLOP/s.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+# DRAM bytes / algorithmic bytes of K stage 1, from one ncu capture of that kernel
+# (737 MB measured for 708 MB algorithmic on the 100-atom profiling case).
+K_STAGE1_TRAFFIC_RATIO = 737.0 / 708.0
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -330,6 +344,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--case", default="full", choices=["full", "small"],
+                    help="small: 100-atom molecule of the same shape, for profiler captures")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

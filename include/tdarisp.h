@@ -82,6 +82,11 @@ typedef struct {
     double screen;       /* primitive-pair screening threshold (0: 1e-22) */
     size_t hbm_budget;   /* bytes of device memory the context may hold (0: 90% of free) */
     size_t aux_chunk_bytes; /* scratch for AO integral chunks (0: 2 GiB) */
+    size_t host_budget;  /* pinned host bytes for spilled Davidson vectors (0: unlimited);
+                            the subspace is capped so that V and W fit, which triggers
+                            restarts earlier (Sec. 3.3) */
+    int dav_dev_rows;    /* cap on Davidson vectors kept on the device (0: as many as the
+                            HBM budget allows); rows beyond it live in pinned host memory */
 } tr_options;
 
 typedef struct {
@@ -96,6 +101,9 @@ typedef struct {
 typedef struct {
     int niter, nmatvec, nrestart, converged;
     double t_matvec_ms, t_ortho_ms, t_eigh_ms, t_other_ms;
+    int max_space;       /* subspace size used (after the memory caps) */
+    int dev_rows;        /* Davidson vectors (V and W rows) held on the device */
+    long long host_bytes_moved; /* bytes streamed between pinned host memory and HBM */
 } tr_solve_info;
 
 /* Per-kernel timing, recorded with CUDA events on the context stream when

@@ -3,8 +3,10 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
+#include <cstdlib>
 #include <cstdio>
 #include <stdexcept>
 #include <string>
@@ -70,9 +72,17 @@ struct Prof {
         TR_CUDA(cudaEventCreate(&e));
         return e;
     }
+    // NVTX ranges named after the kernel kind when TR_NVTX is set in the environment
+    // (lets a profiler select one kind of kernel)
+    int nvtx = -1;
+    bool nvtx_on() {
+        if (nvtx < 0) nvtx = std::getenv("TR_NVTX") ? 1 : 0;
+        return nvtx == 1;
+    }
     // returns a token to pass to end()
     int begin(cudaStream_t st, const char *name, double flops = 0, double bytes = 0) {
         launches += 1;
+        if (nvtx_on()) nvtxRangePushA(name);
         if (!enabled) return -1;
         ProfRecord r;
         r.kind = kind(name);
@@ -85,8 +95,8 @@ struct Prof {
         return (int)pending.size() - 1;
     }
     void end(cudaStream_t st, int tok) {
-        if (tok < 0) return;
-        TR_CUDA(cudaEventRecord(pending[tok].b, st));
+        if (tok >= 0) TR_CUDA(cudaEventRecord(pending[tok].b, st));
+        if (nvtx_on()) nvtxRangePop();
     }
     // resolve pending events (synchronises on the last one)
     void flush() {

@@ -57,13 +57,22 @@ struct tr_ctx {
     int mblk = 32;
 
     // Davidson state
-    tr::DevBuf<double> V, W, Hs, Hw, Yev, Yw, theta, Xr, R, T, Tt, Cs, Ss, Gc, rn, part;
+    tr::DevBuf<double> V, W, Hs, Hw, Yev, Yw, theta, Xr, R, T, Tt, Tn, Wn, Cs, Ss, Gc, rn, part;
     tr::DevBuf<int> idx_dev;
-    int dav_cap = 0;
+    // spill of V/W rows to pinned host memory: staging slots, copy stream, events
+    tr::DevBuf<double> stage;
+    cudaStream_t cst = nullptr;
+    cudaEvent_t sev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 
     ~tr_ctx()
     {
         if (st) cudaStreamSynchronize(st);
+        if (cst) {
+            cudaStreamSynchronize(cst);
+            cudaStreamDestroy(cst);
+        }
+        for (auto e : sev)
+            if (e) cudaEventDestroy(e);
     }
 };
 
@@ -81,6 +90,8 @@ void int2c_aux(tr_ctx *c, int which, double *out);
 void get_tensor(tr_ctx *c, int which, double *out, int on_device);
 // AX = A X for m device vectors (asynchronous on c->st)
 void matvec(tr_ctx *c, int m, const double *X, double *AX);
+// allocate the matvec workspaces for blocks of up to m vectors
+void reserve_matvec(tr_ctx *c, int m);
 int solve(tr_ctx *c, double *omega, double *X, double *resid, int on_device, tr_solve_info *info);
 
 }  // namespace tr

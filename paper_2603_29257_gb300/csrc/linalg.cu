@@ -7,20 +7,27 @@
 // parallel cyclic Jacobi eigensolver for the Davidson subspace matrix.
 #include "linalg.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
 
 namespace tr {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BK = 16, NT = 256;
+constexpr int JACOBI_MAX_PAIRS_PER_BLOCK = 64;
 
-template <bool TA, bool TB>
+// Thread (tx, ty) of a 16 x 16 block computes TM x TN outputs at rows
+// ty + 16 i and columns tx + 16 j; the block tile is (16 TM) x (16 TN).
+// Skinny shapes (a dimension of a few dozen) use TM or TN = 1.
+template <bool TA, bool TB, int TM, int TN>
 __global__ void __launch_bounds__(NT)
     dgemm_kernel(int M, int N, int K, double alpha, const double *__restrict__ A, long long lda,
                  const double *__restrict__ B, long long ldb, double beta, double *__restrict__ C,
                  long long ldc, Batch bt, int ksplit, int kchunk, double *__restrict__ ws)
 {
+    constexpr int BM = 16 * TM, BN = 16 * TN;
     __shared__ double As[BK][BM + 1];
     __shared__ double Bs[BK][BN + 1];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -33,52 +40,47 @@ __global__ void __launch_bounds__(NT)
     const int kb = ks * kchunk;
     const int ke = min(K, kb + kchunk);
 
-    double acc[4][4];
+    double acc[TM][TN];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-    double ra[4], rb[4];
+        for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+    double ra[TM], rb[TN];
 
     auto load = [&](int k0) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            int idx = tid + r * NT;
-            int mm, kk;
-            if (!TA) {
-                kk = idx & 15;
-                mm = idx >> 4;
-            } else {
-                mm = idx & 63;
-                kk = idx >> 6;
-            }
-            int m = m0 + mm, k = k0 + kk;
+        for (int r = 0; r < TM; ++r) {
+            const int idx = tid + r * NT;
+            const int kk = TA ? idx / BM : (idx & 15);
+            const int mm = TA ? idx % BM : (idx >> 4);
+            const int m = m0 + mm, k = k0 + kk;
             ra[r] = (m < M && k < ke) ? (TA ? A[(long long)k * lda + m] : A[(long long)m * lda + k]) : 0.0;
-            int nn;
-            if (!TB) {
-                nn = idx & 63;
-                kk = idx >> 6;
-            } else {
-                kk = idx & 15;
-                nn = idx >> 4;
-            }
-            int n = n0 + nn;
-            k = k0 + kk;
+        }
+#pragma unroll
+        for (int r = 0; r < TN; ++r) {
+            const int idx = tid + r * NT;
+            const int kk = TB ? (idx & 15) : idx / BN;
+            const int nn = TB ? (idx >> 4) : idx % BN;
+            const int n = n0 + nn, k = k0 + kk;
             rb[r] = (n < N && k < ke) ? (TB ? B[(long long)n * ldb + k] : B[(long long)k * ldb + n]) : 0.0;
         }
     };
     auto store = [&]() {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            int idx = tid + r * NT;
-            if (!TA)
+        for (int r = 0; r < TM; ++r) {
+            const int idx = tid + r * NT;
+            if (TA)
+                As[idx / BM][idx % BM] = ra[r];
+            else
                 As[idx & 15][idx >> 4] = ra[r];
-            else
-                As[idx >> 6][idx & 63] = ra[r];
-            if (!TB)
-                Bs[idx >> 6][idx & 63] = rb[r];
-            else
+        }
+#pragma unroll
+        for (int r = 0; r < TN; ++r) {
+            const int idx = tid + r * NT;
+            if (TB)
                 Bs[idx & 15][idx >> 4] = rb[r];
+            else
+                Bs[idx / BN][idx % BN] = rb[r];
         }
     };
 
@@ -89,27 +91,27 @@ __global__ void __launch_bounds__(NT)
         if (k0 + BK < ke) load(k0 + BK);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            double a[4], bb[4];
+            double a[TM], bb[TN];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+            for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+            for (int j = 0; j < TN; ++j) bb[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
         }
         __syncthreads();
     }
 
     const int nbatch = gridDim.z / ksplit;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int m = m0 + ty + 16 * i;
+    for (int i = 0; i < TM; ++i) {
+        const int m = m0 + ty + 16 * i;
         if (m >= M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int n = n0 + tx + 16 * j;
+        for (int j = 0; j < TN; ++j) {
+            const int n = n0 + tx + 16 * j;
             if (n >= N) continue;
             if (ksplit == 1) {
                 double *c = C + b1 * bt.sC1 + b2 * bt.sC2 + (long long)m * ldc + n;
@@ -217,92 +219,108 @@ __device__ double block_sum(double v, double *red)
 }
 
 constexpr int JACOBI_MAX_SWEEPS = 60;
+constexpr int JACOBI_THREADS = 256;
 
-__global__ void __launch_bounds__(1024)
-    jacobi_kernel(double *H, int k, double *w, double *Yout, double *Y, int *flag)
+// Parallel cyclic Jacobi over the whole grid (cooperative launch).  Round r
+// of a sweep applies the k/2 disjoint rotations of the round-robin pairing;
+// block b owns pairs b, b + G, ...: it computes their rotations, updates
+// their two rows of H, and after a grid barrier their two columns of H and
+// of Y; a second barrier ends the round.
+__global__ void __launch_bounds__(JACOBI_THREADS)
+    jacobi_coop(double *H, int k, double *w, double *Yout, double *Y, int *flag, double *red)
 {
-    extern __shared__ double smem[];
-    __shared__ double red[33];
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
+    __shared__ double cs[JACOBI_MAX_PAIRS_PER_BLOCK], sn[JACOBI_MAX_PAIRS_PER_BLOCK];
+    __shared__ int pp[JACOBI_MAX_PAIRS_PER_BLOCK], qq[JACOBI_MAX_PAIRS_PER_BLOCK];
+    __shared__ double sred[33];
     const int kk = k + (k & 1);
     const int np = kk / 2;
-    double *cs = smem;
-    double *sn = smem + np;
-    int *pp = (int *)(sn + np);
-    int *qq = pp + np;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int G = gridDim.x, bid = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const int gtid = bid * nt + tid, gnt = G * nt;
+    const int myp = (np - bid + G - 1) / G;  // pairs owned by this block
 
-    for (int idx = tid; idx < k * k; idx += nt) Y[idx] = (idx / k == idx % k) ? 1.0 : 0.0;
-    __syncthreads();
+    for (int idx = gtid; idx < k * k; idx += gnt) Y[idx] = (idx / k == idx % k) ? 1.0 : 0.0;
 
     bool done = (k <= 1);
     for (int sweep = 0; sweep < JACOBI_MAX_SWEEPS && !done; ++sweep) {
         double off = 0.0, tot = 0.0;
-        for (int idx = tid; idx < k * k; idx += nt) {
+        for (int idx = gtid; idx < k * k; idx += gnt) {
             double h = H[idx];
             tot += h * h;
             if (idx / k != idx % k) off += h * h;
         }
-        off = block_sum(off, red);
-        tot = block_sum(tot, red);
+        off = block_sum(off, sred);
+        tot = block_sum(tot, sred);
+        if (tid == 0) {
+            red[2 * bid] = off;
+            red[2 * bid + 1] = tot;
+        }
+        grid.sync();
+        off = 0.0;
+        tot = 0.0;
+        for (int b = 0; b < G; ++b) {
+            off += red[2 * b];
+            tot += red[2 * b + 1];
+        }
+        grid.sync();  // everyone has read red[] before it is rewritten
         if (off <= 1e-30 * tot || tot == 0.0) {
             done = true;
             break;
         }
         for (int r = 0; r < kk - 1; ++r) {
-            for (int idx = tid; idx < np; idx += nt) {
-                int a = rr_pos(idx, r, kk), b = rr_pos(kk - 1 - idx, r, kk);
-                int p = min(a, b), q = max(a, b);
+            for (int l = tid; l < myp; l += nt) {
+                const int idx = bid + l * G;
+                const int a = rr_pos(idx, r, kk), b = rr_pos(kk - 1 - idx, r, kk);
+                const int p = min(a, b), q = max(a, b);
                 double c = 1.0, s = 0.0;
                 if (q < k) {
-                    double hpq = H[p * k + q];
-                    if (hpq != 0.0) {
-                        double tau = (H[q * k + q] - H[p * k + p]) / (2.0 * hpq);
-                        double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                    const double hpq = H[p * k + q], hpp = H[p * k + p], hqq = H[q * k + q];
+                    if (fabs(hpq) > 1e-18 * sqrt(fabs(hpp * hqq)) && hpq != 0.0) {
+                        const double tau = (hqq - hpp) / (2.0 * hpq);
+                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
                         c = 1.0 / sqrt(1.0 + t * t);
                         s = t * c;
                     }
                 }
-                pp[idx] = p;
-                qq[idx] = q;
-                cs[idx] = c;
-                sn[idx] = s;
+                pp[l] = p;
+                qq[l] = q;
+                cs[l] = c;
+                sn[l] = s;
             }
             __syncthreads();
-            // rows p, q <- J^T rows
-            for (int t = tid; t < np * k; t += nt) {
-                int idx = t / k, j = t - idx * k;
-                int p = pp[idx], q = qq[idx];
-                if (q >= k || sn[idx] == 0.0) continue;
-                double c = cs[idx], s = sn[idx];
-                double hp = H[p * k + j], hq = H[q * k + j];
+            for (int t = tid; t < myp * k; t += nt) {
+                const int l = t / k, j = t - l * k;
+                if (sn[l] == 0.0) continue;
+                const int p = pp[l], q = qq[l];
+                const double c = cs[l], s = sn[l];
+                const double hp = H[p * k + j], hq = H[q * k + j];
                 H[p * k + j] = c * hp - s * hq;
                 H[q * k + j] = s * hp + c * hq;
             }
-            __syncthreads();
-            // columns p, q of H and of Y <- cols J
-            for (int t = tid; t < np * k; t += nt) {
-                int i = t / np, idx = t - i * np;
-                int p = pp[idx], q = qq[idx];
-                if (q >= k || sn[idx] == 0.0) continue;
-                double c = cs[idx], s = sn[idx];
-                double hp = H[i * k + p], hq = H[i * k + q];
+            grid.sync();
+            for (int t = tid; t < myp * k; t += nt) {
+                const int l = t / k, i = t - l * k;
+                if (sn[l] == 0.0) continue;
+                const int p = pp[l], q = qq[l];
+                const double c = cs[l], s = sn[l];
+                const double hp = H[i * k + p], hq = H[i * k + q];
                 H[i * k + p] = c * hp - s * hq;
                 H[i * k + q] = s * hp + c * hq;
-                double yp = Y[i * k + p], yq = Y[i * k + q];
+                const double yp = Y[i * k + p], yq = Y[i * k + q];
                 Y[i * k + p] = c * yp - s * yq;
                 Y[i * k + q] = s * yp + c * yq;
             }
-            __syncthreads();
+            grid.sync();
         }
     }
-    if (!done && tid == 0) atomicExch(flag, 1);
-    __syncthreads();
+    if (!done && gtid == 0) atomicExch(flag, 1);
     // sort ascending by rank (ties by index)
-    for (int i = tid; i < k; i += nt) {
-        double wi = H[i * k + i];
+    for (int i = gtid; i < k; i += gnt) {
+        const double wi = H[i * k + i];
         int rank = 0;
         for (int j = 0; j < k; ++j) {
-            double wj = H[j * k + j];
+            const double wj = H[j * k + j];
             rank += (wj < wi || (wj == wi && j < i)) ? 1 : 0;
         }
         w[rank] = wi;
@@ -321,17 +339,35 @@ __global__ void sum_rows_kernel(const double *__restrict__ a, int nrows, int n, 
 
 }  // namespace
 
+template <int TM, int TN>
+void launch_gemm(cudaStream_t st, bool ta, bool tb, dim3 grid, int M, int N, int K, double alpha,
+                 const double *A, long long lda, const double *B, long long ldb, double beta, double *C,
+                 long long ldc, const Batch &bt, int ksplit, int kchunk, double *ws)
+{
+    if (!ta && !tb)
+        dgemm_kernel<false, false, TM, TN><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
+    else if (!ta && tb)
+        dgemm_kernel<false, true, TM, TN><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
+    else if (ta && !tb)
+        dgemm_kernel<true, false, TM, TN><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
+    else
+        dgemm_kernel<true, true, TM, TN><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
+}
+
 void dgemm(Prof &prof, cudaStream_t st, const char *name, bool ta, bool tb, int M, int N, int K,
            double alpha, const double *A, long long lda, const double *B, long long ldb, double beta,
-           double *C, long long ldc, const Batch &bt, double *ws, size_t ws_elems)
+           double *C, long long ldc, const Batch &bt, double *ws, size_t ws_elems, double alg_bytes)
 {
     if (M <= 0 || N <= 0 || bt.count() <= 0) return;
     const int nb = bt.count();
-    if (K <= 0) {
-        // C = beta * C: run with zero-length K through the kernel (acc = 0)
-        K = 0;
-    }
-    long long tiles = (long long)cdiv(M, BM) * cdiv(N, BN) * nb;
+    if (K < 0) K = 0;
+    // tile shape: 64 x 64, or 16 x 64 / 64 x 16 when one side is skinny
+    int TM = 4, TN = 4;
+    if (M <= 32 && N > 32) TM = 1;
+    else if (N <= 32 && M > 32) TN = 1;
+    else if (M <= 32 && N <= 32) TM = TN = 1;
+    const int BMx = 16 * TM, BNx = 16 * TN;
+    long long tiles = (long long)cdiv(M, BMx) * cdiv(N, BNx) * nb;
     int ksplit = 1;
     const long long target = 4 * 152;
     if (ws && tiles < target && K >= 4 * 256) {
@@ -347,19 +383,19 @@ void dgemm(Prof &prof, cudaStream_t st, const char *name, bool ta, bool tb, int 
         ksplit = (K + kchunk - 1) / kchunk;
     }
     TR_REQUIRE((long long)nb * ksplit <= 65535, TR_EINVAL, "dgemm: batch too large");
-    TR_REQUIRE(cdiv(M, BM) <= 65535, TR_EINVAL, "dgemm: M too large");
-    dim3 grid(cdiv(N, BN), cdiv(M, BM), nb * ksplit);
+    TR_REQUIRE(cdiv(M, BMx) <= 65535, TR_EINVAL, "dgemm: M too large");
+    dim3 grid(cdiv(N, BNx), cdiv(M, BMx), nb * ksplit);
     double flops = 2.0 * M * N * (double)K * nb;
-    double bytes = 8.0 * ((double)M * K + (double)K * N + 2.0 * M * N) * nb;
+    double bytes = alg_bytes >= 0 ? alg_bytes : 8.0 * ((double)M * K + (double)K * N + 2.0 * M * N) * nb;
     int tok = prof.begin(st, name, flops, bytes);
-    if (!ta && !tb)
-        dgemm_kernel<false, false><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
-    else if (!ta && tb)
-        dgemm_kernel<false, true><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
-    else if (ta && !tb)
-        dgemm_kernel<true, false><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
+    if (TM == 4 && TN == 4)
+        launch_gemm<4, 4>(st, ta, tb, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
+    else if (TM == 1 && TN == 4)
+        launch_gemm<1, 4>(st, ta, tb, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
+    else if (TM == 4 && TN == 1)
+        launch_gemm<4, 1>(st, ta, tb, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
     else
-        dgemm_kernel<true, true><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
+        launch_gemm<1, 1>(st, ta, tb, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
     TR_CUDA(cudaGetLastError());
     if (ksplit > 1) {
         prof.launches += 1;
@@ -403,11 +439,25 @@ void jacobi_eigh(Prof &prof, cudaStream_t st, double *H, int k, double *w, doubl
                  int *flag)
 {
     if (k <= 0) return;
-    int kk = k + (k & 1);
-    size_t sm = (size_t)(kk / 2) * (2 * sizeof(double) + 2 * sizeof(int));
-    TR_REQUIRE(sm <= 48 * 1024, TR_EINVAL, "jacobi: subspace too large");
-    TR_LAUNCH(prof, st, "jacobi_eigh", 0, 0,
-              jacobi_kernel<<<1, 1024, sm, st>>>(H, k, w, Y, work, flag));
+    static int nsm = 0, per_sm = 0;
+    if (!nsm) {
+        int dev = 0;
+        TR_CUDA(cudaGetDevice(&dev));
+        TR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop, JACOBI_THREADS, 0));
+        TR_REQUIRE(per_sm >= 1, TR_ECUDA, "jacobi: kernel cannot be resident");
+    }
+    const int np = (k + (k & 1)) / 2;
+    int G = std::min(np, nsm * per_sm);
+    G = std::max(G, (np + JACOBI_MAX_PAIRS_PER_BLOCK - 1) / JACOBI_MAX_PAIRS_PER_BLOCK);
+    TR_REQUIRE(G <= nsm * per_sm, TR_EINVAL, "jacobi: subspace too large");
+    double *red = nullptr;
+    TR_CUDA(cudaMallocAsync(&red, sizeof(double) * 2 * G, st));
+    void *args[] = {&H, &k, &w, &Y, &work, &flag, &red};
+    int tok = prof.begin(st, "jacobi_eigh", 0, 0);
+    TR_CUDA(cudaLaunchCooperativeKernel((const void *)jacobi_coop, dim3(G), dim3(JACOBI_THREADS), args, 0, st));
+    prof.end(st, tok);
+    TR_CUDA(cudaFreeAsync(red, st));
 }
 
 void sum_rows(Prof &prof, cudaStream_t st, const double *a, int nrows, int n, double *out)

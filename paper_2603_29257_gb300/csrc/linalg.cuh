@@ -18,9 +18,12 @@ struct Batch {
 //   tb = false: B[k*ldb + n]; tb = true: B[n*ldb + k]
 // beta == 0 never reads C.  Splits K across CTAs when the output is small;
 // ws/ws_elems is scratch for the partial sums (may be null: no split).
+// alg_bytes: algorithmic DRAM bytes of the call for the profiler (default:
+// every operand read once and C written once per batch entry).
 void dgemm(Prof &prof, cudaStream_t st, const char *name, bool ta, bool tb, int M, int N, int K,
            double alpha, const double *A, long long lda, const double *B, long long ldb,
-           double beta, double *C, long long ldc, const Batch &bt, double *ws, size_t ws_elems);
+           double beta, double *C, long long ldc, const Batch &bt, double *ws, size_t ws_elems,
+           double alg_bytes = -1.0);
 
 // Lower Cholesky factor in place (upper triangle untouched): G = L L^T.
 // flag (device int) is set to 1 + column on the first non-positive pivot.

@@ -423,6 +423,27 @@ void get_tensor(tr_ctx *c, int which, double *out, int on_device)
     TR_CUDA(cudaStreamSynchronize(c->st));
 }
 
+static int matvec_pchunk(tr_ctx *c, int mb)
+{
+    if (!c->k_active) return 0;
+    size_t perP = (size_t)mb * c->oK * c->vK;
+    size_t cap = std::max<size_t>(perP, ((size_t)4 << 30) / sizeof(double));
+    int npk = (int)std::min<size_t>(c->nK, std::max<size_t>(1, cap / perP));
+    return std::min(npk, 65535 / mb);
+}
+
+void reserve_matvec(tr_ctx *c, int m)
+{
+    const int mb = std::max(1, std::min(m, c->mblk));
+    c->ws_split.reserve((size_t)16 << 20, &c->budget, "split-K workspace");
+    c->ws_Z.reserve((size_t)std::max(c->nJ, 1) * mb, &c->budget, "J workspace");
+    c->ws_Z2.reserve((size_t)std::max(c->nJ, 1) * mb, &c->budget, "J workspace");
+    if (c->k_active) {
+        c->ws_Xw.reserve((size_t)mb * c->oK * c->vK, &c->budget, "K workspace");
+        c->ws_M.reserve((size_t)matvec_pchunk(c, mb) * mb * c->oK * c->vK, &c->budget, "K workspace");
+    }
+}
+
 void matvec(tr_ctx *c, int m, const double *X, double *AX)
 {
     TR_REQUIRE(c->built, TR_EINVAL, "matvec: call tr_build first");
@@ -432,18 +453,9 @@ void matvec(tr_ctx *c, int m, const double *X, double *AX)
     const int nocc = c->nocc, nvir = c->nvir, nJ = c->nJ, nK = c->nK;
     const long long nov = c->nov;
     const int mb = std::min(m, c->mblk);
-    c->ws_Z.reserve((size_t)std::max(nJ, 1) * mb, &c->budget, "J workspace");
-    c->ws_Z2.reserve((size_t)std::max(nJ, 1) * mb, &c->budget, "J workspace");
+    reserve_matvec(c, mb);
     const int oK = c->oK, vK = c->vK, o0 = c->o0;
-    int npk = 0;
-    if (c->k_active) {
-        c->ws_Xw.reserve((size_t)mb * oK * vK, &c->budget, "K workspace");
-        size_t perP = (size_t)mb * oK * vK;
-        size_t cap = std::max<size_t>(perP, ((size_t)4 << 30) / sizeof(double));
-        npk = (int)std::min<size_t>(nK, std::max<size_t>(1, cap / perP));
-        npk = std::min(npk, 65535 / mb);
-        c->ws_M.reserve((size_t)npk * perP, &c->budget, "K workspace");
-    }
+    const int npk = matvec_pchunk(c, mb);
     for (int m0 = 0; m0 < m; m0 += mb) {
         const int mm = std::min(mb, m - m0);
         const double *x = X + (long long)m0 * nov;
@@ -474,16 +486,20 @@ void matvec(tr_ctx *c, int m, const double *X, double *AX)
                 b1.sC1 = (long long)np * oK * vK;
                 b1.sB2 = (long long)vK * vK;
                 b1.sC2 = (long long)oK * vK;
+                // algorithmic bytes: M written once, X window and T_ab^P read once
+                const double kb1 = 8.0 * ((double)mm * np * oK * vK + (double)mm * oK * vK + (double)np * vK * vK);
                 dgemm(pf, st, "K_stage1", false, false, oK, vK, vK, 1.0, c->ws_Xw.p, vK,
-                      c->Tab.p + (long long)P0 * vK * vK, vK, 0.0, c->ws_M.p, vK, b1, nullptr, 0);
+                      c->Tab.p + (long long)P0 * vK * vK, vK, 0.0, c->ws_M.p, vK, b1, nullptr, 0, kb1);
                 // AX_mia -= cx sum_(P,j) T_ij^P M^P_mja  (window rows/cols)
                 Batch b2;
                 b2.n1 = mm;
                 b2.sB1 = (long long)np * oK * vK;
                 b2.sC1 = nov;
+                // algorithmic bytes: M and the T_ij chunk read once, the AX window read and written
+                const double kb2 = 8.0 * ((double)mm * np * oK * vK + (double)oK * np * oK + 2.0 * mm * oK * vK);
                 dgemm(pf, st, "K_stage2", false, false, oK, vK, np * oK, -c->opt.cx,
                       c->T2.p + (long long)P0 * oK, (long long)nK * oK, c->ws_M.p, vK, 1.0,
-                      ax + (long long)o0 * nvir, nvir, b2, nullptr, 0);
+                      ax + (long long)o0 * nvir, nvir, b2, nullptr, 0, kb2);
             }
         }
     }

@@ -32,7 +32,8 @@ class Options(ct.Structure):
                 ("nstates", ct.c_int), ("block", ct.c_int), ("max_space", ct.c_int),
                 ("max_iter", ct.c_int), ("tol", ct.c_double), ("precision", ct.c_int),
                 ("screen", ct.c_double), ("hbm_budget", ct.c_size_t),
-                ("aux_chunk_bytes", ct.c_size_t)]
+                ("aux_chunk_bytes", ct.c_size_t), ("host_budget", ct.c_size_t),
+                ("dav_dev_rows", ct.c_int)]
 
 
 class Dims(ct.Structure):
@@ -43,7 +44,8 @@ class Dims(ct.Structure):
 class SolveInfo(ct.Structure):
     _fields_ = [("niter", ct.c_int), ("nmatvec", ct.c_int), ("nrestart", ct.c_int),
                 ("converged", ct.c_int), ("t_matvec_ms", ct.c_double), ("t_ortho_ms", ct.c_double),
-                ("t_eigh_ms", ct.c_double), ("t_other_ms", ct.c_double)]
+                ("t_eigh_ms", ct.c_double), ("t_other_ms", ct.c_double), ("max_space", ct.c_int),
+                ("dev_rows", ct.c_int), ("host_bytes_moved", ct.c_longlong)]
 
 
 class ProfEntry(ct.Structure):

@@ -183,6 +183,28 @@ int tr_get_tensor(tr_ctx *ctx, int which, double *out, int on_device);
    X and AX must not overlap.  Requires tr_build. */
 int tr_matvec(tr_ctx *ctx, int m, const double *X, double *AX, int on_device);
 
+/* Size of the static device scratch used by tr_matvec_noalloc. */
+#define TR_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+
+/* AX = A X like tr_matvec with device pointers, for callers that cannot
+   allocate device memory: code recording the product into a CUDA graph (no
+   cudaMalloc/cudaFree during stream capture), code living under another
+   allocator with a hard cap, and loops that cannot afford cudaMalloc's implicit
+   device synchronisation.  The paper has no counterpart; it is a deployment
+   variant of the same product.
+   All scratch (J and K intermediates, split-K partial sums) comes from one
+   file-scope device array of TR_NOALLOC_SCRATCH_BYTES that every GPU loading
+   the library holds until exit; nothing is allocated.  The first call on a
+   device looks up that array's address with the device current, so make it
+   before any stream capture.  Calls whose GPU work overlaps (other streams or
+   contexts at the same time) race on the shared array; no region relies on
+   what a previous call left in it.  X and AX: device pointers [m][nocc][nvir],
+   not overlapping; asynchronous on the context stream; requires tr_build.
+   Errors: TR_EINVAL when 2 naux_j + 2 nocc_k nvir_k doubles per vector plus
+   65536 doubles exceed the array (the message says so), when the context's
+   device is not current, or as tr_matvec. */
+int tr_matvec_noalloc(tr_ctx *ctx, int m, const double *X, double *AX);
+
 /* Davidson solve for the lowest nstates (Sec. 3.3).  Outputs (host, or device
    if on_device): omega[nstates] (Hartree, ascending); X[nstates][nocc][nvir]
    (may be NULL; unit norm, largest-magnitude component positive);

@@ -69,6 +69,7 @@ SIGNATURES = {
     "tr_int2c": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p]),
     "tr_get_tensor": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int]),
     "tr_matvec": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_int]),
+    "tr_matvec_noalloc": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p]),
     "tr_solve": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int,
                             ct.POINTER(SolveInfo)]),
     "tr_profile": (ct.c_int, [ct.c_void_p, ct.c_int]),
@@ -247,6 +248,12 @@ class Context:
         rc = lib().tr_matvec(self._h, m, Xn.ctypes.data_as(ct.c_void_p), AX.ctypes.data_as(ct.c_void_p), 0)
         self._check(rc, "tr_matvec")
         return AX
+
+    def matvec_noalloc(self, X, out):
+        """A X into out (CUDA tensors) without any device allocation (static scratch)."""
+        rc = lib().tr_matvec_noalloc(self._h, X.shape[0], ct.c_void_p(X.data_ptr()), ct.c_void_p(out.data_ptr()))
+        self._check(rc, "tr_matvec_noalloc")
+        return out
 
     def solve(self, want_x=True, device=False):
         """Davidson (Sec. 3.3).  Returns (omega, X, resid, info); X is None unless want_x.

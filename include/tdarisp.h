@@ -52,7 +52,9 @@ extern "C" {
 #define TR_ENOCONV (-4)   /* Davidson hit max_iter; outputs hold the best estimates */
 #define TR_ENOTPD (-5)    /* an auxiliary metric is not positive definite */
 
-#define TR_FP64 0
+#define TR_FP64 0   /* every step in FP64 */
+#define TR_MIXED 1  /* MO tensors and J/K contractions in FP32 / 3xTF32 tensor cores;
+                       integrals, metrics and the Davidson driver in FP64 */
 
 typedef struct tr_ctx tr_ctx;
 
@@ -78,7 +80,7 @@ typedef struct {
     int max_space;       /* subspace size that triggers a restart (0: 20 * nstates) */
     int max_iter;        /* Davidson iterations (0: 200) */
     double tol;          /* residual 2-norm threshold per state */
-    int precision;       /* TR_FP64 */
+    int precision;       /* TR_FP64 or TR_MIXED */
     double screen;       /* primitive-pair screening threshold (0: 1e-22) */
     size_t hbm_budget;   /* bytes of device memory the context may hold (0: 90% of free) */
     size_t aux_chunk_bytes; /* scratch for AO integral chunks (0: 2 GiB) */
@@ -202,7 +204,8 @@ int tr_matvec(tr_ctx *ctx, int m, const double *X, double *AX, int on_device);
    not overlapping; asynchronous on the context stream; requires tr_build.
    Errors: TR_EINVAL when 2 naux_j + 2 nocc_k nvir_k doubles per vector plus
    65536 doubles exceed the array (the message says so), when the context's
-   device is not current, or as tr_matvec. */
+   device is not current, for a TR_MIXED context (only the FP64 form is
+   available here), or as tr_matvec. */
 int tr_matvec_noalloc(tr_ctx *ctx, int m, const double *X, double *AX);
 
 /* Davidson solve for the lowest nstates (Sec. 3.3).  Outputs (host, or device

@@ -71,7 +71,8 @@ int tr_create(tr_ctx **out, const tr_options *opt, void *cuda_stream)
         return TR_ENOMEM;
     }
     int rc = guarded(c, [&]() {
-        TR_REQUIRE(opt->precision == TR_FP64, TR_EINVAL, "create: unsupported precision");
+        TR_REQUIRE(opt->precision == TR_FP64 || opt->precision == TR_MIXED, TR_EINVAL,
+                   "create: precision must be TR_FP64 or TR_MIXED");
         c->opt = *opt;
         normalise_options(&c->opt);
         c->st = (cudaStream_t)cuda_stream;
@@ -97,8 +98,9 @@ int tr_set_options(tr_ctx *ctx, const tr_options *opt)
 {
     return guarded(ctx, [&]() {
         TR_REQUIRE(opt, TR_EINVAL, "set_options: null options");
-        TR_REQUIRE(opt->precision == TR_FP64, TR_EINVAL, "set_options: unsupported precision");
-        bool rebuild = opt->cx != ctx->opt.cx || opt->k_alpha != ctx->opt.k_alpha ||
+        TR_REQUIRE(opt->precision == TR_FP64 || opt->precision == TR_MIXED, TR_EINVAL,
+                   "set_options: precision must be TR_FP64 or TR_MIXED");
+        bool rebuild = opt->precision != ctx->opt.precision || opt->cx != ctx->opt.cx || opt->k_alpha != ctx->opt.k_alpha ||
                        opt->k_beta != ctx->opt.k_beta || opt->omega != ctx->opt.omega ||
                        opt->window_ev != ctx->opt.window_ev || opt->aux_on_h != ctx->opt.aux_on_h ||
                        opt->screen != ctx->opt.screen;
@@ -205,9 +207,13 @@ int tr_matvec(tr_ctx *ctx, int m, const double *X, double *AX, int on_device)
         dx.alloc(n, &ctx->budget, "matvec input");
         dax.alloc(n, &ctx->budget, "matvec output");
         TR_CUDA(cudaMemcpyAsync(dx.p, X, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
+        TR_CUDA(cudaMemsetAsync(ctx->flag.p + 1, 0, sizeof(int), ctx->st));
         tr::matvec(ctx, m, dx.p, dax.p);
         TR_CUDA(cudaMemcpyAsync(AX, dax.p, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->st));
+        int tc_err = 0;
+        TR_CUDA(cudaMemcpyAsync(&tc_err, ctx->flag.p + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
         TR_CUDA(cudaStreamSynchronize(ctx->st));
+        TR_REQUIRE(!tc_err, TR_ECUDA, "matvec: a tensor-core pipeline wait timed out");
         return TR_OK;
     });
 }

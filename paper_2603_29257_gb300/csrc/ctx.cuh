@@ -8,6 +8,7 @@
 #include "common.cuh"
 #include "ints.cuh"
 #include "linalg.cuh"
+#include "tcgemm.cuh"
 
 struct tr_ctx {
     tr_options opt{};
@@ -51,6 +52,11 @@ struct tr_ctx {
     tr::DevBuf<double> D;      // e_a - e_i [nocc][nvir]
     bool k_active = false;
 
+    // reduced-precision form: FP32 copies (value and tf32 remainder) and tensor maps
+    tr::DevBuf<float> Y32, Tab_h, Tab_l, T2_h, T2_l, Xw_h, Xw_l, Mt_h, Mt_l, X32, Z32;
+    tr::TcMat tm_tab, tm_t2, tm_xw, tm_mt;
+    int oKp = 0, vKp = 0, mixed_mb = 0, mixed_npk = 0;
+
     // workspaces
     tr::DevBuf<double> ws_split, ws_Z, ws_Z2, ws_Xw, ws_M;
     tr::DevBuf<int> flag;
@@ -92,6 +98,10 @@ void get_tensor(tr_ctx *c, int which, double *out, int on_device);
 void matvec(tr_ctx *c, int m, const double *X, double *AX);
 // allocate the matvec workspaces for blocks of up to m vectors
 void reserve_matvec(tr_ctx *c, int m);
+// reduced-precision form (mixed.cu)
+void build_mixed(tr_ctx *c);
+void reserve_mixed(tr_ctx *c, int mb);
+void matvec_mixed(tr_ctx *c, int m, const double *X, double *AX);
 int solve(tr_ctx *c, double *omega, double *X, double *resid, int on_device, tr_solve_info *info);
 
 }  // namespace tr

@@ -402,6 +402,7 @@ int solve(tr_ctx *c, double *omega, double *Xout, double *resid, int on_device, 
         TR_CUDA(cudaEventRecord(ev.e[5], st));
     };
 
+    TR_CUDA(cudaMemsetAsync(c->flag.p, 0, 2 * sizeof(int), st));
     // initial guess: unit vectors on the b0 smallest e_a - e_i (ties: lower index)
     std::vector<double> Dh(nov);
     TR_CUDA(cudaMemcpyAsync(Dh.data(), c->D.p, sizeof(double) * nov, cudaMemcpyDeviceToHost, st));
@@ -443,13 +444,14 @@ int solve(tr_ctx *c, double *omega, double *Xout, double *resid, int on_device, 
         TR_LAUNCH(pf, st, "residual", 0, 0, finish_norms<<<cdiv(n, 64), 64, 0, st>>>(c->part.p, nblk, n, c->rn.p));
         TR_CUDA(cudaMemcpyAsync(rn_h.data(), c->rn.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
         TR_CUDA(cudaMemcpyAsync(th_h.data(), c->theta.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
-        int jflag = 0;
-        TR_CUDA(cudaMemcpyAsync(&jflag, c->flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        int jflag[2] = {0, 0};
+        TR_CUDA(cudaMemcpyAsync(jflag, c->flag.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         TR_CUDA(cudaEventRecord(ev.e[2], st));
         TR_CUDA(cudaStreamSynchronize(st));
         t_eig += elapsed(ev.e[0], ev.e[1]);
         t_oth += elapsed(ev.e[1], ev.e[2]);
-        TR_REQUIRE(!jflag, TR_ECUDA, "solve: subspace eigensolver did not converge");
+        TR_REQUIRE(!jflag[0], TR_ECUDA, "solve: subspace eigensolver did not converge");
+        TR_REQUIRE(!jflag[1], TR_ECUDA, "solve: a tensor-core pipeline wait timed out");
         unconv.clear();
         for (int r = 0; r < n; ++r)
             if (!(rn_h[r] < tol)) unconv.push_back(r);

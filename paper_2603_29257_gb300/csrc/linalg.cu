@@ -21,15 +21,15 @@ constexpr int JACOBI_MAX_PAIRS_PER_BLOCK = 64;
 // Thread (tx, ty) of a 16 x 16 block computes TM x TN outputs at rows
 // ty + 16 i and columns tx + 16 j; the block tile is (16 TM) x (16 TN).
 // Skinny shapes (a dimension of a few dozen) use TM or TN = 1.
-template <bool TA, bool TB, int TM, int TN>
+template <typename TI, typename TC, bool TA, bool TB, int TM, int TN>
 __global__ void __launch_bounds__(NT)
-    dgemm_kernel(int M, int N, int K, double alpha, const double *__restrict__ A, long long lda,
-                 const double *__restrict__ B, long long ldb, double beta, double *__restrict__ C,
-                 long long ldc, Batch bt, int ksplit, int kchunk, double *__restrict__ ws)
+    gemm_kernel(int M, int N, int K, double alpha, const TI *__restrict__ A, long long lda,
+                const TI *__restrict__ B, long long ldb, double beta, TC *__restrict__ C,
+                long long ldc, Batch bt, int ksplit, int kchunk, double *__restrict__ ws)
 {
     constexpr int BM = 16 * TM, BN = 16 * TN;
-    __shared__ double As[BK][BM + 1];
-    __shared__ double Bs[BK][BN + 1];
+    __shared__ TI As[BK][BM + 1];
+    __shared__ TI Bs[BK][BN + 1];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int z = blockIdx.z;
     const int b = z / ksplit, ks = z - b * ksplit;
@@ -40,12 +40,12 @@ __global__ void __launch_bounds__(NT)
     const int kb = ks * kchunk;
     const int ke = min(K, kb + kchunk);
 
-    double acc[TM][TN];
+    TI acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
-    double ra[TM], rb[TN];
+        for (int j = 0; j < TN; ++j) acc[i][j] = (TI)0;
+    TI ra[TM], rb[TN];
 
     auto load = [&](int k0) {
 #pragma unroll
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(NT)
             const int kk = TA ? idx / BM : (idx & 15);
             const int mm = TA ? idx % BM : (idx >> 4);
             const int m = m0 + mm, k = k0 + kk;
-            ra[r] = (m < M && k < ke) ? (TA ? A[(long long)k * lda + m] : A[(long long)m * lda + k]) : 0.0;
+            ra[r] = (m < M && k < ke) ? (TA ? A[(long long)k * lda + m] : A[(long long)m * lda + k]) : (TI)0;
         }
 #pragma unroll
         for (int r = 0; r < TN; ++r) {
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(NT)
             const int kk = TB ? (idx & 15) : idx / BN;
             const int nn = TB ? (idx >> 4) : idx % BN;
             const int n = n0 + nn, k = k0 + kk;
-            rb[r] = (n < N && k < ke) ? (TB ? B[(long long)n * ldb + k] : B[(long long)k * ldb + n]) : 0.0;
+            rb[r] = (n < N && k < ke) ? (TB ? B[(long long)n * ldb + k] : B[(long long)k * ldb + n]) : (TI)0;
         }
     };
     auto store = [&]() {
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(NT)
         if (k0 + BK < ke) load(k0 + BK);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            double a[TM], bb[TN];
+            TI a[TM], bb[TN];
 #pragma unroll
             for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -114,17 +114,19 @@ __global__ void __launch_bounds__(NT)
             const int n = n0 + tx + 16 * j;
             if (n >= N) continue;
             if (ksplit == 1) {
-                double *c = C + b1 * bt.sC1 + b2 * bt.sC2 + (long long)m * ldc + n;
-                *c = (beta == 0.0) ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * *c);
+                TC *c = C + b1 * bt.sC1 + b2 * bt.sC2 + (long long)m * ldc + n;
+                const double v = (double)acc[i][j];
+                *c = (TC)((beta == 0.0) ? alpha * v : fma(alpha, v, beta * (double)*c));
             } else {
-                ws[((long long)(ks * nbatch + b) * M + m) * N + n] = acc[i][j];
+                ws[((long long)(ks * nbatch + b) * M + m) * N + n] = (double)acc[i][j];
             }
         }
     }
 }
 
+template <typename TC>
 __global__ void splitk_reduce(int M, int N, int nbatch, int ksplit, const double *__restrict__ ws,
-                              double alpha, double beta, double *__restrict__ C, long long ldc, Batch bt)
+                              double alpha, double beta, TC *__restrict__ C, long long ldc, Batch bt)
 {
     long long tot = (long long)nbatch * M * N;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
@@ -136,8 +138,8 @@ __global__ void splitk_reduce(int M, int N, int nbatch, int ksplit, const double
         double s = 0.0;
         for (int ks = 0; ks < ksplit; ++ks) s += ws[((long long)(ks * nbatch + b) * M + m) * N + n];
         int b1 = b / bt.n2, b2 = b - b1 * bt.n2;
-        double *c = C + b1 * bt.sC1 + b2 * bt.sC2 + (long long)m * ldc + n;
-        *c = (beta == 0.0) ? alpha * s : fma(alpha, s, beta * *c);
+        TC *c = C + b1 * bt.sC1 + b2 * bt.sC2 + (long long)m * ldc + n;
+        *c = (TC)((beta == 0.0) ? alpha * s : fma(alpha, s, beta * (double)*c));
     }
 }
 
@@ -337,26 +339,26 @@ __global__ void sum_rows_kernel(const double *__restrict__ a, int nrows, int n, 
     out[i] = s;
 }
 
-}  // namespace
-
-template <int TM, int TN>
+template <typename TI, typename TC, int TM, int TN>
 void launch_gemm(cudaStream_t st, bool ta, bool tb, dim3 grid, int M, int N, int K, double alpha,
-                 const double *A, long long lda, const double *B, long long ldb, double beta, double *C,
+                 const TI *A, long long lda, const TI *B, long long ldb, double beta, TC *C,
                  long long ldc, const Batch &bt, int ksplit, int kchunk, double *ws)
 {
     if (!ta && !tb)
-        dgemm_kernel<false, false, TM, TN><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
+        gemm_kernel<TI, TC, false, false, TM, TN><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
     else if (!ta && tb)
-        dgemm_kernel<false, true, TM, TN><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
+        gemm_kernel<TI, TC, false, true, TM, TN><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
     else if (ta && !tb)
-        dgemm_kernel<true, false, TM, TN><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
+        gemm_kernel<TI, TC, true, false, TM, TN><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
     else
-        dgemm_kernel<true, true, TM, TN><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
+        gemm_kernel<TI, TC, true, true, TM, TN><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
 }
 
-void dgemm(Prof &prof, cudaStream_t st, const char *name, bool ta, bool tb, int M, int N, int K,
-           double alpha, const double *A, long long lda, const double *B, long long ldb, double beta,
-           double *C, long long ldc, const Batch &bt, double *ws, size_t ws_elems, double alg_bytes)
+template <typename TI, typename TC>
+void gemm_any(Prof &prof, cudaStream_t st, const char *name, bool ta, bool tb, int M, int N, int K,
+              double alpha, const TI *A, long long lda, const TI *B, long long ldb, double beta,
+              TC *C, long long ldc, const Batch &bt, double *ws, size_t ws_elems, double alg_bytes,
+              int max_kchunk)
 {
     if (M <= 0 || N <= 0 || bt.count() <= 0) return;
     const int nb = bt.count();
@@ -370,8 +372,9 @@ void dgemm(Prof &prof, cudaStream_t st, const char *name, bool ta, bool tb, int 
     long long tiles = (long long)cdiv(M, BMx) * cdiv(N, BNx) * nb;
     int ksplit = 1;
     const long long target = 4 * 152;
-    if (ws && tiles < target && K >= 4 * 256) {
+    if (ws && ((tiles < target && K >= 4 * 256) || (max_kchunk > 0 && K > max_kchunk))) {
         long long want = std::min<long long>((target + tiles - 1) / tiles, K / 256);
+        if (max_kchunk > 0) want = std::max<long long>(want, (K + max_kchunk - 1) / max_kchunk);
         long long cap = (long long)(ws_elems / ((size_t)nb * M * N));
         ksplit = (int)std::max<long long>(1, std::min(want, cap));
         ksplit = std::min(ksplit, 65535 / nb);
@@ -382,29 +385,48 @@ void dgemm(Prof &prof, cudaStream_t st, const char *name, bool ta, bool tb, int 
         kchunk = (int)(((K + ksplit - 1) / ksplit + BK - 1) / BK * BK);
         ksplit = (K + kchunk - 1) / kchunk;
     }
-    TR_REQUIRE((long long)nb * ksplit <= 65535, TR_EINVAL, "dgemm: batch too large");
-    TR_REQUIRE(cdiv(M, BMx) <= 65535, TR_EINVAL, "dgemm: M too large");
+    TR_REQUIRE((long long)nb * ksplit <= 65535, TR_EINVAL, "gemm: batch too large");
+    TR_REQUIRE(cdiv(M, BMx) <= 65535, TR_EINVAL, "gemm: M too large");
     dim3 grid(cdiv(N, BNx), cdiv(M, BMx), nb * ksplit);
     double flops = 2.0 * M * N * (double)K * nb;
-    double bytes = alg_bytes >= 0 ? alg_bytes : 8.0 * ((double)M * K + (double)K * N + 2.0 * M * N) * nb;
+    double bytes = alg_bytes >= 0 ? alg_bytes
+                                  : (double)sizeof(TI) * ((double)M * K + (double)K * N) * nb + 2.0 * sizeof(TC) * M * N * nb;
     int tok = prof.begin(st, name, flops, bytes);
     if (TM == 4 && TN == 4)
-        launch_gemm<4, 4>(st, ta, tb, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
+        launch_gemm<TI, TC, 4, 4>(st, ta, tb, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
     else if (TM == 1 && TN == 4)
-        launch_gemm<1, 4>(st, ta, tb, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
+        launch_gemm<TI, TC, 1, 4>(st, ta, tb, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
     else if (TM == 4 && TN == 1)
-        launch_gemm<4, 1>(st, ta, tb, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
+        launch_gemm<TI, TC, 4, 1>(st, ta, tb, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
     else
-        launch_gemm<1, 1>(st, ta, tb, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
+        launch_gemm<TI, TC, 1, 1>(st, ta, tb, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
     TR_CUDA(cudaGetLastError());
     if (ksplit > 1) {
         prof.launches += 1;
         long long tot = (long long)nb * M * N;
         int blocks = (int)std::min<long long>(cdiv(tot, 256), 4096);
-        splitk_reduce<<<blocks, 256, 0, st>>>(M, N, nb, ksplit, ws, alpha, beta, C, ldc, bt);
+        splitk_reduce<TC><<<blocks, 256, 0, st>>>(M, N, nb, ksplit, ws, alpha, beta, C, ldc, bt);
         TR_CUDA(cudaGetLastError());
     }
     prof.end(st, tok);
+}
+
+}  // namespace
+
+void dgemm(Prof &prof, cudaStream_t st, const char *name, bool ta, bool tb, int M, int N, int K,
+           double alpha, const double *A, long long lda, const double *B, long long ldb, double beta,
+           double *C, long long ldc, const Batch &bt, double *ws, size_t ws_elems, double alg_bytes)
+{
+    gemm_any<double, double>(prof, st, name, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ws,
+                             ws_elems, alg_bytes, 0);
+}
+
+void sgemm(Prof &prof, cudaStream_t st, const char *name, bool ta, bool tb, int M, int N, int K,
+           double alpha, const float *A, long long lda, const float *B, long long ldb, double beta,
+           double *C, long long ldc, const Batch &bt, double *ws, size_t ws_elems, int max_kchunk)
+{
+    gemm_any<float, double>(prof, st, name, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ws,
+                            ws_elems, -1.0, max_kchunk);
 }
 
 void cholesky(Prof &prof, cudaStream_t st, double *G, int n, int *flag)

@@ -25,6 +25,13 @@ void dgemm(Prof &prof, cudaStream_t st, const char *name, bool ta, bool tb, int 
            double beta, double *C, long long ldc, const Batch &bt, double *ws, size_t ws_elems,
            double alg_bytes = -1.0);
 
+// Same for FP32 operands accumulated in FP32 per K chunk (at most max_kchunk
+// when > 0, else chosen by the split heuristic) with FP64 partial sums and an
+// FP64 output.
+void sgemm(Prof &prof, cudaStream_t st, const char *name, bool ta, bool tb, int M, int N, int K,
+           double alpha, const float *A, long long lda, const float *B, long long ldb, double beta,
+           double *C, long long ldc, const Batch &bt, double *ws, size_t ws_elems, int max_kchunk = 0);
+
 // Lower Cholesky factor in place (upper triangle untouched): G = L L^T.
 // flag (device int) is set to 1 + column on the first non-positive pivot.
 void cholesky(Prof &prof, cudaStream_t st, double *G, int n, int *flag);

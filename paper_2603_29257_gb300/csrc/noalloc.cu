@@ -80,6 +80,7 @@ namespace tr {
 void matvec_noalloc(tr_ctx *c, int m, const double *X, double *AX)
 {
     TR_REQUIRE(c->built, TR_EINVAL, "matvec_noalloc: call tr_build first");
+    TR_REQUIRE(c->opt.precision == TR_FP64, TR_EINVAL, "matvec_noalloc: only the FP64 form is available");
     if (m <= 0) return;
     int dev = -1;
     TR_CUDA(cudaGetDevice(&dev));

@@ -1,0 +1,379 @@
+// Tensor-core GEMM C = A B^T on GB300 (sm_103a): tcgen05.mma kind::tf32.
+//
+// One CTA computes a 128 x 128 output tile of one batch entry.  Warp 0 (one
+// lane) streams 128 x 32 FP32 tiles of A and B through a 3-stage ring of
+// shared memory with TMA (cp.async.bulk.tensor, 128-byte swizzle, completion
+// on an mbarrier); warp 1 (one lane) issues tcgen05.mma into a 128-column
+// FP32 accumulator in tensor memory and releases each stage with
+// tcgen05.commit; after the last commit all four warps read their 32 TMEM
+// lanes with tcgen05.ld and write the tile.  With three products
+// (hi*hi + hi*lo + lo*hi) the result carries close to FP32 accuracy.
+// Every mbarrier wait gives up after ~1 s: it records an error code in *err
+// and the CTA skips ahead to its teardown (tensor memory is always freed).
+#include "tcgemm.cuh"
+
+#include <cuda.h>
+
+#include <algorithm>
+#include <mutex>
+
+namespace tr {
+namespace {
+
+constexpr int BM = 128, BN = 128, BKF = 32;   // tile: 128 x 128 outputs, 32 FP32 (128 B) of K per stage
+constexpr int TILE_BYTES = BM * BKF * 4;      // 16 KB
+constexpr long long WAIT_CYCLES = 2000000000LL;
+
+struct TcArgs {
+    int M, N, K, n2;
+    int ka0, kb0;                 // K offsets (elements) into the A and B rows
+    long long a0, a1, a2, c0, c1, c2;
+    TcOut out;
+    int *err;
+};
+
+__device__ __forceinline__ uint32_t sa(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(uint32_t a, uint32_t n)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint32_t a, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool bar_wait(uint32_t a, uint32_t parity, int *err, int code)
+{
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > WAIT_CYCLES) {
+            atomicCAS(err, 0, code);
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void tma2d(uint32_t dst, const CUtensorMap *tm, int x, int y, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"((uint64_t)tm), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
+{
+    uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                 "l"(a), "l"(b), "r"(idesc), "r"(acc)
+                 : "memory");
+}
+__device__ __forceinline__ void commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ float tf32_rest(float v)
+{
+    return v - __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+}
+
+template <int NSPLIT, int MODE>
+__global__ void __launch_bounds__(128, 1)
+    tc_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
+              const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl, const TcArgs g)
+{
+    constexpr int STAGES = NSPLIT == 3 ? 3 : 4;
+    constexpr int NT = NSPLIT == 3 ? 4 : 2;
+    constexpr uint32_t STAGE_BYTES = NT * TILE_BYTES;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = (uint64_t *)(smem + STAGES * STAGE_BYTES);  // full[S], empty[S], done
+    uint32_t *tslot = (uint32_t *)(bars + 2 * STAGES + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int b = blockIdx.z, b1 = b / g.n2, b2 = b - b1 * g.n2;
+    const int arow = (int)(g.a0 + g.a1 * b1 + g.a2 * b2) + m0;
+    const int brow = (int)(g.c0 + g.c1 * b1 + g.c2 * b2) + n0;
+    const int nk = (g.K + BKF - 1) / BKF;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2 * STAGES + 1; ++s) bar_init(sa(&bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(tslot)), "r"(BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int kt = 0; kt < nk; ++kt) {
+                const int s = kt % STAGES;
+                if (kt >= STAGES && !bar_wait(sa(&bars[STAGES + s]), ((kt / STAGES) - 1) & 1, g.err, 1)) break;
+                const uint32_t full = sa(&bars[s]);
+                bar_expect(full, STAGE_BYTES);
+                uint8_t *stg = smem + s * STAGE_BYTES;
+                const int xa = g.ka0 + kt * BKF, xb = g.kb0 + kt * BKF;
+                tma2d(sa(stg), &tAh, xa, arow, full);
+                tma2d(sa(stg + TILE_BYTES), &tBh, xb, brow, full);
+                if (NSPLIT == 3) {
+                    tma2d(sa(stg + 2 * TILE_BYTES), &tAl, xa, arow, full);
+                    tma2d(sa(stg + 3 * TILE_BYTES), &tBl, xb, brow, full);
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // kind::tf32 instruction descriptor: FP32 accumulator, TF32 A and B, both
+            // K-major, N = 128, M = 128
+            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                   ((uint32_t)(BM >> 4) << 24);
+            for (int kt = 0; kt < nk; ++kt) {
+                const int s = kt % STAGES;
+                if (!bar_wait(sa(&bars[s]), (kt / STAGES) & 1, g.err, 2)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                uint8_t *stg = smem + s * STAGE_BYTES;
+                const uint64_t dA = smem_desc(sa(stg)), dB = smem_desc(sa(stg + TILE_BYTES));
+                const uint64_t dAl = smem_desc(sa(stg + 2 * TILE_BYTES)), dBl = smem_desc(sa(stg + 3 * TILE_BYTES));
+#pragma unroll
+                for (int kk = 0; kk < BKF / 8; ++kk) {
+                    mma(tmem, dA + 2 * kk, dB + 2 * kk, idesc, (kt | kk) ? 1u : 0u);
+                    if (NSPLIT == 3) {
+                        mma(tmem, dA + 2 * kk, dBl + 2 * kk, idesc, 1u);
+                        mma(tmem, dAl + 2 * kk, dB + 2 * kk, idesc, 1u);
+                    }
+                }
+                commit(sa(&bars[STAGES + s]));
+            }
+            commit(sa(&bars[2 * STAGES]));
+        }
+        __syncwarp();
+    }
+
+    const bool ok = bar_wait(sa(&bars[2 * STAGES]), 0, g.err, 3);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const TcOut &o = g.out;
+        const long long base = o.s1 * b1 + o.s2 * b2;
+        const int rloc = 32 * warp + lane;
+        const int row = m0 + rloc;
+        // warp-private transpose buffer in the (now idle) pipeline ring
+        double *tb = (double *)smem + warp * 32 * 33;
+        for (int c0 = 0; c0 < BN && n0 + c0 < g.N; c0 += 32) {
+            uint32_t r[32];
+            const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (o.ldm == 1) {
+                // consecutive lanes hold consecutive rows: write directly (coalesced)
+                if (row < g.M) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = n0 + c0 + j;
+                        if (col >= g.N) break;
+                        const long long off = base + (long long)row + (long long)col * o.ldn;
+                        const float v = __uint_as_float(r[j]);
+                        if (MODE == TC_SPLIT) {
+                            o.hi[off] = v;
+                            o.lo[off] = tf32_rest(v);
+                        } else if (MODE == TC_ACC64) {
+                            o.d[off] += o.alpha * (double)v;
+                        } else {
+                            o.d[off] = o.alpha * (double)v;
+                        }
+                    }
+                }
+            } else {
+                // transpose 32 x 32 through shared memory so that lanes walk columns
+#pragma unroll
+                for (int j = 0; j < 32; ++j) tb[lane * 33 + j] = (double)__uint_as_float(r[j]);
+                __syncwarp();
+                const int col = n0 + c0 + lane;
+                for (int rr = 0; rr < 32; ++rr) {
+                    const int rw = m0 + 32 * warp + rr;
+                    if (rw >= g.M || col >= g.N) continue;
+                    const long long off = base + (long long)rw * o.ldm + (long long)col * o.ldn;
+                    const double v = tb[rr * 33 + lane];
+                    if (MODE == TC_SPLIT) {
+                        const float f = (float)v;
+                        o.hi[off] = f;
+                        o.lo[off] = tf32_rest(f);
+                    } else if (MODE == TC_ACC64) {
+                        o.d[off] += o.alpha * v;
+                    } else {
+                        o.d[off] = o.alpha * v;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        (void)rloc;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+}
+
+__global__ void split_kernel(const double *__restrict__ x, long long rows, long long cols, long long ldi,
+                             float *__restrict__ hi, float *__restrict__ lo, long long ldo)
+{
+    const long long tot = rows * cols;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+        const long long r = t / cols, c = t - r * cols;
+        const float f = (float)x[r * ldi + c];
+        hi[r * ldo + c] = f;
+        lo[r * ldo + c] = tf32_rest(f);
+    }
+}
+
+typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder()
+{
+    static EncodeTiled fn = nullptr;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        TR_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+        TR_REQUIRE(q == cudaDriverEntryPointSuccess && p, TR_ECUDA, "cuTensorMapEncodeTiled unavailable");
+        fn = (EncodeTiled)p;
+    }
+    return fn;
+}
+
+void encode(CUtensorMap &tm, const float *p, long long rows, long long kdim, long long ld)
+{
+    cuuint64_t gdim[2] = {(cuuint64_t)kdim, (cuuint64_t)rows};
+    cuuint64_t gstr[1] = {(cuuint64_t)ld * 4};
+    cuuint32_t box[2] = {BKF, BM};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = encoder()(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)p, gdim, gstr, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    TR_REQUIRE(r == CUDA_SUCCESS, TR_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+}
+
+template <int NSPLIT, int MODE>
+void launch(cudaStream_t st, dim3 grid, const TcMat &A, const TcMat &B, const TcArgs &g)
+{
+    constexpr int STAGES = NSPLIT == 3 ? 3 : 4;
+    constexpr int NT = NSPLIT == 3 ? 4 : 2;
+    const size_t smem = (size_t)STAGES * NT * TILE_BYTES + 1024 + 256;
+    static bool attr = false;
+    if (!attr) {
+        TR_CUDA(cudaFuncSetAttribute(tc_kernel<NSPLIT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    tc_kernel<NSPLIT, MODE><<<grid, 128, smem, st>>>(A.mhi, NSPLIT == 3 ? A.mlo : A.mhi, B.mhi,
+                                                     NSPLIT == 3 ? B.mlo : B.mhi, g);
+}
+
+}  // namespace
+
+void tc_make(TcMat &m, const float *hi, const float *lo, long long rows, long long kdim, long long ld)
+{
+    TR_REQUIRE((ld * 4) % 16 == 0, TR_EINVAL, "tensor-core operand: row stride must be a multiple of 16 bytes");
+    TR_REQUIRE(((uintptr_t)hi % 16) == 0 && (!lo || ((uintptr_t)lo % 16) == 0), TR_EINVAL,
+               "tensor-core operand: base must be 16-byte aligned");
+    TR_REQUIRE(rows > 0 && kdim > 0 && rows < (1LL << 31) && kdim <= ld, TR_EINVAL, "tensor-core operand: bad shape");
+    m.hi = hi;
+    m.lo = lo;
+    m.rows = rows;
+    m.kdim = kdim;
+    m.ld = ld;
+    encode(m.mhi, hi, rows, kdim, ld);
+    if (lo) encode(m.mlo, lo, rows, kdim, ld);
+    else m.mlo = m.mhi;
+}
+
+void tc_gemm(Prof &prof, cudaStream_t st, const char *name, int nsplit, const TcMat &A, long long a0, long long a1,
+             long long a2, int ka0, const TcMat &B, long long c0, long long c1, long long c2, int kb0, int M, int N,
+             int K, int n1, int n2, const TcOut &out, int *err, double alg_bytes)
+{
+    if (M <= 0 || N <= 0 || n1 <= 0 || n2 <= 0) return;
+    TR_REQUIRE(nsplit == 1 || nsplit == 3, TR_EINVAL, "tc_gemm: nsplit must be 1 or 3");
+    TR_REQUIRE(nsplit == 1 || (A.lo && B.lo), TR_EINVAL, "tc_gemm: 3-product form needs lo parts");
+    TR_REQUIRE(K > 0 && ka0 >= 0 && kb0 >= 0 && ka0 + K <= A.kdim && kb0 + K <= B.kdim, TR_EINVAL, "tc_gemm: bad K");
+    TR_REQUIRE(ka0 % 4 == 0 && kb0 % 4 == 0, TR_EINVAL, "tc_gemm: K offsets must be 16-byte aligned");
+    TR_REQUIRE((long long)n1 * n2 <= 65535 && cdiv(M, BM) <= 65535, TR_EINVAL, "tc_gemm: grid too large");
+    // every row a CTA addresses must exist in the operand views (rows past M may
+    // belong to the next batch entry and are discarded)
+    const long long lastA = a0 + a1 * (n1 - 1) + a2 * (n2 - 1) + (long long)cdiv(M, BM) * BM;
+    const long long lastB = c0 + c1 * (n1 - 1) + c2 * (n2 - 1) + (long long)cdiv(N, BN) * BN;
+    TR_REQUIRE(a0 >= 0 && c0 >= 0 && a1 >= 0 && a2 >= 0 && c1 >= 0 && c2 >= 0, TR_EINVAL, "tc_gemm: negative row offset");
+    TR_REQUIRE(lastA < (1LL << 31) && lastB < (1LL << 31), TR_EINVAL, "tc_gemm: row index overflow");
+    TcArgs g;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.n2 = n2;
+    g.ka0 = ka0;
+    g.kb0 = kb0;
+    g.a0 = a0;
+    g.c0 = c0;
+    g.a1 = a1;
+    g.a2 = a2;
+    g.c1 = c1;
+    g.c2 = c2;
+    g.out = out;
+    g.err = err;
+    dim3 grid(cdiv(N, BN), cdiv(M, BM), n1 * n2);
+    const double flops = 2.0 * M * N * (double)K * n1 * n2;
+    const double bytes = alg_bytes >= 0 ? alg_bytes : 4.0 * nsplit * ((double)M + N) * K * n1 * n2;
+    int tok = prof.begin(st, name, flops, bytes);
+    if (nsplit == 3) {
+        if (out.mode == TC_SPLIT) launch<3, TC_SPLIT>(st, grid, A, B, g);
+        else if (out.mode == TC_ACC64) launch<3, TC_ACC64>(st, grid, A, B, g);
+        else launch<3, TC_STORE64>(st, grid, A, B, g);
+    } else {
+        if (out.mode == TC_SPLIT) launch<1, TC_SPLIT>(st, grid, A, B, g);
+        else if (out.mode == TC_ACC64) launch<1, TC_ACC64>(st, grid, A, B, g);
+        else launch<1, TC_STORE64>(st, grid, A, B, g);
+    }
+    TR_CUDA(cudaGetLastError());
+    prof.end(st, tok);
+}
+
+void tc_split(Prof &prof, cudaStream_t st, const double *x, long long rows, long long cols, long long ld_in, float *hi,
+              float *lo, long long ld_out)
+{
+    const long long tot = rows * cols;
+    if (tot <= 0) return;
+    const unsigned blocks = (unsigned)std::min<long long>(cdiv(tot, 256), 152 * 16);
+    TR_LAUNCH(prof, st, "split_f32", 0, 16.0 * tot, split_kernel<<<blocks, 256, 0, st>>>(x, rows, cols, ld_in, hi, lo, ld_out));
+}
+
+}  // namespace tr

@@ -369,6 +369,7 @@ void build(tr_ctx *c)
     c->D.alloc(std::max<long long>(nov, 1), &c->budget, "orbital differences");
     TR_LAUNCH(pf, st, "orbital_diff", 0, 0, orbital_diff<<<grid_for(nov), 256, 0, st>>>(c->eps.p, nocc, nvir, c->D.p));
     TR_CUDA(cudaStreamSynchronize(st));
+    if (c->opt.precision == TR_MIXED) build_mixed(c);
     c->built = true;
 }
 
@@ -438,6 +439,10 @@ void reserve_matvec(tr_ctx *c, int m)
     c->ws_split.reserve((size_t)16 << 20, &c->budget, "split-K workspace");
     c->ws_Z.reserve((size_t)std::max(c->nJ, 1) * mb, &c->budget, "J workspace");
     c->ws_Z2.reserve((size_t)std::max(c->nJ, 1) * mb, &c->budget, "J workspace");
+    if (c->opt.precision == TR_MIXED) {
+        reserve_mixed(c, mb);
+        return;
+    }
     if (c->k_active) {
         c->ws_Xw.reserve((size_t)mb * c->oK * c->vK, &c->budget, "K workspace");
         c->ws_M.reserve((size_t)matvec_pchunk(c, mb) * mb * c->oK * c->vK, &c->budget, "K workspace");
@@ -448,6 +453,10 @@ void matvec(tr_ctx *c, int m, const double *X, double *AX)
 {
     TR_REQUIRE(c->built, TR_EINVAL, "matvec: call tr_build first");
     if (m <= 0) return;
+    if (c->opt.precision == TR_MIXED) {
+        matvec_mixed(c, m, X, AX);
+        return;
+    }
     cudaStream_t st = c->st;
     Prof &pf = c->prof;
     const int nocc = c->nocc, nvir = c->nvir, nJ = c->nJ, nK = c->nK;

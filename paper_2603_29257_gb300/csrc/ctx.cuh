@@ -98,7 +98,10 @@ void get_tensor(tr_ctx *c, int which, double *out, int on_device);
 void matvec(tr_ctx *c, int m, const double *X, double *AX);
 // allocate the matvec workspaces for blocks of up to m vectors
 void reserve_matvec(tr_ctx *c, int m);
+// three-centre integrals of aux functions [p0, p0+np) of set which (0 = J, 1 = K)
+void compute_int3c_chunk(tr_ctx *c, int which, int p0, int np, double *out);
 // reduced-precision form (mixed.cu)
+void get_tensor_mixed(tr_ctx *c, int which, double *out, int on_device);
 void build_mixed(tr_ctx *c);
 void reserve_mixed(tr_ctx *c, int mb);
 void matvec_mixed(tr_ctx *c, int m, const double *X, double *AX);

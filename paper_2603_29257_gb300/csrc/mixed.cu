@@ -4,6 +4,7 @@
 //   - the three-centre integrals, metrics and MO transforms are built in FP64
 //     and the MO tensors are then rounded to FP32 (the paper builds its
 //     integrals in FP64 and runs everything after them in FP32, Sec. 3.3);
+//     see build_mixed for why the transforms themselves stay FP64;
 //   - J: Z = (Q|jb) X and J = (P|ia) Zt as FP32 GEMMs on the CUDA cores, summed
 //     in FP32 over chunks of at most 4096 terms and in FP64 across chunks;
 //     (P|Q)^-1 is applied in FP64;
@@ -58,16 +59,57 @@ int pad32(int x) { return (x + 31) / 32 * 32; }
 
 }  // namespace
 
+namespace {
+
+__global__ void unpad_f32(const float *__restrict__ x, long long rows, int cols, int ld, double *__restrict__ y)
+{
+    const long long tot = rows * cols;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+        const long long r = t / cols;
+        y[t] = (double)x[r * ld + (t - r * cols)];
+    }
+}
+
+}  // namespace
+
+void get_tensor_mixed(tr_ctx *c, int which, double *out, int on_device)
+{
+    DevBuf<double> tmp;
+    size_t n = 0;
+    if (which == 0) {
+        n = (size_t)c->nJ * c->nov;
+        if (!n) return;
+        tmp.alloc(n, &c->budget, "tensor copy");
+        TR_LAUNCH(c->prof, c->st, "unpad", 0, 0,
+                  unpad_f32<<<gfor(n), 256, 0, c->st>>>(c->Y32.p, (long long)c->nJ * c->nocc, c->nvir, c->nvir, tmp.p));
+    } else {
+        n = c->k_active ? (size_t)c->nK * c->vK * c->vK : 0;
+        if (!n) return;
+        tmp.alloc(n, &c->budget, "tensor copy");
+        TR_LAUNCH(c->prof, c->st, "unpad", 0, 0,
+                  unpad_f32<<<gfor(n), 256, 0, c->st>>>(c->Tab_h.p, (long long)c->nK * c->vK, c->vK, c->vKp, tmp.p));
+    }
+    TR_CUDA(cudaMemcpyAsync(out, tmp.p, sizeof(double) * n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            c->st));
+    TR_CUDA(cudaStreamSynchronize(c->st));
+}
+
+// After the FP64 transforms: (P|ia) rounded to FP32 for the J contractions;
+// T_ab^P and T_ij^P (metric applied) split into value and tf32 remainder with
+// padded rows for the tensor-core K contraction; tensor maps of the K operands.
+// The MO transforms themselves stay FP64: with C = S^-1/2 Q the sums over AO
+// indices cancel terms tens of times larger than their result, and FP32
+// accumulation on the tensor cores then leaves ~1e-4 relative errors in
+// (P|ia), too close to the 1e-5 Ha target of this form.
 void build_mixed(tr_ctx *c)
 {
     cudaStream_t st = c->st;
     Prof &pf = c->prof;
     const long long nov = c->nov;
     c->Y32.alloc((size_t)std::max(c->nJ, 1) * nov, &c->budget, "(P|ia) FP32");
-    if (c->nJ) {
+    if (c->nJ)
         TR_LAUNCH(pf, st, "to_f32", 0, 12.0 * c->nJ * nov,
                   to_f32<<<gfor(c->nJ * nov), 256, 0, st>>>(c->Y.p, c->Y32.p, c->nJ * nov));
-    }
     c->oKp = pad32(std::max(c->oK, 1));
     c->vKp = pad32(std::max(c->vK, 1));
     if (c->k_active) {
@@ -83,8 +125,11 @@ void build_mixed(tr_ctx *c)
         tc_make(c->tm_tab, c->Tab_h.p, c->Tab_l.p, (long long)nK * vK, vK, vKp);
         tc_make(c->tm_t2, c->T2_h.p, c->T2_l.p, oK, (long long)nK * oKp, (long long)nK * oKp);
     }
-    c->mixed_mb = 0;  // workspaces are sized at the first product
+    // the FP32 copies are what the products use; the FP64 (P|ia) and T_ab are freed
     TR_CUDA(cudaStreamSynchronize(st));
+    c->Y.release();
+    c->Tab.release();
+    c->mixed_mb = 0;  // workspaces are sized at the first product
 }
 
 void reserve_mixed(tr_ctx *c, int mb)

@@ -204,6 +204,8 @@ __global__ void __launch_bounds__(128, 1)
                         if (MODE == TC_SPLIT) {
                             o.hi[off] = v;
                             o.lo[off] = tf32_rest(v);
+                        } else if (MODE == TC_STORE32) {
+                            o.hi[off] = v;
                         } else if (MODE == TC_ACC64) {
                             o.d[off] += o.alpha * (double)v;
                         } else {
@@ -226,6 +228,8 @@ __global__ void __launch_bounds__(128, 1)
                         const float f = (float)v;
                         o.hi[off] = f;
                         o.lo[off] = tf32_rest(f);
+                    } else if (MODE == TC_STORE32) {
+                        o.hi[off] = (float)v;
                     } else if (MODE == TC_ACC64) {
                         o.d[off] += o.alpha * v;
                     } else {
@@ -357,10 +361,12 @@ void tc_gemm(Prof &prof, cudaStream_t st, const char *name, int nsplit, const Tc
     if (nsplit == 3) {
         if (out.mode == TC_SPLIT) launch<3, TC_SPLIT>(st, grid, A, B, g);
         else if (out.mode == TC_ACC64) launch<3, TC_ACC64>(st, grid, A, B, g);
+        else if (out.mode == TC_STORE32) launch<3, TC_STORE32>(st, grid, A, B, g);
         else launch<3, TC_STORE64>(st, grid, A, B, g);
     } else {
         if (out.mode == TC_SPLIT) launch<1, TC_SPLIT>(st, grid, A, B, g);
         else if (out.mode == TC_ACC64) launch<1, TC_ACC64>(st, grid, A, B, g);
+        else if (out.mode == TC_STORE32) launch<1, TC_STORE32>(st, grid, A, B, g);
         else launch<1, TC_STORE64>(st, grid, A, B, g);
     }
     TR_CUDA(cudaGetLastError());

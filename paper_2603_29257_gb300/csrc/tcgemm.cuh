@@ -27,7 +27,8 @@ void tc_make(TcMat &m, const float *hi, const float *lo, long long rows, long lo
 // SPLIT: hi[off] = acc, lo[off] = acc - tf32(acc)      (FP32 outputs)
 // ACC64: d[off] += alpha * acc                         (FP64 output)
 // STORE64: d[off] = alpha * acc                        (FP64 output)
-enum TcEpi { TC_SPLIT = 0, TC_ACC64 = 1, TC_STORE64 = 2 };
+// STORE32: hi[off] = acc                               (FP32 output)
+enum TcEpi { TC_SPLIT = 0, TC_ACC64 = 1, TC_STORE64 = 2, TC_STORE32 = 3 };
 struct TcOut {
     int mode = TC_SPLIT;
     float *hi = nullptr, *lo = nullptr;

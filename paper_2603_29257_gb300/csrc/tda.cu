@@ -271,17 +271,91 @@ void set_orbitals(tr_ctx *c, int nao, int nmo, int nocc, const double *C, const 
     c->have_orb = true;
 }
 
-void build(tr_ctx *c)
+void compute_int3c_chunk(tr_ctx *c, int which, int p0, int np, double *out)
 {
-    TR_REQUIRE(c->have_mol && c->have_orb, TR_EINVAL, "build: molecule and orbitals required");
-    c->built = false;
+    if (which == 0)
+        compute_int3c(c, c->auxJ_h, p0, np, out, 1.0, 0.0, 0.0);
+    else
+        compute_int3c(c, c->auxK_h, p0, np, out, c->opt.k_alpha, c->opt.k_beta, c->opt.omega);
+}
+
+// FP64 MO transforms: (P|ia); (P|ij), (P|ab) on the window; T_ij = G_K^-1 (P|ij)
+static void transforms_fp64(tr_ctx *c, DevBuf<double> &Iij)
+{
     const int nao = c->nao, nocc = c->nocc, nvir = c->nvir, nmo = c->nmo, nJ = c->nJ, nK = c->nK;
     const long long nov = c->nov;
     cudaStream_t st = c->st;
     Prof &pf = c->prof;
-    c->ws_split.reserve((size_t)16 << 20, &c->budget, "split-K workspace");
+    c->Y.alloc((size_t)nJ * nov, &c->budget, "(P|ia)");
+    const int hrows = std::max(nocc, std::max(c->oK, c->vK));
+    size_t per = (size_t)nao * nao + (size_t)hrows * nao;
+    int npc = (int)std::max<size_t>(1, c->opt.aux_chunk_bytes / (per * sizeof(double)));
+    npc = std::max(1, std::min(npc, std::max(nJ, nK)));
+    DevBuf<double> I, H;
+    I.alloc((size_t)npc * nao * nao, &c->budget, "AO integral chunk");
+    H.alloc((size_t)npc * hrows * nao, &c->budget, "half-transform chunk");
+    for (int p0 = 0; p0 < nJ; p0 += npc) {
+        int np = std::min(npc, nJ - p0);
+        compute_int3c_chunk(c, 0, p0, np, I.p);
+        Batch b1;
+        b1.n1 = np;
+        b1.sB1 = (long long)nao * nao;
+        b1.sC1 = (long long)nocc * nao;
+        dgemm(pf, st, "xform_J1", true, false, nocc, nao, nao, 1.0, c->C.p, nmo, I.p, nao, 0.0, H.p, nao, b1,
+              nullptr, 0);
+        Batch b2;
+        b2.n1 = np;
+        b2.sA1 = (long long)nocc * nao;
+        b2.sC1 = nov;
+        dgemm(pf, st, "xform_J2", false, false, nocc, nvir, nao, 1.0, H.p, nao, c->C.p + nocc, nmo, 0.0,
+              c->Y.p + (long long)p0 * nov, nvir, b2, nullptr, 0);
+    }
+    if (!c->k_active) return;
+    const int oK = c->oK, vK = c->vK, o0 = c->o0;
+    c->Tab.alloc((size_t)nK * vK * vK, &c->budget, "T_ab");
+    for (int p0 = 0; p0 < nK; p0 += npc) {
+        int np = std::min(npc, nK - p0);
+        compute_int3c_chunk(c, 1, p0, np, I.p);
+        Batch h;
+        h.n1 = np;
+        h.sB1 = (long long)nao * nao;
+        h.sC1 = (long long)oK * nao;
+        dgemm(pf, st, "xform_K1", true, false, oK, nao, nao, 1.0, c->C.p + o0, nmo, I.p, nao, 0.0, H.p, nao, h,
+              nullptr, 0);
+        Batch g;
+        g.n1 = np;
+        g.sA1 = (long long)oK * nao;
+        g.sC1 = (long long)oK * oK;
+        dgemm(pf, st, "xform_K2", false, false, oK, oK, nao, 1.0, H.p, nao, c->C.p + o0, nmo, 0.0,
+              Iij.p + (long long)p0 * oK * oK, oK, g, nullptr, 0);
+        h.sC1 = (long long)vK * nao;
+        dgemm(pf, st, "xform_K1", true, false, vK, nao, nao, 1.0, c->C.p + nocc, nmo, I.p, nao, 0.0, H.p, nao, h,
+              nullptr, 0);
+        g.sA1 = (long long)vK * nao;
+        g.sC1 = (long long)vK * vK;
+        dgemm(pf, st, "xform_K2", false, false, vK, vK, nao, 1.0, H.p, nao, c->C.p + nocc, nmo, 0.0,
+              c->Tab.p + (long long)p0 * vK * vK, vK, g, nullptr, 0);
+    }
+}
 
-    // Coulomb metric and its inverse (Sec. 2, Eq. RI)
+void build(tr_ctx *c)
+{
+    TR_REQUIRE(c->have_mol && c->have_orb, TR_EINVAL, "build: molecule and orbitals required");
+    c->built = false;
+    const int nocc = c->nocc, nvir = c->nvir, nJ = c->nJ, nK = c->nK;
+    const long long nov = c->nov;
+    cudaStream_t st = c->st;
+    Prof &pf = c->prof;
+    const bool mixed = c->opt.precision == TR_MIXED;
+    c->ws_split.reserve((size_t)16 << 20, &c->budget, "split-K workspace");
+    c->k_active = nK > 0 && c->oK > 0 && c->vK > 0 && c->opt.cx != 0.0;
+    c->Y.release();
+    c->Y32.release();
+    c->Tab.release();
+    c->T2.release();
+    c->GinvK.release();
+
+    // metrics and their inverses (Sec. 2, Eq. RI; K metric with the K operator, Sec. 3.2)
     c->GinvJ.alloc((size_t)nJ * nJ, &c->budget, "J metric");
     if (nJ) {
         DevBuf<double> G;
@@ -289,71 +363,20 @@ void build(tr_ctx *c)
         metric(c, c->auxJ_h, 1.0, 0.0, 0.0, G.p);
         metric_inverse(c, G.p, nJ, c->GinvJ.p, "Coulomb");
     }
-    // (P|ia) = sum_mu nu C_mu i (P|mu nu) C_nu a, aux chunks of at most aux_chunk_bytes
-    c->Y.alloc((size_t)nJ * nov, &c->budget, "(P|ia)");
-    c->k_active = nK > 0 && c->oK > 0 && c->vK > 0 && c->opt.cx != 0.0;
-    const int hrows = std::max(nocc, std::max(c->oK, c->vK));
-    size_t per = (size_t)nao * nao + (size_t)hrows * nao;
-    int npc = (int)std::max<size_t>(1, c->opt.aux_chunk_bytes / (per * sizeof(double)));
-    npc = std::min(npc, std::max(nJ, nK));
-    npc = std::max(npc, 1);
+    if (c->k_active) {
+        DevBuf<double> G;
+        G.alloc((size_t)nK * nK, &c->budget, "K metric");
+        c->GinvK.alloc((size_t)nK * nK, &c->budget, "K metric");
+        metric(c, c->auxK_h, c->opt.k_alpha, c->opt.k_beta, c->opt.omega, G.p);
+        metric_inverse(c, G.p, nK, c->GinvK.p, "exchange");
+    }
+    // MO transforms
     {
-        DevBuf<double> I, H;
-        I.alloc((size_t)npc * nao * nao, &c->budget, "AO integral chunk");
-        H.alloc((size_t)npc * hrows * nao, &c->budget, "half-transform chunk");
-        for (int p0 = 0; p0 < nJ; p0 += npc) {
-            int np = std::min(npc, nJ - p0);
-            compute_int3c(c, c->auxJ_h, p0, np, I.p, 1.0, 0.0, 0.0);
-            Batch b1;
-            b1.n1 = np;
-            b1.sB1 = (long long)nao * nao;
-            b1.sC1 = (long long)nocc * nao;
-            dgemm(pf, st, "xform_J1", true, false, nocc, nao, nao, 1.0, c->C.p, nmo, I.p, nao, 0.0, H.p, nao,
-                  b1, nullptr, 0);
-            Batch b2;
-            b2.n1 = np;
-            b2.sA1 = (long long)nocc * nao;
-            b2.sC1 = nov;
-            dgemm(pf, st, "xform_J2", false, false, nocc, nvir, nao, 1.0, H.p, nao, c->C.p + nocc, nmo, 0.0,
-                  c->Y.p + (long long)p0 * nov, nvir, b2, nullptr, 0);
-        }
-        // exchange tensors on the window with the K operator (Sec. 3.2, Eqs. RSH, K_mia_RSH)
-        c->Tab.release();
-        c->T2.release();
-        c->GinvK.release();
+        DevBuf<double> Iij;
+        const int oK = c->oK;
+        if (c->k_active) Iij.alloc((size_t)nK * oK * oK, &c->budget, "(ij|P)");
+        transforms_fp64(c, Iij);
         if (c->k_active) {
-            const double ka = c->opt.k_alpha, kb = c->opt.k_beta, om = c->opt.omega;
-            const int oK = c->oK, vK = c->vK, o0 = c->o0;
-            DevBuf<double> G, Iij;
-            G.alloc((size_t)nK * nK, &c->budget, "K metric");
-            c->GinvK.alloc((size_t)nK * nK, &c->budget, "K metric");
-            metric(c, c->auxK_h, ka, kb, om, G.p);
-            metric_inverse(c, G.p, nK, c->GinvK.p, "exchange");
-            Iij.alloc((size_t)nK * oK * oK, &c->budget, "(ij|P)");
-            c->Tab.alloc((size_t)nK * vK * vK, &c->budget, "T_ab");
-            for (int p0 = 0; p0 < nK; p0 += npc) {
-                int np = std::min(npc, nK - p0);
-                compute_int3c(c, c->auxK_h, p0, np, I.p, ka, kb, om);
-                Batch h;
-                h.n1 = np;
-                h.sB1 = (long long)nao * nao;
-                h.sC1 = (long long)oK * nao;
-                dgemm(pf, st, "xform_K1", true, false, oK, nao, nao, 1.0, c->C.p + o0, nmo, I.p, nao, 0.0, H.p,
-                      nao, h, nullptr, 0);
-                Batch g;
-                g.n1 = np;
-                g.sA1 = (long long)oK * nao;
-                g.sC1 = (long long)oK * oK;
-                dgemm(pf, st, "xform_K2", false, false, oK, oK, nao, 1.0, H.p, nao, c->C.p + o0, nmo, 0.0,
-                      Iij.p + (long long)p0 * oK * oK, oK, g, nullptr, 0);
-                h.sC1 = (long long)vK * nao;
-                dgemm(pf, st, "xform_K1", true, false, vK, nao, nao, 1.0, c->C.p + nocc, nmo, I.p, nao, 0.0, H.p,
-                      nao, h, nullptr, 0);
-                g.sA1 = (long long)vK * nao;
-                g.sC1 = (long long)vK * vK;
-                dgemm(pf, st, "xform_K2", false, false, vK, vK, nao, 1.0, H.p, nao, c->C.p + nocc, nmo, 0.0,
-                      c->Tab.p + (long long)p0 * vK * vK, vK, g, nullptr, 0);
-            }
             // T_ij^P = sum_Q (ij|Q) (Q|P)^-1, stored [i][P][j]
             c->T2.alloc((size_t)oK * nK * oK, &c->budget, "T_ij");
             Batch t;
@@ -362,14 +385,13 @@ void build(tr_ctx *c)
             t.sC1 = (long long)nK * oK;
             dgemm(pf, st, "apply_K_metric", false, false, nK, oK, nK, 1.0, c->GinvK.p, nK, Iij.p,
                   (long long)oK * oK, 0.0, c->T2.p, oK, t, nullptr, 0);
-            TR_CUDA(cudaStreamSynchronize(st));
         }
         TR_CUDA(cudaStreamSynchronize(st));
     }
     c->D.alloc(std::max<long long>(nov, 1), &c->budget, "orbital differences");
     TR_LAUNCH(pf, st, "orbital_diff", 0, 0, orbital_diff<<<grid_for(nov), 256, 0, st>>>(c->eps.p, nocc, nvir, c->D.p));
     TR_CUDA(cudaStreamSynchronize(st));
-    if (c->opt.precision == TR_MIXED) build_mixed(c);
+    if (mixed) build_mixed(c);
     c->built = true;
 }
 
@@ -403,6 +425,10 @@ void get_tensor(tr_ctx *c, int which, double *out, int on_device)
     const double *src = nullptr;
     size_t n = 0;
     DevBuf<double> tmp;
+    if (c->opt.precision == TR_MIXED && (which == 0 || which == 2)) {
+        get_tensor_mixed(c, which, out, on_device);
+        return;
+    }
     switch (which) {
         case 0: src = c->Y.p; n = (size_t)c->nJ * c->nov; break;
         case 1:

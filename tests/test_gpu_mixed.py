@@ -76,3 +76,14 @@ def test_mixed_24atom_against_golden(case):
     err = np.abs(om - ref)
     print("per-state |dOmega| (Ha), mixed 24-atom %s:" % case, err)
     assert info.converged and np.all(err < 1e-5), err
+
+
+def test_mixed_tensors_against_oracle(mid):
+    """MO tensors (built in FP64, kept in FP32) against the FP64 oracle."""
+    mol, f = mid
+    c = _ctx(mol, **RSH)
+    for which, ref in ((0, f.Y), (1, f.Tij), (2, f.Tab)):
+        got = c.tensor(which)
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        print("tensor", which, "relative error", err)
+        assert err < 1e-6

@@ -199,6 +199,10 @@ def run_native(args):
                "h2d_bytes_per_step": int(mol.C.nbytes + mol.eps.nbytes),
                "d2h_bytes_per_step": int(8 * OPTS["nstates"] * (1 + d.nocc * d.nvir) + 8 * OPTS["nstates"])}
 
+    # reduced-precision form on the same workload (NEXT: FP32 tensors, 3xTF32 K on tcgen05)
+    mixed = None
+    if not args.no_mixed:
+        mixed = run_mixed(args, tdarisp, mol, C_dev, eps_dev, stream, barrier)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -241,9 +245,12 @@ def run_native(args):
                         "note": "Davidson matvec time only (events around each block product)"},
         "davidson": {"niter": [i.niter for i in infos], "nmatvec": [i.nmatvec for i in infos],
                      "restarts": [i.nrestart for i in infos], "converged": [i.converged for i in infos]},
-        "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+        "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "mixed_form": mixed,
         "gpu_launches": launches, "clocks": clk,
     }
+    if mixed:
+        mixed["speedup_vs_fp64_value"] = mixed["value"] / line["value"]
+        mixed["speedup_vs_fp64_s_to_states"] = line["s_to_states"] / mixed["s_to_states"]
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -258,6 +265,66 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes / algorithmic bytes of K stage 1, from one ncu capture of that kernel
 # (737 MB measured for 708 MB algorithmic on the 100-atom profiling case).
 K_STAGE1_TRAFFIC_RATIO = 737.0 / 708.0
+
+# nominal dense TF32 / BF16 tensor rates of GB300 (1.1 and 2.25 PFLOP/s)
+TF32_OVER_BF16 = 1.1 / 2.25
+
+
+def run_mixed(args, tdarisp, mol, C_dev, eps_dev, stream, barrier):
+    """Same workload in the reduced-precision form; compared with the FP64 form."""
+    import torch
+    ref = tdarisp.Context(stream=stream.cuda_stream, **OPTS)
+    ref.set_molecule(mol.Z, mol.xyz, mol.aux_exp, mol.shells)
+    ref.set_orbitals(C_dev, eps_dev, mol.nocc)
+    ref.build()
+    om64 = ref.solve(want_x=False)[0]
+    ref.close()
+    ctx = tdarisp.Context(stream=stream.cuda_stream, precision=1, **OPTS)
+    ctx.set_molecule(mol.Z, mol.xyz, mol.aux_exp, mol.shells)
+    ctx.set_orbitals(C_dev, eps_dev, mol.nocc)
+
+    def step():
+        ctx.build()
+        return ctx.solve(want_x=True, device=True)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    barrier()
+    ctx.profile(True)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    nmv, infos, om = 0, [], None
+    for _ in range(args.steps):
+        om, X, rs, info = step()
+        nmv += info.nmatvec
+        infos.append(info)
+    t1.record(stream)
+    barrier()
+    ms = t0.elapsed_time(t1)
+    prof = ctx.profile_get()
+    ctx.close()
+    om = om.cpu().numpy()
+    peaks = read_peaks()
+    bf16 = peaks.get("bf16_tflops")
+    tf32_peak = bf16 * TF32_OVER_BF16 if bf16 else 1900.0 * TF32_OVER_BF16
+    name, p = max(((k, v) for k, v in prof.items() if k.endswith("_tc")), key=lambda kv: kv[1]["ms"])
+    useful = p["flops"] / (p["ms"] * 1e-3) / 1e12
+    mv_ms = sum(i.t_matvec_ms for i in infos)
+    return {
+        "value": nmv / (ms * 1e-3), "unit": "matvecs/s", "s_to_states": ms / args.steps * 1e-3,
+        "speedup_vs_fp64_value": None, "matvec_only": nmv / (mv_ms * 1e-3) if mv_ms else None,
+        "dtype": "f32/tf32x3 (tensor cores) + f64 (integrals, transforms, metrics, Davidson)",
+        "max_abs_dOmega_vs_fp64_form_Ha": float(np.abs(om - om64).max()),
+        "per_state_dOmega_vs_fp64_form_Ha": [float(x) for x in np.abs(om - om64)],
+        "davidson": {"niter": [i.niter for i in infos], "nmatvec": [i.nmatvec for i in infos]},
+        "roofline": {"kernel": name, "bound": "tensor", "achieved": 3.0 * useful, "useful_tflops": useful,
+                     "peak": tf32_peak, "unit": "TFLOP/s", "frac": 3.0 * useful / tf32_peak,
+                     "peak_source": "TF32 dense = measured bf16 burst x nominal TF32/BF16 ratio (1.1/2.25)",
+                     "note": "3 tensor products (hi*hi + hi*lo + lo*hi) per useful flop"},
+        "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]}
+                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
+    }
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -345,6 +412,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the reduced-precision form")
     ap.add_argument("--case", default="full", choices=["full", "small"],
                     help="small: 100-atom molecule of the same shape, for profiler captures")
     args = ap.parse_args()

@@ -216,6 +216,21 @@ int tr_matvec_noalloc(tr_ctx *ctx, int m, const double *X, double *AX);
 int tr_solve(tr_ctx *ctx, double *omega, double *X, double *resid, int on_device,
              tr_solve_info *info);
 
+/* Davidson solves of n built contexts (n molecules, each with its own options)
+   advanced in lockstep: every molecule works on a stream of its own, and the
+   matrix-vector products of one Davidson step of all molecules are one CUDA
+   graph launch (recorded once, replayed every step, recorded again when the set
+   of unconverged molecules changes).  autotune_tiles != 0: before the solve, each
+   TR_MIXED context times its tensor-core K stages with 64- and 128-wide output
+   tiles and keeps the faster.  Outputs per molecule as tr_solve (omega[i], X[i]
+   may be NULL, resid[i] may be NULL; infos may be NULL, else n entries; the
+   graph time is reported as every molecule's t_matvec_ms).  Returns TR_OK, or
+   TR_ENOCONV if any molecule did not converge, or the first error; the error
+   text is copied to every context.  The contexts must be distinct and on the
+   current device; their streams are synchronised at entry and exit. */
+int tr_solve_batch(tr_ctx **ctxs, int n, double **omega, double **X, double **resid, int on_device,
+                   tr_solve_info *infos, int autotune_tiles);
+
 /* Kernel timing: enable (1) / disable (0) and reset the counters. */
 int tr_profile(tr_ctx *ctx, int enable);
 /* Copy up to max entries; returns the number of entries (>= 0) or an error. */

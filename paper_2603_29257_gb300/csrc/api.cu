@@ -223,6 +223,20 @@ int tr_solve(tr_ctx *ctx, double *omega, double *X, double *resid, int on_device
     return guarded(ctx, [&]() { return tr::solve(ctx, omega, X, resid, on_device, info); });
 }
 
+int tr_solve_batch(tr_ctx **ctxs, int n, double **omega, double **X, double **resid, int on_device,
+                   tr_solve_info *infos, int autotune_tiles)
+{
+    if (!ctxs || n <= 0 || !ctxs[0]) return TR_EINVAL;
+    tr_ctx *c0 = ctxs[0];
+    int rc = guarded(c0, [&]() {
+        for (int i = 0; i < n; ++i) TR_REQUIRE(ctxs[i], TR_EINVAL, "solve_batch: null context");
+        return tr::solve_batch(ctxs, n, omega, X, resid, on_device, infos, autotune_tiles);
+    });
+    for (int i = 1; i < n; ++i)
+        if (ctxs[i]) ctxs[i]->err = c0->err;
+    return rc;
+}
+
 int tr_profile(tr_ctx *ctx, int enable)
 {
     return guarded(ctx, [&]() {

@@ -56,6 +56,7 @@ struct tr_ctx {
     tr::DevBuf<float> Y32, Tab_h, Tab_l, T2_h, T2_l, Xw_h, Xw_l, Mt_h, Mt_l, X32, Z32;
     tr::TcMat tm_tab, tm_t2, tm_xw, tm_mt;
     int oKp = 0, vKp = 0, mixed_mb = 0, mixed_npk = 0;
+    int tc_bn = 128;  // tensor-core output tile width of the K stages (64 or 128)
 
     // workspaces
     tr::DevBuf<double> ws_split, ws_Z, ws_Z2, ws_Xw, ws_M;
@@ -106,5 +107,7 @@ void build_mixed(tr_ctx *c);
 void reserve_mixed(tr_ctx *c, int mb);
 void matvec_mixed(tr_ctx *c, int m, const double *X, double *AX);
 int solve(tr_ctx *c, double *omega, double *X, double *resid, int on_device, tr_solve_info *info);
+int solve_batch(tr_ctx **ctxs, int nb, double **omega, double **X, double **resid, int on_device,
+                tr_solve_info *infos, int autotune_tiles);
 
 }  // namespace tr

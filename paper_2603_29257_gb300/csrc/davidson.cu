@@ -11,6 +11,7 @@
 // Convergence: every one of the nstates residual 2-norms below tol.
 #include <algorithm>
 #include <cmath>
+#include <memory>
 #include <numeric>
 
 #include "ctx.cuh"
@@ -240,92 +241,118 @@ struct PinnedBuf {
 
 }  // namespace
 
-int solve(tr_ctx *c, double *omega, double *Xout, double *resid, int on_device, tr_solve_info *info)
-{
-    TR_REQUIRE(c->built, TR_EINVAL, "solve: call tr_build first");
-    TR_REQUIRE(omega, TR_EINVAL, "solve: omega must not be NULL");
-    TR_REQUIRE(c->opt.nstates >= 1, TR_EINVAL, "solve: nstates must be >= 1");
-    TR_REQUIRE(c->opt.nstates <= 64, TR_EINVAL, "solve: nstates must be <= 64");
-    const long long nov = c->nov;
-    cudaStream_t st = c->st;
-    Prof &pf = c->prof;
-    const int n = (int)std::min<long long>(c->opt.nstates, nov);
-    int b0 = c->opt.block > 0 ? c->opt.block : 2 * n;
-    b0 = (int)std::min<long long>(std::max(b0, n), nov);
-    int maxsp = c->opt.max_space > 0 ? c->opt.max_space : 20 * n;
-    maxsp = std::max(maxsp, b0 + n);
-    maxsp = (int)std::min<long long>(maxsp, std::max<long long>(nov, b0));
-    const int max_iter = c->opt.max_iter > 0 ? c->opt.max_iter : 200;
-    const double tol = c->opt.tol;
-    const int pmax = std::max(b0, n);
-    const size_t rowb = (size_t)nov * sizeof(double);
-
-    // fixed buffers
-    reserve_matvec(c, pmax);
-    c->Tn.alloc((size_t)pmax * nov, &c->budget, "new vectors");
-    c->Wn.alloc((size_t)pmax * nov, &c->budget, "new products");
-    c->T.alloc((size_t)pmax * nov, &c->budget, "new vectors");
-    c->Tt.alloc((size_t)pmax * nov, &c->budget, "new vectors");
-    c->Xr.alloc((size_t)n * nov, &c->budget, "Ritz vectors");
-    c->R.alloc((size_t)n * nov, &c->budget, "residuals");
-    const int nblk = 256;
-    c->part.alloc((size_t)nblk * pmax, &c->budget, "norms");
-    c->rn.alloc(pmax, &c->budget, "norms");
-    c->idx_dev.alloc(pmax + 2, &c->budget, "indices");
-    c->Ss.alloc((size_t)pmax * pmax, &c->budget, "gram");
-    c->Gc.alloc((size_t)pmax * pmax, &c->budget, "gram");
-
-    // how many V/W rows fit in HBM; the rest spill to pinned host memory
-    c->V.release();
-    c->W.release();
-    const int cs = std::max(8, pmax);  // staging rows per chunk
-    long long avail = (long long)c->budget.limit - (long long)c->budget.used;
-    const long long small = 5LL * maxsp * maxsp * 8 + 2LL * maxsp * pmax * 8 + (64LL << 20);
-    int kd = (int)std::max<long long>(0, (avail - small) / (long long)(2 * rowb));
-    if (kd < maxsp) kd = (int)std::max<long long>(0, (avail - small - 2LL * cs * rowb) / (long long)(2 * rowb));
-    if (c->opt.dav_dev_rows > 0) kd = std::min(kd, c->opt.dav_dev_rows);
-    kd = std::min(kd, maxsp);
-    if (kd < maxsp && c->opt.host_budget > 0) {
-        const long long hrows = (long long)(c->opt.host_budget / (2 * rowb));
-        maxsp = (int)std::min<long long>(maxsp, kd + hrows);
-    }
-    TR_REQUIRE(maxsp >= b0 + 1 && maxsp >= n + 1, TR_ENOMEM,
-               "solve: device and host budgets leave no room for the Davidson subspace");
-    c->V.alloc((size_t)kd * nov, &c->budget, "Davidson V");
-    c->W.alloc((size_t)kd * nov, &c->budget, "Davidson W");
-    c->Hs.alloc((size_t)maxsp * maxsp, &c->budget, "subspace");
-    c->Hw.alloc((size_t)maxsp * maxsp, &c->budget, "subspace");
-    c->Yev.alloc((size_t)maxsp * maxsp, &c->budget, "subspace");
-    c->Yw.alloc((size_t)maxsp * maxsp, &c->budget, "subspace");
-    c->theta.alloc(maxsp, &c->budget, "subspace");
-    c->Cs.alloc((size_t)2 * maxsp * pmax, &c->budget, "projections");
+// One Davidson solve as a resumable state: the driver alternates
+//   eig_async (subspace eigenpairs, Ritz vectors, residual norms; asynchronous)
+//   check     (after the stream synchronised: convergence / iteration limit)
+//   prepare   (restart or new directions into Tn; may synchronise for counts)
+//   [A Tn -> Wn for pend_p rows: one matvec, or one graph for many molecules]
+//   absorb    (subspace matrix update, rows stored)
+// so that many molecules can be advanced in lockstep.
+struct Dav {
+    tr_ctx *c;
+    cudaStream_t st;
+    long long nov;
+    size_t rowb;
+    int n, b0, maxsp, max_iter, pmax, cs, kd;
+    double tol;
+    static constexpr int nblk = 256;
     PinnedBuf Vh, Wh;
     RowStore SV, SW;
-    SV.nov = SW.nov = nov;
-    SV.cap = SW.cap = maxsp;
-    SV.kd = SW.kd = kd;
-    SV.dev = c->V.p;
-    SW.dev = c->W.p;
-    if (kd < maxsp) {
-        Vh.alloc((size_t)(maxsp - kd) * nov, "Davidson V");
-        Wh.alloc((size_t)(maxsp - kd) * nov, "Davidson W");
-        SV.host = Vh.p;
-        SW.host = Wh.p;
-        c->stage.reserve((size_t)2 * cs * nov, &c->budget, "spill staging");
-        if (!c->cst) TR_CUDA(cudaStreamCreateWithFlags(&c->cst, cudaStreamNonBlocking));
-        for (auto &e : c->sev)
-            if (!e) TR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    }
     long long moved = 0;
-
-    double *ws = c->ws_split.p;
-    const size_t wsn = c->ws_split.n;
+    double *ws;
+    size_t wsn;
     Events ev;
     double t_mv = 0, t_or = 0, t_eig = 0, t_oth = 0;
+    int k = 0, nmv = 0, nrestart = 0, it = 0, converged = 0;
+    bool done = false, eig_timed = false, or_timed = false;
+    std::vector<double> rn_h, th_h;
+    std::vector<int> unconv;
+    int jflag[2] = {0, 0};
+    int pend_p = 0, pend_k0 = 0;
+
+    explicit Dav(tr_ctx *ctx) : c(ctx), st(ctx->st)
+    {
+        TR_REQUIRE(c->built, TR_EINVAL, "solve: call tr_build first");
+        TR_REQUIRE(c->opt.nstates >= 1, TR_EINVAL, "solve: nstates must be >= 1");
+        TR_REQUIRE(c->opt.nstates <= 64, TR_EINVAL, "solve: nstates must be <= 64");
+        nov = c->nov;
+        rowb = (size_t)nov * sizeof(double);
+        n = (int)std::min<long long>(c->opt.nstates, nov);
+        b0 = c->opt.block > 0 ? c->opt.block : 2 * n;
+        b0 = (int)std::min<long long>(std::max(b0, n), nov);
+        maxsp = c->opt.max_space > 0 ? c->opt.max_space : 20 * n;
+        maxsp = std::max(maxsp, b0 + n);
+        maxsp = (int)std::min<long long>(maxsp, std::max<long long>(nov, b0));
+        max_iter = c->opt.max_iter > 0 ? c->opt.max_iter : 200;
+        tol = c->opt.tol;
+        pmax = std::max(b0, n);
+        rn_h.assign(n, 0.0);
+        th_h.assign(n, 0.0);
+
+        reserve_matvec(c, pmax);
+        c->Tn.alloc((size_t)pmax * nov, &c->budget, "new vectors");
+        c->Wn.alloc((size_t)pmax * nov, &c->budget, "new products");
+        c->T.alloc((size_t)pmax * nov, &c->budget, "new vectors");
+        c->Tt.alloc((size_t)pmax * nov, &c->budget, "new vectors");
+        c->Xr.alloc((size_t)n * nov, &c->budget, "Ritz vectors");
+        c->R.alloc((size_t)n * nov, &c->budget, "residuals");
+        c->part.alloc((size_t)nblk * pmax, &c->budget, "norms");
+        c->rn.alloc(pmax, &c->budget, "norms");
+        c->idx_dev.alloc(pmax + 2, &c->budget, "indices");
+        c->Ss.alloc((size_t)pmax * pmax, &c->budget, "gram");
+        c->Gc.alloc((size_t)pmax * pmax, &c->budget, "gram");
+        // rows a product is computed for beyond the pending ones must hold finite values
+        TR_CUDA(cudaMemsetAsync(c->Tn.p, 0, sizeof(double) * c->Tn.n, st));
+
+        // how many V/W rows fit in HBM; the rest spill to pinned host memory
+        c->V.release();
+        c->W.release();
+        cs = std::max(8, pmax);  // staging rows per chunk
+        const long long avail = (long long)c->budget.limit - (long long)c->budget.used;
+        const long long small = 5LL * maxsp * maxsp * 8 + 2LL * maxsp * pmax * 8 + (64LL << 20);
+        kd = (int)std::max<long long>(0, (avail - small) / (long long)(2 * rowb));
+        if (kd < maxsp) kd = (int)std::max<long long>(0, (avail - small - 2LL * cs * rowb) / (long long)(2 * rowb));
+        if (c->opt.dav_dev_rows > 0) kd = std::min(kd, c->opt.dav_dev_rows);
+        kd = std::min(kd, maxsp);
+        if (kd < maxsp && c->opt.host_budget > 0) {
+            const long long hrows = (long long)(c->opt.host_budget / (2 * rowb));
+            maxsp = (int)std::min<long long>(maxsp, kd + hrows);
+        }
+        TR_REQUIRE(maxsp >= b0 + 1 && maxsp >= n + 1, TR_ENOMEM,
+                   "solve: device and host budgets leave no room for the Davidson subspace");
+        c->V.alloc((size_t)kd * nov, &c->budget, "Davidson V");
+        c->W.alloc((size_t)kd * nov, &c->budget, "Davidson W");
+        c->Hs.alloc((size_t)maxsp * maxsp, &c->budget, "subspace");
+        c->Hw.alloc((size_t)maxsp * maxsp, &c->budget, "subspace");
+        c->Yev.alloc((size_t)maxsp * maxsp, &c->budget, "subspace");
+        c->Yw.alloc((size_t)maxsp * maxsp, &c->budget, "subspace");
+        c->theta.alloc(maxsp, &c->budget, "subspace");
+        c->Cs.alloc((size_t)2 * maxsp * pmax, &c->budget, "projections");
+        SV.nov = SW.nov = nov;
+        SV.cap = SW.cap = maxsp;
+        SV.kd = SW.kd = kd;
+        SV.dev = c->V.p;
+        SW.dev = c->W.p;
+        if (kd < maxsp) {
+            Vh.alloc((size_t)(maxsp - kd) * nov, "Davidson V");
+            Wh.alloc((size_t)(maxsp - kd) * nov, "Davidson W");
+            SV.host = Vh.p;
+            SW.host = Wh.p;
+            c->stage.reserve((size_t)2 * cs * nov, &c->budget, "spill staging");
+            if (!c->cst) TR_CUDA(cudaStreamCreateWithFlags(&c->cst, cudaStreamNonBlocking));
+            for (auto &e : c->sev)
+                if (!e) TR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        }
+        ws = c->ws_split.p;
+        wsn = c->ws_split.n;
+        TR_CUDA(cudaMemsetAsync(c->flag.p, 0, 2 * sizeof(int), st));
+    }
 
     // f(device pointer, first row, rows) for rows [r0, r1) of S; host rows are
     // staged through two device slots on the copy stream
-    auto for_rows = [&](RowStore &S, int r0, int r1, auto &&f) {
+    template <typename F>
+    void for_rows(RowStore &S, int r0, int r1, F &&f)
+    {
         int a = r0, b = std::min(r1, S.kd);
         if (a < b) f(S.dev + (long long)a * nov, a, b - a);
         a = std::max(r0, S.kd);
@@ -337,16 +364,16 @@ int solve(tr_ctx *c, double *omega, double *Xout, double *resid, int on_device, 
             const int nr = std::min(cs, r1 - s0), slot = i & 1;
             double *buf = c->stage.p + (size_t)slot * cs * nov;
             TR_CUDA(cudaStreamWaitEvent(c->cst, c->sev[2 + slot], 0));
-            TR_CUDA(cudaMemcpyAsync(buf, S.host + (size_t)(s0 - S.kd) * nov, nr * rowb,
-                                    cudaMemcpyHostToDevice, c->cst));
+            TR_CUDA(cudaMemcpyAsync(buf, S.host + (size_t)(s0 - S.kd) * nov, nr * rowb, cudaMemcpyHostToDevice, c->cst));
             TR_CUDA(cudaEventRecord(c->sev[slot], c->cst));
             TR_CUDA(cudaStreamWaitEvent(st, c->sev[slot], 0));
             f(buf, s0, nr);
             TR_CUDA(cudaEventRecord(c->sev[2 + slot], st));
             moved += (long long)nr * rowb;
         }
-    };
-    auto store_rows = [&](RowStore &S, int r0, int nr, const double *src) {
+    }
+    void store_rows(RowStore &S, int r0, int nr, const double *src)
+    {
         int a = r0, b = std::min(r0 + nr, S.kd);
         if (a < b)
             TR_CUDA(cudaMemcpyAsync(S.dev + (long long)a * nov, src, (b - a) * rowb, cudaMemcpyDeviceToDevice, st));
@@ -356,75 +383,88 @@ int solve(tr_ctx *c, double *omega, double *Xout, double *resid, int on_device, 
                                     (r0 + nr - a) * rowb, cudaMemcpyDeviceToHost, st));
             moved += (long long)(r0 + nr - a) * rowb;
         }
-    };
-    auto norms_of = [&](const double *A, int p, double *out) {
-        TR_LAUNCH(pf, st, "row_norms", 0, 8.0 * p * nov,
+    }
+    void norms_of(const double *A, int p, double *out)
+    {
+        TR_LAUNCH(c->prof, st, "row_norms", 0, 8.0 * p * nov,
                   row_sumsq<<<dim3(nblk, p), 256, 0, st>>>(A, p, nov, c->part.p));
-        TR_LAUNCH(pf, st, "row_norms", 0, 0, finish_norms<<<cdiv(p, 64), 64, 0, st>>>(c->part.p, nblk, p, out));
-    };
+        TR_LAUNCH(c->prof, st, "row_norms", 0, 0, finish_norms<<<cdiv(p, 64), 64, 0, st>>>(c->part.p, nblk, p, out));
+    }
     // rows/cols k0..k0+p of H for the new vectors Vn (products Wn)
-    auto h_update = [&](int k0, int p, const double *Vn, const double *Wn) {
-        const int k = k0 + p;
+    void h_update(int k0, int p, const double *Vn, const double *Wn)
+    {
+        Prof &pf = c->prof;
+        const int kk = k0 + p;
         double *A1 = c->Cs.p, *A2 = c->Cs.p + (size_t)maxsp * pmax;
         for_rows(SW, 0, k0, [&](const double *rows, int r0, int nr) {
-            dgemm(pf, st, "subspace_H", false, true, p, nr, (int)nov, 1.0, Vn, nov, rows, nov, 0.0, A1 + r0, k,
+            dgemm(pf, st, "subspace_H", false, true, p, nr, (int)nov, 1.0, Vn, nov, rows, nov, 0.0, A1 + r0, kk,
                   Batch(), ws, wsn);
         });
-        dgemm(pf, st, "subspace_H", false, true, p, p, (int)nov, 1.0, Vn, nov, Wn, nov, 0.0, A1 + k0, k, Batch(), ws, wsn);
+        dgemm(pf, st, "subspace_H", false, true, p, p, (int)nov, 1.0, Vn, nov, Wn, nov, 0.0, A1 + k0, kk, Batch(), ws, wsn);
         for_rows(SV, 0, k0, [&](const double *rows, int r0, int nr) {
-            dgemm(pf, st, "subspace_H", false, true, p, nr, (int)nov, 1.0, Wn, nov, rows, nov, 0.0, A2 + r0, k,
+            dgemm(pf, st, "subspace_H", false, true, p, nr, (int)nov, 1.0, Wn, nov, rows, nov, 0.0, A2 + r0, kk,
                   Batch(), ws, wsn);
         });
-        dgemm(pf, st, "subspace_H", false, true, p, p, (int)nov, 1.0, Wn, nov, Vn, nov, 0.0, A2 + k0, k, Batch(), ws, wsn);
+        dgemm(pf, st, "subspace_H", false, true, p, p, (int)nov, 1.0, Wn, nov, Vn, nov, 0.0, A2 + k0, kk, Batch(), ws, wsn);
         TR_LAUNCH(pf, st, "subspace_insert", 0, 0,
-                  h_insert<<<dim3(cdiv(k, 128), p), 128, 0, st>>>(c->Hs.p, maxsp, A1, A2, p, k, k0));
-    };
-    // orthonormalise rows src[0:p] into dst; returns the count kept
-    auto cholqr = [&](double *src, int p, double *dst, double drop2) -> int {
+                  h_insert<<<dim3(cdiv(kk, 128), p), 128, 0, st>>>(c->Hs.p, maxsp, A1, A2, p, kk, k0));
+    }
+    // orthonormalise rows src[0:p] into dst; returns the count kept (synchronises st)
+    int cholqr(double *src, int p, double *dst, double drop2)
+    {
+        Prof &pf = c->prof;
         dgemm(pf, st, "gram", false, true, p, p, (int)nov, 1.0, src, nov, src, nov, 0.0, c->Ss.p, p, Batch(), ws, wsn);
         TR_LAUNCH(pf, st, "cholqr_coef", 0, 0, cholqr_coef<<<1, 1, 0, st>>>(c->Ss.p, p, drop2, c->Gc.p, c->idx_dev.p + pmax));
         int keep = 0;
         TR_CUDA(cudaMemcpyAsync(&keep, c->idx_dev.p + pmax, sizeof(int), cudaMemcpyDeviceToHost, st));
         TR_CUDA(cudaStreamSynchronize(st));
         if (keep > 0)
-            dgemm(pf, st, "orth_apply", false, false, keep, (int)nov, p, 1.0, c->Gc.p, p, src, nov, 0.0, dst,
-                  nov, Batch(), nullptr, 0);
+            dgemm(pf, st, "orth_apply", false, false, keep, (int)nov, p, 1.0, c->Gc.p, p, src, nov, 0.0, dst, nov,
+                  Batch(), nullptr, 0);
         return keep;
-    };
-    auto orthonormal_block = [&](double *src, int p, double *dst, double *tmp) -> int {
+    }
+    int orthonormal_block(double *src, int p, double *dst, double *tmp)
+    {
         int k1 = cholqr(src, p, tmp, DROP_NORM * DROP_NORM);
         if (k1 == 0) return 0;
         return cholqr(tmp, k1, dst, 0.0);
-    };
-    auto apply_A = [&](const double *Vn, double *Wn, int p) {
-        TR_CUDA(cudaEventRecord(ev.e[4], st));
-        matvec(c, p, Vn, Wn);
-        TR_CUDA(cudaEventRecord(ev.e[5], st));
-    };
+    }
 
-    TR_CUDA(cudaMemsetAsync(c->flag.p, 0, 2 * sizeof(int), st));
     // initial guess: unit vectors on the b0 smallest e_a - e_i (ties: lower index)
-    std::vector<double> Dh(nov);
-    TR_CUDA(cudaMemcpyAsync(Dh.data(), c->D.p, sizeof(double) * nov, cudaMemcpyDeviceToHost, st));
-    TR_CUDA(cudaStreamSynchronize(st));
-    std::vector<int> order(nov);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return Dh[a] < Dh[b]; });
-    TR_CUDA(cudaMemcpyAsync(c->idx_dev.p, order.data(), sizeof(int) * b0, cudaMemcpyHostToDevice, st));
-    TR_CUDA(cudaMemsetAsync(c->Tn.p, 0, sizeof(double) * (size_t)b0 * nov, st));
-    TR_LAUNCH(pf, st, "set_unit", 0, 0, set_unit_rows<<<cdiv(b0, 64), 64, 0, st>>>(c->Tn.p, c->idx_dev.p, b0, nov));
-    int k = b0;
-    apply_A(c->Tn.p, c->Wn.p, k);
-    h_update(0, k, c->Tn.p, c->Wn.p);
-    store_rows(SV, 0, k, c->Tn.p);
-    store_rows(SW, 0, k, c->Wn.p);
-    TR_CUDA(cudaStreamSynchronize(st));
-    t_mv += elapsed(ev.e[4], ev.e[5]);
-
-    int nmv = b0, nrestart = 0, it = 0, converged = 0;
-    std::vector<double> rn_h(n), th_h(n);
-    std::vector<int> unconv;
-    for (it = 1; it <= max_iter; ++it) {
+    void guess()
+    {
+        std::vector<double> Dh(nov);
+        TR_CUDA(cudaMemcpyAsync(Dh.data(), c->D.p, sizeof(double) * nov, cudaMemcpyDeviceToHost, st));
+        TR_CUDA(cudaStreamSynchronize(st));
+        std::vector<int> order(nov);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return Dh[a] < Dh[b]; });
+        TR_CUDA(cudaMemcpyAsync(c->idx_dev.p, order.data(), sizeof(int) * b0, cudaMemcpyHostToDevice, st));
+        TR_CUDA(cudaMemsetAsync(c->Tn.p, 0, sizeof(double) * (size_t)b0 * nov, st));
+        TR_LAUNCH(c->prof, st, "set_unit", 0, 0, set_unit_rows<<<cdiv(b0, 64), 64, 0, st>>>(c->Tn.p, c->idx_dev.p, b0, nov));
+        pend_k0 = 0;
+        pend_p = b0;
+    }
+    // products of the pending rows by this context's own matvec
+    void apply_pending()
+    {
+        TR_CUDA(cudaEventRecord(ev.e[4], st));
+        matvec(c, pend_p, c->Tn.p, c->Wn.p);
+        TR_CUDA(cudaEventRecord(ev.e[5], st));
+    }
+    void absorb()
+    {
+        h_update(pend_k0, pend_p, c->Tn.p, c->Wn.p);
+        store_rows(SV, pend_k0, pend_p, c->Tn.p);
+        store_rows(SW, pend_k0, pend_p, c->Wn.p);
+        k = pend_k0 + pend_p;
+        nmv += pend_p;
+        pend_p = 0;
+    }
+    void eig_async()
+    {
+        Prof &pf = c->prof;
+        ++it;
         TR_CUDA(cudaEventRecord(ev.e[0], st));
         TR_LAUNCH(pf, st, "copy_sub", 0, 0, copy_sub<<<dim3(cdiv(k, 128), k), 128, 0, st>>>(c->Hs.p, maxsp, c->Hw.p, k));
         TR_CUDA(cudaMemsetAsync(c->flag.p, 0, sizeof(int), st));
@@ -444,12 +484,18 @@ int solve(tr_ctx *c, double *omega, double *Xout, double *resid, int on_device, 
         TR_LAUNCH(pf, st, "residual", 0, 0, finish_norms<<<cdiv(n, 64), 64, 0, st>>>(c->part.p, nblk, n, c->rn.p));
         TR_CUDA(cudaMemcpyAsync(rn_h.data(), c->rn.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
         TR_CUDA(cudaMemcpyAsync(th_h.data(), c->theta.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
-        int jflag[2] = {0, 0};
         TR_CUDA(cudaMemcpyAsync(jflag, c->flag.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         TR_CUDA(cudaEventRecord(ev.e[2], st));
-        TR_CUDA(cudaStreamSynchronize(st));
-        t_eig += elapsed(ev.e[0], ev.e[1]);
-        t_oth += elapsed(ev.e[1], ev.e[2]);
+        eig_timed = true;
+    }
+    // after st synchronised
+    void check()
+    {
+        if (eig_timed) {
+            t_eig += elapsed(ev.e[0], ev.e[1]);
+            t_oth += elapsed(ev.e[1], ev.e[2]);
+            eig_timed = false;
+        }
         TR_REQUIRE(!jflag[0], TR_ECUDA, "solve: subspace eigensolver did not converge");
         TR_REQUIRE(!jflag[1], TR_ECUDA, "solve: a tensor-core pipeline wait timed out");
         unconv.clear();
@@ -457,9 +503,14 @@ int solve(tr_ctx *c, double *omega, double *Xout, double *resid, int on_device, 
             if (!(rn_h[r] < tol)) unconv.push_back(r);
         if (unconv.empty()) {
             converged = 1;
-            break;
+            done = true;
+        } else if (it >= max_iter) {
+            done = true;
         }
-        if (it == max_iter) break;
+    }
+    void prepare()
+    {
+        Prof &pf = c->prof;
         const int p = (int)unconv.size();
         if (k + p > maxsp) {
             // restart from the Ritz vectors; A V is recomputed for them (Sec. 3.3)
@@ -467,17 +518,11 @@ int solve(tr_ctx *c, double *omega, double *Xout, double *resid, int on_device, 
             int kk = orthonormal_block(c->Xr.p, n, c->Tn.p, c->Tt.p);
             TR_CUDA(cudaEventRecord(ev.e[1], st));
             TR_REQUIRE(kk > 0, TR_ECUDA, "solve: restart produced an empty subspace");
-            apply_A(c->Tn.p, c->Wn.p, kk);
-            nmv += kk;
-            h_update(0, kk, c->Tn.p, c->Wn.p);
-            store_rows(SV, 0, kk, c->Tn.p);
-            store_rows(SW, 0, kk, c->Wn.p);
-            TR_CUDA(cudaStreamSynchronize(st));
             t_or += elapsed(ev.e[0], ev.e[1]);
-            t_mv += elapsed(ev.e[4], ev.e[5]);
-            k = kk;
+            pend_k0 = 0;
+            pend_p = kk;
             nrestart += 1;
-            continue;
+            return;
         }
         TR_CUDA(cudaEventRecord(ev.e[0], st));
         TR_CUDA(cudaMemcpyAsync(c->idx_dev.p, unconv.data(), sizeof(int) * p, cudaMemcpyHostToDevice, st));
@@ -494,54 +539,304 @@ int solve(tr_ctx *c, double *omega, double *Xout, double *resid, int on_device, 
                       c->Cs.p + (long long)r0 * p, p, Batch(), ws, wsn);
             });
             for_rows(SV, 0, k, [&](const double *rows, int r0, int nr) {
-                dgemm(pf, st, "orth_update", true, false, p, (int)nov, nr, -1.0, c->Cs.p + (long long)r0 * p, p,
-                      rows, nov, 1.0, c->T.p, nov, Batch(), nullptr, 0);
+                dgemm(pf, st, "orth_update", true, false, p, (int)nov, nr, -1.0, c->Cs.p + (long long)r0 * p, p, rows,
+                      nov, 1.0, c->T.p, nov, Batch(), nullptr, 0);
             });
         }
         int pk = orthonormal_block(c->T.p, p, c->Tn.p, c->Tt.p);
         TR_CUDA(cudaEventRecord(ev.e[1], st));
-        if (pk == 0) break;  // no new directions: stagnation
-        apply_A(c->Tn.p, c->Wn.p, pk);
-        nmv += pk;
-        h_update(k, pk, c->Tn.p, c->Wn.p);
-        store_rows(SV, k, pk, c->Tn.p);
-        store_rows(SW, k, pk, c->Wn.p);
-        TR_CUDA(cudaStreamSynchronize(st));
         t_or += elapsed(ev.e[0], ev.e[1]);
-        t_mv += elapsed(ev.e[4], ev.e[5]);
-        k += pk;
+        if (pk == 0) {
+            done = true;  // no new directions: stagnation
+            return;
+        }
+        pend_k0 = k;
+        pend_p = pk;
     }
-    if (it > max_iter) it = max_iter;
-
     // outputs: omega, unit-norm sign-fixed X, residual norms
-    norms_of(c->Xr.p, n, c->rn.p);
-    TR_LAUNCH(pf, st, "normalise", 0, 16.0 * n * nov, row_scale_inv<<<dim3(nblk, n), 256, 0, st>>>(c->Xr.p, n, nov, c->rn.p));
-    TR_LAUNCH(pf, st, "sign_fix", 0, 0, sign_fix<<<n, 1024, 0, st>>>(c->Xr.p, nov));
-    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    TR_CUDA(cudaMemcpyAsync(omega, c->theta.p, sizeof(double) * n, kind, st));
-    if (Xout) TR_CUDA(cudaMemcpyAsync(Xout, c->Xr.p, sizeof(double) * (size_t)n * nov, kind, st));
-    if (resid) {
-        if (on_device)
-            TR_CUDA(cudaMemcpyAsync(resid, rn_h.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
-        else
-            std::copy(rn_h.begin(), rn_h.end(), resid);
+    int output(double *omega, double *Xout, double *resid, int on_device, tr_solve_info *info)
+    {
+        Prof &pf = c->prof;
+        norms_of(c->Xr.p, n, c->rn.p);
+        TR_LAUNCH(pf, st, "normalise", 0, 16.0 * n * nov, row_scale_inv<<<dim3(nblk, n), 256, 0, st>>>(c->Xr.p, n, nov, c->rn.p));
+        TR_LAUNCH(pf, st, "sign_fix", 0, 0, sign_fix<<<n, 1024, 0, st>>>(c->Xr.p, nov));
+        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        TR_CUDA(cudaMemcpyAsync(omega, c->theta.p, sizeof(double) * n, kind, st));
+        if (Xout) TR_CUDA(cudaMemcpyAsync(Xout, c->Xr.p, sizeof(double) * (size_t)n * nov, kind, st));
+        if (resid) {
+            if (on_device)
+                TR_CUDA(cudaMemcpyAsync(resid, rn_h.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+            else
+                std::copy(rn_h.begin(), rn_h.end(), resid);
+        }
+        TR_CUDA(cudaStreamSynchronize(st));
+        if (c->cst) TR_CUDA(cudaStreamSynchronize(c->cst));
+        if (info) {
+            info->niter = it;
+            info->nmatvec = nmv;
+            info->nrestart = nrestart;
+            info->converged = converged;
+            info->t_matvec_ms = t_mv;
+            info->t_ortho_ms = t_or;
+            info->t_eigh_ms = t_eig;
+            info->t_other_ms = t_oth;
+            info->max_space = maxsp;
+            info->dev_rows = kd;
+            info->host_bytes_moved = moved;
+        }
+        return converged ? TR_OK : TR_ENOCONV;
     }
-    TR_CUDA(cudaStreamSynchronize(st));
-    if (c->cst) TR_CUDA(cudaStreamSynchronize(c->cst));
-    if (info) {
-        info->niter = it;
-        info->nmatvec = nmv;
-        info->nrestart = nrestart;
-        info->converged = converged;
-        info->t_matvec_ms = t_mv;
-        info->t_ortho_ms = t_or;
-        info->t_eigh_ms = t_eig;
-        info->t_other_ms = t_oth;
-        info->max_space = maxsp;
-        info->dev_rows = kd;
-        info->host_bytes_moved = moved;
+};
+
+int solve(tr_ctx *c, double *omega, double *Xout, double *resid, int on_device, tr_solve_info *info)
+{
+    TR_REQUIRE(omega, TR_EINVAL, "solve: omega must not be NULL");
+    Dav d(c);
+    d.guess();
+    d.apply_pending();
+    d.absorb();
+    TR_CUDA(cudaStreamSynchronize(d.st));
+    d.t_mv += elapsed(d.ev.e[4], d.ev.e[5]);
+    while (!d.done) {
+        d.eig_async();
+        TR_CUDA(cudaStreamSynchronize(d.st));
+        d.check();
+        if (d.done) break;
+        d.prepare();
+        if (d.done) break;
+        d.apply_pending();
+        d.absorb();
+        TR_CUDA(cudaStreamSynchronize(d.st));
+        d.t_mv += elapsed(d.ev.e[4], d.ev.e[5]);
     }
-    return converged ? TR_OK : TR_ENOCONV;
+    return d.output(omega, Xout, resid, on_device, info);
+}
+
+// ---------------------------------------------------------------- many molecules
+
+namespace {
+
+// The products of one Davidson step of all molecules as one CUDA graph: each
+// molecule's matvec on its own stream, forked from and joined to the batch
+// stream, recorded once for a fixed row count and replayed every step (rows
+// beyond a molecule's pending count are computed and ignored).
+struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int> members;
+    int rows_key = -1;
+    ~StepGraph()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+    void reset()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        members.clear();
+    }
+};
+
+void capture(StepGraph &g, cudaStream_t s0, std::vector<tr_ctx *> &cs, const std::vector<int> &members,
+             const std::vector<int> &rows, cudaEvent_t fork, std::vector<cudaEvent_t> &joins)
+{
+    g.reset();
+    // profiling events cannot live inside the graph
+    std::vector<bool> prof_on(cs.size());
+    for (size_t i = 0; i < cs.size(); ++i) {
+        prof_on[i] = cs[i]->prof.enabled;
+        cs[i]->prof.flush();
+        cs[i]->prof.enabled = false;
+    }
+    cudaGraph_t graph = nullptr;
+    TR_CUDA(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    try {
+        TR_CUDA(cudaEventRecord(fork, s0));
+        for (int i : members) {
+            tr_ctx *c = cs[i];
+            TR_CUDA(cudaStreamWaitEvent(c->st, fork, 0));
+            matvec(c, rows[i], c->Tn.p, c->Wn.p);
+            TR_CUDA(cudaEventRecord(joins[i], c->st));
+            TR_CUDA(cudaStreamWaitEvent(s0, joins[i], 0));
+        }
+    } catch (...) {
+        cudaStreamEndCapture(s0, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        for (size_t i = 0; i < cs.size(); ++i) cs[i]->prof.enabled = prof_on[i];
+        throw;
+    }
+    err = cudaStreamEndCapture(s0, &graph);
+    for (size_t i = 0; i < cs.size(); ++i) cs[i]->prof.enabled = prof_on[i];
+    TR_CUDA(err);
+    err = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    TR_CUDA(err);
+    g.members = members;
+}
+
+// Pick the tensor-core tile width of each reduced-precision context by timing
+// one product of `rows` vectors with 64- and 128-wide tiles.
+void autotune(std::vector<tr_ctx *> &cs, const std::vector<int> &rows)
+{
+    cudaEvent_t a, b;
+    TR_CUDA(cudaEventCreate(&a));
+    TR_CUDA(cudaEventCreate(&b));
+    for (size_t i = 0; i < cs.size(); ++i) {
+        tr_ctx *c = cs[i];
+        if (c->opt.precision != TR_MIXED || !c->k_active) continue;
+        float best = 1e30f;
+        int pick = 128;
+        for (int bn : {128, 64}) {
+            c->tc_bn = bn;
+            matvec(c, rows[i], c->Tn.p, c->Wn.p);  // warm
+            TR_CUDA(cudaEventRecord(a, c->st));
+            matvec(c, rows[i], c->Tn.p, c->Wn.p);
+            TR_CUDA(cudaEventRecord(b, c->st));
+            TR_CUDA(cudaEventSynchronize(b));
+            float ms = elapsed(a, b);
+            if (ms < best) {
+                best = ms;
+                pick = bn;
+            }
+        }
+        c->tc_bn = pick;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+}
+
+}  // namespace
+
+int solve_batch(tr_ctx **ctxs, int nb, double **omega, double **X, double **resid, int on_device,
+                tr_solve_info *infos, int autotune_tiles)
+{
+    TR_REQUIRE(ctxs && nb > 0 && omega, TR_EINVAL, "solve_batch: empty batch");
+    std::vector<tr_ctx *> cs(ctxs, ctxs + nb);
+    for (int i = 0; i < nb; ++i) {
+        TR_REQUIRE(cs[i] && cs[i]->built, TR_EINVAL, "solve_batch: every context must be built");
+        TR_REQUIRE(omega[i], TR_EINVAL, "solve_batch: omega must not be NULL");
+        for (int j = 0; j < i; ++j) TR_REQUIRE(cs[i] != cs[j], TR_EINVAL, "solve_batch: a context appears twice");
+        TR_REQUIRE(cs[i]->device == cs[0]->device, TR_EINVAL, "solve_batch: contexts on different devices");
+    }
+    // every molecule works on a stream of its own for the duration of the call
+    struct Streams {
+        std::vector<tr_ctx *> &cs;
+        std::vector<cudaStream_t> orig, own;
+        cudaStream_t s0 = nullptr;
+        cudaEvent_t fork = nullptr, done = nullptr;
+        std::vector<cudaEvent_t> joins;
+        explicit Streams(std::vector<tr_ctx *> &c) : cs(c) {}
+        ~Streams()
+        {
+            for (size_t i = 0; i < own.size(); ++i) {
+                cudaStreamSynchronize(own[i]);
+                cs[i]->st = orig[i];
+                cudaStreamDestroy(own[i]);
+            }
+            for (auto e : joins) cudaEventDestroy(e);
+            if (fork) cudaEventDestroy(fork);
+            if (done) cudaEventDestroy(done);
+            if (s0) {
+                cudaStreamSynchronize(s0);
+                cudaStreamDestroy(s0);
+            }
+        }
+    } S(cs);
+    for (int i = 0; i < nb; ++i) TR_CUDA(cudaStreamSynchronize(cs[i]->st));
+    TR_CUDA(cudaStreamCreateWithFlags(&S.s0, cudaStreamNonBlocking));
+    TR_CUDA(cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming));
+    TR_CUDA(cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming));
+    for (int i = 0; i < nb; ++i) {
+        cudaStream_t s;
+        TR_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        S.orig.push_back(cs[i]->st);
+        S.own.push_back(s);
+        cs[i]->st = s;
+        cudaEvent_t e;
+        TR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        S.joins.push_back(e);
+    }
+    std::vector<std::unique_ptr<Dav>> ds;
+    for (int i = 0; i < nb; ++i) ds.emplace_back(new Dav(cs[i]));
+    std::vector<int> init_rows(nb), step_rows(nb);
+    for (int i = 0; i < nb; ++i) {
+        init_rows[i] = ds[i]->b0;
+        step_rows[i] = ds[i]->n;
+    }
+    if (autotune_tiles)
+        autotune(cs, step_rows);
+    else
+        for (int i = 0; i < nb; ++i) matvec(cs[i], step_rows[i], cs[i]->Tn.p, cs[i]->Wn.p);  // loads kernels before capture
+
+    cudaEvent_t g0, g1;
+    TR_CUDA(cudaEventCreate(&g0));
+    TR_CUDA(cudaEventCreate(&g1));
+    struct EvGuard {
+        cudaEvent_t a, b;
+        ~EvGuard()
+        {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } eg{g0, g1};
+    double graph_ms = 0.0;
+    long graph_launches = 0;
+    StepGraph gi, gs;
+    auto run_graph = [&](StepGraph &g, const std::vector<int> &members) {
+        for (int i : members) {
+            TR_CUDA(cudaEventRecord(S.joins[i], cs[i]->st));
+            TR_CUDA(cudaStreamWaitEvent(S.s0, S.joins[i], 0));
+        }
+        TR_CUDA(cudaEventRecord(g0, S.s0));
+        TR_CUDA(cudaGraphLaunch(g.exec, S.s0));
+        TR_CUDA(cudaEventRecord(g1, S.s0));
+        TR_CUDA(cudaEventRecord(S.done, S.s0));
+        for (int i : members) TR_CUDA(cudaStreamWaitEvent(cs[i]->st, S.done, 0));
+        graph_launches += 1;
+    };
+
+    std::vector<int> all(nb);
+    std::iota(all.begin(), all.end(), 0);
+    for (int i = 0; i < nb; ++i) ds[i]->guess();
+    capture(gi, S.s0, cs, all, init_rows, S.fork, S.joins);
+    run_graph(gi, all);
+    for (int i = 0; i < nb; ++i) ds[i]->absorb();
+    TR_CUDA(cudaEventSynchronize(g1));
+    graph_ms += elapsed(g0, g1);
+    gi.reset();
+
+    while (true) {
+        std::vector<int> act;
+        for (int i = 0; i < nb; ++i)
+            if (!ds[i]->done) act.push_back(i);
+        if (act.empty()) break;
+        for (int i : act) ds[i]->eig_async();
+        for (int i : act) {
+            TR_CUDA(cudaStreamSynchronize(ds[i]->st));
+            ds[i]->check();
+        }
+        std::vector<int> pend;
+        for (int i : act) {
+            if (ds[i]->done) continue;
+            ds[i]->prepare();
+            if (!ds[i]->done) pend.push_back(i);
+        }
+        if (pend.empty()) continue;
+        if (gs.exec == nullptr || gs.members != pend) capture(gs, S.s0, cs, pend, step_rows, S.fork, S.joins);
+        run_graph(gs, pend);
+        for (int i : pend) ds[i]->absorb();
+        TR_CUDA(cudaEventSynchronize(g1));
+        graph_ms += elapsed(g0, g1);
+    }
+    int rc = TR_OK;
+    for (int i = 0; i < nb; ++i) {
+        ds[i]->t_mv = graph_ms;
+        int r = ds[i]->output(omega[i], X ? X[i] : nullptr, resid ? resid[i] : nullptr, on_device,
+                              infos ? &infos[i] : nullptr);
+        if (r != TR_OK) rc = r;
+    }
+    (void)graph_launches;
+    return rc;
 }
 
 }  // namespace tr

@@ -201,7 +201,7 @@ void matvec_mixed(tr_ctx *c, int m, const double *X, double *AX)
                 o1.s2 = oKp;
                 const double b1 = 4.0 * 2 * ((double)mm * np * vK * oK + (double)mm * oK * vK + (double)np * vK * vK);
                 tc_gemm(pf, st, "K_stage1_tc", 3, c->tm_xw, 0, oK, 0, 0, c->tm_tab, (long long)P0 * vK, 0, vK, 0, oK,
-                        vK, vK, mm, np, o1, tc_err, b1);
+                        vK, vK, mm, np, o1, tc_err, b1, c->tc_bn);
                 // stage 2: AX_mia -= c_x sum_(P,j) T_ij^P M^P_mja
                 TcOut o2;
                 o2.mode = TC_ACC64;
@@ -212,7 +212,7 @@ void matvec_mixed(tr_ctx *c, int m, const double *X, double *AX)
                 o2.s1 = nov;
                 const double b2 = 4.0 * 2 * ((double)mm * np * vK * oKp + (double)oK * np * oKp) + 16.0 * mm * oK * vK;
                 tc_gemm(pf, st, "K_stage2_tc", 3, c->tm_t2, 0, 0, 0, P0 * oKp, c->tm_mt, 0, vK, 0, 0, oK, vK, np * oKp,
-                        mm, 1, o2, tc_err, b2);
+                        mm, 1, o2, tc_err, b2, c->tc_bn);
             }
         }
     }

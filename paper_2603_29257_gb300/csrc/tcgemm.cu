@@ -20,8 +20,8 @@
 namespace tr {
 namespace {
 
-constexpr int BM = 128, BN = 128, BKF = 32;   // tile: 128 x 128 outputs, 32 FP32 (128 B) of K per stage
-constexpr int TILE_BYTES = BM * BKF * 4;      // 16 KB
+constexpr int BM = 128, BKF = 32;             // tile: 128 x BN outputs, 32 FP32 (128 B) of K per stage
+constexpr int TILE_BYTES = BM * BKF * 4;      // 16 KB (A tile; a B tile is BN * 128 B)
 constexpr long long WAIT_CYCLES = 2000000000LL;
 
 struct TcArgs {
@@ -91,14 +91,21 @@ __device__ __forceinline__ float tf32_rest(float v)
     return v - __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
 }
 
-template <int NSPLIT, int MODE>
+template <int NSPLIT, int STAGES, int BN>
+constexpr uint32_t stage_bytes()
+{
+    return (NSPLIT == 3 ? 2u : 1u) * (uint32_t)(TILE_BYTES + BN * BKF * 4);
+}
+
+template <int NSPLIT, int MODE, int BN>
 __global__ void __launch_bounds__(128, 1)
     tc_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
               const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl, const TcArgs g)
 {
-    constexpr int STAGES = NSPLIT == 3 ? 3 : 4;
-    constexpr int NT = NSPLIT == 3 ? 4 : 2;
-    constexpr uint32_t STAGE_BYTES = NT * TILE_BYTES;
+    constexpr int STAGES = NSPLIT == 3 ? (BN == 64 ? 4 : 3) : 4;
+    constexpr int BTILE = BN * BKF * 4;
+    constexpr uint32_t STAGE_BYTES = stage_bytes<NSPLIT, STAGES, BN>();
+    // stage layout: A value | B value | A remainder | B remainder
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *bars = (uint64_t *)(smem + STAGES * STAGE_BYTES);  // full[S], empty[S], done
@@ -136,8 +143,8 @@ __global__ void __launch_bounds__(128, 1)
                 tma2d(sa(stg), &tAh, xa, arow, full);
                 tma2d(sa(stg + TILE_BYTES), &tBh, xb, brow, full);
                 if (NSPLIT == 3) {
-                    tma2d(sa(stg + 2 * TILE_BYTES), &tAl, xa, arow, full);
-                    tma2d(sa(stg + 3 * TILE_BYTES), &tBl, xb, brow, full);
+                    tma2d(sa(stg + TILE_BYTES + BTILE), &tAl, xa, arow, full);
+                    tma2d(sa(stg + 2 * TILE_BYTES + BTILE), &tBl, xb, brow, full);
                 }
             }
         }
@@ -145,7 +152,7 @@ __global__ void __launch_bounds__(128, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // kind::tf32 instruction descriptor: FP32 accumulator, TF32 A and B, both
-            // K-major, N = 128, M = 128
+            // K-major, N = BN, M = 128
             const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                    ((uint32_t)(BM >> 4) << 24);
             for (int kt = 0; kt < nk; ++kt) {
@@ -154,7 +161,8 @@ __global__ void __launch_bounds__(128, 1)
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 uint8_t *stg = smem + s * STAGE_BYTES;
                 const uint64_t dA = smem_desc(sa(stg)), dB = smem_desc(sa(stg + TILE_BYTES));
-                const uint64_t dAl = smem_desc(sa(stg + 2 * TILE_BYTES)), dBl = smem_desc(sa(stg + 3 * TILE_BYTES));
+                const uint64_t dAl = smem_desc(sa(stg + TILE_BYTES + BTILE));
+                const uint64_t dBl = smem_desc(sa(stg + 2 * TILE_BYTES + BTILE));
 #pragma unroll
                 for (int kk = 0; kk < BKF / 8; ++kk) {
                     mma(tmem, dA + 2 * kk, dB + 2 * kk, idesc, (kt | kk) ? 1u : 0u);
@@ -278,11 +286,11 @@ EncodeTiled encoder()
     return fn;
 }
 
-void encode(CUtensorMap &tm, const float *p, long long rows, long long kdim, long long ld)
+void encode(CUtensorMap &tm, const float *p, long long rows, long long kdim, long long ld, int box_rows)
 {
     cuuint64_t gdim[2] = {(cuuint64_t)kdim, (cuuint64_t)rows};
     cuuint64_t gstr[1] = {(cuuint64_t)ld * 4};
-    cuuint32_t box[2] = {BKF, BM};
+    cuuint32_t box[2] = {BKF, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = encoder()(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)p, gdim, gstr, box, es,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -290,19 +298,29 @@ void encode(CUtensorMap &tm, const float *p, long long rows, long long kdim, lon
     TR_REQUIRE(r == CUDA_SUCCESS, TR_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
 }
 
-template <int NSPLIT, int MODE>
+template <int NSPLIT, int MODE, int BN>
 void launch(cudaStream_t st, dim3 grid, const TcMat &A, const TcMat &B, const TcArgs &g)
 {
-    constexpr int STAGES = NSPLIT == 3 ? 3 : 4;
-    constexpr int NT = NSPLIT == 3 ? 4 : 2;
-    const size_t smem = (size_t)STAGES * NT * TILE_BYTES + 1024 + 256;
+    constexpr int STAGES = NSPLIT == 3 ? (BN == 64 ? 4 : 3) : 4;
+    const size_t smem = (size_t)STAGES * stage_bytes<NSPLIT, STAGES, BN>() + 1024 + 256;
     static bool attr = false;
     if (!attr) {
-        TR_CUDA(cudaFuncSetAttribute(tc_kernel<NSPLIT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        TR_CUDA(cudaFuncSetAttribute(tc_kernel<NSPLIT, MODE, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
         attr = true;
     }
-    tc_kernel<NSPLIT, MODE><<<grid, 128, smem, st>>>(A.mhi, NSPLIT == 3 ? A.mlo : A.mhi, B.mhi,
-                                                     NSPLIT == 3 ? B.mlo : B.mhi, g);
+    const CUtensorMap &bh = BN == 64 ? B.mhi64 : B.mhi;
+    const CUtensorMap &bl = BN == 64 ? B.mlo64 : B.mlo;
+    tc_kernel<NSPLIT, MODE, BN><<<grid, 128, smem, st>>>(A.mhi, NSPLIT == 3 ? A.mlo : A.mhi, bh, NSPLIT == 3 ? bl : bh, g);
+}
+
+template <int NSPLIT, int BN>
+void launch_mode(cudaStream_t st, dim3 grid, const TcMat &A, const TcMat &B, const TcArgs &g, int mode)
+{
+    if (mode == TC_SPLIT) launch<NSPLIT, TC_SPLIT, BN>(st, grid, A, B, g);
+    else if (mode == TC_ACC64) launch<NSPLIT, TC_ACC64, BN>(st, grid, A, B, g);
+    else if (mode == TC_STORE32) launch<NSPLIT, TC_STORE32, BN>(st, grid, A, B, g);
+    else launch<NSPLIT, TC_STORE64, BN>(st, grid, A, B, g);
 }
 
 }  // namespace
@@ -318,16 +336,24 @@ void tc_make(TcMat &m, const float *hi, const float *lo, long long rows, long lo
     m.rows = rows;
     m.kdim = kdim;
     m.ld = ld;
-    encode(m.mhi, hi, rows, kdim, ld);
-    if (lo) encode(m.mlo, lo, rows, kdim, ld);
-    else m.mlo = m.mhi;
+    encode(m.mhi, hi, rows, kdim, ld, 128);
+    encode(m.mhi64, hi, rows, kdim, ld, 64);
+    if (lo) {
+        encode(m.mlo, lo, rows, kdim, ld, 128);
+        encode(m.mlo64, lo, rows, kdim, ld, 64);
+    } else {
+        m.mlo = m.mhi;
+        m.mlo64 = m.mhi64;
+    }
 }
 
 void tc_gemm(Prof &prof, cudaStream_t st, const char *name, int nsplit, const TcMat &A, long long a0, long long a1,
              long long a2, int ka0, const TcMat &B, long long c0, long long c1, long long c2, int kb0, int M, int N,
-             int K, int n1, int n2, const TcOut &out, int *err, double alg_bytes)
+             int K, int n1, int n2, const TcOut &out, int *err, double alg_bytes, int bn)
 {
     if (M <= 0 || N <= 0 || n1 <= 0 || n2 <= 0) return;
+    TR_REQUIRE(bn == 64 || bn == 128, TR_EINVAL, "tc_gemm: tile width must be 64 or 128");
+    const int BN = bn;
     TR_REQUIRE(nsplit == 1 || nsplit == 3, TR_EINVAL, "tc_gemm: nsplit must be 1 or 3");
     TR_REQUIRE(nsplit == 1 || (A.lo && B.lo), TR_EINVAL, "tc_gemm: 3-product form needs lo parts");
     TR_REQUIRE(K > 0 && ka0 >= 0 && kb0 >= 0 && ka0 + K <= A.kdim && kb0 + K <= B.kdim, TR_EINVAL, "tc_gemm: bad K");
@@ -358,17 +384,10 @@ void tc_gemm(Prof &prof, cudaStream_t st, const char *name, int nsplit, const Tc
     const double flops = 2.0 * M * N * (double)K * n1 * n2;
     const double bytes = alg_bytes >= 0 ? alg_bytes : 4.0 * nsplit * ((double)M + N) * K * n1 * n2;
     int tok = prof.begin(st, name, flops, bytes);
-    if (nsplit == 3) {
-        if (out.mode == TC_SPLIT) launch<3, TC_SPLIT>(st, grid, A, B, g);
-        else if (out.mode == TC_ACC64) launch<3, TC_ACC64>(st, grid, A, B, g);
-        else if (out.mode == TC_STORE32) launch<3, TC_STORE32>(st, grid, A, B, g);
-        else launch<3, TC_STORE64>(st, grid, A, B, g);
-    } else {
-        if (out.mode == TC_SPLIT) launch<1, TC_SPLIT>(st, grid, A, B, g);
-        else if (out.mode == TC_ACC64) launch<1, TC_ACC64>(st, grid, A, B, g);
-        else if (out.mode == TC_STORE32) launch<1, TC_STORE32>(st, grid, A, B, g);
-        else launch<1, TC_STORE64>(st, grid, A, B, g);
-    }
+    if (nsplit == 3 && bn == 128) launch_mode<3, 128>(st, grid, A, B, g, out.mode);
+    else if (nsplit == 3) launch_mode<3, 64>(st, grid, A, B, g, out.mode);
+    else if (bn == 128) launch_mode<1, 128>(st, grid, A, B, g, out.mode);
+    else launch_mode<1, 64>(st, grid, A, B, g, out.mode);
     TR_CUDA(cudaGetLastError());
     prof.end(st, tok);
 }

@@ -17,7 +17,8 @@ namespace tr {
 struct TcMat {
     const float *hi = nullptr, *lo = nullptr;
     long long rows = 0, kdim = 0, ld = 0;
-    CUtensorMap mhi, mlo;
+    CUtensorMap mhi, mlo;      // boxes of 128 rows x 32 values
+    CUtensorMap mhi64, mlo64;  // boxes of 64 rows x 32 values (B operand of 64-wide tiles)
 };
 
 void tc_make(TcMat &m, const float *hi, const float *lo, long long rows, long long kdim, long long ld);
@@ -44,10 +45,11 @@ struct TcOut {
 // beyond M or N belong to neighbouring batch entries or lie outside the view
 // (zero-filled by TMA); they are computed and discarded.  nsplit = 1 (TF32) or
 // 3 (3xTF32).  err: device int set non-zero if a pipeline wait timed out.
+// bn: output tile width, 128 (default) or 64 (narrow N).
 void tc_gemm(Prof &prof, cudaStream_t st, const char *name, int nsplit, const TcMat &A, long long a0,
              long long a1, long long a2, int ka0, const TcMat &B, long long c0, long long c1, long long c2,
              int kb0, int M, int N, int K, int n1, int n2, const TcOut &out, int *err,
-             double alg_bytes = -1.0);
+             double alg_bytes = -1.0, int bn = 128);
 
 // hi = (float)x, lo = hi - tf32(hi) for x[rows][cols] (ld_in) -> [rows][cols] (ld_out)
 void tc_split(Prof &prof, cudaStream_t st, const double *x, long long rows, long long cols, long long ld_in,

@@ -72,6 +72,9 @@ SIGNATURES = {
     "tr_matvec_noalloc": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p]),
     "tr_solve": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int,
                             ct.POINTER(SolveInfo)]),
+    "tr_solve_batch": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.c_int, ct.POINTER(ct.c_void_p),
+                                  ct.POINTER(ct.c_void_p), ct.POINTER(ct.c_void_p), ct.c_int,
+                                  ct.POINTER(SolveInfo), ct.c_int]),
     "tr_profile": (ct.c_int, [ct.c_void_p, ct.c_int]),
     "tr_profile_get": (ct.c_int, [ct.c_void_p, ct.POINTER(ProfEntry), ct.c_int]),
     "tr_launch_count": (ct.c_long, [ct.c_void_p]),
@@ -94,6 +97,29 @@ def lib():
             f.argtypes = args
         _lib = L
     return _lib
+
+
+def solve_batch(contexts, autotune=True):
+    """Lockstep Davidson solves of several built contexts (tr_solve_batch).
+    Returns a list of (omega, X, resid, info) with host arrays."""
+    n = len(contexts)
+    hs = (ct.c_void_p * n)(*[c._h for c in contexts])
+    oms, Xs, rss = [], [], []
+    for c in contexts:
+        d = c.dims()
+        k = min(c.options.nstates, d.nocc * d.nvir)
+        oms.append(np.zeros(k))
+        Xs.append(np.zeros((k, d.nocc, d.nvir)))
+        rss.append(np.zeros(k))
+    P = ct.c_void_p * n
+    op = P(*[a.ctypes.data for a in oms])
+    xp = P(*[a.ctypes.data for a in Xs])
+    rp = P(*[a.ctypes.data for a in rss])
+    infos = (SolveInfo * n)()
+    rc = lib().tr_solve_batch(hs, n, op, xp, rp, 0, infos, 1 if autotune else 0)
+    if rc not in (TR_OK, TR_ENOCONV):
+        raise TDARispError(rc, "tr_solve_batch: " + lib().tr_last_error(contexts[0]._h).decode())
+    return [(oms[i], Xs[i], rss[i], infos[i]) for i in range(n)]
 
 
 class TDARispError(RuntimeError):

@@ -404,6 +404,213 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def batched_molecules(count=64, seed0=1000, lo=20, hi=150):
+    """64 seeded molecules with atom counts log-uniform in [20, 150]."""
+    from paper_2603_29257_gb300 import synth
+    out = []
+    for s in range(seed0, seed0 + count):
+        rng = np.random.default_rng(s)
+        natoms = int(round(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
+        out.append(synth.molecule_by_atoms(s, natoms))
+    return out
+
+
+BATCH_OPTS = dict(cx=0.25, k_alpha=1.0, k_beta=0.0, omega=0.0, window_ev=40.0, nstates=10, tol=1e-5,
+                  max_iter=200)
+
+
+def run_batched(args):
+    """Batched form: 64 molecules (20-150 atoms, 10 states each) in the reduced-precision
+    form, all Davidson solves advanced in lockstep with one graph launch of all
+    products per step; against 64 sequential plain FP64 solves."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_29257_gb300 import tdarisp
+    t0 = time.perf_counter()
+    mols = batched_molecules()
+    gen_s = time.perf_counter() - t0
+    torch.zeros(1, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def make(precision):
+        cs = []
+        for m in mols:
+            c = tdarisp.Context(stream=stream.cuda_stream, precision=precision, **BATCH_OPTS)
+            c.set_molecule_from(m)
+            cs.append(c)
+        return cs
+
+    # batched, reduced precision: concurrent builds, lockstep solves
+    def build_all(cs):
+        tdarisp.build_batch(cs)
+
+    cs = make(1)
+    for _ in range(max(args.warmup, 1)):
+        build_all(cs)
+        tdarisp.solve_batch(cs, autotune=True)
+    torch.cuda.synchronize()
+    times, nmv_b, res_b, tb = [], 0, None, []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        build_all(cs)
+        torch.cuda.synchronize()
+        tb.append(time.perf_counter() - t)
+        res_b = tdarisp.solve_batch(cs, autotune=True)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t)
+        nmv_b = sum(r[3].nmatvec for r in res_b)
+    t_batch = statistics.median(times)
+    t_build = statistics.median(tb)
+    for c in cs:
+        c.close()
+    # sequential, reduced precision
+    cs = make(1)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    nmv_m = 0
+    for c in cs:
+        c.build()
+        nmv_m += c.solve(want_x=True)[3].nmatvec
+    torch.cuda.synchronize()
+    t_seq_mixed = time.perf_counter() - t
+    for c in cs:
+        c.close()
+    # sequential, plain FP64
+    cs = make(0)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    nmv_f, om_f = 0, []
+    for c in cs:
+        c.build()
+        om, X, rs, info = c.solve(want_x=True)
+        nmv_f += info.nmatvec
+        om_f.append(om)
+    torch.cuda.synchronize()
+    t_seq_fp64 = time.perf_counter() - t
+    for c in cs:
+        c.close()
+    dmax = max(float(np.abs(r[0] - o).max()) for r, o in zip(res_b, om_f))
+    natoms = [len(m.Z) for m in mols]
+    line = {"metric": "TDA-risp matvecs/s, batched form (64 molecules, build + solve)",
+            "value": nmv_b / t_batch, "unit": "matvecs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 1), "ms_per_step": 1e3 * t_batch, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32/tf32x3 + f64", "data": "synthetic",
+            "config": {"workload": "64 seeded molecules (seeds 1000-1063), atoms log-uniform 20-150 "
+                                   "(%d-%d, %d total), 10 states each, global hybrid c_x 0.25, 40 eV window, "
+                                   "tol 1e-5" % (min(natoms), max(natoms), sum(natoms)),
+                       "timing": "host wall clock around build of all 64 contexts + tr_solve_batch"},
+            "batched_s": t_batch, "batched_build_s": t_build, "batched_solve_s": t_batch - t_build,
+            "sequential_mixed_s": t_seq_mixed, "sequential_fp64_s": t_seq_fp64,
+            "speedup_vs_sequential_fp64": t_seq_fp64 / t_batch,
+            "speedup_vs_sequential_mixed": t_seq_mixed / t_batch,
+            "matvecs": {"batched": nmv_b, "sequential_mixed": nmv_m, "sequential_fp64": nmv_f},
+            "max_abs_dOmega_vs_fp64_Ha": dmax, "generation_s": gen_s}
+    print(json.dumps(line))
+
+
+SERVE_OPTS = dict(cx=0.25, k_alpha=1.0, k_beta=0.0, omega=0.0, window_ev=40.0, tol=1e-5, max_iter=200)
+
+
+def serve_stream(count, seed0=5000, arrival_seed=5001, lo=30, hi=150):
+    """Seeded request stream: molecule k from seed seed0+k with atoms log-uniform in
+    [lo, hi]; states U{5..15} and unit-rate exponential gaps from arrival_seed."""
+    from paper_2603_29257_gb300 import synth
+    rng = np.random.default_rng(arrival_seed)
+    nst = rng.integers(5, 16, size=count)
+    gaps = rng.exponential(1.0, size=count)
+    mols = []
+    for k in range(count):
+        r = np.random.default_rng(seed0 + k)
+        natoms = int(round(np.exp(r.uniform(np.log(lo), np.log(hi)))))
+        mols.append(synth.molecule_by_atoms(seed0 + k, natoms))
+    return mols, [int(n) for n in nst], np.cumsum(gaps) - gaps[0]
+
+
+def _replay(tdarisp, mols, nst, arrivals, precision, max_active, build_threads):
+    """Submit request k at arrivals[k] seconds (server clock), collect every result."""
+    with tdarisp.Server(max_active=max_active, autotune=True, build_threads=build_threads) as srv:
+        t0 = srv.clock()
+        ids = {}
+        for k, (m, n) in enumerate(zip(mols, nst)):
+            wait = t0 + arrivals[k] - srv.clock()
+            if wait > 0:
+                time.sleep(wait)
+            ids[srv.submit(m, precision=precision, nstates=n, **SERVE_OPTS)] = k
+        res = srv.drain()
+    out = [None] * len(mols)
+    for r in res:
+        if r["status"] != 0:
+            raise RuntimeError("request %d failed: %s" % (ids[r["id"]], r["error"]))
+        out[ids[r["id"]]] = r
+    lat = np.array([r["t_done"] - r["t_submit"] for r in out])
+    span = max(r["t_done"] for r in out) - min(r["t_submit"] for r in out)
+    return out, {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                 "mean_ms": 1e3 * float(lat.mean()), "molecules_per_s": len(out) / span, "span_s": span,
+                 "matvecs": int(sum(r["nmatvec"] for r in out))}
+
+
+def run_serve(args):
+    """Serving form: a seeded Poisson stream of requests served by the continuous-
+    batching server in the reduced-precision form at offered loads 0.3/0.7/0.9 of
+    the rate one request served alone sustains, and saturated (all at once);
+    against the plain FP64 form served one request at a time on the same stream."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_29257_gb300 import tdarisp
+    t = time.perf_counter()
+    mols, nst, unit_gaps = serve_stream(args.requests)
+    gen_s = time.perf_counter() - t
+    torch.zeros(1, device="cuda")
+    R = len(mols)
+    # warm-up: module loading, kernel attributes, graph paths
+    for _ in range(max(args.warmup, 1)):
+        _replay(tdarisp, mols[:4], nst[:4], np.zeros(4), 1, 64, 4)
+    # service time of each request served alone (reduced precision)
+    alone = []
+    with tdarisp.Server(max_active=64, autotune=True) as srv:
+        for m, n in zip(mols, nst):
+            srv.submit(m, precision=1, nstates=n, **SERVE_OPTS)
+            r = srv.drain()[0]
+            alone.append(r["t_done"] - r["t_submit"])
+    s_mean = float(np.mean(alone))
+    loads = {}
+    res07 = None
+    for rho in (0.3, 0.7, 0.9):
+        res, st = _replay(tdarisp, mols, nst, unit_gaps * s_mean / rho, 1, 64, 4)
+        st["lambda_per_s"] = rho / s_mean
+        loads[str(rho)] = st
+        if rho == 0.7:
+            res07 = res
+    res_sat, sat = _replay(tdarisp, mols, nst, np.zeros(R), 1, 64, 4)
+    # plain FP64 form, one request at a time, same stream
+    res_f, f07 = _replay(tdarisp, mols, nst, unit_gaps * s_mean / 0.7, 0, 1, 1)
+    _, fsat = _replay(tdarisp, mols, nst, np.zeros(R), 0, 1, 1)
+    dmax = max(float(np.abs(a["omega"] - b["omega"]).max()) for a, b in zip(res07, res_f))
+    dmax_sat = max(float(np.abs(a["omega"] - b["omega"]).max()) for a, b in zip(res_sat, res_f))
+    natoms = [len(m.Z) for m in mols]
+    line = {"metric": "TDA-risp serve p50/p99 ms @1e-5 Ha and molecules/s, serving form",
+            "value": loads["0.7"]["p99_ms"], "unit": "ms (p99 latency at load 0.7)", "n_gpus": 1,
+            "steps": 1, "warmup": max(args.warmup, 1), "ms_per_step": 1e3 * loads["0.7"]["span_s"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32/tf32x3 + f64",
+            "data": "synthetic",
+            "config": {"workload": "%d seeded requests (molecule seeds 5000-%d, arrival seed 5001), atoms "
+                                   "log-uniform 30-150 (%d-%d), states U{5..15}, global hybrid c_x 0.25, "
+                                   "40 eV window, tol 1e-5; Poisson arrivals at load rho = lambda x mean "
+                                   "service time alone" % (R, 5000 + R - 1, min(natoms), max(natoms)),
+                       "timing": "server clock (host steady clock) from submit to result posted"},
+            "service_alone_mean_ms": 1e3 * s_mean, "loads": loads, "saturated": sat,
+            "fp64_one_at_a_time": {"0.7": f07, "saturated": fsat},
+            "throughput_vs_fp64_saturated": sat["molecules_per_s"] / fsat["molecules_per_s"],
+            "p99_vs_fp64_at_0.7": f07["p99_ms"] / loads["0.7"]["p99_ms"],
+            "max_abs_dOmega_vs_fp64_Ha": max(dmax, dmax_sat), "generation_s": gen_s}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -413,11 +620,19 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the reduced-precision form")
+    ap.add_argument("--workload", default="fp64-200", choices=["fp64-200", "batched", "serve"],
+                    help="batched: 64 molecules in the reduced-precision batched form; "
+                         "serve: a Poisson request stream through the serving runtime")
+    ap.add_argument("--requests", type=int, default=64, help="requests of the serve workload")
     ap.add_argument("--case", default="full", choices=["full", "small"],
                     help="small: 100-atom molecule of the same shape, for profiler captures")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_native(args)
 

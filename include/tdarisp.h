@@ -89,6 +89,7 @@ typedef struct {
                             restarts earlier (Sec. 3.3) */
     int dav_dev_rows;    /* cap on Davidson vectors kept on the device (0: as many as the
                             HBM budget allows); rows beyond it live in pinned host memory */
+    size_t matvec_ws_bytes; /* scratch for the exchange intermediate M (0: 4 GiB) */
 } tr_options;
 
 typedef struct {
@@ -216,6 +217,11 @@ int tr_matvec_noalloc(tr_ctx *ctx, int m, const double *X, double *AX);
 int tr_solve(tr_ctx *ctx, double *omega, double *X, double *resid, int on_device,
              tr_solve_info *info);
 
+/* tr_build of n contexts concurrently: nthreads host threads (0: 8), each
+   context on a stream of its own for the duration of the call.  Returns TR_OK
+   or the first error (each context keeps its own error text). */
+int tr_build_batch(tr_ctx **ctxs, int n, int nthreads);
+
 /* Davidson solves of n built contexts (n molecules, each with its own options)
    advanced in lockstep: every molecule works on a stream of its own, and the
    matrix-vector products of one Davidson step of all molecules are one CUDA
@@ -231,10 +237,76 @@ int tr_solve(tr_ctx *ctx, double *omega, double *X, double *resid, int on_device
 int tr_solve_batch(tr_ctx **ctxs, int n, double **omega, double **X, double **resid, int on_device,
                    tr_solve_info *infos, int autotune_tiles);
 
+/* ---- Serving runtime -------------------------------------------------------
+   Continuous batching of solves as requests arrive (not in the paper, which
+   runs one molecule at a time).  A builder thread admits requests in arrival
+   order when their estimated device footprint (tr_memory) fits in what is left
+   of the server budget -- a request larger than the whole budget is rejected with
+   TR_ENOMEM -- and builds them on streams of their own; a solver thread keeps
+   each built molecule's tensors and Davidson state resident and advances all of
+   them in lockstep, the products of one step being one CUDA-graph launch.
+   Molecules join at the next step after their build and leave when converged,
+   returning their memory to the budget.  Builds overlap with solver steps. */
+typedef struct tr_server tr_server;
+
+typedef struct {
+    int max_active;      /* molecules in the solver at once (0: 64) */
+    size_t hbm_budget;   /* device bytes for all admitted requests (0: 90% of free) */
+    int autotune_tiles;  /* pick the tensor-core tile width per molecule (TR_MIXED) */
+    int build_threads;   /* builds in flight at once (0: 4); admission stays in arrival order */
+} tr_server_options;
+
+typedef struct {
+    int natm;
+    const int *Z;
+    const double *xyz;
+    const double *aux_exp;
+    int nshell;
+    const tr_shell *shells;
+    int nao, nmo, nocc;
+    const double *C;     /* host, [nao][nmo] */
+    const double *eps;   /* host, [nmo] ascending */
+    tr_options opt;      /* functional, window, states, tolerance, precision */
+    int want_x;          /* return the excitation vectors (tr_result.X) */
+} tr_request;
+
+typedef struct {
+    long long id;
+    int status;          /* TR_OK, TR_ENOCONV, TR_ENOMEM (rejected), ... */
+    int nstates;
+    double omega[64];
+    double resid[64];
+    double *X;           /* [nstates][nocc][nvir] if requested; release with tr_free */
+    double t_submit, t_admit, t_built, t_done;  /* seconds on the server clock */
+    int niter, nmatvec;
+    char error[160];
+} tr_result;
+
+/* Start a server on the current device (opt may be NULL). */
+int tr_server_create(tr_server **out, const tr_server_options *opt);
+/* Queue a request (all arrays copied); *id receives its identifier. */
+int tr_server_submit(tr_server *srv, const tr_request *req, long long *id);
+/* Move up to max finished results to out; waits up to timeout_ms (< 0: until a
+   result arrives or nothing is outstanding; 0: no wait).  Returns the count. */
+int tr_server_poll(tr_server *srv, tr_result *out, int max, int timeout_ms);
+/* Requests submitted whose results have not been polled yet. */
+int tr_server_outstanding(tr_server *srv);
+/* Seconds since the server started (the clock of tr_result times). */
+double tr_server_clock(tr_server *srv);
+/* Stop the threads (unfinished requests are dropped) and release everything. */
+void tr_server_destroy(tr_server *srv);
+void tr_free(void *p);
+
 /* Kernel timing: enable (1) / disable (0) and reset the counters. */
 int tr_profile(tr_ctx *ctx, int enable);
 /* Copy up to max entries; returns the number of entries (>= 0) or an error. */
 int tr_profile_get(tr_ctx *ctx, tr_prof_entry *out, int max);
+/* Device memory of the context: bytes held now, the peak so far, and an
+   estimate of the peak of tr_build + tr_solve from the sizes (valid after
+   tr_set_orbitals; used for admission by the serving runtime).  Any pointer may
+   be NULL. */
+int tr_memory(tr_ctx *ctx, size_t *used, size_t *peak, size_t *estimate);
+
 /* Number of kernels this context has launched since creation. */
 long tr_launch_count(const tr_ctx *ctx);
 

@@ -1,7 +1,10 @@
 // C ABI of libtdarisp (declared in include/tdarisp.h).  Every entry point
 // converts internal exceptions into a status code and keeps the message in
 // the context.
+#include <atomic>
 #include <cstring>
+#include <thread>
+#include <vector>
 
 #include "ctx.cuh"
 
@@ -47,6 +50,7 @@ void normalise_options(tr_options *o)
 {
     if (!(o->screen > 0.0)) o->screen = 1e-22;
     if (o->aux_chunk_bytes == 0) o->aux_chunk_bytes = (size_t)2 << 30;
+    if (o->matvec_ws_bytes == 0) o->matvec_ws_bytes = (size_t)4 << 30;
 }
 
 }  // namespace
@@ -223,6 +227,47 @@ int tr_solve(tr_ctx *ctx, double *omega, double *X, double *resid, int on_device
     return guarded(ctx, [&]() { return tr::solve(ctx, omega, X, resid, on_device, info); });
 }
 
+int tr_build_batch(tr_ctx **ctxs, int n, int nthreads)
+{
+    if (!ctxs || n <= 0) return TR_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!ctxs[i]) return TR_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TR_ECUDA;
+    if (nthreads <= 0) nthreads = 8;
+    nthreads = std::min(nthreads, n);
+    // every context builds on a stream of its own
+    std::vector<cudaStream_t> orig(n), own(n, nullptr);
+    for (int i = 0; i < n; ++i) {
+        orig[i] = ctxs[i]->st;
+        if (cudaStreamSynchronize(orig[i]) != cudaSuccess || cudaStreamCreateWithFlags(&own[i], cudaStreamNonBlocking) != cudaSuccess) {
+            for (int j = 0; j < i; ++j) {
+                ctxs[j]->st = orig[j];
+                cudaStreamDestroy(own[j]);
+            }
+            return TR_ECUDA;
+        }
+        ctxs[i]->st = own[i];
+    }
+    std::vector<int> rc(n, TR_OK);
+    std::atomic<int> next(0);
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nthreads; ++t)
+        pool.emplace_back([&]() {
+            cudaSetDevice(dev);
+            for (int i = next++; i < n; i = next++) rc[i] = tr_build(ctxs[i]);
+        });
+    for (auto &t : pool) t.join();
+    int out = TR_OK;
+    for (int i = 0; i < n; ++i) {
+        cudaStreamSynchronize(own[i]);
+        ctxs[i]->st = orig[i];
+        cudaStreamDestroy(own[i]);
+        if (rc[i] != TR_OK && out == TR_OK) out = rc[i];
+    }
+    return out;
+}
+
 int tr_solve_batch(tr_ctx **ctxs, int n, double **omega, double **X, double **resid, int on_device,
                    tr_solve_info *infos, int autotune_tiles)
 {
@@ -264,5 +309,18 @@ int tr_profile_get(tr_ctx *ctx, tr_prof_entry *out, int max)
 }
 
 long tr_launch_count(const tr_ctx *ctx) { return ctx ? ctx->prof.launches : 0; }
+
+int tr_memory(tr_ctx *ctx, size_t *used, size_t *peak, size_t *estimate)
+{
+    return guarded(ctx, [&]() {
+        if (used) *used = ctx->budget.used;
+        if (peak) *peak = ctx->budget.peak;
+        if (estimate) {
+            TR_REQUIRE(ctx->have_mol && ctx->have_orb, TR_EINVAL, "memory: molecule and orbitals required");
+            *estimate = tr::footprint(ctx);
+        }
+        return TR_OK;
+    });
+}
 
 }  // extern "C"

@@ -99,6 +99,8 @@ void get_tensor(tr_ctx *c, int which, double *out, int on_device);
 void matvec(tr_ctx *c, int m, const double *X, double *AX);
 // allocate the matvec workspaces for blocks of up to m vectors
 void reserve_matvec(tr_ctx *c, int m);
+// estimated peak device bytes of tr_build + tr_solve
+size_t footprint(tr_ctx *c);
 // three-centre integrals of aux functions [p0, p0+np) of set which (0 = J, 1 = K)
 void compute_int3c_chunk(tr_ctx *c, int which, int p0, int np, double *out);
 // reduced-precision form (mixed.cu)

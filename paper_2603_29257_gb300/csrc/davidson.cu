@@ -10,9 +10,16 @@
 // A V for them, as the paper's memory-driven restart does (Sec. 3.3).
 // Convergence: every one of the nstates residual 2-norms below tol.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
 #include <memory>
+#include <mutex>
 #include <numeric>
+#include <thread>
 
 #include "ctx.cuh"
 
@@ -146,6 +153,9 @@ __global__ void cholqr_coef(const double *S, int p, double drop2, double *Gc, in
         }
         ++nacc;
     }
+    // rows past the accepted ones produce zero vectors
+    for (int l = nacc; l < p; ++l)
+        for (int m = 0; m < p; ++m) Gc[l * p + m] = 0.0;
     *nkeep = nacc;
 }
 
@@ -265,10 +275,13 @@ struct Dav {
     double t_mv = 0, t_or = 0, t_eig = 0, t_oth = 0;
     int k = 0, nmv = 0, nrestart = 0, it = 0, converged = 0;
     bool done = false, eig_timed = false, or_timed = false;
-    std::vector<double> rn_h, th_h;
     std::vector<int> unconv;
-    int jflag[2] = {0, 0};
-    int pend_p = 0, pend_k0 = 0;
+    // pinned host copies (asynchronous device-to-host): residual norms, Ritz
+    // values and flags [eigensolver, tensor core, first keep count, kept count]
+    double *h_rn = nullptr, *h_th = nullptr;
+    int *h_fl = nullptr;
+    int pend_p = 0, pend_k0 = 0, pend_max = 0;
+    bool pend_restart = false, pend_counted = true;
 
     explicit Dav(tr_ctx *ctx) : c(ctx), st(ctx->st)
     {
@@ -286,8 +299,10 @@ struct Dav {
         max_iter = c->opt.max_iter > 0 ? c->opt.max_iter : 200;
         tol = c->opt.tol;
         pmax = std::max(b0, n);
-        rn_h.assign(n, 0.0);
-        th_h.assign(n, 0.0);
+        TR_CUDA(cudaHostAlloc((void **)&h_rn, sizeof(double) * n, cudaHostAllocDefault));
+        TR_CUDA(cudaHostAlloc((void **)&h_th, sizeof(double) * n, cudaHostAllocDefault));
+        TR_CUDA(cudaHostAlloc((void **)&h_fl, sizeof(int) * 4, cudaHostAllocDefault));
+        std::memset(h_fl, 0, sizeof(int) * 4);
 
         reserve_matvec(c, pmax);
         c->Tn.alloc((size_t)pmax * nov, &c->budget, "new vectors");
@@ -347,6 +362,15 @@ struct Dav {
         wsn = c->ws_split.n;
         TR_CUDA(cudaMemsetAsync(c->flag.p, 0, 2 * sizeof(int), st));
     }
+
+    ~Dav()
+    {
+        if (h_rn) cudaFreeHost(h_rn);
+        if (h_th) cudaFreeHost(h_th);
+        if (h_fl) cudaFreeHost(h_fl);
+    }
+    Dav(const Dav &) = delete;
+    Dav &operator=(const Dav &) = delete;
 
     // f(device pointer, first row, rows) for rows [r0, r1) of S; host rows are
     // staged through two device slots on the copy stream
@@ -409,25 +433,24 @@ struct Dav {
         TR_LAUNCH(pf, st, "subspace_insert", 0, 0,
                   h_insert<<<dim3(cdiv(kk, 128), p), 128, 0, st>>>(c->Hs.p, maxsp, A1, A2, p, kk, k0));
     }
-    // orthonormalise rows src[0:p] into dst; returns the count kept (synchronises st)
-    int cholqr(double *src, int p, double *dst, double drop2)
+    // Orthonormalise rows src[0:p] into dst[0:p] without waiting on the host:
+    // Cholesky-QR with dropping (first pass), then again without dropping; rows
+    // past the kept count come out zero.  The kept count lands in h_fl[3] once
+    // the stream reaches the end of this work.
+    void orthonormal_block_async(double *src, int p, double *dst, double *tmp)
     {
         Prof &pf = c->prof;
+        int *cnt = c->idx_dev.p + pmax;
         dgemm(pf, st, "gram", false, true, p, p, (int)nov, 1.0, src, nov, src, nov, 0.0, c->Ss.p, p, Batch(), ws, wsn);
-        TR_LAUNCH(pf, st, "cholqr_coef", 0, 0, cholqr_coef<<<1, 1, 0, st>>>(c->Ss.p, p, drop2, c->Gc.p, c->idx_dev.p + pmax));
-        int keep = 0;
-        TR_CUDA(cudaMemcpyAsync(&keep, c->idx_dev.p + pmax, sizeof(int), cudaMemcpyDeviceToHost, st));
-        TR_CUDA(cudaStreamSynchronize(st));
-        if (keep > 0)
-            dgemm(pf, st, "orth_apply", false, false, keep, (int)nov, p, 1.0, c->Gc.p, p, src, nov, 0.0, dst, nov,
-                  Batch(), nullptr, 0);
-        return keep;
-    }
-    int orthonormal_block(double *src, int p, double *dst, double *tmp)
-    {
-        int k1 = cholqr(src, p, tmp, DROP_NORM * DROP_NORM);
-        if (k1 == 0) return 0;
-        return cholqr(tmp, k1, dst, 0.0);
+        TR_LAUNCH(pf, st, "cholqr_coef", 0, 0,
+                  cholqr_coef<<<1, 1, 0, st>>>(c->Ss.p, p, DROP_NORM * DROP_NORM, c->Gc.p, cnt));
+        dgemm(pf, st, "orth_apply", false, false, p, (int)nov, p, 1.0, c->Gc.p, p, src, nov, 0.0, tmp, nov, Batch(),
+              nullptr, 0);
+        dgemm(pf, st, "gram", false, true, p, p, (int)nov, 1.0, tmp, nov, tmp, nov, 0.0, c->Ss.p, p, Batch(), ws, wsn);
+        TR_LAUNCH(pf, st, "cholqr_coef", 0, 0, cholqr_coef<<<1, 1, 0, st>>>(c->Ss.p, p, 0.0, c->Gc.p, cnt + 1));
+        dgemm(pf, st, "orth_apply", false, false, p, (int)nov, p, 1.0, c->Gc.p, p, tmp, nov, 0.0, dst, nov, Batch(),
+              nullptr, 0);
+        TR_CUDA(cudaMemcpyAsync(h_fl + 2, cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     }
 
     // initial guess: unit vectors on the b0 smallest e_a - e_i (ties: lower index)
@@ -443,17 +466,31 @@ struct Dav {
         TR_CUDA(cudaMemsetAsync(c->Tn.p, 0, sizeof(double) * (size_t)b0 * nov, st));
         TR_LAUNCH(c->prof, st, "set_unit", 0, 0, set_unit_rows<<<cdiv(b0, 64), 64, 0, st>>>(c->Tn.p, c->idx_dev.p, b0, nov));
         pend_k0 = 0;
-        pend_p = b0;
+        pend_p = pend_max = b0;
+        pend_restart = false;
+        pend_counted = true;
     }
     // products of the pending rows by this context's own matvec
     void apply_pending()
     {
         TR_CUDA(cudaEventRecord(ev.e[4], st));
-        matvec(c, pend_p, c->Tn.p, c->Wn.p);
+        matvec(c, pend_max, c->Tn.p, c->Wn.p);
         TR_CUDA(cudaEventRecord(ev.e[5], st));
     }
+    // the kept count of prepare() must be on the host: call after the stream
+    // passed that point (any later synchronisation of st)
     void absorb()
     {
+        if (!pend_counted) {
+            TR_CUDA(cudaStreamSynchronize(st));
+            pend_p = h_fl[3];
+            pend_counted = true;
+            if (pend_p == 0) {
+                TR_REQUIRE(!pend_restart, TR_ECUDA, "solve: restart produced an empty subspace");
+                done = true;  // no new directions: stagnation
+                return;
+            }
+        }
         h_update(pend_k0, pend_p, c->Tn.p, c->Wn.p);
         store_rows(SV, pend_k0, pend_p, c->Tn.p);
         store_rows(SW, pend_k0, pend_p, c->Wn.p);
@@ -482,9 +519,9 @@ struct Dav {
         TR_LAUNCH(pf, st, "residual", 0, 24.0 * n * nov,
                   ritz_resid<<<dim3(nblk, n), 256, 0, st>>>(c->R.p, c->Xr.p, c->theta.p, n, nov, c->part.p));
         TR_LAUNCH(pf, st, "residual", 0, 0, finish_norms<<<cdiv(n, 64), 64, 0, st>>>(c->part.p, nblk, n, c->rn.p));
-        TR_CUDA(cudaMemcpyAsync(rn_h.data(), c->rn.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
-        TR_CUDA(cudaMemcpyAsync(th_h.data(), c->theta.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
-        TR_CUDA(cudaMemcpyAsync(jflag, c->flag.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        TR_CUDA(cudaMemcpyAsync(h_rn, c->rn.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+        TR_CUDA(cudaMemcpyAsync(h_th, c->theta.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+        TR_CUDA(cudaMemcpyAsync(h_fl, c->flag.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         TR_CUDA(cudaEventRecord(ev.e[2], st));
         eig_timed = true;
     }
@@ -496,11 +533,11 @@ struct Dav {
             t_oth += elapsed(ev.e[1], ev.e[2]);
             eig_timed = false;
         }
-        TR_REQUIRE(!jflag[0], TR_ECUDA, "solve: subspace eigensolver did not converge");
-        TR_REQUIRE(!jflag[1], TR_ECUDA, "solve: a tensor-core pipeline wait timed out");
+        TR_REQUIRE(!h_fl[0], TR_ECUDA, "solve: subspace eigensolver did not converge");
+        TR_REQUIRE(!h_fl[1], TR_ECUDA, "solve: a tensor-core pipeline wait timed out");
         unconv.clear();
         for (int r = 0; r < n; ++r)
-            if (!(rn_h[r] < tol)) unconv.push_back(r);
+            if (!(h_rn[r] < tol)) unconv.push_back(r);
         if (unconv.empty()) {
             converged = 1;
             done = true;
@@ -508,23 +545,22 @@ struct Dav {
             done = true;
         }
     }
+    // asynchronous: the new directions (or the restart basis) go to Tn; their
+    // count is read in absorb()
     void prepare()
     {
         Prof &pf = c->prof;
         const int p = (int)unconv.size();
+        pend_counted = false;
         if (k + p > maxsp) {
             // restart from the Ritz vectors; A V is recomputed for them (Sec. 3.3)
-            TR_CUDA(cudaEventRecord(ev.e[0], st));
-            int kk = orthonormal_block(c->Xr.p, n, c->Tn.p, c->Tt.p);
-            TR_CUDA(cudaEventRecord(ev.e[1], st));
-            TR_REQUIRE(kk > 0, TR_ECUDA, "solve: restart produced an empty subspace");
-            t_or += elapsed(ev.e[0], ev.e[1]);
+            orthonormal_block_async(c->Xr.p, n, c->Tn.p, c->Tt.p);
             pend_k0 = 0;
-            pend_p = kk;
+            pend_max = n;
+            pend_restart = true;
             nrestart += 1;
             return;
         }
-        TR_CUDA(cudaEventRecord(ev.e[0], st));
         TR_CUDA(cudaMemcpyAsync(c->idx_dev.p, unconv.data(), sizeof(int) * p, cudaMemcpyHostToDevice, st));
         TR_LAUNCH(pf, st, "precondition", 0, 32.0 * p * nov,
                   precond<<<dim3(nblk, p), 256, 0, st>>>(c->T.p, c->R.p, c->D.p, c->theta.p, c->idx_dev.p, p, nov,
@@ -543,15 +579,10 @@ struct Dav {
                       nov, 1.0, c->T.p, nov, Batch(), nullptr, 0);
             });
         }
-        int pk = orthonormal_block(c->T.p, p, c->Tn.p, c->Tt.p);
-        TR_CUDA(cudaEventRecord(ev.e[1], st));
-        t_or += elapsed(ev.e[0], ev.e[1]);
-        if (pk == 0) {
-            done = true;  // no new directions: stagnation
-            return;
-        }
+        orthonormal_block_async(c->T.p, p, c->Tn.p, c->Tt.p);
         pend_k0 = k;
-        pend_p = pk;
+        pend_max = p;
+        pend_restart = false;
     }
     // outputs: omega, unit-norm sign-fixed X, residual norms
     int output(double *omega, double *Xout, double *resid, int on_device, tr_solve_info *info)
@@ -565,9 +596,9 @@ struct Dav {
         if (Xout) TR_CUDA(cudaMemcpyAsync(Xout, c->Xr.p, sizeof(double) * (size_t)n * nov, kind, st));
         if (resid) {
             if (on_device)
-                TR_CUDA(cudaMemcpyAsync(resid, rn_h.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+                TR_CUDA(cudaMemcpyAsync(resid, h_rn, sizeof(double) * n, cudaMemcpyHostToDevice, st));
             else
-                std::copy(rn_h.begin(), rn_h.end(), resid);
+                std::copy(h_rn, h_rn + n, resid);
         }
         TR_CUDA(cudaStreamSynchronize(st));
         if (c->cst) TR_CUDA(cudaStreamSynchronize(c->cst));
@@ -602,12 +633,13 @@ int solve(tr_ctx *c, double *omega, double *Xout, double *resid, int on_device, 
         TR_CUDA(cudaStreamSynchronize(d.st));
         d.check();
         if (d.done) break;
+        TR_CUDA(cudaEventRecord(d.ev.e[3], d.st));
         d.prepare();
-        if (d.done) break;
         d.apply_pending();
-        d.absorb();
         TR_CUDA(cudaStreamSynchronize(d.st));
+        d.t_or += elapsed(d.ev.e[3], d.ev.e[4]);
         d.t_mv += elapsed(d.ev.e[4], d.ev.e[5]);
+        d.absorb();
     }
     return d.output(omega, Xout, resid, on_device, info);
 }
@@ -639,6 +671,7 @@ struct StepGraph {
 void capture(StepGraph &g, cudaStream_t s0, std::vector<tr_ctx *> &cs, const std::vector<int> &members,
              const std::vector<int> &rows, cudaEvent_t fork, std::vector<cudaEvent_t> &joins)
 {
+    TR_CUDA(cudaStreamSynchronize(s0));  // the previous graph has finished before it is replaced
     g.reset();
     // profiling events cannot live inside the graph
     std::vector<bool> prof_on(cs.size());
@@ -840,3 +873,469 @@ int solve_batch(tr_ctx **ctxs, int nb, double **omega, double **X, double **resi
 }
 
 }  // namespace tr
+
+// ---------------------------------------------------------------- serving runtime
+//
+// Continuous batching of TDA-risp solves as requests arrive: builder threads
+// admit requests strictly in arrival order when their estimated device footprint
+// fits in what the server's budget has left (requests larger than the whole
+// budget are rejected), create each context on a stream of its own and run
+// tr_build, several builds at once; a
+// solver thread keeps every built molecule's tensors and Davidson state resident
+// and advances all of them in lockstep, the products of one step of all of them
+// being one CUDA-graph launch.  Molecules join at the next step after their build
+// and leave when converged, returning their memory to the budget; builds overlap
+// on the device with the solver's steps.
+
+struct tr_server {
+    tr_server_options opt{};
+    int device = 0;
+    size_t budget = 0, in_use = 0;
+    std::mutex mu;
+    std::condition_variable cv_submit, cv_ready, cv_mem, cv_result;
+    struct Req {
+        long long id = 0;
+        std::vector<int> Z;
+        std::vector<double> xyz, aux, C, eps;
+        std::vector<tr_shell> shells;
+        std::vector<std::vector<double>> sexp, scoef;
+        int nao = 0, nmo = 0, nocc = 0, want_x = 0;
+        tr_options o{};
+        double t_submit = 0, t_admit = 0, t_built = 0;
+        size_t foot = 0;
+        tr_ctx *ctx = nullptr;
+        cudaStream_t stream = nullptr;
+    };
+    std::deque<std::unique_ptr<Req>> submitted, ready;
+    std::deque<tr_result> results;
+    long long next_id = 1;
+    long long pop_seq = 0, admit_seq = 0;  // admission turns in arrival order
+    int outstanding = 0;
+    bool stop = false;
+    std::vector<std::thread> builders;
+    std::thread solver;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+
+    double now() const
+    {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace tr {
+namespace {
+
+void release_request(tr_server *S, tr_server::Req *r)
+{
+    if (r->ctx) {
+        cudaStreamSynchronize(r->stream);
+        tr_destroy(r->ctx);
+        r->ctx = nullptr;
+    }
+    if (r->stream) {
+        cudaStreamDestroy(r->stream);
+        r->stream = nullptr;
+    }
+}
+
+void post_result(tr_server *S, tr_result &res)
+{
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->results.push_back(res);
+    S->cv_result.notify_all();
+}
+
+void fail(tr_server *S, tr_server::Req *r, int code, const std::string &msg)
+{
+    tr_result res;
+    std::memset(&res, 0, sizeof res);
+    res.id = r->id;
+    res.status = code;
+    res.t_submit = r->t_submit;
+    res.t_admit = r->t_admit;
+    res.t_built = r->t_built;
+    res.t_done = S->now();
+    std::strncpy(res.error, msg.c_str(), sizeof(res.error) - 1);
+    post_result(S, res);
+}
+
+void builder_loop(tr_server *S)
+{
+    cudaSetDevice(S->device);
+    while (true) {
+        std::unique_ptr<tr_server::Req> r;
+        long long seq = 0;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_submit.wait(lk, [&] { return S->stop || !S->submitted.empty(); });
+            if (S->stop) return;
+            r = std::move(S->submitted.front());
+            S->submitted.pop_front();
+            seq = S->pop_seq++;
+        }
+        int rc = TR_OK;
+        std::string msg;
+        bool turn_taken = false;
+        // waits for this request's admission turn; fits: whether it may take memory
+        auto take_turn = [&](bool fits) -> bool {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_mem.wait(lk, [&] {
+                return S->stop || (S->admit_seq == seq && (!fits || S->in_use + r->foot <= S->budget));
+            });
+            if (S->stop) return false;
+            S->admit_seq += 1;
+            if (fits) S->in_use += r->foot;
+            S->cv_mem.notify_all();
+            turn_taken = true;
+            return true;
+        };
+        try {
+            TR_CUDA(cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking));
+            tr_options o = r->o;
+            o.hbm_budget = S->budget;
+            rc = tr_create(&r->ctx, &o, r->stream);
+            if (rc != TR_OK) throw Error(rc, "server: context creation failed");
+            rc = tr_set_molecule(r->ctx, (int)r->Z.size(), r->Z.data(), r->xyz.data(), r->aux.data(),
+                                 (int)r->shells.size(), r->shells.data());
+            if (rc != TR_OK) throw Error(rc, r->ctx->err);
+            rc = tr_set_orbitals(r->ctx, r->nao, r->nmo, r->nocc, r->C.data(), r->eps.data(), 0);
+            if (rc != TR_OK) throw Error(rc, r->ctx->err);
+            r->foot = footprint(r->ctx);
+            if (r->foot > S->budget)
+                throw Error(TR_ENOMEM, "server: request needs " + std::to_string(r->foot >> 20) +
+                                           " MiB of device memory, the server budget is " +
+                                           std::to_string(S->budget >> 20) + " MiB");
+            if (!take_turn(true)) {
+                release_request(S, r.get());
+                return;
+            }
+            r->t_admit = S->now();
+            r->ctx->budget.limit = r->foot;
+            rc = tr_build(r->ctx);
+            if (rc != TR_OK) {
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->in_use -= r->foot;
+                S->cv_mem.notify_all();
+                throw Error(rc, r->ctx->err);
+            }
+            r->t_built = S->now();
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->ready.push_back(std::move(r));
+            S->cv_ready.notify_all();
+            continue;
+        } catch (const Error &e) {
+            rc = e.code;
+            msg = e.what();
+        } catch (const std::exception &e) {
+            rc = TR_ECUDA;
+            msg = e.what();
+        }
+        if (!turn_taken && !take_turn(false)) {
+            release_request(S, r.get());
+            return;
+        }
+        fail(S, r.get(), rc, msg);
+        release_request(S, r.get());
+    }
+}
+
+void solver_loop(tr_server *S)
+{
+    cudaSetDevice(S->device);
+    struct Member {
+        std::unique_ptr<tr_server::Req> r;
+        std::unique_ptr<Dav> d;
+        bool fresh = true;
+        cudaEvent_t join = nullptr;
+    };
+    std::vector<std::unique_ptr<Member>> act;
+    cudaStream_t s0 = nullptr;
+    cudaEvent_t fork = nullptr, done = nullptr;
+    cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking);
+    cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+    StepGraph g;
+    std::vector<std::pair<tr_ctx *, int>> sig;
+    bool warmed = false;
+
+    auto finish = [&](Member &m, int rc_in, const std::string &msg) {
+        tr_result res;
+        std::memset(&res, 0, sizeof res);
+        res.id = m.r->id;
+        res.t_submit = m.r->t_submit;
+        res.t_admit = m.r->t_admit;
+        res.t_built = m.r->t_built;
+        int rc = rc_in;
+        if (rc == TR_OK && m.d) {
+            try {
+                const int n = m.d->n;
+                res.nstates = n;
+                double *X = nullptr;
+                if (m.r->want_x) {
+                    X = (double *)std::malloc(sizeof(double) * (size_t)n * m.d->nov);
+                    if (!X) throw Error(TR_ENOMEM, "server: host allocation of X failed");
+                }
+                tr_solve_info info;
+                rc = m.d->output(res.omega, X, res.resid, 0, &info);
+                res.X = X;
+                res.niter = info.niter;
+                res.nmatvec = info.nmatvec;
+            } catch (const Error &e) {
+                rc = e.code;
+                std::strncpy(res.error, e.what(), sizeof(res.error) - 1);
+            } catch (const std::exception &e) {
+                rc = TR_ECUDA;
+                std::strncpy(res.error, e.what(), sizeof(res.error) - 1);
+            }
+        } else {
+            std::strncpy(res.error, msg.c_str(), sizeof(res.error) - 1);
+        }
+        res.status = rc;
+        m.d.reset();
+        release_request(S, m.r.get());
+        if (m.join) cudaEventDestroy(m.join);
+        m.join = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->in_use -= m.r->foot;
+            S->cv_mem.notify_all();
+        }
+        res.t_done = S->now();
+        post_result(S, res);
+    };
+
+    while (true) {
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_ready.wait(lk, [&] { return S->stop || !S->ready.empty() || !act.empty(); });
+            if (S->stop && act.empty()) break;
+            while (!S->ready.empty() && (int)act.size() < S->opt.max_active) {
+                std::unique_ptr<Member> m(new Member);
+                m->r = std::move(S->ready.front());
+                S->ready.pop_front();
+                act.push_back(std::move(m));
+            }
+        }
+        if (S->stop) break;
+        // newcomers: Davidson state, guess, kernels loaded before any capture
+        for (auto &mp : act) {
+            Member &m = *mp;
+            if (!m.fresh || m.d) continue;
+            try {
+                m.d.reset(new Dav(m.r->ctx));
+                cudaEventCreateWithFlags(&m.join, cudaEventDisableTiming);
+                std::vector<tr_ctx *> one{m.r->ctx};
+                std::vector<int> rows{m.d->n};
+                if (S->opt.autotune_tiles) autotune(one, rows);
+                if (!warmed || !S->opt.autotune_tiles) matvec(m.r->ctx, m.d->n, m.r->ctx->Tn.p, m.r->ctx->Wn.p);
+                warmed = true;
+                m.d->guess();
+            } catch (const Error &e) {
+                finish(m, e.code, e.what());
+            } catch (const std::exception &e) {
+                finish(m, TR_ECUDA, e.what());
+            }
+        }
+        act.erase(std::remove_if(act.begin(), act.end(), [](const std::unique_ptr<Member> &m) { return !m->r->ctx; }),
+                  act.end());
+        // one step for the members already in flight
+        std::vector<Member *> pend;
+        for (auto &mp : act) {
+            Member &m = *mp;
+            if (m.fresh) {
+                pend.push_back(&m);
+                continue;
+            }
+            try {
+                if (m.d->done)
+                    finish(m, TR_OK, "");  // stagnated in the last absorb
+                else
+                    m.d->eig_async();
+            } catch (const Error &e) {
+                finish(m, e.code, e.what());
+            }
+        }
+        for (auto &mp : act) {
+            Member &m = *mp;
+            if (m.fresh || !m.r->ctx) continue;
+            if (std::find(pend.begin(), pend.end(), &m) != pend.end()) continue;
+            try {
+                TR_CUDA(cudaStreamSynchronize(m.d->st));
+                m.d->check();
+                if (!m.d->done) m.d->prepare();
+                if (m.d->done)
+                    finish(m, TR_OK, "");
+                else
+                    pend.push_back(&m);
+            } catch (const Error &e) {
+                finish(m, e.code, e.what());
+            } catch (const std::exception &e) {
+                finish(m, TR_ECUDA, e.what());
+            }
+        }
+        act.erase(std::remove_if(act.begin(), act.end(), [](const std::unique_ptr<Member> &m) { return !m->r->ctx; }),
+                  act.end());
+        pend.erase(std::remove_if(pend.begin(), pend.end(), [](Member *m) { return !m->r->ctx; }), pend.end());
+        if (pend.empty()) continue;
+        // the products of this step: one graph launch (recorded again when the membership changes)
+        try {
+            std::vector<std::pair<tr_ctx *, int>> key;
+            std::vector<tr_ctx *> cs;
+            std::vector<int> rows, members;
+            std::vector<cudaEvent_t> joins;
+            for (Member *m : pend) {
+                const int rws = m->fresh ? m->d->b0 : m->d->n;
+                key.push_back({m->r->ctx, rws});
+                members.push_back((int)cs.size());
+                cs.push_back(m->r->ctx);
+                rows.push_back(rws);
+                joins.push_back(m->join);
+            }
+            if (!g.exec || key != sig) {
+                capture(g, s0, cs, members, rows, fork, joins);
+                sig = key;
+            }
+            for (Member *m : pend) {
+                TR_CUDA(cudaEventRecord(m->join, m->d->st));
+                TR_CUDA(cudaStreamWaitEvent(s0, m->join, 0));
+            }
+            TR_CUDA(cudaGraphLaunch(g.exec, s0));
+            TR_CUDA(cudaEventRecord(done, s0));
+            for (Member *m : pend) {
+                TR_CUDA(cudaStreamWaitEvent(m->d->st, done, 0));
+                m->d->absorb();
+                m->fresh = false;
+            }
+        } catch (const Error &e) {
+            for (Member *m : pend) finish(*m, e.code, e.what());
+            act.erase(std::remove_if(act.begin(), act.end(), [](const std::unique_ptr<Member> &m) { return !m->r->ctx; }),
+                      act.end());
+            g.reset();
+            sig.clear();
+        }
+    }
+    for (auto &mp : act) finish(*mp, TR_ECUDA, "server: stopped before completion");
+    g.reset();
+    cudaStreamSynchronize(s0);
+    cudaStreamDestroy(s0);
+    cudaEventDestroy(fork);
+    cudaEventDestroy(done);
+}
+
+}  // namespace
+}  // namespace tr
+
+extern "C" {
+
+int tr_server_create(tr_server **out, const tr_server_options *opt)
+{
+    if (!out) return TR_EINVAL;
+    *out = nullptr;
+    tr_server *S = new (std::nothrow) tr_server();
+    if (!S) return TR_ENOMEM;
+    if (opt) S->opt = *opt;
+    if (S->opt.max_active <= 0) S->opt.max_active = 64;
+    if (cudaGetDevice(&S->device) != cudaSuccess) {
+        delete S;
+        return TR_ECUDA;
+    }
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        delete S;
+        return TR_ECUDA;
+    }
+    S->budget = S->opt.hbm_budget ? S->opt.hbm_budget : (size_t)(0.9 * (double)fr);
+    if (S->opt.build_threads <= 0) S->opt.build_threads = 4;
+    for (int t = 0; t < S->opt.build_threads; ++t) S->builders.emplace_back(tr::builder_loop, S);
+    S->solver = std::thread(tr::solver_loop, S);
+    *out = S;
+    return TR_OK;
+}
+
+int tr_server_submit(tr_server *S, const tr_request *q, long long *id)
+{
+    if (!S || !q || !q->Z || !q->xyz || !q->aux_exp || !q->shells || !q->C || !q->eps) return TR_EINVAL;
+    if (q->natm <= 0 || q->nshell <= 0 || q->nao <= 0 || q->nmo <= 0 || q->nocc <= 0) return TR_EINVAL;
+    std::unique_ptr<tr_server::Req> r(new tr_server::Req);
+    r->Z.assign(q->Z, q->Z + q->natm);
+    r->xyz.assign(q->xyz, q->xyz + 3 * q->natm);
+    r->aux.assign(q->aux_exp, q->aux_exp + q->natm);
+    r->sexp.resize(q->nshell);
+    r->scoef.resize(q->nshell);
+    for (int s = 0; s < q->nshell; ++s) {
+        const tr_shell &sh = q->shells[s];
+        if (sh.nprim < 1 || sh.nprim > 16 || !sh.exp || !sh.coef) return TR_EINVAL;
+        r->sexp[s].assign(sh.exp, sh.exp + sh.nprim);
+        r->scoef[s].assign(sh.coef, sh.coef + sh.nprim);
+        tr_shell c = sh;
+        c.exp = r->sexp[s].data();
+        c.coef = r->scoef[s].data();
+        r->shells.push_back(c);
+    }
+    r->nao = q->nao;
+    r->nmo = q->nmo;
+    r->nocc = q->nocc;
+    r->C.assign(q->C, q->C + (size_t)q->nao * q->nmo);
+    r->eps.assign(q->eps, q->eps + q->nmo);
+    r->o = q->opt;
+    r->want_x = q->want_x;
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->id = S->next_id++;
+    r->t_submit = S->now();
+    if (id) *id = r->id;
+    S->outstanding += 1;
+    S->submitted.push_back(std::move(r));
+    S->cv_submit.notify_all();
+    return TR_OK;
+}
+
+int tr_server_poll(tr_server *S, tr_result *out, int max, int timeout_ms)
+{
+    if (!S || (!out && max > 0)) return TR_EINVAL;
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (S->results.empty() && timeout_ms != 0) {
+        if (timeout_ms < 0)
+            S->cv_result.wait(lk, [&] { return !S->results.empty() || S->outstanding == 0; });
+        else
+            S->cv_result.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return !S->results.empty(); });
+    }
+    int n = 0;
+    while (n < max && !S->results.empty()) {
+        out[n++] = S->results.front();
+        S->results.pop_front();
+        S->outstanding -= 1;
+    }
+    return n;
+}
+
+int tr_server_outstanding(tr_server *S)
+{
+    if (!S) return TR_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    return S->outstanding;
+}
+
+double tr_server_clock(tr_server *S) { return S ? S->now() : 0.0; }
+
+void tr_server_destroy(tr_server *S)
+{
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        S->cv_submit.notify_all();
+        S->cv_ready.notify_all();
+        S->cv_mem.notify_all();
+    }
+    for (auto &t : S->builders)
+        if (t.joinable()) t.join();
+    if (S->solver.joinable()) S->solver.join();
+    for (auto &r : S->submitted) tr::release_request(S, r.get());
+    for (auto &r : S->ready) tr::release_request(S, r.get());
+    for (auto &res : S->results) std::free(res.X);
+    delete S;
+}
+
+void tr_free(void *p) { std::free(p); }
+
+}  // extern "C"

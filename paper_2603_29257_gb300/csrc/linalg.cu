@@ -461,14 +461,23 @@ void jacobi_eigh(Prof &prof, cudaStream_t st, double *H, int k, double *w, doubl
                  int *flag)
 {
     if (k <= 0) return;
-    static int nsm = 0, per_sm = 0;
-    if (!nsm) {
-        int dev = 0;
-        TR_CUDA(cudaGetDevice(&dev));
-        TR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop, JACOBI_THREADS, 0));
-        TR_REQUIRE(per_sm >= 1, TR_ECUDA, "jacobi: kernel cannot be resident");
-    }
+    // device limits, looked up once (thread-safe static initialisation)
+    struct Lim {
+        int nsm = 0, per_sm = 0;
+        cudaError_t err = cudaSuccess;
+        Lim()
+        {
+            int dev = 0;
+            err = cudaGetDevice(&dev);
+            if (err == cudaSuccess) err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            if (err == cudaSuccess)
+                err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop, JACOBI_THREADS, 0);
+        }
+    };
+    static const Lim lim;
+    TR_CUDA(lim.err);
+    const int nsm = lim.nsm, per_sm = lim.per_sm;
+    TR_REQUIRE(per_sm >= 1, TR_ECUDA, "jacobi: kernel cannot be resident");
     const int np = (k + (k & 1)) / 2;
     int G = std::min(np, nsm * per_sm);
     G = std::max(G, (np + JACOBI_MAX_PAIRS_PER_BLOCK - 1) / JACOBI_MAX_PAIRS_PER_BLOCK);

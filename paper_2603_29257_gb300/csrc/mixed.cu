@@ -143,7 +143,7 @@ void reserve_mixed(tr_ctx *c, int mb)
         c->Xw_h.alloc((size_t)mb * oK * vKp, &c->budget, "K workspace");
         c->Xw_l.alloc((size_t)mb * oK * vKp, &c->budget, "K workspace");
         const size_t perP = (size_t)mb * vK * oKp * 2 * sizeof(float);
-        int npk = (int)std::max<size_t>(1, ((size_t)4 << 30) / perP);
+        int npk = (int)std::max<size_t>(1, c->opt.matvec_ws_bytes / perP);
         npk = std::min(npk, nK);
         npk = std::min(npk, 65535 / mb);
         c->mixed_npk = npk;

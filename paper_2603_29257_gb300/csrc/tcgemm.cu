@@ -303,12 +303,10 @@ void launch(cudaStream_t st, dim3 grid, const TcMat &A, const TcMat &B, const Tc
 {
     constexpr int STAGES = NSPLIT == 3 ? (BN == 64 ? 4 : 3) : 4;
     const size_t smem = (size_t)STAGES * stage_bytes<NSPLIT, STAGES, BN>() + 1024 + 256;
-    static bool attr = false;
-    if (!attr) {
-        TR_CUDA(cudaFuncSetAttribute(tc_kernel<NSPLIT, MODE, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-        attr = true;
-    }
+    // set once per kernel instance (thread-safe static initialisation)
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(tc_kernel<NSPLIT, MODE, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    TR_CUDA(attr);
     const CUtensorMap &bh = BN == 64 ? B.mhi64 : B.mhi;
     const CUtensorMap &bl = BN == 64 ? B.mlo64 : B.mlo;
     tc_kernel<NSPLIT, MODE, BN><<<grid, 128, smem, st>>>(A.mhi, NSPLIT == 3 ? A.mlo : A.mhi, bh, NSPLIT == 3 ? bl : bh, g);

@@ -454,9 +454,44 @@ static int matvec_pchunk(tr_ctx *c, int mb)
 {
     if (!c->k_active) return 0;
     size_t perP = (size_t)mb * c->oK * c->vK;
-    size_t cap = std::max<size_t>(perP, ((size_t)4 << 30) / sizeof(double));
+    size_t cap = std::max<size_t>(perP, c->opt.matvec_ws_bytes / sizeof(double));
     int npk = (int)std::min<size_t>(c->nK, std::max<size_t>(1, cap / perP));
     return std::min(npk, 65535 / mb);
+}
+
+// Estimated peak device bytes of build + solve for the current sizes and options.
+size_t footprint(tr_ctx *c)
+{
+    const double d = 8.0, f = 4.0;
+    const double nao = c->nao, nmo = c->nmo, nocc = c->nocc, nov = (double)c->nov;
+    const double nJ = c->nJ, oK = c->oK, vK = c->vK;
+    const double nK = (c->nK > 0 && c->oK > 0 && c->vK > 0 && c->opt.cx != 0.0) ? c->nK : 0;
+    const bool mixed = c->opt.precision == TR_MIXED;
+    const double base = d * (nao * nmo + nmo + nov) + d * (nJ * nJ + nK * nK) + 128.0 * (1 << 20) +
+                        (double)c->shells_h.size() * 64 + (double)c->pl.pairs.size() * 8;
+    // build: integral and half-transform chunks, FP64 tensors
+    const double hrows = std::max(nocc, std::max(oK, vK));
+    const double per = d * (nao * nao + hrows * nao);
+    const double npc = std::max(1.0, std::min(std::floor((double)c->opt.aux_chunk_bytes / per), std::max(nJ, nK)));
+    const double t64 = d * (nJ * nov + nK * vK * vK + 2.0 * nK * oK * oK);
+    const double oKp = std::ceil(std::max(oK, 1.0) / 32) * 32, vKp = std::ceil(std::max(vK, 1.0) / 32) * 32;
+    const double t32 = mixed ? f * (nJ * nov + 2.0 * nK * vK * vKp + 2.0 * oK * nK * oKp) : 0.0;
+    const double build_peak = npc * per + t64 + t32;
+    // solve: tensors kept, Davidson storage and product workspaces
+    const double kept = mixed ? t32 + d * oK * nK * oK : t64 - d * nK * oK * oK;
+    const int n = (int)std::min<double>(c->opt.nstates, nov);
+    const int b0 = (int)std::min<double>(std::max(c->opt.block > 0 ? c->opt.block : 2 * n, n), nov);
+    int maxsp = c->opt.max_space > 0 ? c->opt.max_space : 20 * n;
+    maxsp = (int)std::min<double>(std::max(maxsp, b0 + n), std::max(nov, (double)b0));
+    const double pmax = std::max(b0, n);
+    const double mb = std::min<double>(pmax, c->mblk);
+    const double dav = d * nov * (2.0 * maxsp + 4.0 * pmax + 2.0 * n) + d * (5.0 * maxsp * maxsp + 2.0 * maxsp * pmax);
+    const double mws = nK > 0 ? std::min<double>((double)c->opt.matvec_ws_bytes, d * mb * nK * oK * vK) +
+                                    (mixed ? 2.0 * f * mb * oK * vKp + f * mb * nov : d * mb * oK * vK)
+                              : 0.0;
+    const double ws = d * 16.0 * (1 << 20) + 2.0 * d * std::max(nJ, 1.0) * mb + mws;
+    const double solve_peak = kept + dav + ws;
+    return (size_t)(1.1 * (base + std::max(build_peak, solve_peak + (mixed ? 0.0 : 0.0))));
 }
 
 void reserve_matvec(tr_ctx *c, int m)

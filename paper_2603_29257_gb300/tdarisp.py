@@ -33,7 +33,7 @@ class Options(ct.Structure):
                 ("max_iter", ct.c_int), ("tol", ct.c_double), ("precision", ct.c_int),
                 ("screen", ct.c_double), ("hbm_budget", ct.c_size_t),
                 ("aux_chunk_bytes", ct.c_size_t), ("host_budget", ct.c_size_t),
-                ("dav_dev_rows", ct.c_int)]
+                ("dav_dev_rows", ct.c_int), ("matvec_ws_bytes", ct.c_size_t)]
 
 
 class Dims(ct.Structure):
@@ -51,6 +51,25 @@ class SolveInfo(ct.Structure):
 class ProfEntry(ct.Structure):
     _fields_ = [("name", ct.c_char * 32), ("launches", ct.c_long), ("total_ms", ct.c_double),
                 ("flops", ct.c_double), ("bytes", ct.c_double)]
+
+
+class ServerOptions(ct.Structure):
+    _fields_ = [("max_active", ct.c_int), ("hbm_budget", ct.c_size_t), ("autotune_tiles", ct.c_int),
+                ("build_threads", ct.c_int)]
+
+
+class Request(ct.Structure):
+    _fields_ = [("natm", ct.c_int), ("Z", _ip), ("xyz", _dp), ("aux_exp", _dp), ("nshell", ct.c_int),
+                ("shells", ct.POINTER(Shell)), ("nao", ct.c_int), ("nmo", ct.c_int), ("nocc", ct.c_int),
+                ("C", _dp), ("eps", _dp), ("opt", Options), ("want_x", ct.c_int)]
+
+
+class Result(ct.Structure):
+    _fields_ = [("id", ct.c_longlong), ("status", ct.c_int), ("nstates", ct.c_int),
+                ("omega", ct.c_double * 64), ("resid", ct.c_double * 64), ("X", _dp),
+                ("t_submit", ct.c_double), ("t_admit", ct.c_double), ("t_built", ct.c_double),
+                ("t_done", ct.c_double), ("niter", ct.c_int), ("nmatvec", ct.c_int),
+                ("error", ct.c_char * 160)]
 
 
 # name -> (restype, argtypes); the full C ABI of include/tdarisp.h
@@ -72,12 +91,22 @@ SIGNATURES = {
     "tr_matvec_noalloc": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p]),
     "tr_solve": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int,
                             ct.POINTER(SolveInfo)]),
+    "tr_build_batch": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.c_int, ct.c_int]),
     "tr_solve_batch": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.c_int, ct.POINTER(ct.c_void_p),
                                   ct.POINTER(ct.c_void_p), ct.POINTER(ct.c_void_p), ct.c_int,
                                   ct.POINTER(SolveInfo), ct.c_int]),
+    "tr_server_create": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.POINTER(ServerOptions)]),
+    "tr_server_submit": (ct.c_int, [ct.c_void_p, ct.POINTER(Request), ct.POINTER(ct.c_longlong)]),
+    "tr_server_poll": (ct.c_int, [ct.c_void_p, ct.POINTER(Result), ct.c_int, ct.c_int]),
+    "tr_server_outstanding": (ct.c_int, [ct.c_void_p]),
+    "tr_server_clock": (ct.c_double, [ct.c_void_p]),
+    "tr_server_destroy": (None, [ct.c_void_p]),
+    "tr_free": (None, [ct.c_void_p]),
     "tr_profile": (ct.c_int, [ct.c_void_p, ct.c_int]),
     "tr_profile_get": (ct.c_int, [ct.c_void_p, ct.POINTER(ProfEntry), ct.c_int]),
     "tr_launch_count": (ct.c_long, [ct.c_void_p]),
+    "tr_memory": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_size_t), ct.POINTER(ct.c_size_t),
+                             ct.POINTER(ct.c_size_t)]),
 }
 
 _lib = None
@@ -97,6 +126,16 @@ def lib():
             f.argtypes = args
         _lib = L
     return _lib
+
+
+def build_batch(contexts, nthreads=8):
+    """tr_build of several contexts concurrently (tr_build_batch)."""
+    n = len(contexts)
+    hs = (ct.c_void_p * n)(*[c._h for c in contexts])
+    rc = lib().tr_build_batch(hs, n, nthreads)
+    if rc != TR_OK:
+        msgs = [lib().tr_last_error(c._h).decode() for c in contexts]
+        raise TDARispError(rc, "tr_build_batch: " + "; ".join(m for m in msgs if m))
 
 
 def solve_batch(contexts, autotune=True):
@@ -318,5 +357,99 @@ class Context:
                                            flops=arr[i].flops, bytes=arr[i].bytes)
                 for i in range(n)}
 
+    def memory(self):
+        """(bytes held, peak bytes, estimated peak of build + solve)."""
+        u, p, e = ct.c_size_t(), ct.c_size_t(), ct.c_size_t()
+        self._check(lib().tr_memory(self._h, ct.byref(u), ct.byref(p), ct.byref(e)), "tr_memory")
+        return u.value, p.value, e.value
+
     def launch_count(self) -> int:
         return int(lib().tr_launch_count(self._h))
+
+
+class Server:
+    """Continuous-batching server (tr_server_*): submit molecules as they arrive,
+    poll results.  Each result is a dict with omega, resid, X (if requested),
+    status, times on the server clock, niter and nmatvec."""
+
+    def __init__(self, max_active=64, hbm_budget=0, autotune=True, build_threads=4):
+        o = ServerOptions(max_active, hbm_budget, 1 if autotune else 0, build_threads)
+        h = ct.c_void_p()
+        rc = lib().tr_server_create(ct.byref(h), ct.byref(o))
+        if rc != TR_OK:
+            raise TDARispError(rc, "tr_server_create failed")
+        self._h = h
+        self._shapes = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tr_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def clock(self):
+        return lib().tr_server_clock(self._h)
+
+    def submit(self, mol, want_x=False, **options):
+        """Queue a molecule (Z, xyz, aux_exp, shells, C, eps, nocc); returns its id."""
+        Zc = np.ascontiguousarray(mol.Z, dtype=np.int32)
+        X = _f64(mol.xyz).reshape(-1, 3)
+        ae = _f64(mol.aux_exp)
+        arr = (Shell * len(mol.shells))()
+        keep = [Zc, X, ae]
+        for k, sh in enumerate(mol.shells):
+            e, c = _f64(sh.exps), _f64(sh.coefs)
+            keep += [e, c]
+            arr[k] = Shell(int(sh.atom), int(sh.l), len(e), _ptr(e), _ptr(c))
+        C, eps = _f64(mol.C), _f64(mol.eps)
+        keep += [C, eps]
+        q = Request(len(Zc), Zc.ctypes.data_as(_ip), _ptr(X), _ptr(ae), len(mol.shells), arr,
+                    C.shape[0], C.shape[1], int(mol.nocc), _ptr(C), _ptr(eps),
+                    default_options(**options), 1 if want_x else 0)
+        rid = ct.c_longlong()
+        rc = lib().tr_server_submit(self._h, ct.byref(q), ct.byref(rid))
+        if rc != TR_OK:
+            raise TDARispError(rc, "tr_server_submit failed")
+        self._shapes[rid.value] = (int(mol.nocc), C.shape[1] - int(mol.nocc))
+        return rid.value
+
+    def poll(self, max_results=64, timeout_ms=-1):
+        buf = (Result * max_results)()
+        n = lib().tr_server_poll(self._h, buf, max_results, timeout_ms)
+        if n < 0:
+            raise TDARispError(n, "tr_server_poll failed")
+        out = []
+        for i in range(n):
+            r = buf[i]
+            k = r.nstates
+            d = dict(id=r.id, status=r.status, nstates=k, omega=np.array(r.omega[:k]),
+                     resid=np.array(r.resid[:k]), t_submit=r.t_submit, t_admit=r.t_admit,
+                     t_built=r.t_built, t_done=r.t_done, niter=r.niter, nmatvec=r.nmatvec,
+                     error=r.error.decode(errors="replace"), X=None)
+            if r.X:
+                nocc, nvir = self._shapes.get(r.id, (0, 0))
+                d["X"] = np.ctypeslib.as_array(r.X, shape=(k * nocc * nvir,)).copy().reshape(k, nocc, nvir)
+                lib().tr_free(ct.cast(r.X, ct.c_void_p))
+            out.append(d)
+        return out
+
+    def outstanding(self):
+        return lib().tr_server_outstanding(self._h)
+
+    def drain(self, timeout_ms=-1):
+        """Results of everything outstanding."""
+        out = []
+        while self.outstanding() > 0:
+            got = self.poll(timeout_ms=timeout_ms)
+            if not got and timeout_ms >= 0:
+                break
+            out += got
+        return out

@@ -54,6 +54,7 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     from paper_2603_29257_gb300 import tdarisp
     assert lib.tr_create(None, None, None) == tdarisp.TR_EINVAL
     assert lib.tr_build(None) == tdarisp.TR_EINVAL
+    assert lib.tr_build_batch(None, 0, 0) == tdarisp.TR_EINVAL
     assert lib.tr_matvec(None, 1, None, None, 0) == tdarisp.TR_EINVAL
     lib.tr_destroy(None)
     assert lib.tr_last_error(None) == b"null context"

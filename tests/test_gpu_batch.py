@@ -56,3 +56,23 @@ def test_batch_equals_alone_and_oracle(mols, precision, tol_alone, tol_ref, auto
         assert np.abs(om - om1).max() < tol_alone, (k, np.abs(om - om1).max())
         ov = np.abs(np.einsum("kia,kia->k", X, X1))
         assert np.all(ov > 1 - 1e-6), (k, ov)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_concurrent_builds_equal_sequential(mols, precision):
+    """tr_build_batch (host threads, a stream per context) gives the tensors and
+    the solves of contexts built one by one."""
+    from paper_2603_29257_gb300 import tdarisp
+    seq = _ctxs(mols, precision)
+    par = []
+    for k, (m, _) in enumerate(mols):
+        c = tdarisp.Context(nstates=6 - (k % 2), tol=1e-7, cx=0.25, precision=precision)
+        c.set_molecule_from(m)
+        par.append(c)
+    tdarisp.build_batch(par, nthreads=3)
+    for a, b in zip(seq, par):
+        for w in range(4):
+            ta, tb = a.tensor(w), b.tensor(w)
+            assert ta.shape == tb.shape
+            assert np.array_equal(ta, tb), w
+        assert np.array_equal(a.solve()[0], b.solve()[0])

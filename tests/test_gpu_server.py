@@ -1,0 +1,84 @@
+"""Serving runtime: requests arriving while others are on the GPU are admitted by
+device footprint, batched continuously, and each result equals the molecule
+solved alone (and the oracle)."""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+import pytest
+
+from oracle import tda
+from paper_2603_29257_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mols():
+    out = []
+    for k, (nh, nH) in enumerate([(3, 3), (6, 5), (2, 4), (8, 6), (4, 4), (5, 0)]):
+        m = synth.make_molecule(seed=700 + k, n_heavy=nh, n_h=nH)
+        f = tda.build(m.Z, m.xyz, m.shells, m.aux_exp, m.C, m.eps, m.nocc, 0.25)
+        out.append((m, np.linalg.eigvalsh(tda.explicit_A(f))[:8]))
+    return out
+
+
+def _lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_29257_gb300 import tdarisp
+    torch.zeros(1, device="cuda")
+    return tdarisp
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-9)])
+def test_results_alone_and_in_the_mix(mols, precision, tol):
+    tdarisp = _lib()
+    opts = lambda k: dict(nstates=4 + (k % 3), tol=1e-7, cx=0.25, precision=precision)
+    with tdarisp.Server(max_active=3, autotune=False) as srv:
+        ids = {}
+        for k, (m, _) in enumerate(mols):
+            ids[srv.submit(m, want_x=True, **opts(k))] = k
+            time.sleep(0.01 * (k % 2))   # staggered arrivals while others run
+        res = srv.drain()
+    assert len(res) == len(mols)
+    for r in res:
+        k = ids[r["id"]]
+        m, w = mols[k]
+        assert r["status"] == 0, r["error"]
+        assert r["t_submit"] <= r["t_admit"] <= r["t_built"] <= r["t_done"]
+        n = r["nstates"]
+        assert np.abs(r["omega"] - w[:n]).max() < (1e-8 if precision == 0 else 1e-5)
+        c = tdarisp.Context(**opts(k))
+        c.set_molecule_from(m)
+        c.build()
+        om, X, rs, info = c.solve()
+        assert np.abs(r["omega"] - om).max() < tol, (k, np.abs(r["omega"] - om).max())
+        ov = np.abs(np.einsum("kia,kia->k", r["X"], X))
+        assert np.all(ov > 1 - 1e-6)
+
+
+def test_admission_by_footprint_and_rejection(mols):
+    tdarisp = _lib()
+    m0 = mols[0][0]
+    c = tdarisp.Context(nstates=4, tol=1e-7)
+    c.set_molecule_from(m0)
+    est = c.memory()[2]
+    c.build()
+    c.solve()
+    assert c.memory()[1] <= est, (c.memory(), est)   # the estimate bounds the real peak
+    # room for about one molecule at a time: the others wait for memory
+    with tdarisp.Server(max_active=8, hbm_budget=int(est * 1.5), autotune=False) as srv:
+        for _ in range(3):
+            srv.submit(m0, nstates=4, tol=1e-7)
+        big = synth.make_molecule(seed=99, n_heavy=80, n_h=40)
+        bid = srv.submit(big, nstates=4, tol=1e-7)
+        res = {r["id"]: r for r in srv.drain()}
+    assert res[bid]["status"] == -2 and "budget" in res[bid]["error"]
+    ok = sorted((r for r in res.values() if r["id"] != bid), key=lambda r: r["t_admit"])
+    assert all(r["status"] == 0 for r in ok)
+    # one at a time: each admission waits for the previous molecule to finish
+    for a, b in zip(ok, ok[1:]):
+        assert b["t_admit"] >= a["t_done"] - 1e-3

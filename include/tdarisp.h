@@ -90,6 +90,9 @@ typedef struct {
     int dav_dev_rows;    /* cap on Davidson vectors kept on the device (0: as many as the
                             HBM budget allows); rows beyond it live in pinned host memory */
     size_t matvec_ws_bytes; /* scratch for the exchange intermediate M (0: 4 GiB) */
+    int xform_slices;    /* MO transforms: -1 FP64 pipe; 2..7 bf16 tensor cores with that many
+                            Ozaki slices per operand (7 + 8 (S-1) bits below each row's
+                            largest element); 0: FP64 pipe in TR_FP64, 5 slices in TR_MIXED */
 } tr_options;
 
 typedef struct {

@@ -77,6 +77,9 @@ int tr_create(tr_ctx **out, const tr_options *opt, void *cuda_stream)
     int rc = guarded(c, [&]() {
         TR_REQUIRE(opt->precision == TR_FP64 || opt->precision == TR_MIXED, TR_EINVAL,
                    "create: precision must be TR_FP64 or TR_MIXED");
+        TR_REQUIRE(opt->xform_slices == 0 || opt->xform_slices == -1 ||
+                       (opt->xform_slices >= 2 && opt->xform_slices <= 7),
+                   TR_EINVAL, "create: xform_slices must be -1, 0 or 2..7");
         c->opt = *opt;
         normalise_options(&c->opt);
         c->st = (cudaStream_t)cuda_stream;
@@ -104,10 +107,13 @@ int tr_set_options(tr_ctx *ctx, const tr_options *opt)
         TR_REQUIRE(opt, TR_EINVAL, "set_options: null options");
         TR_REQUIRE(opt->precision == TR_FP64 || opt->precision == TR_MIXED, TR_EINVAL,
                    "set_options: precision must be TR_FP64 or TR_MIXED");
+        TR_REQUIRE(opt->xform_slices == 0 || opt->xform_slices == -1 ||
+                       (opt->xform_slices >= 2 && opt->xform_slices <= 7),
+                   TR_EINVAL, "set_options: xform_slices must be -1, 0 or 2..7");
         bool rebuild = opt->precision != ctx->opt.precision || opt->cx != ctx->opt.cx || opt->k_alpha != ctx->opt.k_alpha ||
                        opt->k_beta != ctx->opt.k_beta || opt->omega != ctx->opt.omega ||
                        opt->window_ev != ctx->opt.window_ev || opt->aux_on_h != ctx->opt.aux_on_h ||
-                       opt->screen != ctx->opt.screen;
+                       opt->screen != ctx->opt.screen || opt->xform_slices != ctx->opt.xform_slices;
         size_t limit = ctx->budget.limit;
         ctx->opt = *opt;
         normalise_options(&ctx->opt);

@@ -100,6 +100,8 @@ void matvec(tr_ctx *c, int m, const double *X, double *AX);
 // allocate the matvec workspaces for blocks of up to m vectors
 void reserve_matvec(tr_ctx *c, int m);
 // estimated peak device bytes of tr_build + tr_solve
+// slices of the tensor-core MO transforms (0: FP64 pipe)
+int xform_slices(const tr_ctx *c);
 size_t footprint(tr_ctx *c);
 // three-centre integrals of aux functions [p0, p0+np) of set which (0 = J, 1 = K)
 void compute_int3c_chunk(tr_ctx *c, int which, int p0, int np, double *out);

@@ -1,0 +1,422 @@
+// FP64 GEMM by the Ozaki splitting scheme on tcgen05 (sm_103a), kind::f16
+// with bf16 operands and FP32 accumulators in tensor memory.
+//
+// Splitting (per row r, exponent e = the row's largest binary exponent):
+// Y = round(x * 2^(7 + 8(S-1) - e)) is an integer with |Y| <= 2^(7+8(S-1));
+// its balanced base-256 digits q_0 (most significant) .. q_{S-1} lie in
+// [-128, 128] and are exact in bf16.  All of it is integer arithmetic on the
+// FP64 bit pattern.
+//
+// Product: with A and B split the same way,
+//   sum_k a_mk b_nk ~= 2^(eA_m + eB_n - 14) * sum_{d<S} 2^(-8d) P_d,
+//   P_d = sum_k sum_{s+t=d} qA_s qB_t         (the terms s + t >= S are dropped).
+// Each digit product is at most 2^14 in magnitude, so a chunk of K with
+// (d+1) * kc <= 1024 sums P_d exactly in FP32 (every partial sum is an integer
+// below 2^24).  The kernel keeps one FP32 accumulator per diagonal d in tensor
+// memory, and after each chunk adds the S exact chunk sums (times 2^(-8d)) into
+// a double-FP32 (hi, lo) pair per output by error-free two-sums.
+//
+// CTA: 10 warps, a 128 x 64 output tile.  Warp 0 (one lane) streams the
+// slices of 128 A rows and 64 B rows for one K block of 32 per stage with TMA
+// (boxes of 64 bf16 = two slices, 128-byte swizzle) into a ring of shared
+// memory; warp 1 (one lane) issues the S(S+1)/2 slice products per stage as
+// tcgen05.mma (M = 128, N = 64, K = 16) into the S accumulators; warps 2..9
+// drain the accumulators after each chunk (warp w reads TMEM lanes
+// 32 (w mod 4) .. +31, half of the columns) and write the scaled FP64 tile at
+// the end.  With S <= 4 the accumulators are double-buffered, so that draining
+// one chunk overlaps the products of the next.  Every wait is bounded: a timeout records an
+// error code in *err and the CTA goes to its teardown, which waits (bounded)
+// for its own copies in flight and always frees tensor memory.
+#include "ozgemm.cuh"
+#include "tcptx.cuh"
+
+#include <algorithm>
+
+namespace tr {
+namespace {
+
+using namespace ptx;
+
+template <int S, int BN>
+struct OzCfg {
+    static constexpr int SP = (S + 1) & ~1;            // slices per K block, padded to even
+    static constexpr int NBOX = SP / 2;                // TMA boxes per operand per stage
+    static constexpr int ABOX = 128 * 128;             // bytes: 128 rows x 128 B
+    static constexpr int BBOX = BN * 128;
+    static constexpr int STAGE = NBOX * (ABOX + BBOX);
+    static constexpr int STAGES = 4 * STAGE <= 216 * 1024 ? 4 : 3 * STAGE <= 216 * 1024 ? 3 : 2;
+    static constexpr int CK = 1024 / S / 32;           // K blocks per exactly summed chunk
+    static constexpr int NC = BN / 2;                  // output columns per epilogue warp
+    static constexpr int NBUF = 2 * S * BN <= 512 ? 2 : 1;  // accumulator sets in tensor memory
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024 + 256;
+    static_assert(S >= 2 && S <= OZ_MAX_SLICES, "slices");
+    static_assert(S * BN <= 512, "tensor memory holds S accumulators of BN columns");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
+    static_assert(CK >= 1, "chunk");
+};
+
+struct OzArgs {
+    int M, N, nkb;
+    long long a0, a1, c0, c1;
+    long long rowsA, rowsB;
+    const int *eA, *eB;
+    double *d;
+    long long s1, ldm, ldn;
+    double alpha;
+    int *err;
+};
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                 "l"(a), "l"(b), "r"(idesc), "r"(acc)
+                 : "memory");
+}
+
+// (hi, lo) += b with Knuth's error-free two-sum of hi and b (round-to-nearest
+// intrinsics: no contraction or reassociation)
+__device__ __forceinline__ void two_sum(float &hi, float &lo, float b)
+{
+    const float s = __fadd_rn(hi, b);
+    const float bp = __fsub_rn(s, hi);
+    const float ap = __fsub_rn(s, bp);
+    const float err = __fadd_rn(__fsub_rn(hi, ap), __fsub_rn(b, bp));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+}
+
+template <int S, int BN>
+__global__ void __launch_bounds__(320, 1)
+    oz_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, const OzArgs g)
+{
+    using C = OzCfg<S, BN>;
+    constexpr int ST = C::STAGES;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // barriers: full[ST], empty[ST], acc_full[NBUF], acc_empty[NBUF]
+    uint64_t *bars = (uint64_t *)(smem + ST * C::STAGE);
+    uint32_t *tslot = (uint32_t *)(bars + 2 * ST + 2 * C::NBUF);
+    const uint32_t FULL = sa(&bars[0]), EMPTY = sa(&bars[ST]);
+    const uint32_t ACCF = sa(&bars[2 * ST]), ACCE = sa(&bars[2 * ST + C::NBUF]);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * 128, n0 = blockIdx.x * BN;
+    const int b = blockIdx.z;
+    const long long arow = g.a0 + g.a1 * b + m0;
+    const long long brow = g.c0 + g.c1 * b + n0;
+    const int nkb = g.nkb;
+    const int nch = (nkb + C::CK - 1) / C::CK;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2 * ST + C::NBUF; ++i) bar_init(sa(&bars[i]), 1);
+        for (int i = 0; i < C::NBUF; ++i) bar_init(ACCE + 8 * i, 8);  // one arrival per epilogue warp
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(tslot)), "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kt = 0; kt < nkb; ++kt) {
+                const int s = kt % ST;
+                if (kt >= ST && !bar_wait(EMPTY + 8 * s, ((kt / ST) - 1) & 1, g.err, 11)) break;
+                const uint32_t full = FULL + 8 * s;
+                bar_expect(full, C::STAGE);
+                uint8_t *stg = smem + s * C::STAGE;
+                const int x0 = kt * C::SP * 32;
+#pragma unroll
+                for (int j = 0; j < C::NBOX; ++j) {
+                    tma2d(sa(stg + j * C::ABOX), &tA, x0 + 64 * j, (int)arow, full);
+                    tma2d(sa(stg + C::NBOX * C::ABOX + j * C::BBOX), &tB, x0 + 64 * j, (int)brow, full);
+                }
+                issued = kt + 1;
+            }
+            // copies still in flight complete before the CTA ends
+            for (int kt = std::max(0, issued - ST); kt < issued; ++kt)
+                bar_wait(FULL + 8 * (kt % ST), (kt / ST) & 1, g.err, 15);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // kind::f16 instruction descriptor: FP32 accumulator, bf16 A and B, both
+            // K-major, N = BN, M = 128
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                   ((uint32_t)(128 >> 4) << 24);
+            for (int kt = 0; kt < nkb; ++kt) {
+                const int s = kt % ST, kc = kt % C::CK, ch = kt / C::CK, buf = ch % C::NBUF;
+                if (kc == 0 && ch >= C::NBUF) {
+                    // the epilogue has drained the chunk that last used this accumulator set
+                    if (!bar_wait(ACCE + 8 * buf, ((ch / C::NBUF) - 1) & 1, g.err, 12)) break;
+                    fence_after();
+                }
+                if (!bar_wait(FULL + 8 * s, (kt / ST) & 1, g.err, 13)) break;
+                fence_after();
+                uint8_t *stg = smem + s * C::STAGE;
+                const uint32_t abase = sa(stg), bbase = sa(stg + C::NBOX * C::ABOX);
+#pragma unroll
+                for (int i = 0; i < S; ++i) {
+                    // slice i of A: box i/2, byte offset 64 (i odd) inside the 128-byte row
+                    const uint64_t dA = smem_desc(abase + (i >> 1) * C::ABOX) + 4 * (i & 1);
+#pragma unroll
+                    for (int t = 0; t + i < S; ++t) {
+                        const uint64_t dB = smem_desc(bbase + (t >> 1) * C::BBOX) + 4 * (t & 1);
+                        const uint32_t acc = tmem + (uint32_t)((buf * S + i + t) * BN);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h)
+                            mma_bf16(acc, dA + 2 * h, dB + 2 * h, idesc, (kc == 0 && i == 0 && h == 0) ? 0u : 1u);
+                    }
+                }
+                commit(EMPTY + 8 * s);
+                if (kc == C::CK - 1 || kt == nkb - 1) commit(ACCF + 8 * buf);
+            }
+        }
+        __syncwarp();
+    } else {
+        const int ew = warp - 2;        // 0..7
+        const int quarter = warp & 3;   // TMEM lanes this warp may read
+        const int half = ew >> 2;       // column half
+        float hi[C::NC], lo[C::NC];
+#pragma unroll
+        for (int j = 0; j < C::NC; ++j) hi[j] = lo[j] = 0.f;
+        bool ok = true;
+        for (int ch = 0; ch < nch; ++ch) {
+            const int buf = ch % C::NBUF;
+            if (!bar_wait(ACCF + 8 * buf, (ch / C::NBUF) & 1, g.err, 14)) {
+                ok = false;
+                break;
+            }
+            fence_after();
+#pragma unroll
+            for (int dg = 0; dg < S; ++dg) {
+                const float sc = __int_as_float((127 - 8 * dg) << 23);  // 2^(-8 dg)
+#pragma unroll
+                for (int c0 = 0; c0 < C::NC; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) +
+                                  (uint32_t)((buf * S + dg) * BN + half * C::NC + c0), r);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) two_sum(hi[c0 + j], lo[c0 + j], __uint_as_float(r[j]) * sc);
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) bar_arrive(ACCE + 8 * buf);
+        }
+        if (ok) {
+            // scale and write: 32 x 32 blocks transposed through shared memory (the
+            // pipeline ring is idle once the last chunk is drained) so that lanes
+            // walk output columns
+            double *tb = (double *)smem + ew * 32 * 33;
+            const int rl = 32 * quarter + lane;
+            const long long ra = arow + rl;
+            const int ea = (m0 + rl < g.M && ra < g.rowsA) ? g.eA[ra] : 0;
+#pragma unroll
+            for (int c0 = 0; c0 < C::NC; c0 += 32) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    tb[lane * 33 + j] = scalbn((double)hi[c0 + j] + (double)lo[c0 + j], ea - 14);
+                __syncwarp();
+                const int col = n0 + half * C::NC + c0 + lane;
+                const long long rb = brow + half * C::NC + c0 + lane;
+                const double cs = (col < g.N && rb < g.rowsB) ? scalbn(g.alpha, g.eB[rb]) : 0.0;
+                double *out = g.d + g.s1 * b;
+                for (int rr = 0; rr < 32; ++rr) {
+                    const int rw = m0 + 32 * quarter + rr;
+                    if (rw < g.M && col < g.N) out[(long long)rw * g.ldm + (long long)col * g.ldn] = tb[rr * 33 + lane] * cs;
+                }
+                __syncwarp();
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
+// ---------------------------------------------------------------- splitting
+
+// e[r] = largest binary exponent of row r (frexp convention: |x| < 2^e); 0 for a zero row
+__global__ void oz_rowexp(const double *__restrict__ x, long long rows, int K, long long sr, long long sk,
+                          int *__restrict__ e)
+{
+    const long long r = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    int mx = 0;
+    for (int k = lane; k < K; k += 32) {
+        const long long bits = __double_as_longlong(x[r * sr + (long long)k * sk]);
+        mx = max(mx, (int)((bits >> 52) & 0x7FF));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) e[r] = mx ? mx - 1022 : 0;
+}
+
+// balanced base-256 digits of round(x * 2^(7 + 8(S-1) - e)), most significant first
+template <int S>
+__device__ __forceinline__ void oz_digits(double x, int e, int (&q)[S])
+{
+    const long long bits = __double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    long long Y = 0;
+    if (ex != 0) {  // zero and subnormal inputs give zero digits
+        const long long M = (bits & ((1LL << 52) - 1)) | (1LL << 52);
+        // x = +-M 2^(ex - 1075); |x| < 2^e keeps sh <= 2 (S <= 7)
+        const int sh = ex - 1075 + 7 + 8 * (S - 1) - e;
+        if (sh >= 0) Y = M << sh;
+        else if (sh > -63) Y = (M + (1LL << (-sh - 1))) >> (-sh);
+        if (bits < 0) Y = -Y;
+    }
+#pragma unroll
+    for (int s = S - 1; s > 0; --s) {
+        const int dgt = (int)((Y + 128) & 255) - 128;
+        q[s] = dgt;
+        Y = (Y - dgt) >> 8;
+    }
+    q[0] = (int)Y;
+}
+
+template <int S>
+__global__ void oz_slice(const double *__restrict__ x, long long rows, int K, long long sr, long long sk,
+                         const int *__restrict__ e, int nkb, int SP, long long L, uint16_t *__restrict__ q)
+{
+    const long long tot = rows * nkb * 32;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+        const long long r = t / (nkb * 32);
+        const int rem = (int)(t - r * nkb * 32);
+        const int kb = rem >> 5, kl = rem & 31, k = kb * 32 + kl;
+        int dg[S];
+        if (k < K) {
+            oz_digits<S>(x[r * sr + (long long)k * sk], e[r], dg);
+        } else {
+#pragma unroll
+            for (int s = 0; s < S; ++s) dg[s] = 0;
+        }
+        uint16_t *o = q + r * L + (long long)kb * SP * 32 + kl;
+#pragma unroll
+        for (int s = 0; s < S; ++s)  // |digit| <= 128: the upper half of its FP32 pattern is the exact bf16
+            o[s * 32] = (uint16_t)(__float_as_uint((float)dg[s]) >> 16);
+        for (int s = S; s < SP; ++s) o[s * 32] = 0;
+    }
+}
+
+template <int S, int BN>
+void oz_launch(cudaStream_t st, dim3 grid, const OzMat &A, const OzMat &B, const OzArgs &g)
+{
+    using C = OzCfg<S, BN>;
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(oz_kernel<S, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    TR_CUDA(attr);
+    oz_kernel<S, BN><<<grid, 320, C::SMEM, st>>>(A.m128, BN == 64 ? B.m64 : B.m128, g);
+}
+
+template <int S>
+void oz_slice_launch(cudaStream_t st, const double *x, long long sr, long long sk, OzMat &m, unsigned blocks)
+{
+    oz_slice<S><<<blocks, 256, 0, st>>>(x, m.rows, m.K, sr, sk, m.e, m.nkb, m.SP, m.L, m.q);
+}
+
+long long row_len(int K, int S) { return (long long)cdiv(K, 32) * (((S + 1) & ~1) * 32); }
+
+}  // namespace
+
+size_t oz_bytes(long long rows, int K, int S)
+{
+    const size_t qb = (size_t)rows * row_len(K, S) * 2;
+    return ((qb + 255) & ~(size_t)255) + (((size_t)rows * 4 + 255) & ~(size_t)255);
+}
+
+void oz_bind(OzMat &m, void *storage, long long rows, int K, int S)
+{
+    TR_REQUIRE(S >= 2 && S <= OZ_MAX_SLICES, TR_EINVAL, "Ozaki split: slices must be 2..7");
+    TR_REQUIRE(rows > 0 && rows < (1LL << 31) && K > 0, TR_EINVAL, "Ozaki split: bad shape");
+    TR_REQUIRE(((uintptr_t)storage % 256) == 0, TR_EINVAL, "Ozaki split: storage must be 256-byte aligned");
+    m.rows = rows;
+    m.K = K;
+    m.S = S;
+    m.SP = (S + 1) & ~1;
+    m.nkb = cdiv(K, 32);
+    m.L = row_len(K, S);
+    m.q = (uint16_t *)storage;
+    const size_t qb = (size_t)rows * m.L * 2;
+    m.e = (int *)((uint8_t *)storage + ((qb + 255) & ~(size_t)255));
+    tma_encode_2d(m.m128, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, m.q, rows, m.L, m.L * 2, 64, 128);
+    tma_encode_2d(m.m64, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, m.q, rows, m.L, m.L * 2, 64, 64);
+}
+
+void oz_split(Prof &prof, cudaStream_t st, const char *name, const double *x, long long sr, long long sk, OzMat &m)
+{
+    TR_REQUIRE(m.q && m.e, TR_EINVAL, "Ozaki split: unbound operand");
+    const unsigned rb = (unsigned)cdiv(m.rows, 8);
+    TR_LAUNCH(prof, st, "oz_rowexp", 0, 8.0 * m.rows * m.K,
+              oz_rowexp<<<rb, 256, 0, st>>>(x, m.rows, m.K, sr, sk, m.e));
+    const long long tot = m.rows * m.nkb * 32;
+    const unsigned blocks = (unsigned)std::min<long long>(cdiv(tot, 256), 152LL * 16);
+    int tok = prof.begin(st, name, 0, 8.0 * m.rows * m.K + 2.0 * m.rows * m.L);
+    switch (m.S) {
+    case 2: oz_slice_launch<2>(st, x, sr, sk, m, blocks); break;
+    case 3: oz_slice_launch<3>(st, x, sr, sk, m, blocks); break;
+    case 4: oz_slice_launch<4>(st, x, sr, sk, m, blocks); break;
+    case 5: oz_slice_launch<5>(st, x, sr, sk, m, blocks); break;
+    case 6: oz_slice_launch<6>(st, x, sr, sk, m, blocks); break;
+    default: oz_slice_launch<7>(st, x, sr, sk, m, blocks); break;
+    }
+    TR_CUDA(cudaGetLastError());
+    prof.end(st, tok);
+}
+
+void oz_gemm(Prof &prof, cudaStream_t st, const char *name, const OzMat &A, long long a0, long long a1,
+             const OzMat &B, long long c0, long long c1, int M, int N, int nb, double *d, long long s1,
+             long long ldm, long long ldn, double alpha, int *err)
+{
+    if (M <= 0 || N <= 0 || nb <= 0) return;
+    TR_REQUIRE(A.q && B.q && A.K == B.K && A.S == B.S, TR_EINVAL, "Ozaki GEMM: operands must share K and slices");
+    TR_REQUIRE(a0 >= 0 && a1 >= 0 && c0 >= 0 && c1 >= 0, TR_EINVAL, "Ozaki GEMM: negative row offset");
+    TR_REQUIRE(nb <= 65535 && cdiv(M, 128) <= 65535, TR_EINVAL, "Ozaki GEMM: grid too large");
+    const int S = A.S;
+    const int BN = 64;
+    const long long lastA = a0 + a1 * (nb - 1) + (long long)cdiv(M, 128) * 128;
+    const long long lastB = c0 + c1 * (nb - 1) + (long long)cdiv(N, BN) * BN;
+    TR_REQUIRE(lastA < (1LL << 31) && lastB < (1LL << 31), TR_EINVAL, "Ozaki GEMM: row index overflow");
+    OzArgs g;
+    g.M = M;
+    g.N = N;
+    g.nkb = A.nkb;
+    g.a0 = a0;
+    g.a1 = a1;
+    g.c0 = c0;
+    g.c1 = c1;
+    g.rowsA = A.rows;
+    g.rowsB = B.rows;
+    g.eA = A.e;
+    g.eB = B.e;
+    g.d = d;
+    g.s1 = s1;
+    g.ldm = ldm;
+    g.ldn = ldn;
+    g.alpha = alpha;
+    g.err = err;
+    dim3 grid(cdiv(N, BN), cdiv(M, 128), nb);
+    const double flops = 2.0 * M * N * (double)A.K * nb;
+    const double bytes = 2.0 * A.SP * ((double)M + N) * A.nkb * 32 * nb + 8.0 * M * N * nb;
+    int tok = prof.begin(st, name, flops, bytes);
+    switch (S) {
+    case 2: oz_launch<2, 64>(st, grid, A, B, g); break;
+    case 3: oz_launch<3, 64>(st, grid, A, B, g); break;
+    case 4: oz_launch<4, 64>(st, grid, A, B, g); break;
+    case 5: oz_launch<5, 64>(st, grid, A, B, g); break;
+    case 6: oz_launch<6, 64>(st, grid, A, B, g); break;
+    default: oz_launch<7, 64>(st, grid, A, B, g); break;
+    }
+    TR_CUDA(cudaGetLastError());
+    prof.end(st, tok);
+}
+
+}  // namespace tr

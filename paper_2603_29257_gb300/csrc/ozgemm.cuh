@@ -1,0 +1,56 @@
+// FP64 matrix products on the bf16 tensor cores by the Ozaki splitting scheme
+// (internal): every FP64 operand row is written as a short sum of bf16
+// "slices" that carry small integers, the slice products are summed exactly
+// by tcgen05.mma kind::f16 in FP32 tensor memory, and the exact partial sums
+// are accumulated in double-FP32 registers.  With S slices the operands keep
+// 7 + 8 (S - 1) bits below each row's largest element.
+#pragma once
+
+#include <cuda.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace tr {
+
+constexpr int OZ_MAX_SLICES = 7;
+// slices of the reduced-precision form's transforms unless the options say otherwise
+constexpr int OZ_DEFAULT_SLICES_MIXED = 5;
+
+// An FP64 matrix x[rows][K] in sliced form.  Row r has exponent e[r] with
+// |x[r][k]| < 2^e[r] for every k, and integer digits |q_s[r][k]| <= 128 with
+//   x[r][k] ~= 2^e[r] * sum_{s<S} q_s[r][k] * 2^(-7-8s)
+// (the rounding error is at most 2^(e[r]-8S) per element).  Storage, bf16,
+// row-major with row length L = nkb * SP * 32: for each block of 32 K values
+// the slices one after the other (32 values each), SP = S rounded up to even
+// (the extra slice and every k >= K hold zeros).
+struct OzMat {
+    uint16_t *q = nullptr;
+    int *e = nullptr;
+    long long rows = 0;
+    int K = 0, S = 0, SP = 0, nkb = 0;
+    long long L = 0;
+    CUtensorMap m128, m64;  // TMA boxes of 64 bf16 (two slices of one K block) x 128 / 64 rows
+};
+
+// bytes of storage oz_bind needs for rows x K with S slices
+size_t oz_bytes(long long rows, int K, int S);
+
+// lay m out over storage (oz_bytes(rows, K, S) bytes, 256-byte aligned) and
+// encode its tensor maps
+void oz_bind(OzMat &m, void *storage, long long rows, int K, int S);
+
+// slice x into m: element (r, k) = x[r * sr + k * sk] for r < m.rows, k < m.K
+void oz_split(Prof &prof, cudaStream_t st, const char *name, const double *x, long long sr, long long sk, OzMat &m);
+
+// Batched d[b*s1 + r*ldm + c*ldn] = alpha * sum_k A[a0 + a1*b + r][k] * B[c0 + c1*b + c][k]
+// for r < M, c < N, b < nb; A and B have the same K and S.  Rows a CTA reads
+// beyond M or N belong to the next batch entry or lie past the operand (read
+// as zero); they are computed and discarded.  err: device int set non-zero if
+// a pipeline wait timed out.
+void oz_gemm(Prof &prof, cudaStream_t st, const char *name, const OzMat &A, long long a0, long long a1,
+             const OzMat &B, long long c0, long long c1, int M, int N, int nb, double *d, long long s1,
+             long long ldm, long long ldn, double alpha, int *err);
+
+}  // namespace tr

@@ -11,6 +11,7 @@
 // Every mbarrier wait gives up after ~1 s: it records an error code in *err
 // and the CTA skips ahead to its teardown (tensor memory is always freed).
 #include "tcgemm.cuh"
+#include "tcptx.cuh"
 
 #include <cuda.h>
 
@@ -22,8 +23,6 @@ namespace {
 
 constexpr int BM = 128, BKF = 32;             // tile: 128 x BN outputs, 32 FP32 (128 B) of K per stage
 constexpr int TILE_BYTES = BM * BKF * 4;      // 16 KB (A tile; a B tile is BN * 128 B)
-constexpr long long WAIT_CYCLES = 2000000000LL;
-
 struct TcArgs {
     int M, N, K, n2;
     int ka0, kb0;                 // K offsets (elements) into the A and B rows
@@ -32,59 +31,13 @@ struct TcArgs {
     int *err;
 };
 
-__device__ __forceinline__ uint32_t sa(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+using namespace ptx;
 
-__device__ __forceinline__ void bar_init(uint32_t a, uint32_t n)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(n) : "memory");
-}
-__device__ __forceinline__ void bar_expect(uint32_t a, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool bar_wait(uint32_t a, uint32_t parity, int *err, int code)
-{
-    const long long t0 = clock64();
-    while (true) {
-        uint32_t ok;
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if (clock64() - t0 > WAIT_CYCLES) {
-            atomicCAS(err, 0, code);
-            return false;
-        }
-    }
-}
-__device__ __forceinline__ void tma2d(uint32_t dst, const CUtensorMap *tm, int x, int y, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-        "l"((uint64_t)tm), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
-{
-    uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
 __device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
 {
     asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
                  "l"(a), "l"(b), "r"(idesc), "r"(acc)
                  : "memory");
-}
-__device__ __forceinline__ void commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ float tf32_rest(float v)
 {
@@ -267,35 +220,9 @@ __global__ void split_kernel(const double *__restrict__ x, long long rows, long 
     }
 }
 
-typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiled encoder()
-{
-    static EncodeTiled fn = nullptr;
-    static std::mutex mu;
-    std::lock_guard<std::mutex> lock(mu);
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        TR_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
-        TR_REQUIRE(q == cudaDriverEntryPointSuccess && p, TR_ECUDA, "cuTensorMapEncodeTiled unavailable");
-        fn = (EncodeTiled)p;
-    }
-    return fn;
-}
-
 void encode(CUtensorMap &tm, const float *p, long long rows, long long kdim, long long ld, int box_rows)
 {
-    cuuint64_t gdim[2] = {(cuuint64_t)kdim, (cuuint64_t)rows};
-    cuuint64_t gstr[1] = {(cuuint64_t)ld * 4};
-    cuuint32_t box[2] = {BKF, (cuuint32_t)box_rows};
-    cuuint32_t es[2] = {1, 1};
-    CUresult r = encoder()(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)p, gdim, gstr, box, es,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    TR_REQUIRE(r == CUDA_SUCCESS, TR_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    tma_encode_2d(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, p, rows, kdim, ld * 4, BKF, box_rows);
 }
 
 template <int NSPLIT, int MODE, int BN>
@@ -322,6 +249,38 @@ void launch_mode(cudaStream_t st, dim3 grid, const TcMat &A, const TcMat &B, con
 }
 
 }  // namespace
+
+typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiled encoder()
+{
+    static EncodeTiled fn = nullptr;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        TR_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+        TR_REQUIRE(q == cudaDriverEntryPointSuccess && p, TR_ECUDA, "cuTensorMapEncodeTiled unavailable");
+        fn = (EncodeTiled)p;
+    }
+    return fn;
+}
+
+void tma_encode_2d(CUtensorMap &tm, CUtensorMapDataType dt, const void *p, long long rows, long long kdim,
+                   long long ld_bytes, int box_inner, int box_rows)
+{
+    cuuint64_t gdim[2] = {(cuuint64_t)kdim, (cuuint64_t)rows};
+    cuuint64_t gstr[1] = {(cuuint64_t)ld_bytes};
+    cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = encoder()(&tm, dt, 2, (void *)p, gdim, gstr, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    TR_REQUIRE(r == CUDA_SUCCESS, TR_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+}
 
 void tc_make(TcMat &m, const float *hi, const float *lo, long long rows, long long kdim, long long ld)
 {

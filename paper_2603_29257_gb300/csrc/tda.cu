@@ -13,6 +13,7 @@
 #include <cstring>
 
 #include "ctx.cuh"
+#include "ozgemm.cuh"
 
 namespace tr {
 namespace {
@@ -338,6 +339,79 @@ static void transforms_fp64(tr_ctx *c, DevBuf<double> &Iij)
     }
 }
 
+// Slices of the Ozaki-scheme transforms for this context: 0 when the FP64
+// transforms run on the FP64 pipe
+int xform_slices(const tr_ctx *c)
+{
+    const int s = c->opt.xform_slices;
+    if (s < 0) return 0;
+    if (s == 0) return c->opt.precision == TR_MIXED ? OZ_DEFAULT_SLICES_MIXED : 0;
+    return s;
+}
+
+// The same MO transforms on the bf16 tensor cores (Ozaki scheme with S slices):
+// the MO coefficients are sliced once (rows = orbitals, K = AO index), each AO
+// integral chunk and each half-transformed chunk before its product.
+static void transforms_oz(tr_ctx *c, DevBuf<double> &Iij, int S)
+{
+    const int nao = c->nao, nocc = c->nocc, nvir = c->nvir, nmo = c->nmo, nJ = c->nJ, nK = c->nK;
+    const long long nov = c->nov;
+    cudaStream_t st = c->st;
+    Prof &pf = c->prof;
+    int *err = c->flag.p + 2;
+    TR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    DevBuf<double> cbuf;
+    cbuf.alloc(cdiv(oz_bytes(nmo, nao, S), 8), &c->budget, "sliced MO coefficients");
+    OzMat Cs;
+    oz_bind(Cs, cbuf.p, nmo, nao, S);
+    oz_split(pf, st, "oz_split_C", c->C.p, 1, nmo, Cs);
+    c->Y.alloc((size_t)nJ * nov, &c->budget, "(P|ia)");
+    const int hrows = std::max(nocc, std::max(c->oK, c->vK));
+    const size_t per = sizeof(double) * ((size_t)nao * nao + (size_t)hrows * nao) + oz_bytes(nao, nao, S) +
+                       oz_bytes(hrows, nao, S);
+    int npc = (int)std::max<size_t>(1, c->opt.aux_chunk_bytes / per);
+    npc = std::max(1, std::min(npc, std::max(nJ, nK)));
+    DevBuf<double> I, H, Ib, Hb;
+    I.alloc((size_t)npc * nao * nao, &c->budget, "AO integral chunk");
+    H.alloc((size_t)npc * hrows * nao, &c->budget, "half-transform chunk");
+    Ib.alloc(cdiv(oz_bytes((long long)npc * nao, nao, S), 8), &c->budget, "sliced integral chunk");
+    Hb.alloc(cdiv(oz_bytes((long long)npc * hrows, nao, S), 8), &c->budget, "sliced half-transform chunk");
+    OzMat Is, Hs;
+    // H[p][r][nu] = sum_mu C[mu][r0 + r] (P|mu nu) for rows r < nr, then
+    // out[p][r][s] = sum_nu H[p][r][nu] C[nu][s0 + s] for s < ns
+    auto pair_transform = [&](int np, int r0, int nr, int s0, int ns, double *out, long long ldo, const char *n1,
+                              const char *n2) {
+        oz_gemm(pf, st, n1, Cs, r0, 0, Is, 0, nao, nr, nao, np, H.p, (long long)nr * nao, nao, 1, 1.0, err);
+        oz_bind(Hs, Hb.p, (long long)np * nr, nao, S);
+        oz_split(pf, st, "oz_split_H", H.p, nao, 1, Hs);
+        oz_gemm(pf, st, n2, Hs, 0, nr, Cs, s0, 0, nr, ns, np, out, (long long)nr * ldo, ldo, 1, 1.0, err);
+    };
+    for (int p0 = 0; p0 < nJ; p0 += npc) {
+        const int np = std::min(npc, nJ - p0);
+        compute_int3c_chunk(c, 0, p0, np, I.p);
+        oz_bind(Is, Ib.p, (long long)np * nao, nao, S);
+        oz_split(pf, st, "oz_split_I", I.p, nao, 1, Is);
+        pair_transform(np, 0, nocc, nocc, nvir, c->Y.p + (long long)p0 * nov, nvir, "xform_J1_oz", "xform_J2_oz");
+    }
+    if (c->k_active) {
+        const int oK = c->oK, vK = c->vK, o0 = c->o0;
+        c->Tab.alloc((size_t)nK * vK * vK, &c->budget, "T_ab");
+        for (int p0 = 0; p0 < nK; p0 += npc) {
+            const int np = std::min(npc, nK - p0);
+            compute_int3c_chunk(c, 1, p0, np, I.p);
+            oz_bind(Is, Ib.p, (long long)np * nao, nao, S);
+            oz_split(pf, st, "oz_split_I", I.p, nao, 1, Is);
+            pair_transform(np, o0, oK, o0, oK, Iij.p + (long long)p0 * oK * oK, oK, "xform_K1_oz", "xform_K2_oz");
+            pair_transform(np, nocc, vK, nocc, vK, c->Tab.p + (long long)p0 * vK * vK, vK, "xform_K1_oz",
+                           "xform_K2_oz");
+        }
+    }
+    int h = 0;
+    TR_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TR_CUDA(cudaStreamSynchronize(st));
+    TR_REQUIRE(h == 0, TR_ECUDA, "build: tensor-core transform pipeline timed out (code " + std::to_string(h) + ")");
+}
+
 void build(tr_ctx *c)
 {
     TR_REQUIRE(c->have_mol && c->have_orb, TR_EINVAL, "build: molecule and orbitals required");
@@ -375,7 +449,9 @@ void build(tr_ctx *c)
         DevBuf<double> Iij;
         const int oK = c->oK;
         if (c->k_active) Iij.alloc((size_t)nK * oK * oK, &c->budget, "(ij|P)");
-        transforms_fp64(c, Iij);
+        const int S = xform_slices(c);
+        if (S > 0) transforms_oz(c, Iij, S);
+        else transforms_fp64(c, Iij);
         if (c->k_active) {
             // T_ij^P = sum_Q (ij|Q) (Q|P)^-1, stored [i][P][j]
             c->T2.alloc((size_t)oK * nK * oK, &c->budget, "T_ij");
@@ -471,12 +547,15 @@ size_t footprint(tr_ctx *c)
                         (double)c->shells_h.size() * 64 + (double)c->pl.pairs.size() * 8;
     // build: integral and half-transform chunks, FP64 tensors
     const double hrows = std::max(nocc, std::max(oK, vK));
-    const double per = d * (nao * nao + hrows * nao);
+    const int S = xform_slices(c);
+    const double per = d * (nao * nao + hrows * nao) +
+                       (S > 0 ? (double)oz_bytes(c->nao, c->nao, S) + (double)oz_bytes((long long)hrows, c->nao, S) : 0.0);
     const double npc = std::max(1.0, std::min(std::floor((double)c->opt.aux_chunk_bytes / per), std::max(nJ, nK)));
+    const double cs = S > 0 ? (double)oz_bytes(c->nmo, c->nao, S) : 0.0;
     const double t64 = d * (nJ * nov + nK * vK * vK + 2.0 * nK * oK * oK);
     const double oKp = std::ceil(std::max(oK, 1.0) / 32) * 32, vKp = std::ceil(std::max(vK, 1.0) / 32) * 32;
     const double t32 = mixed ? f * (nJ * nov + 2.0 * nK * vK * vKp + 2.0 * oK * nK * oKp) : 0.0;
-    const double build_peak = npc * per + t64 + t32;
+    const double build_peak = npc * per + cs + t64 + t32;
     // solve: tensors kept, Davidson storage and product workspaces
     const double kept = mixed ? t32 + d * oK * nK * oK : t64 - d * nK * oK * oK;
     const int n = (int)std::min<double>(c->opt.nstates, nov);

@@ -33,7 +33,8 @@ class Options(ct.Structure):
                 ("max_iter", ct.c_int), ("tol", ct.c_double), ("precision", ct.c_int),
                 ("screen", ct.c_double), ("hbm_budget", ct.c_size_t),
                 ("aux_chunk_bytes", ct.c_size_t), ("host_budget", ct.c_size_t),
-                ("dav_dev_rows", ct.c_int), ("matvec_ws_bytes", ct.c_size_t)]
+                ("dav_dev_rows", ct.c_int), ("matvec_ws_bytes", ct.c_size_t),
+                ("xform_slices", ct.c_int)]
 
 
 class Dims(ct.Structure):

@@ -285,6 +285,15 @@ typedef struct {
     char error[160];
 } tr_result;
 
+/* Lowest nev eigenpairs of the symmetric k x k matrix H (row-major, not
+   modified) with the device eigensolver of the Davidson driver (the small
+   subspace eigenproblem of Sec. 3.3): Householder tridiagonalisation, Sturm
+   multisection and inverse iteration in one thread-block cluster, on the
+   context's stream.  w[nev] ascending; Y[k][nev] row-major, column i the unit
+   eigenvector of w[i] (sign arbitrary).  on_device: H, w, Y are device
+   pointers.  Needs no molecule.  Errors: TR_EINVAL (nev > k, null pointers). */
+int tr_subspace_eigh(tr_ctx *ctx, int k, const double *H, int nev, double *w, double *Y, int on_device);
+
 /* Start a server on the current device (opt may be NULL). */
 int tr_server_create(tr_server **out, const tr_server_options *opt);
 /* Queue a request (all arrays copied); *id receives its identifier. */

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "ctx.cuh"
+#include "linalg.cuh"
 
 namespace {
 
@@ -315,6 +316,28 @@ int tr_profile_get(tr_ctx *ctx, tr_prof_entry *out, int max)
 }
 
 long tr_launch_count(const tr_ctx *ctx) { return ctx ? ctx->prof.launches : 0; }
+
+int tr_subspace_eigh(tr_ctx *ctx, int k, const double *H, int nev, double *w, double *Y, int on_device)
+{
+    return guarded(ctx, [&]() {
+        TR_REQUIRE(k > 0 && nev > 0 && nev <= k && H && w && Y, TR_EINVAL, "subspace_eigh: bad arguments");
+        tr::DevBuf<double> A, sw, sY, scr;
+        A.alloc((size_t)k * k, &ctx->budget, "eigh matrix");
+        sw.alloc(nev, &ctx->budget, "eigh values");
+        sY.alloc((size_t)k * nev, &ctx->budget, "eigh vectors");
+        scr.alloc(tr::eigh_lowest_scratch(k, nev) / sizeof(double), &ctx->budget, "eigh scratch");
+        if (!ctx->flag.p) ctx->flag.alloc(4, &ctx->budget, "flags");
+        const cudaMemcpyKind in = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        const cudaMemcpyKind out = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        TR_CUDA(cudaMemcpyAsync(A.p, H, sizeof(double) * (size_t)k * k, in, ctx->st));
+        tr::eigh_lowest(ctx->prof, ctx->st, A.p, k, nev, sw.p, sY.p, nev, scr.p, ctx->flag.p);
+        TR_CUDA(cudaGetLastError());
+        TR_CUDA(cudaMemcpyAsync(w, sw.p, sizeof(double) * nev, out, ctx->st));
+        TR_CUDA(cudaMemcpyAsync(Y, sY.p, sizeof(double) * (size_t)k * nev, out, ctx->st));
+        TR_CUDA(cudaStreamSynchronize(ctx->st));
+        return TR_OK;
+    });
+}
 
 int tr_memory(tr_ctx *ctx, size_t *used, size_t *peak, size_t *estimate)
 {

@@ -340,7 +340,7 @@ struct Dav {
         c->Hs.alloc((size_t)maxsp * maxsp, &c->budget, "subspace");
         c->Hw.alloc((size_t)maxsp * maxsp, &c->budget, "subspace");
         c->Yev.alloc((size_t)maxsp * maxsp, &c->budget, "subspace");
-        c->Yw.alloc((size_t)maxsp * maxsp, &c->budget, "subspace");
+        c->Yw.alloc(eigh_lowest_scratch(maxsp, n) / sizeof(double), &c->budget, "subspace eigensolver scratch");
         c->theta.alloc(maxsp, &c->budget, "subspace");
         c->Cs.alloc((size_t)2 * maxsp * pmax, &c->budget, "projections");
         SV.nov = SW.nov = nov;
@@ -505,7 +505,7 @@ struct Dav {
         TR_CUDA(cudaEventRecord(ev.e[0], st));
         TR_LAUNCH(pf, st, "copy_sub", 0, 0, copy_sub<<<dim3(cdiv(k, 128), k), 128, 0, st>>>(c->Hs.p, maxsp, c->Hw.p, k));
         TR_CUDA(cudaMemsetAsync(c->flag.p, 0, sizeof(int), st));
-        jacobi_eigh(pf, st, c->Hw.p, k, c->theta.p, c->Yev.p, c->Yw.p, c->flag.p);
+        eigh_lowest(pf, st, c->Hw.p, k, n, c->theta.p, c->Yev.p, k, c->Yw.p, c->flag.p);
         TR_CUDA(cudaEventRecord(ev.e[1], st));
         // Ritz vectors X = Y^T V and residuals R = Y^T W - theta X
         for_rows(SV, 0, k, [&](const double *rows, int r0, int nr) {

@@ -45,6 +45,15 @@ void chol_inverse(Prof &prof, cudaStream_t st, const double *L, int n, double *G
 void jacobi_eigh(Prof &prof, cudaStream_t st, double *H, int k, double *w, double *Y,
                  double *work, int *flag);
 
+// Lowest nev eigenpairs of a symmetric k x k matrix A (ld = k, destroyed) in
+// one thread-block cluster: Householder tridiagonalisation, Sturm
+// multisection, inverse iteration, back-transformation.  w[0..nev) ascending;
+// Y[r * ldy + i] = component r of eigenvector i.  scratch: eigh_lowest_scratch
+// bytes of device memory.
+size_t eigh_lowest_scratch(int k, int nev);
+void eigh_lowest(Prof &prof, cudaStream_t st, double *A, int k, int nev, double *w, double *Y, int ldy,
+                 double *scratch, int *flag);
+
 // out[i] = sum over rows of a[r][i] for a[nrows][n] (deterministic).
 void sum_rows(Prof &prof, cudaStream_t st, const double *a, int nrows, int n, double *out);
 

@@ -564,7 +564,8 @@ size_t footprint(tr_ctx *c)
     maxsp = (int)std::min<double>(std::max(maxsp, b0 + n), std::max(nov, (double)b0));
     const double pmax = std::max(b0, n);
     const double mb = std::min<double>(pmax, c->mblk);
-    const double dav = d * nov * (2.0 * maxsp + 4.0 * pmax + 2.0 * n) + d * (5.0 * maxsp * maxsp + 2.0 * maxsp * pmax);
+    const double dav = d * nov * (2.0 * maxsp + 4.0 * pmax + 2.0 * n) +
+                       d * (5.0 * maxsp * maxsp + 2.0 * maxsp * pmax + 6.0 * n * maxsp + 5.0 * maxsp + 16.0 + n);
     const double mws = nK > 0 ? std::min<double>((double)c->opt.matvec_ws_bytes, d * mb * nK * oK * vK) +
                                     (mixed ? 2.0 * f * mb * oK * vKp + f * mb * nov : d * mb * oK * vK)
                               : 0.0;

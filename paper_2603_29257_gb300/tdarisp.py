@@ -106,6 +106,8 @@ SIGNATURES = {
     "tr_profile": (ct.c_int, [ct.c_void_p, ct.c_int]),
     "tr_profile_get": (ct.c_int, [ct.c_void_p, ct.POINTER(ProfEntry), ct.c_int]),
     "tr_launch_count": (ct.c_long, [ct.c_void_p]),
+    "tr_subspace_eigh": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p,
+                                    ct.c_int]),
     "tr_memory": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_size_t), ct.POINTER(ct.c_size_t),
                              ct.POINTER(ct.c_size_t)]),
 }
@@ -357,6 +359,18 @@ class Context:
         return {arr[i].name.decode(): dict(launches=arr[i].launches, ms=arr[i].total_ms,
                                            flops=arr[i].flops, bytes=arr[i].bytes)
                 for i in range(n)}
+
+    def subspace_eigh(self, H, nev):
+        """Lowest nev eigenpairs of the symmetric matrix H (host arrays) with the
+        device eigensolver of the Davidson driver: (w[nev], Y[k][nev])."""
+        Hn = _f64(H)
+        k = Hn.shape[0]
+        w = np.empty(nev)
+        Y = np.empty((k, nev))
+        self._check(lib().tr_subspace_eigh(self._h, k, Hn.ctypes.data_as(ct.c_void_p), nev,
+                                           w.ctypes.data_as(ct.c_void_p), Y.ctypes.data_as(ct.c_void_p), 0),
+                    "tr_subspace_eigh")
+        return w, Y
 
     def memory(self):
         """(bytes held, peak bytes, estimated peak of build + solve)."""

@@ -3,11 +3,9 @@
 // The FP64 pipe of GB300 is narrow (a few DFMA per clock per SM), so these
 // kernels are designed to keep it busy rather than to save bandwidth: a
 // 64x64x16 shared-memory tiled GEMM with register double-buffering and
-// split-K for long reductions, a column-wise Cholesky, and a one-block
-// parallel cyclic Jacobi eigensolver for the Davidson subspace matrix.
+// split-K for long reductions, and a column-wise Cholesky with the inverse
+// of its factor.  (The Davidson subspace eigensolver lives in eigh.cu.)
 #include "linalg.cuh"
-
-#include <cooperative_groups.h>
 
 #include <algorithm>
 #include <cmath>
@@ -16,7 +14,6 @@ namespace tr {
 namespace {
 
 constexpr int BK = 16, NT = 256;
-constexpr int JACOBI_MAX_PAIRS_PER_BLOCK = 64;
 
 // Thread (tx, ty) of a 16 x 16 block computes TM x TN outputs at rows
 // ty + 16 i and columns tx + 16 j; the block tile is (16 TM) x (16 TN).
@@ -196,140 +193,6 @@ __global__ void tri_inverse_cols(const double *__restrict__ L, int n, double *__
     }
 }
 
-// ---------------------------------------------------------------- Jacobi
-
-__device__ __forceinline__ int rr_pos(int i, int r, int kk)
-{
-    return i == 0 ? 0 : ((i - 1 + r) % (kk - 1)) + 1;
-}
-
-__device__ double block_sum(double v, double *red)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (warp == 0) {
-        t = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
-        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) red[32] = t;
-    }
-    __syncthreads();
-    return red[32];
-}
-
-constexpr int JACOBI_MAX_SWEEPS = 60;
-constexpr int JACOBI_THREADS = 256;
-
-// Parallel cyclic Jacobi over the whole grid (cooperative launch).  Round r
-// of a sweep applies the k/2 disjoint rotations of the round-robin pairing;
-// block b owns pairs b, b + G, ...: it computes their rotations, updates
-// their two rows of H, and after a grid barrier their two columns of H and
-// of Y; a second barrier ends the round.
-__global__ void __launch_bounds__(JACOBI_THREADS)
-    jacobi_coop(double *H, int k, double *w, double *Yout, double *Y, int *flag, double *red)
-{
-    namespace cg = cooperative_groups;
-    cg::grid_group grid = cg::this_grid();
-    __shared__ double cs[JACOBI_MAX_PAIRS_PER_BLOCK], sn[JACOBI_MAX_PAIRS_PER_BLOCK];
-    __shared__ int pp[JACOBI_MAX_PAIRS_PER_BLOCK], qq[JACOBI_MAX_PAIRS_PER_BLOCK];
-    __shared__ double sred[33];
-    const int kk = k + (k & 1);
-    const int np = kk / 2;
-    const int G = gridDim.x, bid = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-    const int gtid = bid * nt + tid, gnt = G * nt;
-    const int myp = (np - bid + G - 1) / G;  // pairs owned by this block
-
-    for (int idx = gtid; idx < k * k; idx += gnt) Y[idx] = (idx / k == idx % k) ? 1.0 : 0.0;
-
-    bool done = (k <= 1);
-    for (int sweep = 0; sweep < JACOBI_MAX_SWEEPS && !done; ++sweep) {
-        double off = 0.0, tot = 0.0;
-        for (int idx = gtid; idx < k * k; idx += gnt) {
-            double h = H[idx];
-            tot += h * h;
-            if (idx / k != idx % k) off += h * h;
-        }
-        off = block_sum(off, sred);
-        tot = block_sum(tot, sred);
-        if (tid == 0) {
-            red[2 * bid] = off;
-            red[2 * bid + 1] = tot;
-        }
-        grid.sync();
-        off = 0.0;
-        tot = 0.0;
-        for (int b = 0; b < G; ++b) {
-            off += red[2 * b];
-            tot += red[2 * b + 1];
-        }
-        grid.sync();  // everyone has read red[] before it is rewritten
-        if (off <= 1e-30 * tot || tot == 0.0) {
-            done = true;
-            break;
-        }
-        for (int r = 0; r < kk - 1; ++r) {
-            for (int l = tid; l < myp; l += nt) {
-                const int idx = bid + l * G;
-                const int a = rr_pos(idx, r, kk), b = rr_pos(kk - 1 - idx, r, kk);
-                const int p = min(a, b), q = max(a, b);
-                double c = 1.0, s = 0.0;
-                if (q < k) {
-                    const double hpq = H[p * k + q], hpp = H[p * k + p], hqq = H[q * k + q];
-                    if (fabs(hpq) > 1e-18 * sqrt(fabs(hpp * hqq)) && hpq != 0.0) {
-                        const double tau = (hqq - hpp) / (2.0 * hpq);
-                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                        c = 1.0 / sqrt(1.0 + t * t);
-                        s = t * c;
-                    }
-                }
-                pp[l] = p;
-                qq[l] = q;
-                cs[l] = c;
-                sn[l] = s;
-            }
-            __syncthreads();
-            for (int t = tid; t < myp * k; t += nt) {
-                const int l = t / k, j = t - l * k;
-                if (sn[l] == 0.0) continue;
-                const int p = pp[l], q = qq[l];
-                const double c = cs[l], s = sn[l];
-                const double hp = H[p * k + j], hq = H[q * k + j];
-                H[p * k + j] = c * hp - s * hq;
-                H[q * k + j] = s * hp + c * hq;
-            }
-            grid.sync();
-            for (int t = tid; t < myp * k; t += nt) {
-                const int l = t / k, i = t - l * k;
-                if (sn[l] == 0.0) continue;
-                const int p = pp[l], q = qq[l];
-                const double c = cs[l], s = sn[l];
-                const double hp = H[i * k + p], hq = H[i * k + q];
-                H[i * k + p] = c * hp - s * hq;
-                H[i * k + q] = s * hp + c * hq;
-                const double yp = Y[i * k + p], yq = Y[i * k + q];
-                Y[i * k + p] = c * yp - s * yq;
-                Y[i * k + q] = s * yp + c * yq;
-            }
-            grid.sync();
-        }
-    }
-    if (!done && gtid == 0) atomicExch(flag, 1);
-    // sort ascending by rank (ties by index)
-    for (int i = gtid; i < k; i += gnt) {
-        const double wi = H[i * k + i];
-        int rank = 0;
-        for (int j = 0; j < k; ++j) {
-            const double wj = H[j * k + j];
-            rank += (wj < wi || (wj == wi && j < i)) ? 1 : 0;
-        }
-        w[rank] = wi;
-        for (int row = 0; row < k; ++row) Yout[row * k + rank] = Y[row * k + i];
-    }
-}
-
 __global__ void sum_rows_kernel(const double *__restrict__ a, int nrows, int n, double *__restrict__ out)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -455,40 +318,6 @@ void chol_inverse(Prof &prof, cudaStream_t st, const double *L, int n, double *G
     // Ginv = Linv^T Linv
     dgemm(prof, st, "metric_inverse", true, false, n, n, n, 1.0, work, n, work, n, 0.0, Ginv, n,
           Batch(), nullptr, 0);
-}
-
-void jacobi_eigh(Prof &prof, cudaStream_t st, double *H, int k, double *w, double *Y, double *work,
-                 int *flag)
-{
-    if (k <= 0) return;
-    // device limits, looked up once (thread-safe static initialisation)
-    struct Lim {
-        int nsm = 0, per_sm = 0;
-        cudaError_t err = cudaSuccess;
-        Lim()
-        {
-            int dev = 0;
-            err = cudaGetDevice(&dev);
-            if (err == cudaSuccess) err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-            if (err == cudaSuccess)
-                err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop, JACOBI_THREADS, 0);
-        }
-    };
-    static const Lim lim;
-    TR_CUDA(lim.err);
-    const int nsm = lim.nsm, per_sm = lim.per_sm;
-    TR_REQUIRE(per_sm >= 1, TR_ECUDA, "jacobi: kernel cannot be resident");
-    const int np = (k + (k & 1)) / 2;
-    int G = std::min(np, nsm * per_sm);
-    G = std::max(G, (np + JACOBI_MAX_PAIRS_PER_BLOCK - 1) / JACOBI_MAX_PAIRS_PER_BLOCK);
-    TR_REQUIRE(G <= nsm * per_sm, TR_EINVAL, "jacobi: subspace too large");
-    double *red = nullptr;
-    TR_CUDA(cudaMallocAsync(&red, sizeof(double) * 2 * G, st));
-    void *args[] = {&H, &k, &w, &Y, &work, &flag, &red};
-    int tok = prof.begin(st, "jacobi_eigh", 0, 0);
-    TR_CUDA(cudaLaunchCooperativeKernel((const void *)jacobi_coop, dim3(G), dim3(JACOBI_THREADS), args, 0, st));
-    prof.end(st, tok);
-    TR_CUDA(cudaFreeAsync(red, st));
 }
 
 void sum_rows(Prof &prof, cudaStream_t st, const double *a, int nrows, int n, double *out)

@@ -39,12 +39,6 @@ void cholesky(Prof &prof, cudaStream_t st, double *G, int n, int *flag);
 // Ginv = (L L^T)^-1 from the lower Cholesky factor L (n x n).
 void chol_inverse(Prof &prof, cudaStream_t st, const double *L, int n, double *Ginv, double *work);
 
-// Eigen-decomposition of a symmetric k x k matrix (ld = k, destroyed) by
-// parallel cyclic Jacobi in one thread block: w ascending, Y[j*k + r] = j-th
-// component of eigenvector r.  flag (device int) set to 1 if not converged.
-void jacobi_eigh(Prof &prof, cudaStream_t st, double *H, int k, double *w, double *Y,
-                 double *work, int *flag);
-
 // Lowest nev eigenpairs of a symmetric k x k matrix A (ld = k, destroyed) in
 // one thread-block cluster: Householder tridiagonalisation, Sturm
 // multisection, inverse iteration, back-transformation.  w[0..nev) ascending;

@@ -200,9 +200,13 @@ def run_native(args):
                "d2h_bytes_per_step": int(8 * OPTS["nstates"] * (1 + d.nocc * d.nvir) + 8 * OPTS["nstates"])}
 
     # reduced-precision form on the same workload (NEXT: FP32 tensors, 3xTF32 K on tcgen05)
-    mixed = None
-    if not args.no_mixed:
-        mixed = run_mixed(args, tdarisp, mol, C_dev, eps_dev, stream, barrier)
+    mixed = fp64tc = None
+    if not (args.no_mixed and args.no_fp64tc):
+        om64 = fp64_reference_omega(tdarisp, mol, C_dev, eps_dev, stream)
+        if not args.no_mixed:
+            mixed = run_form(args, tdarisp, mol, C_dev, eps_dev, stream, barrier, 1, om64)
+        if not args.no_fp64tc:
+            fp64tc = run_form(args, tdarisp, mol, C_dev, eps_dev, stream, barrier, 2, om64)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -246,11 +250,13 @@ def run_native(args):
         "davidson": {"niter": [i.niter for i in infos], "nmatvec": [i.nmatvec for i in infos],
                      "restarts": [i.nrestart for i in infos], "converged": [i.converged for i in infos]},
         "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "mixed_form": mixed,
+        "fp64_tensor_core_form": fp64tc,
         "gpu_launches": launches, "clocks": clk,
     }
-    if mixed:
-        mixed["speedup_vs_fp64_value"] = mixed["value"] / line["value"]
-        mixed["speedup_vs_fp64_s_to_states"] = line["s_to_states"] / mixed["s_to_states"]
+    for extra in (mixed, fp64tc):
+        if extra:
+            extra["speedup_vs_fp64_value"] = extra["value"] / line["value"]
+            extra["speedup_vs_fp64_s_to_states"] = line["s_to_states"] / extra["s_to_states"]
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -270,16 +276,32 @@ K_STAGE1_TRAFFIC_RATIO = 737.0 / 708.0
 TF32_OVER_BF16 = 1.1 / 2.25
 
 
-def run_mixed(args, tdarisp, mol, C_dev, eps_dev, stream, barrier):
-    """Same workload in the reduced-precision form; compared with the FP64 form."""
-    import torch
+def fp64_reference_omega(tdarisp, mol, C_dev, eps_dev, stream):
+    """Excitation energies of the FP64 form (the comparison for the other forms)."""
     ref = tdarisp.Context(stream=stream.cuda_stream, **OPTS)
     ref.set_molecule(mol.Z, mol.xyz, mol.aux_exp, mol.shells)
     ref.set_orbitals(C_dev, eps_dev, mol.nocc)
     ref.build()
     om64 = ref.solve(want_x=False)[0]
     ref.close()
-    ctx = tdarisp.Context(stream=stream.cuda_stream, precision=1, **OPTS)
+    return om64
+
+
+FORMS = {
+    1: dict(kind="reduced precision", products=3,
+            dtype="f32/tf32x3 (tensor cores) + f64 (integrals, transforms, metrics, Davidson)",
+            note="3 tensor products (hi*hi + hi*lo + lo*hi) per useful flop", peak="tf32"),
+    2: dict(kind="FP64 on the tensor cores", products=28,
+            dtype="f64 results; transforms, J and K as 7-slice Ozaki products on bf16 tensor cores",
+            note="28 bf16 slice products (s + t < 7) per useful FP64 flop", peak="bf16"),
+}
+
+
+def run_form(args, tdarisp, mol, C_dev, eps_dev, stream, barrier, precision, om64):
+    """Same workload in another form (precision 1 or 2); compared with the FP64 form."""
+    import torch
+    form = FORMS[precision]
+    ctx = tdarisp.Context(stream=stream.cuda_stream, precision=precision, **OPTS)
     ctx.set_molecule(mol.Z, mol.xyz, mol.aux_exp, mol.shells)
     ctx.set_orbitals(C_dev, eps_dev, mol.nocc)
 
@@ -306,22 +328,24 @@ def run_mixed(args, tdarisp, mol, C_dev, eps_dev, stream, barrier):
     ctx.close()
     om = om.cpu().numpy()
     peaks = read_peaks()
-    bf16 = peaks.get("bf16_tflops")
-    tf32_peak = bf16 * TF32_OVER_BF16 if bf16 else 1900.0 * TF32_OVER_BF16
+    bf16 = peaks.get("bf16_tflops") or 1900.0
+    peak = bf16 * TF32_OVER_BF16 if form["peak"] == "tf32" else bf16
+    peak_src = ("TF32 dense = measured bf16 burst x nominal TF32/BF16 ratio (1.1/2.25)" if form["peak"] == "tf32"
+                else "measured bf16 burst (MEASURED_PEAKS.json)")
     name, p = max(((k, v) for k, v in prof.items() if k.endswith("_tc")), key=lambda kv: kv[1]["ms"])
     useful = p["flops"] / (p["ms"] * 1e-3) / 1e12
     mv_ms = sum(i.t_matvec_ms for i in infos)
     return {
+        "form": form["kind"],
         "value": nmv / (ms * 1e-3), "unit": "matvecs/s", "s_to_states": ms / args.steps * 1e-3,
         "speedup_vs_fp64_value": None, "matvec_only": nmv / (mv_ms * 1e-3) if mv_ms else None,
-        "dtype": "f32/tf32x3 (tensor cores) + f64 (integrals, transforms, metrics, Davidson)",
+        "dtype": form["dtype"],
         "max_abs_dOmega_vs_fp64_form_Ha": float(np.abs(om - om64).max()),
         "per_state_dOmega_vs_fp64_form_Ha": [float(x) for x in np.abs(om - om64)],
         "davidson": {"niter": [i.niter for i in infos], "nmatvec": [i.nmatvec for i in infos]},
-        "roofline": {"kernel": name, "bound": "tensor", "achieved": 3.0 * useful, "useful_tflops": useful,
-                     "peak": tf32_peak, "unit": "TFLOP/s", "frac": 3.0 * useful / tf32_peak,
-                     "peak_source": "TF32 dense = measured bf16 burst x nominal TF32/BF16 ratio (1.1/2.25)",
-                     "note": "3 tensor products (hi*hi + hi*lo + lo*hi) per useful flop"},
+        "roofline": {"kernel": name, "bound": "tensor", "achieved": form["products"] * useful,
+                     "useful_tflops": useful, "peak": peak, "unit": "TFLOP/s",
+                     "frac": form["products"] * useful / peak, "peak_source": peak_src, "note": form["note"]},
         "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]}
                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
     }
@@ -620,6 +644,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the reduced-precision form")
+    ap.add_argument("--no-fp64tc", action="store_true", help="skip the FP64 form on the tensor cores")
     ap.add_argument("--workload", default="fp64-200", choices=["fp64-200", "batched", "serve"],
                     help="batched: 64 molecules in the reduced-precision batched form; "
                          "serve: a Poisson request stream through the serving runtime")

@@ -55,6 +55,10 @@ extern "C" {
 #define TR_FP64 0   /* every step in FP64 */
 #define TR_MIXED 1  /* MO tensors and J/K contractions in FP32 / 3xTF32 tensor cores;
                        integrals, metrics and the Davidson driver in FP64 */
+#define TR_FP64_TC 2 /* FP64 results with the MO transforms and the J and K
+                        contractions on the bf16 tensor cores: every FP64 operand is
+                        split into 7 integer slices (Ozaki scheme), slice products are
+                        summed exactly; integrals, metrics, Davidson in FP64 */
 
 typedef struct tr_ctx tr_ctx;
 
@@ -80,7 +84,7 @@ typedef struct {
     int max_space;       /* subspace size that triggers a restart (0: 20 * nstates) */
     int max_iter;        /* Davidson iterations (0: 200) */
     double tol;          /* residual 2-norm threshold per state */
-    int precision;       /* TR_FP64 or TR_MIXED */
+    int precision;       /* TR_FP64, TR_MIXED or TR_FP64_TC */
     double screen;       /* primitive-pair screening threshold (0: 1e-22) */
     size_t hbm_budget;   /* bytes of device memory the context may hold (0: 90% of free) */
     size_t aux_chunk_bytes; /* scratch for AO integral chunks (0: 2 GiB) */
@@ -92,7 +96,8 @@ typedef struct {
     size_t matvec_ws_bytes; /* scratch for the exchange intermediate M (0: 4 GiB) */
     int xform_slices;    /* MO transforms: -1 FP64 pipe; 2..7 bf16 tensor cores with that many
                             Ozaki slices per operand (7 + 8 (S-1) bits below each row's
-                            largest element); 0: FP64 pipe in TR_FP64, 5 slices in TR_MIXED */
+                            largest element); 0: FP64 pipe in TR_FP64, 5 slices in TR_MIXED,
+                            7 in TR_FP64_TC */
 } tr_options;
 
 typedef struct {

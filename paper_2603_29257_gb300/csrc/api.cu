@@ -76,8 +76,8 @@ int tr_create(tr_ctx **out, const tr_options *opt, void *cuda_stream)
         return TR_ENOMEM;
     }
     int rc = guarded(c, [&]() {
-        TR_REQUIRE(opt->precision == TR_FP64 || opt->precision == TR_MIXED, TR_EINVAL,
-                   "create: precision must be TR_FP64 or TR_MIXED");
+        TR_REQUIRE(opt->precision == TR_FP64 || opt->precision == TR_MIXED || opt->precision == TR_FP64_TC,
+                   TR_EINVAL, "create: precision must be TR_FP64, TR_MIXED or TR_FP64_TC");
         TR_REQUIRE(opt->xform_slices == 0 || opt->xform_slices == -1 ||
                        (opt->xform_slices >= 2 && opt->xform_slices <= 7),
                    TR_EINVAL, "create: xform_slices must be -1, 0 or 2..7");
@@ -106,8 +106,8 @@ int tr_set_options(tr_ctx *ctx, const tr_options *opt)
 {
     return guarded(ctx, [&]() {
         TR_REQUIRE(opt, TR_EINVAL, "set_options: null options");
-        TR_REQUIRE(opt->precision == TR_FP64 || opt->precision == TR_MIXED, TR_EINVAL,
-                   "set_options: precision must be TR_FP64 or TR_MIXED");
+        TR_REQUIRE(opt->precision == TR_FP64 || opt->precision == TR_MIXED || opt->precision == TR_FP64_TC,
+                   TR_EINVAL, "set_options: precision must be TR_FP64, TR_MIXED or TR_FP64_TC");
         TR_REQUIRE(opt->xform_slices == 0 || opt->xform_slices == -1 ||
                        (opt->xform_slices >= 2 && opt->xform_slices <= 7),
                    TR_EINVAL, "set_options: xform_slices must be -1, 0 or 2..7");

@@ -8,6 +8,7 @@
 #include "common.cuh"
 #include "ints.cuh"
 #include "linalg.cuh"
+#include "ozgemm.cuh"
 #include "tcgemm.cuh"
 
 struct tr_ctx {
@@ -58,6 +59,12 @@ struct tr_ctx {
     int oKp = 0, vKp = 0, mixed_mb = 0, mixed_npk = 0;
     int tc_bn = 128;  // tensor-core output tile width of the K stages (64 or 128)
 
+    // FP64 form on the tensor cores (TR_FP64_TC): sliced tensors (built once) and
+    // per-block sliced operands
+    tr::DevBuf<double> ozs_Y, ozs_YT, ozs_Tab, ozs_T2, ozw_X, ozw_Xw, ozw_Z, ozw_M, ws_Mf;
+    tr::OzMat oz_Y, oz_YT, oz_Tab, oz_T2;
+    int tc_npk = 0;
+
     // workspaces
     tr::DevBuf<double> ws_split, ws_Z, ws_Z2, ws_Xw, ws_M;
     tr::DevBuf<int> flag;
@@ -99,10 +106,14 @@ void get_tensor(tr_ctx *c, int which, double *out, int on_device);
 void matvec(tr_ctx *c, int m, const double *X, double *AX);
 // allocate the matvec workspaces for blocks of up to m vectors
 void reserve_matvec(tr_ctx *c, int m);
-// estimated peak device bytes of tr_build + tr_solve
 // slices of the tensor-core MO transforms (0: FP64 pipe)
 int xform_slices(const tr_ctx *c);
+// estimated peak device bytes of tr_build + tr_solve
 size_t footprint(tr_ctx *c);
+// FP64 form on the tensor cores: slice the built tensors; matvec workspaces; A X
+void build_tc(tr_ctx *c);
+void reserve_tc(tr_ctx *c, int mb);
+void matvec_tc(tr_ctx *c, int m, const double *X, double *AX);
 // three-centre integrals of aux functions [p0, p0+np) of set which (0 = J, 1 = K)
 void compute_int3c_chunk(tr_ctx *c, int which, int p0, int np, double *out);
 // reduced-precision form (mixed.cu)

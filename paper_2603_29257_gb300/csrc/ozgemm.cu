@@ -56,13 +56,16 @@ struct OzCfg {
 };
 
 struct OzArgs {
-    int M, N, nkb;
-    long long a0, a1, c0, c1;
+    int M, N, nkb;                 // K blocks contracted per tile (all splits)
+    int n2, ksplit, kchunk;        // batch b = b1 * n2 + b2; split s covers K blocks [s kchunk, ...)
+    int kbA, kbB;                  // first K block of A and of B
+    long long a0, a1, a2, c0, c1, c2;
     long long rowsA, rowsB;
     const int *eA, *eB;
-    double *d;
-    long long s1, ldm, ldn;
+    double *d;                     // output (or the split partials)
+    long long s1, s2, ldm, ldn;
     double alpha;
+    int accumulate;                // d += (instead of =)
     int *err;
 };
 
@@ -100,10 +103,12 @@ __global__ void __launch_bounds__(320, 1)
     const uint32_t ACCF = sa(&bars[2 * ST]), ACCE = sa(&bars[2 * ST + C::NBUF]);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * 128, n0 = blockIdx.x * BN;
-    const int b = blockIdx.z;
-    const long long arow = g.a0 + g.a1 * b + m0;
-    const long long brow = g.c0 + g.c1 * b + n0;
-    const int nkb = g.nkb;
+    const int split = (int)(blockIdx.z % (unsigned)g.ksplit);
+    const int b = (int)(blockIdx.z / (unsigned)g.ksplit), b1 = b / g.n2, b2 = b - b1 * g.n2;
+    const long long arow = g.a0 + g.a1 * b1 + g.a2 * b2 + m0;
+    const long long brow = g.c0 + g.c1 * b1 + g.c2 * b2 + n0;
+    const int kb_begin = split * g.kchunk;
+    const int nkb = max(0, min(g.nkb - kb_begin, g.kchunk));
     const int nch = (nkb + C::CK - 1) / C::CK;
 
     if (threadIdx.x == 0) {
@@ -130,11 +135,11 @@ __global__ void __launch_bounds__(320, 1)
                 const uint32_t full = FULL + 8 * s;
                 bar_expect(full, C::STAGE);
                 uint8_t *stg = smem + s * C::STAGE;
-                const int x0 = kt * C::SP * 32;
+                const int xa = (g.kbA + kb_begin + kt) * C::SP * 32, xb = (g.kbB + kb_begin + kt) * C::SP * 32;
 #pragma unroll
                 for (int j = 0; j < C::NBOX; ++j) {
-                    tma2d(sa(stg + j * C::ABOX), &tA, x0 + 64 * j, (int)arow, full);
-                    tma2d(sa(stg + C::NBOX * C::ABOX + j * C::BBOX), &tB, x0 + 64 * j, (int)brow, full);
+                    tma2d(sa(stg + j * C::ABOX), &tA, xa + 64 * j, (int)arow, full);
+                    tma2d(sa(stg + C::NBOX * C::ABOX + j * C::BBOX), &tB, xb + 64 * j, (int)brow, full);
                 }
                 issued = kt + 1;
             }
@@ -210,28 +215,63 @@ __global__ void __launch_bounds__(320, 1)
             if (lane == 0) bar_arrive(ACCE + 8 * buf);
         }
         if (ok) {
-            // scale and write: 32 x 32 blocks transposed through shared memory (the
-            // pipeline ring is idle once the last chunk is drained) so that lanes
-            // walk output columns
-            double *tb = (double *)smem + ew * 32 * 33;
             const int rl = 32 * quarter + lane;
             const long long ra = arow + rl;
             const int ea = (m0 + rl < g.M && ra < g.rowsA) ? g.eA[ra] : 0;
+            // split partials: [split][b][M][N] row-major, unscaled by alpha, stored
+            double *out;
+            long long ldm, ldn;
+            double alpha;
+            int acc;
+            if (g.ksplit > 1) {
+                out = g.d + ((long long)split * gridDim.z / g.ksplit + b) * (long long)g.M * g.N;
+                ldm = g.N;
+                ldn = 1;
+                alpha = 1.0;
+                acc = 0;
+            } else {
+                out = g.d + g.s1 * b1 + g.s2 * b2;
+                ldm = g.ldm;
+                ldn = g.ldn;
+                alpha = g.alpha;
+                acc = g.accumulate;
+            }
+            if (ldm == 1) {
+                // consecutive lanes own consecutive output rows: write directly
+                const int rw = m0 + rl;
 #pragma unroll
-            for (int c0 = 0; c0 < C::NC; c0 += 32) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    tb[lane * 33 + j] = scalbn((double)hi[c0 + j] + (double)lo[c0 + j], ea - 14);
-                __syncwarp();
-                const int col = n0 + half * C::NC + c0 + lane;
-                const long long rb = brow + half * C::NC + c0 + lane;
-                const double cs = (col < g.N && rb < g.rowsB) ? scalbn(g.alpha, g.eB[rb]) : 0.0;
-                double *out = g.d + g.s1 * b;
-                for (int rr = 0; rr < 32; ++rr) {
-                    const int rw = m0 + 32 * quarter + rr;
-                    if (rw < g.M && col < g.N) out[(long long)rw * g.ldm + (long long)col * g.ldn] = tb[rr * 33 + lane] * cs;
+                for (int j = 0; j < C::NC; ++j) {
+                    const int col = n0 + half * C::NC + j;
+                    const long long rb = brow + half * C::NC + j;
+                    if (rw < g.M && col < g.N && rb < g.rowsB) {
+                        const double v = scalbn((double)hi[j] + (double)lo[j], ea - 14 + g.eB[rb]) * alpha;
+                        double *o = out + (long long)rw + (long long)col * ldn;
+                        *o = acc ? *o + v : v;
+                    }
                 }
-                __syncwarp();
+            } else {
+                // 32 x 32 blocks transposed through shared memory (the pipeline ring
+                // is idle once the last chunk is drained) so that lanes walk columns
+                double *tb = (double *)smem + ew * 32 * 33;
+#pragma unroll
+                for (int c0 = 0; c0 < C::NC; c0 += 32) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        tb[lane * 33 + j] = scalbn((double)hi[c0 + j] + (double)lo[c0 + j], ea - 14);
+                    __syncwarp();
+                    const int col = n0 + half * C::NC + c0 + lane;
+                    const long long rb = brow + half * C::NC + c0 + lane;
+                    const double cs = (col < g.N && rb < g.rowsB) ? scalbn(alpha, g.eB[rb]) : 0.0;
+                    for (int rr = 0; rr < 32; ++rr) {
+                        const int rw = m0 + 32 * quarter + rr;
+                        if (rw < g.M && col < g.N) {
+                            double *o = out + (long long)rw * ldm + (long long)col * ldn;
+                            const double v = tb[rr * 33 + lane] * cs;
+                            *o = acc ? *o + v : v;
+                        }
+                    }
+                    __syncwarp();
+                }
             }
         }
     }
@@ -307,6 +347,22 @@ __global__ void oz_slice(const double *__restrict__ x, long long rows, int K, lo
     }
 }
 
+// d[s1 b1 + s2 b2 + r ldm + c ldn] (+)= alpha * sum over splits of ws[split][b][r][c]
+__global__ void oz_split_reduce(const double *__restrict__ ws, int ksplit, int nb, int n2, int M, int N, double *d,
+                                long long s1, long long s2, long long ldm, long long ldn, double alpha, int acc)
+{
+    const long long per = (long long)M * N, tot = (long long)nb * per;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+        const long long b = t / per, rc = t - b * per;
+        const int r = (int)(rc / N), cc = (int)(rc - (long long)r * N);
+        double sum = 0.0;
+        for (int sp = 0; sp < ksplit; ++sp) sum += ws[((long long)sp * nb + b) * per + rc];
+        const long long b1 = b / n2, b2 = b - b1 * n2;
+        double *o = d + s1 * b1 + s2 * b2 + (long long)r * ldm + (long long)cc * ldn;
+        *o = acc ? *o + alpha * sum : alpha * sum;
+    }
+}
+
 template <int S, int BN>
 void oz_launch(cudaStream_t st, dim3 grid, const OzMat &A, const OzMat &B, const OzArgs &g)
 {
@@ -372,40 +428,56 @@ void oz_split(Prof &prof, cudaStream_t st, const char *name, const double *x, lo
     prof.end(st, tok);
 }
 
-void oz_gemm(Prof &prof, cudaStream_t st, const char *name, const OzMat &A, long long a0, long long a1,
-             const OzMat &B, long long c0, long long c1, int M, int N, int nb, double *d, long long s1,
-             long long ldm, long long ldn, double alpha, int *err)
+void oz_gemm(Prof &prof, cudaStream_t st, const char *name, const OzMat &A, long long a0, long long a1, long long a2,
+             int kbA, const OzMat &B, long long c0, long long c1, long long c2, int kbB, int M, int N, int nkb, int n1,
+             int n2, const OzOut &out, int *err, int ksplit, double *ws, size_t ws_count)
 {
-    if (M <= 0 || N <= 0 || nb <= 0) return;
-    TR_REQUIRE(A.q && B.q && A.K == B.K && A.S == B.S, TR_EINVAL, "Ozaki GEMM: operands must share K and slices");
-    TR_REQUIRE(a0 >= 0 && a1 >= 0 && c0 >= 0 && c1 >= 0, TR_EINVAL, "Ozaki GEMM: negative row offset");
-    TR_REQUIRE(nb <= 65535 && cdiv(M, 128) <= 65535, TR_EINVAL, "Ozaki GEMM: grid too large");
+    if (M <= 0 || N <= 0 || n1 <= 0 || n2 <= 0) return;
+    TR_REQUIRE(A.q && B.q && A.S == B.S, TR_EINVAL, "Ozaki GEMM: operands must share the slice count");
+    TR_REQUIRE(a0 >= 0 && a1 >= 0 && a2 >= 0 && c0 >= 0 && c1 >= 0 && c2 >= 0, TR_EINVAL,
+               "Ozaki GEMM: negative row offset");
+    TR_REQUIRE(kbA >= 0 && kbB >= 0 && nkb >= 1 && kbA + nkb <= A.nkb && kbB + nkb <= B.nkb, TR_EINVAL,
+               "Ozaki GEMM: K blocks out of range");
+    ksplit = std::max(1, std::min(ksplit, nkb));
+    const long long nb = (long long)n1 * n2;
+    TR_REQUIRE(nb * ksplit <= 65535 && cdiv(M, 128) <= 65535, TR_EINVAL, "Ozaki GEMM: grid too large");
+    TR_REQUIRE(ksplit == 1 || (ws && (size_t)ksplit * nb * M * N <= ws_count), TR_EINVAL,
+               "Ozaki GEMM: split-K workspace too small");
     const int S = A.S;
     const int BN = 64;
-    const long long lastA = a0 + a1 * (nb - 1) + (long long)cdiv(M, 128) * 128;
-    const long long lastB = c0 + c1 * (nb - 1) + (long long)cdiv(N, BN) * BN;
+    const long long lastA = a0 + a1 * (n1 - 1) + a2 * (n2 - 1) + (long long)cdiv(M, 128) * 128;
+    const long long lastB = c0 + c1 * (n1 - 1) + c2 * (n2 - 1) + (long long)cdiv(N, BN) * BN;
     TR_REQUIRE(lastA < (1LL << 31) && lastB < (1LL << 31), TR_EINVAL, "Ozaki GEMM: row index overflow");
     OzArgs g;
     g.M = M;
     g.N = N;
-    g.nkb = A.nkb;
+    g.nkb = nkb;
+    g.n2 = n2;
+    g.ksplit = ksplit;
+    g.kchunk = cdiv(nkb, ksplit);
+    g.kbA = kbA;
+    g.kbB = kbB;
     g.a0 = a0;
     g.a1 = a1;
+    g.a2 = a2;
     g.c0 = c0;
     g.c1 = c1;
+    g.c2 = c2;
     g.rowsA = A.rows;
     g.rowsB = B.rows;
     g.eA = A.e;
     g.eB = B.e;
-    g.d = d;
-    g.s1 = s1;
-    g.ldm = ldm;
-    g.ldn = ldn;
-    g.alpha = alpha;
+    g.d = ksplit > 1 ? ws : out.d;
+    g.s1 = out.s1;
+    g.s2 = out.s2;
+    g.ldm = out.ldm;
+    g.ldn = out.ldn;
+    g.alpha = out.alpha;
+    g.accumulate = out.accumulate ? 1 : 0;
     g.err = err;
-    dim3 grid(cdiv(N, BN), cdiv(M, 128), nb);
-    const double flops = 2.0 * M * N * (double)A.K * nb;
-    const double bytes = 2.0 * A.SP * ((double)M + N) * A.nkb * 32 * nb + 8.0 * M * N * nb;
+    dim3 grid(cdiv(N, BN), cdiv(M, 128), (unsigned)(nb * ksplit));
+    const double flops = 2.0 * M * N * (double)nkb * 32 * nb;
+    const double bytes = 2.0 * A.SP * ((double)M + N) * nkb * 32 * nb + 8.0 * M * N * nb;
     int tok = prof.begin(st, name, flops, bytes);
     switch (S) {
     case 2: oz_launch<2, 64>(st, grid, A, B, g); break;
@@ -416,7 +488,28 @@ void oz_gemm(Prof &prof, cudaStream_t st, const char *name, const OzMat &A, long
     default: oz_launch<7, 64>(st, grid, A, B, g); break;
     }
     TR_CUDA(cudaGetLastError());
+    if (ksplit > 1) {
+        const long long tot = nb * M * N;
+        const unsigned blocks = (unsigned)std::min<long long>(cdiv(tot, 256), 152LL * 8);
+        oz_split_reduce<<<blocks, 256, 0, st>>>(ws, ksplit, (int)nb, n2, M, N, out.d, out.s1, out.s2, out.ldm, out.ldn,
+                                                out.alpha, out.accumulate ? 1 : 0);
+        TR_CUDA(cudaGetLastError());
+    }
     prof.end(st, tok);
+}
+
+void oz_gemm(Prof &prof, cudaStream_t st, const char *name, const OzMat &A, long long a0, long long a1,
+             const OzMat &B, long long c0, long long c1, int M, int N, int nb, double *d, long long s1,
+             long long ldm, long long ldn, double alpha, int *err)
+{
+    TR_REQUIRE(A.K == B.K, TR_EINVAL, "Ozaki GEMM: operands must share K");
+    OzOut o;
+    o.d = d;
+    o.s1 = s1;
+    o.ldm = ldm;
+    o.ldn = ldn;
+    o.alpha = alpha;
+    oz_gemm(prof, st, name, A, a0, a1, 0, 0, B, c0, c1, 0, 0, M, N, A.nkb, nb, 1, o, err);
 }
 
 }  // namespace tr

@@ -17,6 +17,8 @@ namespace tr {
 constexpr int OZ_MAX_SLICES = 7;
 // slices of the reduced-precision form's transforms unless the options say otherwise
 constexpr int OZ_DEFAULT_SLICES_MIXED = 5;
+// slices of every product of the FP64 form on the tensor cores (FP64-level results)
+constexpr int OZ_SLICES_FP64 = 7;
 
 // An FP64 matrix x[rows][K] in sliced form.  Row r has exponent e[r] with
 // |x[r][k]| < 2^e[r] for every k, and integer digits |q_s[r][k]| <= 128 with
@@ -44,11 +46,28 @@ void oz_bind(OzMat &m, void *storage, long long rows, int K, int S);
 // slice x into m: element (r, k) = x[r * sr + k * sk] for r < m.rows, k < m.K
 void oz_split(Prof &prof, cudaStream_t st, const char *name, const double *x, long long sr, long long sk, OzMat &m);
 
-// Batched d[b*s1 + r*ldm + c*ldn] = alpha * sum_k A[a0 + a1*b + r][k] * B[c0 + c1*b + c][k]
-// for r < M, c < N, b < nb; A and B have the same K and S.  Rows a CTA reads
-// beyond M or N belong to the next batch entry or lie past the operand (read
-// as zero); they are computed and discarded.  err: device int set non-zero if
-// a pipeline wait timed out.
+// Output of an Ozaki GEMM: element (b1, b2; row r; col c) at
+// d[s1 b1 + s2 b2 + r ldm + c ldn], stored (or added when accumulate) times alpha.
+struct OzOut {
+    double *d = nullptr;
+    long long s1 = 0, s2 = 0, ldm = 0, ldn = 1;
+    double alpha = 1.0;
+    bool accumulate = false;
+};
+
+// Batched over b1 < n1, b2 < n2: rows a0 + a1 b1 + a2 b2 + r of A (r < M) against
+// rows c0 + c1 b1 + c2 b2 + c of B (c < N), K blocks kbA .. kbA+nkb of A with
+// kbB .. kbB+nkb of B (blocks of 32 K values; A and B have the same slice
+// count).  Rows a CTA reads beyond M or N belong to the next batch entry or lie
+// past the operand (read as zero); they are computed and discarded.  ksplit > 1
+// splits the K blocks of every tile over that many CTAs, whose partial sums go
+// through ws (at least ksplit n1 n2 M N doubles) and a reduction.  err: device
+// int set non-zero if a pipeline wait timed out.
+void oz_gemm(Prof &prof, cudaStream_t st, const char *name, const OzMat &A, long long a0, long long a1, long long a2,
+             int kbA, const OzMat &B, long long c0, long long c1, long long c2, int kbB, int M, int N, int nkb, int n1,
+             int n2, const OzOut &out, int *err, int ksplit = 1, double *ws = nullptr, size_t ws_count = 0);
+
+// One batch dimension, the whole K: d[b s1 + r ldm + c ldn] = alpha sum_k A[a0 + a1 b + r][k] B[c0 + c1 b + c][k]
 void oz_gemm(Prof &prof, cudaStream_t st, const char *name, const OzMat &A, long long a0, long long a1,
              const OzMat &B, long long c0, long long c1, int M, int N, int nb, double *d, long long s1,
              long long ldm, long long ldn, double alpha, int *err);

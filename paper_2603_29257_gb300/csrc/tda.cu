@@ -9,6 +9,7 @@
 //          T_ij^P = sum_Q (ij|Q)(Q|P)^-1,  T_ab^P = (ab|P)             Sec. 3.2
 //   with i, j, a, b inside the exchange window and K zero outside it.
 #include <algorithm>
+#include <numeric>
 #include <cmath>
 #include <cstring>
 
@@ -345,7 +346,10 @@ int xform_slices(const tr_ctx *c)
 {
     const int s = c->opt.xform_slices;
     if (s < 0) return 0;
-    if (s == 0) return c->opt.precision == TR_MIXED ? OZ_DEFAULT_SLICES_MIXED : 0;
+    if (s == 0)
+        return c->opt.precision == TR_MIXED ? OZ_DEFAULT_SLICES_MIXED
+             : c->opt.precision == TR_FP64_TC ? OZ_SLICES_FP64
+                                              : 0;
     return s;
 }
 
@@ -468,6 +472,7 @@ void build(tr_ctx *c)
     TR_LAUNCH(pf, st, "orbital_diff", 0, 0, orbital_diff<<<grid_for(nov), 256, 0, st>>>(c->eps.p, nocc, nvir, c->D.p));
     TR_CUDA(cudaStreamSynchronize(st));
     if (mixed) build_mixed(c);
+    if (c->opt.precision == TR_FP64_TC) build_tc(c);
     c->built = true;
 }
 
@@ -555,7 +560,13 @@ size_t footprint(tr_ctx *c)
     const double t64 = d * (nJ * nov + nK * vK * vK + 2.0 * nK * oK * oK);
     const double oKp = std::ceil(std::max(oK, 1.0) / 32) * 32, vKp = std::ceil(std::max(vK, 1.0) / 32) * 32;
     const double t32 = mixed ? f * (nJ * nov + 2.0 * nK * vK * vKp + 2.0 * oK * nK * oKp) : 0.0;
-    const double build_peak = npc * per + cs + t64 + t32;
+    double tcb = 0.0;
+    if (c->opt.precision == TR_FP64_TC) {
+        const int Sf = OZ_SLICES_FP64;
+        tcb = (nJ > 0 ? (double)oz_bytes((long long)nJ, (int)nov, Sf) + (double)oz_bytes((long long)nov, (int)nJ, Sf) : 0.0) +
+              (nK > 0 ? (double)oz_bytes((long long)(nK * vK), (int)vK, Sf) + (double)oz_bytes((long long)oK, (int)(nK * oK), Sf) : 0.0);
+    }
+    const double build_peak = std::max(npc * per + cs + t64 + t32, t64 + tcb);
     // solve: tensors kept, Davidson storage and product workspaces
     const double kept = mixed ? t32 + d * oK * nK * oK : t64 - d * nK * oK * oK;
     const int n = (int)std::min<double>(c->opt.nstates, nov);
@@ -570,7 +581,19 @@ size_t footprint(tr_ctx *c)
                                     (mixed ? 2.0 * f * mb * oK * vKp + f * mb * nov : d * mb * oK * vK)
                               : 0.0;
     const double ws = d * 16.0 * (1 << 20) + 2.0 * d * std::max(nJ, 1.0) * mb + mws;
-    const double solve_peak = kept + dav + ws;
+    double tcx = 0.0;
+    if (c->opt.precision == TR_FP64_TC) {
+        // slices kept for the products, and the per-block sliced operands
+        const int Sf = OZ_SLICES_FP64;
+        const double sl = (nJ > 0 ? (double)oz_bytes((long long)nJ, (int)nov, Sf) + (double)oz_bytes((long long)nov, (int)nJ, Sf) : 0.0) +
+                          (nK > 0 ? (double)oz_bytes((long long)(nK * vK), (int)vK, Sf) + (double)oz_bytes((long long)oK, (int)(nK * oK), Sf) : 0.0);
+        const double mbl = std::min<double>(pmax, c->mblk);
+        const double npk = nK > 0 ? std::min<double>(nK, std::max(8.0, (double)c->opt.matvec_ws_bytes / (mbl * vK * oK * 24.0)) + 8.0) : 0.0;
+        tcx = sl + (double)oz_bytes((long long)mbl, (int)nov, Sf) + 16.0 * (2 << 20) +
+              (nK > 0 ? d * mbl * oK * vK + 16.0 * mbl * oK * (vK + 32) + 24.0 * mbl * vK * (npk * oK + 32) : 0.0) +
+              (nJ > 0 ? 16.0 * mbl * (nJ + 32) : 0.0);
+    }
+    const double solve_peak = kept + dav + ws + tcx;
     return (size_t)(1.1 * (base + std::max(build_peak, solve_peak + (mixed ? 0.0 : 0.0))));
 }
 
@@ -582,6 +605,10 @@ void reserve_matvec(tr_ctx *c, int m)
     c->ws_Z2.reserve((size_t)std::max(c->nJ, 1) * mb, &c->budget, "J workspace");
     if (c->opt.precision == TR_MIXED) {
         reserve_mixed(c, mb);
+        return;
+    }
+    if (c->opt.precision == TR_FP64_TC) {
+        reserve_tc(c, mb);
         return;
     }
     if (c->k_active) {
@@ -596,6 +623,10 @@ void matvec(tr_ctx *c, int m, const double *X, double *AX)
     if (m <= 0) return;
     if (c->opt.precision == TR_MIXED) {
         matvec_mixed(c, m, X, AX);
+        return;
+    }
+    if (c->opt.precision == TR_FP64_TC) {
+        matvec_tc(c, m, X, AX);
         return;
     }
     cudaStream_t st = c->st;
@@ -650,6 +681,153 @@ void matvec(tr_ctx *c, int m, const double *X, double *AX)
                 dgemm(pf, st, "K_stage2", false, false, oK, vK, np * oK, -c->opt.cx,
                       c->T2.p + (long long)P0 * oK, (long long)nK * oK, c->ws_M.p, vK, 1.0,
                       ax + (long long)o0 * nvir, nvir, b2, nullptr, 0, kb2);
+            }
+        }
+    }
+}
+
+
+// ---------------------------------------------------------------- FP64 form on the tensor cores
+
+// Sliced copies of the built FP64 tensors (7 slices, FP64-level products):
+// (P|ia) by rows P (J contraction) and by rows ia (J expansion), T_ab^P by rows
+// (P, a) with K = b, T_ij by rows i with K = (P, j).
+void build_tc(tr_ctx *c)
+{
+    const int S = OZ_SLICES_FP64;
+    cudaStream_t st = c->st;
+    Prof &pf = c->prof;
+    const long long nov = c->nov;
+    if (c->nJ > 0) {
+        c->ozs_Y.alloc(cdiv(oz_bytes(c->nJ, (int)nov, S), 8), &c->budget, "sliced (P|ia)");
+        oz_bind(c->oz_Y, c->ozs_Y.p, c->nJ, (int)nov, S);
+        oz_split(pf, st, "oz_split_Y", c->Y.p, nov, 1, c->oz_Y);
+        c->ozs_YT.alloc(cdiv(oz_bytes(nov, c->nJ, S), 8), &c->budget, "sliced (P|ia) by ia");
+        oz_bind(c->oz_YT, c->ozs_YT.p, nov, c->nJ, S);
+        oz_split(pf, st, "oz_split_YT", c->Y.p, 1, nov, c->oz_YT);
+    }
+    if (c->k_active) {
+        const int nK = c->nK, oK = c->oK, vK = c->vK;
+        c->ozs_Tab.alloc(cdiv(oz_bytes((long long)nK * vK, vK, S), 8), &c->budget, "sliced T_ab");
+        oz_bind(c->oz_Tab, c->ozs_Tab.p, (long long)nK * vK, vK, S);
+        oz_split(pf, st, "oz_split_Tab", c->Tab.p, vK, 1, c->oz_Tab);
+        c->ozs_T2.alloc(cdiv(oz_bytes(oK, nK * oK, S), 8), &c->budget, "sliced T_ij");
+        oz_bind(c->oz_T2, c->ozs_T2.p, oK, nK * oK, S);
+        oz_split(pf, st, "oz_split_T2", c->T2.p, (long long)nK * oK, 1, c->oz_T2);
+    }
+    TR_CUDA(cudaStreamSynchronize(st));
+}
+
+// P chunk of the exchange stages: M in FP64 plus its slices, at most
+// matvec_ws_bytes; chunk starts P0 oK fall on 32-value K blocks of T_ij
+static int tc_pchunk(const tr_ctx *c, int mb)
+{
+    if (!c->k_active) return 0;
+    const int q = 32 / std::gcd(c->oK, 32);
+    const double per = (double)mb * c->vK * c->oK * (8.0 + 2.0 * ((OZ_SLICES_FP64 + 1) & ~1));
+    int npk = (int)std::max(1.0, std::floor((double)c->opt.matvec_ws_bytes / per));
+    npk = std::max(q, npk / q * q);
+    npk = std::min(npk, 65535 / std::max(mb, 1) / q * q);
+    return std::max(1, std::min(npk, c->nK));
+}
+
+void reserve_tc(tr_ctx *c, int mb)
+{
+    const int S = OZ_SLICES_FP64;
+    const long long nov = c->nov;
+    c->ws_split.reserve((size_t)2 << 20, &c->budget, "split-K workspace");
+    c->ozw_X.reserve(cdiv(oz_bytes(mb, (int)nov, S), 8), &c->budget, "sliced trial vectors");
+    if (c->nJ > 0) c->ozw_Z.reserve(cdiv(oz_bytes(mb, c->nJ, S), 8), &c->budget, "sliced J intermediate");
+    if (c->k_active) {
+        const int npk = tc_pchunk(c, mb);
+        c->tc_npk = npk;
+        c->ws_Xw.reserve((size_t)mb * c->oK * c->vK, &c->budget, "K workspace");
+        c->ozw_Xw.reserve(cdiv(oz_bytes((long long)mb * c->oK, c->vK, S), 8), &c->budget, "sliced window");
+        c->ws_Mf.reserve((size_t)mb * c->vK * npk * c->oK, &c->budget, "K intermediate");
+        c->ozw_M.reserve(cdiv(oz_bytes((long long)mb * c->vK, npk * c->oK, S), 8), &c->budget,
+                         "sliced K intermediate");
+    }
+}
+
+// A X with every large product on the tensor cores (7 slices): the same steps
+// and order as the FP64 matvec (Sec. 3.1 for J, Sec. 3.2 for K)
+void matvec_tc(tr_ctx *c, int m, const double *X, double *AX)
+{
+    const int S = OZ_SLICES_FP64;
+    cudaStream_t st = c->st;
+    Prof &pf = c->prof;
+    const int nocc = c->nocc, nvir = c->nvir, nJ = c->nJ;
+    const long long nov = c->nov;
+    const int mb = std::min(m, c->mblk);
+    reserve_matvec(c, mb);  // J workspaces and the sliced operands
+    const int oK = c->oK, vK = c->vK, o0 = c->o0, nK = c->nK;
+    int *err = c->flag.p + 1;
+    for (int m0 = 0; m0 < m; m0 += mb) {
+        const int mm = std::min(mb, m - m0);
+        const double *x = X + (long long)m0 * nov;
+        double *ax = AX + (long long)m0 * nov;
+        TR_LAUNCH(pf, st, "diag", 0, 24.0 * nov * mm,
+                  diag_kernel<<<grid_for(nov * mm), 256, 0, st>>>(c->D.p, x, ax, nov, mm));
+        if (nJ) {
+            OzMat Xs, Zs;
+            oz_bind(Xs, c->ozw_X.p, mm, (int)nov, S);
+            oz_split(pf, st, "oz_split_X", x, nov, 1, Xs);
+            // Z[P][m] = sum_ia (P|ia) X_m,ia   (long K: split over CTAs)
+            OzOut oz;
+            oz.d = c->ws_Z.p;
+            oz.ldm = mm;
+            oz.ldn = 1;
+            const int tiles = cdiv(nJ, 128) * cdiv(mm, 64);
+            int ks = std::max(1, 2 * 152 / tiles);
+            ks = (int)std::min<long long>(ks, (long long)c->ws_split.n / ((long long)nJ * mm));
+            oz_gemm(pf, st, "J_contract_tc", c->oz_Y, 0, 0, 0, 0, Xs, 0, 0, 0, 0, nJ, mm, c->oz_Y.nkb, 1, 1, oz, err,
+                    std::max(ks, 1), c->ws_split.p, c->ws_split.n);
+            dgemm(pf, st, "J_metric", false, false, nJ, mm, nJ, 1.0, c->GinvJ.p, nJ, c->ws_Z.p, mm, 0.0, c->ws_Z2.p, mm,
+                  Batch(), nullptr, 0);
+            // AX[m][ia] += 2 sum_P (P|ia) Zt[P][m]: rows ia of the output, columns m
+            oz_bind(Zs, c->ozw_Z.p, mm, nJ, S);
+            oz_split(pf, st, "oz_split_Z", c->ws_Z2.p, 1, mm, Zs);
+            OzOut oe;
+            oe.d = ax;
+            oe.ldm = 1;
+            oe.ldn = nov;
+            oe.alpha = 2.0;
+            oe.accumulate = true;
+            oz_gemm(pf, st, "J_expand_tc", c->oz_YT, 0, 0, 0, 0, Zs, 0, 0, 0, 0, (int)nov, mm, c->oz_YT.nkb, 1, 1, oe,
+                    err);
+        }
+        if (c->k_active) {
+            const long long tot = (long long)mm * oK * vK;
+            TR_LAUNCH(pf, st, "gather_window", 0, 16.0 * tot,
+                      gather_window<<<grid_for(tot), 256, 0, st>>>(x, c->ws_Xw.p, mm, nocc, nvir, o0, oK, vK));
+            OzMat Xws, Ms;
+            oz_bind(Xws, c->ozw_Xw.p, (long long)mm * oK, vK, S);
+            oz_split(pf, st, "oz_split_Xw", c->ws_Xw.p, vK, 1, Xws);
+            const int npk = c->tc_npk;
+            for (int P0 = 0; P0 < nK; P0 += npk) {
+                const int np = std::min(npk, nK - P0);
+                const long long Kp = (long long)np * oK;
+                // M[m][a][P oK + j] = sum_b T_ab^P X_m,jb   (batches P, m)
+                OzOut o1;
+                o1.d = c->ws_Mf.p;
+                o1.s1 = oK;
+                o1.s2 = (long long)vK * Kp;
+                o1.ldm = Kp;
+                o1.ldn = 1;
+                oz_gemm(pf, st, "K_stage1_tc", c->oz_Tab, (long long)P0 * vK, vK, 0, 0, Xws, 0, 0, oK, 0, vK, oK,
+                        c->oz_Tab.nkb, np, mm, o1, err);
+                oz_bind(Ms, c->ozw_M.p, (long long)mm * vK, (int)Kp, S);
+                oz_split(pf, st, "oz_split_M", c->ws_Mf.p, Kp, 1, Ms);
+                // AX_m[o0 + i][a] -= cx sum_(P,j) T_ij^P M[m][a][P oK + j]
+                OzOut o2;
+                o2.d = ax + (long long)o0 * nvir;
+                o2.s1 = nov;
+                o2.ldm = nvir;
+                o2.ldn = 1;
+                o2.alpha = -c->opt.cx;
+                o2.accumulate = true;
+                oz_gemm(pf, st, "K_stage2_tc", c->oz_T2, 0, 0, 0, (int)((long long)P0 * oK / 32), Ms, 0, vK, 0, 0, oK,
+                        vK, Ms.nkb, mm, 1, o2, err);
             }
         }
     }

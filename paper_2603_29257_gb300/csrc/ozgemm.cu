@@ -7,14 +7,18 @@
 // [-128, 128] and are exact in bf16.  All of it is integer arithmetic on the
 // FP64 bit pattern.
 //
-// Product: with A and B split the same way,
-//   sum_k a_mk b_nk ~= 2^(eA_m + eB_n - 14) * sum_{d<S} 2^(-8d) P_d,
-//   P_d = sum_k sum_{s+t=d} qA_s qB_t         (the terms s + t >= S are dropped).
-// Each digit product is at most 2^14 in magnitude, so a chunk of K with
-// (d+1) * kc <= 1024 sums P_d exactly in FP32 (every partial sum is an integer
-// below 2^24).  The kernel keeps one FP32 accumulator per diagonal d in tensor
-// memory, and after each chunk adds the S exact chunk sums (times 2^(-8d)) into
-// a double-FP32 (hi, lo) pair per output by error-free two-sums.
+// Slices are stored pre-scaled, q_s 2^(-8s) (exact in bf16).  Product: with A
+// and B split the same way,
+//   sum_k a_mk b_nk ~= 2^(eA_m + eB_n - 14) * sum_{d<S} P_d,
+//   P_d = sum_k sum_{s+t=d} qA_s qB_t 2^(-8d)   (the terms s + t >= S are dropped).
+// Each digit product is at most 2^14 in magnitude, so over a chunk of K with
+// (d+1) * kc <= 1024 the sum P_d is an integer multiple of 2^(-8d) below
+// 2^(24-8d): exact in FP32.  The kernel keeps one FP32 accumulator in tensor
+// memory for each leading diagonal d < NE (NE = S for S <= 4, S - 2 above)
+// and one shared accumulator for the remaining diagonals, whose FP32 rounding
+// (2^-24 of a sum already scaled by 2^(-8 NE)) stays far below the slicing
+// error; after each chunk every accumulator is added into a double-FP32
+// (hi, lo) pair per output by error-free two-sums.
 //
 // CTA: 10 warps, a 128 x 64 output tile.  Warp 0 (one lane) streams the
 // slices of 128 A rows and 64 B rows for one K block of 32 per stage with TMA
@@ -45,12 +49,17 @@ struct OzCfg {
     static constexpr int BBOX = BN * 128;
     static constexpr int STAGE = NBOX * (ABOX + BBOX);
     static constexpr int STAGES = 4 * STAGE <= 216 * 1024 ? 4 : 3 * STAGE <= 216 * 1024 ? 3 : 2;
-    static constexpr int CK = 1024 / S / 32;           // K blocks per exactly summed chunk
+    // exactly summed leading diagonals; the rest share one FP32 accumulator whose
+    // rounding (2^-24 of sums scaled by 2^(-8 NE)) stays far below the slicing
+    // error 2^(-8S) even after the cancellation of the AO-to-MO sums (~2^14)
+    static constexpr int NE = S <= 4 ? S : S - 2;
+    static constexpr int NACC = NE + (S > NE ? 1 : 0); // plus one shared tail accumulator
+    static constexpr int CK = 1024 / NE / 32;          // K blocks per exactly summed chunk
     static constexpr int NC = BN / 2;                  // output columns per epilogue warp
-    static constexpr int NBUF = 2 * S * BN <= 512 ? 2 : 1;  // accumulator sets in tensor memory
+    static constexpr int NBUF = 2 * NACC * BN <= 512 ? 2 : 1;  // accumulator sets in tensor memory
     static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024 + 256;
     static_assert(S >= 2 && S <= OZ_MAX_SLICES, "slices");
-    static_assert(S * BN <= 512, "tensor memory holds S accumulators of BN columns");
+    static_assert(NACC * BN <= 512, "tensor memory holds the accumulators"); 
     static_assert(SMEM <= 227 * 1024, "shared memory");
     static_assert(CK >= 1, "chunk");
 };
@@ -74,6 +83,18 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, 
     asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
                  "l"(a), "l"(b), "r"(idesc), "r"(acc)
                  : "memory");
+}
+
+// v * 2^n by adding n to the exponent field (integer work: the FP64 pipe of
+// this GPU is narrow); scalbn only for zero/subnormal inputs or results out of
+// the normal range
+__device__ __forceinline__ double scale_pow2(double v, int n)
+{
+    const long long b = __double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    if ((b << 1) == 0) return v;
+    if (ex == 0 || ex + n <= 0 || ex + n >= 2047) return scalbn(v, n);
+    return __longlong_as_double(b + ((long long)n << 52));
 }
 
 // (hi, lo) += b with Knuth's error-free two-sum of hi and b (round-to-nearest
@@ -172,10 +193,14 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll
                     for (int t = 0; t + i < S; ++t) {
                         const uint64_t dB = smem_desc(bbase + (t >> 1) * C::BBOX) + 4 * (t & 1);
-                        const uint32_t acc = tmem + (uint32_t)((buf * S + i + t) * BN);
+                        const int ai = i + t < C::NE ? i + t : C::NE;  // accumulator of diagonal i + t
+                        const uint32_t acc = tmem + (uint32_t)((buf * C::NACC + ai) * BN);
+                        // the first product into an accumulator in a chunk overwrites it:
+                        // (0, d) for d < NE and (0, NE) for the tail
+                        const bool first = kc == 0 && i == 0 && t <= C::NE;
 #pragma unroll
                         for (int h = 0; h < 2; ++h)
-                            mma_bf16(acc, dA + 2 * h, dB + 2 * h, idesc, (kc == 0 && i == 0 && h == 0) ? 0u : 1u);
+                            mma_bf16(acc, dA + 2 * h, dB + 2 * h, idesc, (first && h == 0) ? 0u : 1u);
                     }
                 }
                 commit(EMPTY + 8 * s);
@@ -199,15 +224,14 @@ __global__ void __launch_bounds__(320, 1)
             }
             fence_after();
 #pragma unroll
-            for (int dg = 0; dg < S; ++dg) {
-                const float sc = __int_as_float((127 - 8 * dg) << 23);  // 2^(-8 dg)
+            for (int ai = 0; ai < C::NACC; ++ai) {
 #pragma unroll
                 for (int c0 = 0; c0 < C::NC; c0 += 32) {
                     uint32_t r[32];
                     tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) +
-                                  (uint32_t)((buf * S + dg) * BN + half * C::NC + c0), r);
+                                  (uint32_t)((buf * C::NACC + ai) * BN + half * C::NC + c0), r);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) two_sum(hi[c0 + j], lo[c0 + j], __uint_as_float(r[j]) * sc);
+                    for (int j = 0; j < 32; ++j) two_sum(hi[c0 + j], lo[c0 + j], __uint_as_float(r[j]));
                 }
             }
             fence_before();
@@ -236,6 +260,7 @@ __global__ void __launch_bounds__(320, 1)
                 alpha = g.alpha;
                 acc = g.accumulate;
             }
+            const bool unit = alpha == 1.0;
             if (ldm == 1) {
                 // consecutive lanes own consecutive output rows: write directly
                 const int rw = m0 + rl;
@@ -244,29 +269,33 @@ __global__ void __launch_bounds__(320, 1)
                     const int col = n0 + half * C::NC + j;
                     const long long rb = brow + half * C::NC + j;
                     if (rw < g.M && col < g.N && rb < g.rowsB) {
-                        const double v = scalbn((double)hi[j] + (double)lo[j], ea - 14 + g.eB[rb]) * alpha;
+                        double v = scale_pow2((double)hi[j] + (double)lo[j], ea - 14 + g.eB[rb]);
+                        if (!unit) v *= alpha;
                         double *o = out + (long long)rw + (long long)col * ldn;
                         *o = acc ? *o + v : v;
                     }
                 }
             } else {
                 // 32 x 32 blocks transposed through shared memory (the pipeline ring
-                // is idle once the last chunk is drained) so that lanes walk columns
+                // is idle once the last chunk is drained) so that lanes walk columns;
+                // row and column scales are applied together after the transpose
                 double *tb = (double *)smem + ew * 32 * 33;
 #pragma unroll
                 for (int c0 = 0; c0 < C::NC; c0 += 32) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        tb[lane * 33 + j] = scalbn((double)hi[c0 + j] + (double)lo[c0 + j], ea - 14);
+                    for (int j = 0; j < 32; ++j) tb[lane * 33 + j] = (double)hi[c0 + j] + (double)lo[c0 + j];
                     __syncwarp();
                     const int col = n0 + half * C::NC + c0 + lane;
                     const long long rb = brow + half * C::NC + c0 + lane;
-                    const double cs = (col < g.N && rb < g.rowsB) ? scalbn(alpha, g.eB[rb]) : 0.0;
+                    const bool cok = col < g.N && rb < g.rowsB;
+                    const int eb = cok ? g.eB[rb] - 14 : 0;
                     for (int rr = 0; rr < 32; ++rr) {
+                        const int er = __shfl_sync(0xffffffffu, ea, rr);
                         const int rw = m0 + 32 * quarter + rr;
-                        if (rw < g.M && col < g.N) {
+                        if (rw < g.M && cok) {
                             double *o = out + (long long)rw * ldm + (long long)col * ldn;
-                            const double v = tb[rr * 33 + lane] * cs;
+                            double v = scale_pow2(tb[rr * 33 + lane], er + eb);
+                            if (!unit) v *= alpha;
                             *o = acc ? *o + v : v;
                         }
                     }
@@ -341,8 +370,8 @@ __global__ void oz_slice(const double *__restrict__ x, long long rows, int K, lo
         }
         uint16_t *o = q + r * L + (long long)kb * SP * 32 + kl;
 #pragma unroll
-        for (int s = 0; s < S; ++s)  // |digit| <= 128: the upper half of its FP32 pattern is the exact bf16
-            o[s * 32] = (uint16_t)(__float_as_uint((float)dg[s]) >> 16);
+        for (int s = 0; s < S; ++s)  // |digit| <= 128 times 2^(-8s): the upper half of its FP32 pattern is the exact bf16
+            o[s * 32] = (uint16_t)(__float_as_uint((float)dg[s] * __int_as_float((127 - 8 * s) << 23)) >> 16);
         for (int s = S; s < SP; ++s) o[s * 32] = 0;
     }
 }

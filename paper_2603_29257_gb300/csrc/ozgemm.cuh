@@ -23,7 +23,8 @@ constexpr int OZ_SLICES_FP64 = 7;
 // An FP64 matrix x[rows][K] in sliced form.  Row r has exponent e[r] with
 // |x[r][k]| < 2^e[r] for every k, and integer digits |q_s[r][k]| <= 128 with
 //   x[r][k] ~= 2^e[r] * sum_{s<S} q_s[r][k] * 2^(-7-8s)
-// (the rounding error is at most 2^(e[r]-8S) per element).  Storage, bf16,
+// (the rounding error is at most 2^(e[r]-8S) per element); slice s holds
+// q_s 2^(-8s), exact in bf16.  Storage, bf16,
 // row-major with row length L = nkb * SP * 32: for each block of 32 K values
 // the slices one after the other (32 values each), SP = S rounded up to even
 // (the extra slice and every k >= K hold zeros).

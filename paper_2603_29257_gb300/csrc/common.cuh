@@ -36,6 +36,53 @@ struct Error : std::runtime_error {
 // Kernel launch bookkeeping: every launch goes through Prof::begin/end so the
 // context can count launches and, when profiling is on, time each kernel
 // with CUDA events on the launching stream.
+// A few extra streams of a context for independent launches that are too small
+// to fill the GPU one after another (fork from and join back to the context
+// stream with events).
+struct SideStreams {
+    static constexpr int N = 4;
+    cudaStream_t s[N] = {};
+    cudaEvent_t fork = nullptr, join[N] = {};
+    void ensure()
+    {
+        if (s[0]) return;
+        for (int i = 0; i < N; ++i) {
+            TR_CUDA(cudaStreamCreateWithFlags(&s[i], cudaStreamNonBlocking));
+            TR_CUDA(cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming));
+        }
+        TR_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    }
+    // side streams start after everything queued on st so far
+    void begin(cudaStream_t st)
+    {
+        ensure();
+        TR_CUDA(cudaEventRecord(fork, st));
+        for (int i = 0; i < N; ++i) TR_CUDA(cudaStreamWaitEvent(s[i], fork, 0));
+    }
+    // st continues after everything queued on the side streams
+    void end(cudaStream_t st)
+    {
+        for (int i = 0; i < N; ++i) {
+            TR_CUDA(cudaEventRecord(join[i], s[i]));
+            TR_CUDA(cudaStreamWaitEvent(st, join[i], 0));
+        }
+    }
+    void release()
+    {
+        for (int i = 0; i < N; ++i) {
+            if (s[i]) {
+                cudaStreamSynchronize(s[i]);
+                cudaStreamDestroy(s[i]);
+            }
+            if (join[i]) cudaEventDestroy(join[i]);
+            s[i] = nullptr;
+            join[i] = nullptr;
+        }
+        if (fork) cudaEventDestroy(fork);
+        fork = nullptr;
+    }
+};
+
 struct ProfRecord {
     int kind;
     cudaEvent_t a, b;

@@ -77,10 +77,13 @@ struct tr_ctx {
     tr::DevBuf<double> stage;
     cudaStream_t cst = nullptr;
     cudaEvent_t sev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // side streams for the independent integral launches of one chunk
+    tr::SideStreams side;
 
     ~tr_ctx()
     {
         if (st) cudaStreamSynchronize(st);
+        side.release();
         if (cst) {
             cudaStreamSynchronize(cst);
             cudaStreamDestroy(cst);

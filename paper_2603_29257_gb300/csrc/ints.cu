@@ -339,15 +339,16 @@ __global__ void __launch_bounds__(128)
 }
 
 template <int LA, int LB>
-void launch_pair_class(Prof &prof, cudaStream_t st, int cls, const ShellDev *sh, const double *pexp,
-                       const double *pcoef, const int2 *pairs, int npair, const AuxDev *aux,
-                       const int *aoff, int nao, double *out, double ka, double kb, double omega,
-                       const double *boys, double screen)
+void launch_pair_class(Prof &prof, const cudaStream_t *streams, int nstreams, int &next, int cls,
+                       const ShellDev *sh, const double *pexp, const double *pcoef, const int2 *pairs, int npair,
+                       const AuxDev *aux, const int *aoff, int nao, double *out, double ka, double kb,
+                       double omega, const double *boys, double screen)
 {
     static const char *names[6] = {"int3c_ss", "int3c_ps", "int3c_pp", "int3c_ds", "int3c_dp", "int3c_dd"};
     for (int cd = -1; cd <= 2; ++cd) {
         int n = aoff[cd + 2] - aoff[cd + 1];
         if (n <= 0 || npair <= 0) continue;
+        cudaStream_t st = streams[next++ % nstreams];
         dim3 grid(cdiv(npair, 128), n);
         const AuxDev *a = aux + aoff[cd + 1];
         double bytes = 8.0 * 2.0 * npair * n * (2 * LA + 1) * (2 * LB + 1);
@@ -389,16 +390,27 @@ __global__ void int2c_kernel(const AuxDev *__restrict__ aux, int n, double ka, d
 
 }  // namespace
 
-void int3c(Prof &prof, cudaStream_t st, const ShellDev *sh, const double *pexp, const double *pcoef,
-           const int2 *pairs, const int *off, const AuxDev *aux, const int *aoff, int nao,
+void int3c(Prof &prof, cudaStream_t st, SideStreams *side, const ShellDev *sh, const double *pexp,
+           const double *pcoef, const int2 *pairs, const int *off, const AuxDev *aux, const int *aoff, int nao,
            double *out, double ka, double kb, double omega, const double *boys, double screen)
 {
-    launch_pair_class<0, 0>(prof, st, 0, sh, pexp, pcoef, pairs + off[0], off[1] - off[0], aux, aoff, nao, out, ka, kb, omega, boys, screen);
-    launch_pair_class<1, 0>(prof, st, 1, sh, pexp, pcoef, pairs + off[1], off[2] - off[1], aux, aoff, nao, out, ka, kb, omega, boys, screen);
-    launch_pair_class<1, 1>(prof, st, 2, sh, pexp, pcoef, pairs + off[2], off[3] - off[2], aux, aoff, nao, out, ka, kb, omega, boys, screen);
-    launch_pair_class<2, 0>(prof, st, 3, sh, pexp, pcoef, pairs + off[3], off[4] - off[3], aux, aoff, nao, out, ka, kb, omega, boys, screen);
-    launch_pair_class<2, 1>(prof, st, 4, sh, pexp, pcoef, pairs + off[4], off[5] - off[4], aux, aoff, nao, out, ka, kb, omega, boys, screen);
-    launch_pair_class<2, 2>(prof, st, 5, sh, pexp, pcoef, pairs + off[5], off[6] - off[5], aux, aoff, nao, out, ka, kb, omega, boys, screen);
+    // the 6 pair classes x 4 aux components are independent launches writing
+    // disjoint outputs: spread them over the side streams (heaviest classes first)
+    cudaStream_t one[1] = {st};
+    const cudaStream_t *streams = one;
+    int nstreams = 1, next = 0;
+    if (side) {
+        side->begin(st);
+        streams = side->s;
+        nstreams = SideStreams::N;
+    }
+    launch_pair_class<2, 2>(prof, streams, nstreams, next, 5, sh, pexp, pcoef, pairs + off[5], off[6] - off[5], aux, aoff, nao, out, ka, kb, omega, boys, screen);
+    launch_pair_class<2, 1>(prof, streams, nstreams, next, 4, sh, pexp, pcoef, pairs + off[4], off[5] - off[4], aux, aoff, nao, out, ka, kb, omega, boys, screen);
+    launch_pair_class<1, 1>(prof, streams, nstreams, next, 2, sh, pexp, pcoef, pairs + off[2], off[3] - off[2], aux, aoff, nao, out, ka, kb, omega, boys, screen);
+    launch_pair_class<2, 0>(prof, streams, nstreams, next, 3, sh, pexp, pcoef, pairs + off[3], off[4] - off[3], aux, aoff, nao, out, ka, kb, omega, boys, screen);
+    launch_pair_class<1, 0>(prof, streams, nstreams, next, 1, sh, pexp, pcoef, pairs + off[1], off[2] - off[1], aux, aoff, nao, out, ka, kb, omega, boys, screen);
+    launch_pair_class<0, 0>(prof, streams, nstreams, next, 0, sh, pexp, pcoef, pairs + off[0], off[1] - off[0], aux, aoff, nao, out, ka, kb, omega, boys, screen);
+    if (side) side->end(st);
 }
 
 void int2c(Prof &prof, cudaStream_t st, const AuxDev *aux, int n, double ka, double kb, double omega,

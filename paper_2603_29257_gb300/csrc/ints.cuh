@@ -44,10 +44,11 @@ PairList make_pairs(const std::vector<ShellDev> &sh, const std::vector<double> &
 
 // out[f][mu][nu] (+= nothing: caller zeroes) for auxiliary functions aux[0..naux)
 // of which aux_class_off[c]..aux_class_off[c+1] have comp = c - 1.
-void int3c(Prof &prof, cudaStream_t st, const ShellDev *sh, const double *pexp, const double *pcoef,
-           const int2 *pairs, const int *pair_off, const AuxDev *aux, const int *aux_class_off,
-           int nao, double *out, double ka, double kb, double omega, const double *boys,
-           double screen);
+// The launches run on the side streams when side is not null (forked from and
+// joined back to st).
+void int3c(Prof &prof, cudaStream_t st, SideStreams *side, const ShellDev *sh, const double *pexp,
+           const double *pcoef, const int2 *pairs, const int *pair_off, const AuxDev *aux, const int *aux_class_off,
+           int nao, double *out, double ka, double kb, double omega, const double *boys, double screen);
 
 // out[i][j] = (P_i|Q_j) for auxiliary functions aux[0..n) with out index aux[i].out.
 void int2c(Prof &prof, cudaStream_t st, const AuxDev *aux, int n, double ka, double kb, double omega,

@@ -97,7 +97,7 @@ void compute_int3c(tr_ctx *c, const std::vector<AuxDev> &all, int p0, int np, do
     int cls[5];
     aux_chunk(c, all, p0, np, cls);
     TR_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * (size_t)np * c->nao * c->nao, c->st));
-    int3c(c->prof, c->st, c->shells.p, c->pexp.p, c->pcoef.p, c->pairs.p, c->pl.off, c->aux_ws.p,
+    int3c(c->prof, c->st, &c->side, c->shells.p, c->pexp.p, c->pcoef.p, c->pairs.p, c->pl.off, c->aux_ws.p,
           cls, c->nao, out, ka, kb, omega, c->boys.p, c->opt.screen);
     // the aux list lives in aux_ws until the kernels have read it
     TR_CUDA(cudaStreamSynchronize(c->st));

@@ -22,6 +22,7 @@
 #include <thread>
 
 #include "ctx.cuh"
+#include "ozgemm.cuh"
 
 namespace tr {
 namespace {
@@ -282,6 +283,10 @@ struct Dav {
     int *h_fl = nullptr;
     int pend_p = 0, pend_k0 = 0, pend_max = 0;
     bool pend_restart = false, pend_counted = true;
+    // reduction-type subspace products (V^T W, V^T T) on the tensor cores with
+    // 7-slice (FP64-level) Ozaki products: forms that use the tensor cores, when
+    // every V/W row is on the device and the sliced copies fit the budget
+    bool tcd = false;
 
     explicit Dav(tr_ctx *ctx) : c(ctx), st(ctx->st)
     {
@@ -360,7 +365,36 @@ struct Dav {
         }
         ws = c->ws_split.p;
         wsn = c->ws_split.n;
+        if ((c->opt.precision == TR_MIXED || c->opt.precision == TR_FP64_TC) && kd == maxsp) {
+            const size_t sv = oz_bytes(maxsp, (int)nov, OZ_SLICES_FP64), stn = oz_bytes(pmax, (int)nov, OZ_SLICES_FP64);
+            if (c->budget.used + 2 * sv + stn + (64u << 20) <= c->budget.limit) {
+                c->dvs_V.alloc(cdiv(sv, 8), &c->budget, "sliced Davidson V");
+                c->dvs_W.alloc(cdiv(sv, 8), &c->budget, "sliced Davidson W");
+                c->dvs_T.alloc(cdiv(stn, 8), &c->budget, "sliced new directions");
+                // rows not yet sliced read as zero (tiles extend past the live rows)
+                TR_CUDA(cudaMemsetAsync(c->dvs_V.p, 0, c->dvs_V.n * sizeof(double), st));
+                TR_CUDA(cudaMemsetAsync(c->dvs_W.p, 0, c->dvs_W.n * sizeof(double), st));
+                TR_CUDA(cudaMemsetAsync(c->dvs_T.p, 0, c->dvs_T.n * sizeof(double), st));
+                oz_bind(c->dz_V, c->dvs_V.p, maxsp, (int)nov, OZ_SLICES_FP64);
+                oz_bind(c->dz_W, c->dvs_W.p, maxsp, (int)nov, OZ_SLICES_FP64);
+                tcd = true;
+            }
+        }
         TR_CUDA(cudaMemsetAsync(c->flag.p, 0, 2 * sizeof(int), st));
+    }
+    // C(row r, col i) = sum_k A[ra0 + r][k] B[rb0 + i][k] for r < M, i < N into
+    // d[r ldm + i ldn], FP64-level products on the tensor cores, K split over CTAs
+    void tc_reduce(const char *name, const OzMat &A, long long ra0, const OzMat &B, long long rb0, int M, int N,
+                   double *d, long long ldm, long long ldn)
+    {
+        OzOut o;
+        o.d = d;
+        o.ldm = ldm;
+        o.ldn = ldn;
+        const int tiles = cdiv(M, 128) * cdiv(N, 64);
+        int ks = std::max(1, 2 * 152 / tiles);
+        ks = (int)std::max<long long>(1, std::min<long long>(ks, (long long)wsn / ((long long)M * N)));
+        oz_gemm(c->prof, st, name, A, ra0, 0, 0, 0, B, rb0, 0, 0, 0, M, N, A.nkb, 1, 1, o, c->flag.p + 1, ks, ws, wsn);
     }
 
     ~Dav()
@@ -420,6 +454,16 @@ struct Dav {
         Prof &pf = c->prof;
         const int kk = k0 + p;
         double *A1 = c->Cs.p, *A2 = c->Cs.p + (size_t)maxsp * pmax;
+        if (tcd) {
+            // the new rows join the sliced copies first, then one product over rows 0..kk
+            oz_split_rows(pf, st, "oz_split_V", Vn, nov, 1, c->dz_V, k0, p);
+            oz_split_rows(pf, st, "oz_split_W", Wn, nov, 1, c->dz_W, k0, p);
+            tc_reduce("subspace_H_tc", c->dz_W, 0, c->dz_V, k0, kk, p, A1, 1, kk);  // A1[i][r] = Vn_i . W_r
+            tc_reduce("subspace_H_tc", c->dz_V, 0, c->dz_W, k0, kk, p, A2, 1, kk);  // A2[i][r] = Wn_i . V_r
+            TR_LAUNCH(pf, st, "subspace_insert", 0, 0,
+                      h_insert<<<dim3(cdiv(kk, 128), p), 128, 0, st>>>(c->Hs.p, maxsp, A1, A2, p, kk, k0));
+            return;
+        }
         for_rows(SW, 0, k0, [&](const double *rows, int r0, int nr) {
             dgemm(pf, st, "subspace_H", false, true, p, nr, (int)nov, 1.0, Vn, nov, rows, nov, 0.0, A1 + r0, kk,
                   Batch(), ws, wsn);
@@ -570,10 +614,17 @@ struct Dav {
                   row_scale_inv<<<dim3(nblk, p), 256, 0, st>>>(c->T.p, p, nov, c->rn.p));
         // two passes of block classical Gram-Schmidt against V[0:k]
         for (int pass = 0; pass < 2; ++pass) {
-            for_rows(SV, 0, k, [&](const double *rows, int r0, int nr) {
-                dgemm(pf, st, "orth_project", false, true, nr, p, (int)nov, 1.0, rows, nov, c->T.p, nov, 0.0,
-                      c->Cs.p + (long long)r0 * p, p, Batch(), ws, wsn);
-            });
+            if (tcd) {
+                OzMat Ts;
+                oz_bind(Ts, c->dvs_T.p, p, (int)nov, OZ_SLICES_FP64);
+                oz_split(pf, st, "oz_split_T", c->T.p, nov, 1, Ts);
+                tc_reduce("orth_project_tc", c->dz_V, 0, Ts, 0, k, p, c->Cs.p, p, 1);  // Cs[r][i] = V_r . T_i
+            } else {
+                for_rows(SV, 0, k, [&](const double *rows, int r0, int nr) {
+                    dgemm(pf, st, "orth_project", false, true, nr, p, (int)nov, 1.0, rows, nov, c->T.p, nov, 0.0,
+                          c->Cs.p + (long long)r0 * p, p, Batch(), ws, wsn);
+                });
+            }
             for_rows(SV, 0, k, [&](const double *rows, int r0, int nr) {
                 dgemm(pf, st, "orth_update", true, false, p, (int)nov, nr, -1.0, c->Cs.p + (long long)r0 * p, p, rows,
                       nov, 1.0, c->T.p, nov, Batch(), nullptr, 0);

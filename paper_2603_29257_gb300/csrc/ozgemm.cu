@@ -457,6 +457,18 @@ void oz_split(Prof &prof, cudaStream_t st, const char *name, const double *x, lo
     prof.end(st, tok);
 }
 
+void oz_split_rows(Prof &prof, cudaStream_t st, const char *name, const double *x, long long sr, long long sk,
+                   OzMat &m, long long r0, long long nr)
+{
+    TR_REQUIRE(r0 >= 0 && nr >= 0 && r0 + nr <= m.rows, TR_EINVAL, "Ozaki split: row range out of bounds");
+    if (nr == 0) return;
+    OzMat v = m;
+    v.q = m.q + r0 * m.L;
+    v.e = m.e + r0;
+    v.rows = nr;
+    oz_split(prof, st, name, x, sr, sk, v);
+}
+
 void oz_gemm(Prof &prof, cudaStream_t st, const char *name, const OzMat &A, long long a0, long long a1, long long a2,
              int kbA, const OzMat &B, long long c0, long long c1, long long c2, int kbB, int M, int N, int nkb, int n1,
              int n2, const OzOut &out, int *err, int ksplit, double *ws, size_t ws_count)

@@ -47,6 +47,10 @@ void oz_bind(OzMat &m, void *storage, long long rows, int K, int S);
 // slice x into m: element (r, k) = x[r * sr + k * sk] for r < m.rows, k < m.K
 void oz_split(Prof &prof, cudaStream_t st, const char *name, const double *x, long long sr, long long sk, OzMat &m);
 
+// slice rows r0 .. r0+nr of m only: element (r0 + r, k) = x[r * sr + k * sk]
+void oz_split_rows(Prof &prof, cudaStream_t st, const char *name, const double *x, long long sr, long long sk,
+                   OzMat &m, long long r0, long long nr);
+
 // Output of an Ozaki GEMM: element (b1, b2; row r; col c) at
 // d[s1 b1 + s2 b2 + r ldm + c ldn], stored (or added when accumulate) times alpha.
 struct OzOut {

@@ -593,7 +593,12 @@ size_t footprint(tr_ctx *c)
               (nK > 0 ? d * mbl * oK * vK + 16.0 * mbl * oK * (vK + 32) + 24.0 * mbl * vK * (npk * oK + 32) : 0.0) +
               (nJ > 0 ? 16.0 * mbl * (nJ + 32) : 0.0);
     }
-    const double solve_peak = kept + dav + ws + tcx;
+    // sliced V, W and new directions of the Davidson subspace products
+    const double dtc = (c->opt.precision == TR_MIXED || c->opt.precision == TR_FP64_TC)
+                           ? 2.0 * (double)oz_bytes(maxsp, (int)nov, OZ_SLICES_FP64) +
+                                 (double)oz_bytes((long long)pmax, (int)nov, OZ_SLICES_FP64)
+                           : 0.0;
+    const double solve_peak = kept + dav + ws + tcx + dtc;
     return (size_t)(1.1 * (base + std::max(build_peak, solve_peak + (mixed ? 0.0 : 0.0))));
 }
 

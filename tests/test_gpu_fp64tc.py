@@ -86,4 +86,6 @@ def test_no_exchange_and_no_aux():
     c = _ctx(mol, precision=TC, nstates=3, tol=1e-10, **HYB)
     om, X, rs, info = c.solve()
     D = np.sort((mol.eps[mol.nocc:][None, :] - mol.eps[:mol.nocc][:, None]).reshape(-1))
-    assert np.array_equal(om, D[:3])
+    # the tensor-core products accumulate in double-FP32 pairs (about 48 bits):
+    # FP64-level, not bit-exact (the FP64-pipe form returns these bits exactly)
+    assert np.all(np.abs(om - D[:3]) <= 4e-15 * np.abs(D[:3])), np.abs(om - D[:3]) / np.abs(D[:3])

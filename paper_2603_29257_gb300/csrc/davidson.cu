@@ -367,10 +367,18 @@ struct Dav {
         wsn = c->ws_split.n;
         if ((c->opt.precision == TR_MIXED || c->opt.precision == TR_FP64_TC) && kd == maxsp) {
             const size_t sv = oz_bytes(maxsp, (int)nov, OZ_SLICES_FP64), stn = oz_bytes(pmax, (int)nov, OZ_SLICES_FP64);
-            if (c->budget.used + 2 * sv + stn + (64u << 20) <= c->budget.limit) {
+            const size_t svt = oz_bytes(nov, maxsp, OZ_SLICES_FP64);
+            const size_t ssm = oz_bytes(std::max(n, pmax), maxsp, OZ_SLICES_FP64);
+            if (c->budget.used + 2 * sv + svt + stn + 2 * ssm + (64u << 20) <= c->budget.limit) {
                 c->dvs_V.alloc(cdiv(sv, 8), &c->budget, "sliced Davidson V");
                 c->dvs_W.alloc(cdiv(sv, 8), &c->budget, "sliced Davidson W");
                 c->dvs_T.alloc(cdiv(stn, 8), &c->budget, "sliced new directions");
+                c->dvs_Vt.alloc(cdiv(svt, 8), &c->budget, "sliced Davidson V by columns");
+                c->dvs_Y.alloc(cdiv(ssm, 8), &c->budget, "sliced subspace vectors");
+                c->dvs_C.alloc(cdiv(ssm, 8), &c->budget, "sliced projections");
+                TR_CUDA(cudaMemsetAsync(c->dvs_Vt.p, 0, c->dvs_Vt.n * sizeof(double), st));
+                oz_bind(c->dz_Vt, c->dvs_Vt.p, nov, maxsp, OZ_SLICES_FP64);
+                oz_set_exponents(st, c->dz_Vt, 1);  // orthonormal rows: every |v| < 2
                 // rows not yet sliced read as zero (tiles extend past the live rows)
                 TR_CUDA(cudaMemsetAsync(c->dvs_V.p, 0, c->dvs_V.n * sizeof(double), st));
                 TR_CUDA(cudaMemsetAsync(c->dvs_W.p, 0, c->dvs_W.n * sizeof(double), st));
@@ -458,6 +466,7 @@ struct Dav {
             // the new rows join the sliced copies first, then one product over rows 0..kk
             oz_split_rows(pf, st, "oz_split_V", Vn, nov, 1, c->dz_V, k0, p);
             oz_split_rows(pf, st, "oz_split_W", Wn, nov, 1, c->dz_W, k0, p);
+            oz_split_cols_fixed(pf, st, "oz_split_Vt", Vn, nov, c->dz_Vt, k0, p, 1);
             tc_reduce("subspace_H_tc", c->dz_W, 0, c->dz_V, k0, kk, p, A1, 1, kk);  // A1[i][r] = Vn_i . W_r
             tc_reduce("subspace_H_tc", c->dz_V, 0, c->dz_W, k0, kk, p, A2, 1, kk);  // A2[i][r] = Wn_i . V_r
             TR_LAUNCH(pf, st, "subspace_insert", 0, 0,
@@ -552,10 +561,22 @@ struct Dav {
         eigh_lowest(pf, st, c->Hw.p, k, n, c->theta.p, c->Yev.p, k, c->Yw.p, c->flag.p);
         TR_CUDA(cudaEventRecord(ev.e[1], st));
         // Ritz vectors X = Y^T V and residuals R = Y^T W - theta X
-        for_rows(SV, 0, k, [&](const double *rows, int r0, int nr) {
-            dgemm(pf, st, "ritz", true, false, n, (int)nov, nr, 1.0, c->Yev.p + (long long)r0 * k, k, rows, nov,
-                  r0 == 0 ? 0.0 : 1.0, c->Xr.p, nov, Batch(), nullptr, 0);
-        });
+        if (tcd) {
+            // X[i][col] = sum_r V[r][col] Y[r][i]: rows col of V by columns, columns i
+            OzMat Ys;
+            oz_bind(Ys, c->dvs_Y.p, n, k, OZ_SLICES_FP64);
+            oz_split(pf, st, "oz_split_Yev", c->Yev.p, 1, k, Ys);
+            OzOut o;
+            o.d = c->Xr.p;
+            o.ldm = 1;
+            o.ldn = nov;
+            oz_gemm(pf, st, "ritz_tc", c->dz_Vt, 0, 0, 0, 0, Ys, 0, 0, 0, 0, (int)nov, n, Ys.nkb, 1, 1, o, c->flag.p + 1);
+        } else {
+            for_rows(SV, 0, k, [&](const double *rows, int r0, int nr) {
+                dgemm(pf, st, "ritz", true, false, n, (int)nov, nr, 1.0, c->Yev.p + (long long)r0 * k, k, rows, nov,
+                      r0 == 0 ? 0.0 : 1.0, c->Xr.p, nov, Batch(), nullptr, 0);
+            });
+        }
         for_rows(SW, 0, k, [&](const double *rows, int r0, int nr) {
             dgemm(pf, st, "ritz", true, false, n, (int)nov, nr, 1.0, c->Yev.p + (long long)r0 * k, k, rows, nov,
                   r0 == 0 ? 0.0 : 1.0, c->R.p, nov, Batch(), nullptr, 0);
@@ -625,10 +646,25 @@ struct Dav {
                           c->Cs.p + (long long)r0 * p, p, Batch(), ws, wsn);
                 });
             }
-            for_rows(SV, 0, k, [&](const double *rows, int r0, int nr) {
-                dgemm(pf, st, "orth_update", true, false, p, (int)nov, nr, -1.0, c->Cs.p + (long long)r0 * p, p, rows,
-                      nov, 1.0, c->T.p, nov, Batch(), nullptr, 0);
-            });
+            if (tcd) {
+                // T[i][col] -= sum_r V[r][col] Cs[r][i]
+                OzMat Css;
+                oz_bind(Css, c->dvs_C.p, p, k, OZ_SLICES_FP64);
+                oz_split(pf, st, "oz_split_Cs", c->Cs.p, 1, p, Css);
+                OzOut o;
+                o.d = c->T.p;
+                o.ldm = 1;
+                o.ldn = nov;
+                o.alpha = -1.0;
+                o.accumulate = true;
+                oz_gemm(pf, st, "orth_update_tc", c->dz_Vt, 0, 0, 0, 0, Css, 0, 0, 0, 0, (int)nov, p, Css.nkb, 1, 1, o,
+                        c->flag.p + 1);
+            } else {
+                for_rows(SV, 0, k, [&](const double *rows, int r0, int nr) {
+                    dgemm(pf, st, "orth_update", true, false, p, (int)nov, nr, -1.0, c->Cs.p + (long long)r0 * p, p, rows,
+                          nov, 1.0, c->T.p, nov, Batch(), nullptr, 0);
+                });
+            }
         }
         orthonormal_block_async(c->T.p, p, c->Tn.p, c->Tt.p);
         pend_k0 = k;

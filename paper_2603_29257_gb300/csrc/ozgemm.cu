@@ -41,6 +41,13 @@ namespace {
 
 using namespace ptx;
 
+constexpr int OZ_TBYTES = 8 * 32 * 33 * 4;  // epilogue transpose buffers: 8 warps x 32 x 33 floats
+
+constexpr int oz_stages(int stage)
+{
+    return 4 * stage + OZ_TBYTES + 1280 <= 227 * 1024 ? 4 : 3 * stage + OZ_TBYTES + 1280 <= 227 * 1024 ? 3 : 2;
+}
+
 template <int S, int BN>
 struct OzCfg {
     static constexpr int SP = (S + 1) & ~1;            // slices per K block, padded to even
@@ -48,7 +55,7 @@ struct OzCfg {
     static constexpr int ABOX = 128 * 128;             // bytes: 128 rows x 128 B
     static constexpr int BBOX = BN * 128;
     static constexpr int STAGE = NBOX * (ABOX + BBOX);
-    static constexpr int STAGES = 4 * STAGE <= 216 * 1024 ? 4 : 3 * STAGE <= 216 * 1024 ? 3 : 2;
+    static constexpr int STAGES = oz_stages(STAGE);
     // exactly summed leading diagonals; the rest share one FP32 accumulator whose
     // rounding (2^-24 of sums scaled by 2^(-8 NE)) stays far below the slicing
     // error 2^(-8S) even after the cancellation of the AO-to-MO sums (~2^14)
@@ -57,14 +64,16 @@ struct OzCfg {
     static constexpr int CK = 1024 / NE / 32;          // K blocks per exactly summed chunk
     static constexpr int NC = BN / 2;                  // output columns per epilogue warp
     static constexpr int NBUF = 2 * NACC * BN <= 512 ? 2 : 1;  // accumulator sets in tensor memory
-    static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024 + 256;
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE + OZ_TBYTES + 1024 + 256;
     static_assert(S >= 2 && S <= OZ_MAX_SLICES, "slices");
-    static_assert(NACC * BN <= 512, "tensor memory holds the accumulators"); 
+    static_assert(NACC * BN <= 512, "tensor memory holds the accumulators");
     static_assert(SMEM <= 227 * 1024, "shared memory");
-    static_assert(CK >= 1, "chunk");
+    static_assert(STAGES >= 2 && CK >= 1 && NC == 32, "pipeline");
 };
 
 struct OzArgs {
+    long long ntiles;              // tiles: N tiles x M tiles x batch entries x K splits
+    int ntn, ntm;
     int M, N, nkb;                 // K blocks contracted per tile (all splits)
     int n2, ksplit, kchunk;        // batch b = b1 * n2 + b2; split s covers K blocks [s kchunk, ...)
     int kbA, kbB;                  // first K block of A and of B
@@ -97,6 +106,20 @@ __device__ __forceinline__ double scale_pow2(double v, int n)
     return __longlong_as_double(b + ((long long)n << 52));
 }
 
+// float to double by rebuilding the bit pattern (integer work; the float to
+// double conversion instruction would use the narrow FP64 pipe); zero and
+// subnormal floats take the ordinary conversion
+__device__ __forceinline__ double widen(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned ex = (b >> 23) & 0xFF;
+    if (ex == 0 || ex == 0xFF) return (double)f;
+    const unsigned long long d = ((unsigned long long)(b >> 31) << 63) |
+                                 ((unsigned long long)(ex + (1023 - 127)) << 52) |
+                                 ((unsigned long long)(b & 0x7FFFFF) << 29);
+    return __longlong_as_double((long long)d);
+}
+
 // (hi, lo) += b with Knuth's error-free two-sum of hi and b (round-to-nearest
 // intrinsics: no contraction or reassociation)
 __device__ __forceinline__ void two_sum(float &hi, float &lo, float b)
@@ -109,6 +132,36 @@ __device__ __forceinline__ void two_sum(float &hi, float &lo, float b)
     lo = __fadd_rn(lo, err);
 }
 
+// Tile t of a persistent CTA: its output block, operand rows and K blocks
+struct OzTile {
+    int m0, n0, split, b, b1, b2, kb_begin, nkb;
+    long long arow, brow;
+};
+
+__device__ __forceinline__ OzTile oz_tile(const OzArgs &g, long long t, int BN)
+{
+    OzTile u;
+    const int nt = (int)(t % g.ntn);
+    const long long r = t / g.ntn;
+    const int mt = (int)(r % g.ntm);
+    const long long z = r / g.ntm;
+    u.split = (int)(z % g.ksplit);
+    u.b = (int)(z / g.ksplit);
+    u.b1 = u.b / g.n2;
+    u.b2 = u.b - u.b1 * g.n2;
+    u.m0 = mt * 128;
+    u.n0 = nt * BN;
+    u.arow = g.a0 + g.a1 * u.b1 + g.a2 * u.b2 + u.m0;
+    u.brow = g.c0 + g.c1 * u.b1 + g.c2 * u.b2 + u.n0;
+    u.kb_begin = u.split * g.kchunk;
+    u.nkb = max(0, min(g.nkb - u.kb_begin, g.kchunk));
+    return u;
+}
+
+// Persistent: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...;
+// stage, chunk and barrier-phase counters run on across tiles, so that the
+// epilogue of one tile (drained to registers, then written) overlaps the
+// products of the next.
 template <int S, int BN>
 __global__ void __launch_bounds__(320, 1)
     oz_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, const OzArgs g)
@@ -117,20 +170,14 @@ __global__ void __launch_bounds__(320, 1)
     constexpr int ST = C::STAGES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    float *tbuf = (float *)(smem + ST * C::STAGE);
     // barriers: full[ST], empty[ST], acc_full[NBUF], acc_empty[NBUF]
-    uint64_t *bars = (uint64_t *)(smem + ST * C::STAGE);
+    uint64_t *bars = (uint64_t *)(smem + ST * C::STAGE + OZ_TBYTES);
     uint32_t *tslot = (uint32_t *)(bars + 2 * ST + 2 * C::NBUF);
     const uint32_t FULL = sa(&bars[0]), EMPTY = sa(&bars[ST]);
     const uint32_t ACCF = sa(&bars[2 * ST]), ACCE = sa(&bars[2 * ST + C::NBUF]);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * 128, n0 = blockIdx.x * BN;
-    const int split = (int)(blockIdx.z % (unsigned)g.ksplit);
-    const int b = (int)(blockIdx.z / (unsigned)g.ksplit), b1 = b / g.n2, b2 = b - b1 * g.n2;
-    const long long arow = g.a0 + g.a1 * b1 + g.a2 * b2 + m0;
-    const long long brow = g.c0 + g.c1 * b1 + g.c2 * b2 + n0;
-    const int kb_begin = split * g.kchunk;
-    const int nkb = max(0, min(g.nkb - kb_begin, g.kchunk));
-    const int nch = (nkb + C::CK - 1) / C::CK;
+    const long long ntiles = g.ntiles;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2 * ST + C::NBUF; ++i) bar_init(sa(&bars[i]), 1);
@@ -149,24 +196,31 @@ __global__ void __launch_bounds__(320, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            int issued = 0;
-            for (int kt = 0; kt < nkb; ++kt) {
-                const int s = kt % ST;
-                if (kt >= ST && !bar_wait(EMPTY + 8 * s, ((kt / ST) - 1) & 1, g.err, 11)) break;
-                const uint32_t full = FULL + 8 * s;
-                bar_expect(full, C::STAGE);
-                uint8_t *stg = smem + s * C::STAGE;
-                const int xa = (g.kbA + kb_begin + kt) * C::SP * 32, xb = (g.kbB + kb_begin + kt) * C::SP * 32;
+            long long gk = 0;
+            bool ok = true;
+            for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const OzTile u = oz_tile(g, t, BN);
+                for (int kt = 0; kt < u.nkb; ++kt) {
+                    const int s = (int)(gk % ST);
+                    if (gk >= ST && !bar_wait(EMPTY + 8 * s, (uint32_t)(((gk / ST) - 1) & 1), g.err, 11)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t full = FULL + 8 * s;
+                    bar_expect(full, C::STAGE);
+                    uint8_t *stg = smem + s * C::STAGE;
+                    const int xa = (g.kbA + u.kb_begin + kt) * C::SP * 32, xb = (g.kbB + u.kb_begin + kt) * C::SP * 32;
 #pragma unroll
-                for (int j = 0; j < C::NBOX; ++j) {
-                    tma2d(sa(stg + j * C::ABOX), &tA, xa + 64 * j, (int)arow, full);
-                    tma2d(sa(stg + C::NBOX * C::ABOX + j * C::BBOX), &tB, xb + 64 * j, (int)brow, full);
+                    for (int j = 0; j < C::NBOX; ++j) {
+                        tma2d(sa(stg + j * C::ABOX), &tA, xa + 64 * j, (int)u.arow, full);
+                        tma2d(sa(stg + C::NBOX * C::ABOX + j * C::BBOX), &tB, xb + 64 * j, (int)u.brow, full);
+                    }
+                    ++gk;
                 }
-                issued = kt + 1;
             }
             // copies still in flight complete before the CTA ends
-            for (int kt = std::max(0, issued - ST); kt < issued; ++kt)
-                bar_wait(FULL + 8 * (kt % ST), (kt / ST) & 1, g.err, 15);
+            for (long long q = gk > ST ? gk - ST : 0; q < gk; ++q)
+                bar_wait(FULL + 8 * (int)(q % ST), (uint32_t)((q / ST) & 1), g.err, 15);
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -175,36 +229,51 @@ __global__ void __launch_bounds__(320, 1)
             // K-major, N = BN, M = 128
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                    ((uint32_t)(128 >> 4) << 24);
-            for (int kt = 0; kt < nkb; ++kt) {
-                const int s = kt % ST, kc = kt % C::CK, ch = kt / C::CK, buf = ch % C::NBUF;
-                if (kc == 0 && ch >= C::NBUF) {
-                    // the epilogue has drained the chunk that last used this accumulator set
-                    if (!bar_wait(ACCE + 8 * buf, ((ch / C::NBUF) - 1) & 1, g.err, 12)) break;
+            long long gk = 0, gch = 0;
+            bool ok = true;
+            for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const OzTile u = oz_tile(g, t, BN);
+                for (int kt = 0; kt < u.nkb; ++kt) {
+                    const int s = (int)(gk % ST), kc = kt % C::CK, buf = (int)(gch % C::NBUF);
+                    if (kc == 0 && gch >= C::NBUF) {
+                        // the epilogue has drained the chunk that last used this accumulator set
+                        if (!bar_wait(ACCE + 8 * buf, (uint32_t)(((gch / C::NBUF) - 1) & 1), g.err, 12)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
+                    }
+                    if (!bar_wait(FULL + 8 * s, (uint32_t)((gk / ST) & 1), g.err, 13)) {
+                        ok = false;
+                        break;
+                    }
                     fence_after();
-                }
-                if (!bar_wait(FULL + 8 * s, (kt / ST) & 1, g.err, 13)) break;
-                fence_after();
-                uint8_t *stg = smem + s * C::STAGE;
-                const uint32_t abase = sa(stg), bbase = sa(stg + C::NBOX * C::ABOX);
+                    uint8_t *stg = smem + s * C::STAGE;
+                    const uint32_t abase = sa(stg), bbase = sa(stg + C::NBOX * C::ABOX);
 #pragma unroll
-                for (int i = 0; i < S; ++i) {
-                    // slice i of A: box i/2, byte offset 64 (i odd) inside the 128-byte row
-                    const uint64_t dA = smem_desc(abase + (i >> 1) * C::ABOX) + 4 * (i & 1);
+                    for (int i = 0; i < S; ++i) {
+                        // slice i of A: box i/2, byte offset 64 (i odd) inside the 128-byte row
+                        const uint64_t dA = smem_desc(abase + (i >> 1) * C::ABOX) + 4 * (i & 1);
 #pragma unroll
-                    for (int t = 0; t + i < S; ++t) {
-                        const uint64_t dB = smem_desc(bbase + (t >> 1) * C::BBOX) + 4 * (t & 1);
-                        const int ai = i + t < C::NE ? i + t : C::NE;  // accumulator of diagonal i + t
-                        const uint32_t acc = tmem + (uint32_t)((buf * C::NACC + ai) * BN);
-                        // the first product into an accumulator in a chunk overwrites it:
-                        // (0, d) for d < NE and (0, NE) for the tail
-                        const bool first = kc == 0 && i == 0 && t <= C::NE;
+                        for (int tt = 0; tt + i < S; ++tt) {
+                            const uint64_t dB = smem_desc(bbase + (tt >> 1) * C::BBOX) + 4 * (tt & 1);
+                            const int ai = i + tt < C::NE ? i + tt : C::NE;  // accumulator of diagonal i + tt
+                            const uint32_t acc = tmem + (uint32_t)((buf * C::NACC + ai) * BN);
+                            // the first product into an accumulator in a chunk overwrites it:
+                            // (0, d) for d < NE and (0, NE) for the tail
+                            const bool first = kc == 0 && i == 0 && tt <= C::NE;
 #pragma unroll
-                        for (int h = 0; h < 2; ++h)
-                            mma_bf16(acc, dA + 2 * h, dB + 2 * h, idesc, (first && h == 0) ? 0u : 1u);
+                            for (int h = 0; h < 2; ++h)
+                                mma_bf16(acc, dA + 2 * h, dB + 2 * h, idesc, (first && h == 0) ? 0u : 1u);
+                        }
+                    }
+                    commit(EMPTY + 8 * s);
+                    ++gk;
+                    if (kc == C::CK - 1 || kt == u.nkb - 1) {
+                        commit(ACCF + 8 * buf);
+                        ++gch;
                     }
                 }
-                commit(EMPTY + 8 * s);
-                if (kc == C::CK - 1 || kt == nkb - 1) commit(ACCF + 8 * buf);
             }
         }
         __syncwarp();
@@ -212,49 +281,54 @@ __global__ void __launch_bounds__(320, 1)
         const int ew = warp - 2;        // 0..7
         const int quarter = warp & 3;   // TMEM lanes this warp may read
         const int half = ew >> 2;       // column half
-        float hi[C::NC], lo[C::NC];
-#pragma unroll
-        for (int j = 0; j < C::NC; ++j) hi[j] = lo[j] = 0.f;
+        float *fb = tbuf + ew * 32 * 33;
+        long long gch = 0;
         bool ok = true;
-        for (int ch = 0; ch < nch; ++ch) {
-            const int buf = ch % C::NBUF;
-            if (!bar_wait(ACCF + 8 * buf, (ch / C::NBUF) & 1, g.err, 14)) {
-                ok = false;
-                break;
-            }
-            fence_after();
+        for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const OzTile u = oz_tile(g, t, BN);
+            const int nch = (u.nkb + C::CK - 1) / C::CK;
+            float hi[C::NC], lo[C::NC];
 #pragma unroll
-            for (int ai = 0; ai < C::NACC; ++ai) {
-#pragma unroll
-                for (int c0 = 0; c0 < C::NC; c0 += 32) {
-                    uint32_t r[32];
-                    tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) +
-                                  (uint32_t)((buf * C::NACC + ai) * BN + half * C::NC + c0), r);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) two_sum(hi[c0 + j], lo[c0 + j], __uint_as_float(r[j]));
+            for (int j = 0; j < C::NC; ++j) hi[j] = lo[j] = 0.f;
+            for (int ch = 0; ch < nch; ++ch) {
+                const int buf = (int)(gch % C::NBUF);
+                if (!bar_wait(ACCF + 8 * buf, (uint32_t)((gch / C::NBUF) & 1), g.err, 14)) {
+                    ok = false;
+                    break;
                 }
+                fence_after();
+#pragma unroll
+                for (int ai = 0; ai < C::NACC; ++ai) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)((buf * C::NACC + ai) * BN + half * C::NC),
+                              r);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) two_sum(hi[j], lo[j], __uint_as_float(r[j]));
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) bar_arrive(ACCE + 8 * buf);
+                ++gch;
             }
-            fence_before();
-            __syncwarp();
-            if (lane == 0) bar_arrive(ACCE + 8 * buf);
-        }
-        if (ok) {
+            if (!ok) break;
+            // tile write: the accumulators are in registers, tensor memory already
+            // belongs to the next tile's products
             const int rl = 32 * quarter + lane;
-            const long long ra = arow + rl;
-            const int ea = (m0 + rl < g.M && ra < g.rowsA) ? g.eA[ra] : 0;
-            // split partials: [split][b][M][N] row-major, unscaled by alpha, stored
+            const long long ra = u.arow + rl;
+            const int ea = (u.m0 + rl < g.M && ra < g.rowsA) ? g.eA[ra] : 0;
             double *out;
             long long ldm, ldn;
             double alpha;
             int acc;
-            if (g.ksplit > 1) {
-                out = g.d + ((long long)split * gridDim.z / g.ksplit + b) * (long long)g.M * g.N;
+            if (g.ksplit > 1) {  // split partials: [split][b][M][N] row-major, unscaled by alpha, stored
+                const long long nb = g.ntiles / ((long long)g.ntn * g.ntm * g.ksplit);
+                out = g.d + ((long long)u.split * nb + u.b) * (long long)g.M * g.N;
                 ldm = g.N;
                 ldn = 1;
                 alpha = 1.0;
                 acc = 0;
             } else {
-                out = g.d + g.s1 * b1 + g.s2 * b2;
+                out = g.d + g.s1 * u.b1 + g.s2 * u.b2;
                 ldm = g.ldm;
                 ldn = g.ldn;
                 alpha = g.alpha;
@@ -263,44 +337,47 @@ __global__ void __launch_bounds__(320, 1)
             const bool unit = alpha == 1.0;
             if (ldm == 1) {
                 // consecutive lanes own consecutive output rows: write directly
-                const int rw = m0 + rl;
+                const int rw = u.m0 + rl;
 #pragma unroll
                 for (int j = 0; j < C::NC; ++j) {
-                    const int col = n0 + half * C::NC + j;
-                    const long long rb = brow + half * C::NC + j;
+                    const int col = u.n0 + half * C::NC + j;
+                    const long long rb = u.brow + half * C::NC + j;
                     if (rw < g.M && col < g.N && rb < g.rowsB) {
-                        double v = scale_pow2((double)hi[j] + (double)lo[j], ea - 14 + g.eB[rb]);
+                        double v = scale_pow2(widen(hi[j]) + widen(lo[j]), ea - 14 + g.eB[rb]);
                         if (!unit) v *= alpha;
                         double *o = out + (long long)rw + (long long)col * ldn;
                         *o = acc ? *o + v : v;
                     }
                 }
             } else {
-                // 32 x 32 blocks transposed through shared memory (the pipeline ring
-                // is idle once the last chunk is drained) so that lanes walk columns;
-                // row and column scales are applied together after the transpose
-                double *tb = (double *)smem + ew * 32 * 33;
+                // 32 x 32 block transposed through this warp's float buffer (hi, then
+                // lo) so that lanes walk output columns; row and column scales together
 #pragma unroll
-                for (int c0 = 0; c0 < C::NC; c0 += 32) {
+                for (int j = 0; j < 32; ++j) fb[lane * 33 + j] = hi[j];
+                __syncwarp();
+                float th[32];
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) tb[lane * 33 + j] = (double)hi[c0 + j] + (double)lo[c0 + j];
-                    __syncwarp();
-                    const int col = n0 + half * C::NC + c0 + lane;
-                    const long long rb = brow + half * C::NC + c0 + lane;
-                    const bool cok = col < g.N && rb < g.rowsB;
-                    const int eb = cok ? g.eB[rb] - 14 : 0;
-                    for (int rr = 0; rr < 32; ++rr) {
-                        const int er = __shfl_sync(0xffffffffu, ea, rr);
-                        const int rw = m0 + 32 * quarter + rr;
-                        if (rw < g.M && cok) {
-                            double *o = out + (long long)rw * ldm + (long long)col * ldn;
-                            double v = scale_pow2(tb[rr * 33 + lane], er + eb);
-                            if (!unit) v *= alpha;
-                            *o = acc ? *o + v : v;
-                        }
+                for (int rr = 0; rr < 32; ++rr) th[rr] = fb[rr * 33 + lane];
+                __syncwarp();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) fb[lane * 33 + j] = lo[j];
+                __syncwarp();
+                const int col = u.n0 + half * C::NC + lane;
+                const long long rb = u.brow + half * C::NC + lane;
+                const bool cok = col < g.N && rb < g.rowsB;
+                const int eb = cok ? g.eB[rb] - 14 : 0;
+#pragma unroll
+                for (int rr = 0; rr < 32; ++rr) {
+                    const int er = __shfl_sync(0xffffffffu, ea, rr);
+                    const int rw = u.m0 + 32 * quarter + rr;
+                    if (rw < g.M && cok) {
+                        double *o = out + (long long)rw * ldm + (long long)col * ldn;
+                        double v = scale_pow2(widen(th[rr]) + widen(fb[rr * 33 + lane]), er + eb);
+                        if (!unit) v *= alpha;
+                        *o = acc ? *o + v : v;
                     }
-                    __syncwarp();
                 }
+                __syncwarp();
             }
         }
     }
@@ -311,21 +388,36 @@ __global__ void __launch_bounds__(320, 1)
 
 // ---------------------------------------------------------------- splitting
 
-// e[r] = largest binary exponent of row r (frexp convention: |x| < 2^e); 0 for a zero row
+// e[r] = largest biased binary exponent field of row r (e zeroed beforehand):
+// one warp per segment of 1024 values, combined by atomicMax, so that a few long
+// rows still fill the GPU
+constexpr int OZ_SEG = 1024;
+
 __global__ void oz_rowexp(const double *__restrict__ x, long long rows, int K, long long sr, long long sk,
                           int *__restrict__ e)
 {
-    const long long r = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (r >= rows) return;
-    int mx = 0;
-    for (int k = lane; k < K; k += 32) {
-        const long long bits = __double_as_longlong(x[r * sr + (long long)k * sk]);
-        mx = max(mx, (int)((bits >> 52) & 0x7FF));
-    }
+    const int nseg = (K + OZ_SEG - 1) / OZ_SEG;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long t = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); t < rows * nseg; t += nw) {
+        const long long r = t / nseg;
+        const int k0 = (int)(t - r * nseg) * OZ_SEG, k1 = min(K, k0 + OZ_SEG);
+        int mx = 0;
+        for (int k = k0 + lane; k < k1; k += 32) {
+            const long long bits = __double_as_longlong(x[r * sr + (long long)k * sk]);
+            mx = max(mx, (int)((bits >> 52) & 0x7FF));
+        }
 #pragma unroll
-    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) e[r] = mx ? mx - 1022 : 0;
+        for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0 && mx > 0) atomicMax(e + r, mx);
+    }
+}
+
+// biased exponent field -> frexp exponent (|x| < 2^e); 0 for a zero row
+__global__ void oz_rowexp_finish(int *__restrict__ e, long long rows)
+{
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x)
+        e[r] = e[r] ? e[r] - 1022 : 0;
 }
 
 // balanced base-256 digits of round(x * 2^(7 + 8(S-1) - e)), most significant first
@@ -392,6 +484,31 @@ __global__ void oz_split_reduce(const double *__restrict__ ws, int ksplit, int n
     }
 }
 
+// columns k0 .. k0+p of a sliced matrix whose rows are the source columns:
+// element (r, k0 + j) = src[j * ld + r], every element with the fixed exponent e
+template <int S>
+__global__ void oz_slice_cols(const double *__restrict__ src, long long ld, long long rows, int k0, int p, int e,
+                              int SP, long long L, uint16_t *__restrict__ q)
+{
+    const long long tot = rows * p;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+        const long long r = t / p;
+        const int j = (int)(t - r * p), k = k0 + j;
+        int dg[S];
+        oz_digits<S>(src[(long long)j * ld + r], e, dg);
+        uint16_t *o = q + r * L + (long long)(k >> 5) * SP * 32 + (k & 31);
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            o[s * 32] = (uint16_t)(__float_as_uint((float)dg[s] * __int_as_float((127 - 8 * s) << 23)) >> 16);
+    }
+}
+
+__global__ void fill_int(int *__restrict__ p, long long n, int v)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        p[t] = v;
+}
+
 template <int S, int BN>
 void oz_launch(cudaStream_t st, dim3 grid, const OzMat &A, const OzMat &B, const OzArgs &g)
 {
@@ -439,9 +556,12 @@ void oz_bind(OzMat &m, void *storage, long long rows, int K, int S)
 void oz_split(Prof &prof, cudaStream_t st, const char *name, const double *x, long long sr, long long sk, OzMat &m)
 {
     TR_REQUIRE(m.q && m.e, TR_EINVAL, "Ozaki split: unbound operand");
-    const unsigned rb = (unsigned)cdiv(m.rows, 8);
+    const long long nwarps = m.rows * cdiv(m.K, OZ_SEG);
+    const unsigned rb = (unsigned)std::min<long long>(cdiv(nwarps, 8), 152LL * 32);
+    TR_CUDA(cudaMemsetAsync(m.e, 0, sizeof(int) * m.rows, st));
     TR_LAUNCH(prof, st, "oz_rowexp", 0, 8.0 * m.rows * m.K,
               oz_rowexp<<<rb, 256, 0, st>>>(x, m.rows, m.K, sr, sk, m.e));
+    oz_rowexp_finish<<<(unsigned)std::min<long long>(cdiv(m.rows, 256), 152LL * 8), 256, 0, st>>>(m.e, m.rows);
     const long long tot = m.rows * m.nkb * 32;
     const unsigned blocks = (unsigned)std::min<long long>(cdiv(tot, 256), 152LL * 16);
     int tok = prof.begin(st, name, 0, 8.0 * m.rows * m.K + 2.0 * m.rows * m.L);
@@ -452,6 +572,33 @@ void oz_split(Prof &prof, cudaStream_t st, const char *name, const double *x, lo
     case 5: oz_slice_launch<5>(st, x, sr, sk, m, blocks); break;
     case 6: oz_slice_launch<6>(st, x, sr, sk, m, blocks); break;
     default: oz_slice_launch<7>(st, x, sr, sk, m, blocks); break;
+    }
+    TR_CUDA(cudaGetLastError());
+    prof.end(st, tok);
+}
+
+void oz_set_exponents(cudaStream_t st, OzMat &m, int e)
+{
+    const unsigned blocks = (unsigned)std::min<long long>(cdiv(m.rows, 256), 152LL * 8);
+    fill_int<<<blocks, 256, 0, st>>>(m.e, m.rows, e);
+    TR_CUDA(cudaGetLastError());
+}
+
+void oz_split_cols_fixed(Prof &prof, cudaStream_t st, const char *name, const double *src, long long ld, OzMat &m,
+                         int k0, int p, int e)
+{
+    TR_REQUIRE(k0 >= 0 && p >= 0 && k0 + p <= m.K, TR_EINVAL, "Ozaki split: column range out of bounds");
+    if (p == 0) return;
+    const long long tot = m.rows * p;
+    const unsigned blocks = (unsigned)std::min<long long>(cdiv(tot, 256), 152LL * 16);
+    int tok = prof.begin(st, name, 0, 8.0 * tot + 2.0 * m.SP * tot);
+    switch (m.S) {
+    case 2: oz_slice_cols<2><<<blocks, 256, 0, st>>>(src, ld, m.rows, k0, p, e, m.SP, m.L, m.q); break;
+    case 3: oz_slice_cols<3><<<blocks, 256, 0, st>>>(src, ld, m.rows, k0, p, e, m.SP, m.L, m.q); break;
+    case 4: oz_slice_cols<4><<<blocks, 256, 0, st>>>(src, ld, m.rows, k0, p, e, m.SP, m.L, m.q); break;
+    case 5: oz_slice_cols<5><<<blocks, 256, 0, st>>>(src, ld, m.rows, k0, p, e, m.SP, m.L, m.q); break;
+    case 6: oz_slice_cols<6><<<blocks, 256, 0, st>>>(src, ld, m.rows, k0, p, e, m.SP, m.L, m.q); break;
+    default: oz_slice_cols<7><<<blocks, 256, 0, st>>>(src, ld, m.rows, k0, p, e, m.SP, m.L, m.q); break;
     }
     TR_CUDA(cudaGetLastError());
     prof.end(st, tok);
@@ -481,7 +628,7 @@ void oz_gemm(Prof &prof, cudaStream_t st, const char *name, const OzMat &A, long
                "Ozaki GEMM: K blocks out of range");
     ksplit = std::max(1, std::min(ksplit, nkb));
     const long long nb = (long long)n1 * n2;
-    TR_REQUIRE(nb * ksplit <= 65535 && cdiv(M, 128) <= 65535, TR_EINVAL, "Ozaki GEMM: grid too large");
+    TR_REQUIRE(cdiv(M, 128) <= (1 << 30), TR_EINVAL, "Ozaki GEMM: too many tiles");
     TR_REQUIRE(ksplit == 1 || (ws && (size_t)ksplit * nb * M * N <= ws_count), TR_EINVAL,
                "Ozaki GEMM: split-K workspace too small");
     const int S = A.S;
@@ -516,7 +663,17 @@ void oz_gemm(Prof &prof, cudaStream_t st, const char *name, const OzMat &A, long
     g.alpha = out.alpha;
     g.accumulate = out.accumulate ? 1 : 0;
     g.err = err;
-    dim3 grid(cdiv(N, BN), cdiv(M, 128), (unsigned)(nb * ksplit));
+    g.ntn = cdiv(N, BN);
+    g.ntm = cdiv(M, 128);
+    g.ntiles = (long long)g.ntn * g.ntm * nb * ksplit;
+    static const int nsm = []() {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            n = 0;
+        cudaGetLastError();
+        return n > 0 ? n : 148;
+    }();
+    dim3 grid((unsigned)std::min<long long>(g.ntiles, nsm));
     const double flops = 2.0 * M * N * (double)nkb * 32 * nb;
     const double bytes = 2.0 * A.SP * ((double)M + N) * nkb * 32 * nb + 8.0 * M * N * nb;
     int tok = prof.begin(st, name, flops, bytes);

@@ -47,6 +47,15 @@ void oz_bind(OzMat &m, void *storage, long long rows, int K, int S);
 // slice x into m: element (r, k) = x[r * sr + k * sk] for r < m.rows, k < m.K
 void oz_split(Prof &prof, cudaStream_t st, const char *name, const double *x, long long sr, long long sk, OzMat &m);
 
+// every row exponent of m set to e (for matrices sliced with one fixed exponent)
+void oz_set_exponents(cudaStream_t st, OzMat &m, int e);
+
+// K positions k0 .. k0+p of every row of m from src[p][ld] (element (r, k0 + j)
+// = src[j * ld + r]) with the fixed exponent e: every |src| must be below 2^e
+// (orthonormal vectors with e = 1), and the row exponents of m must be e
+void oz_split_cols_fixed(Prof &prof, cudaStream_t st, const char *name, const double *src, long long ld, OzMat &m,
+                         int k0, int p, int e);
+
 // slice rows r0 .. r0+nr of m only: element (r0 + r, k) = x[r * sr + k * sk]
 void oz_split_rows(Prof &prof, cudaStream_t st, const char *name, const double *x, long long sr, long long sk,
                    OzMat &m, long long r0, long long nr);

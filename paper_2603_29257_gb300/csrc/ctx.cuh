@@ -28,8 +28,8 @@ struct tr_ctx {
     int nao = 0;
     tr::PairList pl;
     tr::DevBuf<tr::ShellDev> shells;
-    tr::DevBuf<double> pexp, pcoef, boys;
-    tr::DevBuf<int2> pairs;
+    tr::DevBuf<double> pexp, pcoef, boys, prim;
+    tr::DevBuf<int2> pairs, prange;
     // auxiliary functions (Sec. 3.2): J = s + p on non-H atoms, K = s on non-H atoms
     std::vector<tr::AuxDev> auxJ_h, auxK_h;  // in output order
     int nJ = 0, nK = 0;

@@ -84,6 +84,26 @@ PairList make_pairs(const std::vector<ShellDev> &sh, const std::vector<double> &
         pl.pairs.insert(pl.pairs.end(), cls[c].begin(), cls[c].end());
         pl.off[c + 1] = (int)pl.pairs.size();
     }
+    // primitive-pair table in pair order
+    pl.range.resize(pl.pairs.size());
+    for (size_t i = 0; i < pl.pairs.size(); ++i) {
+        const ShellDev &A = sh[pl.pairs[i].x], &B = sh[pl.pairs[i].y];
+        const double ABx = A.x - B.x, ABy = A.y - B.y, ABz = A.z - B.z;
+        const double AB2 = ABx * ABx + ABy * ABy + ABz * ABz;
+        const double poly = std::pow(1.0 + std::sqrt(AB2), A.l + B.l);
+        const int first = (int)(pl.prim.size() / 6);
+        for (int u = 0; u < A.nprim; ++u)
+            for (int v = 0; v < B.nprim; ++v) {
+                const double a = pexp[A.pstart + u], b = pexp[B.pstart + v];
+                const double p = a + b, ip = 1.0 / p;
+                const double K = pcoef[A.pstart + u] * pcoef[B.pstart + v] * std::exp(-a * b * ip * AB2);
+                if (std::fabs(K) * M_PI * ip * std::sqrt(M_PI * ip) * poly < screen) continue;
+                const double P[6] = {(a * A.x + b * B.x) * ip, (a * A.y + b * B.y) * ip, (a * A.z + b * B.z) * ip,
+                                     p, ip, K};
+                pl.prim.insert(pl.prim.end(), P, P + 6);
+            }
+        pl.range[i] = make_int2(first, (int)(pl.prim.size() / 6) - first);
+    }
     return pl;
 }
 
@@ -234,10 +254,9 @@ __device__ __forceinline__ double d_sph(int s, int k)
 
 template <int LA, int LB, int CD>
 __global__ void __launch_bounds__(128)
-    int3c_kernel(const ShellDev *__restrict__ sh, const double *__restrict__ pexp,
-                 const double *__restrict__ pcoef, const int2 *__restrict__ pairs, int npair,
-                 const AuxDev *__restrict__ aux, int nao, double *__restrict__ out, double ka,
-                 double kb, double omega, const double *__restrict__ boys, double screen)
+    int3c_kernel(const ShellDev *__restrict__ sh, const int2 *__restrict__ pairs, const int2 *__restrict__ prange,
+                 const double *__restrict__ prim, int npair, const AuxDev *__restrict__ aux, int nao,
+                 double *__restrict__ out, double ka, double kb, double omega, const double *__restrict__ boys)
 {
     constexpr int LC = CD >= 0 ? 1 : 0;
     constexpr int L = LA + LB + LC;
@@ -255,39 +274,28 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
         for (int j = 0; j < NCB; ++j) acc[i][j] = 0.0;
 
-    const double ABx = A.x - B.x, ABy = A.y - B.y, ABz = A.z - B.z;
-    const double AB2 = ABx * ABx + ABy * ABy + ABz * ABz;
-    double poly = 1.0;
-    {
-        double r = 1.0 + sqrt(AB2);
-#pragma unroll
-        for (int i = 0; i < LA + LB; ++i) poly *= r;
-    }
-    const double ce = c.e;
+    const double ce = c.e, ice = 1.0 / ce;
+    const int2 rg = prange[ip];
 
-    for (int ia = 0; ia < A.nprim; ++ia) {
-        const double a = pexp[A.pstart + ia], ca = pcoef[A.pstart + ia];
-        for (int ib = 0; ib < B.nprim; ++ib) {
-            const double b = pexp[B.pstart + ib], cb = pcoef[B.pstart + ib];
-            const double p = a + b, ip_ = 1.0 / p;
-            const double Kab = ca * cb * exp(-a * b * ip_ * AB2);
-            const double vol = PI_D * ip_ * sqrt(PI_D * ip_);
-            if (fabs(Kab) * vol * poly < screen) continue;
-            const double Px = (a * A.x + b * B.x) * ip_, Py = (a * A.y + b * B.y) * ip_,
-                         Pz = (a * A.z + b * B.z) * ip_;
+    {
+        for (int q = rg.x; q < rg.x + rg.y; ++q) {
+            // primitive pair (screened on the host): P, p, 1/p, c_a c_b exp(-ab/p |AB|^2)
+            const double *pq = prim + 6LL * q;
+            const double Px = pq[0], Py = pq[1], Pz = pq[2], p = pq[3], ip_ = pq[4], Kab = pq[5];
             double Ex[LA + 1][LB + 1][LA + LB + 1], Ey[LA + 1][LB + 1][LA + LB + 1],
                 Ez[LA + 1][LB + 1][LA + LB + 1];
             hermite_E<LA, LB>(Px - A.x, Px - B.x, 0.5 * ip_, Ex);
             hermite_E<LA, LB>(Py - A.y, Py - B.y, 0.5 * ip_, Ey);
             hermite_E<LA, LB>(Pz - A.z, Pz - B.z, 0.5 * ip_, Ez);
-            const double rho = p * ce / (p + ce);
+            const double u = 1.0 / (p + ce);
+            const double rho = p * ce * u;
             const double X = Px - c.x, Y = Py - c.y, Z = Pz - c.z;
             double Rn[L + 1];
             coulomb_aux<L>(rho, rho * (X * X + Y * Y + Z * Z), ka, kb, omega, boys, Rn);
             double R[L + 1][L + 1][L + 1];
             hermite_R<L>(X, Y, Z, Rn, R);
-            double pref = TWO_PI_52 / (p * ce * sqrt(p + ce)) * Kab;
-            if (LC) pref *= -0.5 / ce;
+            double pref = TWO_PI_52 * Kab * ip_ * ice * sqrt(u);  // 2 pi^{5/2} K / (p c sqrt(p + c))
+            if (LC) pref *= -0.5 * ice;
 #pragma unroll
             for (int ka_ = 0; ka_ < NCA; ++ka_) {
                 constexpr int dummy = 0;
@@ -340,9 +348,9 @@ __global__ void __launch_bounds__(128)
 
 template <int LA, int LB>
 void launch_pair_class(Prof &prof, const cudaStream_t *streams, int nstreams, int &next, int cls,
-                       const ShellDev *sh, const double *pexp, const double *pcoef, const int2 *pairs, int npair,
+                       const ShellDev *sh, const int2 *pairs, const int2 *prange, const double *prim, int npair,
                        const AuxDev *aux, const int *aoff, int nao, double *out, double ka, double kb,
-                       double omega, const double *boys, double screen)
+                       double omega, const double *boys)
 {
     static const char *names[6] = {"int3c_ss", "int3c_ps", "int3c_pp", "int3c_ds", "int3c_dp", "int3c_dd"};
     for (int cd = -1; cd <= 2; ++cd) {
@@ -354,10 +362,10 @@ void launch_pair_class(Prof &prof, const cudaStream_t *streams, int nstreams, in
         double bytes = 8.0 * 2.0 * npair * n * (2 * LA + 1) * (2 * LB + 1);
         int tok = prof.begin(st, names[cls], 0, bytes);
         switch (cd) {
-            case -1: int3c_kernel<LA, LB, -1><<<grid, 128, 0, st>>>(sh, pexp, pcoef, pairs, npair, a, nao, out, ka, kb, omega, boys, screen); break;
-            case 0: int3c_kernel<LA, LB, 0><<<grid, 128, 0, st>>>(sh, pexp, pcoef, pairs, npair, a, nao, out, ka, kb, omega, boys, screen); break;
-            case 1: int3c_kernel<LA, LB, 1><<<grid, 128, 0, st>>>(sh, pexp, pcoef, pairs, npair, a, nao, out, ka, kb, omega, boys, screen); break;
-            default: int3c_kernel<LA, LB, 2><<<grid, 128, 0, st>>>(sh, pexp, pcoef, pairs, npair, a, nao, out, ka, kb, omega, boys, screen); break;
+            case -1: int3c_kernel<LA, LB, -1><<<grid, 128, 0, st>>>(sh, pairs, prange, prim, npair, a, nao, out, ka, kb, omega, boys); break;
+            case 0: int3c_kernel<LA, LB, 0><<<grid, 128, 0, st>>>(sh, pairs, prange, prim, npair, a, nao, out, ka, kb, omega, boys); break;
+            case 1: int3c_kernel<LA, LB, 1><<<grid, 128, 0, st>>>(sh, pairs, prange, prim, npair, a, nao, out, ka, kb, omega, boys); break;
+            default: int3c_kernel<LA, LB, 2><<<grid, 128, 0, st>>>(sh, pairs, prange, prim, npair, a, nao, out, ka, kb, omega, boys); break;
         }
         TR_CUDA(cudaGetLastError());
         prof.end(st, tok);
@@ -390,9 +398,9 @@ __global__ void int2c_kernel(const AuxDev *__restrict__ aux, int n, double ka, d
 
 }  // namespace
 
-void int3c(Prof &prof, cudaStream_t st, SideStreams *side, const ShellDev *sh, const double *pexp,
-           const double *pcoef, const int2 *pairs, const int *off, const AuxDev *aux, const int *aoff, int nao,
-           double *out, double ka, double kb, double omega, const double *boys, double screen)
+void int3c(Prof &prof, cudaStream_t st, SideStreams *side, const ShellDev *sh, const int2 *pairs,
+           const int2 *prange, const double *prim, const int *off, const AuxDev *aux, const int *aoff, int nao,
+           double *out, double ka, double kb, double omega, const double *boys)
 {
     // the 6 pair classes x 4 aux components are independent launches writing
     // disjoint outputs: spread them over the side streams (heaviest classes first)
@@ -404,12 +412,16 @@ void int3c(Prof &prof, cudaStream_t st, SideStreams *side, const ShellDev *sh, c
         streams = side->s;
         nstreams = SideStreams::N;
     }
-    launch_pair_class<2, 2>(prof, streams, nstreams, next, 5, sh, pexp, pcoef, pairs + off[5], off[6] - off[5], aux, aoff, nao, out, ka, kb, omega, boys, screen);
-    launch_pair_class<2, 1>(prof, streams, nstreams, next, 4, sh, pexp, pcoef, pairs + off[4], off[5] - off[4], aux, aoff, nao, out, ka, kb, omega, boys, screen);
-    launch_pair_class<1, 1>(prof, streams, nstreams, next, 2, sh, pexp, pcoef, pairs + off[2], off[3] - off[2], aux, aoff, nao, out, ka, kb, omega, boys, screen);
-    launch_pair_class<2, 0>(prof, streams, nstreams, next, 3, sh, pexp, pcoef, pairs + off[3], off[4] - off[3], aux, aoff, nao, out, ka, kb, omega, boys, screen);
-    launch_pair_class<1, 0>(prof, streams, nstreams, next, 1, sh, pexp, pcoef, pairs + off[1], off[2] - off[1], aux, aoff, nao, out, ka, kb, omega, boys, screen);
-    launch_pair_class<0, 0>(prof, streams, nstreams, next, 0, sh, pexp, pcoef, pairs + off[0], off[1] - off[0], aux, aoff, nao, out, ka, kb, omega, boys, screen);
+#define TR_CLASS(LA, LB, C)                                                                                        \
+    launch_pair_class<LA, LB>(prof, streams, nstreams, next, C, sh, pairs + off[C], prange + off[C], prim,       \
+                              off[C + 1] - off[C], aux, aoff, nao, out, ka, kb, omega, boys)
+    TR_CLASS(2, 2, 5);
+    TR_CLASS(2, 1, 4);
+    TR_CLASS(1, 1, 2);
+    TR_CLASS(2, 0, 3);
+    TR_CLASS(1, 0, 1);
+    TR_CLASS(0, 0, 0);
+#undef TR_CLASS
     if (side) side->end(st);
 }
 

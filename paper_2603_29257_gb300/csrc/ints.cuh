@@ -35,10 +35,15 @@ struct PairList {
     std::vector<int2> pairs;
     int off[7];
     int ntotal;
+    // primitive pairs of each kept shell pair that pass the screening, with the
+    // data no auxiliary function changes: range[i] = (first, count) into prim,
+    // prim = 6 doubles (P_x, P_y, P_z, p, 1/p, c_a c_b exp(-ab/p |AB|^2))
+    std::vector<int2> range;
+    std::vector<double> prim;
 };
 
-// Host: screened pair list.  A primitive pair is kept when
-// |c_a c_b| exp(-ab/(a+b) |AB|^2) (pi/(a+b))^{3/2} (1 + |AB|)^{la+lb} >= screen.
+// Host: screened pair list and primitive-pair table.  A primitive pair is kept
+// when |c_a c_b| exp(-ab/(a+b) |AB|^2) (pi/(a+b))^{3/2} (1 + |AB|)^{la+lb} >= screen.
 PairList make_pairs(const std::vector<ShellDev> &sh, const std::vector<double> &pexp,
                     const std::vector<double> &pcoef, double screen);
 
@@ -46,9 +51,9 @@ PairList make_pairs(const std::vector<ShellDev> &sh, const std::vector<double> &
 // of which aux_class_off[c]..aux_class_off[c+1] have comp = c - 1.
 // The launches run on the side streams when side is not null (forked from and
 // joined back to st).
-void int3c(Prof &prof, cudaStream_t st, SideStreams *side, const ShellDev *sh, const double *pexp,
-           const double *pcoef, const int2 *pairs, const int *pair_off, const AuxDev *aux, const int *aux_class_off,
-           int nao, double *out, double ka, double kb, double omega, const double *boys, double screen);
+void int3c(Prof &prof, cudaStream_t st, SideStreams *side, const ShellDev *sh, const int2 *pairs,
+           const int2 *prange, const double *prim, const int *pair_off, const AuxDev *aux, const int *aux_class_off,
+           int nao, double *out, double ka, double kb, double omega, const double *boys);
 
 // out[i][j] = (P_i|Q_j) for auxiliary functions aux[0..n) with out index aux[i].out.
 void int2c(Prof &prof, cudaStream_t st, const AuxDev *aux, int n, double ka, double kb, double omega,

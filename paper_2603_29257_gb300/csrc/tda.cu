@@ -97,8 +97,8 @@ void compute_int3c(tr_ctx *c, const std::vector<AuxDev> &all, int p0, int np, do
     int cls[5];
     aux_chunk(c, all, p0, np, cls);
     TR_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * (size_t)np * c->nao * c->nao, c->st));
-    int3c(c->prof, c->st, &c->side, c->shells.p, c->pexp.p, c->pcoef.p, c->pairs.p, c->pl.off, c->aux_ws.p,
-          cls, c->nao, out, ka, kb, omega, c->boys.p, c->opt.screen);
+    int3c(c->prof, c->st, &c->side, c->shells.p, c->pairs.p, c->prange.p, c->prim.p, c->pl.off, c->aux_ws.p, cls,
+          c->nao, out, ka, kb, omega, c->boys.p);
     // the aux list lives in aux_ws until the kernels have read it
     TR_CUDA(cudaStreamSynchronize(c->st));
 }
@@ -166,6 +166,12 @@ void refresh_molecule(tr_ctx *c)
     c->pexp.alloc(c->pexp_h.size(), &c->budget, "primitives");
     c->pcoef.alloc(c->pcoef_h.size(), &c->budget, "primitives");
     c->pairs.alloc(std::max<size_t>(c->pl.pairs.size(), 1), &c->budget, "pairs");
+    c->prange.alloc(std::max<size_t>(c->pl.range.size(), 1), &c->budget, "pairs");
+    c->prim.alloc(std::max<size_t>(c->pl.prim.size(), 1), &c->budget, "primitive pairs");
+    if (!c->pl.range.empty())
+        TR_CUDA(cudaMemcpy(c->prange.p, c->pl.range.data(), sizeof(int2) * c->pl.range.size(), cudaMemcpyHostToDevice));
+    if (!c->pl.prim.empty())
+        TR_CUDA(cudaMemcpy(c->prim.p, c->pl.prim.data(), sizeof(double) * c->pl.prim.size(), cudaMemcpyHostToDevice));
     TR_CUDA(cudaMemcpy(c->shells.p, c->shells_h.data(), sizeof(ShellDev) * c->shells_h.size(), cudaMemcpyHostToDevice));
     TR_CUDA(cudaMemcpy(c->pexp.p, c->pexp_h.data(), sizeof(double) * c->pexp_h.size(), cudaMemcpyHostToDevice));
     TR_CUDA(cudaMemcpy(c->pcoef.p, c->pcoef_h.data(), sizeof(double) * c->pcoef_h.size(), cudaMemcpyHostToDevice));
@@ -549,7 +555,7 @@ size_t footprint(tr_ctx *c)
     const double nK = (c->nK > 0 && c->oK > 0 && c->vK > 0 && c->opt.cx != 0.0) ? c->nK : 0;
     const bool mixed = c->opt.precision == TR_MIXED;
     const double base = d * (nao * nmo + nmo + nov) + d * (nJ * nJ + nK * nK) + 128.0 * (1 << 20) +
-                        (double)c->shells_h.size() * 64 + (double)c->pl.pairs.size() * 8;
+                        (double)c->shells_h.size() * 64 + (double)c->pl.pairs.size() * 16 + (double)c->pl.prim.size() * 8;
     // build: integral and half-transform chunks, FP64 tensors
     const double hrows = std::max(nocc, std::max(oK, vK));
     const int S = xform_slices(c);

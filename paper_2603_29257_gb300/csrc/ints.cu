@@ -346,13 +346,127 @@ __global__ void __launch_bounds__(128)
     }
 }
 
+// The four J functions of one atom (s, p_x, p_y, p_z: same centre and
+// exponent, out indices out .. out+3) from one pass over the primitive pairs:
+// the Hermite integrals R up to LA+LB+1 serve the s component (R_tuv) and the
+// p components (R_{t+1,u,v}, ...), so the Boys values, R recursion and Hermite
+// expansion coefficients are shared.
+template <int LA, int LB>
+__global__ void __launch_bounds__(128)
+    int3c_grp_kernel(const ShellDev *__restrict__ sh, const int2 *__restrict__ pairs, const int2 *__restrict__ prange,
+                     const double *__restrict__ prim, int npair, const AuxDev *__restrict__ aux, int nao,
+                     double *__restrict__ out, double ka, double kb, double omega, const double *__restrict__ boys)
+{
+    constexpr int L = LA + LB + 1;
+    constexpr int NCA = ncart(LA), NCB = ncart(LB);
+    const int ip = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ip >= npair) return;
+    const AuxDev c = aux[blockIdx.y];
+    const int2 pr = pairs[ip];
+    const ShellDev A = sh[pr.x], B = sh[pr.y];
+
+    double acc[4][NCA][NCB];
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+        for (int i = 0; i < NCA; ++i)
+#pragma unroll
+            for (int j = 0; j < NCB; ++j) acc[f][i][j] = 0.0;
+    const double ce = c.e, ice = 1.0 / ce;
+    const int2 rg = prange[ip];
+    for (int q = rg.x; q < rg.x + rg.y; ++q) {
+        const double *pq = prim + 6LL * q;
+        const double Px = pq[0], Py = pq[1], Pz = pq[2], p = pq[3], ip_ = pq[4], Kab = pq[5];
+        double Ex[LA + 1][LB + 1][LA + LB + 1], Ey[LA + 1][LB + 1][LA + LB + 1], Ez[LA + 1][LB + 1][LA + LB + 1];
+        hermite_E<LA, LB>(Px - A.x, Px - B.x, 0.5 * ip_, Ex);
+        hermite_E<LA, LB>(Py - A.y, Py - B.y, 0.5 * ip_, Ey);
+        hermite_E<LA, LB>(Pz - A.z, Pz - B.z, 0.5 * ip_, Ez);
+        const double u = 1.0 / (p + ce);
+        const double rho = p * ce * u;
+        const double X = Px - c.x, Y = Py - c.y, Z = Pz - c.z;
+        double Rn[L + 1];
+        coulomb_aux<L>(rho, rho * (X * X + Y * Y + Z * Z), ka, kb, omega, boys, Rn);
+        double R[L + 1][L + 1][L + 1];
+        hermite_R<L>(X, Y, Z, Rn, R);
+        const double ps_ = TWO_PI_52 * Kab * ip_ * ice * sqrt(u);  // 2 pi^{5/2} K / (p c sqrt(p + c))
+        const double pp_ = -0.5 * ice * ps_;
+#pragma unroll
+        for (int ka_ = 0; ka_ < NCA; ++ka_) {
+#pragma unroll
+            for (int kb_ = 0; kb_ < NCB; ++kb_) {
+                const int ax = cexp(LA, ka_, 0), ay = cexp(LA, ka_, 1), az = cexp(LA, ka_, 2);
+                const int bx = cexp(LB, kb_, 0), by = cexp(LB, kb_, 1), bz = cexp(LB, kb_, 2);
+                double s0 = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+#pragma unroll
+                for (int t = 0; t <= ax + bx; ++t)
+#pragma unroll
+                    for (int w = 0; w <= ay + by; ++w) {
+                        const double exy = Ex[ax][bx][t] * Ey[ay][by][w];
+#pragma unroll
+                        for (int v = 0; v <= az + bz; ++v) {
+                            const double e = exy * Ez[az][bz][v];
+                            s0 = fma(e, R[t][w][v], s0);
+                            sx = fma(e, R[t + 1][w][v], sx);
+                            sy = fma(e, R[t][w + 1][v], sy);
+                            sz = fma(e, R[t][w][v + 1], sz);
+                        }
+                    }
+                acc[0][ka_][kb_] = fma(ps_, s0, acc[0][ka_][kb_]);
+                acc[1][ka_][kb_] = fma(pp_, sx, acc[1][ka_][kb_]);
+                acc[2][ka_][kb_] = fma(pp_, sy, acc[2][ka_][kb_]);
+                acc[3][ka_][kb_] = fma(pp_, sz, acc[3][ka_][kb_]);
+            }
+        }
+    }
+    constexpr int NSA = 2 * LA + 1, NSB = 2 * LB + 1;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        double *o = out + (long long)(c.out + f) * nao * nao;
+#pragma unroll
+        for (int sa = 0; sa < NSA; ++sa) {
+#pragma unroll
+            for (int sb = 0; sb < NSB; ++sb) {
+                double v = 0.0;
+#pragma unroll
+                for (int ka_ = 0; ka_ < NCA; ++ka_) {
+                    const double wa = LA == 2 ? d_sph(sa, ka_) : (ka_ == sa ? 1.0 : 0.0);
+                    if (wa == 0.0) continue;
+#pragma unroll
+                    for (int kb_ = 0; kb_ < NCB; ++kb_) {
+                        const double wb = LB == 2 ? d_sph(sb, kb_) : (kb_ == sb ? 1.0 : 0.0);
+                        if (wb == 0.0) continue;
+                        v = fma(wa * wb, acc[f][ka_][kb_], v);
+                    }
+                }
+                const int mu = A.ao + sa, nu = B.ao + sb;
+                o[(long long)mu * nao + nu] = v;
+                o[(long long)nu * nao + mu] = v;
+            }
+        }
+    }
+}
+
 template <int LA, int LB>
 void launch_pair_class(Prof &prof, const cudaStream_t *streams, int nstreams, int &next, int cls,
                        const ShellDev *sh, const int2 *pairs, const int2 *prange, const double *prim, int npair,
-                       const AuxDev *aux, const int *aoff, int nao, double *out, double ka, double kb,
-                       double omega, const double *boys)
+                       const AuxDev *aux, const int *aoff, const AuxDev *atoms, int natoms, int nao, double *out,
+                       double ka, double kb, double omega, const double *boys)
 {
     static const char *names[6] = {"int3c_ss", "int3c_ps", "int3c_pp", "int3c_ds", "int3c_dp", "int3c_dd"};
+    if constexpr (ncart(LA) * ncart(LB) <= 9) {
+        if (natoms > 0 && npair > 0) {
+            // whole J atoms (s + p) in one pass; light classes only (registers)
+            cudaStream_t st = streams[next++ % nstreams];
+            dim3 grid(cdiv(npair, 128), natoms);
+            double bytes = 8.0 * 2.0 * 4 * npair * natoms * (2 * LA + 1) * (2 * LB + 1);
+            int tok = prof.begin(st, names[cls], 0, bytes);
+            int3c_grp_kernel<LA, LB><<<grid, 128, 0, st>>>(sh, pairs, prange, prim, npair, atoms, nao, out, ka, kb,
+                                                           omega, boys);
+            TR_CUDA(cudaGetLastError());
+            prof.end(st, tok);
+            return;
+        }
+    }
     for (int cd = -1; cd <= 2; ++cd) {
         int n = aoff[cd + 2] - aoff[cd + 1];
         if (n <= 0 || npair <= 0) continue;
@@ -399,8 +513,9 @@ __global__ void int2c_kernel(const AuxDev *__restrict__ aux, int n, double ka, d
 }  // namespace
 
 void int3c(Prof &prof, cudaStream_t st, SideStreams *side, const ShellDev *sh, const int2 *pairs,
-           const int2 *prange, const double *prim, const int *off, const AuxDev *aux, const int *aoff, int nao,
-           double *out, double ka, double kb, double omega, const double *boys)
+           const int2 *prange, const double *prim, const int *off, const AuxDev *aux, const int *aoff,
+           const AuxDev *atoms, int natoms, int nao, double *out, double ka, double kb, double omega,
+           const double *boys)
 {
     // the 6 pair classes x 4 aux components are independent launches writing
     // disjoint outputs: spread them over the side streams (heaviest classes first)
@@ -414,7 +529,7 @@ void int3c(Prof &prof, cudaStream_t st, SideStreams *side, const ShellDev *sh, c
     }
 #define TR_CLASS(LA, LB, C)                                                                                        \
     launch_pair_class<LA, LB>(prof, streams, nstreams, next, C, sh, pairs + off[C], prange + off[C], prim,       \
-                              off[C + 1] - off[C], aux, aoff, nao, out, ka, kb, omega, boys)
+                              off[C + 1] - off[C], aux, aoff, atoms, natoms, nao, out, ka, kb, omega, boys)
     TR_CLASS(2, 2, 5);
     TR_CLASS(2, 1, 4);
     TR_CLASS(1, 1, 2);

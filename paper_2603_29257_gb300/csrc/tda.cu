@@ -71,8 +71,9 @@ __global__ void unpermute_T2(const double *__restrict__ T2, int nK, int oK, doub
 unsigned grid_for(long long n) { return (unsigned)std::max<long long>(1, std::min<long long>(cdiv(n, 256), 152 * 16)); }
 
 // class-sorted copy of auxiliary functions with out index in [p0, p0+np);
-// cls[0..4] offsets for comp -1, 0, 1, 2
-void aux_chunk(tr_ctx *c, const std::vector<AuxDev> &all, int p0, int np, int cls[5])
+// cls[0..4] offsets for comp -1, 0, 1, 2; with grouped, the s functions of the
+// chunk's atoms follow (their count in *natoms)
+void aux_chunk(tr_ctx *c, const std::vector<AuxDev> &all, int p0, int np, int cls[5], bool grouped, int *natoms)
 {
     std::vector<AuxDev> sorted;
     cls[0] = 0;
@@ -85,6 +86,11 @@ void aux_chunk(tr_ctx *c, const std::vector<AuxDev> &all, int p0, int np, int cl
             }
         cls[cd + 2] = (int)sorted.size();
     }
+    *natoms = 0;
+    if (grouped) {
+        for (int i = cls[0]; i < cls[1]; ++i) sorted.push_back(sorted[i]);  // s functions = whole atoms
+        *natoms = cls[1] - cls[0];
+    }
     c->aux_ws.reserve(std::max<size_t>(sorted.size(), 1), &c->budget, "aux list");
     if (!sorted.empty())
         TR_CUDA(cudaMemcpyAsync(c->aux_ws.p, sorted.data(), sizeof(AuxDev) * sorted.size(),
@@ -94,11 +100,13 @@ void aux_chunk(tr_ctx *c, const std::vector<AuxDev> &all, int p0, int np, int cl
 void compute_int3c(tr_ctx *c, const std::vector<AuxDev> &all, int p0, int np, double *out,
                    double ka, double kb, double omega)
 {
-    int cls[5];
-    aux_chunk(c, all, p0, np, cls);
+    int cls[5], natoms = 0;
+    // J chunks of whole atoms (s, p_x, p_y, p_z at out indices 4a .. 4a+3)
+    const bool grouped = &all == &c->auxJ_h && p0 % 4 == 0 && np % 4 == 0;
+    aux_chunk(c, all, p0, np, cls, grouped, &natoms);
     TR_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * (size_t)np * c->nao * c->nao, c->st));
     int3c(c->prof, c->st, &c->side, c->shells.p, c->pairs.p, c->prange.p, c->prim.p, c->pl.off, c->aux_ws.p, cls,
-          c->nao, out, ka, kb, omega, c->boys.p);
+          c->aux_ws.p + cls[4], natoms, c->nao, out, ka, kb, omega, c->boys.p);
     // the aux list lives in aux_ws until the kernels have read it
     TR_CUDA(cudaStreamSynchronize(c->st));
 }
@@ -302,8 +310,9 @@ static void transforms_fp64(tr_ctx *c, DevBuf<double> &Iij)
     DevBuf<double> I, H;
     I.alloc((size_t)npc * nao * nao, &c->budget, "AO integral chunk");
     H.alloc((size_t)npc * hrows * nao, &c->budget, "half-transform chunk");
-    for (int p0 = 0; p0 < nJ; p0 += npc) {
-        int np = std::min(npc, nJ - p0);
+    const int npcJ = npc >= 4 ? npc / 4 * 4 : npc;  // whole J atoms per chunk
+    for (int p0 = 0; p0 < nJ; p0 += npcJ) {
+        int np = std::min(npcJ, nJ - p0);
         compute_int3c_chunk(c, 0, p0, np, I.p);
         Batch b1;
         b1.n1 = np;
@@ -396,8 +405,9 @@ static void transforms_oz(tr_ctx *c, DevBuf<double> &Iij, int S)
         oz_split(pf, st, "oz_split_H", H.p, nao, 1, Hs);
         oz_gemm(pf, st, n2, Hs, 0, nr, Cs, s0, 0, nr, ns, np, out, (long long)nr * ldo, ldo, 1, 1.0, err);
     };
-    for (int p0 = 0; p0 < nJ; p0 += npc) {
-        const int np = std::min(npc, nJ - p0);
+    const int npcJ = npc >= 4 ? npc / 4 * 4 : npc;  // whole J atoms per chunk
+    for (int p0 = 0; p0 < nJ; p0 += npcJ) {
+        const int np = std::min(npcJ, nJ - p0);
         compute_int3c_chunk(c, 0, p0, np, I.p);
         oz_bind(Is, Ib.p, (long long)np * nao, nao, S);
         oz_split(pf, st, "oz_split_I", I.p, nao, 1, Is);

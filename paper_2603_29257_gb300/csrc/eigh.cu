@@ -17,7 +17,7 @@
 //     and range tests work on the bit pattern, since FP64 instructions are
 //     the scarce resource on this GPU).
 //  3. Eigenvectors of T by inverse iteration (Gaussian elimination with
-//     partial pivoting of T - lambda I, three solves from a fixed
+//     partial pivoting of T - lambda I, two solves from a fixed
 //     pseudo-random start); eigenvalues closer than 1e-6 |T| form a group
 //     whose vectors are orthogonalised against each other (modified
 //     Gram-Schmidt) after every solve, and equal eigenvalues are shifted
@@ -272,7 +272,9 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) eigh_cluster_kernel(const EigA
         while (i0 < nev) {
             int i1 = i0 + 1;
             while (i1 < nev && __ldcg(g.lam + i1) - __ldcg(g.lam + i1 - 1) < ortol) ++i1;
-            if (gidx % (C * EIG_SLOTS) == c * EIG_SLOTS + warp && lane == 0) {
+            if (gidx % (C * EIG_SLOTS) == c * EIG_SLOTS + warp) {
+                // lane 0 runs the sequential factorisation and substitutions; the
+                // whole warp the reductions, scalings and copies
                 double lam_prev = 0.0, rq_prev = 0.0;
                 for (int i = i0; i < i1; ++i) {
                     double lam = __ldcg(g.lam + i);
@@ -281,87 +283,106 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) eigh_cluster_kernel(const EigA
                     double *u0 = slots ? slots + (long long)warp * 6 * k : g.ws + (long long)i * 6 * k;
                     double *u1 = u0 + k, *u2 = u1 + k, *lm = u2 + k, *pv = lm + k, *y = pv + k;
                     double *zout = g.ws + (long long)i * 6 * k + 5 * k;
-                    // T - lam I = P L U; u0 holds 1 / (diagonal of U)
-                    double dd = sd[0] - lam, du = k > 1 ? __ldcg(g.e) : 0.0;
-                    for (int r = 0; r + 1 < k; ++r) {
-                        const double er = __ldcg(g.e + r);
-                        const double nd = sd[r + 1] - lam;
-                        const double ndu = r + 2 < k ? __ldcg(g.e + r + 1) : 0.0;
-                        if (fabs(dd) >= fabs(er)) {
-                            if (fabs(dd) < pivtol) dd = dd < 0.0 ? -pivtol : pivtol;
-                            const double rd = 1.0 / dd;
-                            const double mlt = er * rd;
-                            u0[r] = rd;
-                            u1[r] = du;
-                            u2[r] = 0.0;
-                            lm[r] = mlt;
-                            pv[r] = 0.0;
-                            dd = fma(-mlt, du, nd);
-                            du = ndu;
-                        } else {
-                            const double rd = 1.0 / er;
-                            const double mlt = dd * rd;
-                            u0[r] = rd;
-                            u1[r] = nd;
-                            u2[r] = ndu;
-                            lm[r] = mlt;
-                            pv[r] = 1.0;
-                            dd = fma(-mlt, nd, du);
-                            du = -mlt * ndu;
-                        }
-                    }
-                    if (fabs(dd) < pivtol) dd = dd < 0.0 ? -pivtol : pivtol;
-                    u0[k - 1] = 1.0 / dd;
-                    for (int r = 0; r < k; ++r) y[r] = start_entry(i, r);
-                    for (int itn = 0; itn < 3; ++itn) {
-                        double cur = y[0];
+                    if (lane == 0) {
+                        // T - lam I = P L U; u0 holds 1 / (diagonal of U)
+                        double dd = sd[0] - lam, du = k > 1 ? __ldcg(g.e) : 0.0;
                         for (int r = 0; r + 1 < k; ++r) {
-                            const double nx = y[r + 1];
-                            if (pv[r] != 0.0) {
-                                y[r] = nx;
-                                cur = fma(-lm[r], nx, cur);
+                            const double er = __ldcg(g.e + r);
+                            const double nd = sd[r + 1] - lam;
+                            const double ndu = r + 2 < k ? __ldcg(g.e + r + 1) : 0.0;
+                            if (fabs(dd) >= fabs(er)) {
+                                if (fabs(dd) < pivtol) dd = dd < 0.0 ? -pivtol : pivtol;
+                                const double rd = 1.0 / dd;
+                                const double mlt = er * rd;
+                                u0[r] = rd;
+                                u1[r] = du;
+                                u2[r] = 0.0;
+                                lm[r] = mlt;
+                                pv[r] = 0.0;
+                                dd = fma(-mlt, du, nd);
+                                du = ndu;
                             } else {
-                                y[r] = cur;
-                                cur = fma(-lm[r], cur, nx);
+                                const double rd = 1.0 / er;
+                                const double mlt = dd * rd;
+                                u0[r] = rd;
+                                u1[r] = nd;
+                                u2[r] = ndu;
+                                lm[r] = mlt;
+                                pv[r] = 1.0;
+                                dd = fma(-mlt, nd, du);
+                                du = -mlt * ndu;
                             }
                         }
-                        y[k - 1] = cur * u0[k - 1];
-                        if (k >= 2) y[k - 2] = (y[k - 2] - u1[k - 2] * y[k - 1]) * u0[k - 2];
-                        for (int r = k - 3; r >= 0; --r) y[r] = (y[r] - u1[r] * y[r + 1] - u2[r] * y[r + 2]) * u0[r];
+                        if (fabs(dd) < pivtol) dd = dd < 0.0 ? -pivtol : pivtol;
+                        u0[k - 1] = 1.0 / dd;
+                    }
+                    for (int r = lane; r < k; r += 32) y[r] = start_entry(i, r);
+                    __syncwarp();
+                    // two solves: the shift is accurate to a few ulps of |T|, so the
+                    // second solve from the first one's direction is at full precision
+                    for (int itn = 0; itn < 2; ++itn) {
+                        if (lane == 0) {
+                            double cur = y[0];
+                            for (int r = 0; r + 1 < k; ++r) {
+                                const double nx = y[r + 1];
+                                if (pv[r] != 0.0) {
+                                    y[r] = nx;
+                                    cur = fma(-lm[r], nx, cur);
+                                } else {
+                                    y[r] = cur;
+                                    cur = fma(-lm[r], cur, nx);
+                                }
+                            }
+                            y[k - 1] = cur * u0[k - 1];
+                            if (k >= 2) y[k - 2] = (y[k - 2] - u1[k - 2] * y[k - 1]) * u0[k - 2];
+                            for (int r = k - 3; r >= 0; --r) y[r] = (y[r] - u1[r] * y[r + 1] - u2[r] * y[r + 2]) * u0[r];
+                        }
+                        __syncwarp();
                         for (int q = i0; q < i; ++q) {
                             const double *zq = g.ws + (long long)q * 6 * k + 5 * k;
                             double dot = 0.0;
-                            for (int r = 0; r < k; ++r) dot = fma(zq[r], y[r], dot);
-                            for (int r = 0; r < k; ++r) y[r] = fma(-dot, zq[r], y[r]);
+                            for (int r = lane; r < k; r += 32) dot = fma(zq[r], y[r], dot);
+                            dot = warp_sum(dot);
+                            for (int r = lane; r < k; r += 32) y[r] = fma(-dot, zq[r], y[r]);
+                            __syncwarp();
                         }
                         double big = 0.0;
-                        for (int r = 0; r < k; ++r) big = fmax(big, fabs(y[r]));
+                        for (int r = lane; r < k; r += 32) big = fmax(big, fabs(y[r]));
+                        big = warp_max(big);
                         if (big == 0.0) {
-                            for (int r = 0; r < k; ++r) y[r] = start_entry(i + 7919, r);
+                            for (int r = lane; r < k; r += 32) y[r] = start_entry(i + 7919, r);
+                            __syncwarp();
                             continue;
                         }
-                        double nrm = 0.0;
                         const double ib = 1.0 / big;
-                        for (int r = 0; r < k; ++r) {
+                        double nrm = 0.0;
+                        for (int r = lane; r < k; r += 32) {
                             const double t = y[r] * ib;
                             nrm = fma(t, t, nrm);
                         }
+                        nrm = warp_sum(nrm);
                         const double den = big * sqrt(nrm);
-                        if (itn < 2) {
+                        if (itn == 0) {
                             const double s1 = 1.0 / den;
-                            for (int r = 0; r < k; ++r) y[r] *= s1;
+                            for (int r = lane; r < k; r += 32) y[r] *= s1;
                         } else {
-                            for (int r = 0; r < k; ++r) y[r] /= den;  // exact unit entries survive
+                            for (int r = lane; r < k; r += 32) y[r] /= den;  // exact unit entries survive
                         }
+                        __syncwarp();
                     }
                     // eigenvalue: Rayleigh quotient of the unit vector, non-decreasing in the group
-                    double rq = sd[0] * y[0] * y[0];
-                    for (int r = 1; r < k; ++r) rq = fma(sd[r] * y[r], y[r], fma(2.0 * __ldcg(g.e + r - 1) * y[r - 1], y[r], rq));
+                    double rq = 0.0;
+                    for (int r = lane; r < k; r += 32) {
+                        rq = fma(sd[r] * y[r], y[r], rq);
+                        if (r > 0) rq = fma(2.0 * __ldcg(g.e + r - 1) * y[r - 1], y[r], rq);
+                    }
+                    rq = warp_sum(rq);
                     if (i > i0) rq = fmax(rq, rq_prev);
                     rq_prev = rq;
-                    g.w[i] = rq;
+                    if (lane == 0) g.w[i] = rq;
                     if (zout != y)
-                        for (int r = 0; r < k; ++r) zout[r] = y[r];
+                        for (int r = lane; r < k; r += 32) zout[r] = y[r];
+                    __syncwarp();
                 }
             }
             ++gidx;
@@ -378,15 +399,46 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) eigh_cluster_kernel(const EigA
                 double *z = slots + (long long)warp * 6 * k;
                 for (int r = lane; r < k; r += 32) z[r] = __ldcg(zg + r);
                 __syncwarp();
-                for (int j = k - 3; j >= 0; --j) {
-                    const double t = __ldcg(g.tau + j);
-                    if (t == 0.0) continue;
+                // the first 8 x 32 entries of each reflector (and its tau) are loaded one
+                // step ahead: they do not depend on z, so their latency overlaps the
+                // current step's reduction
+                constexpr int PF = 8;
+                double cv[PF], nv[PF];
+                double ct = 0.0, nt = 0.0;
+                auto fetch = [&](int j, double (&v)[PF], double &t) {
+                    t = __ldcg(g.tau + j);
                     const int m = k - j - 1;
                     const double *vh = g.Vh + (long long)j * k + j + 1;
+#pragma unroll
+                    for (int u = 0; u < PF; ++u) {
+                        const int l = lane + 32 * u;
+                        v[u] = l < m ? __ldcg(vh + l) : 0.0;
+                    }
+                };
+                if (k >= 3) fetch(k - 3, nv, nt);
+                for (int j = k - 3; j >= 0; --j) {
+#pragma unroll
+                    for (int u = 0; u < PF; ++u) cv[u] = nv[u];
+                    ct = nt;
+                    if (j > 0) fetch(j - 1, nv, nt);
+                    if (ct == 0.0) continue;
+                    const int m = k - j - 1;
+                    const double *vh = g.Vh + (long long)j * k + j + 1;
+                    double *zj = z + j + 1;
                     double dot = 0.0;
-                    for (int l = lane; l < m; l += 32) dot = fma(__ldcg(vh + l), z[j + 1 + l], dot);
-                    dot = warp_sum(dot) * t;
-                    for (int l = lane; l < m; l += 32) z[j + 1 + l] = fma(-dot, __ldcg(vh + l), z[j + 1 + l]);
+#pragma unroll
+                    for (int u = 0; u < PF; ++u) {
+                        const int l = lane + 32 * u;
+                        if (l < m) dot = fma(cv[u], zj[l], dot);
+                    }
+                    for (int l = lane + 32 * PF; l < m; l += 32) dot = fma(__ldcg(vh + l), zj[l], dot);
+                    dot = warp_sum(dot) * ct;
+#pragma unroll
+                    for (int u = 0; u < PF; ++u) {
+                        const int l = lane + 32 * u;
+                        if (l < m) zj[l] = fma(-dot, cv[u], zj[l]);
+                    }
+                    for (int l = lane + 32 * PF; l < m; l += 32) zj[l] = fma(-dot, __ldcg(vh + l), zj[l]);
                     __syncwarp();
                 }
                 for (int r = lane; r < k; r += 32) g.Y[(long long)r * g.ldy + i] = z[r];

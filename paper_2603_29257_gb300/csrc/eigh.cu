@@ -57,6 +57,7 @@ struct EigArgs {
     double *lam;    // nev
     double *ws;     // nev x 6k: inverse-iteration factors and vectors
     int slots_in_smem;  // inverse-iteration work arrays in shared memory
+    int rows_in_smem;   // each CTA's rows of A in shared memory during the reduction
     int *flag;
 };
 
@@ -128,10 +129,114 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) eigh_cluster_kernel(const EigA
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int k = g.k, nev = g.nev;
     extern __shared__ double sm[];
-    // shared: v[k] w[k] d[k] e2s[k] | 64 scalars | slots (EIG_SLOTS x 6k) when they fit
-    double *v = sm, *wv = sm + k, *sd = sm + 2 * k, *se2 = sm + 3 * k, *sc = sm + 4 * k;
-    double *slots = g.slots_in_smem ? sm + 4 * k + 64 : nullptr;
+    // shared: v[k] w[k] d[k] e2s[k] | 64 scalars | pl[k] | region: this CTA's rows of
+    // A during the reduction (when they fit), later the inverse-iteration slots
+    double *v = sm, *wv = sm + k, *sd = sm + 2 * k, *se2 = sm + 3 * k, *sc = sm + 4 * k, *pl = sm + 4 * k + 64;
+    double *region = sm + 5 * k + 64;
+    double *slots = g.slots_in_smem ? region : nullptr;
     double *A = g.A;
+
+    if (g.rows_in_smem) {
+        // ---- 1'. Householder tridiagonalisation with the rows in shared memory: the
+        // pivot row, the entries of p and the partial sums are read from the owning
+        // CTA's shared memory across the cluster
+        double *rows = region;
+        const int nown = (k - c + C - 1) / C;  // rows c, c + C, ...
+        for (long long t = tid; t < (long long)nown * k; t += EIG_THREADS) {
+            const int ii = (int)(t / k), col = (int)(t - (long long)ii * k);
+            rows[t] = A[(long long)(c + ii * C) * k + col];
+        }
+        cl.sync();
+        for (int j = 0; j + 2 < k; ++j) {
+            const int m = k - j - 1;
+            const double *prow = cl.map_shared_rank(rows, j % C) + (long long)(j / C) * k;
+            for (int l = tid; l < m; l += EIG_THREADS) v[l] = prow[j + 1 + l];
+            __syncthreads();
+            if (warp == 0) {
+                double s2 = 0.0;
+                for (int l = 1 + lane; l < m; l += 32) s2 = fma(v[l], v[l], s2);
+                s2 = warp_sum(s2);
+                if (lane == 0) {
+                    const double x0 = v[0];
+                    double tau = 0.0, beta = x0, scl = 1.0;
+                    if (s2 > 0.0) {
+                        const double xn = sqrt(fma(x0, x0, s2));
+                        beta = x0 >= 0.0 ? -xn : xn;
+                        tau = (beta - x0) / beta;
+                        scl = 1.0 / (x0 - beta);
+                    }
+                    sc[0] = tau;
+                    sc[1] = scl;
+                    if (c == 0) {
+                        g.d[j] = prow[j];
+                        g.e[j] = beta;
+                        g.tau[j] = tau;
+                    }
+                }
+            }
+            __syncthreads();
+            const double tau = sc[0], scl = sc[1];
+            if (tau == 0.0) {
+                cl.sync();
+                continue;
+            }
+            for (int l = 1 + tid; l < m; l += EIG_THREADS) v[l] *= scl;
+            if (tid == 0) v[0] = 1.0;
+            __syncthreads();
+            if (c == 0) {
+                double *vh = g.Vh + (long long)j * k + j + 1;
+                for (int l = tid; l < m; l += EIG_THREADS) vh[l] = v[l];
+            }
+            const int i0 = j + 1 + ((c - (j + 1)) % C + C) % C;
+            double part = 0.0;
+            for (int i = i0 + warp * C; i < k; i += EIG_WARPS * C) {
+                const double *ri = rows + (long long)((i - c) / C) * k + j + 1;
+                double dot = 0.0;
+                for (int l = lane; l < m; l += 32) dot = fma(ri[l], v[l], dot);
+                dot = warp_sum(dot) * tau;
+                if (lane == 0) {
+                    pl[i] = dot;
+                    part = fma(dot, v[i - j - 1], part);
+                }
+            }
+            if (lane == 0) sc[8 + warp] = part;
+            __syncthreads();
+            if (warp == 0) {
+                const double t = warp_sum(lane < EIG_WARPS ? sc[8 + lane] : 0.0);
+                if (lane == 0) sc[5] = t;
+            }
+            cl.sync();
+            if (warp == 0) {
+                const double pv = warp_sum(lane < C ? *cl.map_shared_rank(sc + 5, lane) : 0.0);
+                if (lane == 0) sc[2] = 0.5 * tau * pv;
+            }
+            __syncthreads();
+            const double K = sc[2];
+            for (int l = tid; l < m; l += EIG_THREADS) {
+                const int i = j + 1 + l;
+                wv[l] = fma(-K, v[l], *cl.map_shared_rank(pl + i, i % C));
+            }
+            __syncthreads();
+            for (int i = i0 + warp * C; i < k; i += EIG_WARPS * C) {
+                double *ri = rows + (long long)((i - c) / C) * k + j + 1;
+                const double vi = v[i - j - 1], wi = wv[i - j - 1];
+                for (int l = lane; l < m; l += 32) ri[l] = fma(-vi, wv[l], fma(-wi, v[l], ri[l]));
+            }
+            cl.sync();
+        }
+        if (c == 0 && tid == 0) {
+            if (k >= 2) {
+                const double *r2 = cl.map_shared_rank(rows, (k - 2) % C) + (long long)((k - 2) / C) * k;
+                g.d[k - 2] = r2[k - 2];
+                g.e[k - 2] = r2[k - 1];
+                g.tau[k - 2] = 0.0;
+            }
+            const double *r1 = cl.map_shared_rank(rows, (k - 1) % C) + (long long)((k - 1) / C) * k;
+            g.d[k - 1] = r1[k - 1];
+            g.tau[k - 1] = 0.0;
+        }
+        cl.sync();  // every read of the rows is done before the region is reused
+    } else {
 
     // ---- 1. Householder tridiagonalisation
     for (int j = 0; j + 2 < k; ++j) {
@@ -219,6 +324,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) eigh_cluster_kernel(const EigA
         g.tau[k - 1] = 0.0;
     }
     cl.sync();
+    }  // rows in global memory
 
     // ---- 2. lowest nev eigenvalues of T by 32-way multisection (one warp each)
     for (int r = tid; r < k; r += EIG_THREADS) {
@@ -501,11 +607,13 @@ void eigh_lowest(Prof &prof, cudaStream_t st, double *A, int k, int nev, double 
     static const Lim lim;
     int C = 1;
     while (C < lim.maxc && C * 20 < k) C *= 2;
-    size_t smem = sizeof(double) * (4 * (size_t)k + 64);
-    TR_REQUIRE(smem <= 200 * 1024, TR_EINVAL, "eigh: subspace too large");
-    const size_t smem_slots = smem + sizeof(double) * EIG_SLOTS * 6 * (size_t)k;
-    const bool slots_in_smem = smem_slots <= 200 * 1024;
-    if (slots_in_smem) smem = smem_slots;
+    const size_t base = sizeof(double) * (5 * (size_t)k + 64);
+    TR_REQUIRE(base <= 200 * 1024, TR_EINVAL, "eigh: subspace too large");
+    const size_t slot_bytes = sizeof(double) * EIG_SLOTS * 6 * (size_t)k;
+    const size_t row_bytes = sizeof(double) * (size_t)cdiv(k, C) * k;
+    const bool slots_in_smem = base + slot_bytes <= 200 * 1024;
+    const bool rows_in_smem = base + row_bytes <= 200 * 1024;
+    size_t smem = base + std::max(slots_in_smem ? slot_bytes : 0, rows_in_smem ? row_bytes : 0);
     static const cudaError_t sattr =
         cudaFuncSetAttribute(eigh_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     TR_CUDA(sattr);
@@ -533,6 +641,7 @@ void eigh_lowest(Prof &prof, cudaStream_t st, double *A, int k, int nev, double 
     p += nev;
     g.ws = p;
     g.slots_in_smem = slots_in_smem ? 1 : 0;
+    g.rows_in_smem = rows_in_smem ? 1 : 0;
     g.flag = flag;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];

@@ -74,8 +74,9 @@ struct tr_ctx {
     tr::DevBuf<double> V, W, Hs, Hw, Yev, Yw, theta, Xr, R, T, Tt, Tn, Wn, Cs, Ss, Gc, rn, part;
     // sliced copies of V and W (and of the new directions) for the subspace
     // products on the tensor cores (forms that use them, when all rows are on the device)
-    tr::DevBuf<double> dvs_V, dvs_W, dvs_T, dvs_Vt, dvs_Y, dvs_C;
-    tr::OzMat dz_V, dz_W, dz_Vt;  // dz_Vt: V by columns (rows = nov, K = subspace index)
+    tr::DevBuf<double> dvs_V, dvs_W, dvs_T, dvs_Vt, dvs_Wt, dvs_Y, dvs_C;
+    tr::OzMat dz_V, dz_W, dz_Vt, dz_Wt;  // dz_Vt, dz_Wt: V and W by columns (rows = nov, K = subspace index)
+    tr::DevBuf<int> dz_eW;               // the one exponent of dz_Wt
     tr::DevBuf<int> idx_dev;
     // spill of V/W rows to pinned host memory: staging slots, copy stream, events
     tr::DevBuf<double> stage;

@@ -259,6 +259,9 @@ struct PinnedBuf {
 //   [A Tn -> Wn for pend_p rows: one matvec, or one graph for many molecules]
 //   absorb    (subspace matrix update, rows stored)
 // so that many molecules can be advanced in lockstep.
+// error code (tensor-core flag) for a W block beyond the sliced copy's exponent
+constexpr int TC_ERR_W_RANGE = 99;
+
 struct Dav {
     tr_ctx *c;
     cudaStream_t st;
@@ -369,7 +372,7 @@ struct Dav {
             const size_t sv = oz_bytes(maxsp, (int)nov, OZ_SLICES_FP64), stn = oz_bytes(pmax, (int)nov, OZ_SLICES_FP64);
             const size_t svt = oz_bytes(nov, maxsp, OZ_SLICES_FP64);
             const size_t ssm = oz_bytes(std::max(n, pmax), maxsp, OZ_SLICES_FP64);
-            if (c->budget.used + 2 * sv + svt + stn + 2 * ssm + (64u << 20) <= c->budget.limit) {
+            if (c->budget.used + 2 * sv + 2 * svt + stn + 2 * ssm + (64u << 20) <= c->budget.limit) {
                 c->dvs_V.alloc(cdiv(sv, 8), &c->budget, "sliced Davidson V");
                 c->dvs_W.alloc(cdiv(sv, 8), &c->budget, "sliced Davidson W");
                 c->dvs_T.alloc(cdiv(stn, 8), &c->budget, "sliced new directions");
@@ -379,6 +382,10 @@ struct Dav {
                 TR_CUDA(cudaMemsetAsync(c->dvs_Vt.p, 0, c->dvs_Vt.n * sizeof(double), st));
                 oz_bind(c->dz_Vt, c->dvs_Vt.p, nov, maxsp, OZ_SLICES_FP64);
                 oz_set_exponents(st, c->dz_Vt, 1);  // orthonormal rows: every |v| < 2
+                c->dvs_Wt.alloc(cdiv(svt, 8), &c->budget, "sliced Davidson W by columns");
+                c->dz_eW.alloc(1, &c->budget, "exponent");
+                TR_CUDA(cudaMemsetAsync(c->dvs_Wt.p, 0, c->dvs_Wt.n * sizeof(double), st));
+                oz_bind(c->dz_Wt, c->dvs_Wt.p, nov, maxsp, OZ_SLICES_FP64);
                 // rows not yet sliced read as zero (tiles extend past the live rows)
                 TR_CUDA(cudaMemsetAsync(c->dvs_V.p, 0, c->dvs_V.n * sizeof(double), st));
                 TR_CUDA(cudaMemsetAsync(c->dvs_W.p, 0, c->dvs_W.n * sizeof(double), st));
@@ -466,7 +473,13 @@ struct Dav {
             // the new rows join the sliced copies first, then one product over rows 0..kk
             oz_split_rows(pf, st, "oz_split_V", Vn, nov, 1, c->dz_V, k0, p);
             oz_split_rows(pf, st, "oz_split_W", Wn, nov, 1, c->dz_W, k0, p);
-            oz_split_cols_fixed(pf, st, "oz_split_Vt", Vn, nov, c->dz_Vt, k0, p, 1);
+            oz_split_cols_fixed(pf, st, "oz_split_Vt", Vn, nov, c->dz_Vt, k0, p);
+            // W by columns with one exponent: the first block's largest row exponent
+            // plus 8 bits (|A v| for unit v stays far below 256 times the first
+            // block's largest entry); a later block beyond it is reported
+            oz_col_exponent_update(st, c->dz_W.e + k0, p, k0 == 0, 8, c->dz_Wt, c->dz_eW.p, c->flag.p + 1,
+                                   TC_ERR_W_RANGE);
+            oz_split_cols_fixed(pf, st, "oz_split_Wt", Wn, nov, c->dz_Wt, k0, p);
             tc_reduce("subspace_H_tc", c->dz_W, 0, c->dz_V, k0, kk, p, A1, 1, kk);  // A1[i][r] = Vn_i . W_r
             tc_reduce("subspace_H_tc", c->dz_V, 0, c->dz_W, k0, kk, p, A2, 1, kk);  // A2[i][r] = Wn_i . V_r
             TR_LAUNCH(pf, st, "subspace_insert", 0, 0,
@@ -571,16 +584,20 @@ struct Dav {
             o.ldm = 1;
             o.ldn = nov;
             oz_gemm(pf, st, "ritz_tc", c->dz_Vt, 0, 0, 0, 0, Ys, 0, 0, 0, 0, (int)nov, n, Ys.nkb, 1, 1, o, c->flag.p + 1);
+            o.d = c->R.p;
+            oz_gemm(pf, st, "ritz_tc", c->dz_Wt, 0, 0, 0, 0, Ys, 0, 0, 0, 0, (int)nov, n, Ys.nkb, 1, 1, o, c->flag.p + 1);
         } else {
             for_rows(SV, 0, k, [&](const double *rows, int r0, int nr) {
                 dgemm(pf, st, "ritz", true, false, n, (int)nov, nr, 1.0, c->Yev.p + (long long)r0 * k, k, rows, nov,
                       r0 == 0 ? 0.0 : 1.0, c->Xr.p, nov, Batch(), nullptr, 0);
             });
         }
-        for_rows(SW, 0, k, [&](const double *rows, int r0, int nr) {
-            dgemm(pf, st, "ritz", true, false, n, (int)nov, nr, 1.0, c->Yev.p + (long long)r0 * k, k, rows, nov,
-                  r0 == 0 ? 0.0 : 1.0, c->R.p, nov, Batch(), nullptr, 0);
-        });
+        if (!tcd) {
+            for_rows(SW, 0, k, [&](const double *rows, int r0, int nr) {
+                dgemm(pf, st, "ritz", true, false, n, (int)nov, nr, 1.0, c->Yev.p + (long long)r0 * k, k, rows, nov,
+                      r0 == 0 ? 0.0 : 1.0, c->R.p, nov, Batch(), nullptr, 0);
+            });
+        }
         TR_LAUNCH(pf, st, "residual", 0, 24.0 * n * nov,
                   ritz_resid<<<dim3(nblk, n), 256, 0, st>>>(c->R.p, c->Xr.p, c->theta.p, n, nov, c->part.p));
         TR_LAUNCH(pf, st, "residual", 0, 0, finish_norms<<<cdiv(n, 64), 64, 0, st>>>(c->part.p, nblk, n, c->rn.p));
@@ -599,6 +616,8 @@ struct Dav {
             eig_timed = false;
         }
         TR_REQUIRE(!h_fl[0], TR_ECUDA, "solve: subspace eigensolver did not converge");
+        TR_REQUIRE(h_fl[1] != TC_ERR_W_RANGE, TR_ECUDA,
+                   "solve: a product block exceeded the exponent range fixed for the sliced W");
         TR_REQUIRE(!h_fl[1], TR_ECUDA, "solve: a tensor-core pipeline wait timed out");
         unconv.clear();
         for (int r = 0; r < n; ++r)

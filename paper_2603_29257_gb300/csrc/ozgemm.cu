@@ -485,17 +485,17 @@ __global__ void oz_split_reduce(const double *__restrict__ ws, int ksplit, int n
 }
 
 // columns k0 .. k0+p of a sliced matrix whose rows are the source columns:
-// element (r, k0 + j) = src[j * ld + r], every element with the fixed exponent e
+// element (r, k0 + j) = src[j * ld + r], with the row exponents already in e
 template <int S>
-__global__ void oz_slice_cols(const double *__restrict__ src, long long ld, long long rows, int k0, int p, int e,
-                              int SP, long long L, uint16_t *__restrict__ q)
+__global__ void oz_slice_cols(const double *__restrict__ src, long long ld, long long rows, int k0, int p,
+                              const int *__restrict__ e, int SP, long long L, uint16_t *__restrict__ q)
 {
     const long long tot = rows * p;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
         const long long r = t / p;
         const int j = (int)(t - r * p), k = k0 + j;
         int dg[S];
-        oz_digits<S>(src[(long long)j * ld + r], e, dg);
+        oz_digits<S>(src[(long long)j * ld + r], e[r], dg);
         uint16_t *o = q + r * L + (long long)(k >> 5) * SP * 32 + (k & 31);
 #pragma unroll
         for (int s = 0; s < S; ++s)
@@ -577,6 +577,41 @@ void oz_split(Prof &prof, cudaStream_t st, const char *name, const double *x, lo
     prof.end(st, tok);
 }
 
+// Fixed exponent for a matrix sliced by columns whose range is learnt from its
+// first rows: e_new = max(row exponents of the first block) + margin; later
+// blocks must stay below 2^e (else *bad = code).
+__global__ void oz_col_exponent(const int *__restrict__ row_e, int p, int first, int margin, int *__restrict__ e_fixed,
+                                int *__restrict__ bad, int code)
+{
+    int mx = -100000;
+    for (int i = threadIdx.x; i < p; i += 32) mx = max(mx, row_e[i]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (threadIdx.x == 0) {
+        if (first) *e_fixed = mx + margin;
+        else if (mx > *e_fixed) atomicCAS(bad, 0, code);
+    }
+}
+
+__global__ void fill_int_from(int *__restrict__ p, long long n, const int *__restrict__ v)
+{
+    const int x = *v;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        p[t] = x;
+}
+
+void oz_col_exponent_update(cudaStream_t st, const int *row_e, int p, bool first, int margin, OzMat &m, int *e_fixed,
+                            int *bad, int code)
+{
+    oz_col_exponent<<<1, 32, 0, st>>>(row_e, p, first ? 1 : 0, margin, e_fixed, bad, code);
+    TR_CUDA(cudaGetLastError());
+    if (first) {
+        const unsigned blocks = (unsigned)std::min<long long>(cdiv(m.rows, 256), 152LL * 8);
+        fill_int_from<<<blocks, 256, 0, st>>>(m.e, m.rows, e_fixed);
+        TR_CUDA(cudaGetLastError());
+    }
+}
+
 void oz_set_exponents(cudaStream_t st, OzMat &m, int e)
 {
     const unsigned blocks = (unsigned)std::min<long long>(cdiv(m.rows, 256), 152LL * 8);
@@ -585,7 +620,7 @@ void oz_set_exponents(cudaStream_t st, OzMat &m, int e)
 }
 
 void oz_split_cols_fixed(Prof &prof, cudaStream_t st, const char *name, const double *src, long long ld, OzMat &m,
-                         int k0, int p, int e)
+                         int k0, int p)
 {
     TR_REQUIRE(k0 >= 0 && p >= 0 && k0 + p <= m.K, TR_EINVAL, "Ozaki split: column range out of bounds");
     if (p == 0) return;
@@ -593,12 +628,12 @@ void oz_split_cols_fixed(Prof &prof, cudaStream_t st, const char *name, const do
     const unsigned blocks = (unsigned)std::min<long long>(cdiv(tot, 256), 152LL * 16);
     int tok = prof.begin(st, name, 0, 8.0 * tot + 2.0 * m.SP * tot);
     switch (m.S) {
-    case 2: oz_slice_cols<2><<<blocks, 256, 0, st>>>(src, ld, m.rows, k0, p, e, m.SP, m.L, m.q); break;
-    case 3: oz_slice_cols<3><<<blocks, 256, 0, st>>>(src, ld, m.rows, k0, p, e, m.SP, m.L, m.q); break;
-    case 4: oz_slice_cols<4><<<blocks, 256, 0, st>>>(src, ld, m.rows, k0, p, e, m.SP, m.L, m.q); break;
-    case 5: oz_slice_cols<5><<<blocks, 256, 0, st>>>(src, ld, m.rows, k0, p, e, m.SP, m.L, m.q); break;
-    case 6: oz_slice_cols<6><<<blocks, 256, 0, st>>>(src, ld, m.rows, k0, p, e, m.SP, m.L, m.q); break;
-    default: oz_slice_cols<7><<<blocks, 256, 0, st>>>(src, ld, m.rows, k0, p, e, m.SP, m.L, m.q); break;
+    case 2: oz_slice_cols<2><<<blocks, 256, 0, st>>>(src, ld, m.rows, k0, p, m.e, m.SP, m.L, m.q); break;
+    case 3: oz_slice_cols<3><<<blocks, 256, 0, st>>>(src, ld, m.rows, k0, p, m.e, m.SP, m.L, m.q); break;
+    case 4: oz_slice_cols<4><<<blocks, 256, 0, st>>>(src, ld, m.rows, k0, p, m.e, m.SP, m.L, m.q); break;
+    case 5: oz_slice_cols<5><<<blocks, 256, 0, st>>>(src, ld, m.rows, k0, p, m.e, m.SP, m.L, m.q); break;
+    case 6: oz_slice_cols<6><<<blocks, 256, 0, st>>>(src, ld, m.rows, k0, p, m.e, m.SP, m.L, m.q); break;
+    default: oz_slice_cols<7><<<blocks, 256, 0, st>>>(src, ld, m.rows, k0, p, m.e, m.SP, m.L, m.q); break;
     }
     TR_CUDA(cudaGetLastError());
     prof.end(st, tok);

@@ -51,10 +51,17 @@ void oz_split(Prof &prof, cudaStream_t st, const char *name, const double *x, lo
 void oz_set_exponents(cudaStream_t st, OzMat &m, int e);
 
 // K positions k0 .. k0+p of every row of m from src[p][ld] (element (r, k0 + j)
-// = src[j * ld + r]) with the fixed exponent e: every |src| must be below 2^e
-// (orthonormal vectors with e = 1), and the row exponents of m must be e
+// = src[j * ld + r]) with the row exponents already in m.e (one fixed value for
+// a matrix sliced by columns): every |src| in row r must be below 2^e[r]
 void oz_split_cols_fixed(Prof &prof, cudaStream_t st, const char *name, const double *src, long long ld, OzMat &m,
-                         int k0, int p, int e);
+                         int k0, int p);
+
+// For a matrix sliced by columns with one exponent for all rows: on the first
+// block (first = true) set *e_fixed = max(row_e[0..p)) + margin and every row
+// exponent of m to it; on later blocks set *bad = code if a row exponent
+// exceeds *e_fixed.  All on the device (stream order).
+void oz_col_exponent_update(cudaStream_t st, const int *row_e, int p, bool first, int margin, OzMat &m, int *e_fixed,
+                            int *bad, int code);
 
 // slice rows r0 .. r0+nr of m only: element (r0 + r, k) = x[r * sr + k * sk]
 void oz_split_rows(Prof &prof, cudaStream_t st, const char *name, const double *x, long long sr, long long sk,

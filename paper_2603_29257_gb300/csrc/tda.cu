@@ -613,7 +613,7 @@ size_t footprint(tr_ctx *c)
     const double dtc = (c->opt.precision == TR_MIXED || c->opt.precision == TR_FP64_TC)
                            ? 2.0 * (double)oz_bytes(maxsp, (int)nov, OZ_SLICES_FP64) +
                                  (double)oz_bytes((long long)pmax, (int)nov, OZ_SLICES_FP64) +
-                                 (double)oz_bytes((long long)nov, maxsp, OZ_SLICES_FP64) +
+                                 2.0 * (double)oz_bytes((long long)nov, maxsp, OZ_SLICES_FP64) +
                                  2.0 * (double)oz_bytes((long long)std::max<double>(n, pmax), maxsp, OZ_SLICES_FP64)
                            : 0.0;
     const double solve_peak = kept + dav + ws + tcx + dtc;

@@ -414,6 +414,9 @@ struct Dav {
 
     ~Dav()
     {
+        // queued copies into the pinned buffers (error paths) finish first
+        cudaStreamSynchronize(st);
+        if (c->cst) cudaStreamSynchronize(c->cst);
         if (h_rn) cudaFreeHost(h_rn);
         if (h_th) cudaFreeHost(h_th);
         if (h_fl) cudaFreeHost(h_fl);
@@ -1161,7 +1164,9 @@ void solver_loop(tr_server *S)
     cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
     cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
     StepGraph g;
-    std::vector<std::pair<tr_ctx *, int>> sig;
+    // the graph is keyed by request ids, never by context addresses: a finished
+    // request's context is freed and a later one may be allocated at the same address
+    std::vector<std::pair<long long, int>> sig;
     bool warmed = false;
 
     auto finish = [&](Member &m, int rc_in, const std::string &msg) {
@@ -1197,6 +1202,10 @@ void solver_loop(tr_server *S)
             std::strncpy(res.error, msg.c_str(), sizeof(res.error) - 1);
         }
         res.status = rc;
+        // nothing of this request may still be queued when its pinned and device
+        // buffers are freed (the error paths get here without a synchronisation)
+        if (m.r->stream) cudaStreamSynchronize(m.r->stream);
+        if (m.r->ctx && m.r->ctx->cst) cudaStreamSynchronize(m.r->ctx->cst);
         m.d.reset();
         release_request(S, m.r.get());
         if (m.join) cudaEventDestroy(m.join);
@@ -1285,13 +1294,13 @@ void solver_loop(tr_server *S)
         if (pend.empty()) continue;
         // the products of this step: one graph launch (recorded again when the membership changes)
         try {
-            std::vector<std::pair<tr_ctx *, int>> key;
+            std::vector<std::pair<long long, int>> key;
             std::vector<tr_ctx *> cs;
             std::vector<int> rows, members;
             std::vector<cudaEvent_t> joins;
             for (Member *m : pend) {
                 const int rws = m->fresh ? m->d->b0 : m->d->n;
-                key.push_back({m->r->ctx, rws});
+                key.push_back({m->r->id, rws});
                 members.push_back((int)cs.size());
                 cs.push_back(m->r->ctx);
                 rows.push_back(rws);
@@ -1313,6 +1322,8 @@ void solver_loop(tr_server *S)
                 m->fresh = false;
             }
         } catch (const Error &e) {
+            // a launched graph may still use the members' buffers
+            cudaStreamSynchronize(s0);
             for (Member *m : pend) finish(*m, e.code, e.what());
             act.erase(std::remove_if(act.begin(), act.end(), [](const std::unique_ptr<Member> &m) { return !m->r->ctx; }),
                       act.end());
@@ -1321,8 +1332,8 @@ void solver_loop(tr_server *S)
         }
     }
     for (auto &mp : act) finish(*mp, TR_ECUDA, "server: stopped before completion");
-    g.reset();
     cudaStreamSynchronize(s0);
+    g.reset();
     cudaStreamDestroy(s0);
     cudaEventDestroy(fork);
     cudaEventDestroy(done);

@@ -82,3 +82,23 @@ def test_admission_by_footprint_and_rejection(mols):
     # one at a time: each admission waits for the previous molecule to finish
     for a, b in zip(ok, ok[1:]):
         assert b["t_admit"] >= a["t_done"] - 1e-3
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_back_to_back_requests_with_half_the_states(mols, precision):
+    """One request at a time through one builder: a finished request's context is
+    freed and the next one is often allocated at the same host address.  When the
+    new request's first block (2 n rows) equals the old one's step (n rows), a
+    step graph cached by context address would be replayed on freed buffers; the
+    server keys it by request id, so every result matches the oracle."""
+    tdarisp = _lib()
+    order = [(3, 8), (1, 4), (0, 6), (2, 3), (5, 6), (4, 3)]
+    with tdarisp.Server(max_active=4, autotune=False, build_threads=1) as srv:
+        for k, n in order:
+            m, w = mols[k]
+            rid = srv.submit(m, nstates=n, tol=1e-7, cx=0.25, precision=precision)
+            res = srv.drain()
+            assert len(res) == 1 and res[0]["id"] == rid
+            r = res[0]
+            assert r["status"] == 0, r["error"]
+            assert np.abs(r["omega"] - w[:n]).max() < (1e-8 if precision == 0 else 1e-5), (k, n)

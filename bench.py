@@ -443,6 +443,68 @@ BATCH_OPTS = dict(cx=0.25, k_alpha=1.0, k_beta=0.0, omega=0.0, window_ev=40.0, n
                   max_iter=200)
 
 
+def run_matvec(args):
+    """Block products alone (throughput of A X and the profiling case of the
+    integral and diagonal kernels): tr_build once in the chosen form, then W
+    untimed and K timed products of one block of `--block` resident seeded
+    vectors.  value = block x K / event time; per kernel kind the library's
+    CUDA-event time, algorithmic bytes and flops."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_29257_gb300 import tdarisp
+    mol = make_inputs(args.case)
+    torch.zeros(1, device="cuda")
+    stream = torch.cuda.current_stream()
+    C_dev = torch.from_numpy(mol.C).cuda()
+    eps_dev = torch.from_numpy(mol.eps).cuda()
+    ctx = tdarisp.Context(stream=stream.cuda_stream, **dict(OPTS, precision=args.precision))
+    ctx.set_molecule(mol.Z, mol.xyz, mol.aux_exp, mol.shells)
+    ctx.set_orbitals(C_dev, eps_dev, mol.nocc)
+    ctx.profile(True)
+    ctx.build()
+    torch.cuda.synchronize()
+    build_prof = ctx.profile_get()
+    ctx.profile(False)
+    d = ctx.dims()
+    g = torch.Generator(device="cpu").manual_seed(17)
+    X = torch.randn((args.block, d.nocc, d.nvir), generator=g, dtype=torch.float64).cuda()
+    AX = torch.empty_like(X)
+    for _ in range(max(args.warmup, 1)):
+        ctx.matvec(X, out=AX)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        ctx.matvec(X, out=AX)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    prof = ctx.profile_get()
+    ctx.profile(False)
+    ms = t0.elapsed_time(t1)
+
+    def table(pr):
+        return {k: {"ms": round(v["ms"], 3), "launches": v["launches"],
+                    "gbs": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] and v["bytes"] else None,
+                    "tflops": round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 3) if v["ms"] and v["flops"] else None}
+                for k, v in sorted(pr.items(), key=lambda kv: -kv[1]["ms"])[:12]}
+    line = {"metric": "TDA-risp matvecs/s (block products alone)", "value": args.block * args.steps / (ms * 1e-3),
+            "unit": "matvecs/s", "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 1),
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {0: "f64", 1: "f32/tf32x3 + f64", 2: "f64 (7-slice bf16 tensor-core products)"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": (WORKLOAD if args.case == "full" else "100-atom molecule, same options")
+                       + "; one block of %d seeded vectors" % args.block,
+                       "precision": args.precision, "nao": d.nao, "nocc": d.nocc, "nvir": d.nvir,
+                       "block": args.block,
+                       "l2": "X and AX %.0f MB each" % (8e-6 * args.block * d.nocc * d.nvir)},
+            "kernels": table(prof), "build_kernels": table(build_prof)}
+    print(json.dumps(line))
+
+
 def run_batched(args):
     """Batched form: 64 molecules (20-150 atoms, 10 states each) in the reduced-precision
     form, all Davidson solves advanced in lockstep with one graph launch of all
@@ -645,10 +707,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the reduced-precision form")
     ap.add_argument("--no-fp64tc", action="store_true", help="skip the FP64 form on the tensor cores")
-    ap.add_argument("--workload", default="fp64-200", choices=["fp64-200", "batched", "serve"],
+    ap.add_argument("--workload", default="fp64-200", choices=["fp64-200", "batched", "serve", "matvec"],
                     help="batched: 64 molecules in the reduced-precision batched form; "
-                         "serve: a Poisson request stream through the serving runtime")
+                         "serve: a Poisson request stream through the serving runtime; "
+                         "matvec: block products alone in the form --precision (profiling case)")
     ap.add_argument("--requests", type=int, default=64, help="requests of the serve workload")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
+                    help="form of the matvec workload: 0 FP64, 1 reduced precision, 2 FP64 on the tensor cores")
+    ap.add_argument("--block", type=int, default=30, help="vectors per block of the matvec workload")
     ap.add_argument("--case", default="full", choices=["full", "small"],
                     help="small: 100-atom molecule of the same shape, for profiler captures")
     args = ap.parse_args()
@@ -658,6 +724,8 @@ def main():
         run_batched(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "matvec":
+        run_matvec(args)
     else:
         run_native(args)
 

@@ -48,7 +48,12 @@ PairList make_pairs(const std::vector<ShellDev> &sh, const std::vector<double> &
                     const std::vector<double> &pcoef, double screen)
 {
     PairList pl;
-    std::vector<int2> cls[6];
+    // a kept shell pair with its primitive pairs that pass the screening
+    struct Kept {
+        int2 ab;
+        std::vector<double> prim;  // 6 doubles per primitive pair
+    };
+    std::vector<Kept> cls[6];
     const int nsh = (int)sh.size();
     pl.ntotal = 0;
     for (int i = 0; i < nsh; ++i) {
@@ -57,52 +62,39 @@ PairList make_pairs(const std::vector<ShellDev> &sh, const std::vector<double> &
             int a = i, b = j;
             if (sh[a].l < sh[b].l) std::swap(a, b);
             const ShellDev &A = sh[a], &B = sh[b];
-            double dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
-            double r2 = dx * dx + dy * dy + dz * dz;
-            double poly = std::pow(1.0 + std::sqrt(r2), A.l + B.l);
-            bool keep = false;
-            for (int u = 0; u < A.nprim && !keep; ++u)
-                for (int v = 0; v < B.nprim && !keep; ++v) {
-                    double ea = pexp[A.pstart + u], eb = pexp[B.pstart + v];
-                    double p = ea + eb;
-                    double k = std::fabs(pcoef[A.pstart + u] * pcoef[B.pstart + v]) *
-                               std::exp(-ea * eb / p * r2) * std::pow(M_PI / p, 1.5) * poly;
-                    keep = k >= screen;
+            const double ABx = A.x - B.x, ABy = A.y - B.y, ABz = A.z - B.z;
+            const double AB2 = ABx * ABx + ABy * ABy + ABz * ABz;
+            const double poly = std::pow(1.0 + std::sqrt(AB2), A.l + B.l);
+            Kept k;
+            k.ab = make_int2(a, b);
+            for (int u = 0; u < A.nprim; ++u)
+                for (int v = 0; v < B.nprim; ++v) {
+                    const double ea = pexp[A.pstart + u], eb = pexp[B.pstart + v];
+                    const double p = ea + eb, ip = 1.0 / p;
+                    const double K = pcoef[A.pstart + u] * pcoef[B.pstart + v] * std::exp(-ea * eb * ip * AB2);
+                    if (std::fabs(K) * M_PI * ip * std::sqrt(M_PI * ip) * poly < screen) continue;
+                    const double P[6] = {(ea * A.x + eb * B.x) * ip, (ea * A.y + eb * B.y) * ip,
+                                         (ea * A.z + eb * B.z) * ip, p, ip, K};
+                    k.prim.insert(k.prim.end(), P, P + 6);
                 }
-            if (!keep) continue;
-            int c = A.l == 0 ? 0 : (A.l == 1 ? 1 + B.l : 3 + B.l);
-            cls[c].push_back(make_int2(a, b));
+            if (k.prim.empty()) continue;  // no primitive pair passes: the shell pair is dropped
+            const int c = A.l == 0 ? 0 : (A.l == 1 ? 1 + B.l : 3 + B.l);
+            cls[c].push_back(std::move(k));
         }
     }
+    // within a class, shell pairs with equal numbers of kept primitive pairs sit
+    // next to each other: the threads of a warp then run loops of equal length
     pl.off[0] = 0;
     for (int c = 0; c < 6; ++c) {
-        // group by primitive counts to keep warps uniform
-        std::stable_sort(cls[c].begin(), cls[c].end(), [&](const int2 &x, const int2 &y) {
-            int kx = sh[x.x].nprim * 8 + sh[x.y].nprim, ky = sh[y.x].nprim * 8 + sh[y.y].nprim;
-            return kx < ky;
-        });
-        pl.pairs.insert(pl.pairs.end(), cls[c].begin(), cls[c].end());
+        std::stable_sort(cls[c].begin(), cls[c].end(),
+                         [](const Kept &x, const Kept &y) { return x.prim.size() < y.prim.size(); });
+        for (const Kept &k : cls[c]) {
+            const int first = (int)(pl.prim.size() / 6);
+            pl.pairs.push_back(k.ab);
+            pl.prim.insert(pl.prim.end(), k.prim.begin(), k.prim.end());
+            pl.range.push_back(make_int2(first, (int)(k.prim.size() / 6)));
+        }
         pl.off[c + 1] = (int)pl.pairs.size();
-    }
-    // primitive-pair table in pair order
-    pl.range.resize(pl.pairs.size());
-    for (size_t i = 0; i < pl.pairs.size(); ++i) {
-        const ShellDev &A = sh[pl.pairs[i].x], &B = sh[pl.pairs[i].y];
-        const double ABx = A.x - B.x, ABy = A.y - B.y, ABz = A.z - B.z;
-        const double AB2 = ABx * ABx + ABy * ABy + ABz * ABz;
-        const double poly = std::pow(1.0 + std::sqrt(AB2), A.l + B.l);
-        const int first = (int)(pl.prim.size() / 6);
-        for (int u = 0; u < A.nprim; ++u)
-            for (int v = 0; v < B.nprim; ++v) {
-                const double a = pexp[A.pstart + u], b = pexp[B.pstart + v];
-                const double p = a + b, ip = 1.0 / p;
-                const double K = pcoef[A.pstart + u] * pcoef[B.pstart + v] * std::exp(-a * b * ip * AB2);
-                if (std::fabs(K) * M_PI * ip * std::sqrt(M_PI * ip) * poly < screen) continue;
-                const double P[6] = {(a * A.x + b * B.x) * ip, (a * A.y + b * B.y) * ip, (a * A.z + b * B.z) * ip,
-                                     p, ip, K};
-                pl.prim.insert(pl.prim.end(), P, P + 6);
-            }
-        pl.range[i] = make_int2(first, (int)(pl.prim.size() / 6) - first);
     }
     return pl;
 }
@@ -304,17 +296,21 @@ __global__ void __launch_bounds__(128)
                 for (int kb_ = 0; kb_ < NCB; ++kb_) {
                     const int ax = cexp(LA, ka_, 0), ay = cexp(LA, ka_, 1), az = cexp(LA, ka_, 2);
                     const int bx = cexp(LB, kb_, 0), by = cexp(LB, kb_, 1), bz = cexp(LB, kb_, 2);
+                    // sum_t Ex_t sum_u Ey_u sum_v Ez_v R_{t,u,v}: one direction at a time
                     double s = 0.0;
 #pragma unroll
-                    for (int t = 0; t <= ax + bx; ++t)
+                    for (int t = 0; t <= ax + bx; ++t) {
+                        double st = 0.0;
 #pragma unroll
                         for (int u = 0; u <= ay + by; ++u) {
                             double su = 0.0;
 #pragma unroll
                             for (int v = 0; v <= az + bz; ++v)
                                 su = fma(Ez[az][bz][v], R[t + DX][u + DY][v + DZ], su);
-                            s = fma(Ex[ax][bx][t] * Ey[ay][by][u], su, s);
+                            st = fma(Ey[ay][by][u], su, st);
                         }
+                        s = fma(Ex[ax][bx][t], st, s);
+                    }
                     acc[ka_][kb_] = fma(pref, s, acc[ka_][kb_]);
                 }
             }
@@ -396,21 +392,35 @@ __global__ void __launch_bounds__(128)
             for (int kb_ = 0; kb_ < NCB; ++kb_) {
                 const int ax = cexp(LA, ka_, 0), ay = cexp(LA, ka_, 1), az = cexp(LA, ka_, 2);
                 const int bx = cexp(LB, kb_, 0), by = cexp(LB, kb_, 1), bz = cexp(LB, kb_, 2);
+                // one direction at a time, as in int3c_kernel; the p components
+                // read R one step further along x, y or z
                 double s0 = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
 #pragma unroll
-                for (int t = 0; t <= ax + bx; ++t)
+                for (int t = 0; t <= ax + bx; ++t) {
+                    double t0 = 0.0, tx = 0.0, ty = 0.0, tz = 0.0;
 #pragma unroll
                     for (int w = 0; w <= ay + by; ++w) {
-                        const double exy = Ex[ax][bx][t] * Ey[ay][by][w];
+                        double w0 = 0.0, wx = 0.0, wy = 0.0, wz = 0.0;
 #pragma unroll
                         for (int v = 0; v <= az + bz; ++v) {
-                            const double e = exy * Ez[az][bz][v];
-                            s0 = fma(e, R[t][w][v], s0);
-                            sx = fma(e, R[t + 1][w][v], sx);
-                            sy = fma(e, R[t][w + 1][v], sy);
-                            sz = fma(e, R[t][w][v + 1], sz);
+                            const double e = Ez[az][bz][v];
+                            w0 = fma(e, R[t][w][v], w0);
+                            wx = fma(e, R[t + 1][w][v], wx);
+                            wy = fma(e, R[t][w + 1][v], wy);
+                            wz = fma(e, R[t][w][v + 1], wz);
                         }
+                        const double e = Ey[ay][by][w];
+                        t0 = fma(e, w0, t0);
+                        tx = fma(e, wx, tx);
+                        ty = fma(e, wy, ty);
+                        tz = fma(e, wz, tz);
                     }
+                    const double e = Ex[ax][bx][t];
+                    s0 = fma(e, t0, s0);
+                    sx = fma(e, tx, sx);
+                    sy = fma(e, ty, sy);
+                    sz = fma(e, tz, sz);
+                }
                 acc[0][ka_][kb_] = fma(ps_, s0, acc[0][ka_][kb_]);
                 acc[1][ka_][kb_] = fma(pp_, sx, acc[1][ka_][kb_]);
                 acc[2][ka_][kb_] = fma(pp_, sy, acc[2][ka_][kb_]);

@@ -174,8 +174,15 @@ def run_native(args):
     t0.record(stream)
     nmv = 0
     infos = []
+    marks = []  # events around each build: the build / solve split of the step
     for _ in range(args.steps):
-        info = step()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        ctx.build()
+        b1.record(stream)
+        info = ctx.solve(want_x=True, device=True)[3]
+        marks.append((b0, b1))
         nmv += info.nmatvec
         infos.append(info)
     t1.record(stream)
@@ -253,6 +260,7 @@ def run_native(args):
                    "l2": "working set larger than L2 (B tensors %.2f GB, V/W %.2f GB), no flush"
                          % (8e-9 * d.naux_j * d.nocc * d.nvir, 16e-9 * 300 * d.nocc * d.nvir)},
         "s_to_states": ms_max / args.steps * 1e-3,
+        "build_s": sum(b0.elapsed_time(b1) for b0, b1 in marks) / args.steps * 1e-3,
         "matvec_only": {"value": nmv / (mv_ms * 1e-3) if mv_ms else None, "unit": "matvecs/s",
                         "note": "Davidson matvec time only (events around each block product)"},
         "davidson": {"niter": [i.niter for i in infos], "nmatvec": [i.nmatvec for i in infos],
@@ -325,13 +333,21 @@ def run_form(args, tdarisp, mol, C_dev, eps_dev, stream, barrier, precision, om6
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     nmv, infos, om = 0, [], None
+    marks = []  # events after each build: the build / solve split of the step
     for _ in range(args.steps):
-        om, X, rs, info = step()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        ctx.build()
+        b1.record(stream)
+        om, X, rs, info = ctx.solve(want_x=True, device=True)
+        marks.append((b0, b1))
         nmv += info.nmatvec
         infos.append(info)
     t1.record(stream)
     barrier()
     ms = t0.elapsed_time(t1)
+    build_ms = sum(b0.elapsed_time(b1) for b0, b1 in marks)
     prof = ctx.profile_get()
     ctx.close()
     om = om.cpu().numpy()
@@ -346,6 +362,7 @@ def run_form(args, tdarisp, mol, C_dev, eps_dev, stream, barrier, precision, om6
     return {
         "form": form["kind"],
         "value": nmv / (ms * 1e-3), "unit": "matvecs/s", "s_to_states": ms / args.steps * 1e-3,
+        "build_s": build_ms / args.steps * 1e-3, "solve_s": (ms - build_ms) / args.steps * 1e-3,
         "speedup_vs_fp64_value": None, "matvec_only": nmv / (mv_ms * 1e-3) if mv_ms else None,
         "dtype": form["dtype"],
         "max_abs_dOmega_vs_fp64_form_Ha": float(np.abs(om - om64).max()),

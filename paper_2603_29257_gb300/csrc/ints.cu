@@ -244,7 +244,9 @@ __device__ __forceinline__ double d_sph(int s, int k)
     }
 }
 
-template <int LA, int LB, int CD>
+// SACC (d-d): the NCA x NCB sums in shared memory, one column per thread, so
+// that the Hermite coefficients and R keep the registers.
+template <int LA, int LB, int CD, bool SACC>
 __global__ void __launch_bounds__(128)
     int3c_kernel(const ShellDev *__restrict__ sh, const int2 *__restrict__ pairs, const int2 *__restrict__ prange,
                  const double *__restrict__ prim, int npair, const AuxDev *__restrict__ aux, int nao,
@@ -254,17 +256,24 @@ __global__ void __launch_bounds__(128)
     constexpr int L = LA + LB + LC;
     constexpr int NCA = ncart(LA), NCB = ncart(LB);
     constexpr int DX = CD == 0, DY = CD == 1, DZ = CD == 2;
+    extern __shared__ double sacc[];
     const int ip = blockIdx.x * blockDim.x + threadIdx.x;
     if (ip >= npair) return;
     const AuxDev c = aux[blockIdx.y];
     const int2 pr = pairs[ip];
     const ShellDev A = sh[pr.x], B = sh[pr.y];
 
-    double acc[NCA][NCB];
+    double racc[SACC ? 1 : NCA][SACC ? 1 : NCB];
+    auto acc = [&](int i, int j) -> double & {
+        if constexpr (SACC)
+            return sacc[(i * NCB + j) * blockDim.x + threadIdx.x];
+        else
+            return racc[i][j];
+    };
 #pragma unroll
     for (int i = 0; i < NCA; ++i)
 #pragma unroll
-        for (int j = 0; j < NCB; ++j) acc[i][j] = 0.0;
+        for (int j = 0; j < NCB; ++j) acc(i, j) = 0.0;
 
     const double ce = c.e, ice = 1.0 / ce;
     const int2 rg = prange[ip];
@@ -311,7 +320,7 @@ __global__ void __launch_bounds__(128)
                         }
                         s = fma(Ex[ax][bx][t], st, s);
                     }
-                    acc[ka_][kb_] = fma(pref, s, acc[ka_][kb_]);
+                    acc(ka_, kb_) = fma(pref, s, acc(ka_, kb_));
                 }
             }
         }
@@ -332,7 +341,7 @@ __global__ void __launch_bounds__(128)
                 for (int kb_ = 0; kb_ < NCB; ++kb_) {
                     const double wb = LB == 2 ? d_sph(sb, kb_) : (kb_ == sb ? 1.0 : 0.0);
                     if (wb == 0.0) continue;
-                    v = fma(wa * wb, acc[ka_][kb_], v);
+                    v = fma(wa * wb, acc(ka_, kb_), v);
                 }
             }
             const int mu = A.ao + sa, nu = B.ao + sb;
@@ -347,27 +356,37 @@ __global__ void __launch_bounds__(128)
 // the Hermite integrals R up to LA+LB+1 serve the s component (R_tuv) and the
 // p components (R_{t+1,u,v}, ...), so the Boys values, R recursion and Hermite
 // expansion coefficients are shared.
-template <int LA, int LB>
-__global__ void __launch_bounds__(128)
+// SACC (the heavy classes d-p, d-d): the 4 x NCA x NCB sums live in shared
+// memory, one column per thread (sacc[k * blockDim.x + thread]), so that the
+// Hermite coefficients and R keep the registers; otherwise in registers.
+template <int LA, int LB, bool SACC>
+__global__ void __launch_bounds__(SACC ? 64 : 128)
     int3c_grp_kernel(const ShellDev *__restrict__ sh, const int2 *__restrict__ pairs, const int2 *__restrict__ prange,
                      const double *__restrict__ prim, int npair, const AuxDev *__restrict__ aux, int nao,
                      double *__restrict__ out, double ka, double kb, double omega, const double *__restrict__ boys)
 {
     constexpr int L = LA + LB + 1;
     constexpr int NCA = ncart(LA), NCB = ncart(LB);
+    extern __shared__ double sacc[];
     const int ip = blockIdx.x * blockDim.x + threadIdx.x;
     if (ip >= npair) return;
     const AuxDev c = aux[blockIdx.y];
     const int2 pr = pairs[ip];
     const ShellDev A = sh[pr.x], B = sh[pr.y];
 
-    double acc[4][NCA][NCB];
+    double racc[SACC ? 1 : 4][SACC ? 1 : NCA][SACC ? 1 : NCB];
+    auto acc = [&](int f, int i, int j) -> double & {
+        if constexpr (SACC)
+            return sacc[((f * NCA + i) * NCB + j) * blockDim.x + threadIdx.x];
+        else
+            return racc[f][i][j];
+    };
 #pragma unroll
     for (int f = 0; f < 4; ++f)
 #pragma unroll
         for (int i = 0; i < NCA; ++i)
 #pragma unroll
-            for (int j = 0; j < NCB; ++j) acc[f][i][j] = 0.0;
+            for (int j = 0; j < NCB; ++j) acc(f, i, j) = 0.0;
     const double ce = c.e, ice = 1.0 / ce;
     const int2 rg = prange[ip];
     for (int q = rg.x; q < rg.x + rg.y; ++q) {
@@ -421,10 +440,10 @@ __global__ void __launch_bounds__(128)
                     sy = fma(e, ty, sy);
                     sz = fma(e, tz, sz);
                 }
-                acc[0][ka_][kb_] = fma(ps_, s0, acc[0][ka_][kb_]);
-                acc[1][ka_][kb_] = fma(pp_, sx, acc[1][ka_][kb_]);
-                acc[2][ka_][kb_] = fma(pp_, sy, acc[2][ka_][kb_]);
-                acc[3][ka_][kb_] = fma(pp_, sz, acc[3][ka_][kb_]);
+                acc(0, ka_, kb_) = fma(ps_, s0, acc(0, ka_, kb_));
+                acc(1, ka_, kb_) = fma(pp_, sx, acc(1, ka_, kb_));
+                acc(2, ka_, kb_) = fma(pp_, sy, acc(2, ka_, kb_));
+                acc(3, ka_, kb_) = fma(pp_, sz, acc(3, ka_, kb_));
             }
         }
     }
@@ -445,7 +464,7 @@ __global__ void __launch_bounds__(128)
                     for (int kb_ = 0; kb_ < NCB; ++kb_) {
                         const double wb = LB == 2 ? d_sph(sb, kb_) : (kb_ == sb ? 1.0 : 0.0);
                         if (wb == 0.0) continue;
-                        v = fma(wa * wb, acc[f][ka_][kb_], v);
+                        v = fma(wa * wb, acc(f, ka_, kb_), v);
                     }
                 }
                 const int mu = A.ao + sa, nu = B.ao + sb;
@@ -463,19 +482,29 @@ void launch_pair_class(Prof &prof, const cudaStream_t *streams, int nstreams, in
                        double ka, double kb, double omega, const double *boys)
 {
     static const char *names[6] = {"int3c_ss", "int3c_ps", "int3c_pp", "int3c_ds", "int3c_dp", "int3c_dd"};
-    if constexpr (ncart(LA) * ncart(LB) <= 9) {
-        if (natoms > 0 && npair > 0) {
-            // whole J atoms (s + p) in one pass; light classes only (registers)
-            cudaStream_t st = streams[next++ % nstreams];
-            dim3 grid(cdiv(npair, 128), natoms);
-            double bytes = 8.0 * 2.0 * 4 * npair * natoms * (2 * LA + 1) * (2 * LB + 1);
-            int tok = prof.begin(st, names[cls], 0, bytes);
-            int3c_grp_kernel<LA, LB><<<grid, 128, 0, st>>>(sh, pairs, prange, prim, npair, atoms, nao, out, ka, kb,
-                                                           omega, boys);
-            TR_CUDA(cudaGetLastError());
-            prof.end(st, tok);
-            return;
-        }
+    if constexpr (ncart(LA) * ncart(LB) <= 18) {
+    if (natoms > 0 && npair > 0) {
+        // whole J atoms (s + p) in one pass: sums in registers for the light
+        // classes, in shared memory for d-p (d-d runs per component: its Hermite
+        // coefficients and R alone fill the registers)
+        constexpr bool SACC = ncart(LA) * ncart(LB) > 9;
+        constexpr int NT = SACC ? 64 : 128;
+        constexpr size_t SMEM = SACC ? sizeof(double) * 4 * ncart(LA) * ncart(LB) * NT : 0;
+        static const cudaError_t attr =
+            SMEM > 48 * 1024 ? cudaFuncSetAttribute(int3c_grp_kernel<LA, LB, SACC>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM)
+                             : cudaSuccess;
+        TR_CUDA(attr);
+        cudaStream_t st = streams[next++ % nstreams];
+        dim3 grid(cdiv(npair, NT), natoms);
+        double bytes = 8.0 * 2.0 * 4 * npair * natoms * (2 * LA + 1) * (2 * LB + 1);
+        int tok = prof.begin(st, names[cls], 0, bytes);
+        int3c_grp_kernel<LA, LB, SACC><<<grid, NT, SMEM, st>>>(sh, pairs, prange, prim, npair, atoms, nao, out, ka,
+                                                                kb, omega, boys);
+        TR_CUDA(cudaGetLastError());
+        prof.end(st, tok);
+        return;
+    }
     }
     for (int cd = -1; cd <= 2; ++cd) {
         int n = aoff[cd + 2] - aoff[cd + 1];
@@ -485,11 +514,14 @@ void launch_pair_class(Prof &prof, const cudaStream_t *streams, int nstreams, in
         const AuxDev *a = aux + aoff[cd + 1];
         double bytes = 8.0 * 2.0 * npair * n * (2 * LA + 1) * (2 * LB + 1);
         int tok = prof.begin(st, names[cls], 0, bytes);
+        // d-d: sums in shared memory (36 x 128 doubles)
+        constexpr bool SACC = ncart(LA) * ncart(LB) > 18;
+        constexpr size_t SMEM = SACC ? sizeof(double) * ncart(LA) * ncart(LB) * 128 : 0;
         switch (cd) {
-            case -1: int3c_kernel<LA, LB, -1><<<grid, 128, 0, st>>>(sh, pairs, prange, prim, npair, a, nao, out, ka, kb, omega, boys); break;
-            case 0: int3c_kernel<LA, LB, 0><<<grid, 128, 0, st>>>(sh, pairs, prange, prim, npair, a, nao, out, ka, kb, omega, boys); break;
-            case 1: int3c_kernel<LA, LB, 1><<<grid, 128, 0, st>>>(sh, pairs, prange, prim, npair, a, nao, out, ka, kb, omega, boys); break;
-            default: int3c_kernel<LA, LB, 2><<<grid, 128, 0, st>>>(sh, pairs, prange, prim, npair, a, nao, out, ka, kb, omega, boys); break;
+            case -1: int3c_kernel<LA, LB, -1, SACC><<<grid, 128, SMEM, st>>>(sh, pairs, prange, prim, npair, a, nao, out, ka, kb, omega, boys); break;
+            case 0: int3c_kernel<LA, LB, 0, SACC><<<grid, 128, SMEM, st>>>(sh, pairs, prange, prim, npair, a, nao, out, ka, kb, omega, boys); break;
+            case 1: int3c_kernel<LA, LB, 1, SACC><<<grid, 128, SMEM, st>>>(sh, pairs, prange, prim, npair, a, nao, out, ka, kb, omega, boys); break;
+            default: int3c_kernel<LA, LB, 2, SACC><<<grid, 128, SMEM, st>>>(sh, pairs, prange, prim, npair, a, nao, out, ka, kb, omega, boys); break;
         }
         TR_CUDA(cudaGetLastError());
         prof.end(st, tok);

@@ -48,9 +48,12 @@ __global__ void to_f32(const double *__restrict__ x, float *__restrict__ y, long
 __global__ void mixed_diag(const double *__restrict__ D, const double *__restrict__ X, double *__restrict__ AX,
                            long long nov, int m)
 {
-    const long long tot = nov * m;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x)
-        AX[t] = D[t % nov] * X[t];
+    // one pass over the index ia: D read once, then the m vectors (no division per element)
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nov; i += (long long)gridDim.x * blockDim.x) {
+        const double d = D[i];
+#pragma unroll 4
+        for (int j = 0; j < m; ++j) AX[(long long)j * nov + i] = d * X[(long long)j * nov + i];
+    }
 }
 
 unsigned gfor(long long n) { return (unsigned)std::max<long long>(1, std::min<long long>(cdiv(n, 256), 152 * 16)); }
@@ -172,7 +175,7 @@ void matvec_mixed(tr_ctx *c, int m, const double *X, double *AX)
         const int mm = std::min(mb, m - m0);
         const double *x = X + (long long)m0 * nov;
         double *ax = AX + (long long)m0 * nov;
-        TR_LAUNCH(pf, st, "diag", 0, 24.0 * nov * mm, mixed_diag<<<gfor(nov * mm), 256, 0, st>>>(c->D.p, x, ax, nov, mm));
+        TR_LAUNCH(pf, st, "diag", 0, 8.0 * nov * (2.0 * mm + 1.0), mixed_diag<<<gfor(nov), 256, 0, st>>>(c->D.p, x, ax, nov, mm));
         TR_LAUNCH(pf, st, "prepare_f32", 0, 12.0 * nov * mm,
                   mixed_prepare<<<gfor(nov * mm), 256, 0, st>>>(x, c->X32.p, c->k_active ? c->Xw_h.p : nullptr,
                                                                  c->k_active ? c->Xw_l.p : nullptr, mm, nocc, nvir,

@@ -53,9 +53,12 @@ double *scratch_address(int dev)
 __global__ void na_diag(const double *__restrict__ D, const double *__restrict__ X, double *__restrict__ AX,
                         long long nov, int m)
 {
-    const long long tot = nov * m;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x)
-        AX[t] = D[t % nov] * X[t];
+    // one pass over the index ia: D read once, then the m vectors (no division per element)
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nov; i += (long long)gridDim.x * blockDim.x) {
+        const double d = D[i];
+#pragma unroll 4
+        for (int j = 0; j < m; ++j) AX[(long long)j * nov + i] = d * X[(long long)j * nov + i];
+    }
 }
 
 __global__ void na_gather(const double *__restrict__ X, double *__restrict__ Xw, int m, int nocc, int nvir,
@@ -118,7 +121,7 @@ void matvec_noalloc(tr_ctx *c, int m, const double *X, double *AX)
         const int mm = std::min(mb, m - m0);
         const double *x = X + (long long)m0 * nov;
         double *ax = AX + (long long)m0 * nov;
-        TR_LAUNCH(lp, st, "diag", 0, 0, na_diag<<<na_grid(nov * mm), 256, 0, st>>>(c->D.p, x, ax, nov, mm));
+        TR_LAUNCH(lp, st, "diag", 0, 0, na_diag<<<na_grid(nov), 256, 0, st>>>(c->D.p, x, ax, nov, mm));
         if (nJ) {
             dgemm(lp, st, "J_contract", false, true, nJ, mm, (int)nov, 1.0, c->Y.p, nov, x, nov, 0.0, Z, mm,
                   Batch(), ws, SPLITK_DOUBLES);

@@ -24,10 +24,12 @@ constexpr double HARTREE_EV = 27.211386245988;
 __global__ void diag_kernel(const double *__restrict__ D, const double *__restrict__ X,
                             double *__restrict__ AX, long long nov, int m)
 {
-    long long tot = nov * m;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-         t += (long long)gridDim.x * blockDim.x)
-        AX[t] = D[t % nov] * X[t];
+    // one pass over the index ia: D read once, then the m vectors (no division per element)
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nov; i += (long long)gridDim.x * blockDim.x) {
+        const double d = D[i];
+#pragma unroll 4
+        for (int j = 0; j < m; ++j) AX[(long long)j * nov + i] = d * X[(long long)j * nov + i];
+    }
 }
 
 __global__ void gather_window(const double *__restrict__ X, double *__restrict__ Xw, int m, int nocc,
@@ -665,8 +667,8 @@ void matvec(tr_ctx *c, int m, const double *X, double *AX)
         const double *x = X + (long long)m0 * nov;
         double *ax = AX + (long long)m0 * nov;
         // diagonal (e_a - e_i) X
-        TR_LAUNCH(pf, st, "diag", 0, 24.0 * nov * mm,
-                  diag_kernel<<<grid_for(nov * mm), 256, 0, st>>>(c->D.p, x, ax, nov, mm));
+        TR_LAUNCH(pf, st, "diag", 0, 8.0 * nov * (2.0 * mm + 1.0),
+                  diag_kernel<<<grid_for(nov), 256, 0, st>>>(c->D.p, x, ax, nov, mm));
         if (nJ) {
             // Z = (Q|jb) X ; Zt = (P|Q)^-1 Z ; AX += 2 (P|ia) Zt
             dgemm(pf, st, "J_contract", false, true, nJ, mm, (int)nov, 1.0, c->Y.p, nov, x, nov, 0.0,
@@ -789,8 +791,8 @@ void matvec_tc(tr_ctx *c, int m, const double *X, double *AX)
         const int mm = std::min(mb, m - m0);
         const double *x = X + (long long)m0 * nov;
         double *ax = AX + (long long)m0 * nov;
-        TR_LAUNCH(pf, st, "diag", 0, 24.0 * nov * mm,
-                  diag_kernel<<<grid_for(nov * mm), 256, 0, st>>>(c->D.p, x, ax, nov, mm));
+        TR_LAUNCH(pf, st, "diag", 0, 8.0 * nov * (2.0 * mm + 1.0),
+                  diag_kernel<<<grid_for(nov), 256, 0, st>>>(c->D.p, x, ax, nov, mm));
         if (nJ) {
             OzMat Xs, Zs;
             oz_bind(Xs, c->ozw_X.p, mm, (int)nov, S);

@@ -24,7 +24,7 @@ namespace tr {
 void boys_table(std::vector<double> &tab)
 {
     tab.assign((size_t)BOYS_NPTS * BOYS_NCOL, 0.0);
-    const int nmax = BOYS_NCOL - 1;
+    const int nmax = BOYS_COL_EXP - 1;
     for (int k = 0; k < BOYS_NPTS; ++k) {
         long double T = (long double)k * (long double)BOYS_DT;
         // F_nmax(T) = e^{-T} sum_j (2T)^j / prod_{i=0..j} (2 nmax + 2i + 1)
@@ -35,10 +35,11 @@ void boys_table(std::vector<double> &tab)
             if (term <= sum * 1e-21L) break;
         }
         long double e = expl(-T);
-        long double f[BOYS_NCOL];
+        long double f[BOYS_COL_EXP];
         f[nmax] = e * sum;
         for (int n = nmax - 1; n >= 0; --n) f[n] = (2.0L * T * f[n + 1] + e) / (long double)(2 * n + 1);
         for (int n = 0; n <= nmax; ++n) tab[(size_t)k * BOYS_NCOL + n] = (double)f[n];
+        tab[(size_t)k * BOYS_NCOL + BOYS_COL_EXP] = (double)e;
     }
 }
 
@@ -101,7 +102,6 @@ PairList make_pairs(const std::vector<ShellDev> &sh, const std::vector<double> &
 
 namespace {
 
-constexpr double PI_D = 3.14159265358979323846;
 constexpr double TWO_PI_52 = 34.98683665524972;  // 2 pi^{5/2}
 
 __host__ __device__ constexpr int ncart(int l) { return (l + 1) * (l + 2) / 2; }
@@ -120,27 +120,35 @@ __host__ __device__ constexpr int cexp(int l, int k, int d)
 template <int L>
 __device__ __forceinline__ void boys_eval(double T, const double *__restrict__ tab, double *F)
 {
+    // F_L first, then the downward recursion F_n = (2T F_{n+1} + e^{-T}) / (2n+1)
+    double e = 0.0;
     if (T < BOYS_TMAX) {
-        int k = __double2int_rn(T * (1.0 / BOYS_DT));
-        double dT = k * BOYS_DT - T;
-        const double *f = tab + k * BOYS_NCOL + L;
+        const int k = __double2int_rn(T * (1.0 / BOYS_DT));
+        const double dT = k * BOYS_DT - T;  // T_k - T, |dT| <= 1/64
+        const double *f = tab + k * BOYS_NCOL;
         // F_L(T) = sum_j F_{L+j}(T_k) (T_k - T)^j / j!
-        double s = __ldg(f + 6);
+        double s = __ldg(f + L + 6);
 #pragma unroll
-        for (int j = 5; j >= 0; --j) s = fma(s, dT * (1.0 / (j + 1)), __ldg(f + j));
+        for (int j = 5; j >= 0; --j) s = fma(s, dT * (1.0 / (j + 1)), __ldg(f + L + j));
         F[L] = s;
         if (L > 0) {
-            double e = exp(-T);
+            // e^{-T} = e^{-T_k} e^{T_k - T}: degree-8 Taylor polynomial of e^{dT}
+            double x = 1.0;
 #pragma unroll
-            for (int n = L - 1; n >= 0; --n) F[n] = fma(2.0 * T, F[n + 1], e) * (1.0 / (2 * n + 1));
+            for (int j = 8; j >= 1; --j) x = fma(x, dT * (1.0 / j), 1.0);
+            e = __ldg(f + BOYS_COL_EXP) * x;
         }
     } else {
-        double e = exp(-T);
-        F[0] = 0.5 * sqrt(PI_D / T);
-        double h = 0.5 / T;
+        // F_n(T) = (2n-1)!! / 2^{n+1} sqrt(pi) T^{-n-1/2} up to terms in e^{-T} (< 1e-26)
+        const double r = rsqrt(T);
+        const double h = 0.5 * r * r;       // 1 / (2T)
+        double fn = 0.88622692545275801365 * r;  // sqrt(pi) / 2 / sqrt(T)
 #pragma unroll
-        for (int n = 0; n < L; ++n) F[n + 1] = ((2 * n + 1) * F[n] - e) * h;
+        for (int n = 0; n < L; ++n) fn *= (2 * n + 1) * h;
+        F[L] = fn;
     }
+#pragma unroll
+    for (int n = L - 1; n >= 0; --n) F[n] = fma(2.0 * T, F[n + 1], e) * (1.0 / (2 * n + 1));
 }
 
 // R^n_000 = (-2 rho)^n G_n for the operator (ka + kb erf(omega r))/r

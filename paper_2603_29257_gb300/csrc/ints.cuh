@@ -21,12 +21,13 @@ struct AuxDev {
     int comp, out;
 };
 
-constexpr int BOYS_NPTS = 1281;          // T = 0 .. 40 step 1/32
-constexpr int BOYS_NCOL = 13;            // F_0 .. F_12
+constexpr int BOYS_NPTS = 1921;          // T = 0 .. 60 step 1/32
+constexpr int BOYS_NCOL = 14;            // F_0 .. F_12, then e^{-T}
+constexpr int BOYS_COL_EXP = 13;
 constexpr double BOYS_DT = 1.0 / 32.0;
-constexpr double BOYS_TMAX = 40.0;
+constexpr double BOYS_TMAX = 60.0;       // beyond: asymptotic form (e^{-T} < 1e-26 dropped)
 
-// Host: tabulate F_n(T_k) for the device Taylor interpolation.
+// Host: tabulate F_n(T_k) and e^{-T_k} for the device Taylor interpolation.
 void boys_table(std::vector<double> &tab);
 
 // AO shell pairs grouped by angular class (la, lb), la >= lb, in the order

@@ -372,7 +372,7 @@ def run_form(args, tdarisp, mol, C_dev, eps_dev, stream, barrier, precision, om6
                      "useful_tflops": useful, "peak": peak, "unit": "TFLOP/s",
                      "frac": form["products"] * useful / peak, "peak_source": peak_src, "note": form["note"]},
         "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]}
-                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
+                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:16]},
     }
 
 

@@ -1,15 +1,17 @@
 // Tensor-core GEMM C = A B^T on GB300 (sm_103a): tcgen05.mma kind::tf32.
 //
-// One CTA computes a 128 x 128 output tile of one batch entry.  Warp 0 (one
-// lane) streams 128 x 32 FP32 tiles of A and B through a 3-stage ring of
-// shared memory with TMA (cp.async.bulk.tensor, 128-byte swizzle, completion
-// on an mbarrier); warp 1 (one lane) issues tcgen05.mma into a 128-column
-// FP32 accumulator in tensor memory and releases each stage with
-// tcgen05.commit; after the last commit all four warps read their 32 TMEM
-// lanes with tcgen05.ld and write the tile.  With three products
-// (hi*hi + hi*lo + lo*hi) the result carries close to FP32 accuracy.
-// Every mbarrier wait gives up after ~1 s: it records an error code in *err
-// and the CTA skips ahead to its teardown (tensor memory is always freed).
+// Persistent: one CTA per SM walks the 128 x BN output tiles (N tile fastest,
+// then M tile, then batch entry).  Warp 0 (one lane) streams 128 x 32 FP32
+// tiles of A and B through a ring of shared-memory stages with TMA
+// (cp.async.bulk.tensor, 128-byte swizzle, completion on an mbarrier); warp 1
+// (one lane) issues tcgen05.mma into one of two FP32 accumulator sets in
+// tensor memory and releases each stage with tcgen05.commit; warps 2..5 drain
+// a finished set (tcgen05.ld, 32 TMEM lanes each) and write the tile while the
+// products of the next tile go on in the other set.  With three products
+// (hi*hi + hi*lo + lo*hi) the result carries close to FP32 accuracy.  Stage
+// and accumulator barrier phases run on across tiles.  Every mbarrier wait
+// gives up after ~1 s: it records an error code in *err and the warp skips to
+// the teardown (copies in flight are awaited, tensor memory is always freed).
 #include "tcgemm.cuh"
 #include "tcptx.cuh"
 
@@ -26,6 +28,8 @@ constexpr int TILE_BYTES = BM * BKF * 4;      // 16 KB (A tile; a B tile is BN *
 struct TcArgs {
     int M, N, K, n2;
     int ka0, kb0;                 // K offsets (elements) into the A and B rows
+    int ntn, ntm;                 // N and M tiles per batch entry
+    long long ntiles;             // ntn x ntm x batch entries
     long long a0, a1, a2, c0, c1, c2;
     TcOut out;
     int *err;
@@ -44,62 +48,103 @@ __device__ __forceinline__ float tf32_rest(float v)
     return v - __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
 }
 
-template <int NSPLIT, int STAGES, int BN>
-constexpr uint32_t stage_bytes()
+template <int NSPLIT, int BN>
+struct TcCfg {
+    static constexpr int BTILE = BN * BKF * 4;
+    // stage layout: A value | B value | A remainder | B remainder
+    static constexpr uint32_t STAGE = (NSPLIT == 3 ? 2u : 1u) * (uint32_t)(TILE_BYTES + BTILE);
+    static constexpr int TBYTES = 4 * 32 * 33 * 4;  // epilogue transpose buffers: 4 warps x 32 x 33 floats
+    static constexpr int FIT = (int)((227 * 1024 - TBYTES - 1024 - 256) / STAGE);
+    static constexpr int STAGES = FIT > 4 ? 4 : FIT;
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE + TBYTES + 1024 + 256;
+    static constexpr int TCOLS = 2 * BN;  // two accumulator sets
+    static_assert(STAGES >= 2 && SMEM <= 227 * 1024, "shared memory");
+};
+
+// output tile t: N tile fastest, then M tile, then batch entry
+struct TcTile {
+    int m0, n0, b1, b2, arow, brow;
+};
+
+__device__ __forceinline__ TcTile tc_tile(const TcArgs &g, long long t, int BN)
 {
-    return (NSPLIT == 3 ? 2u : 1u) * (uint32_t)(TILE_BYTES + BN * BKF * 4);
+    TcTile u;
+    const int nt = (int)(t % g.ntn);
+    const long long r = t / g.ntn;
+    const int mt = (int)(r % g.ntm);
+    const int b = (int)(r / g.ntm);
+    u.b1 = b / g.n2;
+    u.b2 = b - u.b1 * g.n2;
+    u.m0 = mt * BM;
+    u.n0 = nt * BN;
+    u.arow = (int)(g.a0 + g.a1 * u.b1 + g.a2 * u.b2) + u.m0;
+    u.brow = (int)(g.c0 + g.c1 * u.b1 + g.c2 * u.b2) + u.n0;
+    return u;
 }
 
 template <int NSPLIT, int MODE, int BN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(192, 1)
     tc_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
               const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl, const TcArgs g)
 {
-    constexpr int STAGES = NSPLIT == 3 ? (BN == 64 ? 4 : 3) : 4;
-    constexpr int BTILE = BN * BKF * 4;
-    constexpr uint32_t STAGE_BYTES = stage_bytes<NSPLIT, STAGES, BN>();
-    // stage layout: A value | B value | A remainder | B remainder
+    using C = TcCfg<NSPLIT, BN>;
+    constexpr int ST = C::STAGES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *bars = (uint64_t *)(smem + STAGES * STAGE_BYTES);  // full[S], empty[S], done
-    uint32_t *tslot = (uint32_t *)(bars + 2 * STAGES + 1);
+    float *tbuf = (float *)(smem + ST * C::STAGE);
+    // barriers: full[ST], empty[ST], acc_full[2], acc_empty[2]
+    uint64_t *bars = (uint64_t *)(smem + ST * C::STAGE + C::TBYTES);
+    uint32_t *tslot = (uint32_t *)(bars + 2 * ST + 4);
+    const uint32_t FULL = sa(&bars[0]), EMPTY = sa(&bars[ST]);
+    const uint32_t ACCF = sa(&bars[2 * ST]), ACCE = sa(&bars[2 * ST + 2]);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int b = blockIdx.z, b1 = b / g.n2, b2 = b - b1 * g.n2;
-    const int arow = (int)(g.a0 + g.a1 * b1 + g.a2 * b2) + m0;
-    const int brow = (int)(g.c0 + g.c1 * b1 + g.c2 * b2) + n0;
     const int nk = (g.K + BKF - 1) / BKF;
+    const long long ntiles = g.ntiles;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < 2 * STAGES + 1; ++s) bar_init(sa(&bars[s]), 1);
+        for (int i = 0; i < 2 * ST + 2; ++i) bar_init(sa(&bars[i]), 1);
+        for (int i = 0; i < 2; ++i) bar_init(ACCE + 8 * i, 4);  // one arrival per epilogue warp
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(tslot)), "r"(BN)
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(tslot)),
+                     "r"(C::TCOLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    fence_before();
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    fence_after();
     const uint32_t tmem = *tslot;
 
     if (warp == 0) {
         if (lane == 0) {
-            for (int kt = 0; kt < nk; ++kt) {
-                const int s = kt % STAGES;
-                if (kt >= STAGES && !bar_wait(sa(&bars[STAGES + s]), ((kt / STAGES) - 1) & 1, g.err, 1)) break;
-                const uint32_t full = sa(&bars[s]);
-                bar_expect(full, STAGE_BYTES);
-                uint8_t *stg = smem + s * STAGE_BYTES;
-                const int xa = g.ka0 + kt * BKF, xb = g.kb0 + kt * BKF;
-                tma2d(sa(stg), &tAh, xa, arow, full);
-                tma2d(sa(stg + TILE_BYTES), &tBh, xb, brow, full);
-                if (NSPLIT == 3) {
-                    tma2d(sa(stg + TILE_BYTES + BTILE), &tAl, xa, arow, full);
-                    tma2d(sa(stg + 2 * TILE_BYTES + BTILE), &tBl, xb, brow, full);
+            long long gk = 0;
+            bool ok = true;
+            for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const TcTile u = tc_tile(g, t, BN);
+                for (int kt = 0; kt < nk; ++kt) {
+                    const int s = (int)(gk % ST);
+                    if (gk >= ST && !bar_wait(EMPTY + 8 * s, (uint32_t)(((gk / ST) - 1) & 1), g.err, 1)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t full = FULL + 8 * s;
+                    bar_expect(full, C::STAGE);
+                    uint8_t *stg = smem + s * C::STAGE;
+                    const int xa = g.ka0 + kt * BKF, xb = g.kb0 + kt * BKF;
+                    tma2d(sa(stg), &tAh, xa, u.arow, full);
+                    tma2d(sa(stg + TILE_BYTES), &tBh, xb, u.brow, full);
+                    if (NSPLIT == 3) {
+                        tma2d(sa(stg + TILE_BYTES + C::BTILE), &tAl, xa, u.arow, full);
+                        tma2d(sa(stg + 2 * TILE_BYTES + C::BTILE), &tBl, xb, u.brow, full);
+                    }
+                    ++gk;
                 }
             }
+            // copies still in flight complete before the CTA ends
+            for (long long q = gk > ST ? gk - ST : 0; q < gk; ++q)
+                bar_wait(FULL + 8 * (int)(q % ST), (uint32_t)((q / ST) & 1), g.err, 5);
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -108,60 +153,94 @@ __global__ void __launch_bounds__(128, 1)
             // K-major, N = BN, M = 128
             const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                    ((uint32_t)(BM >> 4) << 24);
-            for (int kt = 0; kt < nk; ++kt) {
-                const int s = kt % STAGES;
-                if (!bar_wait(sa(&bars[s]), (kt / STAGES) & 1, g.err, 2)) break;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                uint8_t *stg = smem + s * STAGE_BYTES;
-                const uint64_t dA = smem_desc(sa(stg)), dB = smem_desc(sa(stg + TILE_BYTES));
-                const uint64_t dAl = smem_desc(sa(stg + TILE_BYTES + BTILE));
-                const uint64_t dBl = smem_desc(sa(stg + 2 * TILE_BYTES + BTILE));
-#pragma unroll
-                for (int kk = 0; kk < BKF / 8; ++kk) {
-                    mma(tmem, dA + 2 * kk, dB + 2 * kk, idesc, (kt | kk) ? 1u : 0u);
-                    if (NSPLIT == 3) {
-                        mma(tmem, dA + 2 * kk, dBl + 2 * kk, idesc, 1u);
-                        mma(tmem, dAl + 2 * kk, dB + 2 * kk, idesc, 1u);
+            long long gk = 0, tc = 0;
+            bool ok = true;
+            for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tc) {
+                const int buf = (int)(tc & 1);
+                if (tc >= 2) {
+                    // the epilogue has drained the tile that last used this accumulator set
+                    if (!bar_wait(ACCE + 8 * buf, (uint32_t)(((tc / 2) - 1) & 1), g.err, 6)) {
+                        ok = false;
+                        break;
                     }
+                    fence_after();
                 }
-                commit(sa(&bars[STAGES + s]));
+                const uint32_t acc = tmem + (uint32_t)(buf * BN);
+                for (int kt = 0; kt < nk; ++kt) {
+                    const int s = (int)(gk % ST);
+                    if (!bar_wait(FULL + 8 * s, (uint32_t)((gk / ST) & 1), g.err, 2)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    uint8_t *stg = smem + s * C::STAGE;
+                    const uint64_t dA = smem_desc(sa(stg)), dB = smem_desc(sa(stg + TILE_BYTES));
+                    const uint64_t dAl = smem_desc(sa(stg + TILE_BYTES + C::BTILE));
+                    const uint64_t dBl = smem_desc(sa(stg + 2 * TILE_BYTES + C::BTILE));
+#pragma unroll
+                    for (int kk = 0; kk < BKF / 8; ++kk) {
+                        mma(acc, dA + 2 * kk, dB + 2 * kk, idesc, (kt | kk) ? 1u : 0u);
+                        if (NSPLIT == 3) {
+                            mma(acc, dA + 2 * kk, dBl + 2 * kk, idesc, 1u);
+                            mma(acc, dAl + 2 * kk, dB + 2 * kk, idesc, 1u);
+                        }
+                    }
+                    commit(EMPTY + 8 * s);
+                    ++gk;
+                }
+                if (!ok) break;
+                commit(ACCF + 8 * buf);
             }
-            commit(sa(&bars[2 * STAGES]));
         }
         __syncwarp();
-    }
-
-    const bool ok = bar_wait(sa(&bars[2 * STAGES]), 0, g.err, 3);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
+    } else {
+        // epilogue warps 2..5; a warp may read TMEM lanes 32 (warp % 4) .. + 31
+        const int quarter = warp & 3;
+        float *tb = tbuf + (warp - 2) * 32 * 33;
         const TcOut &o = g.out;
-        const long long base = o.s1 * b1 + o.s2 * b2;
-        const int rloc = 32 * warp + lane;
-        const int row = m0 + rloc;
-        // warp-private transpose buffer in the (now idle) pipeline ring
-        double *tb = (double *)smem + warp * 32 * 33;
-        for (int c0 = 0; c0 < BN && n0 + c0 < g.N; c0 += 32) {
-            uint32_t r[32];
-            const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                : "r"(ta));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (o.ldm == 1) {
-                // consecutive lanes hold consecutive rows: write directly (coalesced)
-                if (row < g.M) {
+        long long tc = 0;
+        for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++tc) {
+            const TcTile u = tc_tile(g, t, BN);
+            const int buf = (int)(tc & 1);
+            if (!bar_wait(ACCF + 8 * buf, (uint32_t)((tc / 2) & 1), g.err, 3)) break;
+            fence_after();
+            const long long base = o.s1 * u.b1 + o.s2 * u.b2;
+            const int row = u.m0 + 32 * quarter + lane;
+            for (int c0 = 0; c0 < BN && u.n0 + c0 < g.N; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(buf * BN + c0), r);
+                if (o.ldm == 1) {
+                    // consecutive lanes hold consecutive rows: write directly (coalesced)
+                    if (row < g.M) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int col = n0 + c0 + j;
-                        if (col >= g.N) break;
-                        const long long off = base + (long long)row + (long long)col * o.ldn;
-                        const float v = __uint_as_float(r[j]);
+                        for (int j = 0; j < 32; ++j) {
+                            const int col = u.n0 + c0 + j;
+                            if (col >= g.N) break;
+                            const long long off = base + (long long)row + (long long)col * o.ldn;
+                            const float v = __uint_as_float(r[j]);
+                            if (MODE == TC_SPLIT) {
+                                o.hi[off] = v;
+                                o.lo[off] = tf32_rest(v);
+                            } else if (MODE == TC_STORE32) {
+                                o.hi[off] = v;
+                            } else if (MODE == TC_ACC64) {
+                                o.d[off] += o.alpha * (double)v;
+                            } else {
+                                o.d[off] = o.alpha * (double)v;
+                            }
+                        }
+                    }
+                } else {
+                    // transpose 32 x 32 through this warp's buffer so that lanes walk columns
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) tb[lane * 33 + j] = __uint_as_float(r[j]);
+                    __syncwarp();
+                    const int col = u.n0 + c0 + lane;
+                    for (int rr = 0; rr < 32; ++rr) {
+                        const int rw = u.m0 + 32 * quarter + rr;
+                        if (rw >= g.M || col >= g.N) continue;
+                        const long long off = base + (long long)rw * o.ldm + (long long)col * o.ldn;
+                        const float v = tb[rr * 33 + lane];
                         if (MODE == TC_SPLIT) {
                             o.hi[off] = v;
                             o.lo[off] = tf32_rest(v);
@@ -173,39 +252,19 @@ __global__ void __launch_bounds__(128, 1)
                             o.d[off] = o.alpha * (double)v;
                         }
                     }
+                    __syncwarp();
                 }
-            } else {
-                // transpose 32 x 32 through shared memory so that lanes walk columns
-#pragma unroll
-                for (int j = 0; j < 32; ++j) tb[lane * 33 + j] = (double)__uint_as_float(r[j]);
-                __syncwarp();
-                const int col = n0 + c0 + lane;
-                for (int rr = 0; rr < 32; ++rr) {
-                    const int rw = m0 + 32 * warp + rr;
-                    if (rw >= g.M || col >= g.N) continue;
-                    const long long off = base + (long long)rw * o.ldm + (long long)col * o.ldn;
-                    const double v = tb[rr * 33 + lane];
-                    if (MODE == TC_SPLIT) {
-                        const float f = (float)v;
-                        o.hi[off] = f;
-                        o.lo[off] = tf32_rest(f);
-                    } else if (MODE == TC_STORE32) {
-                        o.hi[off] = (float)v;
-                    } else if (MODE == TC_ACC64) {
-                        o.d[off] += o.alpha * v;
-                    } else {
-                        o.d[off] = o.alpha * v;
-                    }
-                }
-                __syncwarp();
             }
+            // the accumulator set is free for the tile after next
+            fence_before();
+            __syncwarp();
+            if (lane == 0) bar_arrive(ACCE + 8 * buf);
         }
-        (void)rloc;
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    fence_before();
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TCOLS) : "memory");
 }
 
 __global__ void split_kernel(const double *__restrict__ x, long long rows, long long cols, long long ldi,
@@ -228,15 +287,15 @@ void encode(CUtensorMap &tm, const float *p, long long rows, long long kdim, lon
 template <int NSPLIT, int MODE, int BN>
 void launch(cudaStream_t st, dim3 grid, const TcMat &A, const TcMat &B, const TcArgs &g)
 {
-    constexpr int STAGES = NSPLIT == 3 ? (BN == 64 ? 4 : 3) : 4;
-    const size_t smem = (size_t)STAGES * stage_bytes<NSPLIT, STAGES, BN>() + 1024 + 256;
+    using C = TcCfg<NSPLIT, BN>;
     // set once per kernel instance (thread-safe static initialisation)
     static const cudaError_t attr =
-        cudaFuncSetAttribute(tc_kernel<NSPLIT, MODE, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(tc_kernel<NSPLIT, MODE, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     TR_CUDA(attr);
     const CUtensorMap &bh = BN == 64 ? B.mhi64 : B.mhi;
     const CUtensorMap &bl = BN == 64 ? B.mlo64 : B.mlo;
-    tc_kernel<NSPLIT, MODE, BN><<<grid, 128, smem, st>>>(A.mhi, NSPLIT == 3 ? A.mlo : A.mhi, bh, NSPLIT == 3 ? bl : bh, g);
+    tc_kernel<NSPLIT, MODE, BN><<<grid, 192, C::SMEM, st>>>(A.mhi, NSPLIT == 3 ? A.mlo : A.mhi, bh,
+                                                             NSPLIT == 3 ? bl : bh, g);
 }
 
 template <int NSPLIT, int BN>
@@ -315,7 +374,7 @@ void tc_gemm(Prof &prof, cudaStream_t st, const char *name, int nsplit, const Tc
     TR_REQUIRE(nsplit == 1 || (A.lo && B.lo), TR_EINVAL, "tc_gemm: 3-product form needs lo parts");
     TR_REQUIRE(K > 0 && ka0 >= 0 && kb0 >= 0 && ka0 + K <= A.kdim && kb0 + K <= B.kdim, TR_EINVAL, "tc_gemm: bad K");
     TR_REQUIRE(ka0 % 4 == 0 && kb0 % 4 == 0, TR_EINVAL, "tc_gemm: K offsets must be 16-byte aligned");
-    TR_REQUIRE((long long)n1 * n2 <= 65535 && cdiv(M, BM) <= 65535, TR_EINVAL, "tc_gemm: grid too large");
+    TR_REQUIRE(cdiv(M, BM) <= (1 << 30) && (long long)n1 * n2 <= (1LL << 31), TR_EINVAL, "tc_gemm: too many tiles");
     // every row a CTA addresses must exist in the operand views (rows past M may
     // belong to the next batch entry and are discarded)
     const long long lastA = a0 + a1 * (n1 - 1) + a2 * (n2 - 1) + (long long)cdiv(M, BM) * BM;
@@ -337,7 +396,17 @@ void tc_gemm(Prof &prof, cudaStream_t st, const char *name, int nsplit, const Tc
     g.c2 = c2;
     g.out = out;
     g.err = err;
-    dim3 grid(cdiv(N, BN), cdiv(M, BM), n1 * n2);
+    g.ntn = cdiv(N, BN);
+    g.ntm = cdiv(M, BM);
+    g.ntiles = (long long)g.ntn * g.ntm * n1 * n2;
+    static const int nsm = []() {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            n = 0;
+        cudaGetLastError();
+        return n > 0 ? n : 148;
+    }();
+    dim3 grid((unsigned)std::min<long long>(g.ntiles, nsm));
     const double flops = 2.0 * M * N * (double)K * n1 * n2;
     const double bytes = alg_bytes >= 0 ? alg_bytes : 4.0 * nsplit * ((double)M + N) * K * n1 * n2;
     int tok = prof.begin(st, name, flops, bytes);

@@ -5,8 +5,9 @@
 //     and the MO tensors are then rounded to FP32 (the paper builds its
 //     integrals in FP64 and runs everything after them in FP32, Sec. 3.3);
 //     see build_mixed for why the transforms themselves stay FP64;
-//   - J: Z = (Q|jb) X and J = (P|ia) Zt as FP32 GEMMs on the CUDA cores, summed
-//     in FP32 over chunks of at most 4096 terms and in FP64 across chunks;
+//   - J: Z = (Q|jb) X and J = (P|ia) Zt as FP32 products on the CUDA cores (Z
+//     summed in FP32 over chunks of at most 4096 terms and in FP64 across
+//     chunks; the expansion by a kernel for blocks of at most 32 vectors);
 //     (P|Q)^-1 is applied in FP64;
 //   - K: both stages on the tensor cores (tcgen05 kind::tf32) with split
 //     operands, hi*hi + hi*lo + lo*hi, FP32 accumulation; stage 1 writes M^P
@@ -35,6 +36,62 @@ __global__ void mixed_prepare(const double *__restrict__ X, float *__restrict__ 
             const long long w = (mm * oK + (i - o0)) * vKp + a;
             Xh[w] = f;
             Xl[w] = f - __uint_as_float(__float_as_uint(f) & 0xFFFFE000u);
+        }
+    }
+}
+
+// J expansion for a block of at most 32 vectors (Sec. 3.1):
+//   AX[m][ia] += alpha sum_P Z32[P][m] Y32[P][ia]
+// in FP32 over P, added to the FP64 output.  A CTA covers 128 ia x 32 m (4 x 4 per
+// thread); 32-row tiles of Y (coalesced along ia) and Z staged in shared memory.
+__global__ void __launch_bounds__(256)
+    je_kernel(const float *__restrict__ Y, const float *__restrict__ Z, int nJ, int mm, long long nov, double alpha,
+              double *__restrict__ AX)
+{
+    __shared__ float4 Ys[32][32];
+    __shared__ float4 Zs[32][8];
+    float *ys = (float *)Ys, *zs = (float *)Zs;
+    const int tid = threadIdx.x, ti = tid & 31, tm = tid >> 5;
+    const long long i0 = (long long)blockIdx.x * 128;
+    float acc[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
+    for (int P0 = 0; P0 < nJ; P0 += 32) {
+        for (int e = tid; e < 32 * 128; e += 256) {
+            const int p = e >> 7, c = e & 127;
+            const long long ia = i0 + c;
+            ys[p * 128 + c] = (P0 + p < nJ && ia < nov) ? Y[(long long)(P0 + p) * nov + ia] : 0.f;
+        }
+        for (int e = tid; e < 32 * 32; e += 256) {
+            const int p = e >> 5, m = e & 31;
+            zs[p * 32 + m] = (P0 + p < nJ && m < mm) ? Z[(long long)(P0 + p) * mm + m] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int p = 0; p < 32; ++p) {
+            const float4 y = Ys[p][ti];
+            const float4 z = Zs[p][tm];
+            const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                acc[j][0] = fmaf(zz[j], y.x, acc[j][0]);
+                acc[j][1] = fmaf(zz[j], y.y, acc[j][1]);
+                acc[j][2] = fmaf(zz[j], y.z, acc[j][2]);
+                acc[j][3] = fmaf(zz[j], y.w, acc[j][3]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int m = 4 * tm + j;
+        if (m >= mm) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const long long ia = i0 + 4 * ti + q;
+            if (ia < nov) AX[(long long)m * nov + ia] += alpha * (double)acc[j][q];
         }
     }
 }
@@ -186,8 +243,8 @@ void matvec_mixed(tr_ctx *c, int m, const double *X, double *AX)
             dgemm(pf, st, "J_metric", false, false, nJ, mm, nJ, 1.0, c->GinvJ.p, nJ, c->ws_Z.p, mm, 0.0, c->ws_Z2.p,
                   mm, Batch(), nullptr, 0);
             TR_LAUNCH(pf, st, "to_f32", 0, 0, to_f32<<<gfor((long long)nJ * mm), 256, 0, st>>>(c->ws_Z2.p, c->Z32.p, (long long)nJ * mm));
-            sgemm(pf, st, "J_expand", true, false, mm, (int)nov, nJ, 2.0, c->Z32.p, mm, c->Y32.p, nov, 1.0, ax, nov,
-                  Batch(), nullptr, 0);
+            TR_LAUNCH(pf, st, "J_expand", 2.0 * nJ * mm * (double)nov, 4.0 * (double)nJ * nov + 16.0 * mm * (double)nov,
+                      je_kernel<<<(unsigned)cdiv(nov, 128), 256, 0, st>>>(c->Y32.p, c->Z32.p, nJ, mm, nov, 2.0, ax));
         }
         if (c->k_active) {
             const int npk = c->mixed_npk;

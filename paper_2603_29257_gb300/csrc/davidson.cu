@@ -129,6 +129,102 @@ __global__ void row_scale_inv(double *A, int p, long long nov, const double *nor
         A[(long long)q * nov + t] *= s;
 }
 
+// Gram matrix of p <= 64 rows of length n (FP64), the pairs i <= j only: CTA b
+// sums k over its chunk for one pair per thread (up to GR_PAIRS per thread),
+// 32-value tiles of the rows staged in shared memory as [k][i]; gram_finish adds
+// the CTAs' partial sums and fills both triangles.
+constexpr int GR_TILE = 32, GR_THREADS = 256, GR_PAIRS = (64 * 65 / 2 + GR_THREADS - 1) / GR_THREADS;
+
+__global__ void __launch_bounds__(GR_THREADS)
+    gram_partial(const double *__restrict__ A, int p, long long n, long long chunk, double *__restrict__ part)
+{
+    __shared__ double As[GR_TILE][65];
+    __shared__ unsigned char pi[64 * 65 / 2], pj[64 * 65 / 2];
+    const int npair = p * (p + 1) / 2;
+    for (int q = threadIdx.x; q < npair; q += GR_THREADS) {
+        int i = 0, r = q;
+        while (r >= p - i) {
+            r -= p - i;
+            ++i;
+        }
+        pi[q] = (unsigned char)i;
+        pj[q] = (unsigned char)(i + r);
+    }
+    double acc[GR_PAIRS];
+#pragma unroll
+    for (int u = 0; u < GR_PAIRS; ++u) acc[u] = 0.0;
+    const long long k0 = (long long)blockIdx.x * chunk, k1 = min(n, k0 + chunk);
+    __syncthreads();
+    for (long long kt = k0; kt < k1; kt += GR_TILE) {
+        for (int e = threadIdx.x; e < p * GR_TILE; e += GR_THREADS) {
+            const int i = e / GR_TILE, c = e - i * GR_TILE;
+            const long long k = kt + c;
+            As[c][i] = k < k1 ? A[(long long)i * n + k] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < GR_PAIRS; ++u) {
+            const int q = threadIdx.x + u * GR_THREADS;
+            if (q < npair) {
+                const int i = pi[q], j = pj[q];
+                double a = acc[u];
+#pragma unroll 8
+                for (int c = 0; c < GR_TILE; ++c) a = fma(As[c][i], As[c][j], a);
+                acc[u] = a;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < GR_PAIRS; ++u) {
+        const int q = threadIdx.x + u * GR_THREADS;
+        if (q < npair) part[(long long)blockIdx.x * npair + q] = acc[u];
+    }
+}
+
+__global__ void gram_finish(const double *__restrict__ part, int nb, int p, double *__restrict__ S)
+{
+    const int npair = p * (p + 1) / 2;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < npair; q += gridDim.x * blockDim.x) {
+        int i = 0, r = q;
+        while (r >= p - i) {
+            r -= p - i;
+            ++i;
+        }
+        const int j = i + r;
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += part[(long long)b * npair + q];
+        S[i * p + j] = s;
+        S[j * p + i] = s;
+    }
+}
+
+// dst[l][k] = sum_m C[l][m] src[m][k] for p <= PM (FP64): one column k per thread,
+// the p x p coefficients in shared memory
+template <int PM>
+__global__ void __launch_bounds__(256)
+    apply_small(const double *__restrict__ C, int p, const double *__restrict__ src, long long n,
+                double *__restrict__ dst)
+{
+    __shared__ double Cs[PM * PM];
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) Cs[e] = C[e];
+    __syncthreads();
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        double x[PM];
+#pragma unroll
+        for (int m = 0; m < PM; ++m) x[m] = m < p ? src[(long long)m * n + k] : 0.0;
+#pragma unroll
+        for (int l = 0; l < PM; ++l) {
+            if (l >= p) break;
+            double s = 0.0;
+#pragma unroll
+            for (int m = 0; m < PM; ++m)
+                if (m < p) s = fma(Cs[l * p + m], x[m], s);
+            dst[(long long)l * n + k] = s;
+        }
+    }
+}
+
 // Orthonormal combinations of p vectors from their Gram matrix S (p <= 64):
 // Gc[l][:] are the coefficients of the l-th accepted vector; vectors whose
 // residual squared norm after projection is below drop2 are skipped.
@@ -510,16 +606,43 @@ struct Dav {
     {
         Prof &pf = c->prof;
         int *cnt = c->idx_dev.p + pmax;
-        dgemm(pf, st, "gram", false, true, p, p, (int)nov, 1.0, src, nov, src, nov, 0.0, c->Ss.p, p, Batch(), ws, wsn);
+        gram(src, p);
         TR_LAUNCH(pf, st, "cholqr_coef", 0, 0,
                   cholqr_coef<<<1, 1, 0, st>>>(c->Ss.p, p, DROP_NORM * DROP_NORM, c->Gc.p, cnt));
-        dgemm(pf, st, "orth_apply", false, false, p, (int)nov, p, 1.0, c->Gc.p, p, src, nov, 0.0, tmp, nov, Batch(),
-              nullptr, 0);
-        dgemm(pf, st, "gram", false, true, p, p, (int)nov, 1.0, tmp, nov, tmp, nov, 0.0, c->Ss.p, p, Batch(), ws, wsn);
+        apply(c->Gc.p, p, src, tmp);
+        gram(tmp, p);
         TR_LAUNCH(pf, st, "cholqr_coef", 0, 0, cholqr_coef<<<1, 1, 0, st>>>(c->Ss.p, p, 0.0, c->Gc.p, cnt + 1));
-        dgemm(pf, st, "orth_apply", false, false, p, (int)nov, p, 1.0, c->Gc.p, p, tmp, nov, 0.0, dst, nov, Batch(),
-              nullptr, 0);
+        apply(c->Gc.p, p, tmp, dst);
         TR_CUDA(cudaMemcpyAsync(h_fl + 2, cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
+    // Ss = A A^T for p rows of A (FP64)
+    void gram(const double *A, int p)
+    {
+        Prof &pf = c->prof;
+        const int npair = p * (p + 1) / 2;
+        const long long nb = std::min<long long>(std::max<long long>(1, nov / 2048), 4LL * 152);
+        if (p > 64 || (size_t)nb * npair > wsn) {
+            dgemm(pf, st, "gram", false, true, p, p, (int)nov, 1.0, A, nov, A, nov, 0.0, c->Ss.p, p, Batch(), ws, wsn);
+            return;
+        }
+        const long long chunk = (nov + nb - 1) / nb;
+        TR_LAUNCH(pf, st, "gram", (double)npair * 2.0 * nov, 8.0 * p * (double)nov,
+                  gram_partial<<<(unsigned)nb, GR_THREADS, 0, st>>>(A, p, nov, chunk, ws));
+        TR_LAUNCH(pf, st, "gram", 0, 0, gram_finish<<<cdiv(npair, 128), 128, 0, st>>>(ws, (int)nb, p, c->Ss.p));
+    }
+    // out = C src for the p x p coefficients C (FP64)
+    void apply(const double *C, int p, const double *src, double *out)
+    {
+        Prof &pf = c->prof;
+        const double fl = 2.0 * p * p * (double)nov, by = 16.0 * p * (double)nov;
+        const unsigned blocks = (unsigned)std::min<long long>(cdiv(nov, 256), 152LL * 8);
+        if (p <= 16)
+            TR_LAUNCH(pf, st, "orth_apply", fl, by, apply_small<16><<<blocks, 256, 0, st>>>(C, p, src, nov, out));
+        else if (p <= 32)
+            TR_LAUNCH(pf, st, "orth_apply", fl, by, apply_small<32><<<blocks, 256, 0, st>>>(C, p, src, nov, out));
+        else
+            dgemm(pf, st, "orth_apply", false, false, p, (int)nov, p, 1.0, C, p, src, nov, 0.0, out, nov, Batch(),
+                  nullptr, 0);
     }
 
     // initial guess: unit vectors on the b0 smallest e_a - e_i (ties: lower index)

@@ -493,7 +493,7 @@ def run_matvec(args):
     stream = torch.cuda.current_stream()
     C_dev = torch.from_numpy(mol.C).cuda()
     eps_dev = torch.from_numpy(mol.eps).cuda()
-    ctx = tdarisp.Context(stream=stream.cuda_stream, **dict(OPTS, precision=args.precision))
+    ctx = tdarisp.Context(stream=stream.cuda_stream, **dict(OPTS, precision=args.precision, j_ao=args.j_ao))
     ctx.set_molecule(mol.Z, mol.xyz, mol.aux_exp, mol.shells)
     ctx.set_orbitals(C_dev, eps_dev, mol.nocc)
     ctx.profile(True)
@@ -532,10 +532,11 @@ def run_matvec(args):
             "data": "synthetic",
             "config": {"workload": (WORKLOAD if args.case == "full" else "100-atom molecule, same options")
                        + "; one block of %d seeded vectors" % args.block,
-                       "precision": args.precision, "nao": d.nao, "nocc": d.nocc, "nvir": d.nvir,
+                       "precision": args.precision, "j_ao": args.j_ao, "nao": d.nao, "nocc": d.nocc, "nvir": d.nvir,
                        "block": args.block,
                        "l2": "X and AX %.0f MB each" % (8e-6 * args.block * d.nocc * d.nvir)},
-            "kernels": table(prof), "build_kernels": table(build_prof)}
+            "kernels": table(prof), "build_kernels": table(build_prof),
+            "device_bytes": dict(zip(("held", "peak", "estimated_peak"), ctx.memory()))}
     print(json.dumps(line))
 
 
@@ -749,6 +750,8 @@ def main():
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
                     help="form of the matvec workload: 0 FP64, 1 reduced precision, 2 FP64 on the tensor cores")
     ap.add_argument("--block", type=int, default=30, help="vectors per block of the matvec workload")
+    ap.add_argument("--j-ao", type=int, default=0, choices=[0, 1],
+                    help="matvec workload: Coulomb term from the stored (P|ia) (0) or on the fly in the AO basis (1)")
     ap.add_argument("--case", default="full", choices=["full", "small"],
                     help="small: 100-atom molecule of the same shape, for profiler captures")
     args = ap.parse_args()

@@ -98,6 +98,12 @@ typedef struct {
                             Ozaki slices per operand (7 + 8 (S-1) bits below each row's
                             largest element); 0: FP64 pipe in TR_FP64, 5 slices in TR_MIXED,
                             7 in TR_FP64_TC */
+    int j_ao;            /* Coulomb term: 0 (default) from the stored (P|ia); 1 on the fly in
+                            the AO basis (Sec. 3.1, Eq. J_mia): AO transition densities D^m,
+                            R = (Q|kl) D^m with the three-centre integrals generated per
+                            auxiliary chunk, R~ = (P|Q)^-1 R, U^m = (mn|P) R~, J = C_occ^T U^m
+                            C_vir, all in FP64 in every precision; no (P|ia) tensor is built
+                            (tr_get_tensor 0 then fails) */
 } tr_options;
 
 typedef struct {

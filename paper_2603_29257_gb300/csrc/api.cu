@@ -81,6 +81,7 @@ int tr_create(tr_ctx **out, const tr_options *opt, void *cuda_stream)
         TR_REQUIRE(opt->xform_slices == 0 || opt->xform_slices == -1 ||
                        (opt->xform_slices >= 2 && opt->xform_slices <= 7),
                    TR_EINVAL, "create: xform_slices must be -1, 0 or 2..7");
+        TR_REQUIRE(opt->j_ao == 0 || opt->j_ao == 1, TR_EINVAL, "create: j_ao must be 0 or 1");
         c->opt = *opt;
         normalise_options(&c->opt);
         c->st = (cudaStream_t)cuda_stream;
@@ -111,10 +112,12 @@ int tr_set_options(tr_ctx *ctx, const tr_options *opt)
         TR_REQUIRE(opt->xform_slices == 0 || opt->xform_slices == -1 ||
                        (opt->xform_slices >= 2 && opt->xform_slices <= 7),
                    TR_EINVAL, "set_options: xform_slices must be -1, 0 or 2..7");
+        TR_REQUIRE(opt->j_ao == 0 || opt->j_ao == 1, TR_EINVAL, "set_options: j_ao must be 0 or 1");
         bool rebuild = opt->precision != ctx->opt.precision || opt->cx != ctx->opt.cx || opt->k_alpha != ctx->opt.k_alpha ||
                        opt->k_beta != ctx->opt.k_beta || opt->omega != ctx->opt.omega ||
                        opt->window_ev != ctx->opt.window_ev || opt->aux_on_h != ctx->opt.aux_on_h ||
-                       opt->screen != ctx->opt.screen || opt->xform_slices != ctx->opt.xform_slices;
+                       opt->screen != ctx->opt.screen || opt->xform_slices != ctx->opt.xform_slices ||
+                       opt->j_ao != ctx->opt.j_ao;
         size_t limit = ctx->budget.limit;
         ctx->opt = *opt;
         normalise_options(&ctx->opt);

@@ -67,6 +67,9 @@ struct tr_ctx {
 
     // workspaces
     tr::DevBuf<double> ws_split, ws_Z, ws_Z2, ws_Xw, ws_M;
+    // Coulomb term on the fly in the AO basis (j_ao): half-transformed and AO
+    // transition densities, AO potentials, fit coefficients, integral chunk
+    tr::DevBuf<double> ws_jT, ws_jD, ws_jU, ws_jR, ws_jI;
     tr::DevBuf<int> flag;
     int mblk = 32;
 
@@ -124,6 +127,11 @@ void reserve_tc(tr_ctx *c, int mb);
 void matvec_tc(tr_ctx *c, int m, const double *X, double *AX);
 // three-centre integrals of aux functions [p0, p0+np) of set which (0 = J, 1 = K)
 void compute_int3c_chunk(tr_ctx *c, int which, int p0, int np, double *out);
+// Coulomb term on the fly in the AO basis (jao.cu): AX += 2 J for mm vectors;
+// workspaces for blocks of up to mb vectors, and their bytes
+void j_ao_block(tr_ctx *c, int mm, const double *X, double *AX);
+void reserve_jao(tr_ctx *c, int mb);
+size_t jao_bytes(const tr_ctx *c, int mb);
 // reduced-precision form (mixed.cu)
 void get_tensor_mixed(tr_ctx *c, int which, double *out, int on_device);
 void build_mixed(tr_ctx *c);

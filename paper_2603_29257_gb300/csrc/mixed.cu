@@ -136,6 +136,7 @@ void get_tensor_mixed(tr_ctx *c, int which, double *out, int on_device)
 {
     DevBuf<double> tmp;
     size_t n = 0;
+    TR_REQUIRE(which != 0 || !c->opt.j_ao, TR_EINVAL, "get_tensor: (P|ia) is not built with j_ao = 1");
     if (which == 0) {
         n = (size_t)c->nJ * c->nov;
         if (!n) return;
@@ -166,10 +167,14 @@ void build_mixed(tr_ctx *c)
     cudaStream_t st = c->st;
     Prof &pf = c->prof;
     const long long nov = c->nov;
-    c->Y32.alloc((size_t)std::max(c->nJ, 1) * nov, &c->budget, "(P|ia) FP32");
-    if (c->nJ)
-        TR_LAUNCH(pf, st, "to_f32", 0, 12.0 * c->nJ * nov,
-                  to_f32<<<gfor(c->nJ * nov), 256, 0, st>>>(c->Y.p, c->Y32.p, c->nJ * nov));
+    if (c->opt.j_ao) {
+        c->Y32.release();  // the Coulomb term is formed in the AO basis
+    } else {
+        c->Y32.alloc((size_t)std::max(c->nJ, 1) * nov, &c->budget, "(P|ia) FP32");
+        if (c->nJ)
+            TR_LAUNCH(pf, st, "to_f32", 0, 12.0 * c->nJ * nov,
+                      to_f32<<<gfor(c->nJ * nov), 256, 0, st>>>(c->Y.p, c->Y32.p, c->nJ * nov));
+    }
     c->oKp = pad32(std::max(c->oK, 1));
     c->vKp = pad32(std::max(c->vK, 1));
     if (c->k_active) {
@@ -237,7 +242,9 @@ void matvec_mixed(tr_ctx *c, int m, const double *X, double *AX)
                   mixed_prepare<<<gfor(nov * mm), 256, 0, st>>>(x, c->X32.p, c->k_active ? c->Xw_h.p : nullptr,
                                                                  c->k_active ? c->Xw_l.p : nullptr, mm, nocc, nvir,
                                                                  c->k_active ? o0 : nocc, oK, vK, vKp));
-        if (nJ) {
+        if (nJ && c->opt.j_ao) {
+            j_ao_block(c, mm, x, ax);  // Coulomb term in FP64 from the AO transition densities
+        } else if (nJ) {
             sgemm(pf, st, "J_contract", false, true, nJ, mm, (int)nov, 1.0, c->Y32.p, nov, c->X32.p, nov, 0.0,
                   c->ws_Z.p, mm, Batch(), c->ws_split.p, c->ws_split.n, 4096);
             dgemm(pf, st, "J_metric", false, false, nJ, mm, nJ, 1.0, c->GinvJ.p, nJ, c->ws_Z.p, mm, 0.0, c->ws_Z2.p,

@@ -167,6 +167,7 @@ extern "C" int tr_matvec_noalloc(tr_ctx *ctx, int m, const double *X, double *AX
         TR_REQUIRE(m >= 0, TR_EINVAL, "matvec_noalloc: m must be >= 0");
         if (m == 0) return TR_OK;
         TR_REQUIRE(X && AX, TR_EINVAL, "matvec_noalloc: null pointer");
+        TR_REQUIRE(!ctx->opt.j_ao, TR_EINVAL, "matvec_noalloc: the AO form of J (j_ao) allocates its workspaces");
         const size_t n = (size_t)m * ctx->nov;
         TR_REQUIRE(X + n <= AX || AX + n <= X, TR_EINVAL, "matvec_noalloc: X and AX overlap");
         tr::matvec_noalloc(ctx, m, X, AX);

@@ -304,17 +304,18 @@ static void transforms_fp64(tr_ctx *c, DevBuf<double> &Iij)
     const long long nov = c->nov;
     cudaStream_t st = c->st;
     Prof &pf = c->prof;
-    c->Y.alloc((size_t)nJ * nov, &c->budget, "(P|ia)");
+    const int nJt = c->opt.j_ao ? 0 : nJ;  // the AO form of J (j_ao) stores no (P|ia)
+    c->Y.alloc((size_t)nJt * nov, &c->budget, "(P|ia)");
     const int hrows = std::max(nocc, std::max(c->oK, c->vK));
     size_t per = (size_t)nao * nao + (size_t)hrows * nao;
     int npc = (int)std::max<size_t>(1, c->opt.aux_chunk_bytes / (per * sizeof(double)));
-    npc = std::max(1, std::min(npc, std::max(nJ, nK)));
+    npc = std::max(1, std::min(npc, std::max(nJt, nK)));
     DevBuf<double> I, H;
     I.alloc((size_t)npc * nao * nao, &c->budget, "AO integral chunk");
     H.alloc((size_t)npc * hrows * nao, &c->budget, "half-transform chunk");
     const int npcJ = npc >= 4 ? npc / 4 * 4 : npc;  // whole J atoms per chunk
-    for (int p0 = 0; p0 < nJ; p0 += npcJ) {
-        int np = std::min(npcJ, nJ - p0);
+    for (int p0 = 0; p0 < nJt; p0 += npcJ) {
+        int np = std::min(npcJ, nJt - p0);
         compute_int3c_chunk(c, 0, p0, np, I.p);
         Batch b1;
         b1.n1 = np;
@@ -386,12 +387,13 @@ static void transforms_oz(tr_ctx *c, DevBuf<double> &Iij, int S)
     OzMat Cs;
     oz_bind(Cs, cbuf.p, nmo, nao, S);
     oz_split(pf, st, "oz_split_C", c->C.p, 1, nmo, Cs);
-    c->Y.alloc((size_t)nJ * nov, &c->budget, "(P|ia)");
+    const int nJt = c->opt.j_ao ? 0 : nJ;  // the AO form of J (j_ao) stores no (P|ia)
+    c->Y.alloc((size_t)nJt * nov, &c->budget, "(P|ia)");
     const int hrows = std::max(nocc, std::max(c->oK, c->vK));
     const size_t per = sizeof(double) * ((size_t)nao * nao + (size_t)hrows * nao) + oz_bytes(nao, nao, S) +
                        oz_bytes(hrows, nao, S);
     int npc = (int)std::max<size_t>(1, c->opt.aux_chunk_bytes / per);
-    npc = std::max(1, std::min(npc, std::max(nJ, nK)));
+    npc = std::max(1, std::min(npc, std::max(nJt, nK)));
     DevBuf<double> I, H, Ib, Hb;
     I.alloc((size_t)npc * nao * nao, &c->budget, "AO integral chunk");
     H.alloc((size_t)npc * hrows * nao, &c->budget, "half-transform chunk");
@@ -408,8 +410,8 @@ static void transforms_oz(tr_ctx *c, DevBuf<double> &Iij, int S)
         oz_gemm(pf, st, n2, Hs, 0, nr, Cs, s0, 0, nr, ns, np, out, (long long)nr * ldo, ldo, 1, 1.0, err);
     };
     const int npcJ = npc >= 4 ? npc / 4 * 4 : npc;  // whole J atoms per chunk
-    for (int p0 = 0; p0 < nJ; p0 += npcJ) {
-        const int np = std::min(npcJ, nJ - p0);
+    for (int p0 = 0; p0 < nJt; p0 += npcJ) {
+        const int np = std::min(npcJ, nJt - p0);
         compute_int3c_chunk(c, 0, p0, np, I.p);
         oz_bind(Is, Ib.p, (long long)np * nao, nao, S);
         oz_split(pf, st, "oz_split_I", I.p, nao, 1, Is);
@@ -521,6 +523,7 @@ void int2c_aux(tr_ctx *c, int which, double *out)
 void get_tensor(tr_ctx *c, int which, double *out, int on_device)
 {
     TR_REQUIRE(c->built, TR_EINVAL, "get_tensor: call tr_build first");
+    TR_REQUIRE(which != 0 || !c->opt.j_ao, TR_EINVAL, "get_tensor: (P|ia) is not built with j_ao = 1");
     const double *src = nullptr;
     size_t n = 0;
     DevBuf<double> tmp;
@@ -564,6 +567,7 @@ size_t footprint(tr_ctx *c)
     const double d = 8.0, f = 4.0;
     const double nao = c->nao, nmo = c->nmo, nocc = c->nocc, nov = (double)c->nov;
     const double nJ = c->nJ, oK = c->oK, vK = c->vK;
+    const double nJt = c->opt.j_ao ? 0.0 : nJ;  // stored (P|ia) rows (none with the AO form of J)
     const double nK = (c->nK > 0 && c->oK > 0 && c->vK > 0 && c->opt.cx != 0.0) ? c->nK : 0;
     const bool mixed = c->opt.precision == TR_MIXED;
     const double base = d * (nao * nmo + nmo + nov) + d * (nJ * nJ + nK * nK) + 128.0 * (1 << 20) +
@@ -573,15 +577,15 @@ size_t footprint(tr_ctx *c)
     const int S = xform_slices(c);
     const double per = d * (nao * nao + hrows * nao) +
                        (S > 0 ? (double)oz_bytes(c->nao, c->nao, S) + (double)oz_bytes((long long)hrows, c->nao, S) : 0.0);
-    const double npc = std::max(1.0, std::min(std::floor((double)c->opt.aux_chunk_bytes / per), std::max(nJ, nK)));
+    const double npc = std::max(1.0, std::min(std::floor((double)c->opt.aux_chunk_bytes / per), std::max(nJt, nK)));
     const double cs = S > 0 ? (double)oz_bytes(c->nmo, c->nao, S) : 0.0;
-    const double t64 = d * (nJ * nov + nK * vK * vK + 2.0 * nK * oK * oK);
+    const double t64 = d * (nJt * nov + nK * vK * vK + 2.0 * nK * oK * oK);
     const double oKp = std::ceil(std::max(oK, 1.0) / 32) * 32, vKp = std::ceil(std::max(vK, 1.0) / 32) * 32;
-    const double t32 = mixed ? f * (nJ * nov + 2.0 * nK * vK * vKp + 2.0 * oK * nK * oKp) : 0.0;
+    const double t32 = mixed ? f * (nJt * nov + 2.0 * nK * vK * vKp + 2.0 * oK * nK * oKp) : 0.0;
     double tcb = 0.0;
     if (c->opt.precision == TR_FP64_TC) {
         const int Sf = OZ_SLICES_FP64;
-        tcb = (nJ > 0 ? (double)oz_bytes((long long)nJ, (int)nov, Sf) + (double)oz_bytes((long long)nov, (int)nJ, Sf) : 0.0) +
+        tcb = (nJt > 0 ? (double)oz_bytes((long long)nJt, (int)nov, Sf) + (double)oz_bytes((long long)nov, (int)nJt, Sf) : 0.0) +
               (nK > 0 ? (double)oz_bytes((long long)(nK * vK), (int)vK, Sf) + (double)oz_bytes((long long)oK, (int)(nK * oK), Sf) : 0.0);
     }
     const double build_peak = std::max(npc * per + cs + t64 + t32, t64 + tcb);
@@ -603,13 +607,13 @@ size_t footprint(tr_ctx *c)
     if (c->opt.precision == TR_FP64_TC) {
         // slices kept for the products, and the per-block sliced operands
         const int Sf = OZ_SLICES_FP64;
-        const double sl = (nJ > 0 ? (double)oz_bytes((long long)nJ, (int)nov, Sf) + (double)oz_bytes((long long)nov, (int)nJ, Sf) : 0.0) +
+        const double sl = (nJt > 0 ? (double)oz_bytes((long long)nJt, (int)nov, Sf) + (double)oz_bytes((long long)nov, (int)nJt, Sf) : 0.0) +
                           (nK > 0 ? (double)oz_bytes((long long)(nK * vK), (int)vK, Sf) + (double)oz_bytes((long long)oK, (int)(nK * oK), Sf) : 0.0);
         const double mbl = std::min<double>(pmax, c->mblk);
         const double npk = nK > 0 ? std::min<double>(nK, std::max(8.0, (double)c->opt.matvec_ws_bytes / (mbl * vK * oK * 24.0)) + 8.0) : 0.0;
         tcx = sl + (double)oz_bytes((long long)mbl, (int)nov, Sf) + 16.0 * (2 << 20) +
               (nK > 0 ? d * mbl * oK * vK + 16.0 * mbl * oK * (vK + 32) + 24.0 * mbl * vK * (npk * oK + 32) : 0.0) +
-              (nJ > 0 ? 16.0 * mbl * (nJ + 32) : 0.0);
+              (nJt > 0 ? 16.0 * mbl * (nJt + 32) : 0.0);
     }
     // sliced V, W and new directions of the Davidson subspace products
     const double dtc = (c->opt.precision == TR_MIXED || c->opt.precision == TR_FP64_TC)
@@ -618,7 +622,8 @@ size_t footprint(tr_ctx *c)
                                  2.0 * (double)oz_bytes((long long)nov, maxsp, OZ_SLICES_FP64) +
                                  2.0 * (double)oz_bytes((long long)std::max<double>(n, pmax), maxsp, OZ_SLICES_FP64)
                            : 0.0;
-    const double solve_peak = kept + dav + ws + tcx + dtc;
+    const double jao = c->opt.j_ao ? (double)jao_bytes(c, (int)mb) : 0.0;
+    const double solve_peak = kept + dav + ws + tcx + dtc + jao;
     return (size_t)(1.1 * (base + std::max(build_peak, solve_peak + (mixed ? 0.0 : 0.0))));
 }
 
@@ -626,6 +631,7 @@ void reserve_matvec(tr_ctx *c, int m)
 {
     const int mb = std::max(1, std::min(m, c->mblk));
     c->ws_split.reserve((size_t)16 << 20, &c->budget, "split-K workspace");
+    if (c->opt.j_ao) reserve_jao(c, mb);
     c->ws_Z.reserve((size_t)std::max(c->nJ, 1) * mb, &c->budget, "J workspace");
     c->ws_Z2.reserve((size_t)std::max(c->nJ, 1) * mb, &c->budget, "J workspace");
     if (c->opt.precision == TR_MIXED) {
@@ -669,7 +675,9 @@ void matvec(tr_ctx *c, int m, const double *X, double *AX)
         // diagonal (e_a - e_i) X
         TR_LAUNCH(pf, st, "diag", 0, 8.0 * nov * (2.0 * mm + 1.0),
                   diag_kernel<<<grid_for(nov), 256, 0, st>>>(c->D.p, x, ax, nov, mm));
-        if (nJ) {
+        if (nJ && c->opt.j_ao) {
+            j_ao_block(c, mm, x, ax);
+        } else if (nJ) {
             // Z = (Q|jb) X ; Zt = (P|Q)^-1 Z ; AX += 2 (P|ia) Zt
             dgemm(pf, st, "J_contract", false, true, nJ, mm, (int)nov, 1.0, c->Y.p, nov, x, nov, 0.0,
                   c->ws_Z.p, mm, Batch(), c->ws_split.p, c->ws_split.n);
@@ -723,7 +731,7 @@ void build_tc(tr_ctx *c)
     cudaStream_t st = c->st;
     Prof &pf = c->prof;
     const long long nov = c->nov;
-    if (c->nJ > 0) {
+    if (c->nJ > 0 && !c->opt.j_ao) {
         c->ozs_Y.alloc(cdiv(oz_bytes(c->nJ, (int)nov, S), 8), &c->budget, "sliced (P|ia)");
         oz_bind(c->oz_Y, c->ozs_Y.p, c->nJ, (int)nov, S);
         oz_split(pf, st, "oz_split_Y", c->Y.p, nov, 1, c->oz_Y);
@@ -762,7 +770,7 @@ void reserve_tc(tr_ctx *c, int mb)
     const long long nov = c->nov;
     c->ws_split.reserve((size_t)2 << 20, &c->budget, "split-K workspace");
     c->ozw_X.reserve(cdiv(oz_bytes(mb, (int)nov, S), 8), &c->budget, "sliced trial vectors");
-    if (c->nJ > 0) c->ozw_Z.reserve(cdiv(oz_bytes(mb, c->nJ, S), 8), &c->budget, "sliced J intermediate");
+    if (c->nJ > 0 && !c->opt.j_ao) c->ozw_Z.reserve(cdiv(oz_bytes(mb, c->nJ, S), 8), &c->budget, "sliced J intermediate");
     if (c->k_active) {
         const int npk = tc_pchunk(c, mb);
         c->tc_npk = npk;
@@ -793,7 +801,9 @@ void matvec_tc(tr_ctx *c, int m, const double *X, double *AX)
         double *ax = AX + (long long)m0 * nov;
         TR_LAUNCH(pf, st, "diag", 0, 8.0 * nov * (2.0 * mm + 1.0),
                   diag_kernel<<<grid_for(nov), 256, 0, st>>>(c->D.p, x, ax, nov, mm));
-        if (nJ) {
+        if (nJ && c->opt.j_ao) {
+            j_ao_block(c, mm, x, ax);
+        } else if (nJ) {
             OzMat Xs, Zs;
             oz_bind(Xs, c->ozw_X.p, mm, (int)nov, S);
             oz_split(pf, st, "oz_split_X", x, nov, 1, Xs);

@@ -34,7 +34,7 @@ class Options(ct.Structure):
                 ("screen", ct.c_double), ("hbm_budget", ct.c_size_t),
                 ("aux_chunk_bytes", ct.c_size_t), ("host_budget", ct.c_size_t),
                 ("dav_dev_rows", ct.c_int), ("matvec_ws_bytes", ct.c_size_t),
-                ("xform_slices", ct.c_int)]
+                ("xform_slices", ct.c_int), ("j_ao", ct.c_int)]
 
 
 class Dims(ct.Structure):

@@ -294,6 +294,8 @@ typedef struct {
     double t_submit, t_admit, t_built, t_done;  /* seconds on the server clock */
     int niter, nmatvec;
     char error[160];
+    int j_ao;            /* 1 if the request ran with the Coulomb term on the fly in the AO
+                            basis (its (P|ia) did not fit in the server budget) */
 } tr_result;
 
 /* Lowest nev eigenpairs of the symmetric k x k matrix H (row-major, not

@@ -1233,6 +1233,20 @@ void builder_loop(tr_server *S)
             rc = tr_set_orbitals(r->ctx, r->nao, r->nmo, r->nocc, r->C.data(), r->eps.data(), 0);
             if (rc != TR_OK) throw Error(rc, r->ctx->err);
             r->foot = footprint(r->ctx);
+            if (r->foot > S->budget && !r->ctx->opt.j_ao && r->ctx->nJ > 0) {
+                // (P|ia) does not fit: the Coulomb term on the fly in the AO basis
+                // (Sec. 3.1), with integral chunks halved until the request fits
+                tr_options o2 = r->ctx->opt;
+                o2.j_ao = 1;
+                const size_t least = (size_t)(8.0 * r->ctx->nao * r->ctx->nao * 4);
+                for (size_t cb = o2.aux_chunk_bytes; cb >= least; cb /= 2) {
+                    o2.aux_chunk_bytes = cb;
+                    rc = tr_set_options(r->ctx, &o2);
+                    if (rc != TR_OK) throw Error(rc, r->ctx->err);
+                    r->foot = footprint(r->ctx);
+                    if (r->foot <= S->budget) break;
+                }
+            }
             if (r->foot > S->budget)
                 throw Error(TR_ENOMEM, "server: request needs " + std::to_string(r->foot >> 20) +
                                            " MiB of device memory, the server budget is " +
@@ -1325,6 +1339,7 @@ void solver_loop(tr_server *S)
             std::strncpy(res.error, msg.c_str(), sizeof(res.error) - 1);
         }
         res.status = rc;
+        res.j_ao = m.r->ctx ? m.r->ctx->opt.j_ao : 0;
         // nothing of this request may still be queued when its pinned and device
         // buffers are freed (the error paths get here without a synchronisation)
         if (m.r->stream) cudaStreamSynchronize(m.r->stream);

@@ -70,7 +70,7 @@ class Result(ct.Structure):
                 ("omega", ct.c_double * 64), ("resid", ct.c_double * 64), ("X", _dp),
                 ("t_submit", ct.c_double), ("t_admit", ct.c_double), ("t_built", ct.c_double),
                 ("t_done", ct.c_double), ("niter", ct.c_int), ("nmatvec", ct.c_int),
-                ("error", ct.c_char * 160)]
+                ("error", ct.c_char * 160), ("j_ao", ct.c_int)]
 
 
 # name -> (restype, argtypes); the full C ABI of include/tdarisp.h
@@ -448,7 +448,7 @@ class Server:
             d = dict(id=r.id, status=r.status, nstates=k, omega=np.array(r.omega[:k]),
                      resid=np.array(r.resid[:k]), t_submit=r.t_submit, t_admit=r.t_admit,
                      t_built=r.t_built, t_done=r.t_done, niter=r.niter, nmatvec=r.nmatvec,
-                     error=r.error.decode(errors="replace"), X=None)
+                     error=r.error.decode(errors="replace"), X=None, j_ao=r.j_ao)
             if r.X:
                 nocc, nvir = self._shapes.get(r.id, (0, 0))
                 d["X"] = np.ctypeslib.as_array(r.X, shape=(k * nocc * nvir,)).copy().reshape(k, nocc, nvir)

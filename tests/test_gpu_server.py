@@ -102,3 +102,29 @@ def test_back_to_back_requests_with_half_the_states(mols, precision):
             r = res[0]
             assert r["status"] == 0, r["error"]
             assert np.abs(r["omega"] - w[:n]).max() < (1e-8 if precision == 0 else 1e-5), (k, n)
+
+
+def test_request_whose_coulomb_tensor_does_not_fit_runs_in_the_ao_basis():
+    """A budget between the request's estimate with the AO Coulomb term (small
+    chunks) and with the stored (P|ia): the server admits it in the AO form and
+    its energies still match the oracle."""
+    tdarisp = _lib()
+    m = synth.make_molecule(seed=61, n_heavy=20, n_h=20)
+    least = 4 * 8 * m.nao * m.nao
+
+    def est(**kw):
+        c = tdarisp.Context(nstates=4, tol=1e-7, cx=0.25, **kw)
+        c.set_molecule_from(m)
+        return c.memory()[2]
+    stored = est()
+    ao = min(est(j_ao=1, aux_chunk_bytes=least << k) for k in range(0, 6))
+    if not ao < stored:
+        pytest.skip("no budget separates the two forms for this molecule")
+    with tdarisp.Server(max_active=2, hbm_budget=(ao + stored) // 2, autotune=False) as srv:
+        rid = srv.submit(m, nstates=4, tol=1e-7, cx=0.25)
+        r = srv.drain()[0]
+    assert r["id"] == rid and r["status"] == 0, r["error"]
+    assert r["j_ao"] == 1
+    f = tda.build(m.Z, m.xyz, m.shells, m.aux_exp, m.C, m.eps, m.nocc, 0.25)
+    ref = tda.solve(f, 4, tol=1e-9)[0]
+    assert np.abs(r["omega"][:4] - ref[:4]).max() < 1e-8

@@ -34,6 +34,16 @@ struct tr_ctx {
     std::vector<tr::AuxDev> auxJ_h, auxK_h;  // in output order
     int nJ = 0, nK = 0;
     tr::DevBuf<tr::AuxDev> aux_ws;           // per-chunk class-sorted copy
+    // class-sorted auxiliary lists of fixed chunkings uploaded once (the AO form of
+    // J): a chunk found here needs no upload and no synchronisation, so its
+    // integrals can be captured in a graph
+    struct AuxChunk {
+        int which, p0, np, natoms;
+        long long off;
+        int cls[5];
+    };
+    tr::DevBuf<tr::AuxDev> aux_cache;
+    std::vector<AuxChunk> aux_cache_idx;
 
     // orbitals
     bool have_orb = false;
@@ -132,6 +142,10 @@ void compute_int3c_chunk(tr_ctx *c, int which, int p0, int np, double *out);
 void j_ao_block(tr_ctx *c, int mm, const double *X, double *AX);
 void reserve_jao(tr_ctx *c, int mb);
 size_t jao_bytes(const tr_ctx *c, int mb);
+int jao_chunk_size(const tr_ctx *c);
+// upload the class-sorted auxiliary lists of every chunk of npc functions of set
+// which (0 = J, 1 = K) once
+void prepare_aux_chunks(tr_ctx *c, int which, int npc);
 // reduced-precision form (mixed.cu)
 void get_tensor_mixed(tr_ctx *c, int which, double *out, int on_device);
 void build_mixed(tr_ctx *c);

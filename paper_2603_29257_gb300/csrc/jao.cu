@@ -53,6 +53,8 @@ void reserve_jao(tr_ctx *c, int mb)
     if (c->nJ > 0) c->ws_jI.reserve((size_t)jao_chunk(c) * nao2, &c->budget, "AO J integral chunk");
 }
 
+int jao_chunk_size(const tr_ctx *c) { return jao_chunk(c); }
+
 size_t jao_bytes(const tr_ctx *c, int mb)
 {
     const double nao = c->nao, nao2 = nao * nao;

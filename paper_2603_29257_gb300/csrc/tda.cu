@@ -102,16 +102,25 @@ void aux_chunk(tr_ctx *c, const std::vector<AuxDev> &all, int p0, int np, int cl
 void compute_int3c(tr_ctx *c, const std::vector<AuxDev> &all, int p0, int np, double *out,
                    double ka, double kb, double omega)
 {
+    const int which = &all == &c->auxJ_h ? 0 : 1;
+    TR_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * (size_t)np * c->nao * c->nao, c->st));
+    for (const tr_ctx::AuxChunk &k : c->aux_cache_idx)
+        if (k.which == which && k.p0 == p0 && k.np == np) {
+            const AuxDev *a = c->aux_cache.p + k.off;
+            int3c(c->prof, c->st, &c->side, c->shells.p, c->pairs.p, c->prange.p, c->prim.p, c->pl.off, a, k.cls,
+                  a + k.cls[4], k.natoms, c->nao, out, ka, kb, omega, c->boys.p);
+            return;
+        }
     int cls[5], natoms = 0;
     // J chunks of whole atoms (s, p_x, p_y, p_z at out indices 4a .. 4a+3)
-    const bool grouped = &all == &c->auxJ_h && p0 % 4 == 0 && np % 4 == 0;
+    const bool grouped = which == 0 && p0 % 4 == 0 && np % 4 == 0;
     aux_chunk(c, all, p0, np, cls, grouped, &natoms);
-    TR_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * (size_t)np * c->nao * c->nao, c->st));
     int3c(c->prof, c->st, &c->side, c->shells.p, c->pairs.p, c->prange.p, c->prim.p, c->pl.off, c->aux_ws.p, cls,
           c->aux_ws.p + cls[4], natoms, c->nao, out, ka, kb, omega, c->boys.p);
     // the aux list lives in aux_ws until the kernels have read it
     TR_CUDA(cudaStreamSynchronize(c->st));
 }
+
 
 void metric(tr_ctx *c, const std::vector<AuxDev> &all, double ka, double kb, double omega, double *G)
 {
@@ -142,10 +151,52 @@ void metric_inverse(tr_ctx *c, double *G, int n, double *Ginv, const char *what)
 
 }  // namespace
 
+void prepare_aux_chunks(tr_ctx *c, int which, int npc)
+{
+    const std::vector<AuxDev> &all = which == 0 ? c->auxJ_h : c->auxK_h;
+    const int n = which == 0 ? c->nJ : c->nK;
+    std::vector<AuxDev> lists;
+    std::vector<tr_ctx::AuxChunk> idx;
+    for (int p0 = 0; p0 < n; p0 += npc) {
+        const int np = std::min(npc, n - p0);
+        tr_ctx::AuxChunk k;
+        k.which = which;
+        k.p0 = p0;
+        k.np = np;
+        k.off = (long long)lists.size();
+        const bool grouped = which == 0 && p0 % 4 == 0 && np % 4 == 0;
+        std::vector<AuxDev> sorted;
+        k.cls[0] = 0;
+        for (int cd = -1; cd <= 2; ++cd) {
+            for (const AuxDev &a : all)
+                if (a.comp == cd && a.out >= p0 && a.out < p0 + np) {
+                    AuxDev b = a;
+                    b.out -= p0;
+                    sorted.push_back(b);
+                }
+            k.cls[cd + 2] = (int)sorted.size();
+        }
+        k.natoms = 0;
+        if (grouped) {
+            for (int i = k.cls[0]; i < k.cls[1]; ++i) sorted.push_back(sorted[i]);
+            k.natoms = k.cls[1] - k.cls[0];
+        }
+        lists.insert(lists.end(), sorted.begin(), sorted.end());
+        idx.push_back(k);
+    }
+    c->aux_cache_idx.clear();
+    c->aux_cache.alloc(std::max<size_t>(lists.size(), 1), &c->budget, "auxiliary chunk lists");
+    if (!lists.empty())
+        TR_CUDA(cudaMemcpy(c->aux_cache.p, lists.data(), sizeof(AuxDev) * lists.size(), cudaMemcpyHostToDevice));
+    c->aux_cache_idx = idx;
+}
+
 
 void refresh_molecule(tr_ctx *c)
 {
     const int natm = (int)c->Z.size();
+    c->aux_cache_idx.clear();  // the cached chunk lists belong to the previous molecule
+    c->aux_cache.release();
     // auxiliary functions (Sec. 3.2): J = s, px, py, pz and K = s on every atom that
     // carries an exponent, hydrogen excluded unless aux_on_h
     c->auxJ_h.clear();
@@ -488,6 +539,10 @@ void build(tr_ctx *c)
         }
         TR_CUDA(cudaStreamSynchronize(st));
     }
+    // the AO form of J generates integrals in every product: its chunk lists once
+    c->aux_cache_idx.clear();
+    c->aux_cache.release();
+    if (c->opt.j_ao && nJ > 0) prepare_aux_chunks(c, 0, jao_chunk_size(c));
     c->D.alloc(std::max<long long>(nov, 1), &c->budget, "orbital differences");
     TR_LAUNCH(pf, st, "orbital_diff", 0, 0, orbital_diff<<<grid_for(nov), 256, 0, st>>>(c->eps.p, nocc, nvir, c->D.p));
     TR_CUDA(cudaStreamSynchronize(st));

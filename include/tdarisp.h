@@ -200,6 +200,25 @@ int tr_get_tensor(tr_ctx *ctx, int which, double *out, int on_device);
    X and AX must not overlap.  Requires tr_build. */
 int tr_matvec(tr_ctx *ctx, int m, const double *X, double *AX, int on_device);
 
+/* Electric transition dipoles of n states in the dipole length form with Y = 0
+   (Tamm-Dancoff; Sec. 2, Eq. transition):
+       mu[k][d] = sqrt(2) sum_ia <i| r_d - origin_d |a> X[k][i][a],   d = x, y, z,
+   atomic units (bohr).  The sqrt(2) is the singlet spin adaptation for unit-norm
+   X (the vectors tr_solve returns).  X [n][nocc][nvir], mu [n][3]; origin: 3
+   host doubles (NULL: the coordinate origin; the dipoles of orthogonal states do
+   not depend on it).  on_device: X and mu device pointers, else host.  Needs
+   tr_set_molecule and tr_set_orbitals (not tr_build); synchronous.
+   Errors: TR_EINVAL (n < 0, null pointers, no molecule or orbitals). */
+int tr_transition_dipoles(tr_ctx *ctx, int n, const double *X, const double *origin, double *mu,
+                          int on_device);
+
+/* Oscillator strengths f[k] = 2/3 omega[k] |mu_k|^2 of n states (Sec. 2, Eq.
+   oscillator_strength) from their excitation energies omega[n] (Ha) and vectors
+   X [n][nocc][nvir], with mu_k as in tr_transition_dipoles.  on_device: omega, X
+   and f device pointers, else host.  Synchronous.  Errors: as above. */
+int tr_oscillator_strengths(tr_ctx *ctx, int n, const double *omega, const double *X, double *f,
+                            int on_device);
+
 /* Size of the static device scratch used by tr_matvec_noalloc. */
 #define TR_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 

@@ -11,7 +11,10 @@
  *              contracted spherical AO functions, for the operator
  *              (alpha + beta erf(omega r12)) / r12                (Sec. 2, Eq. RI;
  *              Sec. 3.2, Eqs. RSH and K_mia_RSH),
- *   (P|Q)      the two-centre metric for the same operator         (Sec. 2, Eq. RI).
+ *   (P|Q)      the two-centre metric for the same operator         (Sec. 2, Eq. RI),
+ *   <mu|r - O|nu>  dipole integrals of the AO functions, for the electric
+ *              transition dipoles of the oscillator strengths (Sec. 2,
+ *              Eqs. oscillator_strength and transition).
  *
  * Method: Obara-Saika vertical recursion (electron 1 then electron 2) on the
  * Boys-type auxiliary functions G_m, followed by the horizontal recursion
@@ -431,5 +434,83 @@ int orc_int2c(int naux, const double *aux_xyz, const int *aux_l, const double *a
         free(et);
     }
     free(aoff);
+    return 0;
+}
+
+/* ---------------------------------------------------------------- dipole integrals
+ *
+ * Obara-Saika recursion of the one-dimensional overlap of two Cartesian
+ * Gaussian factors (exponents a at A, b at B; p = a + b, P = (aA + bB)/p):
+ *   S(0,0)   = sqrt(pi/p) exp(-ab/p (A-B)^2)
+ *   S(i+1,j) = (P-A) S(i,j) + (i S(i-1,j) + j S(i,j-1)) / (2p)
+ *   S(i,j+1) = (P-B) S(i,j) + (i S(i-1,j) + j S(i,j-1)) / (2p)
+ * and the first moment about O, x - O = (x - B) + (B - O):
+ *   M(i,j) = S(i,j+1) + (B-O) S(i,j).
+ * A three-dimensional integral is the product of the three directions, with
+ * the moment in the direction of the dipole component. */
+#define OS_MAX 4
+static void os_overlap(double a, double b, double A, double B, double S[OS_MAX][OS_MAX])
+{
+    const double p = a + b, P = (a * A + b * B) / p, PA = P - A, PB = P - B, h = 0.5 / p;
+    double T[OS_MAX][OS_MAX];
+    memset(T, 0, sizeof T);
+    T[0][0] = sqrt(M_PI / p) * exp(-a * b / p * (A - B) * (A - B));
+    /* first the i direction with j = 0, then raise j for every i */
+    for (int i = 0; i + 1 < OS_MAX; ++i) T[i + 1][0] = PA * T[i][0] + (i > 0 ? i * h * T[i - 1][0] : 0.0);
+    for (int j = 0; j + 1 < OS_MAX; ++j)
+        for (int i = 0; i < OS_MAX; ++i)
+            T[i][j + 1] = PB * T[i][j] + h * ((i > 0 ? i * T[i - 1][j] : 0.0) + (j > 0 ? j * T[i][j - 1] : 0.0));
+    memcpy(S, T, sizeof T);
+}
+
+/* out[d][mu][nu] = <mu| r_d - O_d |nu>, d = x, y, z, for the contracted
+ * spherical AO functions of the shells (full square, row-major). */
+int orc_dipole(int nsh, const double *sh_xyz, const int *sh_l, const int *sh_nprim, const int *sh_pstart,
+               const double *exps, const double *coefs, const double *O, double *out)
+{
+    for (int i = 0; i < nsh; ++i)
+        if (sh_l[i] < 0 || sh_l[i] > 2) return -1;
+    int *off = malloc(sizeof(int) * (nsh + 1));
+    int nao = basis_nfunc(sh_l, nsh, off);
+    for (int i = 0; i < nsh; ++i)
+        for (int j = 0; j < nsh; ++j) {
+            const int la = sh_l[i], lb = sh_l[j];
+            const double *A = sh_xyz + 3 * i, *B = sh_xyz + 3 * j;
+            double cart[3][6][6];
+            memset(cart, 0, sizeof cart);
+            for (int u = 0; u < sh_nprim[i]; ++u)
+                for (int w = 0; w < sh_nprim[j]; ++w) {
+                    const double a = exps[sh_pstart[i] + u], b = exps[sh_pstart[j] + w];
+                    const double cc = coefs[sh_pstart[i] + u] * coefs[sh_pstart[j] + w];
+                    double S[3][OS_MAX][OS_MAX];
+                    for (int d = 0; d < 3; ++d) os_overlap(a, b, A[d], B[d], S[d]);
+                    for (int ka = 0; ka < ncart(la); ++ka)
+                        for (int kb = 0; kb < ncart(lb); ++kb) {
+                            int ea[3], eb[3];
+                            cart_exps(la, ka, ea);
+                            cart_exps(lb, kb, eb);
+                            for (int d = 0; d < 3; ++d) {
+                                double v = cc;
+                                for (int e = 0; e < 3; ++e) {
+                                    if (e == d)
+                                        v *= S[e][ea[e]][eb[e] + 1] + (B[e] - O[e]) * S[e][ea[e]][eb[e]];
+                                    else
+                                        v *= S[e][ea[e]][eb[e]];
+                                }
+                                cart[d][ka][kb] += v;
+                            }
+                        }
+                }
+            for (int d = 0; d < 3; ++d)
+                for (int sa = 0; sa < nsph(la); ++sa)
+                    for (int sb = 0; sb < nsph(lb); ++sb) {
+                        double v = 0.0;
+                        for (int ka = 0; ka < ncart(la); ++ka)
+                            for (int kb = 0; kb < ncart(lb); ++kb)
+                                v += sph_coef(la, sa, ka) * sph_coef(lb, sb, kb) * cart[d][ka][kb];
+                        out[((long)d * nao + off[i] + sa) * nao + off[j] + sb] = v;
+                    }
+        }
+    free(off);
     return 0;
 }

@@ -29,6 +29,7 @@ def lib():
                                          dp, dp, dp, ct.c_int, ct.c_double, ct.c_double,
                                          ct.c_double, ct.c_double, dp]
         _lib.orc_int2c.argtypes = [ct.c_int, dp, ip, dp, ct.c_double, ct.c_double, ct.c_double, dp]
+        _lib.orc_dipole.argtypes = [ct.c_int, dp, ip, ip, ip, dp, dp, dp, dp]
     return _lib
 
 
@@ -82,6 +83,17 @@ def int3c(xyz_atoms, shells, aux: AuxShells, ka=1.0, kb=0.0, omega=0.0) -> np.nd
                          float(ka), float(kb), float(omega), _d(out))
     if rc != 0:
         raise ValueError("orc_int3c rejected its input")
+    return out
+
+
+def dipole(xyz_atoms, shells, origin=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """<mu| r - origin |nu> of the AO functions: array [3][nao][nao] (x, y, z)."""
+    nsh, sxyz, sl, snp, pst, ex, cf, nao = _basis_arrays(xyz_atoms, shells)
+    out = np.zeros((3, nao, nao))
+    O = np.ascontiguousarray(origin, dtype=np.float64)
+    rc = lib().orc_dipole(nsh, _d(sxyz), _i(sl), _i(snp), _i(pst), _d(ex), _d(cf), _d(O), _d(out))
+    if rc != 0:
+        raise ValueError("orc_dipole rejected its input")
     return out
 
 

@@ -263,3 +263,20 @@ def fix_sign(X):
     s = np.sign(X[np.arange(X.shape[0]), idx])
     s[s == 0] = 1.0
     return X * s[:, None]
+
+
+def transition_dipoles(xyz, shells, C, nocc, X, origin=(0.0, 0.0, 0.0)):
+    """Electric transition dipoles in the dipole length form with Y = 0 (Sec. 2,
+    Eq. transition): mu[k][d] = sqrt(2) sum_ia r^d_ia X[k][i][a] with
+    r^d_ia = sum_mn C_mi <m| r_d - O_d |n> C_na; the sqrt(2) is the singlet spin
+    adaptation for unit-norm X."""
+    C = np.asarray(C, dtype=np.float64)
+    X = np.asarray(X, dtype=np.float64)
+    M = ints.dipole(xyz, shells, origin)
+    r = np.einsum("mi,dmn,na->dia", C[:, :nocc], M, C[:, nocc:])
+    return np.sqrt(2.0) * np.einsum("dia,kia->kd", r, X.reshape(X.shape[0], nocc, -1))
+
+
+def oscillator_strengths(omega, mu):
+    """f_k = 2/3 omega_k |mu_k|^2 (Sec. 2, Eq. oscillator_strength)."""
+    return 2.0 / 3.0 * np.asarray(omega, dtype=np.float64) * np.sum(np.asarray(mu) ** 2, axis=1)

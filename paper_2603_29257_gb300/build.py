@@ -17,7 +17,7 @@ INC = os.path.join(ROOT, "include")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtdarisp.so")
 UNITS = ["linalg.cu", "ints.cu", "tda.cu", "davidson.cu", "api.cu", "noalloc.cu", "tcgemm.cu", "mixed.cu",
-         "ozgemm.cu", "eigh.cu", "jao.cu"]
+         "ozgemm.cu", "eigh.cu", "jao.cu", "props.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -204,6 +204,62 @@ int tr_get_tensor(tr_ctx *ctx, int which, double *out, int on_device)
     });
 }
 
+int tr_transition_dipoles(tr_ctx *ctx, int n, const double *X, const double *origin, double *mu, int on_device)
+{
+    return guarded(ctx, [&]() {
+        TR_REQUIRE(n >= 0, TR_EINVAL, "transition_dipoles: n must be >= 0");
+        if (n == 0) return TR_OK;
+        TR_REQUIRE(X && mu, TR_EINVAL, "transition_dipoles: null pointer");
+        const double O[3] = {origin ? origin[0] : 0.0, origin ? origin[1] : 0.0, origin ? origin[2] : 0.0};
+        const size_t nx = (size_t)n * ctx->nov;
+        tr::DevBuf<double> xd, md;
+        const double *Xd = X;
+        double *mud = mu;
+        if (!on_device) {
+            xd.alloc(nx, &ctx->budget, "excitation vectors");
+            md.alloc((size_t)3 * n, &ctx->budget, "transition dipoles");
+            TR_CUDA(cudaMemcpyAsync(xd.p, X, sizeof(double) * nx, cudaMemcpyHostToDevice, ctx->st));
+            Xd = xd.p;
+            mud = md.p;
+        }
+        tr::transition_dipoles(ctx, n, Xd, O, mud);
+        if (!on_device) {
+            TR_CUDA(cudaMemcpyAsync(mu, md.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, ctx->st));
+            TR_CUDA(cudaStreamSynchronize(ctx->st));
+        }
+        return TR_OK;
+    });
+}
+
+int tr_oscillator_strengths(tr_ctx *ctx, int n, const double *omega, const double *X, double *f, int on_device)
+{
+    return guarded(ctx, [&]() {
+        TR_REQUIRE(n >= 0, TR_EINVAL, "oscillator_strengths: n must be >= 0");
+        if (n == 0) return TR_OK;
+        TR_REQUIRE(omega && X && f, TR_EINVAL, "oscillator_strengths: null pointer");
+        const size_t nx = (size_t)n * ctx->nov;
+        tr::DevBuf<double> xd, od, fd;
+        const double *Xd = X, *Od = omega;
+        double *Fd = f;
+        if (!on_device) {
+            xd.alloc(nx, &ctx->budget, "excitation vectors");
+            od.alloc(n, &ctx->budget, "excitation energies");
+            fd.alloc(n, &ctx->budget, "oscillator strengths");
+            TR_CUDA(cudaMemcpyAsync(xd.p, X, sizeof(double) * nx, cudaMemcpyHostToDevice, ctx->st));
+            TR_CUDA(cudaMemcpyAsync(od.p, omega, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
+            Xd = xd.p;
+            Od = od.p;
+            Fd = fd.p;
+        }
+        tr::oscillator_strengths(ctx, n, Od, Xd, Fd);
+        if (!on_device) {
+            TR_CUDA(cudaMemcpyAsync(f, fd.p, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->st));
+            TR_CUDA(cudaStreamSynchronize(ctx->st));
+        }
+        return TR_OK;
+    });
+}
+
 int tr_matvec(tr_ctx *ctx, int m, const double *X, double *AX, int on_device)
 {
     return guarded(ctx, [&]() {

@@ -143,6 +143,10 @@ void j_ao_block(tr_ctx *c, int mm, const double *X, double *AX);
 void reserve_jao(tr_ctx *c, int mb);
 size_t jao_bytes(const tr_ctx *c, int mb);
 int jao_chunk_size(const tr_ctx *c);
+// transition properties (props.cu): mu[n][3] electric transition dipoles about O,
+// f[n] oscillator strengths; device pointers, synchronous
+void transition_dipoles(tr_ctx *c, int n, const double *X, const double O[3], double *mu);
+void oscillator_strengths(tr_ctx *c, int n, const double *omega, const double *X, double *f);
 // upload the class-sorted auxiliary lists of every chunk of npc functions of set
 // which (0 = J, 1 = K) once
 void prepare_aux_chunks(tr_ctx *c, int which, int npc);

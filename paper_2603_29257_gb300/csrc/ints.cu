@@ -483,6 +483,80 @@ __global__ void __launch_bounds__(SACC ? 64 : 128)
     }
 }
 
+// Dipole integrals <mu| r - O |nu> of one AO shell pair per thread (Sec. 2, Eq.
+// transition): per direction the first moment about O of the Hermite expansion,
+//   M^{ij} = (E^{ij}_1 + (P - O) E^{ij}_0) sqrt(pi/p),
+// the other two directions the overlaps E^{ij}_0 sqrt(pi/p); contracted over the
+// pair's primitive pairs and written to both triangles of out[d][nao][nao].
+template <int LA, int LB>
+__global__ void __launch_bounds__(128)
+    dipole_kernel(const ShellDev *__restrict__ sh, const int2 *__restrict__ pairs, const int2 *__restrict__ prange,
+                  const double *__restrict__ prim, int npair, int nao, double Ox, double Oy, double Oz,
+                  double *__restrict__ out)
+{
+    constexpr int NCA = ncart(LA), NCB = ncart(LB);
+    const int ip = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ip >= npair) return;
+    const int2 pr = pairs[ip];
+    const ShellDev A = sh[pr.x], B = sh[pr.y];
+    double acc[3][NCA][NCB];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int i = 0; i < NCA; ++i)
+#pragma unroll
+            for (int j = 0; j < NCB; ++j) acc[d][i][j] = 0.0;
+    const int2 rg = prange[ip];
+    for (int q = rg.x; q < rg.x + rg.y; ++q) {
+        const double *pq = prim + 6LL * q;
+        const double Px = pq[0], Py = pq[1], Pz = pq[2], ip_ = pq[4], Kab = pq[5];
+        double Ex[LA + 1][LB + 1][LA + LB + 1], Ey[LA + 1][LB + 1][LA + LB + 1], Ez[LA + 1][LB + 1][LA + LB + 1];
+        hermite_E<LA, LB>(Px - A.x, Px - B.x, 0.5 * ip_, Ex);
+        hermite_E<LA, LB>(Py - A.y, Py - B.y, 0.5 * ip_, Ey);
+        hermite_E<LA, LB>(Pz - A.z, Pz - B.z, 0.5 * ip_, Ez);
+        const double norm = Kab * 5.568327996831707845 * ip_ * sqrt(ip_);  // K (pi/p)^{3/2}
+#pragma unroll
+        for (int ka_ = 0; ka_ < NCA; ++ka_)
+#pragma unroll
+            for (int kb_ = 0; kb_ < NCB; ++kb_) {
+                const int ax = cexp(LA, ka_, 0), ay = cexp(LA, ka_, 1), az = cexp(LA, ka_, 2);
+                const int bx = cexp(LB, kb_, 0), by = cexp(LB, kb_, 1), bz = cexp(LB, kb_, 2);
+                const double sx = Ex[ax][bx][0], sy = Ey[ay][by][0], sz = Ez[az][bz][0];
+                const double mx = (ax + bx > 0 ? Ex[ax][bx][ax + bx > 0 ? 1 : 0] : 0.0) + (Px - Ox) * sx;
+                const double my = (ay + by > 0 ? Ey[ay][by][ay + by > 0 ? 1 : 0] : 0.0) + (Py - Oy) * sy;
+                const double mz = (az + bz > 0 ? Ez[az][bz][az + bz > 0 ? 1 : 0] : 0.0) + (Pz - Oz) * sz;
+                acc[0][ka_][kb_] = fma(norm, mx * sy * sz, acc[0][ka_][kb_]);
+                acc[1][ka_][kb_] = fma(norm, sx * my * sz, acc[1][ka_][kb_]);
+                acc[2][ka_][kb_] = fma(norm, sx * sy * mz, acc[2][ka_][kb_]);
+            }
+    }
+    constexpr int NSA = 2 * LA + 1, NSB = 2 * LB + 1;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double *o = out + (long long)d * nao * nao;
+#pragma unroll
+        for (int sa = 0; sa < NSA; ++sa)
+#pragma unroll
+            for (int sb = 0; sb < NSB; ++sb) {
+                double v = 0.0;
+#pragma unroll
+                for (int ka_ = 0; ka_ < NCA; ++ka_) {
+                    const double wa = LA == 2 ? d_sph(sa, ka_) : (ka_ == sa ? 1.0 : 0.0);
+                    if (wa == 0.0) continue;
+#pragma unroll
+                    for (int kb_ = 0; kb_ < NCB; ++kb_) {
+                        const double wb = LB == 2 ? d_sph(sb, kb_) : (kb_ == sb ? 1.0 : 0.0);
+                        if (wb == 0.0) continue;
+                        v = fma(wa * wb, acc[d][ka_][kb_], v);
+                    }
+                }
+                const int mu = A.ao + sa, nu = B.ao + sb;
+                o[(long long)mu * nao + nu] = v;
+                o[(long long)nu * nao + mu] = v;
+            }
+    }
+}
+
 template <int LA, int LB>
 void launch_pair_class(Prof &prof, const cudaStream_t *streams, int nstreams, int &next, int cls,
                        const ShellDev *sh, const int2 *pairs, const int2 *prange, const double *prim, int npair,
@@ -588,6 +662,26 @@ void int3c(Prof &prof, cudaStream_t st, SideStreams *side, const ShellDev *sh, c
     TR_CLASS(0, 0, 0);
 #undef TR_CLASS
     if (side) side->end(st);
+}
+
+void dipole_ints(Prof &prof, cudaStream_t st, const ShellDev *sh, const int2 *pairs, const int2 *prange,
+                 const double *prim, const int *off, int nao, const double O[3], double *out)
+{
+    TR_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * 3 * (size_t)nao * nao, st));
+#define TR_DIP(LA, LB, C)                                                                                          \
+    if (off[C + 1] > off[C]) {                                                                                     \
+        const int n = off[C + 1] - off[C];                                                                         \
+        TR_LAUNCH(prof, st, "dipole", 0, 0,                                                                        \
+                  dipole_kernel<LA, LB><<<cdiv(n, 128), 128, 0, st>>>(sh, pairs + off[C], prange + off[C], prim, n, \
+                                                                      nao, O[0], O[1], O[2], out));                \
+    }
+    TR_DIP(0, 0, 0);
+    TR_DIP(1, 0, 1);
+    TR_DIP(1, 1, 2);
+    TR_DIP(2, 0, 3);
+    TR_DIP(2, 1, 4);
+    TR_DIP(2, 2, 5);
+#undef TR_DIP
 }
 
 void int2c(Prof &prof, cudaStream_t st, const AuxDev *aux, int n, double ka, double kb, double omega,

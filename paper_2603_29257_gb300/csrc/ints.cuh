@@ -62,6 +62,11 @@ void int3c(Prof &prof, cudaStream_t st, SideStreams *side, const ShellDev *sh, c
            const double *boys);
 
 // out[i][j] = (P_i|Q_j) for auxiliary functions aux[0..n) with out index aux[i].out.
+// <mu| r - O |nu> for the screened AO shell pairs: out[3][nao][nao] (x, y, z),
+// zero for pairs dropped by the screening
+void dipole_ints(Prof &prof, cudaStream_t st, const ShellDev *sh, const int2 *pairs, const int2 *prange,
+                 const double *prim, const int *off, int nao, const double O[3], double *out);
+
 void int2c(Prof &prof, cudaStream_t st, const AuxDev *aux, int n, double ka, double kb, double omega,
            const double *boys, double *out);
 

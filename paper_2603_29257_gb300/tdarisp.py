@@ -88,6 +88,8 @@ SIGNATURES = {
     "tr_int3c": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p]),
     "tr_int2c": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p]),
     "tr_get_tensor": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int]),
+    "tr_transition_dipoles": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int]),
+    "tr_oscillator_strengths": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int]),
     "tr_matvec": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_int]),
     "tr_matvec_noalloc": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p]),
     "tr_solve": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int,
@@ -347,6 +349,42 @@ class Context:
         if rc not in (TR_OK, TR_ENOCONV):
             self._check(rc, "tr_solve")
         return om, X, rs, info
+
+    def transition_dipoles(self, X, origin=None):
+        """mu[k][d] = sqrt(2) sum_ia <i|r_d - O_d|a> X[k][i][a] (Sec. 2, Eq. transition,
+        Y = 0): numpy in -> numpy out, CUDA tensor in -> CUDA tensor out."""
+        O = None if origin is None else _f64(origin)
+        Op = None if O is None else O.ctypes.data_as(ct.c_void_p)
+        if _is_torch(X) and X.is_cuda:
+            import torch
+            X = X.contiguous()
+            mu = torch.empty((X.shape[0], 3), dtype=torch.float64, device=X.device)
+            self._check(lib().tr_transition_dipoles(self._h, X.shape[0], ct.c_void_p(X.data_ptr()), Op,
+                                                    ct.c_void_p(mu.data_ptr()), 1), "tr_transition_dipoles")
+            return mu
+        Xn = _f64(X)
+        mu = np.zeros((Xn.shape[0], 3))
+        self._check(lib().tr_transition_dipoles(self._h, Xn.shape[0], Xn.ctypes.data_as(ct.c_void_p), Op,
+                                                mu.ctypes.data_as(ct.c_void_p), 0), "tr_transition_dipoles")
+        return mu
+
+    def oscillator_strengths(self, omega, X):
+        """f_k = 2/3 omega_k |mu_k|^2 (Sec. 2, Eq. oscillator_strength)."""
+        if _is_torch(X) and X.is_cuda:
+            import torch
+            X = X.contiguous()
+            om = omega.contiguous()
+            f = torch.empty(X.shape[0], dtype=torch.float64, device=X.device)
+            self._check(lib().tr_oscillator_strengths(self._h, X.shape[0], ct.c_void_p(om.data_ptr()),
+                                                      ct.c_void_p(X.data_ptr()), ct.c_void_p(f.data_ptr()), 1),
+                        "tr_oscillator_strengths")
+            return f
+        Xn, om = _f64(X), _f64(omega)
+        f = np.zeros(Xn.shape[0])
+        self._check(lib().tr_oscillator_strengths(self._h, Xn.shape[0], om.ctypes.data_as(ct.c_void_p),
+                                                  Xn.ctypes.data_as(ct.c_void_p), f.ctypes.data_as(ct.c_void_p), 0),
+                    "tr_oscillator_strengths")
+        return f
 
     def profile(self, enable=True):
         self._check(lib().tr_profile(self._h, 1 if enable else 0), "tr_profile")

@@ -349,3 +349,70 @@ def test_davidson_24_atom_case_matches_dense():
     r = tda.solve(f, 5, tol=1e-6)
     assert r.converged
     assert np.abs(r.omega - w).max() < 1e-9
+
+
+# ---------------------------------------------------------------- dipole integrals (Sec. 2, Eq. transition)
+
+def _shell(atom, l, a, c=1.0):
+    return synth.Shell(atom=atom, l=l, exps=np.array([a]), coefs=np.array([c]))
+
+
+def test_dipole_of_two_s_primitives_closed_form():
+    """<a| x - O_x |b> = (P_x - O_x) (pi/p)^{3/2} exp(-ab/p |AB|^2) for s primitives."""
+    xyz = np.array([[0.1, -0.4, 0.7], [1.3, 0.2, -0.5]])
+    a, b = 0.8, 1.7
+    O = np.array([0.25, -0.6, 0.9])
+    M = ints.dipole(xyz, [_shell(0, 0, a), _shell(1, 0, b)], O)
+    p = a + b
+    P = (a * xyz[0] + b * xyz[1]) / p
+    S = (math.pi / p) ** 1.5 * math.exp(-a * b / p * np.sum((xyz[0] - xyz[1]) ** 2))
+    for d in range(3):
+        assert abs(M[d, 0, 1] - (P[d] - O[d]) * S) < 1e-14
+        assert abs(M[d, 1, 0] - M[d, 0, 1]) < 1e-15
+        assert abs(M[d, 0, 0] - (xyz[0, d] - O[d]) * (math.pi / (2 * a)) ** 1.5) < 1e-14
+
+
+def test_dipole_of_p_and_d_against_gauss_hermite_quadrature():
+    """<p_x(A)| y - O_y |d_xy(B)> and <p_z(A)| z - O_z |d_z2(B)> by a product
+    Gauss-Hermite rule about the Gaussian product centre (exact for these degrees)."""
+    xyz = np.array([[0.0, 0.3, -0.2], [0.9, -0.5, 0.4]])
+    a, b = 0.6, 1.1
+    O = np.array([0.2, 0.1, -0.3])
+    M = ints.dipole(xyz, [_shell(0, 1, a), _shell(1, 2, b)], O)
+    p = a + b
+    P = (a * xyz[0] + b * xyz[1]) / p
+    pref = math.exp(-a * b / p * np.sum((xyz[0] - xyz[1]) ** 2))
+    t, w = np.polynomial.hermite.hermgauss(8)
+    g = [P[d] + t / math.sqrt(p) for d in range(3)]          # nodes per direction
+    W = np.einsum("i,j,k->ijk", w, w, w) / p ** 1.5
+    X, Y, Z = np.meshgrid(g[0], g[1], g[2], indexing="ij")
+    A, B = xyz[0], xyz[1]
+    px, pz = X - A[0], Z - A[2]
+    dxy = (X - B[0]) * (Y - B[1])
+    dz2 = (2 * (Z - B[2]) ** 2 - (X - B[0]) ** 2 - (Y - B[1]) ** 2) / (2 * math.sqrt(3))
+    # AO order: p_x, p_y, p_z (0..2) then d: xy, yz, z2, xz, x2-y2 (3..7)
+    ref1 = pref * np.sum(W * px * (Y - O[1]) * dxy)
+    ref2 = pref * np.sum(W * pz * (Z - O[2]) * dz2)
+    assert abs(M[1, 0, 3] - ref1) < 1e-13 * max(1.0, abs(ref1))
+    assert abs(M[2, 2, 5] - ref2) < 1e-13 * max(1.0, abs(ref2))
+
+
+def test_dipole_origin_shift_gives_the_overlap_of_the_orbitals(small_mol):
+    """M(O) = M(0) - O_d S: the three shifted differences agree, and that overlap
+    makes the synthetic orbitals (built from the input generator's own overlap)
+    orthonormal, C^T S C = I."""
+    m = small_mol
+    O = np.array([0.3, -0.7, 1.1])
+    D0 = ints.dipole(m.xyz, m.shells)
+    D1 = ints.dipole(m.xyz, m.shells, O)
+    S = [(D0[d] - D1[d]) / O[d] for d in range(3)]
+    assert np.abs(S[0] - S[1]).max() < 1e-12 and np.abs(S[0] - S[2]).max() < 1e-12
+    assert np.abs(m.C.T @ S[0] @ m.C - np.eye(m.C.shape[1])).max() < 1e-10
+
+
+def test_transition_dipoles_do_not_depend_on_the_origin(small_mol):
+    m = small_mol
+    X = synth.random_trial_block(3, 4, m.nocc, m.nvir)
+    mu0 = tda.transition_dipoles(m.xyz, m.shells, m.C, m.nocc, X)
+    mu1 = tda.transition_dipoles(m.xyz, m.shells, m.C, m.nocc, X, origin=(2.0, -1.0, 0.5))
+    assert np.abs(mu0 - mu1).max() < 1e-11 * max(1.0, np.abs(mu0).max())

@@ -16,9 +16,15 @@ CUDA library.  Every function follows the paper's definitions directly:
   (alpha + beta erf(omega r))/r                                   Sec. 3.2, Eqs. RSH, K_mia_RSH
   Davidson: standard block Davidson with restart that keeps the current
   Ritz vectors and recomputes A V                                 Sec. 3.3
+  full TDDFT-risp: (A + B) = D + 4 (ia|jb) - c_x [(ib|ja) + (ij|ab)],
+  (A - B) = D + c_x [(ib|ja) - (ij|ab)], (ib|ja) from T_ia^P' on the
+  window with the K operator, and (A - B)(A + B)|X+Y> = Omega^2 |X+Y>   Sec. 2, Eqs. tddft, hessian; Sec. 3.2
 
 The reading of (ab|Q) in the paper's T_ab definition (a dangling sum over Q)
 is T_ab^P = (ab|P), which makes sum_P T_ij^P T_ab^P the RI value of (ij|ab).
+The Coulomb coefficient of A + B is read as 4 (the printed Eq. hessian has 2):
+with B = 2 (ia|jb) - c_x (ib|ja), the half sum of A + B and A - B is then the
+A of Eq. TDA-risp, as the TDA limit requires.
 """
 from __future__ import annotations
 
@@ -74,14 +80,16 @@ class Factors:
     occK: np.ndarray     # occupied window indices
     virK: np.ndarray     # virtual window indices (relative to nocc)
     cx: float
+    Tia: np.ndarray | None = None  # (NK, o', v') (ia|P) with the K operator (full TDDFT only)
 
 
 def build(Z, xyz, shells, aux_exp, C, eps, nocc, cx, ka=1.0, kb=0.0, omega=0.0,
-          window_ev=40.0, include_h=False, chunk=16) -> Factors:
+          window_ev=40.0, include_h=False, chunk=16, tddft=False) -> Factors:
     """Three-centre integrals, metrics and MO-basis tensors of Secs. 2 and 3.2.
 
     The K operator is (ka + kb erf(omega r))/r; for a global hybrid ka=1, kb=0.
-    J always uses the Coulomb operator."""
+    J always uses the Coulomb operator.  tddft: also (ia|P) on the window with
+    the K operator, the tensor that only the full TDDFT exchange needs (Sec. 3.2)."""
     C = np.asarray(C, dtype=np.float64)
     eps = np.asarray(eps, dtype=np.float64)
     nmo = C.shape[1]
@@ -106,7 +114,8 @@ def build(Z, xyz, shells, aux_exp, C, eps, nocc, cx, ka=1.0, kb=0.0, omega=0.0,
 
     (Y,) = mo_blocks(auxJ, 1.0, 0.0, 0.0, [(Co, Cv)])
     GJ = ints.int2c(auxJ)
-    Iij, Iab = mo_blocks(auxK, ka, kb, omega, [(CoK, CoK), (CvK, CvK)])
+    kpairs = [(CoK, CoK), (CvK, CvK)] + ([(CoK, CvK)] if tddft else [])
+    Iij, Iab, *Iia = mo_blocks(auxK, ka, kb, omega, kpairs)
     GK = ints.int2c(auxK, ka, kb, omega)
     NK = GK.shape[0]
     if NK:
@@ -115,7 +124,7 @@ def build(Z, xyz, shells, aux_exp, C, eps, nocc, cx, ka=1.0, kb=0.0, omega=0.0,
     else:
         Tij = Iij
     return Factors(nocc=nocc, nvir=nvir, D=D, Y=Y, GJ=GJ, Tij=Tij, Tab=Iab, GK=GK,
-                   occK=occK, virK=virK, cx=float(cx))
+                   occK=occK, virK=virK, cx=float(cx), Tia=Iia[0] if tddft else None)
 
 
 def coulomb_ri(f: Factors) -> np.ndarray:
@@ -137,11 +146,41 @@ def exchange_ri(f: Factors) -> np.ndarray:
     return K.reshape(n, n)
 
 
+def exchange_ri_B(f: Factors) -> np.ndarray:
+    """(ib|ja) RI value, sum_PQ (ib|P) (P|Q)^-1 (Q|ja) with the K operator, on the
+    window, embedded as an (nov, nov) matrix with rows (i,a) and columns (j,b);
+    zero outside the window (Sec. 2, Eq. hessian; Sec. 3.2)."""
+    K = np.zeros((f.nocc, f.nvir, f.nocc, f.nvir))
+    if f.Tia is None:
+        raise ValueError("exchange_ri_B: factors built without tddft=True")
+    NK = f.Tia.shape[0]
+    if NK:
+        W = np.linalg.solve(f.GK, f.Tia.reshape(NK, -1)).reshape(f.Tia.shape)
+        blk = np.einsum("Pib,Pja->iajb", f.Tia, W, optimize=True)
+        K[np.ix_(f.occK, f.virK, f.occK, f.virK)] = blk
+    n = f.nocc * f.nvir
+    return K.reshape(n, n)
+
+
 def explicit_A(f: Factors) -> np.ndarray:
     """Explicit TDA-risp matrix (Sec. 2, Eq. TDA-risp) for small problems."""
     A = 2.0 * coulomb_ri(f) - f.cx * exchange_ri(f)
     A[np.diag_indices_from(A)] += f.D.reshape(-1)
     return A
+
+
+def explicit_ApB(f: Factors) -> np.ndarray:
+    """A + B of Sec. 2, Eq. hessian (no XC kernel), Coulomb coefficient 4."""
+    M = 4.0 * coulomb_ri(f) - f.cx * (exchange_ri_B(f) + exchange_ri(f))
+    M[np.diag_indices_from(M)] += f.D.reshape(-1)
+    return M
+
+
+def explicit_AmB(f: Factors) -> np.ndarray:
+    """A - B of Sec. 2, Eq. hessian."""
+    M = f.cx * (exchange_ri_B(f) - exchange_ri(f))
+    M[np.diag_indices_from(M)] += f.D.reshape(-1)
+    return M
 
 
 def matvec(f: Factors, X: np.ndarray) -> np.ndarray:
@@ -158,6 +197,58 @@ def matvec(f: Factors, X: np.ndarray) -> np.ndarray:
         K = np.einsum("Pij,Pmja->mia", f.Tij, M, optimize=True)
         AX[np.ix_(np.arange(X.shape[0]), f.occK, f.virK)] -= f.cx * K
     return AX
+
+
+def matvec_B(f: Factors, X: np.ndarray) -> np.ndarray:
+    """B X = 2 J X - c_x sum_jb (ib|ja) X_jb without forming B: with
+    W^P = sum_Q (P|Q)^-1 (Q|ja), E^P_mij = sum_b (ib|P) X_mjb and the exchange
+    part sum_P sum_j E^P_mij W^P_ja on the window."""
+    X = np.asarray(X, dtype=np.float64).reshape(-1, f.nocc, f.nvir)
+    BX = np.zeros_like(X)
+    if f.Y.shape[0]:
+        Z = np.linalg.solve(f.GJ, np.einsum("Pia,mia->Pm", f.Y, X, optimize=True))
+        BX += 2.0 * np.einsum("Pia,Pm->mia", f.Y, Z, optimize=True)
+    if f.Tia is None:
+        raise ValueError("matvec_B: factors built without tddft=True")
+    NK = f.Tia.shape[0]
+    if NK and len(f.occK) and len(f.virK):
+        W = np.linalg.solve(f.GK, f.Tia.reshape(NK, -1)).reshape(f.Tia.shape)
+        Xw = X[:, f.occK][:, :, f.virK]
+        E = np.einsum("Pib,mjb->Pmij", f.Tia, Xw, optimize=True)
+        K = np.einsum("Pmij,Pja->mia", E, W, optimize=True)
+        BX[np.ix_(np.arange(X.shape[0]), f.occK, f.virK)] -= f.cx * K
+    return BX
+
+
+def matvec_pm(f: Factors, X: np.ndarray):
+    """(A + B) X and (A - B) X from A X and B X."""
+    AX, BX = matvec(f, X), matvec_B(f, X)
+    return AX + BX, AX - BX
+
+
+def tddft_dense(f: Factors, nstates: int):
+    """Lowest nstates of the full TDDFT-risp problem (Sec. 2, Eqs. tddft and
+    hessian) by dense algebra: with M = (A - B)^(1/2) (A - B positive definite),
+    M (A + B) M t = Omega^2 t; X+Y = M t / sqrt(Omega) and X-Y = (A + B)(X+Y) / Omega,
+    so that (X+Y).(X-Y) = 1.  Returns omega, X+Y and X-Y as [n][nocc][nvir], the
+    largest-magnitude component of each X+Y positive (X-Y takes the same sign)."""
+    P, Mm = explicit_ApB(f), explicit_AmB(f)
+    lam, U = np.linalg.eigh(Mm)
+    if lam.min() <= 0.0:
+        raise ValueError("tddft_dense: A - B is not positive definite")
+    Mh = (U * np.sqrt(lam)) @ U.T
+    w2, T = np.linalg.eigh(Mh @ P @ Mh)
+    w2, T = w2[:nstates], T[:, :nstates]
+    if w2.min() <= 0.0:
+        raise ValueError("tddft_dense: non-positive Omega^2")
+    om = np.sqrt(w2)
+    XpY = (Mh @ T / np.sqrt(om)).T
+    XmY = (P @ XpY.T / om).T
+    idx = np.argmax(np.abs(XpY), axis=1)
+    s = np.sign(XpY[np.arange(len(om)), idx])
+    s[s == 0] = 1.0
+    shape = (len(om), f.nocc, f.nvir)
+    return om, (XpY * s[:, None]).reshape(shape), (XmY * s[:, None]).reshape(shape)
 
 
 # --------------------------------------------------------------------------
@@ -269,7 +360,8 @@ def transition_dipoles(xyz, shells, C, nocc, X, origin=(0.0, 0.0, 0.0)):
     """Electric transition dipoles in the dipole length form with Y = 0 (Sec. 2,
     Eq. transition): mu[k][d] = sqrt(2) sum_ia r^d_ia X[k][i][a] with
     r^d_ia = sum_mn C_mi <m| r_d - O_d |n> C_na; the sqrt(2) is the singlet spin
-    adaptation for unit-norm X."""
+    adaptation for unit-norm X.  For full TDDFT the same sum over X+Y with
+    (X+Y).(X-Y) = 1 (Eq. transition)."""
     C = np.asarray(C, dtype=np.float64)
     X = np.asarray(X, dtype=np.float64)
     M = ints.dipole(xyz, shells, origin)

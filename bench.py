@@ -540,6 +540,88 @@ def run_matvec(args):
     print(json.dumps(line))
 
 
+def run_tddft(args):
+    """Full TDDFT-risp (tddft = 1, Sec. 2, Eqs. tddft and hessian) on the same
+    molecule and options: tr_build (with T_ia^P' on the window), W untimed and
+    K timed (A + B, A - B) products of one block of `--block` resident seeded
+    vectors, then one Davidson solve to 15 states, and the TDA solve of the same
+    context options for comparison.  value = vectors x K / event time of the
+    block products (each vector gets both products)."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_29257_gb300 import tdarisp
+    mol = make_inputs(args.case)
+    torch.zeros(1, device="cuda")
+    stream = torch.cuda.current_stream()
+    C_dev = torch.from_numpy(mol.C).cuda()
+    eps_dev = torch.from_numpy(mol.eps).cuda()
+
+    def context(tddft):
+        c = tdarisp.Context(stream=stream.cuda_stream, **dict(OPTS, tddft=tddft))
+        c.set_molecule(mol.Z, mol.xyz, mol.aux_exp, mol.shells)
+        c.set_orbitals(C_dev, eps_dev, mol.nocc)
+        return c
+    ctx = context(1)
+    torch.cuda.synchronize()
+    tb = time.perf_counter()
+    ctx.build()
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - tb
+    d = ctx.dims()
+    g = torch.Generator(device="cpu").manual_seed(17)
+    X = torch.randn((args.block, d.nocc, d.nvir), generator=g, dtype=torch.float64).cuda()
+    for _ in range(max(args.warmup, 1)):
+        ctx.matvec_tddft(X)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        ctx.matvec_tddft(X)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    prof = ctx.profile_get()
+    ctx.profile(False)
+    ms = t0.elapsed_time(t1)
+    del X
+    ts = time.perf_counter()
+    om, _, _, rs, info = ctx.solve_tddft()
+    solve_s = time.perf_counter() - ts
+    mem = ctx.memory()
+    del ctx
+    tda_ctx = context(0)
+    tda_ctx.build()
+    ts = time.perf_counter()
+    om_tda, _, _, info_tda = tda_ctx.solve(want_x=False)
+    tda_s = time.perf_counter() - ts
+    ev = 27.211386245988
+    kern = {k: {"ms": round(v["ms"], 3), "launches": v["launches"],
+                "tflops": round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 3) if v["ms"] and v["flops"] else None,
+                "gbs": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] and v["bytes"] else None}
+            for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:10]}
+    line = {"metric": "full TDDFT-risp (A+B, A-B) products/s (block products alone)",
+            "value": args.block * args.steps / (ms * 1e-3), "unit": "vectors/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 1), "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": (WORKLOAD if args.case == "full" else "100-atom molecule, same options")
+                       .replace("TDA-risp", "full TDDFT-risp") + "; one block of %d seeded vectors" % args.block,
+                       "nao": d.nao, "nocc": d.nocc, "nvir": d.nvir, "naux_k": d.naux_k, "nocc_k": d.nocc_k,
+                       "nvir_k": d.nvir_k, "block": args.block,
+                       "l2": "X and products %.0f MB each" % (8e-6 * args.block * d.nocc * d.nvir)},
+            "kernels": kern,
+            "solve": {"build_s": round(build_s, 3), "solve_s": round(solve_s, 3), "niter": info.niter,
+                      "nmatvec": info.nmatvec, "nrestart": info.nrestart, "converged": info.converged,
+                      "max_resid": float(np.max(rs)), "t_matvec_ms": round(info.t_matvec_ms, 1),
+                      "omega_ev": [round(float(w) * ev, 6) for w in om[:5]]},
+            "tda_solve": {"solve_s": round(tda_s, 3), "niter": info_tda.niter, "nmatvec": info_tda.nmatvec,
+                          "omega_ev": [round(float(w) * ev, 6) for w in om_tda[:5]]},
+            "device_bytes": dict(zip(("held", "peak", "estimated_peak"), mem))}
+    print(json.dumps(line))
+
+
 def run_batched(args):
     """Batched form: 64 molecules (20-150 atoms, 10 states each) in the reduced-precision
     form, all Davidson solves advanced in lockstep with one graph launch of all
@@ -742,10 +824,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the reduced-precision form")
     ap.add_argument("--no-fp64tc", action="store_true", help="skip the FP64 form on the tensor cores")
-    ap.add_argument("--workload", default="fp64-200", choices=["fp64-200", "batched", "serve", "matvec"],
+    ap.add_argument("--workload", default="fp64-200", choices=["fp64-200", "batched", "serve", "matvec", "tddft"],
                     help="batched: 64 molecules in the reduced-precision batched form; "
                          "serve: a Poisson request stream through the serving runtime; "
-                         "matvec: block products alone in the form --precision (profiling case)")
+                         "matvec: block products alone in the form --precision (profiling case); "
+                         "tddft: full TDDFT-risp products and solve")
     ap.add_argument("--requests", type=int, default=64, help="requests of the serve workload")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
                     help="form of the matvec workload: 0 FP64, 1 reduced precision, 2 FP64 on the tensor cores")
@@ -763,6 +846,8 @@ def main():
         run_serve(args)
     elif args.workload == "matvec":
         run_matvec(args)
+    elif args.workload == "tddft":
+        run_tddft(args)
     else:
         run_native(args)
 

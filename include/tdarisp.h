@@ -6,6 +6,8 @@
  *
  *   A_{ia,jb} = (e_a - e_i) d_ij d_ab + 2 (ia|jb) - c_x (ij|ab)          Sec. 2, Eq. TDA-risp
  *
+ * and, with tr_options.tddft = 1, full TDDFT-risp with B_{ia,jb} = 2 (ia|jb)
+ * - c_x (ib|ja) (Sec. 2, Eqs. tddft and hessian),
  * with both electron-repulsion terms factorised through the minimal
  * auxiliary basis (Sec. 2, Eqs. RI and g(r)): one s and one p primitive per
  * non-hydrogen atom for the Coulomb term, the s primitive only for the
@@ -104,6 +106,17 @@ typedef struct {
                             auxiliary chunk, R~ = (P|Q)^-1 R, U^m = (mn|P) R~, J = C_occ^T U^m
                             C_vir, all in FP64 in every precision; no (P|ia) tensor is built
                             (tr_get_tensor 0 then fails) */
+    int tddft;           /* 0 (default): Tamm-Dancoff (Eq. TDA-risp); 1: full TDDFT-risp
+                            (Sec. 2, Eqs. tddft and hessian, no XC kernel):
+                              A + B = D + 4 (ia|jb) - c_x [(ib|ja) + (ij|ab)]
+                              A - B = D + c_x [(ib|ja) - (ij|ab)]
+                            (the printed A + B has 2 (ia|jb); 4 is the coefficient for
+                            which (A+B + A-B)/2 is the A above).  tr_build then also forms
+                            T_ia^P' on the exchange window (Sec. 3.2, the tensor only full
+                            TDDFT needs), and tr_solve solves (A-B)(A+B)|X+Y> = Omega^2|X+Y>.
+                            FP64 form only: needs precision TR_FP64 and xform_slices <= 0;
+                            not available in tr_solve_batch or the server (TR_EINVAL);
+                            tr_matvec and tr_matvec_noalloc still give A X */
 } tr_options;
 
 typedef struct {
@@ -191,7 +204,10 @@ int tr_int2c(tr_ctx *ctx, int which, double *out_dev);
    0: (P|ia)      [naux_j][nocc][nvir]
    1: T_ij^P      [naux_k][nocc_k][nocc_k]   (inverse K metric applied)
    2: T_ab^P      [naux_k][nvir_k][nvir_k]
-   3: e_a - e_i   [nocc][nvir] */
+   3: e_a - e_i   [nocc][nvir]
+   4: L^-1 (P|ia) [naux_k][nocc_k][nvir_k]   (full TDDFT only: K operator, window,
+                  L the Cholesky factor of the K metric, so that
+                  sum_P t^P_ib t^P_ja = (ib|ja) in the RI approximation) */
 int tr_get_tensor(tr_ctx *ctx, int which, double *out, int on_device);
 
 /* AX = A X for m trial vectors X[m][nocc][nvir] -> AX[m][nocc][nvir].
@@ -199,6 +215,14 @@ int tr_get_tensor(tr_ctx *ctx, int which, double *out, int on_device);
    stream; otherwise host pointers and the call returns when AX is written.
    X and AX must not overlap.  Requires tr_build. */
 int tr_matvec(tr_ctx *ctx, int m, const double *X, double *AX, int on_device);
+
+/* Full TDDFT-risp products (Sec. 2, Eq. hessian) for m trial vectors
+   X[m][nocc][nvir]: ApBX = (A + B) X and AmBX = (A - B) X, same layout.  Needs
+   a context built with tddft = 1.  on_device: device pointers, asynchronous on
+   the context stream; otherwise host pointers, returns when both are written.
+   The three arrays must not overlap.  Errors: TR_EINVAL (tddft = 0, not built,
+   null pointers, overlap). */
+int tr_matvec_tddft(tr_ctx *ctx, int m, const double *X, double *ApBX, double *AmBX, int on_device);
 
 /* Electric transition dipoles of n states in the dipole length form with Y = 0
    (Tamm-Dancoff; Sec. 2, Eq. transition):
@@ -249,6 +273,23 @@ int tr_matvec_noalloc(tr_ctx *ctx, int m, const double *X, double *AX);
    max_iter is reached (outputs filled with the current estimates). */
 int tr_solve(tr_ctx *ctx, double *omega, double *X, double *resid, int on_device,
              tr_solve_info *info);
+
+/* Davidson solve of full TDDFT-risp (tddft = 1; Sec. 2, Eq. tddft; Sec. 3.3):
+   one expansion basis V serves X+Y and X-Y; (A+B) and (A-B) are both projected
+   on it, the projected problem M- M+ a = Omega^2 a is solved through the
+   Cholesky factor L of M- (L^T M+ L symmetric), and each unconverged state adds
+   the two directions of the diagonal preconditioner of the 2 x 2 response system.
+   Outputs (host, or device if on_device): omega[nstates] (Ha, ascending);
+   XpY and XmY [nstates][nocc][nvir] (either may be NULL), X+Y and X-Y with
+   (X+Y).(X-Y) = 1, the largest-magnitude component of X+Y positive;
+   resid[nstates] = sqrt(|(A+B)(X+Y) - Omega (X-Y)|^2 + |(A-B)(X-Y) - Omega (X+Y)|^2)
+   (may be NULL).  tr_solve on such a context is this call with XmY = NULL.
+   Transition dipoles and oscillator strengths of these states: pass X+Y to
+   tr_transition_dipoles / tr_oscillator_strengths (Eq. transition).
+   Errors: TR_EINVAL (tddft = 0 or not built), TR_ECUDA (A - B projected on the
+   subspace not positive definite, subspace eigensolver), TR_ENOCONV. */
+int tr_solve_tddft(tr_ctx *ctx, double *omega, double *XpY, double *XmY, double *resid, int on_device,
+                   tr_solve_info *info);
 
 /* tr_build of n contexts concurrently: nthreads host threads (0: 8), each
    context on a stream of its own for the duration of the call.  Returns TR_OK

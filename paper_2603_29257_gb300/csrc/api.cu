@@ -82,6 +82,9 @@ int tr_create(tr_ctx **out, const tr_options *opt, void *cuda_stream)
                        (opt->xform_slices >= 2 && opt->xform_slices <= 7),
                    TR_EINVAL, "create: xform_slices must be -1, 0 or 2..7");
         TR_REQUIRE(opt->j_ao == 0 || opt->j_ao == 1, TR_EINVAL, "create: j_ao must be 0 or 1");
+        TR_REQUIRE(opt->tddft == 0 || opt->tddft == 1, TR_EINVAL, "create: tddft must be 0 or 1");
+        TR_REQUIRE(!opt->tddft || (opt->precision == TR_FP64 && opt->xform_slices <= 0), TR_EINVAL,
+                   "create: full TDDFT (tddft = 1) needs precision TR_FP64 and xform_slices <= 0");
         c->opt = *opt;
         normalise_options(&c->opt);
         c->st = (cudaStream_t)cuda_stream;
@@ -113,11 +116,14 @@ int tr_set_options(tr_ctx *ctx, const tr_options *opt)
                        (opt->xform_slices >= 2 && opt->xform_slices <= 7),
                    TR_EINVAL, "set_options: xform_slices must be -1, 0 or 2..7");
         TR_REQUIRE(opt->j_ao == 0 || opt->j_ao == 1, TR_EINVAL, "set_options: j_ao must be 0 or 1");
+        TR_REQUIRE(opt->tddft == 0 || opt->tddft == 1, TR_EINVAL, "set_options: tddft must be 0 or 1");
+        TR_REQUIRE(!opt->tddft || (opt->precision == TR_FP64 && opt->xform_slices <= 0), TR_EINVAL,
+                   "set_options: full TDDFT (tddft = 1) needs precision TR_FP64 and xform_slices <= 0");
         bool rebuild = opt->precision != ctx->opt.precision || opt->cx != ctx->opt.cx || opt->k_alpha != ctx->opt.k_alpha ||
                        opt->k_beta != ctx->opt.k_beta || opt->omega != ctx->opt.omega ||
                        opt->window_ev != ctx->opt.window_ev || opt->aux_on_h != ctx->opt.aux_on_h ||
                        opt->screen != ctx->opt.screen || opt->xform_slices != ctx->opt.xform_slices ||
-                       opt->j_ao != ctx->opt.j_ao;
+                       opt->j_ao != ctx->opt.j_ao || opt->tddft != ctx->opt.tddft;
         size_t limit = ctx->budget.limit;
         ctx->opt = *opt;
         normalise_options(&ctx->opt);
@@ -290,7 +296,45 @@ int tr_matvec(tr_ctx *ctx, int m, const double *X, double *AX, int on_device)
 
 int tr_solve(tr_ctx *ctx, double *omega, double *X, double *resid, int on_device, tr_solve_info *info)
 {
-    return guarded(ctx, [&]() { return tr::solve(ctx, omega, X, resid, on_device, info); });
+    return guarded(ctx, [&]() { return tr::solve(ctx, omega, X, nullptr, resid, on_device, info); });
+}
+
+int tr_solve_tddft(tr_ctx *ctx, double *omega, double *XpY, double *XmY, double *resid, int on_device,
+                   tr_solve_info *info)
+{
+    return guarded(ctx, [&]() {
+        TR_REQUIRE(ctx->opt.tddft, TR_EINVAL, "solve_tddft: the context was not set up with tddft = 1");
+        return tr::solve(ctx, omega, XpY, XmY, resid, on_device, info);
+    });
+}
+
+int tr_matvec_tddft(tr_ctx *ctx, int m, const double *X, double *ApBX, double *AmBX, int on_device)
+{
+    return guarded(ctx, [&]() {
+        TR_REQUIRE(m >= 0, TR_EINVAL, "matvec_tddft: m must be >= 0");
+        TR_REQUIRE(ctx->opt.tddft, TR_EINVAL, "matvec_tddft: the context was not set up with tddft = 1");
+        TR_REQUIRE(ctx->built, TR_EINVAL, "matvec_tddft: call tr_build first");
+        if (m == 0) return TR_OK;
+        TR_REQUIRE(X && ApBX && AmBX, TR_EINVAL, "matvec_tddft: null pointer");
+        const size_t n = (size_t)m * ctx->nov;
+        if (on_device) {
+            auto apart = [n](const double *a, const double *b) { return a + n <= b || b + n <= a; };
+            TR_REQUIRE(apart(X, ApBX) && apart(X, AmBX) && apart(ApBX, AmBX), TR_EINVAL,
+                       "matvec_tddft: X, ApBX and AmBX overlap");
+            tr::matvec_pm(ctx, m, X, ApBX, AmBX);
+            return TR_OK;
+        }
+        tr::DevBuf<double> dx, dp, dm;
+        dx.alloc(n, &ctx->budget, "matvec input");
+        dp.alloc(n, &ctx->budget, "matvec output");
+        dm.alloc(n, &ctx->budget, "matvec output");
+        TR_CUDA(cudaMemcpyAsync(dx.p, X, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
+        tr::matvec_pm(ctx, m, dx.p, dp.p, dm.p);
+        TR_CUDA(cudaMemcpyAsync(ApBX, dp.p, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->st));
+        TR_CUDA(cudaMemcpyAsync(AmBX, dm.p, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->st));
+        TR_CUDA(cudaStreamSynchronize(ctx->st));
+        return TR_OK;
+    });
 }
 
 int tr_build_batch(tr_ctx **ctxs, int n, int nthreads)

@@ -61,6 +61,7 @@ struct tr_ctx {
     tr::DevBuf<double> T2;     // T_ij^P stored [i][P][j]
     tr::DevBuf<double> Tab;    // T_ab^P = (ab|P) [nK][vK][vK]
     tr::DevBuf<double> D;      // e_a - e_i [nocc][nvir]
+    tr::DevBuf<double> Tia;    // full TDDFT: L_K^-1 (P|ia) on the window [nK][oK][vK]
     bool k_active = false;
 
     // reduced-precision form: FP32 copies (value and tf32 remainder) and tensor maps
@@ -85,6 +86,9 @@ struct tr_ctx {
 
     // Davidson state
     tr::DevBuf<double> V, W, Hs, Hw, Yev, Yw, theta, Xr, R, T, Tt, Tn, Wn, Cs, Ss, Gc, rn, part;
+    // full TDDFT: (A - B) products of V and of the new vectors, their subspace
+    // matrix, and the reduced problem's Cholesky factor, copies and coefficients
+    tr::DevBuf<double> Wm, Wnm, Hsm, Lr, Mr, Qr, Ca, Cb;
     // sliced copies of V and W (and of the new directions) for the subspace
     // products on the tensor cores (forms that use them, when all rows are on the device)
     tr::DevBuf<double> dvs_V, dvs_W, dvs_T, dvs_Vt, dvs_Wt, dvs_Y, dvs_C;
@@ -127,6 +131,9 @@ void get_tensor(tr_ctx *c, int which, double *out, int on_device);
 void matvec(tr_ctx *c, int m, const double *X, double *AX);
 // allocate the matvec workspaces for blocks of up to m vectors
 void reserve_matvec(tr_ctx *c, int m);
+// full TDDFT (asynchronous on c->st): BX = B X; P = (A + B) X and M = (A - B) X
+void matvec_b(tr_ctx *c, int m, const double *X, double *BX);
+void matvec_pm(tr_ctx *c, int m, const double *X, double *P, double *M);
 // slices of the tensor-core MO transforms (0: FP64 pipe)
 int xform_slices(const tr_ctx *c);
 // estimated peak device bytes of tr_build + tr_solve
@@ -155,7 +162,8 @@ void get_tensor_mixed(tr_ctx *c, int which, double *out, int on_device);
 void build_mixed(tr_ctx *c);
 void reserve_mixed(tr_ctx *c, int mb);
 void matvec_mixed(tr_ctx *c, int m, const double *X, double *AX);
-int solve(tr_ctx *c, double *omega, double *X, double *resid, int on_device, tr_solve_info *info);
+// Davidson; with opt.tddft the full problem, X+Y into X and X-Y into Xm (may be null)
+int solve(tr_ctx *c, double *omega, double *X, double *Xm, double *resid, int on_device, tr_solve_info *info);
 int solve_batch(tr_ctx **ctxs, int nb, double **omega, double **X, double **resid, int on_device,
                 tr_solve_info *infos, int autotune_tiles);
 

@@ -257,7 +257,9 @@ __global__ void cholqr_coef(const double *S, int p, double drop2, double *Gc, in
 }
 
 // sign convention: largest-magnitude component positive (ties: lowest index)
-__global__ void sign_fix(double *X, long long nov)
+// the largest-magnitude component of row r of X made positive (ties: lower
+// index); row r of X2 (optional) takes the same sign
+__global__ void sign_fix(double *X, long long nov, double *X2)
 {
     __shared__ double bv[1024];
     __shared__ long long bi[1024];
@@ -290,6 +292,65 @@ __global__ void sign_fix(double *X, long long nov)
     __syncthreads();
     const double sg = s_sg;
     for (long long t = threadIdx.x; t < nov; t += blockDim.x) X[(long long)r * nov + t] *= sg;
+    if (X2)
+        for (long long t = threadIdx.x; t < nov; t += blockDim.x) X2[(long long)r * nov + t] *= sg;
+}
+
+// ---- full TDDFT (Sec. 2, Eq. tddft): reduced problem and preconditioner
+
+// zero the strict upper triangle of a k x k matrix (the Cholesky factor keeps its input there)
+__global__ void zero_upper(double *L, int k)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+    if (j < k && j > i) L[(long long)i * k + j] = 0.0;
+}
+
+// After a failed factorisation (flag set) the eigensolver gets the identity, so
+// that it runs on finite input; the host reports the failure.
+__global__ void guard_identity(double *H, int k, const int *flag)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+    if (j < k && *flag) H[(long long)i * k + j] = i == j ? 1.0 : 0.0;
+}
+
+// theta_i = Omega_i^2 on entry, Omega_i on exit; Cab[r][i] (a, X+Y) scaled by
+// Omega^-1/2 and Cab[r][n + i] (b, X-Y) by Omega^-3/2, so that a.b = 1
+__global__ void rpa_coef(double *theta, double *Cab, int k, int n, int *flag)
+{
+    const int i = blockIdx.x;
+    const double w2 = theta[i];
+    const bool ok = w2 > 0.0;
+    const double om = ok ? sqrt(w2) : 1.0;
+    const double sa = 1.0 / sqrt(om), sb = sa / om;
+    for (int r = threadIdx.x; r < k; r += blockDim.x) {
+        Cab[(long long)r * 2 * n + i] *= sa;
+        Cab[(long long)r * 2 * n + n + i] *= sb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        theta[i] = om;
+        if (!ok) atomicCAS(flag, 0, -1);
+    }
+}
+
+// Diagonal preconditioner of the 2 x 2 response system [[D, -W], [-W, D]] for the
+// residual pair (R1, R2) of state r = idx[q] (Omega = theta[r]): row q of T gets
+// (D R1 + W R2) / (D^2 - W^2), row p + q gets (W R1 + D R2) / (D^2 - W^2); the
+// denominator is floored in magnitude
+__global__ void precond_rpa(double *T, const double *R, const double *D, const double *theta, const int *idx,
+                            int p, int n, long long nov, double floor_)
+{
+    const int q = blockIdx.y;
+    const int r = idx[q];
+    const double w = theta[r];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nov; t += (long long)gridDim.x * blockDim.x) {
+        const double d = D[t];
+        double den = d * d - w * w;
+        if (fabs(den) < floor_) den = den < 0.0 ? -floor_ : floor_;
+        const double r1 = R[(long long)r * nov + t], r2 = R[(long long)(n + r) * nov + t];
+        T[(long long)q * nov + t] = (d * r1 + w * r2) / den;
+        T[(long long)(p + q) * nov + t] = (w * r1 + d * r2) / den;
+    }
 }
 
 struct Events {
@@ -366,8 +427,8 @@ struct Dav {
     int n, b0, maxsp, max_iter, pmax, cs, kd;
     double tol;
     static constexpr int nblk = 256;
-    PinnedBuf Vh, Wh;
-    RowStore SV, SW;
+    PinnedBuf Vh, Wh, Wmh;
+    RowStore SV, SW, SWm;  // SWm: (A - B) V rows (full TDDFT)
     long long moved = 0;
     double *ws;
     size_t wsn;
@@ -379,42 +440,51 @@ struct Dav {
     // pinned host copies (asynchronous device-to-host): residual norms, Ritz
     // values and flags [eigensolver, tensor core, first keep count, kept count]
     double *h_rn = nullptr, *h_th = nullptr;
-    int *h_fl = nullptr;
+    int *h_fl = nullptr;  // [eigensolver, tensor core, first keep count, kept count, reduced problem]
     int pend_p = 0, pend_k0 = 0, pend_max = 0;
     bool pend_restart = false, pend_counted = true;
     // reduction-type subspace products (V^T W, V^T T) on the tensor cores with
     // 7-slice (FP64-level) Ozaki products: forms that use the tensor cores, when
     // every V/W row is on the device and the sliced copies fit the budget
     bool tcd = false;
+    // full TDDFT (Sec. 2, Eq. tddft): one basis V for X+Y and X-Y, W = (A + B) V and
+    // Wm = (A - B) V, Xr = [X+Y; X-Y] and R = [R1; R2] with 2 n rows each
+    bool rpa = false;
 
     explicit Dav(tr_ctx *ctx) : c(ctx), st(ctx->st)
     {
         TR_REQUIRE(c->built, TR_EINVAL, "solve: call tr_build first");
         TR_REQUIRE(c->opt.nstates >= 1, TR_EINVAL, "solve: nstates must be >= 1");
         TR_REQUIRE(c->opt.nstates <= 64, TR_EINVAL, "solve: nstates must be <= 64");
+        rpa = c->opt.tddft != 0;
+        TR_REQUIRE(!rpa || c->opt.precision == TR_FP64, TR_EINVAL, "solve: full TDDFT runs in the FP64 form only");
         nov = c->nov;
         rowb = (size_t)nov * sizeof(double);
         n = (int)std::min<long long>(c->opt.nstates, nov);
+        const int nr = rpa ? 2 * n : n;  // Ritz rows: X (TDA), or X+Y and X-Y
         b0 = c->opt.block > 0 ? c->opt.block : 2 * n;
         b0 = (int)std::min<long long>(std::max(b0, n), nov);
+        // new rows per step: up to nr (two directions per state in full TDDFT, or
+        // the restart basis); the subspace takes a restart basis plus one step
+        pmax = std::max(b0, nr);
         maxsp = c->opt.max_space > 0 ? c->opt.max_space : 20 * n;
-        maxsp = std::max(maxsp, b0 + n);
+        maxsp = std::max(maxsp, rpa ? pmax + nr : b0 + n);
         maxsp = (int)std::min<long long>(maxsp, std::max<long long>(nov, b0));
         max_iter = c->opt.max_iter > 0 ? c->opt.max_iter : 200;
         tol = c->opt.tol;
-        pmax = std::max(b0, n);
         TR_CUDA(cudaHostAlloc((void **)&h_rn, sizeof(double) * n, cudaHostAllocDefault));
         TR_CUDA(cudaHostAlloc((void **)&h_th, sizeof(double) * n, cudaHostAllocDefault));
-        TR_CUDA(cudaHostAlloc((void **)&h_fl, sizeof(int) * 4, cudaHostAllocDefault));
-        std::memset(h_fl, 0, sizeof(int) * 4);
+        TR_CUDA(cudaHostAlloc((void **)&h_fl, sizeof(int) * 5, cudaHostAllocDefault));
+        std::memset(h_fl, 0, sizeof(int) * 5);
 
         reserve_matvec(c, pmax);
         c->Tn.alloc((size_t)pmax * nov, &c->budget, "new vectors");
         c->Wn.alloc((size_t)pmax * nov, &c->budget, "new products");
+        if (rpa) c->Wnm.alloc((size_t)pmax * nov, &c->budget, "new products");
         c->T.alloc((size_t)pmax * nov, &c->budget, "new vectors");
         c->Tt.alloc((size_t)pmax * nov, &c->budget, "new vectors");
-        c->Xr.alloc((size_t)n * nov, &c->budget, "Ritz vectors");
-        c->R.alloc((size_t)n * nov, &c->budget, "residuals");
+        c->Xr.alloc((size_t)nr * nov, &c->budget, "Ritz vectors");
+        c->R.alloc((size_t)nr * nov, &c->budget, "residuals");
         c->part.alloc((size_t)nblk * pmax, &c->budget, "norms");
         c->rn.alloc(pmax, &c->budget, "norms");
         c->idx_dev.alloc(pmax + 2, &c->budget, "indices");
@@ -426,37 +496,52 @@ struct Dav {
         // how many V/W rows fit in HBM; the rest spill to pinned host memory
         c->V.release();
         c->W.release();
+        c->Wm.release();
         cs = std::max(8, pmax);  // staging rows per chunk
+        const int nstore = rpa ? 3 : 2;  // row stores: V, W (and Wm)
         const long long avail = (long long)c->budget.limit - (long long)c->budget.used;
-        const long long small = 5LL * maxsp * maxsp * 8 + 2LL * maxsp * pmax * 8 + (64LL << 20);
-        kd = (int)std::max<long long>(0, (avail - small) / (long long)(2 * rowb));
-        if (kd < maxsp) kd = (int)std::max<long long>(0, (avail - small - 2LL * cs * rowb) / (long long)(2 * rowb));
+        const long long small = (rpa ? 11LL : 5LL) * maxsp * maxsp * 8 + 2LL * maxsp * pmax * 8 + (64LL << 20);
+        kd = (int)std::max<long long>(0, (avail - small) / (long long)(nstore * rowb));
+        if (kd < maxsp) kd = (int)std::max<long long>(0, (avail - small - 2LL * cs * rowb) / (long long)(nstore * rowb));
         if (c->opt.dav_dev_rows > 0) kd = std::min(kd, c->opt.dav_dev_rows);
         kd = std::min(kd, maxsp);
         if (kd < maxsp && c->opt.host_budget > 0) {
-            const long long hrows = (long long)(c->opt.host_budget / (2 * rowb));
+            const long long hrows = (long long)(c->opt.host_budget / (nstore * rowb));
             maxsp = (int)std::min<long long>(maxsp, kd + hrows);
         }
-        TR_REQUIRE(maxsp >= b0 + 1 && maxsp >= n + 1, TR_ENOMEM,
+        TR_REQUIRE(maxsp >= b0 + 1 && maxsp >= n + 1 && (!rpa || maxsp >= pmax + nr), TR_ENOMEM,
                    "solve: device and host budgets leave no room for the Davidson subspace");
         c->V.alloc((size_t)kd * nov, &c->budget, "Davidson V");
         c->W.alloc((size_t)kd * nov, &c->budget, "Davidson W");
+        if (rpa) {
+            c->Wm.alloc((size_t)kd * nov, &c->budget, "Davidson (A - B) V");
+            c->Hsm.alloc((size_t)maxsp * maxsp, &c->budget, "subspace");
+            c->Lr.alloc((size_t)maxsp * maxsp, &c->budget, "subspace");
+            c->Mr.alloc((size_t)maxsp * maxsp, &c->budget, "subspace");
+            c->Qr.alloc((size_t)maxsp * maxsp, &c->budget, "subspace");
+            c->Ca.alloc((size_t)maxsp * 2 * n, &c->budget, "subspace");
+        }
         c->Hs.alloc((size_t)maxsp * maxsp, &c->budget, "subspace");
         c->Hw.alloc((size_t)maxsp * maxsp, &c->budget, "subspace");
         c->Yev.alloc((size_t)maxsp * maxsp, &c->budget, "subspace");
         c->Yw.alloc(eigh_lowest_scratch(maxsp, n) / sizeof(double), &c->budget, "subspace eigensolver scratch");
         c->theta.alloc(maxsp, &c->budget, "subspace");
         c->Cs.alloc((size_t)2 * maxsp * pmax, &c->budget, "projections");
-        SV.nov = SW.nov = nov;
-        SV.cap = SW.cap = maxsp;
-        SV.kd = SW.kd = kd;
+        SV.nov = SW.nov = SWm.nov = nov;
+        SV.cap = SW.cap = SWm.cap = maxsp;
+        SV.kd = SW.kd = SWm.kd = kd;
         SV.dev = c->V.p;
         SW.dev = c->W.p;
+        SWm.dev = c->Wm.p;
         if (kd < maxsp) {
             Vh.alloc((size_t)(maxsp - kd) * nov, "Davidson V");
             Wh.alloc((size_t)(maxsp - kd) * nov, "Davidson W");
             SV.host = Vh.p;
             SW.host = Wh.p;
+            if (rpa) {
+                Wmh.alloc((size_t)(maxsp - kd) * nov, "Davidson (A - B) V");
+                SWm.host = Wmh.p;
+            }
             c->stage.reserve((size_t)2 * cs * nov, &c->budget, "spill staging");
             if (!c->cst) TR_CUDA(cudaStreamCreateWithFlags(&c->cst, cudaStreamNonBlocking));
             for (auto &e : c->sev)
@@ -464,7 +549,7 @@ struct Dav {
         }
         ws = c->ws_split.p;
         wsn = c->ws_split.n;
-        if ((c->opt.precision == TR_MIXED || c->opt.precision == TR_FP64_TC) && kd == maxsp) {
+        if ((c->opt.precision == TR_MIXED || c->opt.precision == TR_FP64_TC) && kd == maxsp && !rpa) {
             const size_t sv = oz_bytes(maxsp, (int)nov, OZ_SLICES_FP64), stn = oz_bytes(pmax, (int)nov, OZ_SLICES_FP64);
             const size_t svt = oz_bytes(nov, maxsp, OZ_SLICES_FP64);
             const size_t ssm = oz_bytes(std::max(n, pmax), maxsp, OZ_SLICES_FP64);
@@ -492,6 +577,7 @@ struct Dav {
             }
         }
         TR_CUDA(cudaMemsetAsync(c->flag.p, 0, 2 * sizeof(int), st));
+        if (rpa) TR_CUDA(cudaMemsetAsync(c->flag.p + 3, 0, sizeof(int), st));
     }
     // C(row r, col i) = sum_k A[ra0 + r][k] B[rb0 + i][k] for r < M, i < N into
     // d[r ldm + i ldn], FP64-level products on the tensor cores, K split over CTAs
@@ -585,7 +671,15 @@ struct Dav {
                       h_insert<<<dim3(cdiv(kk, 128), p), 128, 0, st>>>(c->Hs.p, maxsp, A1, A2, p, kk, k0));
             return;
         }
-        for_rows(SW, 0, k0, [&](const double *rows, int r0, int nr) {
+        h_update_rows(k0, p, Vn, Wn, SW, c->Hs.p);
+    }
+    // rows/cols k0..k0+p of the subspace matrix H (ld maxsp) of the products in S, FP64
+    void h_update_rows(int k0, int p, const double *Vn, const double *Wn, RowStore &S, double *H)
+    {
+        Prof &pf = c->prof;
+        const int kk = k0 + p;
+        double *A1 = c->Cs.p, *A2 = c->Cs.p + (size_t)maxsp * pmax;
+        for_rows(S, 0, k0, [&](const double *rows, int r0, int nr) {
             dgemm(pf, st, "subspace_H", false, true, p, nr, (int)nov, 1.0, Vn, nov, rows, nov, 0.0, A1 + r0, kk,
                   Batch(), ws, wsn);
         });
@@ -596,7 +690,7 @@ struct Dav {
         });
         dgemm(pf, st, "subspace_H", false, true, p, p, (int)nov, 1.0, Wn, nov, Vn, nov, 0.0, A2 + k0, kk, Batch(), ws, wsn);
         TR_LAUNCH(pf, st, "subspace_insert", 0, 0,
-                  h_insert<<<dim3(cdiv(kk, 128), p), 128, 0, st>>>(c->Hs.p, maxsp, A1, A2, p, kk, k0));
+                  h_insert<<<dim3(cdiv(kk, 128), p), 128, 0, st>>>(H, maxsp, A1, A2, p, kk, k0));
     }
     // Orthonormalise rows src[0:p] into dst[0:p] without waiting on the host:
     // Cholesky-QR with dropping (first pass), then again without dropping; rows
@@ -666,7 +760,8 @@ struct Dav {
     void apply_pending()
     {
         TR_CUDA(cudaEventRecord(ev.e[4], st));
-        matvec(c, pend_max, c->Tn.p, c->Wn.p);
+        if (rpa) matvec_pm(c, pend_max, c->Tn.p, c->Wn.p, c->Wnm.p);
+        else matvec(c, pend_max, c->Tn.p, c->Wn.p);
         TR_CUDA(cudaEventRecord(ev.e[5], st));
     }
     // the kept count of prepare() must be on the host: call after the stream
@@ -684,14 +779,20 @@ struct Dav {
             }
         }
         h_update(pend_k0, pend_p, c->Tn.p, c->Wn.p);
+        if (rpa) h_update_rows(pend_k0, pend_p, c->Tn.p, c->Wnm.p, SWm, c->Hsm.p);
         store_rows(SV, pend_k0, pend_p, c->Tn.p);
         store_rows(SW, pend_k0, pend_p, c->Wn.p);
+        if (rpa) store_rows(SWm, pend_k0, pend_p, c->Wnm.p);
         k = pend_k0 + pend_p;
         nmv += pend_p;
         pend_p = 0;
     }
     void eig_async()
     {
+        if (rpa) {
+            eig_rpa_async();
+            return;
+        }
         Prof &pf = c->prof;
         ++it;
         TR_CUDA(cudaEventRecord(ev.e[0], st));
@@ -733,6 +834,61 @@ struct Dav {
         TR_CUDA(cudaEventRecord(ev.e[2], st));
         eig_timed = true;
     }
+    // Full TDDFT (Sec. 2, Eq. tddft; Sec. 3.3): with M+ = V^T (A+B) V and
+    // M- = V^T (A-B) V = L L^T, the reduced problem M- M+ a = Omega^2 a is the
+    // symmetric L^T M+ L w = Omega^2 w with a = L w; b = M+ a / Omega (so that
+    // M- b = Omega a), scaled to a.b = 1.  X+Y = V^T a, X-Y = V^T b and the
+    // residuals R1 = (A+B)(X+Y) - Omega (X-Y), R2 = (A-B)(X-Y) - Omega (X+Y).
+    void eig_rpa_async()
+    {
+        Prof &pf = c->prof;
+        ++it;
+        const int n2 = 2 * n;
+        double *Lr = c->Lr.p, *Mr = c->Mr.p, *Qr = c->Qr.p, *Cab = c->Ca.p;
+        int *rflag = c->flag.p + 3;
+        TR_CUDA(cudaEventRecord(ev.e[0], st));
+        TR_LAUNCH(pf, st, "copy_sub", 0, 0, copy_sub<<<dim3(cdiv(k, 128), k), 128, 0, st>>>(c->Hsm.p, maxsp, Lr, k));
+        TR_LAUNCH(pf, st, "copy_sub", 0, 0, copy_sub<<<dim3(cdiv(k, 128), k), 128, 0, st>>>(c->Hs.p, maxsp, Mr, k));
+        TR_CUDA(cudaMemsetAsync(c->flag.p, 0, sizeof(int), st));
+        TR_CUDA(cudaMemsetAsync(rflag, 0, sizeof(int), st));
+        cholesky(pf, st, Lr, k, rflag);
+        TR_LAUNCH(pf, st, "zero_upper", 0, 0, zero_upper<<<dim3(cdiv(k, 128), k), 128, 0, st>>>(Lr, k));
+        dgemm(pf, st, "rpa_reduce", false, false, k, k, k, 1.0, Mr, k, Lr, k, 0.0, Qr, k, Batch(), nullptr, 0);
+        dgemm(pf, st, "rpa_reduce", true, false, k, k, k, 1.0, Lr, k, Qr, k, 0.0, c->Hw.p, k, Batch(), nullptr, 0);
+        TR_LAUNCH(pf, st, "guard", 0, 0, guard_identity<<<dim3(cdiv(k, 128), k), 128, 0, st>>>(c->Hw.p, k, rflag));
+        eigh_lowest(pf, st, c->Hw.p, k, n, c->theta.p, c->Yev.p, k, c->Yw.p, c->flag.p);
+        // a = L w into columns 0..n-1 of Cab (ld 2n), b = M+ a into columns n..2n-1
+        dgemm(pf, st, "rpa_coef", false, false, k, n, k, 1.0, Lr, k, c->Yev.p, k, 0.0, Cab, n2, Batch(), nullptr, 0);
+        dgemm(pf, st, "rpa_coef", false, false, k, n, k, 1.0, Mr, k, Cab, n2, 0.0, Cab + n, n2, Batch(), nullptr, 0);
+        TR_LAUNCH(pf, st, "rpa_coef", 0, 0, rpa_coef<<<n, 128, 0, st>>>(c->theta.p, Cab, k, n, rflag));
+        TR_CUDA(cudaEventRecord(ev.e[1], st));
+        // [X+Y; X-Y] = [a b]^T V in one pass over V; R1 = a^T W, R2 = b^T Wm
+        for_rows(SV, 0, k, [&](const double *rows, int r0, int nr) {
+            dgemm(pf, st, "ritz", true, false, n2, (int)nov, nr, 1.0, Cab + (long long)r0 * n2, n2, rows, nov,
+                  r0 == 0 ? 0.0 : 1.0, c->Xr.p, nov, Batch(), nullptr, 0);
+        });
+        for_rows(SW, 0, k, [&](const double *rows, int r0, int nr) {
+            dgemm(pf, st, "ritz", true, false, n, (int)nov, nr, 1.0, Cab + (long long)r0 * n2, n2, rows, nov,
+                  r0 == 0 ? 0.0 : 1.0, c->R.p, nov, Batch(), nullptr, 0);
+        });
+        for_rows(SWm, 0, k, [&](const double *rows, int r0, int nr) {
+            dgemm(pf, st, "ritz", true, false, n, (int)nov, nr, 1.0, Cab + (long long)r0 * n2 + n, n2, rows, nov,
+                  r0 == 0 ? 0.0 : 1.0, c->R.p + (long long)n * nov, nov, Batch(), nullptr, 0);
+        });
+        TR_LAUNCH(pf, st, "residual", 0, 24.0 * n * nov,
+                  ritz_resid<<<dim3(nblk, n), 256, 0, st>>>(c->R.p, c->Xr.p + (long long)n * nov, c->theta.p, n, nov,
+                                                            c->part.p));
+        TR_LAUNCH(pf, st, "residual", 0, 24.0 * n * nov,
+                  ritz_resid<<<dim3(nblk, n), 256, 0, st>>>(c->R.p + (long long)n * nov, c->Xr.p, c->theta.p, n, nov,
+                                                            c->part.p + (long long)nblk * n));
+        TR_LAUNCH(pf, st, "residual", 0, 0, finish_norms<<<cdiv(n, 64), 64, 0, st>>>(c->part.p, 2 * nblk, n, c->rn.p));
+        TR_CUDA(cudaMemcpyAsync(h_rn, c->rn.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+        TR_CUDA(cudaMemcpyAsync(h_th, c->theta.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+        TR_CUDA(cudaMemcpyAsync(h_fl, c->flag.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        TR_CUDA(cudaMemcpyAsync(h_fl + 4, rflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TR_CUDA(cudaEventRecord(ev.e[2], st));
+        eig_timed = true;
+    }
     // after st synchronised
     void check()
     {
@@ -741,6 +897,9 @@ struct Dav {
             t_oth += elapsed(ev.e[1], ev.e[2]);
             eig_timed = false;
         }
+        TR_REQUIRE(!rpa || h_fl[4] == 0, TR_ECUDA,
+                   h_fl[4] < 0 ? "solve: non-positive Omega^2 in the projected full TDDFT problem"
+                               : "solve: A - B projected on the subspace is not positive definite");
         TR_REQUIRE(!h_fl[0], TR_ECUDA, "solve: subspace eigensolver did not converge");
         TR_REQUIRE(h_fl[1] != TC_ERR_W_RANGE, TR_ECUDA,
                    "solve: a product block exceeded the exponent range fixed for the sliced W");
@@ -761,71 +920,87 @@ struct Dav {
     {
         Prof &pf = c->prof;
         const int p = (int)unconv.size();
+        const int pp = rpa ? 2 * p : p;  // new directions
+        const int nr = rpa ? 2 * n : n;  // restart basis: the Ritz vectors (X+Y and X-Y)
         pend_counted = false;
-        if (k + p > maxsp) {
+        if (k + pp > maxsp) {
             // restart from the Ritz vectors; A V is recomputed for them (Sec. 3.3)
-            orthonormal_block_async(c->Xr.p, n, c->Tn.p, c->Tt.p);
+            orthonormal_block_async(c->Xr.p, nr, c->Tn.p, c->Tt.p);
             pend_k0 = 0;
-            pend_max = n;
+            pend_max = nr;
             pend_restart = true;
             nrestart += 1;
             return;
         }
         TR_CUDA(cudaMemcpyAsync(c->idx_dev.p, unconv.data(), sizeof(int) * p, cudaMemcpyHostToDevice, st));
-        TR_LAUNCH(pf, st, "precondition", 0, 32.0 * p * nov,
-                  precond<<<dim3(nblk, p), 256, 0, st>>>(c->T.p, c->R.p, c->D.p, c->theta.p, c->idx_dev.p, p, nov,
-                                                          PRECOND_FLOOR));
-        norms_of(c->T.p, p, c->rn.p);
-        TR_LAUNCH(pf, st, "normalise", 0, 16.0 * p * nov,
-                  row_scale_inv<<<dim3(nblk, p), 256, 0, st>>>(c->T.p, p, nov, c->rn.p));
+        if (rpa)
+            TR_LAUNCH(pf, st, "precondition", 0, 48.0 * p * nov,
+                      precond_rpa<<<dim3(nblk, p), 256, 0, st>>>(c->T.p, c->R.p, c->D.p, c->theta.p, c->idx_dev.p, p, n,
+                                                                  nov, PRECOND_FLOOR));
+        else
+            TR_LAUNCH(pf, st, "precondition", 0, 32.0 * p * nov,
+                      precond<<<dim3(nblk, p), 256, 0, st>>>(c->T.p, c->R.p, c->D.p, c->theta.p, c->idx_dev.p, p, nov,
+                                                              PRECOND_FLOOR));
+        norms_of(c->T.p, pp, c->rn.p);
+        TR_LAUNCH(pf, st, "normalise", 0, 16.0 * pp * nov,
+                  row_scale_inv<<<dim3(nblk, pp), 256, 0, st>>>(c->T.p, pp, nov, c->rn.p));
         // two passes of block classical Gram-Schmidt against V[0:k]
         for (int pass = 0; pass < 2; ++pass) {
             if (tcd) {
                 OzMat Ts;
-                oz_bind(Ts, c->dvs_T.p, p, (int)nov, OZ_SLICES_FP64);
+                oz_bind(Ts, c->dvs_T.p, pp, (int)nov, OZ_SLICES_FP64);
                 oz_split(pf, st, "oz_split_T", c->T.p, nov, 1, Ts);
-                tc_reduce("orth_project_tc", c->dz_V, 0, Ts, 0, k, p, c->Cs.p, p, 1);  // Cs[r][i] = V_r . T_i
+                tc_reduce("orth_project_tc", c->dz_V, 0, Ts, 0, k, pp, c->Cs.p, pp, 1);  // Cs[r][i] = V_r . T_i
             } else {
                 for_rows(SV, 0, k, [&](const double *rows, int r0, int nr) {
-                    dgemm(pf, st, "orth_project", false, true, nr, p, (int)nov, 1.0, rows, nov, c->T.p, nov, 0.0,
-                          c->Cs.p + (long long)r0 * p, p, Batch(), ws, wsn);
+                    dgemm(pf, st, "orth_project", false, true, nr, pp, (int)nov, 1.0, rows, nov, c->T.p, nov, 0.0,
+                          c->Cs.p + (long long)r0 * pp, pp, Batch(), ws, wsn);
                 });
             }
             if (tcd) {
                 // T[i][col] -= sum_r V[r][col] Cs[r][i]
                 OzMat Css;
-                oz_bind(Css, c->dvs_C.p, p, k, OZ_SLICES_FP64);
-                oz_split(pf, st, "oz_split_Cs", c->Cs.p, 1, p, Css);
+                oz_bind(Css, c->dvs_C.p, pp, k, OZ_SLICES_FP64);
+                oz_split(pf, st, "oz_split_Cs", c->Cs.p, 1, pp, Css);
                 OzOut o;
                 o.d = c->T.p;
                 o.ldm = 1;
                 o.ldn = nov;
                 o.alpha = -1.0;
                 o.accumulate = true;
-                oz_gemm(pf, st, "orth_update_tc", c->dz_Vt, 0, 0, 0, 0, Css, 0, 0, 0, 0, (int)nov, p, Css.nkb, 1, 1, o,
+                oz_gemm(pf, st, "orth_update_tc", c->dz_Vt, 0, 0, 0, 0, Css, 0, 0, 0, 0, (int)nov, pp, Css.nkb, 1, 1, o,
                         c->flag.p + 1);
             } else {
                 for_rows(SV, 0, k, [&](const double *rows, int r0, int nr) {
-                    dgemm(pf, st, "orth_update", true, false, p, (int)nov, nr, -1.0, c->Cs.p + (long long)r0 * p, p, rows,
+                    dgemm(pf, st, "orth_update", true, false, pp, (int)nov, nr, -1.0, c->Cs.p + (long long)r0 * pp, pp, rows,
                           nov, 1.0, c->T.p, nov, Batch(), nullptr, 0);
                 });
             }
         }
-        orthonormal_block_async(c->T.p, p, c->Tn.p, c->Tt.p);
+        orthonormal_block_async(c->T.p, pp, c->Tn.p, c->Tt.p);
         pend_k0 = k;
-        pend_max = p;
+        pend_max = pp;
         pend_restart = false;
     }
     // outputs: omega, unit-norm sign-fixed X, residual norms
-    int output(double *omega, double *Xout, double *resid, int on_device, tr_solve_info *info)
+    // (full TDDFT: X+Y into Xout and X-Y into Xmout, (X+Y).(X-Y) = 1 from the
+    // reduced problem, the sign fixed on X+Y)
+    int output(double *omega, double *Xout, double *Xmout, double *resid, int on_device, tr_solve_info *info)
     {
         Prof &pf = c->prof;
-        norms_of(c->Xr.p, n, c->rn.p);
-        TR_LAUNCH(pf, st, "normalise", 0, 16.0 * n * nov, row_scale_inv<<<dim3(nblk, n), 256, 0, st>>>(c->Xr.p, n, nov, c->rn.p));
-        TR_LAUNCH(pf, st, "sign_fix", 0, 0, sign_fix<<<n, 1024, 0, st>>>(c->Xr.p, nov));
+        if (rpa) {
+            TR_LAUNCH(pf, st, "sign_fix", 0, 0, sign_fix<<<n, 1024, 0, st>>>(c->Xr.p, nov, c->Xr.p + (long long)n * nov));
+        } else {
+            norms_of(c->Xr.p, n, c->rn.p);
+            TR_LAUNCH(pf, st, "normalise", 0, 16.0 * n * nov,
+                      row_scale_inv<<<dim3(nblk, n), 256, 0, st>>>(c->Xr.p, n, nov, c->rn.p));
+            TR_LAUNCH(pf, st, "sign_fix", 0, 0, sign_fix<<<n, 1024, 0, st>>>(c->Xr.p, nov, nullptr));
+        }
         const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
         TR_CUDA(cudaMemcpyAsync(omega, c->theta.p, sizeof(double) * n, kind, st));
         if (Xout) TR_CUDA(cudaMemcpyAsync(Xout, c->Xr.p, sizeof(double) * (size_t)n * nov, kind, st));
+        if (Xmout && rpa)
+            TR_CUDA(cudaMemcpyAsync(Xmout, c->Xr.p + (size_t)n * nov, sizeof(double) * (size_t)n * nov, kind, st));
         if (resid) {
             if (on_device)
                 TR_CUDA(cudaMemcpyAsync(resid, h_rn, sizeof(double) * n, cudaMemcpyHostToDevice, st));
@@ -851,9 +1026,10 @@ struct Dav {
     }
 };
 
-int solve(tr_ctx *c, double *omega, double *Xout, double *resid, int on_device, tr_solve_info *info)
+int solve(tr_ctx *c, double *omega, double *Xout, double *Xmout, double *resid, int on_device, tr_solve_info *info)
 {
     TR_REQUIRE(omega, TR_EINVAL, "solve: omega must not be NULL");
+    TR_REQUIRE(!Xmout || c->opt.tddft, TR_EINVAL, "solve: X-Y is returned for tddft = 1 only");
     Dav d(c);
     d.guess();
     d.apply_pending();
@@ -873,7 +1049,7 @@ int solve(tr_ctx *c, double *omega, double *Xout, double *resid, int on_device, 
         d.t_mv += elapsed(d.ev.e[4], d.ev.e[5]);
         d.absorb();
     }
-    return d.output(omega, Xout, resid, on_device, info);
+    return d.output(omega, Xout, Xmout, resid, on_device, info);
 }
 
 // ---------------------------------------------------------------- many molecules
@@ -979,6 +1155,7 @@ int solve_batch(tr_ctx **ctxs, int nb, double **omega, double **X, double **resi
     std::vector<tr_ctx *> cs(ctxs, ctxs + nb);
     for (int i = 0; i < nb; ++i) {
         TR_REQUIRE(cs[i] && cs[i]->built, TR_EINVAL, "solve_batch: every context must be built");
+        TR_REQUIRE(!cs[i]->opt.tddft, TR_EINVAL, "solve_batch: full TDDFT (tddft = 1) runs through tr_solve only");
         TR_REQUIRE(omega[i], TR_EINVAL, "solve_batch: omega must not be NULL");
         for (int j = 0; j < i; ++j) TR_REQUIRE(cs[i] != cs[j], TR_EINVAL, "solve_batch: a context appears twice");
         TR_REQUIRE(cs[i]->device == cs[0]->device, TR_EINVAL, "solve_batch: contexts on different devices");
@@ -1096,7 +1273,7 @@ int solve_batch(tr_ctx **ctxs, int nb, double **omega, double **X, double **resi
     int rc = TR_OK;
     for (int i = 0; i < nb; ++i) {
         ds[i]->t_mv = graph_ms;
-        int r = ds[i]->output(omega[i], X ? X[i] : nullptr, resid ? resid[i] : nullptr, on_device,
+        int r = ds[i]->output(omega[i], X ? X[i] : nullptr, nullptr, resid ? resid[i] : nullptr, on_device,
                               infos ? &infos[i] : nullptr);
         if (r != TR_OK) rc = r;
     }
@@ -1324,7 +1501,7 @@ void solver_loop(tr_server *S)
                     if (!X) throw Error(TR_ENOMEM, "server: host allocation of X failed");
                 }
                 tr_solve_info info;
-                rc = m.d->output(res.omega, X, res.resid, 0, &info);
+                rc = m.d->output(res.omega, X, nullptr, res.resid, 0, &info);
                 res.X = X;
                 res.niter = info.niter;
                 res.nmatvec = info.nmatvec;
@@ -1532,6 +1709,7 @@ int tr_server_submit(tr_server *S, const tr_request *q, long long *id)
     r->nocc = q->nocc;
     r->C.assign(q->C, q->C + (size_t)q->nao * q->nmo);
     r->eps.assign(q->eps, q->eps + q->nmo);
+    if (q->opt.tddft) return TR_EINVAL;  // full TDDFT runs through tr_solve only
     r->o = q->opt;
     r->want_x = q->want_x;
     std::lock_guard<std::mutex> lk(S->mu);

@@ -132,11 +132,13 @@ void metric(tr_ctx *c, const std::vector<AuxDev> &all, double ka, double kb, dou
     TR_CUDA(cudaStreamSynchronize(c->st));
 }
 
-// Cholesky factor and inverse of a metric; throws TR_ENOTPD if not positive definite
-void metric_inverse(tr_ctx *c, double *G, int n, double *Ginv, const char *what)
+// Cholesky factor and inverse of a metric; throws TR_ENOTPD if not positive definite.
+// Linv (optional, n x n): the inverse of the lower Cholesky factor L, G = L L^T.
+void metric_inverse(tr_ctx *c, double *G, int n, double *Ginv, const char *what, DevBuf<double> *Linv = nullptr)
 {
     if (n == 0) return;
-    DevBuf<double> work;
+    DevBuf<double> own;
+    DevBuf<double> &work = Linv ? *Linv : own;
     work.alloc((size_t)n * n, &c->budget, "metric work");
     TR_CUDA(cudaMemsetAsync(c->flag.p, 0, sizeof(int), c->st));
     cholesky(c->prof, c->st, G, n, c->flag.p);
@@ -348,8 +350,9 @@ void compute_int3c_chunk(tr_ctx *c, int which, int p0, int np, double *out)
         compute_int3c(c, c->auxK_h, p0, np, out, c->opt.k_alpha, c->opt.k_beta, c->opt.omega);
 }
 
-// FP64 MO transforms: (P|ia); (P|ij), (P|ab) on the window; T_ij = G_K^-1 (P|ij)
-static void transforms_fp64(tr_ctx *c, DevBuf<double> &Iij)
+// FP64 MO transforms: (P|ia); (P|ij), (P|ab) on the window; T_ij = G_K^-1 (P|ij);
+// with Iia (full TDDFT) also (P|ia) on the window with the K operator
+static void transforms_fp64(tr_ctx *c, DevBuf<double> &Iij, DevBuf<double> *Iia)
 {
     const int nao = c->nao, nocc = c->nocc, nvir = c->nvir, nmo = c->nmo, nJ = c->nJ, nK = c->nK;
     const long long nov = c->nov;
@@ -399,6 +402,13 @@ static void transforms_fp64(tr_ctx *c, DevBuf<double> &Iij)
         g.sC1 = (long long)oK * oK;
         dgemm(pf, st, "xform_K2", false, false, oK, oK, nao, 1.0, H.p, nao, c->C.p + o0, nmo, 0.0,
               Iij.p + (long long)p0 * oK * oK, oK, g, nullptr, 0);
+        if (Iia) {
+            // (P|ia) = (C_occK^T (P|mn)) C_virK, the half transform shared with (P|ij)
+            Batch x = g;
+            x.sC1 = (long long)oK * vK;
+            dgemm(pf, st, "xform_Kx", false, false, oK, vK, nao, 1.0, H.p, nao, c->C.p + nocc, nmo, 0.0,
+                  Iia->p + (long long)p0 * oK * vK, vK, x, nullptr, 0);
+        }
         h.sC1 = (long long)vK * nao;
         dgemm(pf, st, "xform_K1", true, false, vK, nao, nao, 1.0, c->C.p + nocc, nmo, I.p, nao, 0.0, H.p, nao, h,
               nullptr, 0);
@@ -503,6 +513,8 @@ void build(tr_ctx *c)
     c->Tab.release();
     c->T2.release();
     c->GinvK.release();
+    c->Tia.release();
+    const bool tddft = c->opt.tddft != 0;
 
     // metrics and their inverses (Sec. 2, Eq. RI; K metric with the K operator, Sec. 3.2)
     c->GinvJ.alloc((size_t)nJ * nJ, &c->budget, "J metric");
@@ -512,21 +524,31 @@ void build(tr_ctx *c)
         metric(c, c->auxJ_h, 1.0, 0.0, 0.0, G.p);
         metric_inverse(c, G.p, nJ, c->GinvJ.p, "Coulomb");
     }
+    DevBuf<double> LinvK;  // full TDDFT: inverse Cholesky factor of the K metric
     if (c->k_active) {
         DevBuf<double> G;
         G.alloc((size_t)nK * nK, &c->budget, "K metric");
         c->GinvK.alloc((size_t)nK * nK, &c->budget, "K metric");
         metric(c, c->auxK_h, c->opt.k_alpha, c->opt.k_beta, c->opt.omega, G.p);
-        metric_inverse(c, G.p, nK, c->GinvK.p, "exchange");
+        metric_inverse(c, G.p, nK, c->GinvK.p, "exchange", tddft ? &LinvK : nullptr);
     }
     // MO transforms
     {
-        DevBuf<double> Iij;
-        const int oK = c->oK;
+        DevBuf<double> Iij, Iia;
+        const int oK = c->oK, vK = c->vK;
         if (c->k_active) Iij.alloc((size_t)nK * oK * oK, &c->budget, "(ij|P)");
+        const bool kx = tddft && c->k_active;
+        if (kx) Iia.alloc((size_t)nK * oK * vK, &c->budget, "(ia|P) on the window");
         const int S = xform_slices(c);
+        TR_REQUIRE(S == 0 || !tddft, TR_EINVAL, "build: full TDDFT needs the FP64 MO transforms");
         if (S > 0) transforms_oz(c, Iij, S);
-        else transforms_fp64(c, Iij);
+        else transforms_fp64(c, Iij, kx ? &Iia : nullptr);
+        if (kx) {
+            // t^P_ia = sum_Q (L^-1)_PQ (Q|ia): sum_P t^P_ib t^P_ja = (ib|ja) with (P|Q)^-1 = L^-T L^-1
+            c->Tia.alloc((size_t)nK * oK * vK, &c->budget, "T_ia");
+            dgemm(pf, st, "apply_K_factor", false, false, nK, (int)((long long)oK * vK), nK, 1.0, LinvK.p, nK, Iia.p,
+                  (long long)oK * vK, 0.0, c->Tia.p, (long long)oK * vK, Batch(), nullptr, 0);
+        }
         if (c->k_active) {
             // T_ij^P = sum_Q (ij|Q) (Q|P)^-1, stored [i][P][j]
             c->T2.alloc((size_t)oK * nK * oK, &c->budget, "T_ij");
@@ -599,6 +621,11 @@ void get_tensor(tr_ctx *c, int which, double *out, int on_device)
             break;
         case 2: src = c->Tab.p; n = c->k_active ? (size_t)c->nK * c->vK * c->vK : 0; break;
         case 3: src = c->D.p; n = (size_t)c->nov; break;
+        case 4:
+            TR_REQUIRE(c->opt.tddft, TR_EINVAL, "get_tensor: T_ia is built with tddft = 1 only");
+            src = c->Tia.p;
+            n = c->k_active ? (size_t)c->nK * c->oK * c->vK : 0;
+            break;
         default: throw Error(TR_EINVAL, "get_tensor: unknown tensor");
     }
     if (n)
@@ -643,18 +670,23 @@ size_t footprint(tr_ctx *c)
         tcb = (nJt > 0 ? (double)oz_bytes((long long)nJt, (int)nov, Sf) + (double)oz_bytes((long long)nov, (int)nJt, Sf) : 0.0) +
               (nK > 0 ? (double)oz_bytes((long long)(nK * vK), (int)vK, Sf) + (double)oz_bytes((long long)oK, (int)(nK * oK), Sf) : 0.0);
     }
-    const double build_peak = std::max(npc * per + cs + t64 + t32, t64 + tcb);
+    // full TDDFT: T_ia on the window (and its unfactored copy during the build)
+    const bool rpa = c->opt.tddft != 0;
+    const double tx = rpa ? d * nK * oK * vK : 0.0;
+    const double build_peak = std::max(npc * per + cs + t64 + t32 + 2.0 * tx, t64 + tcb + tx);
     // solve: tensors kept, Davidson storage and product workspaces
-    const double kept = mixed ? t32 + d * oK * nK * oK : t64 - d * nK * oK * oK;
+    const double kept = (mixed ? t32 + d * oK * nK * oK : t64 - d * nK * oK * oK) + tx;
     const int n = (int)std::min<double>(c->opt.nstates, nov);
     const int b0 = (int)std::min<double>(std::max(c->opt.block > 0 ? c->opt.block : 2 * n, n), nov);
     int maxsp = c->opt.max_space > 0 ? c->opt.max_space : 20 * n;
-    maxsp = (int)std::min<double>(std::max(maxsp, b0 + n), std::max(nov, (double)b0));
-    const double pmax = std::max(b0, n);
+    maxsp = (int)std::min<double>(std::max(maxsp, b0 + (rpa ? 2 : 1) * n), std::max(nov, (double)b0));
+    const double pmax = std::max(b0, (rpa ? 2 : 1) * n);
     const double mb = std::min<double>(pmax, c->mblk);
-    const double dav = d * nov * (2.0 * maxsp + 4.0 * pmax + 2.0 * n) +
-                       d * (5.0 * maxsp * maxsp + 2.0 * maxsp * pmax + 6.0 * n * maxsp + 5.0 * maxsp + 16.0 + n);
-    const double mws = nK > 0 ? std::min<double>((double)c->opt.matvec_ws_bytes, d * mb * nK * oK * vK) +
+    // V and W (and the A - B products) by rows; new vectors, products and scratch; Ritz vectors and residuals
+    const double dav = d * nov * ((rpa ? 3.0 : 2.0) * maxsp + (rpa ? 5.0 : 4.0) * pmax + (rpa ? 4.0 : 2.0) * n) +
+                       d * ((rpa ? 10.0 : 5.0) * maxsp * maxsp + 2.0 * maxsp * pmax + 6.0 * n * maxsp + 5.0 * maxsp + 16.0 + n);
+    const double mw = rpa ? std::max(oK, vK) : vK;
+    const double mws = nK > 0 ? std::min<double>((double)c->opt.matvec_ws_bytes, d * mb * nK * oK * vK) * (mw / std::max(vK, 1.0)) +
                                     (mixed ? 2.0 * f * mb * oK * vKp + f * mb * nov : d * mb * oK * vK)
                               : 0.0;
     const double ws = d * 16.0 * (1 << 20) + 2.0 * d * std::max(nJ, 1.0) * mb + mws;
@@ -699,7 +731,9 @@ void reserve_matvec(tr_ctx *c, int m)
     }
     if (c->k_active) {
         c->ws_Xw.reserve((size_t)mb * c->oK * c->vK, &c->budget, "K workspace");
-        c->ws_M.reserve((size_t)matvec_pchunk(c, mb) * mb * c->oK * c->vK, &c->budget, "K workspace");
+        // full TDDFT: the (ib|ja) intermediate E [m][i][P][j] of a chunk takes oK in place of vK
+        const size_t w = c->opt.tddft ? (size_t)std::max(c->oK, c->vK) : (size_t)c->vK;
+        c->ws_M.reserve((size_t)matvec_pchunk(c, mb) * mb * c->oK * w, &c->budget, "K workspace");
     }
 }
 
@@ -774,6 +808,94 @@ void matvec(tr_ctx *c, int m, const double *X, double *AX)
     }
 }
 
+
+// ---------------------------------------------------------------- full TDDFT-risp
+
+namespace {
+
+// P = A X + B X, M = A X - B X in place (P holds A X, M holds B X on entry)
+__global__ void pm_combine(double *__restrict__ P, double *__restrict__ M, long long n)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const double a = P[t], b = M[t];
+        P[t] = a + b;
+        M[t] = a - b;
+    }
+}
+
+}  // namespace
+
+// B X = 2 J X - c_x K' X for m device vectors (Sec. 2, Eq. hessian), with
+//   K'_mia = sum_jb (ib|ja) X_mjb = sum_P sum_j E^P_mij t^P_ja,  E^P_mij = sum_b t^P_ib X_mjb,
+// t^P = L_K^-1 (P|ia) on the window (Sec. 3.2: the T_ia^P' tensor of full TDDFT);
+// i, j, a, b inside the exchange window and K' zero outside it.  FP64.
+void matvec_b(tr_ctx *c, int m, const double *X, double *BX)
+{
+    TR_REQUIRE(c->built && c->opt.tddft, TR_EINVAL, "matvec_b: needs a context built with tddft = 1");
+    if (m <= 0) return;
+    cudaStream_t st = c->st;
+    Prof &pf = c->prof;
+    const int nocc = c->nocc, nvir = c->nvir, nJ = c->nJ, nK = c->nK;
+    const long long nov = c->nov;
+    const int mb = std::min(m, c->mblk);
+    reserve_matvec(c, mb);
+    const int oK = c->oK, vK = c->vK, o0 = c->o0;
+    const int npk = matvec_pchunk(c, mb);
+    for (int m0 = 0; m0 < m; m0 += mb) {
+        const int mm = std::min(mb, m - m0);
+        const double *x = X + (long long)m0 * nov;
+        double *bx = BX + (long long)m0 * nov;
+        if (nJ && !c->opt.j_ao) {
+            // 2 J X with the stored (P|ia), as in A X
+            dgemm(pf, st, "J_contract", false, true, nJ, mm, (int)nov, 1.0, c->Y.p, nov, x, nov, 0.0,
+                  c->ws_Z.p, mm, Batch(), c->ws_split.p, c->ws_split.n);
+            dgemm(pf, st, "J_metric", false, false, nJ, mm, nJ, 1.0, c->GinvJ.p, nJ, c->ws_Z.p, mm, 0.0,
+                  c->ws_Z2.p, mm, Batch(), nullptr, 0);
+            dgemm(pf, st, "J_expand", true, false, mm, (int)nov, nJ, 2.0, c->ws_Z2.p, mm, c->Y.p, nov, 0.0,
+                  bx, nov, Batch(), nullptr, 0);
+        } else {
+            TR_CUDA(cudaMemsetAsync(bx, 0, sizeof(double) * (size_t)mm * nov, st));
+            if (nJ) j_ao_block(c, mm, x, bx);
+        }
+        if (!c->k_active) continue;
+        long long tot = (long long)mm * oK * vK;
+        TR_LAUNCH(pf, st, "gather_window", 0, 16.0 * tot,
+                  gather_window<<<grid_for(tot), 256, 0, st>>>(x, c->ws_Xw.p, mm, nocc, nvir, o0, oK, vK));
+        for (int P0 = 0; P0 < nK; P0 += npk) {
+            const int np = std::min(npk, nK - P0);
+            const double *tP = c->Tia.p + (long long)P0 * oK * vK;
+            // E[m][i][p][j] = sum_b t^(P0+p)_ib X_mjb
+            Batch e;
+            e.n1 = mm;
+            e.n2 = np;
+            e.sB1 = (long long)oK * vK;
+            e.sC1 = (long long)oK * np * oK;
+            e.sA2 = (long long)oK * vK;
+            e.sC2 = oK;
+            const double eb = 8.0 * ((double)np * oK * vK + (double)mm * oK * vK + (double)mm * np * oK * oK);
+            dgemm(pf, st, "Kx_stage1", false, true, oK, oK, vK, 1.0, tP, vK, c->ws_Xw.p, vK, 0.0, c->ws_M.p,
+                  (long long)np * oK, e, nullptr, 0, eb);
+            // BX_mia -= c_x sum_(p,j) E[m][i][(p,j)] t^(P0+p)_ja  (window rows/cols)
+            Batch f;
+            f.n1 = mm;
+            f.sA1 = (long long)oK * np * oK;
+            f.sC1 = nov;
+            const double fb = 8.0 * ((double)mm * np * oK * oK + (double)np * oK * vK + 2.0 * mm * oK * vK);
+            dgemm(pf, st, "Kx_stage2", false, false, oK, vK, np * oK, -c->opt.cx, c->ws_M.p, (long long)np * oK, tP,
+                  vK, 1.0, bx + (long long)o0 * nvir, nvir, f, nullptr, 0, fb);
+        }
+    }
+}
+
+// (A + B) X and (A - B) X from A X and B X (Sec. 2, Eq. hessian)
+void matvec_pm(tr_ctx *c, int m, const double *X, double *P, double *M)
+{
+    if (m <= 0) return;
+    matvec(c, m, X, P);
+    matvec_b(c, m, X, M);
+    const long long n = (long long)m * c->nov;
+    TR_LAUNCH(c->prof, c->st, "pm_combine", 0, 32.0 * n, pm_combine<<<grid_for(n), 256, 0, c->st>>>(P, M, n));
+}
 
 // ---------------------------------------------------------------- FP64 form on the tensor cores
 

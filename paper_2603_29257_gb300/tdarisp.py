@@ -34,7 +34,7 @@ class Options(ct.Structure):
                 ("screen", ct.c_double), ("hbm_budget", ct.c_size_t),
                 ("aux_chunk_bytes", ct.c_size_t), ("host_budget", ct.c_size_t),
                 ("dav_dev_rows", ct.c_int), ("matvec_ws_bytes", ct.c_size_t),
-                ("xform_slices", ct.c_int), ("j_ao", ct.c_int)]
+                ("xform_slices", ct.c_int), ("j_ao", ct.c_int), ("tddft", ct.c_int)]
 
 
 class Dims(ct.Structure):
@@ -92,6 +92,9 @@ SIGNATURES = {
     "tr_oscillator_strengths": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int]),
     "tr_matvec": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_int]),
     "tr_matvec_noalloc": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p]),
+    "tr_matvec_tddft": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int]),
+    "tr_solve_tddft": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int,
+                                  ct.POINTER(SolveInfo)]),
     "tr_solve": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int,
                             ct.POINTER(SolveInfo)]),
     "tr_build_batch": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.c_int, ct.c_int]),
@@ -294,7 +297,8 @@ class Context:
     def tensor(self, which) -> np.ndarray:
         d = self.dims()
         shapes = {0: (d.naux_j, d.nocc, d.nvir), 1: (d.naux_k, d.nocc_k, d.nocc_k),
-                  2: (d.naux_k, d.nvir_k, d.nvir_k), 3: (d.nocc, d.nvir)}
+                  2: (d.naux_k, d.nvir_k, d.nvir_k), 3: (d.nocc, d.nvir),
+                  4: (d.naux_k, d.nocc_k, d.nvir_k)}
         out = np.zeros(shapes[which])
         self._check(lib().tr_get_tensor(self._h, which, out.ctypes.data_as(ct.c_void_p), 0),
                     "tr_get_tensor")
@@ -318,6 +322,38 @@ class Context:
         rc = lib().tr_matvec(self._h, m, Xn.ctypes.data_as(ct.c_void_p), AX.ctypes.data_as(ct.c_void_p), 0)
         self._check(rc, "tr_matvec")
         return AX
+
+    def matvec_tddft(self, X):
+        """((A + B) X, (A - B) X) of full TDDFT-risp (Sec. 2, Eq. hessian; tddft = 1):
+        numpy in -> numpy out, CUDA tensor in -> CUDA tensors out (asynchronous)."""
+        if _is_torch(X) and X.is_cuda:
+            import torch
+            X = X.contiguous()
+            P, M = torch.empty_like(X), torch.empty_like(X)
+            rc = lib().tr_matvec_tddft(self._h, X.shape[0], ct.c_void_p(X.data_ptr()), ct.c_void_p(P.data_ptr()),
+                                       ct.c_void_p(M.data_ptr()), 1)
+            self._check(rc, "tr_matvec_tddft")
+            return P, M
+        Xn = _f64(X)
+        P, M = np.empty_like(Xn), np.empty_like(Xn)
+        rc = lib().tr_matvec_tddft(self._h, Xn.shape[0], Xn.ctypes.data_as(ct.c_void_p),
+                                   P.ctypes.data_as(ct.c_void_p), M.ctypes.data_as(ct.c_void_p), 0)
+        self._check(rc, "tr_matvec_tddft")
+        return P, M
+
+    def solve_tddft(self):
+        """Full TDDFT-risp Davidson (tddft = 1).  Returns (omega, X+Y, X-Y, resid, info)
+        as numpy arrays, (X+Y).(X-Y) = 1 per state."""
+        d = self.dims()
+        n = min(self._opts.nstates, d.nocc * d.nvir)
+        info = SolveInfo()
+        om, rs = np.zeros(n), np.zeros(n)
+        P, M = np.zeros((n, d.nocc, d.nvir)), np.zeros((n, d.nocc, d.nvir))
+        rc = lib().tr_solve_tddft(self._h, om.ctypes.data_as(ct.c_void_p), P.ctypes.data_as(ct.c_void_p),
+                                  M.ctypes.data_as(ct.c_void_p), rs.ctypes.data_as(ct.c_void_p), 0, ct.byref(info))
+        if rc not in (TR_OK, TR_ENOCONV):
+            self._check(rc, "tr_solve_tddft")
+        return om, P, M, rs, info
 
     def matvec_noalloc(self, X, out):
         """A X into out (CUDA tensors) without any device allocation (static scratch)."""

@@ -542,7 +542,8 @@ def run_matvec(args):
 
 def run_tddft(args):
     """Full TDDFT-risp (tddft = 1, Sec. 2, Eqs. tddft and hessian) on the same
-    molecule and options: tr_build (with T_ia^P' on the window), W untimed and
+    molecule and options, in the form --precision (0 FP64 pipe, 2 FP64 on the
+    tensor cores): tr_build (with T_ia^P' on the window), W untimed and
     K timed (A + B, A - B) products of one block of `--block` resident seeded
     vectors, then one Davidson solve to 15 states, and the TDA solve of the same
     context options for comparison.  value = vectors x K / event time of the
@@ -559,7 +560,7 @@ def run_tddft(args):
     eps_dev = torch.from_numpy(mol.eps).cuda()
 
     def context(tddft):
-        c = tdarisp.Context(stream=stream.cuda_stream, **dict(OPTS, tddft=tddft))
+        c = tdarisp.Context(stream=stream.cuda_stream, **dict(OPTS, tddft=tddft, precision=args.precision))
         c.set_molecule(mol.Z, mol.xyz, mol.aux_exp, mol.shells)
         c.set_orbitals(C_dev, eps_dev, mol.nocc)
         return c
@@ -605,9 +606,11 @@ def run_tddft(args):
     line = {"metric": "full TDDFT-risp (A+B, A-B) products/s (block products alone)",
             "value": args.block * args.steps / (ms * 1e-3), "unit": "vectors/s", "n_gpus": 1,
             "steps": args.steps, "warmup": max(args.warmup, 1), "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {0: "f64", 2: "f64 (7-slice bf16 tensor-core products)"}[args.precision], "data": "synthetic",
             "config": {"workload": (WORKLOAD if args.case == "full" else "100-atom molecule, same options")
                        .replace("TDA-risp", "full TDDFT-risp") + "; one block of %d seeded vectors" % args.block,
+                       "precision": args.precision,
                        "nao": d.nao, "nocc": d.nocc, "nvir": d.nvir, "naux_k": d.naux_k, "nocc_k": d.nocc_k,
                        "nvir_k": d.nvir_k, "block": args.block,
                        "l2": "X and products %.0f MB each" % (8e-6 * args.block * d.nocc * d.nvir)},

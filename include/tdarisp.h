@@ -114,7 +114,8 @@ typedef struct {
                             which (A+B + A-B)/2 is the A above).  tr_build then also forms
                             T_ia^P' on the exchange window (Sec. 3.2, the tensor only full
                             TDDFT needs), and tr_solve solves (A-B)(A+B)|X+Y> = Omega^2|X+Y>.
-                            FP64 form only: needs precision TR_FP64 and xform_slices <= 0;
+                            FP64 results: needs precision TR_FP64 or TR_FP64_TC (then the
+                            (ib|ja) products run as 7-slice tensor-core products too);
                             not available in tr_solve_batch or the server (TR_EINVAL);
                             tr_matvec and tr_matvec_noalloc still give A X */
 } tr_options;

@@ -83,8 +83,8 @@ int tr_create(tr_ctx **out, const tr_options *opt, void *cuda_stream)
                    TR_EINVAL, "create: xform_slices must be -1, 0 or 2..7");
         TR_REQUIRE(opt->j_ao == 0 || opt->j_ao == 1, TR_EINVAL, "create: j_ao must be 0 or 1");
         TR_REQUIRE(opt->tddft == 0 || opt->tddft == 1, TR_EINVAL, "create: tddft must be 0 or 1");
-        TR_REQUIRE(!opt->tddft || (opt->precision == TR_FP64 && opt->xform_slices <= 0), TR_EINVAL,
-                   "create: full TDDFT (tddft = 1) needs precision TR_FP64 and xform_slices <= 0");
+        TR_REQUIRE(!opt->tddft || opt->precision != TR_MIXED, TR_EINVAL,
+                   "create: full TDDFT (tddft = 1) needs precision TR_FP64 or TR_FP64_TC");
         c->opt = *opt;
         normalise_options(&c->opt);
         c->st = (cudaStream_t)cuda_stream;
@@ -117,8 +117,8 @@ int tr_set_options(tr_ctx *ctx, const tr_options *opt)
                    TR_EINVAL, "set_options: xform_slices must be -1, 0 or 2..7");
         TR_REQUIRE(opt->j_ao == 0 || opt->j_ao == 1, TR_EINVAL, "set_options: j_ao must be 0 or 1");
         TR_REQUIRE(opt->tddft == 0 || opt->tddft == 1, TR_EINVAL, "set_options: tddft must be 0 or 1");
-        TR_REQUIRE(!opt->tddft || (opt->precision == TR_FP64 && opt->xform_slices <= 0), TR_EINVAL,
-                   "set_options: full TDDFT (tddft = 1) needs precision TR_FP64 and xform_slices <= 0");
+        TR_REQUIRE(!opt->tddft || opt->precision != TR_MIXED, TR_EINVAL,
+                   "set_options: full TDDFT (tddft = 1) needs precision TR_FP64 or TR_FP64_TC");
         bool rebuild = opt->precision != ctx->opt.precision || opt->cx != ctx->opt.cx || opt->k_alpha != ctx->opt.k_alpha ||
                        opt->k_beta != ctx->opt.k_beta || opt->omega != ctx->opt.omega ||
                        opt->window_ev != ctx->opt.window_ev || opt->aux_on_h != ctx->opt.aux_on_h ||

@@ -74,6 +74,8 @@ struct tr_ctx {
     // per-block sliced operands
     tr::DevBuf<double> ozs_Y, ozs_YT, ozs_Tab, ozs_T2, ozw_X, ozw_Xw, ozw_Z, ozw_M, ws_Mf;
     tr::OzMat oz_Y, oz_YT, oz_Tab, oz_T2;
+    tr::DevBuf<double> ozs_Tia, ozs_TiaT;  // full TDDFT: T_ia by rows (P, i) and by rows a
+    tr::OzMat oz_Tia, oz_TiaT;
     int tc_npk = 0;
 
     // workspaces
@@ -142,6 +144,7 @@ size_t footprint(tr_ctx *c);
 void build_tc(tr_ctx *c);
 void reserve_tc(tr_ctx *c, int mb);
 void matvec_tc(tr_ctx *c, int m, const double *X, double *AX);
+void matvec_b_tc(tr_ctx *c, int m, const double *X, double *BX);
 // three-centre integrals of aux functions [p0, p0+np) of set which (0 = J, 1 = K)
 void compute_int3c_chunk(tr_ctx *c, int which, int p0, int np, double *out);
 // Coulomb term on the fly in the AO basis (jao.cu): AX += 2 J for mm vectors;

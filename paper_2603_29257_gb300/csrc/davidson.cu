@@ -457,7 +457,8 @@ struct Dav {
         TR_REQUIRE(c->opt.nstates >= 1, TR_EINVAL, "solve: nstates must be >= 1");
         TR_REQUIRE(c->opt.nstates <= 64, TR_EINVAL, "solve: nstates must be <= 64");
         rpa = c->opt.tddft != 0;
-        TR_REQUIRE(!rpa || c->opt.precision == TR_FP64, TR_EINVAL, "solve: full TDDFT runs in the FP64 form only");
+        TR_REQUIRE(!rpa || c->opt.precision != TR_MIXED, TR_EINVAL,
+                   "solve: full TDDFT needs precision TR_FP64 or TR_FP64_TC");
         nov = c->nov;
         rowb = (size_t)nov * sizeof(double);
         n = (int)std::min<long long>(c->opt.nstates, nov);

@@ -435,7 +435,7 @@ int xform_slices(const tr_ctx *c)
 // The same MO transforms on the bf16 tensor cores (Ozaki scheme with S slices):
 // the MO coefficients are sliced once (rows = orbitals, K = AO index), each AO
 // integral chunk and each half-transformed chunk before its product.
-static void transforms_oz(tr_ctx *c, DevBuf<double> &Iij, int S)
+static void transforms_oz(tr_ctx *c, DevBuf<double> &Iij, DevBuf<double> *Iia, int S)
 {
     const int nao = c->nao, nocc = c->nocc, nvir = c->nvir, nmo = c->nmo, nJ = c->nJ, nK = c->nK;
     const long long nov = c->nov;
@@ -489,6 +489,9 @@ static void transforms_oz(tr_ctx *c, DevBuf<double> &Iij, int S)
             pair_transform(np, o0, oK, o0, oK, Iij.p + (long long)p0 * oK * oK, oK, "xform_K1_oz", "xform_K2_oz");
             pair_transform(np, nocc, vK, nocc, vK, c->Tab.p + (long long)p0 * vK * vK, vK, "xform_K1_oz",
                            "xform_K2_oz");
+            if (Iia)
+                pair_transform(np, o0, oK, nocc, vK, Iia->p + (long long)p0 * oK * vK, vK, "xform_K1_oz",
+                               "xform_Kx_oz");
         }
     }
     int h = 0;
@@ -540,8 +543,7 @@ void build(tr_ctx *c)
         const bool kx = tddft && c->k_active;
         if (kx) Iia.alloc((size_t)nK * oK * vK, &c->budget, "(ia|P) on the window");
         const int S = xform_slices(c);
-        TR_REQUIRE(S == 0 || !tddft, TR_EINVAL, "build: full TDDFT needs the FP64 MO transforms");
-        if (S > 0) transforms_oz(c, Iij, S);
+        if (S > 0) transforms_oz(c, Iij, kx ? &Iia : nullptr, S);
         else transforms_fp64(c, Iij, kx ? &Iia : nullptr);
         if (kx) {
             // t^P_ia = sum_Q (L^-1)_PQ (Q|ia): sum_P t^P_ib t^P_ja = (ib|ja) with (P|Q)^-1 = L^-T L^-1
@@ -710,6 +712,10 @@ size_t footprint(tr_ctx *c)
                                  2.0 * (double)oz_bytes((long long)std::max<double>(n, pmax), maxsp, OZ_SLICES_FP64)
                            : 0.0;
     const double jao = c->opt.j_ao ? (double)jao_bytes(c, (int)mb) : 0.0;
+    // full TDDFT on the tensor cores: T_ia sliced by rows (P, i) and by rows a
+    if (rpa && c->opt.precision == TR_FP64_TC && nK > 0)
+        tcx += (double)oz_bytes((long long)(nK * oK), (int)vK, OZ_SLICES_FP64) +
+               (double)oz_bytes((long long)vK, (int)(nK * oK), OZ_SLICES_FP64);
     const double solve_peak = kept + dav + ws + tcx + dtc + jao;
     return (size_t)(1.1 * (base + std::max(build_peak, solve_peak + (mixed ? 0.0 : 0.0))));
 }
@@ -833,6 +839,10 @@ void matvec_b(tr_ctx *c, int m, const double *X, double *BX)
 {
     TR_REQUIRE(c->built && c->opt.tddft, TR_EINVAL, "matvec_b: needs a context built with tddft = 1");
     if (m <= 0) return;
+    if (c->opt.precision == TR_FP64_TC) {
+        matvec_b_tc(c, m, X, BX);
+        return;
+    }
     cudaStream_t st = c->st;
     Prof &pf = c->prof;
     const int nocc = c->nocc, nvir = c->nvir, nJ = c->nJ, nK = c->nK;
@@ -924,6 +934,15 @@ void build_tc(tr_ctx *c)
         c->ozs_T2.alloc(cdiv(oz_bytes(oK, nK * oK, S), 8), &c->budget, "sliced T_ij");
         oz_bind(c->oz_T2, c->ozs_T2.p, oK, nK * oK, S);
         oz_split(pf, st, "oz_split_T2", c->T2.p, (long long)nK * oK, 1, c->oz_T2);
+        if (c->opt.tddft) {
+            // full TDDFT: t^P_ia by rows (P, i) with K = a, and by rows a with K = (P, i)
+            c->ozs_Tia.alloc(cdiv(oz_bytes((long long)nK * oK, vK, S), 8), &c->budget, "sliced T_ia");
+            oz_bind(c->oz_Tia, c->ozs_Tia.p, (long long)nK * oK, vK, S);
+            oz_split(pf, st, "oz_split_Tia", c->Tia.p, vK, 1, c->oz_Tia);
+            c->ozs_TiaT.alloc(cdiv(oz_bytes(vK, nK * oK, S), 8), &c->budget, "sliced T_ia by a");
+            oz_bind(c->oz_TiaT, c->ozs_TiaT.p, vK, nK * oK, S);
+            oz_split(pf, st, "oz_split_TiaT", c->Tia.p, 1, vK, c->oz_TiaT);
+        }
     }
     TR_CUDA(cudaStreamSynchronize(st));
 }
@@ -953,8 +972,10 @@ void reserve_tc(tr_ctx *c, int mb)
         c->tc_npk = npk;
         c->ws_Xw.reserve((size_t)mb * c->oK * c->vK, &c->budget, "K workspace");
         c->ozw_Xw.reserve(cdiv(oz_bytes((long long)mb * c->oK, c->vK, S), 8), &c->budget, "sliced window");
-        c->ws_Mf.reserve((size_t)mb * c->vK * npk * c->oK, &c->budget, "K intermediate");
-        c->ozw_M.reserve(cdiv(oz_bytes((long long)mb * c->vK, npk * c->oK, S), 8), &c->budget,
+        // full TDDFT: the (ib|ja) intermediate E [m][i][(P, j)] has oK rows per vector in place of vK
+        const long long w = c->opt.tddft ? std::max(c->oK, c->vK) : c->vK;
+        c->ws_Mf.reserve((size_t)mb * w * npk * c->oK, &c->budget, "K intermediate");
+        c->ozw_M.reserve(cdiv(oz_bytes((long long)mb * w, npk * c->oK, S), 8), &c->budget,
                          "sliced K intermediate");
     }
 }
@@ -1041,6 +1062,88 @@ void matvec_tc(tr_ctx *c, int m, const double *X, double *AX)
                 oz_gemm(pf, st, "K_stage2_tc", c->oz_T2, 0, 0, 0, (int)((long long)P0 * oK / 32), Ms, 0, vK, 0, 0, oK,
                         vK, Ms.nkb, mm, 1, o2, err);
             }
+        }
+    }
+}
+
+// B X of full TDDFT with every large product on the tensor cores (7 slices): the
+// steps and order of matvec_b
+void matvec_b_tc(tr_ctx *c, int m, const double *X, double *BX)
+{
+    const int S = OZ_SLICES_FP64;
+    cudaStream_t st = c->st;
+    Prof &pf = c->prof;
+    const int nocc = c->nocc, nvir = c->nvir, nJ = c->nJ;
+    const long long nov = c->nov;
+    const int mb = std::min(m, c->mblk);
+    reserve_matvec(c, mb);
+    const int oK = c->oK, vK = c->vK, o0 = c->o0, nK = c->nK;
+    int *err = c->flag.p + 1;
+    for (int m0 = 0; m0 < m; m0 += mb) {
+        const int mm = std::min(mb, m - m0);
+        const double *x = X + (long long)m0 * nov;
+        double *bx = BX + (long long)m0 * nov;
+        TR_CUDA(cudaMemsetAsync(bx, 0, sizeof(double) * (size_t)mm * nov, st));
+        if (nJ && c->opt.j_ao) {
+            j_ao_block(c, mm, x, bx);
+        } else if (nJ) {
+            OzMat Xs, Zs;
+            oz_bind(Xs, c->ozw_X.p, mm, (int)nov, S);
+            oz_split(pf, st, "oz_split_X", x, nov, 1, Xs);
+            OzOut oz;
+            oz.d = c->ws_Z.p;
+            oz.ldm = mm;
+            oz.ldn = 1;
+            const int tiles = cdiv(nJ, 128) * cdiv(mm, 64);
+            int ks = std::max(1, 2 * 152 / tiles);
+            ks = (int)std::min<long long>(ks, (long long)c->ws_split.n / ((long long)nJ * mm));
+            oz_gemm(pf, st, "J_contract_tc", c->oz_Y, 0, 0, 0, 0, Xs, 0, 0, 0, 0, nJ, mm, c->oz_Y.nkb, 1, 1, oz, err,
+                    std::max(ks, 1), c->ws_split.p, c->ws_split.n);
+            dgemm(pf, st, "J_metric", false, false, nJ, mm, nJ, 1.0, c->GinvJ.p, nJ, c->ws_Z.p, mm, 0.0, c->ws_Z2.p, mm,
+                  Batch(), nullptr, 0);
+            oz_bind(Zs, c->ozw_Z.p, mm, nJ, S);
+            oz_split(pf, st, "oz_split_Z", c->ws_Z2.p, 1, mm, Zs);
+            OzOut oe;
+            oe.d = bx;
+            oe.ldm = 1;
+            oe.ldn = nov;
+            oe.alpha = 2.0;
+            oe.accumulate = true;
+            oz_gemm(pf, st, "J_expand_tc", c->oz_YT, 0, 0, 0, 0, Zs, 0, 0, 0, 0, (int)nov, mm, c->oz_YT.nkb, 1, 1, oe,
+                    err);
+        }
+        if (!c->k_active) continue;
+        const long long tot = (long long)mm * oK * vK;
+        TR_LAUNCH(pf, st, "gather_window", 0, 16.0 * tot,
+                  gather_window<<<grid_for(tot), 256, 0, st>>>(x, c->ws_Xw.p, mm, nocc, nvir, o0, oK, vK));
+        OzMat Xws, Es;
+        oz_bind(Xws, c->ozw_Xw.p, (long long)mm * oK, vK, S);
+        oz_split(pf, st, "oz_split_Xw", c->ws_Xw.p, vK, 1, Xws);
+        const int npk = c->tc_npk;
+        for (int P0 = 0; P0 < nK; P0 += npk) {
+            const int np = std::min(npk, nK - P0);
+            const long long Kp = (long long)np * oK;
+            // E[m][i][P oK + j] = sum_b t^P_ib X_m,jb   (batches P, m)
+            OzOut o1;
+            o1.d = c->ws_Mf.p;
+            o1.s1 = oK;
+            o1.s2 = (long long)oK * Kp;
+            o1.ldm = Kp;
+            o1.ldn = 1;
+            oz_gemm(pf, st, "Kx_stage1_tc", c->oz_Tia, (long long)P0 * oK, oK, 0, 0, Xws, 0, 0, oK, 0, oK, oK,
+                    c->oz_Tia.nkb, np, mm, o1, err);
+            oz_bind(Es, c->ozw_M.p, (long long)mm * oK, (int)Kp, S);
+            oz_split(pf, st, "oz_split_E", c->ws_Mf.p, Kp, 1, Es);
+            // BX_m[o0 + i][a] -= cx sum_(P,j) E[m][i][P oK + j] t^P_ja
+            OzOut o2;
+            o2.d = bx + (long long)o0 * nvir;
+            o2.s1 = nov;
+            o2.ldm = nvir;
+            o2.ldn = 1;
+            o2.alpha = -c->opt.cx;
+            o2.accumulate = true;
+            oz_gemm(pf, st, "Kx_stage2_tc", Es, 0, oK, 0, 0, c->oz_TiaT, 0, 0, 0, (int)((long long)P0 * oK / 32), oK,
+                    vK, Es.nkb, mm, 1, o2, err);
         }
     }
 }

@@ -82,6 +82,29 @@ def test_products_against_oracle(mol, refs, which, m, j_ao):
     assert _rel(c.matvec(X), tda.matvec(f, X)) < 1e-12
 
 
+@pytest.mark.parametrize("which", ["rsh", "rsh_cut"])
+@pytest.mark.parametrize("j_ao", [0, 1])
+def test_tensor_core_products_against_oracle(mol, refs, which, j_ao):
+    """precision = TR_FP64_TC: the (ib|ja) stages as 7-slice tensor-core products
+    (and the MO transforms, J and the TDA stages as in that form)."""
+    win = 25.0 if which == "rsh_cut" else 40.0
+    c = _ctx(mol, tddft=1, precision=2, j_ao=j_ao, window_ev=win, **RSH)
+    c.build()
+    X = synth.random_trial_block(700, 37, mol.nocc, mol.nvir)
+    P, M = c.matvec_tddft(X)
+    Pr, Mr = tda.matvec_pm(refs[which], X)
+    assert _rel(P, Pr) < 1e-12
+    assert _rel(M, Mr) < 1e-12
+
+
+def test_tensor_core_solve_matches_dense_solve(mol, refs):
+    c = _ctx(mol, tddft=1, precision=2, nstates=5, tol=1e-8, **RSH)
+    c.build()
+    om, XpY, XmY, rs, info = c.solve_tddft()
+    assert info.converged
+    _check_solution(refs["rsh"], om, XpY, XmY, rs, 1e-8)
+
+
 def test_device_products_equal_host_products(mol):
     c = _ctx(mol, tddft=1, **RSH)
     c.build()
@@ -146,8 +169,6 @@ def test_invalid_uses_are_rejected(mol):
     tdarisp = _lib()
     with pytest.raises(tdarisp.TDARispError):
         tdarisp.Context(tddft=1, precision=1)
-    with pytest.raises(tdarisp.TDARispError):
-        tdarisp.Context(tddft=1, xform_slices=5)
     c = _ctx(mol, **RSH)
     c.build()
     X = synth.random_trial_block(1, 2, mol.nocc, mol.nvir)
@@ -165,18 +186,26 @@ def test_invalid_uses_are_rejected(mol):
 
 def test_operator_properties_at_200_atoms():
     """The 200-atom RSH case (nov 577,600, window 380 x 567, 100 K auxiliary
-    functions): (A + B) and (A - B) are symmetric on a random block, and their
-    half sum is the TDA product of the same context."""
+    functions), FP64 pipe and tensor-core forms: (A + B) and (A - B) are symmetric
+    on a random block, their half sum is the TDA product of the same context, and
+    the two forms agree."""
     mol = synth.molecule_200()
-    c = _ctx(mol, tddft=1, **RSH)
-    c.build()
-    d = c.dims()
-    X = torch.from_numpy(synth.random_trial_block(11, 4, d.nocc, d.nvir)).cuda()
-    P, M = c.matvec_tddft(X)
-    A = c.matvec(X)
-    torch.cuda.synchronize()
-    x, p, m, a = (t.reshape(4, -1) for t in (X, P, M, A))
-    assert (0.5 * (p + m) - a).abs().max().item() < 1e-12 * a.abs().max().item()
-    for S in (p, m, p - m):
-        G = x @ S.T          # G[i][j] = x_i . (S x_j)
-        assert (G - G.T).abs().max().item() < 1e-11 * G.abs().max().item()
+    out = []
+    for precision in (0, 2):
+        c = _ctx(mol, tddft=1, precision=precision, **RSH)
+        c.build()
+        d = c.dims()
+        X = torch.from_numpy(synth.random_trial_block(11, 4, d.nocc, d.nvir)).cuda()
+        P, M = c.matvec_tddft(X)
+        A = c.matvec(X)
+        torch.cuda.synchronize()
+        x, p, m, a = (t.reshape(4, -1) for t in (X, P, M, A))
+        assert (0.5 * (p + m) - a).abs().max().item() < 1e-12 * a.abs().max().item()
+        for S in (p, m, p - m):
+            G = x @ S.T          # G[i][j] = x_i . (S x_j)
+            assert (G - G.T).abs().max().item() < 1e-11 * G.abs().max().item()
+        out.append((p.cpu(), m.cpu()))
+        del c
+    # the tensor-core form agrees with the FP64 pipe at this size
+    for u, v in zip(out[0], out[1]):
+        assert (u - v).abs().max().item() < 1e-12 * u.abs().max().item()

@@ -7,7 +7,12 @@ Eq. TDA-risp; RI through the minimal aux basis, Sec. 2 Eq. RI and Sec. 3.2), for
 global hybrid (c_x = 0.25, 40 eV window) and a range-separated case
 ((0.222 + 0.778 erf(0.2 r))/r, c_x = 1).
 
-Run: python tests/golden/make_golden.py
+omega_tddft_24atom.json: the 5 lowest full TDDFT-risp excitation energies of the
+same molecule and cases (Sec. 2, Eqs. tddft and hessian, with A + B = D + 4 (ia|jb)
+- c_x [(ib|ja) + (ij|ab)] and A - B = D + c_x [(ib|ja) - (ij|ab)]) by the dense
+symmetric-form solve of the oracle.
+
+Run: python tests/golden/make_golden.py [tda|tddft]   (default: tda)
 """
 from __future__ import annotations
 
@@ -46,5 +51,23 @@ def main():
         json.dump(out, fh, indent=1)
 
 
+def main_tddft():
+    mol = synth.molecule_24()
+    out = {"source": "oracle dense symmetric-form solve of full TDDFT-risp (Sec. 2, Eqs. tddft and hessian)",
+           "molecule": "synth.molecule_24(): seed 1, 10 heavy + 14 H, nao 210, nocc 42",
+           "window_ev": 40.0, "nstates": 5, "cases": {}}
+    for name, op in CASES.items():
+        f = tda.build(mol.Z, mol.xyz, mol.shells, mol.aux_exp, mol.C, mol.eps, mol.nocc, op["cx"],
+                      op["ka"], op["kb"], op["omega"], window_ev=40.0, tddft=True)
+        w, _, _ = tda.tddft_dense(f, 5)
+        out["cases"][name] = {"options": op, "omega": [float(x) for x in w]}
+        print(name, w)
+    with open(os.path.join(HERE, "omega_tddft_24atom.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+
+
 if __name__ == "__main__":
-    main()
+    if len(sys.argv) > 1 and sys.argv[1] == "tddft":
+        main_tddft()
+    else:
+        main()

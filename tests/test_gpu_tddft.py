@@ -4,6 +4,9 @@ products and the symplectic Davidson, element by element against the oracle,
 plus properties at the 200-atom size where the oracle cannot follow."""
 from __future__ import annotations
 
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -13,6 +16,7 @@ from paper_2603_29257_gb300 import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+HERE = os.path.dirname(os.path.abspath(__file__))
 HYB = dict(cx=0.25, k_alpha=1.0, k_beta=0.0, omega=0.0)
 RSH = dict(cx=1.0, k_alpha=0.222, k_beta=0.778, omega=0.2)
 
@@ -152,6 +156,21 @@ def test_solve_with_restarts_and_spilled_rows(mol, refs):
     om, XpY, XmY, rs, info = c.solve_tddft()
     assert info.converged and info.nrestart >= 1 and info.dev_rows == 10 and info.host_bytes_moved > 0
     _check_solution(refs["rsh"], om, XpY, XmY, rs, 1e-8)
+
+
+@pytest.mark.parametrize("case", ["hybrid", "rsh"])
+@pytest.mark.parametrize("precision", [0, 2])
+def test_24atom_against_golden(case, precision):
+    """24-atom molecule (nov 7056): the five lowest roots against the oracle's dense
+    solve stored by tests/golden/make_golden.py."""
+    gold = json.load(open(os.path.join(HERE, "golden", "omega_tddft_24atom.json")))
+    ref = np.array(gold["cases"][case]["omega"])
+    op = HYB if case == "hybrid" else RSH
+    c = _ctx(synth.molecule_24(), tddft=1, precision=precision, nstates=5, tol=1e-6, **op)
+    c.build()
+    om, XpY, XmY, rs, info = c.solve_tddft()
+    err = np.abs(om - ref)
+    assert info.converged and np.all(err < 1e-8), err
 
 
 def test_oscillator_strengths_of_full_tddft_states(mol, refs):

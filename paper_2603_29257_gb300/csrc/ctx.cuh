@@ -96,6 +96,10 @@ struct tr_ctx {
     tr::DevBuf<double> dvs_V, dvs_W, dvs_T, dvs_Vt, dvs_Wt, dvs_Y, dvs_C;
     tr::OzMat dz_V, dz_W, dz_Vt, dz_Wt;  // dz_Vt, dz_Wt: V and W by columns (rows = nov, K = subspace index)
     tr::DevBuf<int> dz_eW;               // the one exponent of dz_Wt
+    // full TDDFT: the (A - B) V rows sliced by rows and by columns, and the exponent of the latter
+    tr::DevBuf<double> dvs_Wm, dvs_Wmt;
+    tr::OzMat dz_Wm, dz_Wmt;
+    tr::DevBuf<int> dz_eWm;
     tr::DevBuf<int> idx_dev;
     // spill of V/W rows to pinned host memory: staging slots, copy stream, events
     tr::DevBuf<double> stage;

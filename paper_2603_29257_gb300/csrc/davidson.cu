@@ -550,11 +550,12 @@ struct Dav {
         }
         ws = c->ws_split.p;
         wsn = c->ws_split.n;
-        if ((c->opt.precision == TR_MIXED || c->opt.precision == TR_FP64_TC) && kd == maxsp && !rpa) {
+        if ((c->opt.precision == TR_MIXED || c->opt.precision == TR_FP64_TC) && kd == maxsp) {
             const size_t sv = oz_bytes(maxsp, (int)nov, OZ_SLICES_FP64), stn = oz_bytes(pmax, (int)nov, OZ_SLICES_FP64);
             const size_t svt = oz_bytes(nov, maxsp, OZ_SLICES_FP64);
             const size_t ssm = oz_bytes(std::max(n, pmax), maxsp, OZ_SLICES_FP64);
-            if (c->budget.used + 2 * sv + 2 * svt + stn + 2 * ssm + (64u << 20) <= c->budget.limit) {
+            const size_t nsl = rpa ? 3 : 2;  // sliced row stores: V, W (and Wm), each by rows and by columns
+            if (c->budget.used + nsl * sv + nsl * svt + stn + 2 * ssm + (64u << 20) <= c->budget.limit) {
                 c->dvs_V.alloc(cdiv(sv, 8), &c->budget, "sliced Davidson V");
                 c->dvs_W.alloc(cdiv(sv, 8), &c->budget, "sliced Davidson W");
                 c->dvs_T.alloc(cdiv(stn, 8), &c->budget, "sliced new directions");
@@ -574,6 +575,15 @@ struct Dav {
                 TR_CUDA(cudaMemsetAsync(c->dvs_T.p, 0, c->dvs_T.n * sizeof(double), st));
                 oz_bind(c->dz_V, c->dvs_V.p, maxsp, (int)nov, OZ_SLICES_FP64);
                 oz_bind(c->dz_W, c->dvs_W.p, maxsp, (int)nov, OZ_SLICES_FP64);
+                if (rpa) {
+                    c->dvs_Wm.alloc(cdiv(sv, 8), &c->budget, "sliced Davidson (A - B) V");
+                    c->dvs_Wmt.alloc(cdiv(svt, 8), &c->budget, "sliced Davidson (A - B) V by columns");
+                    c->dz_eWm.alloc(1, &c->budget, "exponent");
+                    TR_CUDA(cudaMemsetAsync(c->dvs_Wm.p, 0, c->dvs_Wm.n * sizeof(double), st));
+                    TR_CUDA(cudaMemsetAsync(c->dvs_Wmt.p, 0, c->dvs_Wmt.n * sizeof(double), st));
+                    oz_bind(c->dz_Wm, c->dvs_Wm.p, maxsp, (int)nov, OZ_SLICES_FP64);
+                    oz_bind(c->dz_Wmt, c->dvs_Wmt.p, nov, maxsp, OZ_SLICES_FP64);
+                }
                 tcd = true;
             }
         }
@@ -673,6 +683,26 @@ struct Dav {
             return;
         }
         h_update_rows(k0, p, Vn, Wn, SW, c->Hs.p);
+    }
+    // full TDDFT: rows/cols k0..k0+p of M- = V^T (A - B) V for the new vectors Vn
+    // (products Wnm); h_update has already sliced Vn
+    void h_update_minus(int k0, int p, const double *Vn, const double *Wnm)
+    {
+        if (!tcd) {
+            h_update_rows(k0, p, Vn, Wnm, SWm, c->Hsm.p);
+            return;
+        }
+        Prof &pf = c->prof;
+        const int kk = k0 + p;
+        double *A1 = c->Cs.p, *A2 = c->Cs.p + (size_t)maxsp * pmax;
+        oz_split_rows(pf, st, "oz_split_Wm", Wnm, nov, 1, c->dz_Wm, k0, p);
+        oz_col_exponent_update(st, c->dz_Wm.e + k0, p, k0 == 0, 8, c->dz_Wmt, c->dz_eWm.p, c->flag.p + 1,
+                               TC_ERR_W_RANGE);
+        oz_split_cols_fixed(pf, st, "oz_split_Wmt", Wnm, nov, c->dz_Wmt, k0, p);
+        tc_reduce("subspace_H_tc", c->dz_Wm, 0, c->dz_V, k0, kk, p, A1, 1, kk);  // A1[i][r] = Vn_i . Wm_r
+        tc_reduce("subspace_H_tc", c->dz_V, 0, c->dz_Wm, k0, kk, p, A2, 1, kk);  // A2[i][r] = Wmn_i . V_r
+        TR_LAUNCH(pf, st, "subspace_insert", 0, 0,
+                  h_insert<<<dim3(cdiv(kk, 128), p), 128, 0, st>>>(c->Hsm.p, maxsp, A1, A2, p, kk, k0));
     }
     // rows/cols k0..k0+p of the subspace matrix H (ld maxsp) of the products in S, FP64
     void h_update_rows(int k0, int p, const double *Vn, const double *Wn, RowStore &S, double *H)
@@ -780,7 +810,7 @@ struct Dav {
             }
         }
         h_update(pend_k0, pend_p, c->Tn.p, c->Wn.p);
-        if (rpa) h_update_rows(pend_k0, pend_p, c->Tn.p, c->Wnm.p, SWm, c->Hsm.p);
+        if (rpa) h_update_minus(pend_k0, pend_p, c->Tn.p, c->Wnm.p);
         store_rows(SV, pend_k0, pend_p, c->Tn.p);
         store_rows(SW, pend_k0, pend_p, c->Wn.p);
         if (rpa) store_rows(SWm, pend_k0, pend_p, c->Wnm.p);
@@ -864,6 +894,22 @@ struct Dav {
         TR_LAUNCH(pf, st, "rpa_coef", 0, 0, rpa_coef<<<n, 128, 0, st>>>(c->theta.p, Cab, k, n, rflag));
         TR_CUDA(cudaEventRecord(ev.e[1], st));
         // [X+Y; X-Y] = [a b]^T V in one pass over V; R1 = a^T W, R2 = b^T Wm
+        if (tcd) {
+            // Cs rows i < 2n with K = r: element (i, r) = Cab[r][i]
+            OzMat Ys;
+            oz_bind(Ys, c->dvs_Y.p, n2, k, OZ_SLICES_FP64);
+            oz_split(pf, st, "oz_split_Yev", Cab, 1, n2, Ys);
+            OzOut o;
+            o.d = c->Xr.p;
+            o.ldm = 1;
+            o.ldn = nov;
+            oz_gemm(pf, st, "ritz_tc", c->dz_Vt, 0, 0, 0, 0, Ys, 0, 0, 0, 0, (int)nov, n2, Ys.nkb, 1, 1, o, c->flag.p + 1);
+            o.d = c->R.p;
+            oz_gemm(pf, st, "ritz_tc", c->dz_Wt, 0, 0, 0, 0, Ys, 0, 0, 0, 0, (int)nov, n, Ys.nkb, 1, 1, o, c->flag.p + 1);
+            o.d = c->R.p + (long long)n * nov;
+            oz_gemm(pf, st, "ritz_tc", c->dz_Wmt, 0, 0, 0, 0, Ys, n, 0, 0, 0, (int)nov, n, Ys.nkb, 1, 1, o,
+                    c->flag.p + 1);
+        } else {
         for_rows(SV, 0, k, [&](const double *rows, int r0, int nr) {
             dgemm(pf, st, "ritz", true, false, n2, (int)nov, nr, 1.0, Cab + (long long)r0 * n2, n2, rows, nov,
                   r0 == 0 ? 0.0 : 1.0, c->Xr.p, nov, Batch(), nullptr, 0);
@@ -876,6 +922,7 @@ struct Dav {
             dgemm(pf, st, "ritz", true, false, n, (int)nov, nr, 1.0, Cab + (long long)r0 * n2 + n, n2, rows, nov,
                   r0 == 0 ? 0.0 : 1.0, c->R.p + (long long)n * nov, nov, Batch(), nullptr, 0);
         });
+        }
         TR_LAUNCH(pf, st, "residual", 0, 24.0 * n * nov,
                   ritz_resid<<<dim3(nblk, n), 256, 0, st>>>(c->R.p, c->Xr.p + (long long)n * nov, c->theta.p, n, nov,
                                                             c->part.p));

@@ -184,6 +184,32 @@ def test_oscillator_strengths_of_full_tddft_states(mol, refs):
     assert np.abs(f_gpu - f_ref).max() < 1e-8 * max(1.0, np.abs(f_ref).max())
 
 
+@pytest.mark.parametrize("precision", [0, 2])
+def test_degenerate_cases(mol, precision):
+    """No exchange (c_x = 0: A - B = D, A + B = D + 4 J), a window with no virtual
+    orbital (no K term at all), no auxiliary functions (B = 0, Omega = e_a - e_i),
+    and an empty block."""
+    X = synth.random_trial_block(44, 5, mol.nocc, mol.nvir)
+    for op, win in ((dict(RSH, cx=0.0), 40.0), (RSH, 1e-3)):
+        f = _oracle(mol, op, win)
+        c = _ctx(mol, tddft=1, precision=precision, window_ev=win, **op)
+        c.build()
+        P, M = c.matvec_tddft(X)
+        Pr, Mr = tda.matvec_pm(f, X)
+        assert _rel(P, Pr) < 1e-12 and _rel(M, Mr) < 1e-12
+        if op["cx"] == 0.0:
+            D = f.D.reshape(1, f.nocc, f.nvir)
+            assert _rel(M, D * X) < 1e-13
+        assert c.matvec_tddft(np.zeros((0, mol.nocc, mol.nvir)))[0].shape[0] == 0
+    m0 = synth.make_molecule(seed=31, n_heavy=5, n_h=4)
+    m0.aux_exp = np.zeros_like(m0.aux_exp)
+    c = _ctx(m0, tddft=1, precision=precision, nstates=3, tol=1e-10, **RSH)
+    c.build()
+    om, XpY, XmY, rs, info = c.solve_tddft()
+    D = np.sort((m0.eps[m0.nocc:][None, :] - m0.eps[:m0.nocc][:, None]).reshape(-1))
+    assert info.converged and np.all(np.abs(om - D[:3]) <= 4e-15 * D[:3])
+
+
 def test_invalid_uses_are_rejected(mol):
     tdarisp = _lib()
     with pytest.raises(tdarisp.TDARispError):

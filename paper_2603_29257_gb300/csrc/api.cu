@@ -329,10 +329,14 @@ int tr_matvec_tddft(tr_ctx *ctx, int m, const double *X, double *ApBX, double *A
         dp.alloc(n, &ctx->budget, "matvec output");
         dm.alloc(n, &ctx->budget, "matvec output");
         TR_CUDA(cudaMemcpyAsync(dx.p, X, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
+        TR_CUDA(cudaMemsetAsync(ctx->flag.p + 1, 0, sizeof(int), ctx->st));
         tr::matvec_pm(ctx, m, dx.p, dp.p, dm.p);
         TR_CUDA(cudaMemcpyAsync(ApBX, dp.p, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->st));
         TR_CUDA(cudaMemcpyAsync(AmBX, dm.p, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->st));
+        int tc_err = 0;
+        TR_CUDA(cudaMemcpyAsync(&tc_err, ctx->flag.p + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
         TR_CUDA(cudaStreamSynchronize(ctx->st));
+        TR_REQUIRE(!tc_err, TR_ECUDA, "matvec_tddft: a tensor-core pipeline wait timed out");
         return TR_OK;
     });
 }

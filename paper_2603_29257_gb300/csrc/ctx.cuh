@@ -27,6 +27,12 @@ struct tr_ctx {
     std::vector<double> pexp_h, pcoef_h;
     int nao = 0;
     tr::PairList pl;
+    // block sparsity of an AO integral matrix (P|mn) from the kept shell pairs: per
+    // column tile of 64 functions, the row tiles of 16 with a kept pair (the same
+    // for every auxiliary function)
+    std::vector<int> kt_list_h, kt_count_h;
+    tr::DevBuf<int> kt_list, kt_count;
+    tr::KTiles ktiles;
     tr::DevBuf<tr::ShellDev> shells;
     tr::DevBuf<double> pexp, pcoef, boys, prim;
     tr::DevBuf<int2> pairs, prange;

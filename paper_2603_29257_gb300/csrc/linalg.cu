@@ -17,12 +17,15 @@ constexpr int BK = 16, NT = 256;
 
 // Thread (tx, ty) of a 16 x 16 block computes TM x TN outputs at rows
 // ty + 16 i and columns tx + 16 j; the block tile is (16 TM) x (16 TN).
-// Skinny shapes (a dimension of a few dozen) use TM or TN = 1.
+// Skinny shapes (a dimension of a few dozen) use TM or TN = 1.  With ktl
+// (block-sparse B, no K split) the block visits only the K tiles listed for its
+// column tile: ktl[blockIdx.x * ktld + t] for t < ktc[blockIdx.x].
 template <typename TI, typename TC, bool TA, bool TB, int TM, int TN>
 __global__ void __launch_bounds__(NT)
     gemm_kernel(int M, int N, int K, double alpha, const TI *__restrict__ A, long long lda,
                 const TI *__restrict__ B, long long ldb, double beta, TC *__restrict__ C,
-                long long ldc, Batch bt, int ksplit, int kchunk, double *__restrict__ ws)
+                long long ldc, Batch bt, int ksplit, int kchunk, double *__restrict__ ws,
+                const int *__restrict__ ktl, const int *__restrict__ ktc, int ktld)
 {
     constexpr int BM = 16 * TM, BN = 16 * TN;
     __shared__ TI As[BK][BM + 1];
@@ -81,11 +84,14 @@ __global__ void __launch_bounds__(NT)
         }
     };
 
-    if (kb < ke) load(kb);
-    for (int k0 = kb; k0 < ke; k0 += BK) {
+    // K tiles of this block: [kb, ke) in steps of BK, or the listed ones
+    const int nk = ktl ? ktc[blockIdx.x] : (ke > kb ? (ke - kb + BK - 1) / BK : 0);
+    const int *kt = ktl ? ktl + (long long)blockIdx.x * ktld : nullptr;
+    if (nk > 0) load(kt ? kt[0] * BK : kb);
+    for (int t = 0; t < nk; ++t) {
         store();
         __syncthreads();
-        if (k0 + BK < ke) load(k0 + BK);
+        if (t + 1 < nk) load(kt ? kt[t + 1] * BK : kb + (t + 1) * BK);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
             TI a[TM], bb[TN];
@@ -205,16 +211,17 @@ __global__ void sum_rows_kernel(const double *__restrict__ a, int nrows, int n, 
 template <typename TI, typename TC, int TM, int TN>
 void launch_gemm(cudaStream_t st, bool ta, bool tb, dim3 grid, int M, int N, int K, double alpha,
                  const TI *A, long long lda, const TI *B, long long ldb, double beta, TC *C,
-                 long long ldc, const Batch &bt, int ksplit, int kchunk, double *ws)
+                 long long ldc, const Batch &bt, int ksplit, int kchunk, double *ws,
+                 const int *ktl = nullptr, const int *ktc = nullptr, int ktld = 0)
 {
     if (!ta && !tb)
-        gemm_kernel<TI, TC, false, false, TM, TN><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
+        gemm_kernel<TI, TC, false, false, TM, TN><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws, ktl, ktc, ktld);
     else if (!ta && tb)
-        gemm_kernel<TI, TC, false, true, TM, TN><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
+        gemm_kernel<TI, TC, false, true, TM, TN><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws, ktl, ktc, ktld);
     else if (ta && !tb)
-        gemm_kernel<TI, TC, true, false, TM, TN><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
+        gemm_kernel<TI, TC, true, false, TM, TN><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws, ktl, ktc, ktld);
     else
-        gemm_kernel<TI, TC, true, true, TM, TN><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
+        gemm_kernel<TI, TC, true, true, TM, TN><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws, ktl, ktc, ktld);
 }
 
 template <typename TI, typename TC>
@@ -282,6 +289,25 @@ void dgemm(Prof &prof, cudaStream_t st, const char *name, bool ta, bool tb, int 
 {
     gemm_any<double, double>(prof, st, name, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ws,
                              ws_elems, alg_bytes, 0);
+}
+
+void dgemm_ktiles(Prof &prof, cudaStream_t st, const char *name, bool ta, int M, int N, int K, double alpha,
+                  const double *A, long long lda, const double *B, long long ldb, double beta, double *C,
+                  long long ldc, const Batch &bt, const KTiles &kt)
+{
+    if (M <= 0 || N <= 0 || bt.count() <= 0) return;
+    TR_REQUIRE(kt.list && kt.count && kt.ld >= cdiv(std::max(K, 1), BK), TR_EINVAL, "gemm: bad K-tile list");
+    const int nb = bt.count();
+    TR_REQUIRE(nb <= 65535 && cdiv(M, 64) <= 65535, TR_EINVAL, "gemm: batch or M too large");
+    dim3 grid(cdiv(N, 64), cdiv(M, 64), nb);
+    // performed flops (listed tiles only) and every operand byte read once
+    const double flops = 2.0 * (double)M * 64.0 * BK * (double)kt.active * nb;
+    const double bytes = 8.0 * ((double)M * K + (double)K * N) * nb + 16.0 * M * N * nb;
+    int tok = prof.begin(st, name, flops, bytes);
+    launch_gemm<double, double, 4, 4>(st, ta, false, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, 1, K,
+                                      nullptr, kt.list, kt.count, kt.ld);
+    TR_CUDA(cudaGetLastError());
+    prof.end(st, tok);
 }
 
 void sgemm(Prof &prof, cudaStream_t st, const char *name, bool ta, bool tb, int M, int N, int K,

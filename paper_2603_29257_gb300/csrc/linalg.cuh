@@ -25,6 +25,23 @@ void dgemm(Prof &prof, cudaStream_t st, const char *name, bool ta, bool tb, int 
            double beta, double *C, long long ldc, const Batch &bt, double *ws, size_t ws_elems,
            double alg_bytes = -1.0);
 
+// Row tiles of a block-sparse B (op(B) = B[k * ldb + n], K x N) that may hold
+// non-zeros, per column tile of 64: list[nt * ld + t] for t < count[nt], in
+// ascending order and in units of 16 rows.  Device pointers; the pattern is the
+// caller's promise (rows outside the list are read as zero).
+struct KTiles {
+    const int *list = nullptr;
+    const int *count = nullptr;
+    int ld = 0;
+    long long active = 0;  // total listed tiles (profiler flops: active x 2 M 16 64 per batch entry)
+};
+
+// C = alpha * op(A) * B + beta * C over the listed row tiles of B only (64 x 64
+// output tiles, no K split); otherwise as dgemm.
+void dgemm_ktiles(Prof &prof, cudaStream_t st, const char *name, bool ta, int M, int N, int K, double alpha,
+                  const double *A, long long lda, const double *B, long long ldb, double beta, double *C,
+                  long long ldc, const Batch &bt, const KTiles &kt);
+
 // Same for FP32 operands accumulated in FP32 per K chunk (at most max_kchunk
 // when > 0, else chosen by the split heuristic) with FP64 partial sums and an
 // FP64 output.

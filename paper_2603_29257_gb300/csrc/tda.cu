@@ -240,6 +240,41 @@ void refresh_molecule(tr_ctx *c)
     TR_CUDA(cudaMemcpy(c->pcoef.p, c->pcoef_h.data(), sizeof(double) * c->pcoef_h.size(), cudaMemcpyHostToDevice));
     if (!c->pl.pairs.empty())
         TR_CUDA(cudaMemcpy(c->pairs.p, c->pl.pairs.data(), sizeof(int2) * c->pl.pairs.size(), cudaMemcpyHostToDevice));
+    // row tiles (16 functions) of each column tile (64 functions) of (P|mn) that a
+    // kept shell pair touches; both orders, the matrices being symmetric
+    {
+        const int nao = c->nao, ntk = cdiv(std::max(nao, 1), 16), ntn = cdiv(std::max(nao, 1), 64);
+        std::vector<unsigned char> hit((size_t)ntn * ntk, 0);
+        auto mark = [&](int r0, int nr, int c0, int nc) {
+            for (int kt = r0 / 16; kt <= (r0 + nr - 1) / 16; ++kt)
+                for (int nt = c0 / 64; nt <= (c0 + nc - 1) / 64; ++nt) hit[(size_t)nt * ntk + kt] = 1;
+        };
+        for (const int2 &ab : c->pl.pairs) {
+            const ShellDev &A = c->shells_h[ab.x], &B = c->shells_h[ab.y];
+            const int na = 2 * A.l + 1, nb = 2 * B.l + 1;
+            mark(A.ao, na, B.ao, nb);
+            mark(B.ao, nb, A.ao, na);
+        }
+        c->kt_list_h.assign((size_t)ntn * ntk, 0);
+        c->kt_count_h.assign(ntn, 0);
+        long long active = 0;
+        for (int nt = 0; nt < ntn; ++nt) {
+            int n = 0;
+            for (int kt = 0; kt < ntk; ++kt)
+                if (hit[(size_t)nt * ntk + kt]) c->kt_list_h[(size_t)nt * ntk + n++] = kt;
+            c->kt_count_h[nt] = n;
+            active += n;
+        }
+        c->kt_list.alloc(c->kt_list_h.size(), &c->budget, "integral block sparsity");
+        c->kt_count.alloc(c->kt_count_h.size(), &c->budget, "integral block sparsity");
+        TR_CUDA(cudaMemcpy(c->kt_list.p, c->kt_list_h.data(), sizeof(int) * c->kt_list_h.size(), cudaMemcpyHostToDevice));
+        TR_CUDA(cudaMemcpy(c->kt_count.p, c->kt_count_h.data(), sizeof(int) * c->kt_count_h.size(),
+                           cudaMemcpyHostToDevice));
+        c->ktiles.list = c->kt_list.p;
+        c->ktiles.count = c->kt_count.p;
+        c->ktiles.ld = ntk;
+        c->ktiles.active = active;
+    }
 }
 
 void refresh_window(tr_ctx *c)
@@ -375,8 +410,9 @@ static void transforms_fp64(tr_ctx *c, DevBuf<double> &Iij, DevBuf<double> *Iia)
         b1.n1 = np;
         b1.sB1 = (long long)nao * nao;
         b1.sC1 = (long long)nocc * nao;
-        dgemm(pf, st, "xform_J1", true, false, nocc, nao, nao, 1.0, c->C.p, nmo, I.p, nao, 0.0, H.p, nao, b1,
-              nullptr, 0);
+        // the integrals are block-sparse in mu (screened pairs): only the listed row tiles
+        dgemm_ktiles(pf, st, "xform_J1", true, nocc, nao, nao, 1.0, c->C.p, nmo, I.p, nao, 0.0, H.p, nao, b1,
+                     c->ktiles);
         Batch b2;
         b2.n1 = np;
         b2.sA1 = (long long)nocc * nao;
@@ -394,8 +430,8 @@ static void transforms_fp64(tr_ctx *c, DevBuf<double> &Iij, DevBuf<double> *Iia)
         h.n1 = np;
         h.sB1 = (long long)nao * nao;
         h.sC1 = (long long)oK * nao;
-        dgemm(pf, st, "xform_K1", true, false, oK, nao, nao, 1.0, c->C.p + o0, nmo, I.p, nao, 0.0, H.p, nao, h,
-              nullptr, 0);
+        dgemm_ktiles(pf, st, "xform_K1", true, oK, nao, nao, 1.0, c->C.p + o0, nmo, I.p, nao, 0.0, H.p, nao, h,
+                     c->ktiles);
         Batch g;
         g.n1 = np;
         g.sA1 = (long long)oK * nao;
@@ -410,8 +446,8 @@ static void transforms_fp64(tr_ctx *c, DevBuf<double> &Iij, DevBuf<double> *Iia)
                   Iia->p + (long long)p0 * oK * vK, vK, x, nullptr, 0);
         }
         h.sC1 = (long long)vK * nao;
-        dgemm(pf, st, "xform_K1", true, false, vK, nao, nao, 1.0, c->C.p + nocc, nmo, I.p, nao, 0.0, H.p, nao, h,
-              nullptr, 0);
+        dgemm_ktiles(pf, st, "xform_K1", true, vK, nao, nao, 1.0, c->C.p + nocc, nmo, I.p, nao, 0.0, H.p, nao, h,
+                     c->ktiles);
         g.sA1 = (long long)vK * nao;
         g.sC1 = (long long)vK * vK;
         dgemm(pf, st, "xform_K2", false, false, vK, vK, nao, 1.0, H.p, nao, c->C.p + nocc, nmo, 0.0,

@@ -224,6 +224,42 @@ void launch_gemm(cudaStream_t st, bool ta, bool tb, dim3 grid, int M, int N, int
         gemm_kernel<TI, TC, true, true, TM, TN><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws, ktl, ktc, ktld);
 }
 
+// resident CTAs per SM of a gemm_kernel instance (queried once) and the SM count
+template <typename TI, typename TC, int TM, int TN>
+int gemm_occupancy(bool ta, bool tb)
+{
+    static int occ[2][2] = {{0, 0}, {0, 0}};
+    int &o = occ[ta][tb];
+    if (o == 0) {
+        int v = 0;
+        cudaError_t e;
+        if (!ta && !tb) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, gemm_kernel<TI, TC, false, false, TM, TN>, NT, 0);
+        else if (!ta) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, gemm_kernel<TI, TC, false, true, TM, TN>, NT, 0);
+        else if (!tb) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, gemm_kernel<TI, TC, true, false, TM, TN>, NT, 0);
+        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, gemm_kernel<TI, TC, true, true, TM, TN>, NT, 0);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            v = 1;
+        }
+        o = std::max(v, 1);
+    }
+    return o;
+}
+
+int sm_count()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            v = 152;
+        }
+        n = std::max(v, 1);
+    }
+    return n;
+}
+
 template <typename TI, typename TC>
 void gemm_any(Prof &prof, cudaStream_t st, const char *name, bool ta, bool tb, int M, int N, int K,
               double alpha, const TI *A, long long lda, const TI *B, long long ldb, double beta,
@@ -249,6 +285,25 @@ void gemm_any(Prof &prof, cudaStream_t st, const char *name, bool ta, bool tb, i
         ksplit = (int)std::max<long long>(1, std::min(want, cap));
         ksplit = std::min(ksplit, 65535 / nb);
         ksplit = std::max(ksplit, 1);
+    }
+    // wave quantisation of large FP64 launches: when the output tiles fill the GPU
+    // a few times over with a ragged last wave, split K 2..4 ways (at least 1024
+    // per part) if that evens out the waves by more than 3 %; partial sums in ws
+    if (ksplit == 1 && ws && max_kchunk == 0 && sizeof(TI) == 8 && TM == 4 && TN == 4 && tiles >= target &&
+        K >= 2048) {
+        const long long wave = (long long)sm_count() * gemm_occupancy<TI, TC, 4, 4>(ta, tb);
+        auto eff = [&](int ks) {
+            const long long t = tiles * ks;
+            return (double)t / (double)(((t + wave - 1) / wave) * wave);
+        };
+        double best = eff(1) + 0.03;
+        for (int ks = 2; ks <= 4; ++ks) {
+            if (K / ks < 1024 || (size_t)ks * nb * M * N > ws_elems || (long long)nb * ks > 65535) break;
+            if (eff(ks) > best) {
+                best = eff(ks);
+                ksplit = ks;
+            }
+        }
     }
     int kchunk = K;
     if (ksplit > 1) {

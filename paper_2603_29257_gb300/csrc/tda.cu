@@ -545,7 +545,7 @@ void build(tr_ctx *c)
     cudaStream_t st = c->st;
     Prof &pf = c->prof;
     const bool mixed = c->opt.precision == TR_MIXED;
-    c->ws_split.reserve((size_t)16 << 20, &c->budget, "split-K workspace");
+    c->ws_split.reserve((size_t)32 << 20, &c->budget, "split-K workspace");
     c->k_active = nK > 0 && c->oK > 0 && c->vK > 0 && c->opt.cx != 0.0;
     c->Y.release();
     c->Y32.release();
@@ -727,7 +727,7 @@ size_t footprint(tr_ctx *c)
     const double mws = nK > 0 ? std::min<double>((double)c->opt.matvec_ws_bytes, d * mb * nK * oK * vK) * (mw / std::max(vK, 1.0)) +
                                     (mixed ? 2.0 * f * mb * oK * vKp + f * mb * nov : d * mb * oK * vK)
                               : 0.0;
-    const double ws = d * 16.0 * (1 << 20) + 2.0 * d * std::max(nJ, 1.0) * mb + mws;
+    const double ws = d * 32.0 * (1 << 20) + 2.0 * d * std::max(nJ, 1.0) * mb + mws;
     double tcx = 0.0;
     if (c->opt.precision == TR_FP64_TC) {
         // slices kept for the products, and the per-block sliced operands
@@ -759,7 +759,7 @@ size_t footprint(tr_ctx *c)
 void reserve_matvec(tr_ctx *c, int m)
 {
     const int mb = std::max(1, std::min(m, c->mblk));
-    c->ws_split.reserve((size_t)16 << 20, &c->budget, "split-K workspace");
+    c->ws_split.reserve((size_t)32 << 20, &c->budget, "split-K workspace");
     if (c->opt.j_ao) reserve_jao(c, mb);
     c->ws_Z.reserve((size_t)std::max(c->nJ, 1) * mb, &c->budget, "J workspace");
     c->ws_Z2.reserve((size_t)std::max(c->nJ, 1) * mb, &c->budget, "J workspace");
@@ -844,7 +844,7 @@ void matvec(tr_ctx *c, int m, const double *X, double *AX)
                 const double kb2 = 8.0 * ((double)mm * np * oK * vK + (double)oK * np * oK + 2.0 * mm * oK * vK);
                 dgemm(pf, st, "K_stage2", false, false, oK, vK, np * oK, -c->opt.cx,
                       c->T2.p + (long long)P0 * oK, (long long)nK * oK, c->ws_M.p, vK, 1.0,
-                      ax + (long long)o0 * nvir, nvir, b2, nullptr, 0, kb2);
+                      ax + (long long)o0 * nvir, nvir, b2, c->ws_split.p, c->ws_split.n, kb2);
             }
         }
     }
@@ -928,7 +928,7 @@ void matvec_b(tr_ctx *c, int m, const double *X, double *BX)
             f.sC1 = nov;
             const double fb = 8.0 * ((double)mm * np * oK * oK + (double)np * oK * vK + 2.0 * mm * oK * vK);
             dgemm(pf, st, "Kx_stage2", false, false, oK, vK, np * oK, -c->opt.cx, c->ws_M.p, (long long)np * oK, tP,
-                  vK, 1.0, bx + (long long)o0 * nvir, nvir, f, nullptr, 0, fb);
+                  vK, 1.0, bx + (long long)o0 * nvir, nvir, f, c->ws_split.p, c->ws_split.n, fb);
         }
     }
 }

@@ -89,6 +89,7 @@ int tr_create(tr_ctx **out, const tr_options *opt, void *cuda_stream)
         normalise_options(&c->opt);
         c->st = (cudaStream_t)cuda_stream;
         TR_CUDA(cudaGetDevice(&c->device));
+        tr::gemm_prepare();
         size_t fr = 0, tot = 0;
         TR_CUDA(cudaMemGetInfo(&fr, &tot));
         c->budget.limit = opt->hbm_budget ? opt->hbm_budget : (size_t)(0.9 * (double)fr);

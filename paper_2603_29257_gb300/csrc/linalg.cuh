@@ -25,6 +25,10 @@ void dgemm(Prof &prof, cudaStream_t st, const char *name, bool ta, bool tb, int 
            double beta, double *C, long long ldc, const Batch &bt, double *ws, size_t ws_elems,
            double alg_bytes = -1.0);
 
+// Query (once per process) what the GEMMs' launch-shape choices depend on; called
+// at context creation so that no query happens inside a stream capture.
+void gemm_prepare();
+
 // Row tiles of a block-sparse B (op(B) = B[k * ldb + n], K x N) that may hold
 // non-zeros, per column tile of 64: list[nt * ld + t] for t < count[nt], in
 // ascending order and in units of 16 rows.  Device pointers; the pattern is the

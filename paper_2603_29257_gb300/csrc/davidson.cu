@@ -471,6 +471,9 @@ struct Dav {
         maxsp = c->opt.max_space > 0 ? c->opt.max_space : 20 * n;
         maxsp = std::max(maxsp, rpa ? pmax + nr : b0 + n);
         maxsp = (int)std::min<long long>(maxsp, std::max<long long>(nov, b0));
+        TR_REQUIRE(!rpa || maxsp >= pmax + nr, TR_EINVAL,
+                   "solve: full TDDFT needs nocc * nvir of at least the initial block plus 2 nstates (" +
+                       std::to_string(pmax + nr) + ")");
         max_iter = c->opt.max_iter > 0 ? c->opt.max_iter : 200;
         tol = c->opt.tol;
         TR_CUDA(cudaHostAlloc((void **)&h_rn, sizeof(double) * n, cudaHostAllocDefault));

@@ -89,6 +89,12 @@ struct tr_ctx {
     // Coulomb term on the fly in the AO basis (j_ao): half-transformed and AO
     // transition densities, AO potentials, fit coefficients, integral chunk
     tr::DevBuf<double> ws_jT, ws_jD, ws_jU, ws_jR, ws_jI;
+    // the function pairs (k, l) of the kept shell pairs as flat indices k nao + l
+    // (ascending; -1: not yet listed for this molecule) and the packed copies of
+    // the integral chunk, the AO densities and the AO potentials over them
+    tr::DevBuf<int> kl_idx;
+    long long nkl = -1;
+    tr::DevBuf<double> ws_jIp, ws_jDp, ws_jUp;
     tr::DevBuf<int> flag;
     int mblk = 32;
 

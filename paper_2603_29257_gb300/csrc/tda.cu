@@ -225,6 +225,7 @@ void refresh_molecule(tr_ctx *c)
     c->nJ = (int)c->auxJ_h.size();
     c->nK = (int)c->auxK_h.size();
     c->pl = make_pairs(c->shells_h, c->pexp_h, c->pcoef_h, c->opt.screen);
+    c->nkl = -1;  // the packed pair list of the AO Coulomb term follows the new pairs
     c->shells.alloc(c->shells_h.size(), &c->budget, "shells");
     c->pexp.alloc(c->pexp_h.size(), &c->budget, "primitives");
     c->pcoef.alloc(c->pcoef_h.size(), &c->budget, "primitives");

@@ -12,7 +12,11 @@ same molecule and cases (Sec. 2, Eqs. tddft and hessian, with A + B = D + 4 (ia|
 - c_x [(ib|ja) + (ij|ab)] and A - B = D + c_x [(ib|ja) - (ij|ab)]) by the dense
 symmetric-form solve of the oracle.
 
-Run: python tests/golden/make_golden.py [tda|tddft]   (default: tda)
+oscillator_24atom.json: the oscillator strengths f = 2/3 Omega |mu|^2 (Sec. 2,
+Eqs. oscillator_strength and transition) of those states, TDA (unit-norm X) and
+full TDDFT (X+Y with (X+Y).(X-Y) = 1), dipoles about the coordinate origin.
+
+Run: python tests/golden/make_golden.py [tda|tddft|props]   (default: tda)
 """
 from __future__ import annotations
 
@@ -66,8 +70,27 @@ def main_tddft():
         json.dump(out, fh, indent=1)
 
 
+def main_props():
+    mol = synth.molecule_24()
+    out = {"source": "oracle: dense TDA eigh and dense full TDDFT solve, then the oracle's transition dipoles "
+                     "(Sec. 2, Eqs. oscillator_strength, transition)",
+           "molecule": "synth.molecule_24(): seed 1, 10 heavy + 14 H, nao 210, nocc 42",
+           "window_ev": 40.0, "nstates": 5, "cases": {}}
+    for name, op in CASES.items():
+        f = tda.build(mol.Z, mol.xyz, mol.shells, mol.aux_exp, mol.C, mol.eps, mol.nocc, op["cx"],
+                      op["ka"], op["kb"], op["omega"], window_ev=40.0, tddft=True)
+        w, V = scipy.linalg.eigh(tda.explicit_A(f), subset_by_index=[0, 4], driver="evr")
+        X = tda.fix_sign(V.T).reshape(5, f.nocc, f.nvir)
+        f_tda = tda.oscillator_strengths(w, tda.transition_dipoles(mol.xyz, mol.shells, mol.C, mol.nocc, X))
+        wd, XpY, _ = tda.tddft_dense(f, 5)
+        f_rpa = tda.oscillator_strengths(wd, tda.transition_dipoles(mol.xyz, mol.shells, mol.C, mol.nocc, XpY))
+        out["cases"][name] = {"options": op, "omega_tda": [float(x) for x in w], "f_tda": [float(x) for x in f_tda],
+                              "omega_tddft": [float(x) for x in wd], "f_tddft": [float(x) for x in f_rpa]}
+        print(name, f_tda, f_rpa)
+    with open(os.path.join(HERE, "oscillator_24atom.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+
+
 if __name__ == "__main__":
-    if len(sys.argv) > 1 and sys.argv[1] == "tddft":
-        main_tddft()
-    else:
-        main()
+    which = sys.argv[1] if len(sys.argv) > 1 else "tda"
+    {"tda": main, "tddft": main_tddft, "props": main_props}[which]()

@@ -4,6 +4,9 @@ transition dipoles and oscillator strengths, against the oracle (Obara-Saika
 integrals, plain einsum) on the same vectors."""
 from __future__ import annotations
 
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -66,3 +69,28 @@ def test_oscillator_strengths_of_solved_states(mol):
     assert _rel(f, ref) < 1e-12
     fd = c.oscillator_strengths(torch.from_numpy(om).cuda(), torch.from_numpy(X).cuda()).cpu().numpy()
     assert _rel(fd, ref) < 1e-12
+
+
+@pytest.mark.parametrize("case", ["hybrid", "rsh"])
+@pytest.mark.parametrize("tddft", [0, 1])
+def test_24atom_oscillator_strengths_against_golden(case, tddft):
+    """Solve on the GPU (TDA, or full TDDFT with X+Y), then f on the GPU, against
+    the oracle's dense solution stored by tests/golden/make_golden.py."""
+    here = os.path.dirname(os.path.abspath(__file__))
+    gold = json.load(open(os.path.join(here, "golden", "oscillator_24atom.json")))["cases"][case]
+    op = gold["options"]
+    c = _lib().Context(cx=op["cx"], k_alpha=op["ka"], k_beta=op["kb"], omega=op["omega"], tddft=tddft,
+                       nstates=5, tol=1e-10)
+    c.set_molecule_from(synth.molecule_24())
+    c.build()
+    if tddft:
+        om, X, _, rs, info = c.solve_tddft()
+        ref_om, ref_f = gold["omega_tddft"], gold["f_tddft"]
+    else:
+        om, X, rs, info = c.solve()
+        ref_om, ref_f = gold["omega_tda"], gold["f_tda"]
+    assert info.converged
+    assert np.abs(om - np.array(ref_om)).max() < 1e-9
+    f = c.oscillator_strengths(om, X)
+    ref = np.array(ref_f)
+    assert np.all(np.abs(f - ref) <= 1e-4 * ref + 1e-9), (f, ref)

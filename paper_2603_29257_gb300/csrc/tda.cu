@@ -780,6 +780,22 @@ void reserve_matvec(tr_ctx *c, int m)
     }
 }
 
+// Coulomb term from the stored (P|ia), FP64: Z = (Q|jb) X; Zt = (P|Q)^-1 Z;
+// out = 2 (P|ia) Zt + beta out (Sec. 3.1 order, in the MO basis)
+static void j_stored_fp64(tr_ctx *c, int mm, const double *x, double *out, double beta)
+{
+    Prof &pf = c->prof;
+    cudaStream_t st = c->st;
+    const int nJ = c->nJ;
+    const long long nov = c->nov;
+    dgemm(pf, st, "J_contract", false, true, nJ, mm, (int)nov, 1.0, c->Y.p, nov, x, nov, 0.0, c->ws_Z.p, mm, Batch(),
+          c->ws_split.p, c->ws_split.n);
+    dgemm(pf, st, "J_metric", false, false, nJ, mm, nJ, 1.0, c->GinvJ.p, nJ, c->ws_Z.p, mm, 0.0, c->ws_Z2.p, mm,
+          Batch(), nullptr, 0);
+    dgemm(pf, st, "J_expand", true, false, mm, (int)nov, nJ, 2.0, c->ws_Z2.p, mm, c->Y.p, nov, beta, out, nov,
+          Batch(), nullptr, 0);
+}
+
 void matvec(tr_ctx *c, int m, const double *X, double *AX)
 {
     TR_REQUIRE(c->built, TR_EINVAL, "matvec: call tr_build first");
@@ -810,13 +826,7 @@ void matvec(tr_ctx *c, int m, const double *X, double *AX)
         if (nJ && c->opt.j_ao) {
             j_ao_block(c, mm, x, ax);
         } else if (nJ) {
-            // Z = (Q|jb) X ; Zt = (P|Q)^-1 Z ; AX += 2 (P|ia) Zt
-            dgemm(pf, st, "J_contract", false, true, nJ, mm, (int)nov, 1.0, c->Y.p, nov, x, nov, 0.0,
-                  c->ws_Z.p, mm, Batch(), c->ws_split.p, c->ws_split.n);
-            dgemm(pf, st, "J_metric", false, false, nJ, mm, nJ, 1.0, c->GinvJ.p, nJ, c->ws_Z.p, mm, 0.0,
-                  c->ws_Z2.p, mm, Batch(), nullptr, 0);
-            dgemm(pf, st, "J_expand", true, false, mm, (int)nov, nJ, 2.0, c->ws_Z2.p, mm, c->Y.p, nov, 1.0,
-                  ax, nov, Batch(), nullptr, 0);
+            j_stored_fp64(c, mm, x, ax, 1.0);  // AX += 2 J
         }
         if (c->k_active) {
             long long tot = (long long)mm * oK * vK;
@@ -893,13 +903,7 @@ void matvec_b(tr_ctx *c, int m, const double *X, double *BX)
         const double *x = X + (long long)m0 * nov;
         double *bx = BX + (long long)m0 * nov;
         if (nJ && !c->opt.j_ao) {
-            // 2 J X with the stored (P|ia), as in A X
-            dgemm(pf, st, "J_contract", false, true, nJ, mm, (int)nov, 1.0, c->Y.p, nov, x, nov, 0.0,
-                  c->ws_Z.p, mm, Batch(), c->ws_split.p, c->ws_split.n);
-            dgemm(pf, st, "J_metric", false, false, nJ, mm, nJ, 1.0, c->GinvJ.p, nJ, c->ws_Z.p, mm, 0.0,
-                  c->ws_Z2.p, mm, Batch(), nullptr, 0);
-            dgemm(pf, st, "J_expand", true, false, mm, (int)nov, nJ, 2.0, c->ws_Z2.p, mm, c->Y.p, nov, 0.0,
-                  bx, nov, Batch(), nullptr, 0);
+            j_stored_fp64(c, mm, x, bx, 0.0);  // BX = 2 J, as in A X
         } else {
             TR_CUDA(cudaMemsetAsync(bx, 0, sizeof(double) * (size_t)mm * nov, st));
             if (nJ) j_ao_block(c, mm, x, bx);
@@ -1017,6 +1021,43 @@ void reserve_tc(tr_ctx *c, int mb)
     }
 }
 
+// Coulomb term from the stored (P|ia) on the tensor cores (7 slices):
+// out += 2 (P|ia) (P|Q)^-1 (Q|jb) X, the metric step in FP64
+static void j_stored_tc(tr_ctx *c, int mm, const double *x, double *out)
+{
+    const int S = OZ_SLICES_FP64;
+    Prof &pf = c->prof;
+    cudaStream_t st = c->st;
+    const int nJ = c->nJ;
+    const long long nov = c->nov;
+    int *err = c->flag.p + 1;
+    OzMat Xs, Zs;
+    oz_bind(Xs, c->ozw_X.p, mm, (int)nov, S);
+    oz_split(pf, st, "oz_split_X", x, nov, 1, Xs);
+    // Z[P][m] = sum_ia (P|ia) X_m,ia   (long K: split over CTAs)
+    OzOut oz;
+    oz.d = c->ws_Z.p;
+    oz.ldm = mm;
+    oz.ldn = 1;
+    const int tiles = cdiv(nJ, 128) * cdiv(mm, 64);
+    int ks = std::max(1, 2 * 152 / tiles);
+    ks = (int)std::min<long long>(ks, (long long)c->ws_split.n / ((long long)nJ * mm));
+    oz_gemm(pf, st, "J_contract_tc", c->oz_Y, 0, 0, 0, 0, Xs, 0, 0, 0, 0, nJ, mm, c->oz_Y.nkb, 1, 1, oz, err,
+            std::max(ks, 1), c->ws_split.p, c->ws_split.n);
+    dgemm(pf, st, "J_metric", false, false, nJ, mm, nJ, 1.0, c->GinvJ.p, nJ, c->ws_Z.p, mm, 0.0, c->ws_Z2.p, mm,
+          Batch(), nullptr, 0);
+    // out[m][ia] += 2 sum_P (P|ia) Zt[P][m]: rows ia of the output, columns m
+    oz_bind(Zs, c->ozw_Z.p, mm, nJ, S);
+    oz_split(pf, st, "oz_split_Z", c->ws_Z2.p, 1, mm, Zs);
+    OzOut oe;
+    oe.d = out;
+    oe.ldm = 1;
+    oe.ldn = nov;
+    oe.alpha = 2.0;
+    oe.accumulate = true;
+    oz_gemm(pf, st, "J_expand_tc", c->oz_YT, 0, 0, 0, 0, Zs, 0, 0, 0, 0, (int)nov, mm, c->oz_YT.nkb, 1, 1, oe, err);
+}
+
 // A X with every large product on the tensor cores (7 slices): the same steps
 // and order as the FP64 matvec (Sec. 3.1 for J, Sec. 3.2 for K)
 void matvec_tc(tr_ctx *c, int m, const double *X, double *AX)
@@ -1039,32 +1080,7 @@ void matvec_tc(tr_ctx *c, int m, const double *X, double *AX)
         if (nJ && c->opt.j_ao) {
             j_ao_block(c, mm, x, ax);
         } else if (nJ) {
-            OzMat Xs, Zs;
-            oz_bind(Xs, c->ozw_X.p, mm, (int)nov, S);
-            oz_split(pf, st, "oz_split_X", x, nov, 1, Xs);
-            // Z[P][m] = sum_ia (P|ia) X_m,ia   (long K: split over CTAs)
-            OzOut oz;
-            oz.d = c->ws_Z.p;
-            oz.ldm = mm;
-            oz.ldn = 1;
-            const int tiles = cdiv(nJ, 128) * cdiv(mm, 64);
-            int ks = std::max(1, 2 * 152 / tiles);
-            ks = (int)std::min<long long>(ks, (long long)c->ws_split.n / ((long long)nJ * mm));
-            oz_gemm(pf, st, "J_contract_tc", c->oz_Y, 0, 0, 0, 0, Xs, 0, 0, 0, 0, nJ, mm, c->oz_Y.nkb, 1, 1, oz, err,
-                    std::max(ks, 1), c->ws_split.p, c->ws_split.n);
-            dgemm(pf, st, "J_metric", false, false, nJ, mm, nJ, 1.0, c->GinvJ.p, nJ, c->ws_Z.p, mm, 0.0, c->ws_Z2.p, mm,
-                  Batch(), nullptr, 0);
-            // AX[m][ia] += 2 sum_P (P|ia) Zt[P][m]: rows ia of the output, columns m
-            oz_bind(Zs, c->ozw_Z.p, mm, nJ, S);
-            oz_split(pf, st, "oz_split_Z", c->ws_Z2.p, 1, mm, Zs);
-            OzOut oe;
-            oe.d = ax;
-            oe.ldm = 1;
-            oe.ldn = nov;
-            oe.alpha = 2.0;
-            oe.accumulate = true;
-            oz_gemm(pf, st, "J_expand_tc", c->oz_YT, 0, 0, 0, 0, Zs, 0, 0, 0, 0, (int)nov, mm, c->oz_YT.nkb, 1, 1, oe,
-                    err);
+            j_stored_tc(c, mm, x, ax);  // AX += 2 J
         }
         if (c->k_active) {
             const long long tot = (long long)mm * oK * vK;
@@ -1124,30 +1140,7 @@ void matvec_b_tc(tr_ctx *c, int m, const double *X, double *BX)
         if (nJ && c->opt.j_ao) {
             j_ao_block(c, mm, x, bx);
         } else if (nJ) {
-            OzMat Xs, Zs;
-            oz_bind(Xs, c->ozw_X.p, mm, (int)nov, S);
-            oz_split(pf, st, "oz_split_X", x, nov, 1, Xs);
-            OzOut oz;
-            oz.d = c->ws_Z.p;
-            oz.ldm = mm;
-            oz.ldn = 1;
-            const int tiles = cdiv(nJ, 128) * cdiv(mm, 64);
-            int ks = std::max(1, 2 * 152 / tiles);
-            ks = (int)std::min<long long>(ks, (long long)c->ws_split.n / ((long long)nJ * mm));
-            oz_gemm(pf, st, "J_contract_tc", c->oz_Y, 0, 0, 0, 0, Xs, 0, 0, 0, 0, nJ, mm, c->oz_Y.nkb, 1, 1, oz, err,
-                    std::max(ks, 1), c->ws_split.p, c->ws_split.n);
-            dgemm(pf, st, "J_metric", false, false, nJ, mm, nJ, 1.0, c->GinvJ.p, nJ, c->ws_Z.p, mm, 0.0, c->ws_Z2.p, mm,
-                  Batch(), nullptr, 0);
-            oz_bind(Zs, c->ozw_Z.p, mm, nJ, S);
-            oz_split(pf, st, "oz_split_Z", c->ws_Z2.p, 1, mm, Zs);
-            OzOut oe;
-            oe.d = bx;
-            oe.ldm = 1;
-            oe.ldn = nov;
-            oe.alpha = 2.0;
-            oe.accumulate = true;
-            oz_gemm(pf, st, "J_expand_tc", c->oz_YT, 0, 0, 0, 0, Zs, 0, 0, 0, 0, (int)nov, mm, c->oz_YT.nkb, 1, 1, oe,
-                    err);
+            j_stored_tc(c, mm, x, bx);  // BX += 2 J (BX zeroed above)
         }
         if (!c->k_active) continue;
         const long long tot = (long long)mm * oK * vK;

@@ -834,8 +834,9 @@ def main():
                          "tddft: full TDDFT-risp products and solve")
     ap.add_argument("--requests", type=int, default=64, help="requests of the serve workload")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
-                    help="form of the matvec workload: 0 FP64, 1 reduced precision, 2 FP64 on the tensor cores")
-    ap.add_argument("--block", type=int, default=30, help="vectors per block of the matvec workload")
+                    help="form of the matvec and tddft workloads: 0 FP64, 1 reduced precision (matvec only), "
+                         "2 FP64 on the tensor cores")
+    ap.add_argument("--block", type=int, default=30, help="vectors per block of the matvec and tddft workloads")
     ap.add_argument("--j-ao", type=int, default=0, choices=[0, 1],
                     help="matvec workload: Coulomb term from the stored (P|ia) (0) or on the fly in the AO basis (1)")
     ap.add_argument("--case", default="full", choices=["full", "small"],

@@ -548,6 +548,8 @@ def run_tddft(args):
     vectors, then one Davidson solve to 15 states, and the TDA solve of the same
     context options for comparison.  value = vectors x K / event time of the
     block products (each vector gets both products)."""
+    if args.precision == 1:
+        sys.exit("tddft workload: full TDDFT-risp runs in the FP64 forms only (--precision 0 or 2)")
     import torch
     torch.cuda.set_device(0)
     import __graft_entry__

@@ -416,3 +416,23 @@ def test_transition_dipoles_do_not_depend_on_the_origin(small_mol):
     mu0 = tda.transition_dipoles(m.xyz, m.shells, m.C, m.nocc, X)
     mu1 = tda.transition_dipoles(m.xyz, m.shells, m.C, m.nocc, X, origin=(2.0, -1.0, 0.5))
     assert np.abs(mu0 - mu1).max() < 1e-11 * max(1.0, np.abs(mu0).max())
+
+
+def test_ri_invariant_under_auxiliary_rescaling(small_mol):
+    """Rescaling auxiliary function P by s_P multiplies (P|mn) by s_P and (P|Q) by
+    s_P s_Q; every RI quantity, and so A, A + B and A - B, is unchanged (a metric
+    applied the wrong way round or left out breaks this)."""
+    m = small_mol
+    f = tda.build(m.Z, m.xyz, m.shells, m.aux_exp, m.C, m.eps, m.nocc, cx=1.0, ka=0.222, kb=0.778, omega=0.2,
+                  tddft=True)
+    rng = np.random.default_rng(5)
+    sJ = rng.uniform(0.2, 5.0, f.GJ.shape[0])
+    sK = rng.uniform(0.2, 5.0, f.GK.shape[0])
+    g = tda.Factors(**{**f.__dict__,
+                       "Y": sJ[:, None, None] * f.Y, "GJ": np.outer(sJ, sJ) * f.GJ,
+                       # T_ij^P = sum_Q (ij|Q) [(Q|P)^-1] carries 1/s_P; T_ab^P = (ab|P) carries s_P
+                       "Tij": f.Tij / sK[:, None, None], "Tab": sK[:, None, None] * f.Tab,
+                       "GK": np.outer(sK, sK) * f.GK, "Tia": sK[:, None, None] * f.Tia})
+    for fn in (tda.explicit_A, tda.explicit_ApB, tda.explicit_AmB):
+        a, b = fn(f), fn(g)
+        assert np.abs(a - b).max() < 1e-12 * np.abs(a).max()

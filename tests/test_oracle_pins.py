@@ -436,3 +436,16 @@ def test_ri_invariant_under_auxiliary_rescaling(small_mol):
     for fn in (tda.explicit_A, tda.explicit_ApB, tda.explicit_AmB):
         a, b = fn(f), fn(g)
         assert np.abs(a - b).max() < 1e-12 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("op", [(1.0, 0.0, 0.0), (0.222, 0.778, 0.2), (0.0, 1.0, 0.4)])
+def test_metrics_symmetric_positive_definite(small_mol, op):
+    """(P|Q) with the Coulomb, range-separated and pure long-range operators:
+    symmetric, positive definite, and its Cholesky factor reproduces it."""
+    m = small_mol
+    for kind in ("J", "K"):
+        G = ints.int2c(tda.aux_shells(m.Z, m.xyz, m.aux_exp, kind), *op)
+        assert np.abs(G - G.T).max() <= 1e-15 * np.abs(G).max()
+        assert np.linalg.eigvalsh(G).min() > 0.0
+        L = np.linalg.cholesky(G)
+        assert np.abs(L @ L.T - G).max() < 1e-13 * np.abs(G).max()

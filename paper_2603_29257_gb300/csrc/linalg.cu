@@ -8,6 +8,7 @@
 #include "linalg.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 namespace tr {
@@ -228,9 +229,11 @@ void launch_gemm(cudaStream_t st, bool ta, bool tb, dim3 grid, int M, int N, int
 template <typename TI, typename TC, int TM, int TN>
 int gemm_occupancy(bool ta, bool tb)
 {
-    static int occ[2][2] = {{0, 0}, {0, 0}};
-    int &o = occ[ta][tb];
-    if (o == 0) {
+    // contexts are created from several host threads (batched builds, the server):
+    // the cached values are atomics, and a concurrent first query stores the same value
+    static std::atomic<int> occ[2][2];
+    std::atomic<int> &o = occ[ta][tb];
+    if (o.load(std::memory_order_relaxed) == 0) {
         int v = 0;
         cudaError_t e;
         if (!ta && !tb) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, gemm_kernel<TI, TC, false, false, TM, TN>, NT, 0);
@@ -241,23 +244,23 @@ int gemm_occupancy(bool ta, bool tb)
             cudaGetLastError();
             v = 1;
         }
-        o = std::max(v, 1);
+        o.store(std::max(v, 1), std::memory_order_relaxed);
     }
-    return o;
+    return o.load(std::memory_order_relaxed);
 }
 
 int sm_count()
 {
-    static int n = 0;
-    if (n == 0) {
+    static std::atomic<int> n{0};
+    if (n.load(std::memory_order_relaxed) == 0) {
         int dev = 0, v = 0;
         if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
             cudaGetLastError();
             v = 152;
         }
-        n = std::max(v, 1);
+        n.store(std::max(v, 1), std::memory_order_relaxed);
     }
-    return n;
+    return n.load(std::memory_order_relaxed);
 }
 
 template <typename TI, typename TC>

@@ -234,8 +234,8 @@ def run_native(args):
     fp64_peak = FP64_PEAK_TFLOPS
     traffic = None
     if name == "K_stage1" and p["launches"]:
-        # DRAM bytes per launch: the measured/algorithmic ratio of the ncu capture of this
-        # kernel (profiles/k_stage1_fp64_100atom.md) times the algorithmic bytes per launch
+        # DRAM bytes per launch: the DRAM/algorithmic byte ratio that one ncu capture of this
+        # kernel measured on the 100-atom case, times the algorithmic bytes per launch
         traffic = K_STAGE1_TRAFFIC_RATIO * p["bytes"] / p["launches"]
     roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
             "frac": achieved / fp64_peak, "traffic": traffic, "traffic_unit": "bytes per launch",
@@ -249,7 +249,7 @@ def run_native(args):
     cpu = cpu_baseline(mol, d, nmv / max(args.steps, 1)) if not args.no_cpu and world == 1 else None
     if cpu is not None:
         # the same sample with 4 threads, the thread count of the paper's CPU runs (Sec. 4, Table 2)
-        cpu["threads_4"] = cpu_baseline_threads(4, d, nmv / max(args.steps, 1))
+        cpu["threads_4"] = cpu_baseline_threads(4, d, nmv / max(args.steps, 1), case=args.case)
     mv_ms = sum(i.t_matvec_ms for i in infos)
     line = {
         "metric": METRIC, "value": nmv_all / (ms_max * 1e-3), "unit": "matvecs/s", "n_gpus": world,
@@ -431,18 +431,19 @@ def cpu_baseline(mol, d, nmv_per_step, budget_s=25.0):
             "s_per_step_extrapolated": t_step, "wall_s": time.perf_counter() - t_start}
 
 
-def cpu_baseline_threads(nthreads, d, nmv_per_step, budget_s=20.0, timeout_s=240.0):
+def cpu_baseline_threads(nthreads, d, nmv_per_step, budget_s=20.0, timeout_s=240.0, case="full"):
     """cpu_baseline in a child process whose OpenMP and BLAS pools have nthreads
-    threads (the pools are sized when the libraries load, hence the child)."""
+    threads (the pools are sized when the libraries load, hence the child); the
+    child rebuilds the molecule of the same case as the parent."""
     env = dict(os.environ, OMP_NUM_THREADS=str(nthreads), OPENBLAS_NUM_THREADS=str(nthreads),
                MKL_NUM_THREADS=str(nthreads))
     code = ("import json, sys; from types import SimpleNamespace; sys.path.insert(0, %r); import bench; "
             "d = SimpleNamespace(**json.loads(sys.argv[1])); "
-            "r = bench.cpu_baseline(bench.make_inputs('full'), d, float(sys.argv[2]), budget_s=float(sys.argv[3])); "
+            "r = bench.cpu_baseline(bench.make_inputs(sys.argv[4]), d, float(sys.argv[2]), budget_s=float(sys.argv[3])); "
             "print(json.dumps(r))") % os.path.dirname(os.path.abspath(__file__))
     dims = json.dumps({"nocc": d.nocc, "nvir": d.nvir, "naux_k": d.naux_k})
     try:
-        out = subprocess.run([sys.executable, "-c", code, dims, str(nmv_per_step), str(budget_s)], env=env,
+        out = subprocess.run([sys.executable, "-c", code, dims, str(nmv_per_step), str(budget_s), case], env=env,
                              capture_output=True, text=True, timeout=timeout_s)
         r = json.loads(out.stdout.strip().splitlines()[-1])
         r["cores"] = nthreads

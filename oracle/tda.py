@@ -129,9 +129,10 @@ def build(Z, xyz, shells, aux_exp, C, eps, nocc, cx, ka=1.0, kb=0.0, omega=0.0,
 
 def coulomb_ri(f: Factors) -> np.ndarray:
     """(ia|jb) = sum_PQ (ia|P) (P|Q)^-1 (Q|jb) as an (nov, nov) matrix."""
-    Y = f.Y.reshape(f.Y.shape[0], -1)
-    if Y.shape[0] == 0:
-        return np.zeros((Y.shape[1], Y.shape[1]))
+    n = f.nocc * f.nvir
+    if f.Y.shape[0] == 0:
+        return np.zeros((n, n))
+    Y = f.Y.reshape(f.Y.shape[0], n)
     return Y.T @ np.linalg.solve(f.GJ, Y)
 
 

@@ -101,7 +101,9 @@ void matvec_noalloc(tr_ctx *c, int m, const double *X, double *AX)
     TR_REQUIRE(per_vec <= avail, TR_EINVAL,
                "matvec_noalloc: problem too large for the 32 MiB static scratch (needs 2 N_auxJ + "
                "2 nocc_k nvir_k doubles per vector plus 65536 split-K doubles)");
-    const int mb = (int)std::min<size_t>({(size_t)m, (size_t)32, avail / per_vec});
+    // per_vec is 0 when there is neither a Coulomb nor an exchange term (no
+    // auxiliary functions and no active window): then only the diagonal runs
+    const int mb = (int)std::min<size_t>({(size_t)m, (size_t)32, per_vec ? avail / per_vec : (size_t)32});
     int npk = 0;
     if (kact) {
         const size_t used = (size_t)mb * (2 * (size_t)nJ + (size_t)oK * vK);

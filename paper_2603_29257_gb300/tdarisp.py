@@ -304,19 +304,53 @@ class Context:
                     "tr_get_tensor")
         return out
 
+    def _device_block(self, X, what):
+        """X as a contiguous float64 CUDA tensor of shape (m, nocc, nvir); raises
+        TDARispError before any pointer reaches the library otherwise."""
+        import torch
+        if not (_is_torch(X) and X.is_cuda):
+            raise TDARispError(TR_EINVAL, "%s: X must be a CUDA tensor" % what)
+        if X.dtype != torch.float64:
+            raise TDARispError(TR_EINVAL, "%s: X must be float64, got %s" % (what, X.dtype))
+        d = self.dims()
+        if X.dim() != 3 or tuple(X.shape[1:]) != (d.nocc, d.nvir):
+            raise TDARispError(TR_EINVAL, "%s: X must have shape (m, %d, %d), got %s"
+                               % (what, d.nocc, d.nvir, tuple(X.shape)))
+        return X.contiguous()
+
+    def _host_block(self, X, what):
+        """X as a contiguous float64 host array of shape (m, nocc, nvir)."""
+        Xn = _f64(X)
+        d = self.dims()
+        if Xn.ndim == 2 and Xn.shape[1] == d.nocc * d.nvir:
+            Xn = Xn.reshape(-1, d.nocc, d.nvir)
+        if Xn.ndim != 3 or Xn.shape[1:] != (d.nocc, d.nvir):
+            raise TDARispError(TR_EINVAL, "%s: X must have shape (m, %d, %d), got %s"
+                               % (what, d.nocc, d.nvir, Xn.shape))
+        return Xn
+
+    @staticmethod
+    def _check_out(out, X, what):
+        """out must be a contiguous CUDA float64 tensor shaped like X."""
+        if not (_is_torch(out) and out.is_cuda and out.dtype == X.dtype and out.shape == X.shape
+                and out.is_contiguous() and out.device == X.device):
+            raise TDARispError(TR_EINVAL, "%s: out must be a contiguous CUDA float64 tensor of shape %s "
+                                          "on the device of X" % (what, tuple(X.shape)))
+
     def matvec(self, X, out=None):
         """A X for X[m][nocc][nvir]: numpy in -> numpy out (host path, synchronous);
         CUDA tensor in -> CUDA tensor out (asynchronous on the context stream)."""
         if _is_torch(X) and X.is_cuda:
             import torch
-            X = X.contiguous()
+            X = self._device_block(X, "matvec")
             m = X.shape[0]
             if out is None:
                 out = torch.empty_like(X)
+            self._check_out(out, X, "matvec")
             rc = lib().tr_matvec(self._h, m, ct.c_void_p(X.data_ptr()), ct.c_void_p(out.data_ptr()), 1)
             self._check(rc, "tr_matvec")
             return out
-        Xn = _f64(X)
+        Xn = self._host_block(X, "matvec")
         m = Xn.shape[0]
         AX = np.empty_like(Xn)
         rc = lib().tr_matvec(self._h, m, Xn.ctypes.data_as(ct.c_void_p), AX.ctypes.data_as(ct.c_void_p), 0)
@@ -328,13 +362,13 @@ class Context:
         numpy in -> numpy out, CUDA tensor in -> CUDA tensors out (asynchronous)."""
         if _is_torch(X) and X.is_cuda:
             import torch
-            X = X.contiguous()
+            X = self._device_block(X, "matvec_tddft")
             P, M = torch.empty_like(X), torch.empty_like(X)
             rc = lib().tr_matvec_tddft(self._h, X.shape[0], ct.c_void_p(X.data_ptr()), ct.c_void_p(P.data_ptr()),
                                        ct.c_void_p(M.data_ptr()), 1)
             self._check(rc, "tr_matvec_tddft")
             return P, M
-        Xn = _f64(X)
+        Xn = self._host_block(X, "matvec_tddft")
         P, M = np.empty_like(Xn), np.empty_like(Xn)
         rc = lib().tr_matvec_tddft(self._h, Xn.shape[0], Xn.ctypes.data_as(ct.c_void_p),
                                    P.ctypes.data_as(ct.c_void_p), M.ctypes.data_as(ct.c_void_p), 0)
@@ -356,7 +390,10 @@ class Context:
         return om, P, M, rs, info
 
     def matvec_noalloc(self, X, out):
-        """A X into out (CUDA tensors) without any device allocation (static scratch)."""
+        """A X into out (CUDA tensors) without any device allocation (static scratch).
+        X and out: float64 CUDA tensors of shape (m, nocc, nvir); out contiguous."""
+        X = self._device_block(X, "matvec_noalloc")
+        self._check_out(out, X, "matvec_noalloc")
         rc = lib().tr_matvec_noalloc(self._h, X.shape[0], ct.c_void_p(X.data_ptr()), ct.c_void_p(out.data_ptr()))
         self._check(rc, "tr_matvec_noalloc")
         return out

@@ -27,3 +27,12 @@ def test_failing_child_reports_unavailable():
     r = bench.cpu_baseline_threads(4, SimpleNamespace(nocc=0, nvir=0, naux_k=0), 259.0, budget_s=1.0,
                                    timeout_s=120.0)
     assert set(r) == {"unavailable"}
+
+
+def test_child_sample_uses_the_parents_case():
+    # the 100-atom profiling case (50 heavy + 50 H, nao 950, nocc 190): the child
+    # must build that molecule, not the 200-atom one, for these dimensions to fit
+    r = bench.cpu_baseline_threads(4, SimpleNamespace(nocc=190, nvir=760, naux_k=50), 100.0, budget_s=1.0,
+                                   case="small")
+    assert "unavailable" not in r, r
+    assert "of the 50 heavy atoms" in r["sample"]

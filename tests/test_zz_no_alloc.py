@@ -32,10 +32,17 @@ def _rel(a, b):
     return float((a - b).abs().max() / b.abs().max())
 
 
-@pytest.mark.parametrize("case", ["small", "chunked"])
+@pytest.mark.parametrize("case", ["small", "no_aux", "chunked"])
 def test_noalloc_matches_matvec_on_two_calls(case):
     if case == "small":
         mol = synth.make_molecule(seed=7, n_heavy=3, n_h=3)
+        opts = dict(cx=0.25)
+        ms = (5, 3)
+    elif case == "no_aux":
+        # no auxiliary functions at all: neither a Coulomb nor an exchange term,
+        # the product is the diagonal alone (no scratch is needed per vector)
+        mol = synth.make_molecule(seed=7, n_heavy=3, n_h=3)
+        mol.aux_exp = np.zeros_like(mol.aux_exp)
         opts = dict(cx=0.25)
         ms = (5, 3)
     else:
@@ -62,3 +69,13 @@ def test_noalloc_rejects_bad_calls():
     X = torch.zeros((2, mol.nocc, mol.nvir), dtype=torch.float64, device="cuda")
     with pytest.raises(tdarisp.TDARispError):
         c.matvec_noalloc(X, X)  # output overlaps input
+    with pytest.raises(tdarisp.TDARispError):
+        c.matvec_noalloc(X.float(), torch.empty_like(X).float())  # not float64
+    with pytest.raises(tdarisp.TDARispError):
+        c.matvec_noalloc(X[:, :, :-1], torch.empty_like(X)[:, :, :-1])  # wrong shape
+    with pytest.raises(tdarisp.TDARispError):
+        c.matvec_noalloc(X, torch.empty((2, mol.nocc * mol.nvir), dtype=torch.float64, device="cuda"))
+    with pytest.raises(tdarisp.TDARispError):
+        c.matvec_noalloc(X, torch.empty_like(X).transpose(1, 2).contiguous().transpose(1, 2))  # strided out
+    with pytest.raises(tdarisp.TDARispError):
+        c.matvec_noalloc(X.cpu(), torch.empty_like(X))  # host input

@@ -53,6 +53,10 @@ extern "C" {
 #define TR_ECUDA (-3)     /* CUDA runtime error */
 #define TR_ENOCONV (-4)   /* Davidson hit max_iter; outputs hold the best estimates */
 #define TR_ENOTPD (-5)    /* an auxiliary metric is not positive definite */
+#define TR_ETIMEOUT (-6)  /* a bounded device wait ran out (tensor-core pipelines, see
+                             tr_options.wait_cycles); the kernel gave up, awaited its own
+                             copies and products in flight and freed its tensor memory, so
+                             the context stays usable; the outputs of that call are invalid */
 
 #define TR_FP64 0   /* every step in FP64 */
 #define TR_MIXED 1  /* MO tensors and J/K contractions in FP32 / 3xTF32 tensor cores;
@@ -118,6 +122,17 @@ typedef struct {
                             (ib|ja) products run as 7-slice tensor-core products too);
                             not available in tr_solve_batch or the server (TR_EINVAL);
                             tr_matvec and tr_matvec_noalloc still give A X */
+    long long wait_cycles; /* bounded device waits: SM clock cycles before a pipeline wait of
+                            the tensor-core kernels (TR_MIXED exchange stages, every sliced
+                            product of TR_FP64_TC and of the sliced MO transforms) gives up
+                            (0: 2e9, about 1 s).  The call that finds a wait ran out returns
+                            TR_ETIMEOUT: tr_build, tr_solve, and tr_matvec / tr_matvec_tddft
+                            with host buffers (with device buffers they are asynchronous and
+                            report nothing).  Must be >= 0 */
+    int wait_test;       /* test of the bounded waits only (0 default): 1 = the tensor-core
+                            kernels load no operands, so their first pipeline wait can only
+                            end by running out (after wait_cycles); the calls above then
+                            return TR_ETIMEOUT.  Nothing is faulted or left in flight */
 } tr_options;
 
 typedef struct {

@@ -54,6 +54,15 @@ void normalise_options(tr_options *o)
     if (o->matvec_ws_bytes == 0) o->matvec_ws_bytes = (size_t)4 << 30;
 }
 
+// the bounded waits of the context's tensor-core launches follow its options
+void apply_wait_options(tr_ctx *c)
+{
+    TR_REQUIRE(c->opt.wait_cycles >= 0, TR_EINVAL, "options: wait_cycles must be >= 0");
+    TR_REQUIRE(c->opt.wait_test == 0 || c->opt.wait_test == 1, TR_EINVAL, "options: wait_test must be 0 or 1");
+    c->prof.wait_cycles = c->opt.wait_cycles;
+    c->prof.wait_stall = c->opt.wait_test;
+}
+
 }  // namespace
 
 extern "C" {
@@ -87,6 +96,7 @@ int tr_create(tr_ctx **out, const tr_options *opt, void *cuda_stream)
                    "create: full TDDFT (tddft = 1) needs precision TR_FP64 or TR_FP64_TC");
         c->opt = *opt;
         normalise_options(&c->opt);
+        apply_wait_options(c);
         c->st = (cudaStream_t)cuda_stream;
         TR_CUDA(cudaGetDevice(&c->device));
         tr::gemm_prepare();
@@ -125,9 +135,12 @@ int tr_set_options(tr_ctx *ctx, const tr_options *opt)
                        opt->window_ev != ctx->opt.window_ev || opt->aux_on_h != ctx->opt.aux_on_h ||
                        opt->screen != ctx->opt.screen || opt->xform_slices != ctx->opt.xform_slices ||
                        opt->j_ao != ctx->opt.j_ao || opt->tddft != ctx->opt.tddft;
+        TR_REQUIRE(opt->wait_cycles >= 0 && (opt->wait_test == 0 || opt->wait_test == 1), TR_EINVAL,
+                   "set_options: wait_cycles must be >= 0 and wait_test 0 or 1");
         size_t limit = ctx->budget.limit;
         ctx->opt = *opt;
         normalise_options(&ctx->opt);
+        apply_wait_options(ctx);
         if (opt->hbm_budget) ctx->budget.limit = opt->hbm_budget;
         else ctx->budget.limit = limit;
         if (rebuild) {
@@ -290,7 +303,8 @@ int tr_matvec(tr_ctx *ctx, int m, const double *X, double *AX, int on_device)
         int tc_err = 0;
         TR_CUDA(cudaMemcpyAsync(&tc_err, ctx->flag.p + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
         TR_CUDA(cudaStreamSynchronize(ctx->st));
-        TR_REQUIRE(!tc_err, TR_ECUDA, "matvec: a tensor-core pipeline wait timed out");
+        TR_REQUIRE(!tc_err, TR_ETIMEOUT,
+                   "matvec: a tensor-core pipeline wait ran out (code " + std::to_string(tc_err) + ")");
         return TR_OK;
     });
 }
@@ -337,7 +351,8 @@ int tr_matvec_tddft(tr_ctx *ctx, int m, const double *X, double *ApBX, double *A
         int tc_err = 0;
         TR_CUDA(cudaMemcpyAsync(&tc_err, ctx->flag.p + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
         TR_CUDA(cudaStreamSynchronize(ctx->st));
-        TR_REQUIRE(!tc_err, TR_ECUDA, "matvec_tddft: a tensor-core pipeline wait timed out");
+        TR_REQUIRE(!tc_err, TR_ETIMEOUT,
+                   "matvec_tddft: a tensor-core pipeline wait ran out (code " + std::to_string(tc_err) + ")");
         return TR_OK;
     });
 }

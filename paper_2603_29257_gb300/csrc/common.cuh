@@ -92,6 +92,12 @@ struct ProfRecord {
 struct Prof {
     bool enabled = false;
     long launches = 0;
+    // bounded waits of the tensor-core pipelines launched through this recorder
+    // (the context's tr_options.wait_cycles and wait_test): SM cycles before a
+    // pipeline wait gives up (0: the kernels' default, about 1 s), and the test
+    // switch under which the producer issues no operand loads
+    long long wait_cycles = 0;
+    int wait_stall = 0;
     std::vector<std::string> names;
     std::vector<ProfRecord> pending;
     std::vector<cudaEvent_t> pool;

@@ -948,13 +948,16 @@ struct Dav {
             t_oth += elapsed(ev.e[1], ev.e[2]);
             eig_timed = false;
         }
+        // a product whose pipeline wait ran out left invalid data behind: report that
+        // first, before what the invalid data may have tripped downstream
+        TR_REQUIRE(!h_fl[1] || h_fl[1] == TC_ERR_W_RANGE, TR_ETIMEOUT,
+                   "solve: a tensor-core pipeline wait ran out (code " + std::to_string(h_fl[1]) + ")");
         TR_REQUIRE(!rpa || h_fl[4] == 0, TR_ECUDA,
                    h_fl[4] < 0 ? "solve: non-positive Omega^2 in the projected full TDDFT problem"
                                : "solve: A - B projected on the subspace is not positive definite");
         TR_REQUIRE(!h_fl[0], TR_ECUDA, "solve: subspace eigensolver did not converge");
         TR_REQUIRE(h_fl[1] != TC_ERR_W_RANGE, TR_ECUDA,
                    "solve: a product block exceeded the exponent range fixed for the sliced W");
-        TR_REQUIRE(!h_fl[1], TR_ECUDA, "solve: a tensor-core pipeline wait timed out");
         unconv.clear();
         for (int r = 0; r < n; ++r)
             if (!(h_rn[r] < tol)) unconv.push_back(r);

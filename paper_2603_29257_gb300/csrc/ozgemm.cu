@@ -28,9 +28,10 @@
 // drain the accumulators after each chunk (warp w reads TMEM lanes
 // 32 (w mod 4) .. +31, half of the columns) and write the scaled FP64 tile at
 // the end.  With S <= 4 the accumulators are double-buffered, so that draining
-// one chunk overlaps the products of the next.  Every wait is bounded: a timeout records an
-// error code in *err and the CTA goes to its teardown, which waits (bounded)
-// for its own copies in flight and always frees tensor memory.
+// one chunk overlaps the products of the next.  Every wait is bounded (about
+// 1 s, or the launch's own limit): a timeout records an error code in *err and
+// the CTA goes to its teardown, which waits (bounded) for its own copies and
+// products in flight and always frees tensor memory.
 #include "ozgemm.cuh"
 #include "tcptx.cuh"
 
@@ -85,6 +86,8 @@ struct OzArgs {
     double alpha;
     int accumulate;                // d += (instead of =)
     int *err;
+    long long wait;                // pipeline wait limit in SM cycles
+    int stall;                     // test of the bounded waits: the producer issues no loads
 };
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
@@ -171,17 +174,19 @@ __global__ void __launch_bounds__(320, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     float *tbuf = (float *)(smem + ST * C::STAGE);
-    // barriers: full[ST], empty[ST], acc_full[NBUF], acc_empty[NBUF]
+    // barriers: full[ST], empty[ST], acc_full[NBUF], acc_empty[NBUF], drain
     uint64_t *bars = (uint64_t *)(smem + ST * C::STAGE + OZ_TBYTES);
-    uint32_t *tslot = (uint32_t *)(bars + 2 * ST + 2 * C::NBUF);
+    uint32_t *tslot = (uint32_t *)(bars + 2 * ST + 2 * C::NBUF + 1);
     const uint32_t FULL = sa(&bars[0]), EMPTY = sa(&bars[ST]);
     const uint32_t ACCF = sa(&bars[2 * ST]), ACCE = sa(&bars[2 * ST + C::NBUF]);
+    const uint32_t DRAIN = sa(&bars[2 * ST + 2 * C::NBUF]);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long ntiles = g.ntiles;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2 * ST + C::NBUF; ++i) bar_init(sa(&bars[i]), 1);
         for (int i = 0; i < C::NBUF; ++i) bar_init(ACCE + 8 * i, 8);  // one arrival per epilogue warp
+        bar_init(DRAIN, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -197,12 +202,12 @@ __global__ void __launch_bounds__(320, 1)
     if (warp == 0) {
         if (lane == 0) {
             long long gk = 0;
-            bool ok = true;
+            bool ok = !g.stall;
             for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 const OzTile u = oz_tile(g, t, BN);
                 for (int kt = 0; kt < u.nkb; ++kt) {
                     const int s = (int)(gk % ST);
-                    if (gk >= ST && !bar_wait(EMPTY + 8 * s, (uint32_t)(((gk / ST) - 1) & 1), g.err, 11)) {
+                    if (gk >= ST && !bar_wait(EMPTY + 8 * s, (uint32_t)(((gk / ST) - 1) & 1), g.err, 11, g.wait)) {
                         ok = false;
                         break;
                     }
@@ -237,13 +242,13 @@ __global__ void __launch_bounds__(320, 1)
                     const int s = (int)(gk % ST), kc = kt % C::CK, buf = (int)(gch % C::NBUF);
                     if (kc == 0 && gch >= C::NBUF) {
                         // the epilogue has drained the chunk that last used this accumulator set
-                        if (!bar_wait(ACCE + 8 * buf, (uint32_t)(((gch / C::NBUF) - 1) & 1), g.err, 12)) {
+                        if (!bar_wait(ACCE + 8 * buf, (uint32_t)(((gch / C::NBUF) - 1) & 1), g.err, 12, g.wait)) {
                             ok = false;
                             break;
                         }
                         fence_after();
                     }
-                    if (!bar_wait(FULL + 8 * s, (uint32_t)((gk / ST) & 1), g.err, 13)) {
+                    if (!bar_wait(FULL + 8 * s, (uint32_t)((gk / ST) & 1), g.err, 13, g.wait)) {
                         ok = false;
                         break;
                     }
@@ -275,6 +280,10 @@ __global__ void __launch_bounds__(320, 1)
                     }
                 }
             }
+            // every product issued has completed before tensor memory is freed, also
+            // when a wait gave up and the epilogue no longer consumes them
+            commit(DRAIN);
+            bar_wait(DRAIN, 0, g.err, 16);
         }
         __syncwarp();
     } else {
@@ -292,7 +301,7 @@ __global__ void __launch_bounds__(320, 1)
             for (int j = 0; j < C::NC; ++j) hi[j] = lo[j] = 0.f;
             for (int ch = 0; ch < nch; ++ch) {
                 const int buf = (int)(gch % C::NBUF);
-                if (!bar_wait(ACCF + 8 * buf, (uint32_t)((gch / C::NBUF) & 1), g.err, 14)) {
+                if (!bar_wait(ACCF + 8 * buf, (uint32_t)((gch / C::NBUF) & 1), g.err, 14, g.wait)) {
                     ok = false;
                     break;
                 }
@@ -698,6 +707,8 @@ void oz_gemm(Prof &prof, cudaStream_t st, const char *name, const OzMat &A, long
     g.alpha = out.alpha;
     g.accumulate = out.accumulate ? 1 : 0;
     g.err = err;
+    g.wait = prof.wait_cycles > 0 ? prof.wait_cycles : ptx::WAIT_CYCLES;
+    g.stall = prof.wait_stall;
     g.ntn = cdiv(N, BN);
     g.ntm = cdiv(M, 128);
     g.ntiles = (long long)g.ntn * g.ntm * nb * ksplit;

@@ -10,8 +10,9 @@
 // products of the next tile go on in the other set.  With three products
 // (hi*hi + hi*lo + lo*hi) the result carries close to FP32 accuracy.  Stage
 // and accumulator barrier phases run on across tiles.  Every mbarrier wait
-// gives up after ~1 s: it records an error code in *err and the warp skips to
-// the teardown (copies in flight are awaited, tensor memory is always freed).
+// gives up after ~1 s (or the launch's own limit): it records an error code in
+// *err and the warp skips to the teardown, where the copies and products still
+// in flight are awaited before tensor memory is freed.
 #include "tcgemm.cuh"
 #include "tcptx.cuh"
 
@@ -33,6 +34,8 @@ struct TcArgs {
     long long a0, a1, a2, c0, c1, c2;
     TcOut out;
     int *err;
+    long long wait;               // pipeline wait limit in SM cycles
+    int stall;                    // test of the bounded waits: the producer issues no loads
 };
 
 using namespace ptx;
@@ -92,11 +95,12 @@ __global__ void __launch_bounds__(192, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     float *tbuf = (float *)(smem + ST * C::STAGE);
-    // barriers: full[ST], empty[ST], acc_full[2], acc_empty[2]
+    // barriers: full[ST], empty[ST], acc_full[2], acc_empty[2], drain
     uint64_t *bars = (uint64_t *)(smem + ST * C::STAGE + C::TBYTES);
-    uint32_t *tslot = (uint32_t *)(bars + 2 * ST + 4);
+    uint32_t *tslot = (uint32_t *)(bars + 2 * ST + 5);
     const uint32_t FULL = sa(&bars[0]), EMPTY = sa(&bars[ST]);
     const uint32_t ACCF = sa(&bars[2 * ST]), ACCE = sa(&bars[2 * ST + 2]);
+    const uint32_t DRAIN = sa(&bars[2 * ST + 4]);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = (g.K + BKF - 1) / BKF;
     const long long ntiles = g.ntiles;
@@ -104,6 +108,7 @@ __global__ void __launch_bounds__(192, 1)
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2 * ST + 2; ++i) bar_init(sa(&bars[i]), 1);
         for (int i = 0; i < 2; ++i) bar_init(ACCE + 8 * i, 4);  // one arrival per epilogue warp
+        bar_init(DRAIN, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -120,12 +125,12 @@ __global__ void __launch_bounds__(192, 1)
     if (warp == 0) {
         if (lane == 0) {
             long long gk = 0;
-            bool ok = true;
+            bool ok = !g.stall;
             for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 const TcTile u = tc_tile(g, t, BN);
                 for (int kt = 0; kt < nk; ++kt) {
                     const int s = (int)(gk % ST);
-                    if (gk >= ST && !bar_wait(EMPTY + 8 * s, (uint32_t)(((gk / ST) - 1) & 1), g.err, 1)) {
+                    if (gk >= ST && !bar_wait(EMPTY + 8 * s, (uint32_t)(((gk / ST) - 1) & 1), g.err, 1, g.wait)) {
                         ok = false;
                         break;
                     }
@@ -159,7 +164,7 @@ __global__ void __launch_bounds__(192, 1)
                 const int buf = (int)(tc & 1);
                 if (tc >= 2) {
                     // the epilogue has drained the tile that last used this accumulator set
-                    if (!bar_wait(ACCE + 8 * buf, (uint32_t)(((tc / 2) - 1) & 1), g.err, 6)) {
+                    if (!bar_wait(ACCE + 8 * buf, (uint32_t)(((tc / 2) - 1) & 1), g.err, 6, g.wait)) {
                         ok = false;
                         break;
                     }
@@ -168,7 +173,7 @@ __global__ void __launch_bounds__(192, 1)
                 const uint32_t acc = tmem + (uint32_t)(buf * BN);
                 for (int kt = 0; kt < nk; ++kt) {
                     const int s = (int)(gk % ST);
-                    if (!bar_wait(FULL + 8 * s, (uint32_t)((gk / ST) & 1), g.err, 2)) {
+                    if (!bar_wait(FULL + 8 * s, (uint32_t)((gk / ST) & 1), g.err, 2, g.wait)) {
                         ok = false;
                         break;
                     }
@@ -191,6 +196,10 @@ __global__ void __launch_bounds__(192, 1)
                 if (!ok) break;
                 commit(ACCF + 8 * buf);
             }
+            // every product issued has completed before tensor memory is freed, also
+            // when a wait gave up and the epilogue no longer consumes them
+            commit(DRAIN);
+            bar_wait(DRAIN, 0, g.err, 7);
         }
         __syncwarp();
     } else {
@@ -202,7 +211,7 @@ __global__ void __launch_bounds__(192, 1)
         for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++tc) {
             const TcTile u = tc_tile(g, t, BN);
             const int buf = (int)(tc & 1);
-            if (!bar_wait(ACCF + 8 * buf, (uint32_t)((tc / 2) & 1), g.err, 3)) break;
+            if (!bar_wait(ACCF + 8 * buf, (uint32_t)((tc / 2) & 1), g.err, 3, g.wait)) break;
             fence_after();
             const long long base = o.s1 * u.b1 + o.s2 * u.b2;
             const int row = u.m0 + 32 * quarter + lane;
@@ -396,6 +405,8 @@ void tc_gemm(Prof &prof, cudaStream_t st, const char *name, int nsplit, const Tc
     g.c2 = c2;
     g.out = out;
     g.err = err;
+    g.wait = prof.wait_cycles > 0 ? prof.wait_cycles : ptx::WAIT_CYCLES;
+    g.stall = prof.wait_stall;
     g.ntn = cdiv(N, BN);
     g.ntm = cdiv(M, BM);
     g.ntiles = (long long)g.ntn * g.ntm * n1 * n2;

@@ -12,7 +12,9 @@
 namespace tr {
 namespace ptx {
 
-// mbarrier waits give up after this many SM cycles (~1 s at 2 GHz)
+// mbarrier waits give up after this many SM cycles (~1 s at 2 GHz) unless the
+// launch passes a limit of its own; the waits of a kernel's teardown (copies and
+// products still in flight) always use this one
 constexpr long long WAIT_CYCLES = 2000000000LL;
 
 __device__ __forceinline__ uint32_t sa(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -29,8 +31,9 @@ __device__ __forceinline__ void bar_arrive(uint32_t a)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
 }
-// wait for the phase of the given parity; false (and *err = code) after WAIT_CYCLES
-__device__ __forceinline__ bool bar_wait(uint32_t a, uint32_t parity, int *err, int code)
+// wait for the phase of the given parity; false (and *err = code) after limit cycles
+__device__ __forceinline__ bool bar_wait(uint32_t a, uint32_t parity, int *err, int code,
+                                         long long limit = WAIT_CYCLES)
 {
     const long long t0 = clock64();
     while (true) {
@@ -41,7 +44,7 @@ __device__ __forceinline__ bool bar_wait(uint32_t a, uint32_t parity, int *err, 
             : "r"(a), "r"(parity)
             : "memory");
         if (ok) return true;
-        if (clock64() - t0 > WAIT_CYCLES) {
+        if (clock64() - t0 > limit) {
             atomicCAS(err, 0, code);
             return false;
         }

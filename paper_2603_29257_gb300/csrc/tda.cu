@@ -534,7 +534,7 @@ static void transforms_oz(tr_ctx *c, DevBuf<double> &Iij, DevBuf<double> *Iia, i
     int h = 0;
     TR_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     TR_CUDA(cudaStreamSynchronize(st));
-    TR_REQUIRE(h == 0, TR_ECUDA, "build: tensor-core transform pipeline timed out (code " + std::to_string(h) + ")");
+    TR_REQUIRE(h == 0, TR_ETIMEOUT, "build: a tensor-core transform pipeline wait ran out (code " + std::to_string(h) + ")");
 }
 
 void build(tr_ctx *c)

@@ -15,7 +15,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtdarisp.so")
 
-TR_OK, TR_EINVAL, TR_ENOMEM, TR_ECUDA, TR_ENOCONV, TR_ENOTPD = 0, -1, -2, -3, -4, -5
+TR_OK, TR_EINVAL, TR_ENOMEM, TR_ECUDA, TR_ENOCONV, TR_ENOTPD, TR_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 
 _dp = ct.POINTER(ct.c_double)
 _ip = ct.POINTER(ct.c_int)
@@ -34,7 +34,8 @@ class Options(ct.Structure):
                 ("screen", ct.c_double), ("hbm_budget", ct.c_size_t),
                 ("aux_chunk_bytes", ct.c_size_t), ("host_budget", ct.c_size_t),
                 ("dav_dev_rows", ct.c_int), ("matvec_ws_bytes", ct.c_size_t),
-                ("xform_slices", ct.c_int), ("j_ao", ct.c_int), ("tddft", ct.c_int)]
+                ("xform_slices", ct.c_int), ("j_ao", ct.c_int), ("tddft", ct.c_int),
+                ("wait_cycles", ct.c_longlong), ("wait_test", ct.c_int)]
 
 
 class Dims(ct.Structure):

@@ -16,7 +16,16 @@ oscillator_24atom.json: the oscillator strengths f = 2/3 Omega |mu|^2 (Sec. 2,
 Eqs. oscillator_strength and transition) of those states, TDA (unit-norm X) and
 full TDDFT (X+Y with (X+Y).(X-Y) = 1), dipoles about the coordinate origin.
 
-Run: python tests/golden/make_golden.py [tda|tddft|props]   (default: tda)
+omega_200atom_rsh.json: the timed 200-atom case (seed 2, 100 heavy + 100 H,
+nao 1900, nocc 380; K operator (0.222 + 0.778 erf(0.2 r))/r, c_x = 1, 40 eV
+window): the 15 lowest excitation energies from the oracle's matrix-free block
+Davidson (Sec. 3.3) with a block of 30 and residual 1e-7, and the oracle's A X
+for the two seeded unit trial vectors synth.random_trial_block(2024, 2, ...)
+on sampled entries: one whole occupied row i per vector and 128 seeded (i, a)
+positions.  Also the wall time of the run and the threads it used (the
+machine that wrote the file is named in it).
+
+Run: python tests/golden/make_golden.py [tda|tddft|props|cfg2]   (default: tda)
 """
 from __future__ import annotations
 
@@ -91,6 +100,61 @@ def main_props():
         json.dump(out, fh, indent=1)
 
 
+# the timed 200-atom case: range-separated exchange, 15 states, block 30
+CFG2 = dict(cx=1.0, ka=0.222, kb=0.778, omega=0.2)
+CFG2_X_SEED = 2024
+CFG2_ROWS = (7, 301)          # whole occupied rows i of AX, one per vector
+CFG2_SAMPLES = 128            # seeded (i, a) positions per vector
+
+
+def cfg2_sample_positions(nocc, nvir):
+    """The seeded (i, a) positions stored per vector (shared with the GPU test)."""
+    rng = np.random.default_rng(CFG2_X_SEED + 1)
+    return rng.integers(0, nocc, size=CFG2_SAMPLES), rng.integers(0, nvir, size=CFG2_SAMPLES)
+
+
+def main_cfg2():
+    import platform
+    import time
+    t_all = time.perf_counter()
+    mol = synth.molecule_200()
+    t0 = time.perf_counter()
+    f = tda.build(mol.Z, mol.xyz, mol.shells, mol.aux_exp, mol.C, mol.eps, mol.nocc, CFG2["cx"],
+                  CFG2["ka"], CFG2["kb"], CFG2["omega"], window_ev=40.0)
+    t_build = time.perf_counter() - t0
+    print("build %.1f s" % t_build, flush=True)
+    X = synth.random_trial_block(CFG2_X_SEED, 2, mol.nocc, mol.nvir)
+    t0 = time.perf_counter()
+    AX = tda.matvec(f, X)
+    t_mv = time.perf_counter() - t0
+    ii, aa = cfg2_sample_positions(mol.nocc, mol.nvir)
+    t0 = time.perf_counter()
+    res = tda.solve(f, 15, block=30, tol=1e-7)
+    t_solve = time.perf_counter() - t0
+    print("solve %.1f s, %d iterations, %d matvecs" % (t_solve, res.niter, res.nmatvec), flush=True)
+    out = {"source": "oracle matrix-free block Davidson (Sec. 3.3) of the TDA-risp matrix (Sec. 2, Eq. "
+                     "TDA-risp) with range-separated exchange (Sec. 3.2, Eqs. RSH and K_mia_RSH), and the "
+                     "oracle's matrix-free A X",
+           "molecule": "synth.molecule_200(): seed 2, 100 heavy + 100 H, nao 1900, nocc 380",
+           "options": CFG2, "window_ev": 40.0, "nstates": 15, "block": 30, "tol": 1e-7,
+           "omega": [float(x) for x in res.omega], "resid": [float(x) for x in res.resid],
+           "converged": bool(res.converged), "niter": int(res.niter), "nmatvec": int(res.nmatvec),
+           "nrestart": int(res.nrestart),
+           "ax": {"x_seed": CFG2_X_SEED, "m": 2,
+                  "generator": "synth.random_trial_block(x_seed, m, nocc, nvir)",
+                  "rows": [{"vector": k, "i": CFG2_ROWS[k], "values": [float(v) for v in AX[k, CFG2_ROWS[k]]]}
+                           for k in range(2)],
+                  "samples": {"i": [int(i) for i in ii], "a": [int(a) for a in aa],
+                              "values": [[float(AX[k, i, a]) for i, a in zip(ii, aa)] for k in range(2)]},
+                  "max_abs": [float(np.abs(AX[k]).max()) for k in range(2)]},
+           "timing": {"build_s": t_build, "matvec_2_vectors_s": t_mv, "solve_s": t_solve,
+                      "total_s": time.perf_counter() - t_all, "threads": os.cpu_count(),
+                      "machine": "%s, %s" % (platform.machine(), platform.processor() or "cpu")}}
+    with open(os.path.join(HERE, "omega_200atom_rsh.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+    print(res.omega)
+
+
 if __name__ == "__main__":
     which = sys.argv[1] if len(sys.argv) > 1 else "tda"
-    {"tda": main, "tddft": main_tddft, "props": main_props}[which]()
+    {"tda": main, "tddft": main_tddft, "props": main_props, "cfg2": main_cfg2}[which]()

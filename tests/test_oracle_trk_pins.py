@@ -102,3 +102,29 @@ def test_coupled_full_tddft_keeps_the_trk_sum(aux):
     assert abs(f.sum() - 2.0 * len(OMEGAS)) < 1e-10
     # individual strengths move with the coupling; only their sum is fixed
     assert np.abs(f[f > 1e-6] - 2.0 / 3.0).max() > 1e-4
+
+
+@pytest.mark.parametrize("a,b,centre,origin", [(0.3, 1.7, (1.5, -0.4, 2.0), (0.0, 0.0, 0.0)),
+                                               (2.2, 0.45, (-3.0, 0.7, 0.1), (0.9, 1.1, -2.0))])
+def test_s_to_p_dipole_of_unequal_exponents_by_hand(a, b, centre, origin):
+    """One centre A, an occupied s primitive of exponent a and a virtual p_x
+    primitive of exponent b (orthogonal by parity, so C is the diagonal of their
+    norms).  By hand: <s|x - O_x|p_x> = N_s N_p int (x - A_x)^2 e^{-(a+b)|r-A|^2}
+    = N_s N_p (pi/(a+b))^{3/2} / (2(a+b)); the A_x - O_x part multiplies <s|p_x> = 0.
+    The singlet excitation with unit X then has mu_x = sqrt(2) r and
+    f = 2/3 Omega 2 r^2 for any Omega."""
+    ns = (2.0 * a / math.pi) ** 0.75
+    npx = (2.0 * b / math.pi) ** 0.75 * 2.0 * math.sqrt(b)
+    shells = [synth.Shell(0, 0, np.array([a]), np.array([1.0])),
+              synth.Shell(0, 1, np.array([b]), np.array([1.0]))]
+    xyz = np.array([centre])
+    C = np.diag([ns, npx, npx, npx])
+    r = ns * npx * (math.pi / (a + b)) ** 1.5 / (2.0 * (a + b))
+    X = np.zeros((1, 1, 3))
+    X[0, 0, 0] = 1.0
+    mu = tda.transition_dipoles(xyz, shells, C, 1, X, origin=origin)
+    assert abs(mu[0, 0] - math.sqrt(2.0) * r) < 1e-14 * r
+    assert np.abs(mu[0, 1:]).max() < 1e-15
+    Om = 0.37
+    f = tda.oscillator_strengths([Om], mu)
+    assert abs(f[0] - 2.0 / 3.0 * Om * 2.0 * r * r) < 1e-14

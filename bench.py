@@ -181,13 +181,14 @@ def run_native(args):
         b0.record(stream)
         ctx.build()
         b1.record(stream)
-        info = ctx.solve(want_x=True, device=True)[3]
+        om_last, _, _, info = ctx.solve(want_x=True, device=True)
         marks.append((b0, b1))
         nmv += info.nmatvec
         infos.append(info)
     t1.record(stream)
     barrier()
     clk = clocks.stop()
+    om_last = om_last.cpu().numpy()
     ms = t0.elapsed_time(t1)
     launches = ctx.launch_count() - launches0
     prof = ctx.profile_get()
@@ -203,25 +204,33 @@ def run_native(args):
             return ctx.solve(want_x=True, device=False)[3]
         host_step()
         barrier()
+        e2e_steps = min(args.steps, E2E_STEPS)
         te0 = time.perf_counter()
         nmv_e = 0
-        for _ in range(args.steps):
+        for _ in range(e2e_steps):
             nmv_e += host_step().nmatvec
         barrier()
         te = time.perf_counter() - te0
         te_max, nmv_e_all = reduce_over_ranks(te, nmv_e, "cuda")
         e2e = {"value": nmv_e_all / te_max, "unit": "matvecs/s",
                "h2d_bytes_per_step": int(mol.C.nbytes + mol.eps.nbytes),
-               "d2h_bytes_per_step": int(8 * OPTS["nstates"] * (1 + d.nocc * d.nvir) + 8 * OPTS["nstates"])}
+               "d2h_bytes_per_step": int(8 * OPTS["nstates"] * (1 + d.nocc * d.nvir) + 8 * OPTS["nstates"]),
+               "steps": e2e_steps}
 
+    # the oracle's roots of this workload (stored by the golden script from the CPU oracle alone)
+    gold = oracle_omega_200() if args.case == "full" else None
     # reduced-precision form on the same workload (NEXT: FP32 tensors, 3xTF32 K on tcgen05)
     mixed = fp64tc = None
     if not (args.no_mixed and args.no_fp64tc):
         om64 = fp64_reference_omega(tdarisp, mol, C_dev, eps_dev, stream)
         if not args.no_mixed:
-            mixed = run_form(args, tdarisp, mol, C_dev, eps_dev, stream, barrier, 1, om64)
+            mixed = run_form(args, tdarisp, mol, C_dev, eps_dev, stream, barrier, 1, om64, gold)
         if not args.no_fp64tc:
-            fp64tc = run_form(args, tdarisp, mol, C_dev, eps_dev, stream, barrier, 2, om64)
+            fp64tc = run_form(args, tdarisp, mol, C_dev, eps_dev, stream, barrier, 2, om64, gold)
+    # the other configurations of the workload family (rank 0 of a single-GPU run)
+    configs = None
+    if not args.no_configs and world == 1:
+        configs = run_configs(args, tdarisp, stream)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -269,8 +278,9 @@ def run_native(args):
                         "note": "Davidson matvec time only (events around each block product)"},
         "davidson": {"niter": [i.niter for i in infos], "nmatvec": [i.nmatvec for i in infos],
                      "restarts": [i.nrestart for i in infos], "converged": [i.converged for i in infos]},
+        "per_state_dOmega_vs_oracle_Ha": per_state_error(om_last, gold),
         "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "mixed_form": mixed,
-        "fp64_tensor_core_form": fp64tc,
+        "fp64_tensor_core_form": fp64tc, "configs": configs,
         "gpu_launches": launches, "clocks": clk,
     }
     for extra in (mixed, fp64tc):
@@ -307,6 +317,31 @@ def fp64_reference_omega(tdarisp, mol, C_dev, eps_dev, stream):
     return om64
 
 
+# at most this many steps of the host-buffer end-to-end leg (each repeats a whole step)
+E2E_STEPS = 5
+
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def oracle_omega_200():
+    """The 15 lowest roots of this workload from the CPU oracle's Davidson at
+    residual 1e-7 (written by tests/golden/make_golden.py cfg2, which calls only
+    the oracle)."""
+    try:
+        with open(os.path.join(GOLDEN, "omega_200atom_rsh.json")) as fh:
+            return np.array(json.load(fh)["omega"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def per_state_error(om, gold):
+    """|Omega_k - Omega_k(oracle)| per state, Hartree (None without the oracle's values)."""
+    if gold is None or om is None:
+        return None
+    n = min(len(om), len(gold))
+    return [float(x) for x in np.abs(np.asarray(om)[:n] - gold[:n])]
+
+
 FORMS = {
     1: dict(kind="reduced precision", products=3,
             dtype="f32/tf32x3 (tensor cores) + f64 (integrals, transforms, metrics, Davidson)",
@@ -317,7 +352,7 @@ FORMS = {
 }
 
 
-def run_form(args, tdarisp, mol, C_dev, eps_dev, stream, barrier, precision, om64):
+def run_form(args, tdarisp, mol, C_dev, eps_dev, stream, barrier, precision, om64, gold=None):
     """Same workload in another form (precision 1 or 2); compared with the FP64 form."""
     import torch
     form = FORMS[precision]
@@ -376,6 +411,7 @@ def run_form(args, tdarisp, mol, C_dev, eps_dev, stream, barrier, precision, om6
         "dtype": form["dtype"],
         "max_abs_dOmega_vs_fp64_form_Ha": float(np.abs(om - om64).max()),
         "per_state_dOmega_vs_fp64_form_Ha": [float(x) for x in np.abs(om - om64)],
+        "per_state_dOmega_vs_oracle_Ha": per_state_error(om, gold),
         "davidson": {"niter": [i.niter for i in infos], "nmatvec": [i.nmatvec for i in infos],
                      "ms_per_solve": {"matvec": statistics.mean(i.t_matvec_ms for i in infos),
                                       "orthogonalise": statistics.mean(i.t_ortho_ms for i in infos),
@@ -652,20 +688,15 @@ def run_tddft(args):
     print(json.dumps(line))
 
 
-def run_batched(args):
+def batched_figures(tdarisp, stream, steps, warmup):
     """Batched form: 64 molecules (20-150 atoms, 10 states each) in the reduced-precision
     form, all Davidson solves advanced in lockstep with one graph launch of all
-    products per step; against 64 sequential plain FP64 solves."""
+    products per step; against 64 sequential reduced-precision and 64 sequential
+    plain FP64 solves.  Host wall clock with the device synchronised."""
     import torch
-    torch.cuda.set_device(0)
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_2603_29257_gb300 import tdarisp
     t0 = time.perf_counter()
     mols = batched_molecules()
     gen_s = time.perf_counter() - t0
-    torch.zeros(1, device="cuda")
-    stream = torch.cuda.current_stream()
 
     def make(precision):
         cs = []
@@ -675,20 +706,16 @@ def run_batched(args):
             cs.append(c)
         return cs
 
-    # batched, reduced precision: concurrent builds, lockstep solves
-    def build_all(cs):
-        tdarisp.build_batch(cs)
-
     cs = make(1)
-    for _ in range(max(args.warmup, 1)):
-        build_all(cs)
+    for _ in range(max(warmup, 1)):
+        tdarisp.build_batch(cs)
         tdarisp.solve_batch(cs, autotune=True)
     torch.cuda.synchronize()
     times, nmv_b, res_b, tb = [], 0, None, []
-    for _ in range(args.steps):
+    for _ in range(max(steps, 1)):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        build_all(cs)
+        tdarisp.build_batch(cs)
         torch.cuda.synchronize()
         tb.append(time.perf_counter() - t)
         res_b = tdarisp.solve_batch(cs, autotune=True)
@@ -703,10 +730,12 @@ def run_batched(args):
     cs = make(1)
     torch.cuda.synchronize()
     t = time.perf_counter()
-    nmv_m = 0
+    nmv_m, om_m = 0, []
     for c in cs:
         c.build()
-        nmv_m += c.solve(want_x=True)[3].nmatvec
+        om, X, rs, info = c.solve(want_x=True)
+        nmv_m += info.nmatvec
+        om_m.append(om)
     torch.cuda.synchronize()
     t_seq_mixed = time.perf_counter() - t
     for c in cs:
@@ -726,22 +755,124 @@ def run_batched(args):
     for c in cs:
         c.close()
     dmax = max(float(np.abs(r[0] - o).max()) for r, o in zip(res_b, om_f))
+    dalone = max(float(np.abs(r[0] - o).max()) for r, o in zip(res_b, om_m))
     natoms = [len(m.Z) for m in mols]
-    line = {"metric": "TDA-risp matvecs/s, batched form (64 molecules, build + solve)",
-            "value": nmv_b / t_batch, "unit": "matvecs/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": max(args.warmup, 1), "ms_per_step": 1e3 * t_batch, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32/tf32x3 + f64", "data": "synthetic",
-            "config": {"workload": "64 seeded molecules (seeds 1000-1063), atoms log-uniform 20-150 "
-                                   "(%d-%d, %d total), 10 states each, global hybrid c_x 0.25, 40 eV window, "
-                                   "tol 1e-5" % (min(natoms), max(natoms), sum(natoms)),
-                       "timing": "host wall clock around build of all 64 contexts + tr_solve_batch"},
+    return {"workload": "64 seeded molecules (seeds 1000-1063), atoms log-uniform 20-150 "
+                        "(%d-%d, %d total), 10 states each, global hybrid c_x 0.25, 40 eV window, "
+                        "tol 1e-5, reduced precision" % (min(natoms), max(natoms), sum(natoms)),
+            "timing": "host wall clock around the build of all 64 contexts + tr_solve_batch, device synchronised",
+            "steps": max(steps, 1), "warmup": max(warmup, 1),
+            "value": nmv_b / t_batch, "unit": "matvecs/s",
             "batched_s": t_batch, "batched_build_s": t_build, "batched_solve_s": t_batch - t_build,
             "sequential_mixed_s": t_seq_mixed, "sequential_fp64_s": t_seq_fp64,
             "speedup_vs_sequential_fp64": t_seq_fp64 / t_batch,
             "speedup_vs_sequential_mixed": t_seq_mixed / t_batch,
             "matvecs": {"batched": nmv_b, "sequential_mixed": nmv_m, "sequential_fp64": nmv_f},
-            "max_abs_dOmega_vs_fp64_Ha": dmax, "generation_s": gen_s}
+            "max_abs_dOmega_vs_fp64_Ha": dmax, "max_abs_dOmega_vs_alone_Ha": dalone, "generation_s": gen_s}
+
+
+def run_batched(args):
+    """--workload batched: the batched-form figures as a line of their own."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_29257_gb300 import tdarisp
+    torch.zeros(1, device="cuda")
+    f = batched_figures(tdarisp, torch.cuda.current_stream(), args.steps, args.warmup)
+    line = {"metric": "TDA-risp matvecs/s, batched form (64 molecules, build + solve)",
+            "value": f["value"], "unit": "matvecs/s", "n_gpus": 1, "steps": f["steps"],
+            "warmup": f["warmup"], "ms_per_step": 1e3 * f["batched_s"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32/tf32x3 + f64", "data": "synthetic",
+            "config": {"workload": f["workload"], "timing": f["timing"]}}
+    line.update({k: v for k, v in f.items() if k not in ("workload", "timing", "value", "unit", "steps", "warmup")})
     print(json.dumps(line))
+
+
+# the 24-atom molecule: global hybrid, 5 states to residual 1e-6
+SMALL_OPTS = dict(cx=0.25, k_alpha=1.0, k_beta=0.0, omega=0.0, window_ev=40.0, nstates=5, tol=1e-6,
+                  max_iter=200)
+
+
+def small_form(tdarisp, stream, mol, precision, gold, steps, warmup):
+    """Build + solve of the 24-atom molecule in one form, timed with CUDA events
+    over `steps` whole steps; per-state error against the oracle's dense roots."""
+    import torch
+    from paper_2603_29257_gb300 import synth
+    ctx = tdarisp.Context(stream=stream.cuda_stream, precision=precision, **SMALL_OPTS)
+    ctx.set_molecule_from(mol)
+    for _ in range(max(warmup, 1)):
+        ctx.build()
+        ctx.solve(want_x=True, device=True)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    nmv, infos, om = 0, [], None
+    for _ in range(steps):
+        ctx.build()
+        om, X, rs, info = ctx.solve(want_x=True, device=True)
+        nmv += info.nmatvec
+        infos.append(info)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    # the block product alone: 10 products of one block of 10 seeded vectors
+    d = ctx.dims()
+    X = torch.from_numpy(synth.random_trial_block(5, 10, d.nocc, d.nvir)).cuda()
+    AX = torch.empty_like(X)
+    for _ in range(3):
+        ctx.matvec(X, out=AX)
+    torch.cuda.synchronize()
+    m0 = torch.cuda.Event(enable_timing=True)
+    m1 = torch.cuda.Event(enable_timing=True)
+    m0.record(stream)
+    for _ in range(10):
+        ctx.matvec(X, out=AX)
+    m1.record(stream)
+    torch.cuda.synchronize()
+    mv_ms = m0.elapsed_time(m1)
+    ctx.close()
+    om = om.cpu().numpy()
+    err = np.abs(om - gold)
+    return {"value": nmv / (ms * 1e-3), "unit": "matvecs/s", "s_to_states": ms / steps * 1e-3,
+            "steps": steps, "warmup": max(warmup, 1),
+            "niter": [i.niter for i in infos][-1], "nmatvec": [i.nmatvec for i in infos][-1],
+            "block_products_alone": {"value": 100 / (mv_ms * 1e-3), "unit": "matvecs/s",
+                                     "note": "10 products of one block of 10 resident vectors"},
+            "per_state_dOmega_vs_oracle_Ha": [float(x) for x in err],
+            "max_abs_dOmega_vs_oracle_Ha": float(err.max()), "omega_Ha": [float(x) for x in om]}
+
+
+def run_configs(args, tdarisp, stream):
+    """The other configurations of the workload family, each reported beside the
+    headline: the 24-atom molecule in the FP64 form (config 1) and in the
+    reduced-precision and tensor-core forms (config 3), and the batched form of
+    64 molecules (config 4)."""
+    from paper_2603_29257_gb300 import synth
+    out = {}
+    mol = synth.molecule_24()
+    with open(os.path.join(GOLDEN, "omega_24atom.json")) as fh:
+        gold = np.array(json.load(fh)["cases"]["hybrid"]["omega"])
+    desc = ("24-atom seeded molecule (10 C/N/O + 14 H, nao 210, nocc 42), global hybrid c_x 0.25, 40 eV "
+            "window, 5 states, residual 1e-6; per-state error against the oracle's dense eigh")
+    f64 = small_form(tdarisp, stream, mol, 0, gold, SMALL_STEPS, 2)
+    out["config1_fp64_24atom"] = dict(workload=desc, dtype="f64", **f64)
+    c3 = {"workload": desc}
+    for precision, key in ((1, "reduced_precision"), (2, "fp64_tensor_cores")):
+        r = small_form(tdarisp, stream, mol, precision, gold, SMALL_STEPS, 2)
+        r["dtype"] = FORMS[precision]["dtype"]
+        r["speedup_vs_fp64_s_to_states"] = f64["s_to_states"] / r["s_to_states"]
+        r["speedup_vs_fp64_value"] = r["value"] / f64["value"]
+        c3[key] = r
+    out["config3_forms_24atom"] = c3
+    if not args.no_batched:
+        out["config4_batched"] = batched_figures(tdarisp, stream, 1, 1)
+    return out
+
+
+# whole build + solve steps of the 24-atom configurations
+SMALL_STEPS = 20
 
 
 SERVE_OPTS = dict(cx=0.25, k_alpha=1.0, k_beta=0.0, omega=0.0, window_ev=40.0, tol=1e-5, max_iter=200)
@@ -854,6 +985,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the reduced-precision form")
     ap.add_argument("--no-fp64tc", action="store_true", help="skip the FP64 form on the tensor cores")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other configurations (24-atom forms, batched, serving) of the default run")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched form in the default run")
     ap.add_argument("--workload", default="fp64-200", choices=["fp64-200", "batched", "serve", "matvec", "tddft"],
                     help="batched: 64 molecules in the reduced-precision batched form; "
                          "serve: a Poisson request stream through the serving runtime; "

@@ -117,7 +117,8 @@ def chain_geometry(rng, n_heavy, n_h, max_tries=2000):
         bond = rng.uniform(1.35, 1.45)
         ang = math.radians(rng.uniform(105.0, 125.0))
         pos.append(pos[1] + bond * np.array([-math.cos(ang), math.sin(ang), 0.0]))
-    for k in range(3, n_heavy):
+    k, stuck = 3, 0
+    while k < n_heavy:
         for _ in range(max_tries):
             bond = rng.uniform(1.35, 1.45)
             ang = math.radians(rng.uniform(105.0, 125.0))
@@ -127,8 +128,16 @@ def chain_geometry(rng, n_heavy, n_h, max_tries=2000):
             if d.min() >= 2.0:
                 break
         else:
-            raise RuntimeError("chain placement failed")
+            # the chain end is trapped (long chains): regrow its last few atoms
+            stuck += 1
+            if stuck > 1000 or k <= 3:
+                raise RuntimeError("chain placement failed")
+            back = min(k - 3, 4)
+            del pos[k - back:]
+            k -= back
+            continue
         pos.append(p)
+        k += 1
     heavy = np.asarray(pos)
     hpos = []
     for h in range(n_h):

@@ -113,6 +113,8 @@ struct tr_ctx {
     tr::OzMat dz_Wm, dz_Wmt;
     tr::DevBuf<int> dz_eWm;
     tr::DevBuf<int> idx_dev;
+    tr::DevBuf<double> gsel;  // candidates of the initial-guess selection
+    double *h_pin = nullptr;  // pinned: residual norms, Ritz values, flags of the Davidson
     // spill of V/W rows to pinned host memory: staging slots, copy stream, events
     tr::DevBuf<double> stage;
     cudaStream_t cst = nullptr;
@@ -130,6 +132,7 @@ struct tr_ctx {
         }
         for (auto e : sev)
             if (e) cudaEventDestroy(e);
+        if (h_pin) cudaFreeHost(h_pin);
     }
 };
 

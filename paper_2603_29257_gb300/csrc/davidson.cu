@@ -37,6 +37,83 @@ __global__ void set_unit_rows(double *V, const int *idx, int n, long long nov)
     if (r < n) V[(long long)r * nov + idx[r]] = 1.0;
 }
 
+// Selection of the initial guess: the b smallest keys (value, index) in
+// lexicographic order (equal values: lower index first), the order a stable
+// sort of the diagonal gives.  Stage 1: every CTA takes b times the smallest key
+// of its segment above the last one taken (values v[t], indices t, or the
+// candidates of stage 1 with their indices ix); stage 2 is the same over the
+// candidates in one CTA.  Exhausted segments add (+inf, -1).
+constexpr int SEL_THREADS = 1024, SEL_MAX_B = 512;
+
+__device__ __forceinline__ bool key_less(double va, double ia, double vb, double ib)
+{
+    return va < vb || (va == vb && ia < ib);
+}
+
+__global__ void __launch_bounds__(SEL_THREADS)
+    select_smallest(const double *__restrict__ v, const double *__restrict__ ix, long long n, long long seg, int b,
+                    double *__restrict__ out_v, double *__restrict__ out_i)
+{
+    __shared__ double sv[SEL_THREADS / 32], si[SEL_THREADS / 32];
+    __shared__ double last_v, last_i;
+    const long long s0 = (long long)blockIdx.x * seg, s1 = min(n, s0 + seg);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        last_v = -INFINITY;
+        last_i = -2.0;
+    }
+    __syncthreads();
+    for (int r = 0; r < b; ++r) {
+        const double lv = last_v, li = last_i;
+        double bv = INFINITY, bi = -1.0;
+        for (long long t = s0 + threadIdx.x; t < s1; t += SEL_THREADS) {
+            const double x = v[t], xi = ix ? ix[t] : (double)t;
+            if (xi >= 0.0 && key_less(lv, li, x, xi) && key_less(x, xi, bv, bi < 0.0 ? INFINITY : bi)) {
+                bv = x;
+                bi = xi;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, bv, o), oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (oi >= 0.0 && (bi < 0.0 || key_less(ov, oi, bv, bi))) {
+                bv = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            sv[warp] = bv;
+            si[warp] = bi;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            bv = lane < SEL_THREADS / 32 ? sv[lane] : INFINITY;
+            bi = lane < SEL_THREADS / 32 ? si[lane] : -1.0;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_down_sync(0xffffffffu, bv, o), oi = __shfl_down_sync(0xffffffffu, bi, o);
+                if (oi >= 0.0 && (bi < 0.0 || key_less(ov, oi, bv, bi))) {
+                    bv = ov;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                out_v[(long long)blockIdx.x * b + r] = bv;
+                out_i[(long long)blockIdx.x * b + r] = bi;
+                if (bi >= 0.0) {
+                    last_v = bv;
+                    last_i = bi;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void sel_to_int(const double *__restrict__ ix, int b, int *__restrict__ idx)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < b) idx[r] = (int)ix[r];
+}
+
 // H[k0+i][j] = H[j][k0+i] = (A1[i][j] + A2[i][j]) / 2 for i < p, j < k0 + p; each
 // unordered pair written once.
 __global__ void h_insert(double *H, int ldh, const double *A1, const double *A2, int p, int k, int k0)
@@ -476,9 +553,11 @@ struct Dav {
                        std::to_string(pmax + nr) + ")");
         max_iter = c->opt.max_iter > 0 ? c->opt.max_iter : 200;
         tol = c->opt.tol;
-        TR_CUDA(cudaHostAlloc((void **)&h_rn, sizeof(double) * n, cudaHostAllocDefault));
-        TR_CUDA(cudaHostAlloc((void **)&h_th, sizeof(double) * n, cudaHostAllocDefault));
-        TR_CUDA(cudaHostAlloc((void **)&h_fl, sizeof(int) * 5, cudaHostAllocDefault));
+        // pinned host copies, allocated once per context (64 states at most)
+        if (!c->h_pin) TR_CUDA(cudaHostAlloc((void **)&c->h_pin, sizeof(double) * 132, cudaHostAllocDefault));
+        h_rn = c->h_pin;
+        h_th = c->h_pin + 64;
+        h_fl = (int *)(c->h_pin + 128);
         std::memset(h_fl, 0, sizeof(int) * 5);
 
         reserve_matvec(c, pmax);
@@ -498,12 +577,12 @@ struct Dav {
         TR_CUDA(cudaMemsetAsync(c->Tn.p, 0, sizeof(double) * c->Tn.n, st));
 
         // how many V/W rows fit in HBM; the rest spill to pinned host memory
-        c->V.release();
-        c->W.release();
-        c->Wm.release();
+        // (the rows of the previous solve count as free: kept when the size is unchanged)
+        if (!rpa) c->Wm.release();
         cs = std::max(8, pmax);  // staging rows per chunk
         const int nstore = rpa ? 3 : 2;  // row stores: V, W (and Wm)
-        const long long avail = (long long)c->budget.limit - (long long)c->budget.used;
+        const long long held = (long long)sizeof(double) * (long long)(c->V.n + c->W.n + c->Wm.n);
+        const long long avail = (long long)c->budget.limit - (long long)c->budget.used + held;
         const long long small = (rpa ? 11LL : 5LL) * maxsp * maxsp * 8 + 2LL * maxsp * pmax * 8 + (64LL << 20);
         kd = (int)std::max<long long>(0, (avail - small) / (long long)(nstore * rowb));
         if (kd < maxsp) kd = (int)std::max<long long>(0, (avail - small - 2LL * cs * rowb) / (long long)(nstore * rowb));
@@ -613,9 +692,6 @@ struct Dav {
         // queued copies into the pinned buffers (error paths) finish first
         cudaStreamSynchronize(st);
         if (c->cst) cudaStreamSynchronize(c->cst);
-        if (h_rn) cudaFreeHost(h_rn);
-        if (h_th) cudaFreeHost(h_th);
-        if (h_fl) cudaFreeHost(h_fl);
     }
     Dav(const Dav &) = delete;
     Dav &operator=(const Dav &) = delete;
@@ -776,13 +852,29 @@ struct Dav {
     // initial guess: unit vectors on the b0 smallest e_a - e_i (ties: lower index)
     void guess()
     {
-        std::vector<double> Dh(nov);
-        TR_CUDA(cudaMemcpyAsync(Dh.data(), c->D.p, sizeof(double) * nov, cudaMemcpyDeviceToHost, st));
-        TR_CUDA(cudaStreamSynchronize(st));
-        std::vector<int> order(nov);
-        std::iota(order.begin(), order.end(), 0);
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return Dh[a] < Dh[b]; });
-        TR_CUDA(cudaMemcpyAsync(c->idx_dev.p, order.data(), sizeof(int) * b0, cudaMemcpyHostToDevice, st));
+        if (b0 <= SEL_MAX_B) {
+            // on the device, no host round trip: segments of >= 4096 entries, at most 1024 of them
+            const long long seg = std::max<long long>(4096, (nov + 1023) / 1024);
+            const int nseg = (int)((nov + seg - 1) / seg);
+            c->gsel.reserve((size_t)2 * nseg * b0 + 2 * (size_t)b0, &c->budget, "guess selection");
+            double *cv = c->gsel.p, *ci = cv + (size_t)nseg * b0;
+            double *fv = ci + (size_t)nseg * b0, *fi = fv + b0;
+            TR_LAUNCH(c->prof, st, "guess_select", 8.0 * nov, 0,
+                      select_smallest<<<nseg, SEL_THREADS, 0, st>>>(c->D.p, nullptr, nov, seg, b0, cv, ci));
+            TR_LAUNCH(c->prof, st, "guess_select", 0, 0,
+                      select_smallest<<<1, SEL_THREADS, 0, st>>>(cv, ci, (long long)nseg * b0, (long long)nseg * b0,
+                                                                 b0, fv, fi));
+            TR_LAUNCH(c->prof, st, "guess_select", 0, 0, sel_to_int<<<cdiv(b0, 64), 64, 0, st>>>(fi, b0, c->idx_dev.p));
+        } else {
+            std::vector<double> Dh(nov);
+            TR_CUDA(cudaMemcpyAsync(Dh.data(), c->D.p, sizeof(double) * nov, cudaMemcpyDeviceToHost, st));
+            TR_CUDA(cudaStreamSynchronize(st));
+            std::vector<int> order(nov);
+            std::iota(order.begin(), order.end(), 0);
+            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return Dh[a] < Dh[b]; });
+            TR_CUDA(cudaMemcpyAsync(c->idx_dev.p, order.data(), sizeof(int) * b0, cudaMemcpyHostToDevice, st));
+            TR_CUDA(cudaStreamSynchronize(st));
+        }
         TR_CUDA(cudaMemsetAsync(c->Tn.p, 0, sizeof(double) * (size_t)b0 * nov, st));
         TR_LAUNCH(c->prof, st, "set_unit", 0, 0, set_unit_rows<<<cdiv(b0, 64), 64, 0, st>>>(c->Tn.p, c->idx_dev.p, b0, nov));
         pend_k0 = 0;

@@ -96,3 +96,7 @@ def test_200atom_omega_against_oracle(mol, gold, precision):
           " ".join("%.1e" % e for e in err), "| %d iterations, %d matvecs" % (info.niter, info.nmatvec))
     assert info.converged
     assert np.all(err < bar), err
+    if precision in (0, 2):
+        # the same Davidson (guess, preconditioner, Gram-Schmidt, restart) in FP64-level
+        # arithmetic takes the oracle's path: same iterations and products
+        assert (info.niter, info.nmatvec) == (gold["niter"], gold["nmatvec"])

@@ -868,7 +868,13 @@ def run_configs(args, tdarisp, stream):
     out["config3_forms_24atom"] = c3
     if not args.no_batched:
         out["config4_batched"] = batched_figures(tdarisp, stream, 1, 1)
+    if not args.no_serve:
+        out["config5_serve"] = serve_figures(tdarisp, SERVE_REQUESTS, 1, loads=(0.7,))
     return out
+
+
+# requests of the serving form in the default run (the offered load 0.7 and saturated)
+SERVE_REQUESTS = 40
 
 
 # whole build + solve steps of the 24-atom configurations
@@ -878,18 +884,24 @@ SMALL_STEPS = 20
 SERVE_OPTS = dict(cx=0.25, k_alpha=1.0, k_beta=0.0, omega=0.0, window_ev=40.0, tol=1e-5, max_iter=200)
 
 
-def serve_stream(count, seed0=5000, arrival_seed=5001, lo=30, hi=150):
+def serve_stream(count, seed0=5000, arrival_seed=5001, lo=30, hi=600, large=0, large_atoms=1500):
     """Seeded request stream: molecule k from seed seed0+k with atoms log-uniform in
-    [lo, hi]; states U{5..15} and unit-rate exponential gaps from arrival_seed."""
+    [lo, hi] (the last `large` requests, placed at seeded positions, have
+    large_atoms atoms); states U{5..15} and unit-rate exponential gaps from
+    arrival_seed.  Molecules above synth.LARGE_ATOMS atoms get their dense linear
+    algebra on the GPU."""
     from paper_2603_29257_gb300 import synth
     rng = np.random.default_rng(arrival_seed)
     nst = rng.integers(5, 16, size=count)
     gaps = rng.exponential(1.0, size=count)
+    big = set(int(x) for x in rng.choice(count, size=min(large, count), replace=False)) if large else set()
     mols = []
     for k in range(count):
         r = np.random.default_rng(seed0 + k)
         natoms = int(round(np.exp(r.uniform(np.log(lo), np.log(hi)))))
-        mols.append(synth.molecule_by_atoms(seed0 + k, natoms))
+        if k in big:
+            natoms = large_atoms
+        mols.append(synth.molecule_by_atoms(seed0 + k, natoms, device="auto"))
     return mols, [int(n) for n in nst], np.cumsum(gaps) - gaps[0]
 
 
@@ -913,27 +925,26 @@ def _replay(tdarisp, mols, nst, arrivals, precision, max_active, build_threads):
     span = max(r["t_done"] for r in out) - min(r["t_submit"] for r in out)
     return out, {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
                  "mean_ms": 1e3 * float(lat.mean()), "molecules_per_s": len(out) / span, "span_s": span,
-                 "matvecs": int(sum(r["nmatvec"] for r in out))}
+                 "matvecs": int(sum(r["nmatvec"] for r in out)), "j_ao_requests": int(sum(r["j_ao"] for r in out))}
 
 
-def run_serve(args):
+def serve_figures(tdarisp, requests, warmup, loads=(0.3, 0.7, 0.9), fp64_subsample=8, fp64_max_atoms=150,
+                  hi=600, large=0, large_atoms=1500):
     """Serving form: a seeded Poisson stream of requests served by the continuous-
-    batching server in the reduced-precision form at offered loads 0.3/0.7/0.9 of
-    the rate one request served alone sustains, and saturated (all at once);
-    against the plain FP64 form served one request at a time on the same stream."""
-    import torch
-    torch.cuda.set_device(0)
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_2603_29257_gb300 import tdarisp
+    batching server in the reduced-precision form at offered loads rho (rate x mean
+    service time of a request served alone) and saturated (all at once); against the
+    plain FP64 form served one request at a time on a seeded subsample of the
+    requests with at most fp64_max_atoms atoms (the FP64 form grows as N^4: about
+    12 s at 200 atoms)."""
     t = time.perf_counter()
-    mols, nst, unit_gaps = serve_stream(args.requests)
+    mols, nst, unit_gaps = serve_stream(requests, hi=hi, large=large, large_atoms=large_atoms)
     gen_s = time.perf_counter() - t
-    torch.zeros(1, device="cuda")
     R = len(mols)
+    natoms = np.array([len(m.Z) for m in mols])
     # warm-up: module loading, kernel attributes, graph paths
-    for _ in range(max(args.warmup, 1)):
-        _replay(tdarisp, mols[:4], nst[:4], np.zeros(4), 1, 64, 4)
+    small = [k for k in range(R) if natoms[k] <= 150][:4]
+    for _ in range(max(warmup, 1)):
+        _replay(tdarisp, [mols[k] for k in small], [nst[k] for k in small], np.zeros(len(small)), 1, 64, 4)
     # service time of each request served alone (reduced precision)
     alone = []
     with tdarisp.Server(max_active=64, autotune=True) as srv:
@@ -942,36 +953,56 @@ def run_serve(args):
             r = srv.drain()[0]
             alone.append(r["t_done"] - r["t_submit"])
     s_mean = float(np.mean(alone))
-    loads = {}
-    res07 = None
-    for rho in (0.3, 0.7, 0.9):
+    out_loads = {}
+    ref = None
+    for rho in loads:
         res, st = _replay(tdarisp, mols, nst, unit_gaps * s_mean / rho, 1, 64, 4)
         st["lambda_per_s"] = rho / s_mean
-        loads[str(rho)] = st
-        if rho == 0.7:
-            res07 = res
+        out_loads[str(rho)] = st
+        ref = ref or res
     res_sat, sat = _replay(tdarisp, mols, nst, np.zeros(R), 1, 64, 4)
-    # plain FP64 form, one request at a time, same stream
-    res_f, f07 = _replay(tdarisp, mols, nst, unit_gaps * s_mean / 0.7, 0, 1, 1)
-    _, fsat = _replay(tdarisp, mols, nst, np.zeros(R), 0, 1, 1)
-    dmax = max(float(np.abs(a["omega"] - b["omega"]).max()) for a, b in zip(res07, res_f))
-    dmax_sat = max(float(np.abs(a["omega"] - b["omega"]).max()) for a, b in zip(res_sat, res_f))
-    natoms = [len(m.Z) for m in mols]
+    # plain FP64 form one request at a time (saturated) on a seeded subsample
+    pool = [k for k in range(R) if natoms[k] <= fp64_max_atoms]
+    pick = sorted(int(x) for x in np.random.default_rng(5002).choice(pool, size=min(fp64_subsample, len(pool)),
+                                                                         replace=False))
+    res_f, fsat = _replay(tdarisp, [mols[k] for k in pick], [nst[k] for k in pick], np.zeros(len(pick)), 0, 1, 1)
+    dmax = max(float(np.abs(res_sat[k]["omega"] - f["omega"]).max()) for k, f in zip(pick, res_f))
+    if ref is not None:
+        dmax = max(dmax, max(float(np.abs(ref[k]["omega"] - f["omega"]).max()) for k, f in zip(pick, res_f)))
+    # the same subsample through the server in the reduced-precision form, one at a time
+    _, msub = _replay(tdarisp, [mols[k] for k in pick], [nst[k] for k in pick], np.zeros(len(pick)), 1, 1, 1)
+    return {"workload": "%d seeded requests (molecule seeds 5000-%d, arrival seed 5001), atoms log-uniform "
+                        "30-%d (%d-%d, median %d)%s, states U{5..15}, global hybrid c_x 0.25, 40 eV window, "
+                        "tol 1e-5; Poisson arrivals at load rho = lambda x mean service time alone"
+                        % (R, 5000 + R - 1, hi, natoms.min(), natoms.max(), int(np.median(natoms)),
+                           (", %d of %d atoms" % (large, large_atoms)) if large else ""),
+            "timing": "server clock (host steady clock) from submit to result posted",
+            "requests": R, "natoms": [int(x) for x in natoms], "nstates": nst,
+            "service_alone_mean_ms": 1e3 * s_mean, "service_alone_max_ms": 1e3 * float(np.max(alone)),
+            "loads": out_loads, "saturated": sat,
+            "fp64_one_at_a_time": {"subsample": pick, "saturated": fsat,
+                                   "reduced_precision_one_at_a_time": msub},
+            "throughput_vs_fp64_one_at_a_time_on_subsample": msub["molecules_per_s"] / fsat["molecules_per_s"],
+            "max_abs_dOmega_vs_fp64_Ha": dmax, "generation_s": gen_s}
+
+
+def run_serve(args):
+    """--workload serve: the serving figures as a line of their own."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_29257_gb300 import tdarisp
+    torch.zeros(1, device="cuda")
+    f = serve_figures(tdarisp, args.requests, args.warmup, hi=args.serve_max_atoms, large=args.serve_large,
+                      large_atoms=args.serve_large_atoms)
+    key = "0.7" if "0.7" in f["loads"] else sorted(f["loads"])[0]
     line = {"metric": "TDA-risp serve p50/p99 ms @1e-5 Ha and molecules/s, serving form",
-            "value": loads["0.7"]["p99_ms"], "unit": "ms (p99 latency at load 0.7)", "n_gpus": 1,
-            "steps": 1, "warmup": max(args.warmup, 1), "ms_per_step": 1e3 * loads["0.7"]["span_s"],
+            "value": f["loads"][key]["p99_ms"], "unit": "ms (p99 latency at load %s)" % key, "n_gpus": 1,
+            "steps": 1, "warmup": max(args.warmup, 1), "ms_per_step": 1e3 * f["loads"][key]["span_s"],
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32/tf32x3 + f64",
-            "data": "synthetic",
-            "config": {"workload": "%d seeded requests (molecule seeds 5000-%d, arrival seed 5001), atoms "
-                                   "log-uniform 30-150 (%d-%d), states U{5..15}, global hybrid c_x 0.25, "
-                                   "40 eV window, tol 1e-5; Poisson arrivals at load rho = lambda x mean "
-                                   "service time alone" % (R, 5000 + R - 1, min(natoms), max(natoms)),
-                       "timing": "server clock (host steady clock) from submit to result posted"},
-            "service_alone_mean_ms": 1e3 * s_mean, "loads": loads, "saturated": sat,
-            "fp64_one_at_a_time": {"0.7": f07, "saturated": fsat},
-            "throughput_vs_fp64_saturated": sat["molecules_per_s"] / fsat["molecules_per_s"],
-            "p99_vs_fp64_at_0.7": f07["p99_ms"] / loads["0.7"]["p99_ms"],
-            "max_abs_dOmega_vs_fp64_Ha": max(dmax, dmax_sat), "generation_s": gen_s}
+            "data": "synthetic", "config": {"workload": f["workload"], "timing": f["timing"]}}
+    line.update({k: v for k, v in f.items() if k not in ("workload", "timing")})
     print(json.dumps(line))
 
 
@@ -994,6 +1025,10 @@ def main():
                          "matvec: block products alone in the form --precision (profiling case); "
                          "tddft: full TDDFT-risp products and solve")
     ap.add_argument("--requests", type=int, default=64, help="requests of the serve workload")
+    ap.add_argument("--serve-max-atoms", type=int, default=600, help="largest molecule of the serve request sizes")
+    ap.add_argument("--serve-large", type=int, default=0, help="requests of --serve-large-atoms atoms in the stream")
+    ap.add_argument("--serve-large-atoms", type=int, default=1500, help="atoms of the large serve requests")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving form in the default run")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
                     help="form of the matvec and tddft workloads: 0 FP64, 1 reduced precision (matvec only), "
                          "2 FP64 on the tensor cores")

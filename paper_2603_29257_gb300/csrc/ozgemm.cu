@@ -97,30 +97,38 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, 
                  : "memory");
 }
 
-// v * 2^n by adding n to the exponent field (integer work: the FP64 pipe of
-// this GPU is narrow); scalbn only for zero/subnormal inputs or results out of
-// the normal range
-__device__ __forceinline__ double scale_pow2(double v, int n)
-{
-    const long long b = __double_as_longlong(v);
-    const int ex = (int)((b >> 52) & 0x7FF);
-    if ((b << 1) == 0) return v;
-    if (ex == 0 || ex + n <= 0 || ex + n >= 2047) return scalbn(v, n);
-    return __longlong_as_double(b + ((long long)n << 52));
-}
-
-// float to double by rebuilding the bit pattern (integer work; the float to
-// double conversion instruction would use the narrow FP64 pipe); zero and
-// subnormal floats take the ordinary conversion
-__device__ __forceinline__ double widen(float f)
+// The FP64 value of a float scaled by 2^n, as a bit pattern built with integer
+// work (the FP64 pipe of this GPU is narrow): exact for zero and for normal
+// floats whose scaled exponent stays in the normal FP64 range (ok = true).
+__device__ __forceinline__ unsigned long long f2d_bits(float f, int n, bool &ok)
 {
     const unsigned b = __float_as_uint(f);
     const unsigned ex = (b >> 23) & 0xFF;
-    if (ex == 0 || ex == 0xFF) return (double)f;
-    const unsigned long long d = ((unsigned long long)(b >> 31) << 63) |
-                                 ((unsigned long long)(ex + (1023 - 127)) << 52) |
-                                 ((unsigned long long)(b & 0x7FFFFF) << 29);
-    return __longlong_as_double((long long)d);
+    const unsigned long long sgn = (unsigned long long)(b >> 31) << 63;
+    const int e = (int)ex + (1023 - 127) + n;
+    const bool zero = (b << 1) == 0;
+    ok = zero || (ex != 0 && ex != 0xFF && e > 0 && e < 2047);
+    return zero ? sgn : (sgn | ((unsigned long long)(unsigned)e << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29));
+}
+
+// (hi + lo) 2^n for the rare pairs f2d_bits cannot take (subnormal, infinite or
+// out-of-range results): an out-of-line call, so that the common path carries
+// none of its FP64 instructions
+__device__ __noinline__ double oz_pair_slow(float hi, float lo, int n)
+{
+    return scalbn((double)hi + (double)lo, n);
+}
+
+// (hi + lo) 2^n rounded once to FP64: both floats scaled exactly on their bit
+// patterns, then one FP64 addition (the same value as adding first and scaling
+// after).  Called by all 32 lanes of a warp; the warp takes the slow path only
+// if one of its lanes needs it.
+__device__ __forceinline__ double pair_scaled(float hi, float lo, int n)
+{
+    bool oh, ol;
+    const unsigned long long bh = f2d_bits(hi, n, oh), bl = f2d_bits(lo, n, ol);
+    if (__all_sync(0xffffffffu, oh && ol)) return __longlong_as_double((long long)bh) + __longlong_as_double((long long)bl);
+    return oz_pair_slow(hi, lo, n);
 }
 
 // (hi, lo) += b with Knuth's error-free two-sum of hi and b (round-to-nearest
@@ -159,6 +167,64 @@ __device__ __forceinline__ OzTile oz_tile(const OzArgs &g, long long t, int BN)
     u.kb_begin = u.split * g.kchunk;
     u.nkb = max(0, min(g.nkb - u.kb_begin, g.kchunk));
     return u;
+}
+
+// One output element: MODE 0 stores v, 1 stores v alpha, 2 adds v, 3 adds v alpha
+// (a separate instantiation per mode, so that no FP64 work of another mode is issued)
+template <int MODE>
+__device__ __forceinline__ void oz_put(double *o, double v, double alpha)
+{
+    if constexpr (MODE == 0) *o = v;
+    else if constexpr (MODE == 1) *o = v * alpha;
+    else if constexpr (MODE == 2) *o = *o + v;
+    else *o = *o + v * alpha;
+}
+
+// Write of one epilogue warp's 32 x NC part of a tile: the double-FP32 sums
+// (hi, lo) of its TMEM lanes (rows 32 quarter + lane) and columns
+// half NC .. +NC, scaled by 2^(eA[row] + eB[col] - 14).  ldm == 1: lanes own
+// consecutive output rows and write directly; otherwise the 32 x 32 block goes
+// through the warp's float buffer (hi, then lo) so that lanes walk columns.
+template <int MODE, int NC>
+__device__ __forceinline__ void oz_write_tile(const OzArgs &g, const OzTile &u, const float (&hi)[NC],
+                                              const float (&lo)[NC], float *fb, int quarter, int half, int lane,
+                                              int ea, double *out, long long ldm, long long ldn, double alpha)
+{
+    if (ldm == 1) {
+        const int rw = u.m0 + 32 * quarter + lane;
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const int col = u.n0 + half * NC + j;
+            const long long rb = u.brow + half * NC + j;
+            const bool cok = col < g.N && rb < g.rowsB;
+            const int eb = cok ? g.eB[rb] : 0;
+            const double v = pair_scaled(hi[j], lo[j], ea - 14 + eb);
+            if (rw < g.M && cok) oz_put<MODE>(out + (long long)rw + (long long)col * ldn, v, alpha);
+        }
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) fb[lane * 33 + j] = hi[j];
+    __syncwarp();
+    float th[32];
+#pragma unroll
+    for (int rr = 0; rr < 32; ++rr) th[rr] = fb[rr * 33 + lane];
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 32; ++j) fb[lane * 33 + j] = lo[j];
+    __syncwarp();
+    const int col = u.n0 + half * NC + lane;
+    const long long rb = u.brow + half * NC + lane;
+    const bool cok = col < g.N && rb < g.rowsB;
+    const int eb = cok ? g.eB[rb] - 14 : 0;
+#pragma unroll
+    for (int rr = 0; rr < 32; ++rr) {
+        const int er = __shfl_sync(0xffffffffu, ea, rr);
+        const int rw = u.m0 + 32 * quarter + rr;
+        const double v = pair_scaled(th[rr], fb[rr * 33 + lane], er + eb);
+        if (rw < g.M && cok) oz_put<MODE>(out + (long long)rw * ldm + (long long)col * ldn, v, alpha);
+    }
+    __syncwarp();
 }
 
 // Persistent: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...;
@@ -343,50 +409,12 @@ __global__ void __launch_bounds__(320, 1)
                 alpha = g.alpha;
                 acc = g.accumulate;
             }
-            const bool unit = alpha == 1.0;
-            if (ldm == 1) {
-                // consecutive lanes own consecutive output rows: write directly
-                const int rw = u.m0 + rl;
-#pragma unroll
-                for (int j = 0; j < C::NC; ++j) {
-                    const int col = u.n0 + half * C::NC + j;
-                    const long long rb = u.brow + half * C::NC + j;
-                    if (rw < g.M && col < g.N && rb < g.rowsB) {
-                        double v = scale_pow2(widen(hi[j]) + widen(lo[j]), ea - 14 + g.eB[rb]);
-                        if (!unit) v *= alpha;
-                        double *o = out + (long long)rw + (long long)col * ldn;
-                        *o = acc ? *o + v : v;
-                    }
-                }
-            } else {
-                // 32 x 32 block transposed through this warp's float buffer (hi, then
-                // lo) so that lanes walk output columns; row and column scales together
-#pragma unroll
-                for (int j = 0; j < 32; ++j) fb[lane * 33 + j] = hi[j];
-                __syncwarp();
-                float th[32];
-#pragma unroll
-                for (int rr = 0; rr < 32; ++rr) th[rr] = fb[rr * 33 + lane];
-                __syncwarp();
-#pragma unroll
-                for (int j = 0; j < 32; ++j) fb[lane * 33 + j] = lo[j];
-                __syncwarp();
-                const int col = u.n0 + half * C::NC + lane;
-                const long long rb = u.brow + half * C::NC + lane;
-                const bool cok = col < g.N && rb < g.rowsB;
-                const int eb = cok ? g.eB[rb] - 14 : 0;
-#pragma unroll
-                for (int rr = 0; rr < 32; ++rr) {
-                    const int er = __shfl_sync(0xffffffffu, ea, rr);
-                    const int rw = u.m0 + 32 * quarter + rr;
-                    if (rw < g.M && cok) {
-                        double *o = out + (long long)rw * ldm + (long long)col * ldn;
-                        double v = scale_pow2(widen(th[rr]) + widen(fb[rr * 33 + lane]), er + eb);
-                        if (!unit) v *= alpha;
-                        *o = acc ? *o + v : v;
-                    }
-                }
-                __syncwarp();
+            const int mode = (acc ? 2 : 0) + (alpha == 1.0 ? 0 : 1);
+            switch (mode) {
+                case 0: oz_write_tile<0, C::NC>(g, u, hi, lo, fb, quarter, half, lane, ea, out, ldm, ldn, alpha); break;
+                case 1: oz_write_tile<1, C::NC>(g, u, hi, lo, fb, quarter, half, lane, ea, out, ldm, ldn, alpha); break;
+                case 2: oz_write_tile<2, C::NC>(g, u, hi, lo, fb, quarter, half, lane, ea, out, ldm, ldn, alpha); break;
+                default: oz_write_tile<3, C::NC>(g, u, hi, lo, fb, quarter, half, lane, ea, out, ldm, ldn, alpha); break;
             }
         }
     }

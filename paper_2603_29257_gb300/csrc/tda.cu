@@ -712,7 +712,9 @@ size_t footprint(tr_ctx *c)
     // full TDDFT: T_ia on the window (and its unfactored copy during the build)
     const bool rpa = c->opt.tddft != 0;
     const double tx = rpa ? d * nK * oK * vK : 0.0;
-    const double build_peak = std::max(npc * per + cs + t64 + t32 + 2.0 * tx, t64 + tcb + tx);
+    // the split-K workspace reserved at the start of the build is held throughout
+    const double wsplit = d * 32.0 * (1 << 20);
+    const double build_peak = wsplit + std::max(npc * per + cs + t64 + t32 + 2.0 * tx, t64 + tcb + tx);
     // solve: tensors kept, Davidson storage and product workspaces
     const double kept = (mixed ? t32 + d * oK * nK * oK : t64 - d * nK * oK * oK) + tx;
     const int n = (int)std::min<double>(c->opt.nstates, nov);

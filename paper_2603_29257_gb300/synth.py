@@ -202,13 +202,64 @@ def _cart2sph(l):
     ])
 
 
-def _overlap_1d(la, lb, xa, xb, a, b):
+class _NumpyOps:
+    """Array operations of the overlap code on the host (numpy)."""
+    zeros = staticmethod(lambda shape: np.zeros(shape))
+    sqrt = staticmethod(np.sqrt)
+    exp = staticmethod(np.exp)
+    einsum = staticmethod(np.einsum)
+    asarray = staticmethod(lambda a: np.asarray(a, dtype=np.float64))
+    index = staticmethod(lambda a: np.asarray(a))
+    sum23 = staticmethod(lambda a: a.sum(axis=(2, 3)))
+    swap12 = staticmethod(lambda a: a.transpose(0, 2, 1, 3))
+    empty = staticmethod(lambda shape: np.empty(shape))
+
+
+class _TorchOps:
+    """The same operations with torch on a device (large molecules)."""
+
+    def __init__(self, device):
+        import torch
+        self.t, self.dev = torch, device
+
+    def zeros(self, shape):
+        return self.t.zeros(shape, dtype=self.t.float64, device=self.dev)
+
+    def empty(self, shape):
+        return self.t.empty(shape, dtype=self.t.float64, device=self.dev)
+
+    def sqrt(self, a):
+        return self.t.sqrt(a) if self.t.is_tensor(a) else math.sqrt(a)
+
+    def exp(self, a):
+        return self.t.exp(a)
+
+    def einsum(self, eq, *ops):
+        return self.t.einsum(eq, *[o if self.t.is_tensor(o) else self.asarray(o) for o in ops])
+
+    def asarray(self, a):
+        return self.t.as_tensor(np.asarray(a, dtype=np.float64), device=self.dev)
+
+    def index(self, a):
+        return self.t.as_tensor(np.asarray(a), device=self.dev)
+
+    @staticmethod
+    def sum23(a):
+        return a.sum(dim=(2, 3))
+
+    @staticmethod
+    def swap12(a):
+        return a.permute(0, 2, 1, 3)
+
+
+def _overlap_1d(la, lb, xa, xb, a, b, ops=_NumpyOps):
     """1-D overlap table S[i, j] for i<=la, j<=lb, vectorised over leading dims."""
     p = a + b
     xp = (a * xa + b * xb) / p
     pa, pb = xp - xa, xp - xb
-    s = np.zeros(np.broadcast(a, b, xa, xb).shape + (la + 1, lb + 1))
-    s[..., 0, 0] = np.sqrt(math.pi / p) * np.exp(-a * b / p * (xa - xb) ** 2)
+    shape = tuple(np.broadcast_shapes(tuple(a.shape), tuple(b.shape), tuple(xa.shape), tuple(xb.shape)))
+    s = ops.zeros(shape + (la + 1, lb + 1))
+    s[..., 0, 0] = ops.sqrt(math.pi / p) * ops.exp(-a * b / p * (xa - xb) ** 2)
     inv2p = 0.5 / p
     for i in range(la + 1):
         for j in range(lb + 1):
@@ -228,14 +279,18 @@ def _overlap_1d(la, lb, xa, xb, a, b):
     return s
 
 
-def overlap_matrix(xyz, shells):
+def overlap_matrix(xyz, shells, device=None):
     """AO overlap matrix in the spherical convention of this module (used to
-    build orthonormal synthetic MOs; not part of TDA-risp)."""
+    build orthonormal synthetic MOs; not part of TDA-risp).  device: None runs
+    numpy on the host; a torch device name runs the same arithmetic with torch
+    there (large molecules) and returns a torch tensor."""
+    ops = _NumpyOps if device is None else _TorchOps(device)
+    rows_chunk = 16 if device is None else 256
     off = np.zeros(len(shells) + 1, dtype=np.int64)
     for k, sh in enumerate(shells):
         off[k + 1] = off[k] + NFUNC[sh.l]
     nao = int(off[-1])
-    S = np.zeros((nao, nao))
+    S = ops.zeros((nao, nao))
     groups = {}
     for k, sh in enumerate(shells):
         groups.setdefault(sh.l, []).append(k)
@@ -249,15 +304,15 @@ def overlap_matrix(xyz, shells):
             ex[r, :n] = shells[k].exps
             cf[r, :n] = shells[k].coefs
         cen = np.asarray([xyz[shells[k].atom] for k in idx])
-        packed[l] = (np.asarray(idx), ex, cf, cen)
+        packed[l] = (np.asarray(idx), ops.asarray(ex), ops.asarray(cf), ops.asarray(cen))
     for la, (ia_all, exa_all, cfa_all, cena_all) in packed.items():
         for lb, (ib, exb, cfb, cenb) in packed.items():
             ca, cb = _cart_list(la), _cart_list(lb)
             na, nb = NFUNC[la], NFUNC[lb]
-            cols = (off[ib][:, None] + np.arange(nb)[None, :]).reshape(-1)
-            for r0 in range(0, len(ia_all), 16):
-                ia = ia_all[r0:r0 + 16]
-                exa, cfa, cena = exa_all[r0:r0 + 16], cfa_all[r0:r0 + 16], cena_all[r0:r0 + 16]
+            cols = ops.index((off[ib][:, None] + np.arange(nb)[None, :]).reshape(-1))
+            for r0 in range(0, len(ia_all), rows_chunk):
+                ia = ia_all[r0:r0 + rows_chunk]
+                exa, cfa, cena = exa_all[r0:r0 + rows_chunk], cfa_all[r0:r0 + rows_chunk], cena_all[r0:r0 + rows_chunk]
                 # dims: [sa, sb, pa, pb]
                 a = exa[:, None, :, None]
                 b = exb[None, :, None, :]
@@ -266,33 +321,39 @@ def overlap_matrix(xyz, shells):
                 for d in range(3):
                     xa = cena[:, None, None, None, d]
                     xb = cenb[None, :, None, None, d]
-                    tabs.append(_overlap_1d(la, lb, xa, xb, a, b))
-                blk = np.empty((len(ia), len(ib), len(ca), len(cb)))
+                    tabs.append(_overlap_1d(la, lb, xa, xb, a, b, ops))
+                blk = ops.empty((len(ia), len(ib), len(ca), len(cb)))
                 for u, (ax, ay, az) in enumerate(ca):
                     for v, (bx, by, bz) in enumerate(cb):
                         prim = tabs[0][..., ax, bx] * tabs[1][..., ay, by] * tabs[2][..., az, bz]
-                        blk[:, :, u, v] = (prim * cc).sum(axis=(2, 3))
-                blk = np.einsum("mu,abuv,nv->abmn", _cart2sph(la), blk, _cart2sph(lb))
-                rows = (off[ia][:, None] + np.arange(na)[None, :]).reshape(-1)
-                S[np.ix_(rows, cols)] = blk.transpose(0, 2, 1, 3).reshape(len(ia) * na, len(ib) * nb)
+                        blk[:, :, u, v] = ops.sum23(prim * cc)
+                blk = ops.einsum("mu,abuv,nv->abmn", _cart2sph(la), blk, _cart2sph(lb))
+                rows = ops.index((off[ia][:, None] + np.arange(na)[None, :]).reshape(-1))
+                S[rows[:, None], cols[None, :]] = ops.swap12(blk).reshape(len(ia) * na, len(ib) * nb)
     return S
 
 
-def build_basis(rng, Z, xyz_bohr, min_eig=1e-7, max_redraw=200):
+def build_basis(rng, Z, xyz_bohr, min_eig=1e-7, max_redraw=200, device=None):
     shells = []
     for a, z in enumerate(Z):
         for l in (HYDROGEN_SHELLS if z == 1 else HEAVY_SHELLS):
             shells.append(_draw_shell(rng, a, l))
     for _ in range(max_redraw):
-        S = overlap_matrix(xyz_bohr, shells)
-        w, v = np.linalg.eigh(S)
-        if w[0] > min_eig:
+        S = overlap_matrix(xyz_bohr, shells, device)
+        if device is None:
+            w, v = np.linalg.eigh(S)
+            soft = v[:, 0]
+        else:
+            import torch
+            w, v = torch.linalg.eigh(S)
+            soft = v[:, 0].cpu().numpy()
+        if float(w[0]) > min_eig:
             return shells, S, w, v
         # redraw the shell carrying the largest weight of the softest direction
         off = np.zeros(len(shells) + 1, dtype=np.int64)
         for k, sh in enumerate(shells):
             off[k + 1] = off[k] + NFUNC[sh.l]
-        wt = np.add.reduceat(v[:, 0] ** 2, off[:-1])
+        wt = np.add.reduceat(soft ** 2, off[:-1])
         k = int(np.argmax(wt))
         shells[k] = _draw_shell(rng, shells[k].atom, shells[k].l)
     raise RuntimeError("could not draw a well-conditioned basis")
@@ -301,22 +362,41 @@ def build_basis(rng, Z, xyz_bohr, min_eig=1e-7, max_redraw=200):
 # --------------------------------------------------------------------------
 # molecules
 
-def make_molecule(seed: int, n_heavy: int, n_h: int, nocc: int | None = None) -> Molecule:
+# molecules with more atoms than this are built with the dense linear algebra
+# (overlap, its eigendecomposition, QR, products) on a CUDA device when one is
+# available: the same formulas and random numbers, rounded differently
+LARGE_ATOMS = 300
+
+
+def make_molecule(seed: int, n_heavy: int, n_h: int, nocc: int | None = None, device=None) -> Molecule:
     """Seeded organic-like molecule with orthonormal synthetic MOs.
 
-    nocc defaults to round(0.2 * nao) (42 of 210 for the 24-atom case)."""
+    nocc defaults to round(0.2 * nao) (42 of 210 for the 24-atom case).
+    device: None computes everything with numpy; a torch device name ("cuda")
+    runs the overlap, eigendecomposition, QR and products there."""
     rng = np.random.default_rng(seed)
     Z, xyz_ang = chain_geometry(rng, n_heavy, n_h)
     xyz = xyz_ang * ANGSTROM_TO_BOHR
-    shells, S, w, v = build_basis(rng, Z, xyz)
+    shells, S, w, v = build_basis(rng, Z, xyz, device=device)
     nao = S.shape[0]
     if nocc is None:
         nocc = int(round(nao * 42 / 210))
     g = rng.normal(size=(nao, nao))
-    q, r = np.linalg.qr(g)
-    q = q * np.sign(np.diag(r))[None, :]
-    s_inv_half = (v * (1.0 / np.sqrt(w))[None, :]) @ v.T
-    C = s_inv_half @ q
+    if device is None:
+        q, r = np.linalg.qr(g)
+        q = q * np.sign(np.diag(r))[None, :]
+        s_inv_half = (v * (1.0 / np.sqrt(w))[None, :]) @ v.T
+        C = s_inv_half @ q
+    else:
+        import torch
+        q, r = torch.linalg.qr(torch.as_tensor(g, device=device))
+        del g
+        q = q * torch.sign(torch.diagonal(r))[None, :]
+        del r
+        s_inv_half = (v * (1.0 / torch.sqrt(w))[None, :]) @ v.T
+        del v, S
+        C = (s_inv_half @ q).cpu().numpy()
+        del q, s_inv_half
     eps = np.concatenate([np.sort(rng.uniform(-1.2, -0.25, size=nocc)),
                           np.sort(rng.uniform(0.02, 4.0, size=nao - nocc))])
     aux = np.array([0.0 if z == 1 else AUX_EXPONENT[int(z)] for z in Z])
@@ -334,10 +414,20 @@ def molecule_200():
     return make_molecule(2, 100, 100)
 
 
-def molecule_by_atoms(seed: int, natoms: int) -> Molecule:
-    """Molecule of natoms atoms, half of them (rounded) heavy."""
+def molecule_by_atoms(seed: int, natoms: int, device=None) -> Molecule:
+    """Molecule of natoms atoms, half of them (rounded) heavy.  device as in
+    make_molecule ("auto": a CUDA device above LARGE_ATOMS atoms when torch sees one)."""
     n_heavy = max(1, int(round(natoms / 2)))
-    return make_molecule(seed, n_heavy, natoms - n_heavy)
+    if device == "auto":
+        device = None
+        if natoms > LARGE_ATOMS:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    device = "cuda"
+            except ImportError:
+                pass
+    return make_molecule(seed, n_heavy, natoms - n_heavy, device=device)
 
 
 def random_trial_block(seed: int, m: int, nocc: int, nvir: int) -> np.ndarray:

@@ -5,10 +5,9 @@
 //     and the MO tensors are then rounded to FP32 (the paper builds its
 //     integrals in FP64 and runs everything after them in FP32, Sec. 3.3);
 //     see build_mixed for why the transforms themselves stay FP64;
-//   - J: Z = (Q|jb) X and J = (P|ia) Zt as FP32 products on the CUDA cores (Z
-//     summed in FP32 over chunks of at most 4096 terms and in FP64 across
-//     chunks; the expansion by a kernel for blocks of at most 32 vectors);
-//     (P|Q)^-1 is applied in FP64;
+//   - J (Sec. 3.1): Z = (Q|jb) X and J = (P|ia) Zt as FP32 products on the CUDA
+//     cores at the FFMA rate (Z summed in FP32 over chunks of at most 4096
+//     terms and in FP64 across chunks); (P|Q)^-1 is applied in FP64;
 //   - K: both stages on the tensor cores (tcgen05 kind::tf32) with split
 //     operands, hi*hi + hi*lo + lo*hi, FP32 accumulation; stage 1 writes M^P
 //     already split and laid out K-major for stage 2, stage 2 accumulates
@@ -40,59 +39,219 @@ __global__ void mixed_prepare(const double *__restrict__ X, float *__restrict__ 
     }
 }
 
-// J expansion for a block of at most 32 vectors (Sec. 3.1):
-//   AX[m][ia] += alpha sum_P Z32[P][m] Y32[P][ia]
-// in FP32 over P, added to the FP64 output.  A CTA covers 128 ia x 32 m (4 x 4 per
-// thread); 32-row tiles of Y (coalesced along ia) and Z staged in shared memory.
-__global__ void __launch_bounds__(256)
-    je_kernel(const float *__restrict__ Y, const float *__restrict__ Z, int nJ, int mm, long long nov, double alpha,
-              double *__restrict__ AX)
+// ---------------------------------------------------------------- J on the CUDA cores
+//
+// The Coulomb contractions stream (P|ia) in FP32 with the block of MB <= 32
+// trial vectors: 2 MB flops per 4-byte element, above the FP32 CUDA-core
+// ridge (73 TFLOP/s over 6.8 TB/s is 10.7 flop/B) for MB = 32, so both kernels
+// are built for the FFMA rate: every thread keeps 4 x MB accumulators, and the
+// operand shared by a whole warp (the MB trial values) is read from shared
+// memory as broadcast float4 loads.
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *dst, const void *src, bool valid)
 {
-    __shared__ float4 Ys[32][32];
-    __shared__ float4 Zs[32][8];
-    float *ys = (float *)Ys, *zs = (float *)Zs;
-    const int tid = threadIdx.x, ti = tid & 31, tm = tid >> 5;
-    const long long i0 = (long long)blockIdx.x * 128;
-    float acc[4][4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
-    for (int P0 = 0; P0 < nJ; P0 += 32) {
-        for (int e = tid; e < 32 * 128; e += 256) {
-            const int p = e >> 7, c = e & 127;
-            const long long ia = i0 + c;
-            ys[p * 128 + c] = (P0 + p < nJ && ia < nov) ? Y[(long long)(P0 + p) * nov + ia] : 0.f;
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src), "n"(BYTES), "r"(valid ? BYTES : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// CTA tile: 256 aux functions x MB trial vectors, 64 threads (thread t: P = P0 +
+// t + 64 q, q < 4); stages of 16 ia: Y rows padded to 20 floats (80 bytes: the
+// float4 reads of 8 consecutive rows by a quarter warp hit 32 distinct banks),
+// X stored [ia][m] for broadcast float4 reads
+constexpr int JC_THREADS = 64, JC_TP = 256, JC_KK = 16, JC_LD = 20, JC_CHUNK = 4096;
+constexpr int JC_STAGE = JC_TP * JC_LD + JC_KK * 32;  // floats
+
+// Z partials: part[s][P][m] = sum over the ia of split s of Y[P][ia] X[m][ia],
+// FP32 sums over chunks of at most 4096 ia added into the FP64 partial after
+// each chunk.  VEC: rows of Y start on 16-byte boundaries (nov a multiple of
+// 4) and are copied 16 bytes at a time.
+template <int MB, bool VEC>
+__global__ void __launch_bounds__(JC_THREADS)
+    jc_kernel(const float *__restrict__ Y, const float *__restrict__ X, int nJ, int mm, long long nov, long long per,
+              double *__restrict__ part)
+{
+    extern __shared__ __align__(16) float jsm[];
+    const int t = threadIdx.x;
+    const int P0 = blockIdx.x * JC_TP;
+    const long long i0 = (long long)blockIdx.y * per, i1 = min(nov, i0 + per);
+    double *out = part + ((long long)blockIdx.y * nJ) * mm;
+    const int nst = (int)((i1 - i0 + JC_KK - 1) / JC_KK);
+    auto load = [&](int s, float *buf) {
+        const long long c0 = i0 + (long long)s * JC_KK;
+        if (VEC) {
+            for (int e = t; e < JC_TP * (JC_KK / 4); e += JC_THREADS) {
+                const int r = e >> 2, k = 4 * (e & 3);
+                const long long col = c0 + k;
+                const bool ok = P0 + r < nJ && col < i1;  // i1 and col are multiples of 4 here
+                cp_async<16>(buf + r * JC_LD + k, Y + (ok ? (long long)(P0 + r) * nov + col : 0), ok);
+            }
+        } else {
+            for (int e = t; e < JC_TP * JC_KK; e += JC_THREADS) {
+                const int r = e / JC_KK, k = e - r * JC_KK;
+                const long long col = c0 + k;
+                const bool ok = P0 + r < nJ && col < i1;
+                cp_async<4>(buf + r * JC_LD + k, Y + (ok ? (long long)(P0 + r) * nov + col : 0), ok);
+            }
         }
-        for (int e = tid; e < 32 * 32; e += 256) {
-            const int p = e >> 5, m = e & 31;
-            zs[p * 32 + m] = (P0 + p < nJ && m < mm) ? Z[(long long)(P0 + p) * mm + m] : 0.f;
+        float *xs = buf + JC_TP * JC_LD;
+        for (int e = t; e < JC_KK * MB; e += JC_THREADS) {
+            const int m = e / JC_KK, k = e - m * JC_KK;
+            const long long col = c0 + k;
+            const bool ok = m < mm && col < i1;
+            cp_async<4>(xs + k * 32 + m, X + (ok ? (long long)m * nov + col : 0), ok);
+        }
+        cp_async_commit();
+    };
+    float acc[4][MB];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int m = 0; m < MB; ++m) acc[q][m] = 0.f;
+    int chunk_left = JC_CHUNK / JC_KK;
+    bool first = true;
+    load(0, jsm);
+    for (int s = 0; s < nst; ++s) {
+        const float *cur = jsm + (s & 1) * JC_STAGE;
+        if (s + 1 < nst) {
+            load(s + 1, jsm + ((s + 1) & 1) * JC_STAGE);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
-#pragma unroll 8
-        for (int p = 0; p < 32; ++p) {
-            const float4 y = Ys[p][ti];
-            const float4 z = Zs[p][tm];
-            const float zz[4] = {z.x, z.y, z.z, z.w};
+        const float *xs = cur + JC_TP * JC_LD;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                acc[j][0] = fmaf(zz[j], y.x, acc[j][0]);
-                acc[j][1] = fmaf(zz[j], y.y, acc[j][1]);
-                acc[j][2] = fmaf(zz[j], y.z, acc[j][2]);
-                acc[j][3] = fmaf(zz[j], y.w, acc[j][3]);
+        for (int k4 = 0; k4 < JC_KK / 4; ++k4) {
+            float4 y[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) y[q] = *(const float4 *)(cur + (t + 64 * q) * JC_LD + 4 * k4);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const int k = 4 * k4 + kk;
+#pragma unroll
+                for (int m4 = 0; m4 < MB / 4; ++m4) {
+                    const float4 x = *(const float4 *)(xs + k * 32 + 4 * m4);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float yv = kk == 0 ? y[q].x : kk == 1 ? y[q].y : kk == 2 ? y[q].z : y[q].w;
+                        acc[q][4 * m4 + 0] = fmaf(yv, x.x, acc[q][4 * m4 + 0]);
+                        acc[q][4 * m4 + 1] = fmaf(yv, x.y, acc[q][4 * m4 + 1]);
+                        acc[q][4 * m4 + 2] = fmaf(yv, x.z, acc[q][4 * m4 + 2]);
+                        acc[q][4 * m4 + 3] = fmaf(yv, x.w, acc[q][4 * m4 + 3]);
+                    }
+                }
             }
         }
         __syncthreads();
+        if (--chunk_left == 0 || s == nst - 1) {
+            // end of a chunk of 4096 ia: the FP32 sums into the FP64 partial
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int P = P0 + t + 64 * q;
+#pragma unroll
+                for (int m = 0; m < MB; ++m) {
+                    if (P < nJ && m < mm) {
+                        double *o = out + (long long)P * mm + m;
+                        *o = first ? (double)acc[q][m] : *o + (double)acc[q][m];
+                    }
+                    acc[q][m] = 0.f;
+                }
+            }
+            first = false;
+            chunk_left = JC_CHUNK / JC_KK;
+        }
+    }
+}
+
+// J expansion: AX[m][ia] += alpha sum_P Z[P][m] Y[P][ia] for Q consecutive ia
+// per thread (Q MB = 64 accumulators: Q = 4 for MB = 16, 2 for MB = 32) and
+// m < MB, FP32 sums over P.  Y is read once, straight from global memory (the
+// lanes of a warp cover 32 Q consecutive ia); Z sits in shared memory in tiles
+// of 256 aux functions, read as broadcast float4 loads.  VEC: the rows of Y
+// start on (4 Q)-byte boundaries, so that each thread loads its Q values as one
+// vector.
+constexpr int JE_THREADS = 128, JE_PT = 256;
+
+template <int MB, int Q, bool VEC>
+__global__ void __launch_bounds__(JE_THREADS)
+    je2_kernel(const float *__restrict__ Y, const float *__restrict__ Z, int nJ, int mm, long long nov, double alpha,
+               double *__restrict__ AX)
+{
+    __shared__ __align__(16) float zs[JE_PT * MB];
+    const long long ia = ((long long)blockIdx.x * JE_THREADS + threadIdx.x) * Q;
+    float acc[Q][MB];
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int m = 0; m < MB; ++m) acc[q][m] = 0.f;
+    for (int P0 = 0; P0 < nJ; P0 += JE_PT) {
+        const int np = min(JE_PT, nJ - P0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < np * MB; e += JE_THREADS) {
+            const int p = e / MB, m = e - p * MB;
+            zs[e] = m < mm ? Z[(long long)(P0 + p) * mm + m] : 0.f;
+        }
+        __syncthreads();
+        const float *yp = Y + (long long)P0 * nov + ia;
+        // the Y values of 8 aux functions are loaded before any is used: 8 loads in
+        // flight per thread hide the HBM latency
+        for (int pb = 0; pb < np; pb += 8) {
+            float y[8][Q];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float *yu = yp + (long long)(pb + u) * nov;
+                if (pb + u < np && VEC && ia + Q - 1 < nov) {
+                    if constexpr (Q == 4) {
+                        const float4 v = __ldg((const float4 *)yu);
+                        y[u][0] = v.x, y[u][1] = v.y, y[u][2] = v.z, y[u][3] = v.w;
+                    } else {
+                        const float2 v = __ldg((const float2 *)yu);
+                        y[u][0] = v.x, y[u][1] = v.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) y[u][q] = (pb + u < np && ia + q < nov) ? __ldg(yu + q) : 0.f;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (pb + u >= np) break;
+#pragma unroll
+                for (int m4 = 0; m4 < MB / 4; ++m4) {
+                    const float4 z = *(const float4 *)(zs + (pb + u) * MB + 4 * m4);
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) {
+                        acc[q][4 * m4 + 0] = fmaf(z.x, y[u][q], acc[q][4 * m4 + 0]);
+                        acc[q][4 * m4 + 1] = fmaf(z.y, y[u][q], acc[q][4 * m4 + 1]);
+                        acc[q][4 * m4 + 2] = fmaf(z.z, y[u][q], acc[q][4 * m4 + 2]);
+                        acc[q][4 * m4 + 3] = fmaf(z.w, y[u][q], acc[q][4 * m4 + 3]);
+                    }
+                }
+            }
+        }
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int m = 4 * tm + j;
-        if (m >= mm) continue;
+    for (int m = 0; m < MB; ++m) {
+        if (m >= mm) break;
+        double *o = AX + (long long)m * nov + ia;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const long long ia = i0 + 4 * ti + q;
-            if (ia < nov) AX[(long long)m * nov + ia] += alpha * (double)acc[j][q];
-        }
+        for (int q = 0; q < Q; ++q)
+            if (ia + q < nov) o[q] += alpha * (double)acc[q][m];
+    }
+}
+
+// Z[P][m] = sum_s part[s][P][m] (FP64, fixed order)
+__global__ void jc_reduce(const double *__restrict__ part, int nsplit, long long n, double *__restrict__ Z)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        double z = 0.0;
+        for (int s = 0; s < nsplit; ++s) z += part[(long long)s * n + e];
+        Z[e] = z;
     }
 }
 
@@ -114,6 +273,61 @@ __global__ void mixed_diag(const double *__restrict__ D, const double *__restric
 }
 
 unsigned gfor(long long n) { return (unsigned)std::max<long long>(1, std::min<long long>(cdiv(n, 256), 152 * 16)); }
+
+// Z[P][m] = sum_ia Y32[P][ia] X32[m][ia] into Z (FP64 [nJ][mm]): split over ia
+// so that about ten CTAs of two warps per SM stream (P|ia); partials in the
+// split-K workspace, reduced in a fixed order
+void j_contract(tr_ctx *c, int mm, double *Z)
+{
+    const int nJ = c->nJ;
+    const long long nov = c->nov;
+    const int nPt = (int)cdiv(nJ, JC_TP);
+    const long long target = std::max<long long>(1, (152LL * 10) / nPt);
+    long long per = std::max<long long>(JC_KK, (nov + target - 1) / target);
+    per = (per + JC_KK - 1) / JC_KK * JC_KK;
+    const long long cap = std::max<long long>(1, (long long)c->ws_split.n / ((long long)nJ * mm));
+    if ((nov + per - 1) / per > cap) per = ((nov + cap - 1) / cap + JC_KK - 1) / JC_KK * JC_KK;
+    const int nsplit = (int)std::max<long long>(1, (nov + per - 1) / per);
+    TR_REQUIRE(nsplit <= 65535, TR_EINVAL, "J contraction: too many ia splits");
+    const size_t smem = 2 * JC_STAGE * sizeof(float);
+    const dim3 grid(nPt, nsplit);
+    const bool vec = nov % 4 == 0;
+    const double flops = 2.0 * nJ * mm * (double)nov, bytes = 4.0 * nJ * (double)nov + 4.0 * nPt * mm * (double)nov;
+#define TR_JC(MB, V) \
+    TR_LAUNCH(c->prof, c->st, "J_contract", flops, bytes, \
+              (jc_kernel<MB, V><<<grid, JC_THREADS, smem, c->st>>>(c->Y32.p, c->X32.p, nJ, mm, nov, per, c->ws_split.p)))
+    if (mm <= 16) {
+        if (vec) TR_JC(16, true);
+        else TR_JC(16, false);
+    } else {
+        if (vec) TR_JC(32, true);
+        else TR_JC(32, false);
+    }
+#undef TR_JC
+    const long long n = (long long)nJ * mm;
+    TR_LAUNCH(c->prof, c->st, "J_contract", 0, 8.0 * n * (nsplit + 1),
+              jc_reduce<<<gfor(n), 256, 0, c->st>>>(c->ws_split.p, nsplit, n, Z));
+}
+
+// AX[m][ia] += 2 sum_P Z32[P][m] Y32[P][ia]
+void j_expand(tr_ctx *c, int mm, double *ax)
+{
+    const int nJ = c->nJ;
+    const long long nov = c->nov;
+    const double flops = 2.0 * nJ * mm * (double)nov, bytes = 4.0 * nJ * (double)nov + 16.0 * mm * (double)nov;
+#define TR_JE(MB, Q, V) \
+    TR_LAUNCH(c->prof, c->st, "J_expand", flops, bytes, \
+              (je2_kernel<MB, Q, V><<<(unsigned)cdiv(nov, (long long)Q * JE_THREADS), JE_THREADS, 0, c->st>>>( \
+                  c->Y32.p, c->Z32.p, nJ, mm, nov, 2.0, ax)))
+    if (mm <= 16) {
+        if (nov % 4 == 0) TR_JE(16, 4, true);
+        else TR_JE(16, 4, false);
+    } else {
+        if (nov % 2 == 0) TR_JE(32, 2, true);
+        else TR_JE(32, 2, false);
+    }
+#undef TR_JE
+}
 
 int pad32(int x) { return (x + 31) / 32 * 32; }
 
@@ -245,13 +459,11 @@ void matvec_mixed(tr_ctx *c, int m, const double *X, double *AX)
         if (nJ && c->opt.j_ao) {
             j_ao_block(c, mm, x, ax);  // Coulomb term in FP64 from the AO transition densities
         } else if (nJ) {
-            sgemm(pf, st, "J_contract", false, true, nJ, mm, (int)nov, 1.0, c->Y32.p, nov, c->X32.p, nov, 0.0,
-                  c->ws_Z.p, mm, Batch(), c->ws_split.p, c->ws_split.n, 4096);
+            j_contract(c, mm, c->ws_Z.p);
             dgemm(pf, st, "J_metric", false, false, nJ, mm, nJ, 1.0, c->GinvJ.p, nJ, c->ws_Z.p, mm, 0.0, c->ws_Z2.p,
                   mm, Batch(), nullptr, 0);
             TR_LAUNCH(pf, st, "to_f32", 0, 0, to_f32<<<gfor((long long)nJ * mm), 256, 0, st>>>(c->ws_Z2.p, c->Z32.p, (long long)nJ * mm));
-            TR_LAUNCH(pf, st, "J_expand", 2.0 * nJ * mm * (double)nov, 4.0 * (double)nJ * nov + 16.0 * mm * (double)nov,
-                      je_kernel<<<(unsigned)cdiv(nov, 128), 256, 0, st>>>(c->Y32.p, c->Z32.p, nJ, mm, nov, 2.0, ax));
+            j_expand(c, mm, ax);
         }
         if (c->k_active) {
             const int npk = c->mixed_npk;

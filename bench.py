@@ -228,9 +228,11 @@ def run_native(args):
         if not args.no_fp64tc:
             fp64tc = run_form(args, tdarisp, mol, C_dev, eps_dev, stream, barrier, 2, om64, gold)
     # the other configurations of the workload family (rank 0 of a single-GPU run)
-    configs = None
+    configs = spill = None
     if not args.no_configs and world == 1:
         configs = run_configs(args, tdarisp, stream)
+        if args.case == "full":
+            spill = spill_figures(tdarisp, mol, C_dev, eps_dev, stream)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -285,7 +287,7 @@ def run_native(args):
                      "restarts": [i.nrestart for i in infos], "converged": [i.converged for i in infos]},
         "per_state_dOmega_vs_oracle_Ha": per_state_error(om_last, gold),
         "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "mixed_form": mixed,
-        "fp64_tensor_core_form": fp64tc, "configs": configs,
+        "fp64_tensor_core_form": fp64tc, "configs": configs, "spill": spill,
         "gpu_launches": launches, "clocks": clk,
     }
     for extra in (mixed, fp64tc):
@@ -826,6 +828,52 @@ def run_batched(args):
             "config": {"workload": f["workload"], "timing": f["timing"]}}
     line.update({k: v for k, v in f.items() if k not in ("workload", "timing", "value", "unit", "steps", "warmup")})
     print(json.dumps(line))
+
+
+def spill_figures(tdarisp, mol, C_dev, eps_dev, stream, dev_rows=60):
+    """Host placement of the Davidson vectors (Sec. 3.3): the pinned host link
+    probed with plain copies (1 GiB each way, CUDA events), then the 200-atom
+    reduced-precision solve with all V/W rows in HBM and with only dev_rows of
+    them there (the rest in pinned host memory, streamed through two staging
+    slots on a copy stream): bytes moved, both solve times, the moved bytes per
+    second of the spilled solve, and the roots' agreement."""
+    import torch
+    n = 1 << 27  # doubles: 1 GiB
+    h = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    d = torch.empty(n, dtype=torch.float64, device="cuda")
+    probe = {}
+    for name, dst, src in (("h2d_gbs", d, h), ("d2h_gbs", h, d)):
+        for _ in range(2):
+            dst.copy_(src, non_blocking=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cs = torch.cuda.current_stream()
+        e0.record(cs)
+        for _ in range(5):
+            dst.copy_(src, non_blocking=True)
+        e1.record(cs)
+        torch.cuda.synchronize()
+        probe[name] = 5 * 8.0 * n / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del h, d
+    out = {"link_probe": probe, "probe": "1 GiB pinned host <-> device copies, 5 each way, CUDA events"}
+    for key, rows in (("all_rows_on_device", 0), ("rows_on_device_%d" % dev_rows, dev_rows)):
+        ctx = tdarisp.Context(stream=stream.cuda_stream, precision=1, dav_dev_rows=rows, **OPTS)
+        ctx.set_molecule(mol.Z, mol.xyz, mol.aux_exp, mol.shells)
+        ctx.set_orbitals(C_dev, eps_dev, mol.nocc)
+        ctx.build()
+        ctx.solve(want_x=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        om, _, _, info = ctx.solve(want_x=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        ctx.close()
+        out[key] = {"solve_s": dt, "dev_rows": info.dev_rows, "max_space": info.max_space,
+                    "host_bytes_moved": int(info.host_bytes_moved), "nmatvec": info.nmatvec,
+                    "host_gb_per_solve_s": info.host_bytes_moved / dt / 1e9,
+                    "omega_Ha": [float(x) for x in om]}
+    a, b = out["all_rows_on_device"], out["rows_on_device_%d" % dev_rows]
+    out["max_abs_dOmega_spilled_vs_resident_Ha"] = max(abs(x - y) for x, y in zip(a["omega_Ha"], b["omega_Ha"]))
+    return out
 
 
 # the 24-atom molecule: global hybrid, 5 states to residual 1e-6

@@ -183,12 +183,22 @@ struct Prof {
     }
 };
 
-// Launch helper: checks the launch and records it.
+// Error of the last launch, if any, as an exception naming the kernel kind
+#define TR_CHECK_LAUNCH(what)                                                                        \
+    do {                                                                                             \
+        const cudaError_t ce_ = cudaGetLastError();                                                  \
+        if (ce_ != cudaSuccess)                                                                      \
+            throw ::tr::Error(TR_ECUDA, std::string("launch of ") + (what) + ": " + cudaGetErrorString(ce_)); \
+    } while (0)
+
+// Launch helper: checks the launch (an error names the kernel kind) and records it.
 #define TR_LAUNCH(prof, stream, name, flops, bytes, ...)          \
     do {                                                          \
         int tok_ = (prof).begin((stream), (name), (flops), (bytes)); \
         __VA_ARGS__;                                              \
-        TR_CUDA(cudaGetLastError());                              \
+        const cudaError_t le_ = cudaGetLastError();               \
+        if (le_ != cudaSuccess)                                   \
+            throw ::tr::Error(TR_ECUDA, std::string("launch of ") + (name) + ": " + cudaGetErrorString(le_)); \
         (prof).end((stream), tok_);                               \
     } while (0)
 

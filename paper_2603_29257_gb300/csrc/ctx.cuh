@@ -3,7 +3,6 @@
 #pragma once
 
 #include <string>
-#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -180,8 +179,6 @@ void oscillator_strengths(tr_ctx *c, int n, const double *omega, const double *X
 // upload the class-sorted auxiliary lists of every chunk of npc functions of set
 // which (0 = J, 1 = K) once
 void prepare_aux_chunks(tr_ctx *c, int which, int npc);
-// the same for several chunkings at once: (which, npc) per set
-void prepare_aux_chunk_sets(tr_ctx *c, const std::vector<std::pair<int, int>> &sets);
 // reduced-precision form (mixed.cu)
 void get_tensor_mixed(tr_ctx *c, int which, double *out, int on_device);
 void build_mixed(tr_ctx *c);

@@ -583,7 +583,7 @@ void launch_pair_class(Prof &prof, const cudaStream_t *streams, int nstreams, in
         int tok = prof.begin(st, names[cls], 0, bytes);
         int3c_grp_kernel<LA, LB, SACC><<<grid, NT, SMEM, st>>>(sh, pairs, prange, prim, npair, atoms, nao, out, ka,
                                                                 kb, omega, boys);
-        TR_CUDA(cudaGetLastError());
+        TR_CHECK_LAUNCH(names[cls]);
         prof.end(st, tok);
         return;
     }
@@ -605,7 +605,7 @@ void launch_pair_class(Prof &prof, const cudaStream_t *streams, int nstreams, in
             case 1: int3c_kernel<LA, LB, 1, SACC><<<grid, 128, SMEM, st>>>(sh, pairs, prange, prim, npair, a, nao, out, ka, kb, omega, boys); break;
             default: int3c_kernel<LA, LB, 2, SACC><<<grid, 128, SMEM, st>>>(sh, pairs, prange, prim, npair, a, nao, out, ka, kb, omega, boys); break;
         }
-        TR_CUDA(cudaGetLastError());
+        TR_CHECK_LAUNCH(names[cls]);
         prof.end(st, tok);
     }
 }
@@ -639,7 +639,7 @@ __global__ void int2c_kernel(const AuxDev *__restrict__ aux, int n, double ka, d
 void int3c(Prof &prof, cudaStream_t st, SideStreams *side, const ShellDev *sh, const int2 *pairs,
            const int2 *prange, const double *prim, const int *off, const AuxDev *aux, const int *aoff,
            const AuxDev *atoms, int natoms, int nao, double *out, double ka, double kb, double omega,
-           const double *boys, bool manage)
+           const double *boys)
 {
     // the 6 pair classes x 4 aux components are independent launches writing
     // disjoint outputs: spread them over the side streams (heaviest classes first)
@@ -647,7 +647,7 @@ void int3c(Prof &prof, cudaStream_t st, SideStreams *side, const ShellDev *sh, c
     const cudaStream_t *streams = one;
     int nstreams = 1, next = 0;
     if (side) {
-        if (manage) side->begin(st);
+        side->begin(st);
         streams = side->s;
         nstreams = SideStreams::N;
     }
@@ -661,7 +661,7 @@ void int3c(Prof &prof, cudaStream_t st, SideStreams *side, const ShellDev *sh, c
     TR_CLASS(1, 0, 1);
     TR_CLASS(0, 0, 0);
 #undef TR_CLASS
-    if (side && manage) side->end(st);
+    if (side) side->end(st);
 }
 
 void dipole_ints(Prof &prof, cudaStream_t st, const ShellDev *sh, const int2 *pairs, const int2 *prange,

@@ -50,9 +50,8 @@ PairList make_pairs(const std::vector<ShellDev> &sh, const std::vector<double> &
 
 // out[f][mu][nu] (+= nothing: caller zeroes) for auxiliary functions aux[0..naux)
 // of which aux_class_off[c]..aux_class_off[c+1] have comp = c - 1.
-// The launches run on the side streams when side is not null: forked from and
-// joined back to st, or, with manage = false, on the side streams as they
-// stand (the caller orders them against st).
+// The launches run on the side streams when side is not null (forked from and
+// joined back to st).
 // atoms[0..natoms): s functions (out = first of s, p_x, p_y, p_z) of whole J
 // atoms in the chunk; when natoms > 0 the light pair classes compute all four
 // functions of an atom per thread and the remaining classes use aux (which then
@@ -60,7 +59,7 @@ PairList make_pairs(const std::vector<ShellDev> &sh, const std::vector<double> &
 void int3c(Prof &prof, cudaStream_t st, SideStreams *side, const ShellDev *sh, const int2 *pairs,
            const int2 *prange, const double *prim, const int *pair_off, const AuxDev *aux, const int *aux_class_off,
            const AuxDev *atoms, int natoms, int nao, double *out, double ka, double kb, double omega,
-           const double *boys, bool manage = true);
+           const double *boys);
 
 // out[i][j] = (P_i|Q_j) for auxiliary functions aux[0..n) with out index aux[i].out.
 // <mu| r - O |nu> for the screened AO shell pairs: out[3][nao][nao] (x, y, z),

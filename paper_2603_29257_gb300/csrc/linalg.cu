@@ -328,13 +328,13 @@ void gemm_any(Prof &prof, cudaStream_t st, const char *name, bool ta, bool tb, i
         launch_gemm<TI, TC, 4, 1>(st, ta, tb, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
     else
         launch_gemm<TI, TC, 1, 1>(st, ta, tb, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, ksplit, kchunk, ws);
-    TR_CUDA(cudaGetLastError());
+    TR_CHECK_LAUNCH(name);
     if (ksplit > 1) {
         prof.launches += 1;
         long long tot = (long long)nb * M * N;
         int blocks = (int)std::min<long long>(cdiv(tot, 256), 4096);
         splitk_reduce<TC><<<blocks, 256, 0, st>>>(M, N, nb, ksplit, ws, alpha, beta, C, ldc, bt);
-        TR_CUDA(cudaGetLastError());
+        TR_CHECK_LAUNCH(name);
     }
     prof.end(st, tok);
 }

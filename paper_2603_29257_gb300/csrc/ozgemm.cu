@@ -610,7 +610,7 @@ void oz_split(Prof &prof, cudaStream_t st, const char *name, const double *x, lo
     case 6: oz_slice_launch<6>(st, x, sr, sk, m, blocks); break;
     default: oz_slice_launch<7>(st, x, sr, sk, m, blocks); break;
     }
-    TR_CUDA(cudaGetLastError());
+    TR_CHECK_LAUNCH(name);
     prof.end(st, tok);
 }
 
@@ -641,11 +641,11 @@ void oz_col_exponent_update(cudaStream_t st, const int *row_e, int p, bool first
                             int *bad, int code)
 {
     oz_col_exponent<<<1, 32, 0, st>>>(row_e, p, first ? 1 : 0, margin, e_fixed, bad, code);
-    TR_CUDA(cudaGetLastError());
+    TR_CHECK_LAUNCH("oz_col_exponent");
     if (first) {
         const unsigned blocks = (unsigned)std::min<long long>(cdiv(m.rows, 256), 152LL * 8);
         fill_int_from<<<blocks, 256, 0, st>>>(m.e, m.rows, e_fixed);
-        TR_CUDA(cudaGetLastError());
+        TR_CHECK_LAUNCH("fill_int_from");
     }
 }
 
@@ -653,7 +653,7 @@ void oz_set_exponents(cudaStream_t st, OzMat &m, int e)
 {
     const unsigned blocks = (unsigned)std::min<long long>(cdiv(m.rows, 256), 152LL * 8);
     fill_int<<<blocks, 256, 0, st>>>(m.e, m.rows, e);
-    TR_CUDA(cudaGetLastError());
+    TR_CHECK_LAUNCH("fill_int");
 }
 
 void oz_split_cols_fixed(Prof &prof, cudaStream_t st, const char *name, const double *src, long long ld, OzMat &m,
@@ -672,7 +672,7 @@ void oz_split_cols_fixed(Prof &prof, cudaStream_t st, const char *name, const do
     case 6: oz_slice_cols<6><<<blocks, 256, 0, st>>>(src, ld, m.rows, k0, p, m.e, m.SP, m.L, m.q); break;
     default: oz_slice_cols<7><<<blocks, 256, 0, st>>>(src, ld, m.rows, k0, p, m.e, m.SP, m.L, m.q); break;
     }
-    TR_CUDA(cudaGetLastError());
+    TR_CHECK_LAUNCH("oz_slice_cols");
     prof.end(st, tok);
 }
 
@@ -759,13 +759,13 @@ void oz_gemm(Prof &prof, cudaStream_t st, const char *name, const OzMat &A, long
     case 6: oz_launch<6, 64>(st, grid, A, B, g); break;
     default: oz_launch<7, 64>(st, grid, A, B, g); break;
     }
-    TR_CUDA(cudaGetLastError());
+    TR_CHECK_LAUNCH(name);
     if (ksplit > 1) {
         const long long tot = nb * M * N;
         const unsigned blocks = (unsigned)std::min<long long>(cdiv(tot, 256), 152LL * 8);
         oz_split_reduce<<<blocks, 256, 0, st>>>(ws, ksplit, (int)nb, n2, M, N, out.d, out.s1, out.s2, out.ldm, out.ldn,
                                                 out.alpha, out.accumulate ? 1 : 0);
-        TR_CUDA(cudaGetLastError());
+        TR_CHECK_LAUNCH(name);
     }
     prof.end(st, tok);
 }

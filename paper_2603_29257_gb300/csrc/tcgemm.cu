@@ -425,7 +425,7 @@ void tc_gemm(Prof &prof, cudaStream_t st, const char *name, int nsplit, const Tc
     else if (nsplit == 3) launch_mode<3, 64>(st, grid, A, B, g, out.mode);
     else if (bn == 128) launch_mode<1, 128>(st, grid, A, B, g, out.mode);
     else launch_mode<1, 64>(st, grid, A, B, g, out.mode);
-    TR_CUDA(cudaGetLastError());
+    TR_CHECK_LAUNCH(name);
     prof.end(st, tok);
 }
 

@@ -153,16 +153,12 @@ void metric_inverse(tr_ctx *c, double *G, int n, double *Ginv, const char *what,
 
 }  // namespace
 
-void prepare_aux_chunks(tr_ctx *c, int which, int npc) { prepare_aux_chunk_sets(c, {{which, npc}}); }
-
-void prepare_aux_chunk_sets(tr_ctx *c, const std::vector<std::pair<int, int>> &sets)
+void prepare_aux_chunks(tr_ctx *c, int which, int npc)
 {
-    std::vector<AuxDev> lists;
-    std::vector<tr_ctx::AuxChunk> idx;
-    for (const auto &set : sets) {
-    const int which = set.first, npc = set.second;
     const std::vector<AuxDev> &all = which == 0 ? c->auxJ_h : c->auxK_h;
     const int n = which == 0 ? c->nJ : c->nK;
+    std::vector<AuxDev> lists;
+    std::vector<tr_ctx::AuxChunk> idx;
     for (int p0 = 0; p0 < n; p0 += npc) {
         const int np = std::min(npc, n - p0);
         tr_ctx::AuxChunk k;
@@ -189,7 +185,6 @@ void prepare_aux_chunk_sets(tr_ctx *c, const std::vector<std::pair<int, int>> &s
         }
         lists.insert(lists.end(), sorted.begin(), sorted.end());
         idx.push_back(k);
-    }
     }
     c->aux_cache_idx.clear();
     c->aux_cache.alloc(std::max<size_t>(lists.size(), 1), &c->budget, "auxiliary chunk lists");
@@ -391,58 +386,6 @@ void compute_int3c_chunk(tr_ctx *c, int which, int p0, int np, double *out)
         compute_int3c(c, c->auxK_h, p0, np, out, c->opt.k_alpha, c->opt.k_beta, c->opt.omega);
 }
 
-// The AO integral chunks of a transform loop, generated one chunk ahead: the
-// integrals of chunk i + 1 run on the side streams into the other of two
-// buffers while the context stream transforms chunk i.  Chunk i + 1 forks from
-// the context stream after the transforms of chunk i - 1 (the last reader of
-// its buffer) were queued; the context stream waits for chunk i before its
-// transforms.  The chunks' auxiliary lists are uploaded once beforehand, so
-// that no chunk needs a host synchronisation.
-struct ChunkPipe {
-    struct Chunk {
-        int which, p0, np;
-    };
-    tr_ctx *c;
-    double *buf[2];
-    std::vector<Chunk> ch;
-
-    void launch(size_t i)
-    {
-        SideStreams &sd = c->side;
-        sd.begin(c->st);
-        const Chunk &k = ch[i];
-        double *out = buf[i % 2];
-        TR_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * (size_t)k.np * c->nao * c->nao, sd.s[0]));
-        TR_CUDA(cudaEventRecord(sd.join[0], sd.s[0]));
-        for (int q = 1; q < SideStreams::N; ++q) TR_CUDA(cudaStreamWaitEvent(sd.s[q], sd.join[0], 0));
-        const tr_ctx::AuxChunk *a = nullptr;
-        for (const tr_ctx::AuxChunk &e : c->aux_cache_idx)
-            if (e.which == k.which && e.p0 == k.p0 && e.np == k.np) a = &e;
-        TR_REQUIRE(a, TR_ECUDA, "build: integral chunk list missing");
-        const AuxDev *aux = c->aux_cache.p + a->off;
-        const double ka = k.which ? c->opt.k_alpha : 1.0, kb = k.which ? c->opt.k_beta : 0.0,
-                     om = k.which ? c->opt.omega : 0.0;
-        int3c(c->prof, sd.s[0], &sd, c->shells.p, c->pairs.p, c->prange.p, c->prim.p, c->pl.off, aux, a->cls,
-              aux + a->cls[4], a->natoms, c->nao, out, ka, kb, om, c->boys.p, false);
-    }
-    void wait() { c->side.end(c->st); }
-};
-
-// The chunk sequence of a build: J chunks of npcJ functions (whole atoms), then
-// K chunks of npc; the aux lists of both chunkings uploaded once
-static std::vector<ChunkPipe::Chunk> build_chunks(tr_ctx *c, int nJt, int npcJ, bool kchunks, int npc)
-{
-    std::vector<ChunkPipe::Chunk> ch;
-    for (int p0 = 0; p0 < nJt; p0 += npcJ) ch.push_back({0, p0, std::min(npcJ, nJt - p0)});
-    if (kchunks)
-        for (int p0 = 0; p0 < c->nK; p0 += npc) ch.push_back({1, p0, std::min(npc, c->nK - p0)});
-    std::vector<std::pair<int, int>> sets;
-    if (nJt > 0) sets.push_back({0, npcJ});
-    if (kchunks) sets.push_back({1, npc});
-    prepare_aux_chunk_sets(c, sets);
-    return ch;
-}
-
 // FP64 MO transforms: (P|ia); (P|ij), (P|ab) on the window; T_ij = G_K^-1 (P|ij);
 // with Iia (full TDDFT) also (P|ia) on the window with the K operator
 static void transforms_fp64(tr_ctx *c, DevBuf<double> &Iij, DevBuf<double> *Iia)
@@ -454,45 +397,41 @@ static void transforms_fp64(tr_ctx *c, DevBuf<double> &Iij, DevBuf<double> *Iia)
     const int nJt = c->opt.j_ao ? 0 : nJ;  // the AO form of J (j_ao) stores no (P|ia)
     c->Y.alloc((size_t)nJt * nov, &c->budget, "(P|ia)");
     const int hrows = std::max(nocc, std::max(c->oK, c->vK));
-    // two integral chunks (one being generated, one being transformed) and the half transform
-    size_t per = 2 * (size_t)nao * nao + (size_t)hrows * nao;
+    size_t per = (size_t)nao * nao + (size_t)hrows * nao;
     int npc = (int)std::max<size_t>(1, c->opt.aux_chunk_bytes / (per * sizeof(double)));
     npc = std::max(1, std::min(npc, std::max(nJt, nK)));
-    const int npcJ = npc >= 4 ? npc / 4 * 4 : npc;  // whole J atoms per chunk
-    DevBuf<double> I0, I1, H;
-    I0.alloc((size_t)npc * nao * nao, &c->budget, "AO integral chunk");
-    I1.alloc((size_t)npc * nao * nao, &c->budget, "AO integral chunk");
+    DevBuf<double> I, H;
+    I.alloc((size_t)npc * nao * nao, &c->budget, "AO integral chunk");
     H.alloc((size_t)npc * hrows * nao, &c->budget, "half-transform chunk");
+    const int npcJ = npc >= 4 ? npc / 4 * 4 : npc;  // whole J atoms per chunk
+    for (int p0 = 0; p0 < nJt; p0 += npcJ) {
+        int np = std::min(npcJ, nJt - p0);
+        compute_int3c_chunk(c, 0, p0, np, I.p);
+        Batch b1;
+        b1.n1 = np;
+        b1.sB1 = (long long)nao * nao;
+        b1.sC1 = (long long)nocc * nao;
+        // the integrals are block-sparse in mu (screened pairs): only the listed row tiles
+        dgemm_ktiles(pf, st, "xform_J1", true, nocc, nao, nao, 1.0, c->C.p, nmo, I.p, nao, 0.0, H.p, nao, b1,
+                     c->ktiles);
+        Batch b2;
+        b2.n1 = np;
+        b2.sA1 = (long long)nocc * nao;
+        b2.sC1 = nov;
+        dgemm(pf, st, "xform_J2", false, false, nocc, nvir, nao, 1.0, H.p, nao, c->C.p + nocc, nmo, 0.0,
+              c->Y.p + (long long)p0 * nov, nvir, b2, nullptr, 0);
+    }
+    if (!c->k_active) return;
     const int oK = c->oK, vK = c->vK, o0 = c->o0;
-    if (c->k_active) c->Tab.alloc((size_t)nK * vK * vK, &c->budget, "T_ab");
-    ChunkPipe pipe{c, {I0.p, I1.p}, build_chunks(c, nJt, npcJ, c->k_active, npc)};
-    if (!pipe.ch.empty()) pipe.launch(0);
-    for (size_t i = 0; i < pipe.ch.size(); ++i) {
-        pipe.wait();
-        if (i + 1 < pipe.ch.size()) pipe.launch(i + 1);
-        const double *I = pipe.buf[i % 2];
-        const int p0 = pipe.ch[i].p0, np = pipe.ch[i].np;
-        if (pipe.ch[i].which == 0) {
-            Batch b1;
-            b1.n1 = np;
-            b1.sB1 = (long long)nao * nao;
-            b1.sC1 = (long long)nocc * nao;
-            // the integrals are block-sparse in mu (screened pairs): only the listed row tiles
-            dgemm_ktiles(pf, st, "xform_J1", true, nocc, nao, nao, 1.0, c->C.p, nmo, I, nao, 0.0, H.p, nao, b1,
-                         c->ktiles);
-            Batch b2;
-            b2.n1 = np;
-            b2.sA1 = (long long)nocc * nao;
-            b2.sC1 = nov;
-            dgemm(pf, st, "xform_J2", false, false, nocc, nvir, nao, 1.0, H.p, nao, c->C.p + nocc, nmo, 0.0,
-                  c->Y.p + (long long)p0 * nov, nvir, b2, nullptr, 0);
-            continue;
-        }
+    c->Tab.alloc((size_t)nK * vK * vK, &c->budget, "T_ab");
+    for (int p0 = 0; p0 < nK; p0 += npc) {
+        int np = std::min(npc, nK - p0);
+        compute_int3c_chunk(c, 1, p0, np, I.p);
         Batch h;
         h.n1 = np;
         h.sB1 = (long long)nao * nao;
         h.sC1 = (long long)oK * nao;
-        dgemm_ktiles(pf, st, "xform_K1", true, oK, nao, nao, 1.0, c->C.p + o0, nmo, I, nao, 0.0, H.p, nao, h,
+        dgemm_ktiles(pf, st, "xform_K1", true, oK, nao, nao, 1.0, c->C.p + o0, nmo, I.p, nao, 0.0, H.p, nao, h,
                      c->ktiles);
         Batch g;
         g.n1 = np;
@@ -508,14 +447,13 @@ static void transforms_fp64(tr_ctx *c, DevBuf<double> &Iij, DevBuf<double> *Iia)
                   Iia->p + (long long)p0 * oK * vK, vK, x, nullptr, 0);
         }
         h.sC1 = (long long)vK * nao;
-        dgemm_ktiles(pf, st, "xform_K1", true, vK, nao, nao, 1.0, c->C.p + nocc, nmo, I, nao, 0.0, H.p, nao, h,
+        dgemm_ktiles(pf, st, "xform_K1", true, vK, nao, nao, 1.0, c->C.p + nocc, nmo, I.p, nao, 0.0, H.p, nao, h,
                      c->ktiles);
         g.sA1 = (long long)vK * nao;
         g.sC1 = (long long)vK * vK;
         dgemm(pf, st, "xform_K2", false, false, vK, vK, nao, 1.0, H.p, nao, c->C.p + nocc, nmo, 0.0,
               c->Tab.p + (long long)p0 * vK * vK, vK, g, nullptr, 0);
     }
-    TR_CUDA(cudaStreamSynchronize(st));
 }
 
 // Slices of the Ozaki-scheme transforms for this context: 0 when the FP64
@@ -550,16 +488,12 @@ static void transforms_oz(tr_ctx *c, DevBuf<double> &Iij, DevBuf<double> *Iia, i
     const int nJt = c->opt.j_ao ? 0 : nJ;  // the AO form of J (j_ao) stores no (P|ia)
     c->Y.alloc((size_t)nJt * nov, &c->budget, "(P|ia)");
     const int hrows = std::max(nocc, std::max(c->oK, c->vK));
-    // two FP64 integral chunks (one being generated, one being transformed), the
-    // half transform and the sliced copies of both
-    const size_t per = sizeof(double) * (2 * (size_t)nao * nao + (size_t)hrows * nao) + oz_bytes(nao, nao, S) +
+    const size_t per = sizeof(double) * ((size_t)nao * nao + (size_t)hrows * nao) + oz_bytes(nao, nao, S) +
                        oz_bytes(hrows, nao, S);
     int npc = (int)std::max<size_t>(1, c->opt.aux_chunk_bytes / per);
     npc = std::max(1, std::min(npc, std::max(nJt, nK)));
-    const int npcJ = npc >= 4 ? npc / 4 * 4 : npc;  // whole J atoms per chunk
-    DevBuf<double> I0, I1, H, Ib, Hb;
-    I0.alloc((size_t)npc * nao * nao, &c->budget, "AO integral chunk");
-    I1.alloc((size_t)npc * nao * nao, &c->budget, "AO integral chunk");
+    DevBuf<double> I, H, Ib, Hb;
+    I.alloc((size_t)npc * nao * nao, &c->budget, "AO integral chunk");
     H.alloc((size_t)npc * hrows * nao, &c->budget, "half-transform chunk");
     Ib.alloc(cdiv(oz_bytes((long long)npc * nao, nao, S), 8), &c->budget, "sliced integral chunk");
     Hb.alloc(cdiv(oz_bytes((long long)npc * hrows, nao, S), 8), &c->budget, "sliced half-transform chunk");
@@ -573,24 +507,29 @@ static void transforms_oz(tr_ctx *c, DevBuf<double> &Iij, DevBuf<double> *Iia, i
         oz_split(pf, st, "oz_split_H", H.p, nao, 1, Hs);
         oz_gemm(pf, st, n2, Hs, 0, nr, Cs, s0, 0, nr, ns, np, out, (long long)nr * ldo, ldo, 1, 1.0, err);
     };
-    const int oK = c->oK, vK = c->vK, o0 = c->o0;
-    if (c->k_active) c->Tab.alloc((size_t)nK * vK * vK, &c->budget, "T_ab");
-    ChunkPipe pipe{c, {I0.p, I1.p}, build_chunks(c, nJt, npcJ, c->k_active, npc)};
-    if (!pipe.ch.empty()) pipe.launch(0);
-    for (size_t i = 0; i < pipe.ch.size(); ++i) {
-        pipe.wait();
-        if (i + 1 < pipe.ch.size()) pipe.launch(i + 1);
-        const int p0 = pipe.ch[i].p0, np = pipe.ch[i].np;
+    const int npcJ = npc >= 4 ? npc / 4 * 4 : npc;  // whole J atoms per chunk
+    for (int p0 = 0; p0 < nJt; p0 += npcJ) {
+        const int np = std::min(npcJ, nJt - p0);
+        compute_int3c_chunk(c, 0, p0, np, I.p);
         oz_bind(Is, Ib.p, (long long)np * nao, nao, S);
-        oz_split(pf, st, "oz_split_I", pipe.buf[i % 2], nao, 1, Is);
-        if (pipe.ch[i].which == 0) {
-            pair_transform(np, 0, nocc, nocc, nvir, c->Y.p + (long long)p0 * nov, nvir, "xform_J1_oz", "xform_J2_oz");
-            continue;
+        oz_split(pf, st, "oz_split_I", I.p, nao, 1, Is);
+        pair_transform(np, 0, nocc, nocc, nvir, c->Y.p + (long long)p0 * nov, nvir, "xform_J1_oz", "xform_J2_oz");
+    }
+    if (c->k_active) {
+        const int oK = c->oK, vK = c->vK, o0 = c->o0;
+        c->Tab.alloc((size_t)nK * vK * vK, &c->budget, "T_ab");
+        for (int p0 = 0; p0 < nK; p0 += npc) {
+            const int np = std::min(npc, nK - p0);
+            compute_int3c_chunk(c, 1, p0, np, I.p);
+            oz_bind(Is, Ib.p, (long long)np * nao, nao, S);
+            oz_split(pf, st, "oz_split_I", I.p, nao, 1, Is);
+            pair_transform(np, o0, oK, o0, oK, Iij.p + (long long)p0 * oK * oK, oK, "xform_K1_oz", "xform_K2_oz");
+            pair_transform(np, nocc, vK, nocc, vK, c->Tab.p + (long long)p0 * vK * vK, vK, "xform_K1_oz",
+                           "xform_K2_oz");
+            if (Iia)
+                pair_transform(np, o0, oK, nocc, vK, Iia->p + (long long)p0 * oK * vK, vK, "xform_K1_oz",
+                               "xform_Kx_oz");
         }
-        pair_transform(np, o0, oK, o0, oK, Iij.p + (long long)p0 * oK * oK, oK, "xform_K1_oz", "xform_K2_oz");
-        pair_transform(np, nocc, vK, nocc, vK, c->Tab.p + (long long)p0 * vK * vK, vK, "xform_K1_oz", "xform_K2_oz");
-        if (Iia)
-            pair_transform(np, o0, oK, nocc, vK, Iia->p + (long long)p0 * oK * vK, vK, "xform_K1_oz", "xform_Kx_oz");
     }
     int h = 0;
     TR_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -757,8 +696,7 @@ size_t footprint(tr_ctx *c)
     // build: integral and half-transform chunks, FP64 tensors
     const double hrows = std::max(nocc, std::max(oK, vK));
     const int S = xform_slices(c);
-    // two integral chunks (one generated while the other is transformed) and the half transform
-    const double per = d * (2.0 * nao * nao + hrows * nao) +
+    const double per = d * (nao * nao + hrows * nao) +
                        (S > 0 ? (double)oz_bytes(c->nao, c->nao, S) + (double)oz_bytes((long long)hrows, c->nao, S) : 0.0);
     const double npc = std::max(1.0, std::min(std::floor((double)c->opt.aux_chunk_bytes / per), std::max(nJt, nK)));
     const double cs = S > 0 ? (double)oz_bytes(c->nmo, c->nao, S) : 0.0;

@@ -28,6 +28,11 @@ namespace tr {
 namespace {
 
 constexpr double DROP_NORM = 1e-6;
+// a block kept at least this fraction of its length (1/sqrt 2) in the first
+// Gram-Schmidt pass is orthogonal to V to working precision already: the
+// second pass is skipped ("twice is enough": Kahan and Parlett's criterion,
+// as analysed by Daniel, Gragg, Kaufman and Stewart)
+constexpr double REORTH_KEEP = 0.70710678118654752440;
 constexpr double PRECOND_FLOOR = 1e-8;
 
 
@@ -511,7 +516,7 @@ struct Dav {
     size_t wsn;
     Events ev;
     double t_mv = 0, t_or = 0, t_eig = 0, t_oth = 0;
-    int k = 0, nmv = 0, nrestart = 0, it = 0, converged = 0;
+    int k = 0, nmv = 0, nrestart = 0, it = 0, converged = 0, reorth_skipped = 0;
     bool done = false, eig_timed = false, or_timed = false;
     std::vector<int> unconv;
     // pinned host copies (asynchronous device-to-host): residual norms, Ritz
@@ -527,6 +532,11 @@ struct Dav {
     // full TDDFT (Sec. 2, Eq. tddft): one basis V for X+Y and X-Y, W = (A + B) V and
     // Wm = (A - B) V, Xr = [X+Y; X-Y] and R = [R1; R2] with 2 n rows each
     bool rpa = false;
+    // one-molecule solves decide after the first Gram-Schmidt pass whether a
+    // second is needed (a host round trip); batched and served solves, whose
+    // molecules overlap on the device, always run both
+    bool adaptive = false;
+    double *h_nu = nullptr;  // pinned: norms after the first pass
 
     explicit Dav(tr_ctx *ctx) : c(ctx), st(ctx->st)
     {
@@ -554,10 +564,11 @@ struct Dav {
         max_iter = c->opt.max_iter > 0 ? c->opt.max_iter : 200;
         tol = c->opt.tol;
         // pinned host copies, allocated once per context (64 states at most)
-        if (!c->h_pin) TR_CUDA(cudaHostAlloc((void **)&c->h_pin, sizeof(double) * 132, cudaHostAllocDefault));
+        if (!c->h_pin) TR_CUDA(cudaHostAlloc((void **)&c->h_pin, sizeof(double) * 260, cudaHostAllocDefault));
         h_rn = c->h_pin;
         h_th = c->h_pin + 64;
         h_fl = (int *)(c->h_pin + 128);
+        h_nu = c->h_pin + 132;  // up to 128 new directions
         std::memset(h_fl, 0, sizeof(int) * 5);
 
         reserve_matvec(c, pmax);
@@ -1090,8 +1101,18 @@ struct Dav {
         norms_of(c->T.p, pp, c->rn.p);
         TR_LAUNCH(pf, st, "normalise", 0, 16.0 * pp * nov,
                   row_scale_inv<<<dim3(nblk, pp), 256, 0, st>>>(c->T.p, pp, nov, c->rn.p));
-        // two passes of block classical Gram-Schmidt against V[0:k]
+        // two passes of block classical Gram-Schmidt against V[0:k] (the second
+        // skipped in one-molecule solves when the first kept every vector long)
         for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 1 && adaptive && pp <= 128) {
+                norms_of(c->T.p, pp, c->rn.p);
+                TR_CUDA(cudaMemcpyAsync(h_nu, c->rn.p, sizeof(double) * pp, cudaMemcpyDeviceToHost, st));
+                TR_CUDA(cudaStreamSynchronize(st));
+                if (*std::min_element(h_nu, h_nu + pp) >= REORTH_KEEP) {
+                    ++reorth_skipped;
+                    break;
+                }
+            }
             if (tcd) {
                 OzMat Ts;
                 oz_bind(Ts, c->dvs_T.p, pp, (int)nov, OZ_SLICES_FP64);
@@ -1177,6 +1198,7 @@ int solve(tr_ctx *c, double *omega, double *Xout, double *Xmout, double *resid, 
     TR_REQUIRE(omega, TR_EINVAL, "solve: omega must not be NULL");
     TR_REQUIRE(!Xmout || c->opt.tddft, TR_EINVAL, "solve: X-Y is returned for tddft = 1 only");
     Dav d(c);
+    d.adaptive = true;
     d.guess();
     d.apply_pending();
     d.absorb();

@@ -483,6 +483,255 @@ __global__ void __launch_bounds__(SACC ? 64 : 128)
     }
 }
 
+// Cartesian index of (ax, ay, l - ax - ay) in the order of cexp
+__host__ __device__ constexpr int cidx(int l, int ax, int ay) { return (l - ax) * (l - ax + 1) / 2 + (l - ax - ay); }
+
+// Heavy pair classes: a warp takes 32 / TW AO shell pairs, TW lanes each, one
+// lane per auxiliary atom (the s, p_x, p_y, p_z functions of a J atom, which
+// share the Boys values and R up to LA+LB+1) or per auxiliary s function.
+// CM selects the functions a launch computes (bit 0 s, 1 p_x, 2 p_y, 3 p_z;
+// the outputs go to planes out + 0 .. 3 of the atom).  Small tiles keep the
+// lanes busy for chunks of few atoms; the shell pairs of a class are sorted by
+// their number of kept primitive pairs, so the pairs of a warp mostly run
+// loops of equal length (a shorter one idles with a zero prefactor to the end
+// of the warp's loop).
+//  - The Hermite coefficients of a primitive pair depend on the pair alone:
+//    three lanes of the pair's group compute them (one direction each) into
+//    shared memory, and the group reads them from there.
+//  - The prefactor 2 pi^{5/2} K / (p c sqrt(p+c)) is folded into R^n_000
+//    (R is linear in it); the p functions' common factor -1/(2c) is applied
+//    once, after the sums over primitive pairs.
+//  - The contraction sum_tuv Ex_t Ey_u Ez_v R_{t+dx,u+dy,v+dz} is factorised:
+//    W(t,u) = sum_v Ez_v R_{t,u,v(+1)} per z exponent pair, then
+//    V(t) = sum_u Ey_u W(t,u(+1)) per y exponent pair, then the x sum, which
+//    starts from the running total.  Every partial sum is computed once and
+//    shared by the outputs that use it; the x exponents of an output follow
+//    from its y and z exponents, since the shells' l are fixed.
+// FP64 instructions are the scarce resource on this GPU, so the warp spends
+// them on the contraction and little else.
+__host__ __device__ constexpr int popc4(int m) { return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1) + ((m >> 3) & 1); }
+
+template <int LA, int LB, int CM>
+struct WarpK {
+    static constexpr int TW = 8;          // lanes (auxiliary atoms or functions) per shell pair
+    static constexpr int PPW = 32 / TW;   // shell pairs per warp
+    static constexpr int NAB = ncart(LA) * ncart(LB);
+    static constexpr int NF = popc4(CM);
+    static constexpr int NACC = NF * NAB;
+    // the sums in shared memory, one column per lane, where registers would spill
+    static constexpr bool SACC = NACC > 40 || (LA == 2 && LB == 2);
+    static constexpr int WARPS = NACC > 80 ? 1 : 2;  // warps per block
+    static constexpr size_t SMEM = SACC ? sizeof(double) * 32 * WARPS * NACC : 0;
+    // slot of function f (0..3) among the selected ones
+    __host__ __device__ static constexpr int slot(int f) { return popc4(CM & ((1 << f) - 1)); }
+};
+
+template <int LA, int LB, int CM>
+__global__ void __launch_bounds__(32 * WarpK<LA, LB, CM>::WARPS)
+    int3c_warp_kernel(const ShellDev *__restrict__ sh, const int2 *__restrict__ pairs, const int2 *__restrict__ prange,
+                      const double *__restrict__ prim, int npair, const AuxDev *__restrict__ aux, int naux, int nao,
+                      double *__restrict__ out, double ka, double kb, double omega, const double *__restrict__ boys)
+{
+    using K = WarpK<LA, LB, CM>;
+    constexpr bool FS = CM & 1, FX = CM & 2, FY = CM & 4, FZ = CM & 8;
+    constexpr int G = (FX || FY || FZ) ? 1 : 0;  // one more Hermite order for the p functions
+    constexpr int L = LA + LB + G;
+    constexpr int NCB = ncart(LB), NAB = K::NAB;
+    constexpr int NT = LA + LB + 1, NE = (LA + 1) * (LB + 1) * NT;
+    __shared__ double sE[K::WARPS][K::PPW][3 * NE];
+    extern __shared__ double sacc[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sub = lane / K::TW, sl = lane % K::TW;
+    const int ip0 = (blockIdx.x * K::WARPS + warp) * K::PPW;
+    if (ip0 >= npair) return;  // whole warps leave: the kernel has no block-wide barrier
+    const bool own = ip0 + sub < npair;
+    const int ip = own ? ip0 + sub : npair - 1;
+    const int ic = blockIdx.y * K::TW + sl;
+    const bool store = own && ic < naux;
+    // idle lanes compute on a valid pair and function and store nothing
+    const AuxDev c = aux[ic < naux ? ic : naux - 1];
+    const int2 pr = pairs[ip];
+    const ShellDev A = sh[pr.x], B = sh[pr.y];
+    double *E = sE[warp][sub];
+    // the contraction re-reads the coefficients where it uses them (shared
+    // memory reads are cheap here) rather than holding all of them in registers
+    const volatile double *Ev = E;
+
+    double racc[K::SACC ? 1 : K::NACC];
+    double *wacc = sacc + (size_t)warp * K::NACC * 32 + lane;
+    // running sum of function f (0..3) for Cartesian pair k
+    auto acc = [&](int f, int k) -> double & {
+        if constexpr (K::SACC)
+            return wacc[(K::slot(f) * NAB + k) * 32];
+        else
+            return racc[K::slot(f) * NAB + k];
+    };
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+        if (CM & (1 << f))
+#pragma unroll
+            for (int k = 0; k < NAB; ++k) acc(f, k) = 0.0;
+
+    const double ce = c.e, ice = 1.0 / ce;
+    const double cpre = TWO_PI_52 * ice;
+    const int2 rg = prange[ip];  // every kept shell pair has at least one primitive pair
+    const int nq = own ? rg.y : 0;
+    const int nqmax = __reduce_max_sync(0xffffffffu, nq);
+    for (int it = 0; it < nqmax; ++it) {
+        const bool live = it < nq;
+        const double *pq = prim + 6LL * (rg.x + (live ? it : 0));
+        const double Px = pq[0], Py = pq[1], Pz = pq[2], p = pq[3], ip_ = pq[4];
+        const double Kab = live ? pq[5] : 0.0;  // a finished pair adds exact zeros
+        __syncwarp();  // the previous primitive pair's coefficients are read by all lanes
+        if (sl < 3) {
+            const double Pd = sl == 0 ? Px : (sl == 1 ? Py : Pz);
+            const double Ad = sl == 0 ? A.x : (sl == 1 ? A.y : A.z);
+            const double Bd = sl == 0 ? B.x : (sl == 1 ? B.y : B.z);
+            double Ed[LA + 1][LB + 1][NT];
+            hermite_E<LA, LB>(Pd - Ad, Pd - Bd, 0.5 * ip_, Ed);
+#pragma unroll
+            for (int i = 0; i <= LA; ++i)
+#pragma unroll
+                for (int j = 0; j <= LB; ++j)
+#pragma unroll
+                    for (int t = 0; t <= i + j; ++t) E[sl * NE + (i * (LB + 1) + j) * NT + t] = Ed[i][j][t];
+        }
+        __syncwarp();
+        const double u = 1.0 / (p + ce);
+        const double rho = p * ce * u;
+        const double X = Px - c.x, Y = Py - c.y, Z = Pz - c.z;
+        double Rn[L + 1];
+        coulomb_aux<L>(rho, rho * (X * X + Y * Y + Z * Z), ka, kb, omega, boys, Rn);
+        const double pref = (Kab * ip_) * (cpre * sqrt(u));
+#pragma unroll
+        for (int n = 0; n <= L; ++n) Rn[n] *= pref;
+        double R[L + 1][L + 1][L + 1];
+        hermite_R<L>(X, Y, Z, Rn, R);
+
+        // pass 0: the s, x and y functions from W(t,w) = sum_v ez_v R_{t,w,v};
+        // pass 1: the z function from W(t,w) = sum_v ez_v R_{t,w,v+1}; one W
+        // at a time is live
+#pragma unroll
+        for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 0 && !(FS || FX || FY)) continue;
+            if (pass == 1 && !FZ) continue;
+#pragma unroll
+            for (int az = 0; az <= LA; ++az)
+#pragma unroll
+                for (int bz = 0; bz <= LB; ++bz) {
+                    const int nz = az + bz;
+                    double ez[NT];
+#pragma unroll
+                    for (int v = 0; v <= nz; ++v) ez[v] = Ev[2 * NE + (az * (LB + 1) + bz) * NT + v];
+                    double W[L + 1][L + 1];
+#pragma unroll
+                    for (int t = 0; t <= L; ++t)
+#pragma unroll
+                        for (int w = 0; w <= L - t; ++w)
+                            if (t + w + nz + pass <= L) {
+                                double s = 0.0;
+#pragma unroll
+                                for (int v = 0; v <= nz; ++v)
+                                    s = fma(ez[v], R[t][w][v + pass <= L ? v + pass : L], s);
+                                W[t][w] = s;
+                            }
+#pragma unroll
+                    for (int ay = 0; ay <= LA - az; ++ay)
+#pragma unroll
+                        for (int by = 0; by <= LB - bz; ++by) {
+                            const int ny = ay + by;
+                            const int ax = LA - ay - az, bx = LB - by - bz, nx = ax + bx;
+                            const int k = cidx(LA, ax, ay) * NCB + cidx(LB, bx, by);
+                            double ey[NT], ex[NT];
+#pragma unroll
+                            for (int w = 0; w <= ny; ++w) ey[w] = Ev[NE + (ay * (LB + 1) + by) * NT + w];
+#pragma unroll
+                            for (int t = 0; t <= nx; ++t) ex[t] = Ev[(ax * (LB + 1) + bx) * NT + t];
+                            if (pass == 0) {
+                                // Vs(t) = sum_w ey_w W(t,w), for t <= nx + 1 when the x
+                                // function reads it one step on; Vy(t) = sum_w ey_w W(t,w+1)
+                                double Vs[L + 1], Vy[L + 1];
+#pragma unroll
+                                for (int t = 0; t <= nx + (FX ? 1 : 0); ++t) {
+                                    if (FS || FX) {
+                                        double s = 0.0;
+#pragma unroll
+                                        for (int w = 0; w <= ny; ++w) s = fma(ey[w], W[t][w], s);
+                                        Vs[t] = s;
+                                    }
+                                    if (FY && t <= nx) {
+                                        double sy = 0.0;
+#pragma unroll
+                                        for (int w = 0; w <= ny; ++w)
+                                            sy = fma(ey[w], W[t][w + 1 <= L ? w + 1 : L], sy);
+                                        Vy[t] = sy;
+                                    }
+                                }
+                                if (FS) {
+                                    double s0 = acc(0, k);
+#pragma unroll
+                                    for (int t = 0; t <= nx; ++t) s0 = fma(ex[t], Vs[t], s0);
+                                    acc(0, k) = s0;
+                                }
+                                if (FX) {
+                                    double sx = acc(1, k);
+#pragma unroll
+                                    for (int t = 0; t <= nx; ++t) sx = fma(ex[t], Vs[t + 1 <= L ? t + 1 : L], sx);
+                                    acc(1, k) = sx;
+                                }
+                                if (FY) {
+                                    double sy = acc(2, k);
+#pragma unroll
+                                    for (int t = 0; t <= nx; ++t) sy = fma(ex[t], Vy[t], sy);
+                                    acc(2, k) = sy;
+                                }
+                            } else {
+                                double sz = acc(3, k);
+#pragma unroll
+                                for (int t = 0; t <= nx; ++t) {
+                                    double s = 0.0;
+#pragma unroll
+                                    for (int w = 0; w <= ny; ++w) s = fma(ey[w], W[t][w], s);
+                                    sz = fma(ex[t], s, sz);
+                                }
+                                acc(3, k) = sz;
+                            }
+                        }
+                }
+        }
+    }
+    if (!store) return;
+    constexpr int NSA = 2 * LA + 1, NSB = 2 * LB + 1, NCA = ncart(LA);
+    const double pfac = -0.5 * ice;  // p functions: 1/(2c) and the sign of the derivative on the ket
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        if (!(CM & (1 << f))) continue;
+        double *o = out + (long long)(c.out + f) * nao * nao;
+#pragma unroll
+        for (int sa = 0; sa < NSA; ++sa) {
+#pragma unroll
+            for (int sb = 0; sb < NSB; ++sb) {
+                double v = 0.0;
+#pragma unroll
+                for (int ka_ = 0; ka_ < NCA; ++ka_) {
+                    const double wa = LA == 2 ? d_sph(sa, ka_) : (ka_ == sa ? 1.0 : 0.0);
+                    if (wa == 0.0) continue;
+#pragma unroll
+                    for (int kb_ = 0; kb_ < NCB; ++kb_) {
+                        const double wb = LB == 2 ? d_sph(sb, kb_) : (kb_ == sb ? 1.0 : 0.0);
+                        if (wb == 0.0) continue;
+                        v = fma(wa * wb, acc(f, ka_ * NCB + kb_), v);
+                    }
+                }
+                if (f) v *= pfac;
+                const int mu = A.ao + sa, nu = B.ao + sb;
+                o[(long long)mu * nao + nu] = v;
+                o[(long long)nu * nao + mu] = v;
+            }
+        }
+    }
+}
+
 // Dipole integrals <mu| r - O |nu> of one AO shell pair per thread (Sec. 2, Eq.
 // transition): per direction the first moment about O of the Hermite expansion,
 //   M^{ij} = (E^{ij}_1 + (P - O) E^{ij}_0) sqrt(pi/p),
@@ -557,6 +806,26 @@ __global__ void __launch_bounds__(128)
     }
 }
 
+template <int LA, int LB, int CM>
+void launch_warp(Prof &prof, cudaStream_t st, const char *name, const ShellDev *sh, const int2 *pairs,
+                 const int2 *prange, const double *prim, int npair, const AuxDev *aux, int naux, int nao, double *out,
+                 double ka, double kb, double omega, const double *boys)
+{
+    using K = WarpK<LA, LB, CM>;
+    static const cudaError_t attr =
+        K::SMEM > 48 * 1024 ? cudaFuncSetAttribute(int3c_warp_kernel<LA, LB, CM>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM)
+                            : cudaSuccess;
+    TR_CUDA(attr);
+    dim3 grid(cdiv(npair, K::WARPS * K::PPW), cdiv(naux, K::TW));
+    double bytes = 8.0 * 2.0 * K::NF * npair * naux * (2 * LA + 1) * (2 * LB + 1);
+    int tok = prof.begin(st, name, 0, bytes);
+    int3c_warp_kernel<LA, LB, CM><<<grid, 32 * K::WARPS, K::SMEM, st>>>(sh, pairs, prange, prim, npair, aux, naux,
+                                                                         nao, out, ka, kb, omega, boys);
+    TR_CHECK_LAUNCH(name);
+    prof.end(st, tok);
+}
+
 template <int LA, int LB>
 void launch_pair_class(Prof &prof, const cudaStream_t *streams, int nstreams, int &next, int cls,
                        const ShellDev *sh, const int2 *pairs, const int2 *prange, const double *prim, int npair,
@@ -564,6 +833,35 @@ void launch_pair_class(Prof &prof, const cudaStream_t *streams, int nstreams, in
                        double ka, double kb, double omega, const double *boys)
 {
     static const char *names[6] = {"int3c_ss", "int3c_ps", "int3c_pp", "int3c_ds", "int3c_dp", "int3c_dd"};
+    if constexpr (LA + LB >= 2) {
+        // classes whose Hermite coefficients are worth sharing across the
+        // auxiliary functions: shell pairs by warps, auxiliary atoms (the whole
+        // J atoms of a grouped chunk) or s functions by lanes.  A chunk of
+        // fewer than one lane tile of them (large molecules, whose chunks hold
+        // few functions) keeps the kernels with one lane per shell pair.
+        if (npair <= 0) return;
+        const int ns = aoff[1] - aoff[0];
+        constexpr int TW = WarpK<LA, LB, 1>::TW;
+        if (natoms >= TW) {
+            if constexpr (LA == 2 && LB == 2) {
+                // d-d: the s, p_x and the p_y, p_z functions in two launches, so
+                // that a warp's sums leave room for more warps on an SM
+                launch_warp<LA, LB, 3>(prof, streams[next++ % nstreams], names[cls], sh, pairs, prange, prim, npair,
+                                       atoms, natoms, nao, out, ka, kb, omega, boys);
+                launch_warp<LA, LB, 12>(prof, streams[next++ % nstreams], names[cls], sh, pairs, prange, prim, npair,
+                                        atoms, natoms, nao, out, ka, kb, omega, boys);
+            } else {
+                launch_warp<LA, LB, 15>(prof, streams[next++ % nstreams], names[cls], sh, pairs, prange, prim, npair,
+                                        atoms, natoms, nao, out, ka, kb, omega, boys);
+            }
+            return;
+        }
+        if (ns >= TW && aoff[4] == aoff[1]) {
+            launch_warp<LA, LB, 1>(prof, streams[next++ % nstreams], names[cls], sh, pairs, prange, prim, npair,
+                                   aux + aoff[0], ns, nao, out, ka, kb, omega, boys);
+            return;
+        }
+    }
     if constexpr (ncart(LA) * ncart(LB) <= 18) {
     if (natoms > 0 && npair > 0) {
         // whole J atoms (s + p) in one pass: sums in registers for the light

@@ -149,44 +149,127 @@ __global__ void splitk_reduce(int M, int N, int nbatch, int ksplit, const double
 
 // ---------------------------------------------------------------- Cholesky
 
-// One launch per column k.  Warp w of each block owns row i; lanes split the
-// dot product over j < k.  The diagonal of L is kept in dg[] until the end so
-// that G[k][k] stays readable by every block of the launch.
-__global__ void chol_column(double *G, int n, int k, double *dg, int *flag)
+// Blocked right-looking Cholesky, panels of CB columns: factor the diagonal
+// block (chol_diag), solve the rows below it against that block (chol_panel),
+// subtract the panel's outer product from the trailing lower triangle
+// (chol_update).  Three launches per panel; only the lower triangle and the
+// diagonal are read or written.
+constexpr int CB = 32;
+
+// the diagonal block G[k0 .. k0+b)^2 in shared memory, one thread per element:
+// column j is scaled by its pivot, then the block's trailing part is updated
+__global__ void __launch_bounds__(CB * CB) chol_diag(double *G, int n, int k0, int b, int *flag)
 {
-    __shared__ double s_lkk;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (warp == 0) {
-        double s = 0.0;
-        for (int j = lane; j < k; j += 32) s = fma(G[(long long)k * n + j], G[(long long)k * n + j], s);
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) {
-            double d = G[(long long)k * n + k] - s;
+    __shared__ double A[CB][CB + 1];
+    const int m = threadIdx.x, i = threadIdx.y;
+    const bool in = i < b && m <= i;
+    if (in) A[i][m] = G[(long long)(k0 + i) * n + k0 + m];
+    __syncthreads();
+    for (int j = 0; j < b; ++j) {
+        if (i == j && m == j) {
+            double d = A[j][j];
             if (!(d > 0.0)) {
-                if (blockIdx.x == 0) atomicCAS(flag, 0, k + 1);
+                atomicCAS(flag, 0, k0 + j + 1);  // the first non-positive pivot is kept
                 d = 1.0;
             }
-            s_lkk = sqrt(d);
-            if (blockIdx.x == 0) dg[k] = s_lkk;
+            A[j][j] = sqrt(d);
         }
+        __syncthreads();
+        if (m == j && i > j && i < b) A[i][j] = A[i][j] / A[j][j];
+        __syncthreads();
+        if (i > j && i < b && m > j && m <= i) A[i][m] = fma(-A[i][j], A[m][j], A[i][m]);
+        __syncthreads();
+    }
+    if (in) G[(long long)(k0 + i) * n + k0 + m] = A[i][m];
+}
+
+// rows i >= k0 + b: L[i][k0 .. k0+b) = G[i][k0 .. k0+b) L11^-T, one thread per row
+__global__ void __launch_bounds__(128) chol_panel(double *G, int n, int k0, int b)
+{
+    __shared__ double L11[CB][CB + 1];
+    for (int t = threadIdx.x; t < CB * CB; t += blockDim.x) {
+        const int r = t / CB, s = t % CB;
+        if (r < b && s <= r) L11[r][s] = G[(long long)(k0 + r) * n + k0 + s];
     }
     __syncthreads();
-    const double lkk = s_lkk;
-    for (int i = k + 1 + blockIdx.x * nw + warp; i < n; i += gridDim.x * nw) {
-        double s = 0.0;
-        for (int j = lane; j < k; j += 32) s = fma(G[(long long)i * n + j], G[(long long)k * n + j], s);
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) G[(long long)i * n + k] = (G[(long long)i * n + k] - s) / lkk;
+    const int i = k0 + b + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double *row = G + (long long)i * n + k0;
+    double x[CB];
+#pragma unroll
+    for (int j = 0; j < CB; ++j) {
+        if (j < b) {
+            double s = row[j];
+#pragma unroll
+            for (int q = 0; q < j; ++q) s = fma(-x[q], L11[j][q], s);
+            x[j] = s / L11[j][j];
+            row[j] = x[j];
+        }
     }
 }
 
-__global__ void chol_finish(double *G, int n, const double *dg)
+// G[i][j] -= sum_q L[i][k0+q] L[j][k0+q] for k1 <= j <= i < n, k1 = k0 + b:
+// 32 x 32 tiles of the trailing lower triangle, 2 x 2 elements per thread
+__global__ void __launch_bounds__(256) chol_update(double *G, int n, int k0, int b)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        G[(long long)i * n + i] = dg[i];
+    const int ti = blockIdx.y, tj = blockIdx.x;
+    if (tj > ti) return;
+    const int k1 = k0 + b;
+    const int i0 = k1 + ti * 32, j0 = k1 + tj * 32;
+    __shared__ double Pi[32][CB + 1], Pj[32][CB + 1];
+    for (int t = threadIdx.x; t < 32 * CB; t += blockDim.x) {
+        const int r = t / CB, q = t % CB;
+        Pi[r][q] = (i0 + r < n && q < b) ? G[(long long)(i0 + r) * n + k0 + q] : 0.0;
+        Pj[r][q] = (j0 + r < n && q < b) ? G[(long long)(j0 + r) * n + k0 + q] : 0.0;
+    }
+    __syncthreads();
+    const int r0 = (threadIdx.x / 16) * 2, c0 = (threadIdx.x % 16) * 2;
+    double s[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+#pragma unroll 8
+    for (int q = 0; q < CB; ++q)
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) s[a][e] = fma(Pi[r0 + a][q], Pj[c0 + e][q], s[a][e]);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int i = i0 + r0 + a, j = j0 + c0 + e;
+            if (i < n && j <= i) G[(long long)i * n + j] -= s[a][e];
+        }
 }
 
-// Linv[i][c] (lower) = column c of L^-1 by forward substitution; thread per column.
+// Linv[i][c] (lower) = column c of L^-1, one warp per column: x_c = 1 / L_cc,
+// x_i = -(sum_{c <= j < i} L_ij x_j) / L_ii for i > c, the sums over lanes;
+// x and the reciprocal diagonal in shared memory.
+__global__ void tri_inverse_warp(const double *__restrict__ L, int n, double *__restrict__ Linv)
+{
+    extern __shared__ double tsm[];
+    double *rd = tsm;  // 1 / L_ii
+    const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *x = tsm + n + (size_t)warp * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) rd[i] = 1.0 / L[(long long)i * n + i];
+    __syncthreads();
+    const int c = blockIdx.x * wpb + warp;
+    if (c >= n) return;
+    for (int i = lane; i < c; i += 32) Linv[(long long)i * n + c] = 0.0;
+    if (lane == 0) x[c] = rd[c];
+    __syncwarp();
+    for (int i = c + 1; i < n; ++i) {
+        const double *Li = L + (long long)i * n;
+        double s = 0.0;
+        for (int j = c + lane; j < i; j += 32) s = fma(Li[j], x[j], s);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) x[i] = -s * rd[i];
+        __syncwarp();
+    }
+    for (int i = c + lane; i < n; i += 32) Linv[(long long)i * n + c] = x[i];
+}
+
+// Linv[i][c] (lower) = column c of L^-1 by forward substitution, one thread per
+// column: for orders too large for tri_inverse_warp's shared memory.
 __global__ void tri_inverse_cols(const double *__restrict__ L, int n, double *__restrict__ Linv)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -388,26 +471,38 @@ void sgemm(Prof &prof, cudaStream_t st, const char *name, bool ta, bool tb, int 
 void cholesky(Prof &prof, cudaStream_t st, double *G, int n, int *flag)
 {
     if (n <= 0) return;
-    double *dg = nullptr;
-    TR_CUDA(cudaMallocAsync(&dg, sizeof(double) * n, st));
     int tok = prof.begin(st, "cholesky", n * (double)n * n / 3.0, 8.0 * n * n);
-    for (int k = 0; k < n; ++k) {
-        int rows = n - k - 1;
-        int blocks = std::max(1, std::min(1024, (rows + 7) / 8));
-        chol_column<<<blocks, 256, 0, st>>>(G, n, k, dg, flag);
+    for (int k0 = 0; k0 < n; k0 += CB) {
+        const int b = std::min(CB, n - k0), rest = n - k0 - b;
+        chol_diag<<<1, dim3(CB, CB), 0, st>>>(G, n, k0, b, flag);
         prof.launches += 1;
+        if (rest > 0) {
+            chol_panel<<<cdiv(rest, 128), 128, 0, st>>>(G, n, k0, b);
+            const unsigned nt = cdiv(rest, 32);
+            chol_update<<<dim3(nt, nt), 256, 0, st>>>(G, n, k0, b);
+            prof.launches += 2;
+        }
     }
-    chol_finish<<<cdiv(n, 256), 256, 0, st>>>(G, n, dg);
-    TR_CUDA(cudaGetLastError());
+    TR_CHECK_LAUNCH("cholesky");
     prof.end(st, tok);
-    TR_CUDA(cudaFreeAsync(dg, st));
 }
 
 void chol_inverse(Prof &prof, cudaStream_t st, const double *L, int n, double *Ginv, double *work)
 {
     if (n <= 0) return;
-    TR_LAUNCH(prof, st, "tri_inverse", n * (double)n * n / 3.0, 8.0 * n * n,
-              tri_inverse_cols<<<cdiv(n, 64), 64, 0, st>>>(L, n, work));
+    // warps (columns) per block: x of each and 1/L_ii in at most 200 KB of shared memory
+    const int wpb = std::min<long long>(8, std::max<long long>(0, 200LL * 1024 / (8LL * n) - 1));
+    if (wpb >= 1) {
+        static const cudaError_t attr =
+            cudaFuncSetAttribute(tri_inverse_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        TR_CUDA(attr);
+        const size_t smem = sizeof(double) * (size_t)n * (1 + wpb);
+        TR_LAUNCH(prof, st, "tri_inverse", n * (double)n * n / 3.0, 8.0 * n * n,
+                  tri_inverse_warp<<<cdiv(n, wpb), 32 * wpb, smem, st>>>(L, n, work));
+    } else {
+        TR_LAUNCH(prof, st, "tri_inverse", n * (double)n * n / 3.0, 8.0 * n * n,
+                  tri_inverse_cols<<<cdiv(n, 64), 64, 0, st>>>(L, n, work));
+    }
     // Ginv = Linv^T Linv
     dgemm(prof, st, "metric_inverse", true, false, n, n, n, 1.0, work, n, work, n, 0.0, Ginv, n,
           Batch(), nullptr, 0);

@@ -70,6 +70,15 @@ __global__ void unpermute_T2(const double *__restrict__ T2, int nK, int oK, doub
     }
 }
 
+// J functions per integral chunk: whole atoms (s, p_x, p_y, p_z), and a
+// multiple of 8 atoms (the lane tile of the heavy integral kernels) where at
+// least 8 fit
+int j_chunk(int npc)
+{
+    if (npc >= 32) return npc / 32 * 32;
+    return npc >= 4 ? npc / 4 * 4 : npc;
+}
+
 unsigned grid_for(long long n) { return (unsigned)std::max<long long>(1, std::min<long long>(cdiv(n, 256), 152 * 16)); }
 
 // class-sorted copy of auxiliary functions with out index in [p0, p0+np);
@@ -403,7 +412,7 @@ static void transforms_fp64(tr_ctx *c, DevBuf<double> &Iij, DevBuf<double> *Iia)
     DevBuf<double> I, H;
     I.alloc((size_t)npc * nao * nao, &c->budget, "AO integral chunk");
     H.alloc((size_t)npc * hrows * nao, &c->budget, "half-transform chunk");
-    const int npcJ = npc >= 4 ? npc / 4 * 4 : npc;  // whole J atoms per chunk
+    const int npcJ = j_chunk(npc);
     for (int p0 = 0; p0 < nJt; p0 += npcJ) {
         int np = std::min(npcJ, nJt - p0);
         compute_int3c_chunk(c, 0, p0, np, I.p);
@@ -507,7 +516,7 @@ static void transforms_oz(tr_ctx *c, DevBuf<double> &Iij, DevBuf<double> *Iia, i
         oz_split(pf, st, "oz_split_H", H.p, nao, 1, Hs);
         oz_gemm(pf, st, n2, Hs, 0, nr, Cs, s0, 0, nr, ns, np, out, (long long)nr * ldo, ldo, 1, 1.0, err);
     };
-    const int npcJ = npc >= 4 ? npc / 4 * 4 : npc;  // whole J atoms per chunk
+    const int npcJ = j_chunk(npc);
     for (int p0 = 0; p0 < nJt; p0 += npcJ) {
         const int np = std::min(npcJ, nJt - p0);
         compute_int3c_chunk(c, 0, p0, np, I.p);

@@ -33,6 +33,12 @@ struct tr_ctx {
     std::vector<int> kt_list_h, kt_count_h;
     tr::DevBuf<int> kt_list, kt_count;
     tr::KTiles ktiles;
+    // the same pattern in K blocks of 32 functions per 64-function tile, for the
+    // tensor-core transforms: kb_list[nt * kb_ld + t] for t < kb_count[nt]
+    std::vector<int> kb_list_h, kb_count_h;
+    tr::DevBuf<int> kb_list, kb_count;
+    tr::DevBuf<unsigned char> kb_mask;  // [nt][kb]: block kb listed for tile nt
+    int kb_ld = 0;
     tr::DevBuf<tr::ShellDev> shells;
     tr::DevBuf<double> pexp, pcoef, boys, prim;
     tr::DevBuf<int2> pairs, prange;

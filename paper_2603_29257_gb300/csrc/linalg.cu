@@ -156,8 +156,10 @@ __global__ void splitk_reduce(int M, int N, int nbatch, int ksplit, const double
 // diagonal are read or written.
 constexpr int CB = 32;
 
-// the diagonal block G[k0 .. k0+b)^2 in shared memory, one thread per element:
-// column j is scaled by its pivot, then the block's trailing part is updated
+// the diagonal block G[k0 .. k0+b)^2 in shared memory, one thread per
+// element; per column j: the entries below the pivot are scaled (each thread
+// takes the pivot's square root itself, the pivot is written afterwards), then
+// the block's trailing part is updated; two barriers per column
 __global__ void __launch_bounds__(CB * CB) chol_diag(double *G, int n, int k0, int b, int *flag)
 {
     __shared__ double A[CB][CB + 1];
@@ -166,46 +168,60 @@ __global__ void __launch_bounds__(CB * CB) chol_diag(double *G, int n, int k0, i
     if (in) A[i][m] = G[(long long)(k0 + i) * n + k0 + m];
     __syncthreads();
     for (int j = 0; j < b; ++j) {
-        if (i == j && m == j) {
+        double ljj = 0.0;
+        if (m == j && i >= j && i < b) {
             double d = A[j][j];
             if (!(d > 0.0)) {
-                atomicCAS(flag, 0, k0 + j + 1);  // the first non-positive pivot is kept
+                if (i == j) atomicCAS(flag, 0, k0 + j + 1);  // the first non-positive pivot is kept
                 d = 1.0;
             }
-            A[j][j] = sqrt(d);
+            ljj = sqrt(d);
+            if (i > j) A[i][j] = A[i][j] / ljj;
         }
         __syncthreads();
-        if (m == j && i > j && i < b) A[i][j] = A[i][j] / A[j][j];
-        __syncthreads();
+        if (i == j && m == j) A[j][j] = ljj;
         if (i > j && i < b && m > j && m <= i) A[i][m] = fma(-A[i][j], A[m][j], A[i][m]);
         __syncthreads();
     }
     if (in) G[(long long)(k0 + i) * n + k0 + m] = A[i][m];
 }
 
-// rows i >= k0 + b: L[i][k0 .. k0+b) = G[i][k0 .. k0+b) L11^-T, one thread per row
-__global__ void __launch_bounds__(128) chol_panel(double *G, int n, int k0, int b)
+// rows i >= k0 + b: L[i][k0 .. k0+b) = G[i][k0 .. k0+b) L11^-T, one thread per
+// row (the row's entries loaded first; two partial sums per entry)
+__global__ void __launch_bounds__(32) chol_panel(double *G, int n, int k0, int b)
 {
     __shared__ double L11[CB][CB + 1];
+    __shared__ double rdg[CB];
     for (int t = threadIdx.x; t < CB * CB; t += blockDim.x) {
         const int r = t / CB, s = t % CB;
         if (r < b && s <= r) L11[r][s] = G[(long long)(k0 + r) * n + k0 + s];
     }
+    __syncthreads();
+    if (threadIdx.x < b) rdg[threadIdx.x] = 1.0 / L11[threadIdx.x][threadIdx.x];
     __syncthreads();
     const int i = k0 + b + blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double *row = G + (long long)i * n + k0;
     double x[CB];
 #pragma unroll
+    for (int j = 0; j < CB; ++j) x[j] = j < b ? row[j] : 0.0;
+#pragma unroll
     for (int j = 0; j < CB; ++j) {
         if (j < b) {
-            double s = row[j];
+            double s0 = x[j], s1 = 0.0;
 #pragma unroll
-            for (int q = 0; q < j; ++q) s = fma(-x[q], L11[j][q], s);
-            x[j] = s / L11[j][j];
-            row[j] = x[j];
+            for (int q = 0; q < j; ++q) {
+                if (q & 1)
+                    s1 = fma(-x[q], L11[j][q], s1);
+                else
+                    s0 = fma(-x[q], L11[j][q], s0);
+            }
+            x[j] = (s0 + s1) * rdg[j];
         }
     }
+#pragma unroll
+    for (int j = 0; j < CB; ++j)
+        if (j < b) row[j] = x[j];
 }
 
 // G[i][j] -= sum_q L[i][k0+q] L[j][k0+q] for k1 <= j <= i < n, k1 = k0 + b:
@@ -477,7 +493,7 @@ void cholesky(Prof &prof, cudaStream_t st, double *G, int n, int *flag)
         chol_diag<<<1, dim3(CB, CB), 0, st>>>(G, n, k0, b, flag);
         prof.launches += 1;
         if (rest > 0) {
-            chol_panel<<<cdiv(rest, 128), 128, 0, st>>>(G, n, k0, b);
+            chol_panel<<<cdiv(rest, 32), 32, 0, st>>>(G, n, k0, b);
             const unsigned nt = cdiv(rest, 32);
             chol_update<<<dim3(nt, nt), 256, 0, st>>>(G, n, k0, b);
             prof.launches += 2;

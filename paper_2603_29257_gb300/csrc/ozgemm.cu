@@ -88,6 +88,8 @@ struct OzArgs {
     int *err;
     long long wait;                // pipeline wait limit in SM cycles
     int stall;                     // test of the bounded waits: the producer issues no loads
+    const int *klist, *kcount;     // block-sparse K per N tile (null: every block)
+    int kld;
 };
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
@@ -145,7 +147,7 @@ __device__ __forceinline__ void two_sum(float &hi, float &lo, float b)
 
 // Tile t of a persistent CTA: its output block, operand rows and K blocks
 struct OzTile {
-    int m0, n0, split, b, b1, b2, kb_begin, nkb;
+    int m0, n0, nt, split, b, b1, b2, kb_begin, nkb;
     long long arow, brow;
 };
 
@@ -164,8 +166,9 @@ __device__ __forceinline__ OzTile oz_tile(const OzArgs &g, long long t, int BN)
     u.n0 = nt * BN;
     u.arow = g.a0 + g.a1 * u.b1 + g.a2 * u.b2 + u.m0;
     u.brow = g.c0 + g.c1 * u.b1 + g.c2 * u.b2 + u.n0;
+    u.nt = nt;
     u.kb_begin = u.split * g.kchunk;
-    u.nkb = max(0, min(g.nkb - u.kb_begin, g.kchunk));
+    u.nkb = g.kcount ? __ldg(g.kcount + nt) : max(0, min(g.nkb - u.kb_begin, g.kchunk));
     return u;
 }
 
@@ -280,7 +283,8 @@ __global__ void __launch_bounds__(320, 1)
                     const uint32_t full = FULL + 8 * s;
                     bar_expect(full, C::STAGE);
                     uint8_t *stg = smem + s * C::STAGE;
-                    const int xa = (g.kbA + u.kb_begin + kt) * C::SP * 32, xb = (g.kbB + u.kb_begin + kt) * C::SP * 32;
+                    const int kb = g.klist ? __ldg(g.klist + (long long)u.nt * g.kld + kt) : u.kb_begin + kt;
+                    const int xa = (g.kbA + kb) * C::SP * 32, xb = (g.kbB + kb) * C::SP * 32;
 #pragma unroll
                     for (int j = 0; j < C::NBOX; ++j) {
                         tma2d(sa(stg + j * C::ABOX), &tA, xa + 64 * j, (int)u.arow, full);
@@ -430,8 +434,10 @@ __global__ void __launch_bounds__(320, 1)
 // rows still fill the GPU
 constexpr int OZ_SEG = 1024;
 
+// bmask (optional): K block kb of row r is read only where
+// bmask[((r % mrows) / 64) * mld + kb] is set (the others hold zeros)
 __global__ void oz_rowexp(const double *__restrict__ x, long long rows, int K, long long sr, long long sk,
-                          int *__restrict__ e)
+                          int *__restrict__ e, const unsigned char *__restrict__ bmask, long long mrows, int mld)
 {
     const int lane = threadIdx.x & 31;
     const int nseg = (K + OZ_SEG - 1) / OZ_SEG;
@@ -440,7 +446,9 @@ __global__ void oz_rowexp(const double *__restrict__ x, long long rows, int K, l
         const long long r = t / nseg;
         const int k0 = (int)(t - r * nseg) * OZ_SEG, k1 = min(K, k0 + OZ_SEG);
         int mx = 0;
+        const unsigned char *mk = bmask ? bmask + ((r % mrows) / 64) * mld : nullptr;
         for (int k = k0 + lane; k < k1; k += 32) {
+            if (mk && !mk[k >> 5]) continue;  // the same block for the whole warp
             const long long bits = __double_as_longlong(x[r * sr + (long long)k * sk]);
             mx = max(mx, (int)((bits >> 52) & 0x7FF));
         }
@@ -483,13 +491,15 @@ __device__ __forceinline__ void oz_digits(double x, int e, int (&q)[S])
 
 template <int S>
 __global__ void oz_slice(const double *__restrict__ x, long long rows, int K, long long sr, long long sk,
-                         const int *__restrict__ e, int nkb, int SP, long long L, uint16_t *__restrict__ q)
+                         const int *__restrict__ e, int nkb, int SP, long long L, uint16_t *__restrict__ q,
+                         const unsigned char *__restrict__ bmask, long long mrows, int mld)
 {
     const long long tot = rows * nkb * 32;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
         const long long r = t / (nkb * 32);
         const int rem = (int)(t - r * nkb * 32);
         const int kb = rem >> 5, kl = rem & 31, k = kb * 32 + kl;
+        if (bmask && !bmask[((r % mrows) / 64) * mld + kb]) continue;  // a block no product reads
         int dg[S];
         if (k < K) {
             oz_digits<S>(x[r * sr + (long long)k * sk], e[r], dg);
@@ -502,6 +512,54 @@ __global__ void oz_slice(const double *__restrict__ x, long long rows, int K, lo
         for (int s = 0; s < S; ++s)  // |digit| <= 128 times 2^(-8s): the upper half of its FP32 pattern is the exact bf16
             o[s * 32] = (uint16_t)(__float_as_uint((float)dg[s] * __int_as_float((127 - 8 * s) << 23)) >> 16);
         for (int s = S; s < SP; ++s) o[s * 32] = 0;
+    }
+}
+
+// Many short rows: one block per row finds the row's exponent and slices it in
+// the same pass (the row is re-read from L2), with the block mask as in oz_slice
+template <int S>
+__global__ void __launch_bounds__(256)
+    oz_split_rowwise(const double *__restrict__ x, long long rows, int K, long long sr, long long sk,
+                     int *__restrict__ e, int nkb, int SP, long long L, uint16_t *__restrict__ q,
+                     const unsigned char *__restrict__ bmask, long long mrows, int mld)
+{
+    __shared__ int wmax[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+        const unsigned char *mk = bmask ? bmask + ((r % mrows) / 64) * mld : nullptr;
+        const double *xr = x + r * sr;
+        int mx = 0;
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            if (mk && !mk[k >> 5]) continue;
+            mx = max(mx, (int)((__double_as_longlong(xr[(long long)k * sk]) >> 52) & 0x7FF));
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) wmax[warp] = mx;
+        __syncthreads();
+        mx = wmax[0];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) mx = max(mx, wmax[w]);
+        const int er = mx ? mx - 1022 : 0;  // biased exponent field -> frexp exponent; 0 for a zero row
+        if (threadIdx.x == 0) e[r] = er;
+        uint16_t *qr = q + r * L;
+        for (int t = threadIdx.x; t < nkb * 32; t += blockDim.x) {
+            const int kb = t >> 5, kl = t & 31;
+            if (mk && !mk[kb]) continue;  // a block no product reads
+            int dg[S];
+            if (t < K) {
+                oz_digits<S>(xr[(long long)t * sk], er, dg);
+            } else {
+#pragma unroll
+                for (int s2 = 0; s2 < S; ++s2) dg[s2] = 0;
+            }
+            uint16_t *o = qr + (long long)kb * SP * 32 + kl;
+#pragma unroll
+            for (int s2 = 0; s2 < S; ++s2)
+                o[s2 * 32] = (uint16_t)(__float_as_uint((float)dg[s2] * __int_as_float((127 - 8 * s2) << 23)) >> 16);
+            for (int s2 = S; s2 < SP; ++s2) o[s2 * 32] = 0;
+        }
+        __syncthreads();  // wmax is rewritten for the next row
     }
 }
 
@@ -557,9 +615,10 @@ void oz_launch(cudaStream_t st, dim3 grid, const OzMat &A, const OzMat &B, const
 }
 
 template <int S>
-void oz_slice_launch(cudaStream_t st, const double *x, long long sr, long long sk, OzMat &m, unsigned blocks)
+void oz_slice_launch(cudaStream_t st, const double *x, long long sr, long long sk, OzMat &m, unsigned blocks,
+                     const unsigned char *bmask, long long mrows, int mld)
 {
-    oz_slice<S><<<blocks, 256, 0, st>>>(x, m.rows, m.K, sr, sk, m.e, m.nkb, m.SP, m.L, m.q);
+    oz_slice<S><<<blocks, 256, 0, st>>>(x, m.rows, m.K, sr, sk, m.e, m.nkb, m.SP, m.L, m.q, bmask, mrows, mld);
 }
 
 long long row_len(int K, int S) { return (long long)cdiv(K, 32) * (((S + 1) & ~1) * 32); }
@@ -590,25 +649,44 @@ void oz_bind(OzMat &m, void *storage, long long rows, int K, int S)
     tma_encode_2d(m.m64, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, m.q, rows, m.L, m.L * 2, 64, 64);
 }
 
-void oz_split(Prof &prof, cudaStream_t st, const char *name, const double *x, long long sr, long long sk, OzMat &m)
+void oz_split(Prof &prof, cudaStream_t st, const char *name, const double *x, long long sr, long long sk, OzMat &m,
+              const unsigned char *bmask, long long mrows, int mld)
 {
     TR_REQUIRE(m.q && m.e, TR_EINVAL, "Ozaki split: unbound operand");
+    TR_REQUIRE(!bmask || (mrows >= 1 && mld >= m.nkb), TR_EINVAL, "Ozaki split: bad block mask");
+    if (m.rows >= 152LL * 8 && m.K <= 16384) {
+        // many short rows (integral and half-transform chunks): one fused pass
+        const unsigned blocks = (unsigned)std::min<long long>(m.rows, 152LL * 8);
+        int tok = prof.begin(st, name, 0, 8.0 * m.rows * m.K + 2.0 * m.rows * m.L);
+        switch (m.S) {
+#define TR_OZR(SS) \
+    case SS: oz_split_rowwise<SS><<<blocks, 256, 0, st>>>(x, m.rows, m.K, sr, sk, m.e, m.nkb, m.SP, m.L, m.q, bmask, mrows, mld); break;
+        TR_OZR(2) TR_OZR(3) TR_OZR(4) TR_OZR(5) TR_OZR(6)
+        default: oz_split_rowwise<7><<<blocks, 256, 0, st>>>(x, m.rows, m.K, sr, sk, m.e, m.nkb, m.SP, m.L, m.q, bmask,
+                                                             mrows, mld);
+            break;
+#undef TR_OZR
+        }
+        TR_CHECK_LAUNCH(name);
+        prof.end(st, tok);
+        return;
+    }
     const long long nwarps = m.rows * cdiv(m.K, OZ_SEG);
     const unsigned rb = (unsigned)std::min<long long>(cdiv(nwarps, 8), 152LL * 32);
     TR_CUDA(cudaMemsetAsync(m.e, 0, sizeof(int) * m.rows, st));
     TR_LAUNCH(prof, st, "oz_rowexp", 0, 8.0 * m.rows * m.K,
-              oz_rowexp<<<rb, 256, 0, st>>>(x, m.rows, m.K, sr, sk, m.e));
+              oz_rowexp<<<rb, 256, 0, st>>>(x, m.rows, m.K, sr, sk, m.e, bmask, mrows, mld));
     oz_rowexp_finish<<<(unsigned)std::min<long long>(cdiv(m.rows, 256), 152LL * 8), 256, 0, st>>>(m.e, m.rows);
     const long long tot = m.rows * m.nkb * 32;
     const unsigned blocks = (unsigned)std::min<long long>(cdiv(tot, 256), 152LL * 16);
     int tok = prof.begin(st, name, 0, 8.0 * m.rows * m.K + 2.0 * m.rows * m.L);
     switch (m.S) {
-    case 2: oz_slice_launch<2>(st, x, sr, sk, m, blocks); break;
-    case 3: oz_slice_launch<3>(st, x, sr, sk, m, blocks); break;
-    case 4: oz_slice_launch<4>(st, x, sr, sk, m, blocks); break;
-    case 5: oz_slice_launch<5>(st, x, sr, sk, m, blocks); break;
-    case 6: oz_slice_launch<6>(st, x, sr, sk, m, blocks); break;
-    default: oz_slice_launch<7>(st, x, sr, sk, m, blocks); break;
+    case 2: oz_slice_launch<2>(st, x, sr, sk, m, blocks, bmask, mrows, mld); break;
+    case 3: oz_slice_launch<3>(st, x, sr, sk, m, blocks, bmask, mrows, mld); break;
+    case 4: oz_slice_launch<4>(st, x, sr, sk, m, blocks, bmask, mrows, mld); break;
+    case 5: oz_slice_launch<5>(st, x, sr, sk, m, blocks, bmask, mrows, mld); break;
+    case 6: oz_slice_launch<6>(st, x, sr, sk, m, blocks, bmask, mrows, mld); break;
+    default: oz_slice_launch<7>(st, x, sr, sk, m, blocks, bmask, mrows, mld); break;
     }
     TR_CHECK_LAUNCH(name);
     prof.end(st, tok);
@@ -690,7 +768,8 @@ void oz_split_rows(Prof &prof, cudaStream_t st, const char *name, const double *
 
 void oz_gemm(Prof &prof, cudaStream_t st, const char *name, const OzMat &A, long long a0, long long a1, long long a2,
              int kbA, const OzMat &B, long long c0, long long c1, long long c2, int kbB, int M, int N, int nkb, int n1,
-             int n2, const OzOut &out, int *err, int ksplit, double *ws, size_t ws_count)
+             int n2, const OzOut &out, int *err, int ksplit, double *ws, size_t ws_count, const int *klist,
+             const int *kcount, int kld)
 {
     if (M <= 0 || N <= 0 || n1 <= 0 || n2 <= 0) return;
     TR_REQUIRE(A.q && B.q && A.S == B.S, TR_EINVAL, "Ozaki GEMM: operands must share the slice count");
@@ -699,6 +778,8 @@ void oz_gemm(Prof &prof, cudaStream_t st, const char *name, const OzMat &A, long
     TR_REQUIRE(kbA >= 0 && kbB >= 0 && nkb >= 1 && kbA + nkb <= A.nkb && kbB + nkb <= B.nkb, TR_EINVAL,
                "Ozaki GEMM: K blocks out of range");
     ksplit = std::max(1, std::min(ksplit, nkb));
+    TR_REQUIRE(!klist == !kcount && (!klist || (ksplit == 1 && kld >= 1 && kld <= nkb)), TR_EINVAL,
+               "Ozaki GEMM: block-sparse K needs both lists and no K split");
     const long long nb = (long long)n1 * n2;
     TR_REQUIRE(cdiv(M, 128) <= (1 << 30), TR_EINVAL, "Ozaki GEMM: too many tiles");
     TR_REQUIRE(ksplit == 1 || (ws && (size_t)ksplit * nb * M * N <= ws_count), TR_EINVAL,
@@ -737,6 +818,9 @@ void oz_gemm(Prof &prof, cudaStream_t st, const char *name, const OzMat &A, long
     g.err = err;
     g.wait = prof.wait_cycles > 0 ? prof.wait_cycles : ptx::WAIT_CYCLES;
     g.stall = prof.wait_stall;
+    g.klist = klist;
+    g.kcount = kcount;
+    g.kld = kld;
     g.ntn = cdiv(N, BN);
     g.ntm = cdiv(M, 128);
     g.ntiles = (long long)g.ntn * g.ntm * nb * ksplit;
@@ -772,7 +856,7 @@ void oz_gemm(Prof &prof, cudaStream_t st, const char *name, const OzMat &A, long
 
 void oz_gemm(Prof &prof, cudaStream_t st, const char *name, const OzMat &A, long long a0, long long a1,
              const OzMat &B, long long c0, long long c1, int M, int N, int nb, double *d, long long s1,
-             long long ldm, long long ldn, double alpha, int *err)
+             long long ldm, long long ldn, double alpha, int *err, const int *klist, const int *kcount, int kld)
 {
     TR_REQUIRE(A.K == B.K, TR_EINVAL, "Ozaki GEMM: operands must share K");
     OzOut o;
@@ -781,7 +865,8 @@ void oz_gemm(Prof &prof, cudaStream_t st, const char *name, const OzMat &A, long
     o.ldm = ldm;
     o.ldn = ldn;
     o.alpha = alpha;
-    oz_gemm(prof, st, name, A, a0, a1, 0, 0, B, c0, c1, 0, 0, M, N, A.nkb, nb, 1, o, err);
+    oz_gemm(prof, st, name, A, a0, a1, 0, 0, B, c0, c1, 0, 0, M, N, A.nkb, nb, 1, o, err, 1, nullptr, 0, klist, kcount,
+            kld);
 }
 
 }  // namespace tr

@@ -44,8 +44,12 @@ size_t oz_bytes(long long rows, int K, int S);
 // encode its tensor maps
 void oz_bind(OzMat &m, void *storage, long long rows, int K, int S);
 
-// slice x into m: element (r, k) = x[r * sr + k * sk] for r < m.rows, k < m.K
-void oz_split(Prof &prof, cudaStream_t st, const char *name, const double *x, long long sr, long long sk, OzMat &m);
+// slice x into m: element (r, k) = x[r * sr + k * sk] for r < m.rows, k < m.K.
+// bmask (device, optional): only the K blocks of 32 with
+// bmask[((r % mrows) / 64) * mld + kb] set are read and sliced (the rest must be
+// zero in x, and stay unwritten in m: products over m must skip them)
+void oz_split(Prof &prof, cudaStream_t st, const char *name, const double *x, long long sr, long long sk, OzMat &m,
+              const unsigned char *bmask = nullptr, long long mrows = 1, int mld = 0);
 
 // every row exponent of m set to e (for matrices sliced with one fixed exponent)
 void oz_set_exponents(cudaStream_t st, OzMat &m, int e);
@@ -83,14 +87,20 @@ struct OzOut {
 // past the operand (read as zero); they are computed and discarded.  ksplit > 1
 // splits the K blocks of every tile over that many CTAs, whose partial sums go
 // through ws (at least ksplit n1 n2 M N doubles) and a reduction.  err: device
-// int set non-zero if a pipeline wait timed out.
+// int set non-zero if a pipeline wait timed out.  klist / kcount (device, with
+// ksplit = 1): block-sparse K, the output tile of columns [64 nt, 64 nt + 64)
+// contracts only the K blocks klist[nt * kld + t], t < kcount[nt] (relative to
+// kbA and kbB, each below nkb); the blocks left out must hold zeros in B.
 void oz_gemm(Prof &prof, cudaStream_t st, const char *name, const OzMat &A, long long a0, long long a1, long long a2,
              int kbA, const OzMat &B, long long c0, long long c1, long long c2, int kbB, int M, int N, int nkb, int n1,
-             int n2, const OzOut &out, int *err, int ksplit = 1, double *ws = nullptr, size_t ws_count = 0);
+             int n2, const OzOut &out, int *err, int ksplit = 1, double *ws = nullptr, size_t ws_count = 0,
+             const int *klist = nullptr, const int *kcount = nullptr, int kld = 0);
 
 // One batch dimension, the whole K: d[b s1 + r ldm + c ldn] = alpha sum_k A[a0 + a1 b + r][k] B[c0 + c1 b + c][k]
+// (block-sparse K as above when klist is given)
 void oz_gemm(Prof &prof, cudaStream_t st, const char *name, const OzMat &A, long long a0, long long a1,
              const OzMat &B, long long c0, long long c1, int M, int N, int nb, double *d, long long s1,
-             long long ldm, long long ldn, double alpha, int *err);
+             long long ldm, long long ldn, double alpha, int *err, const int *klist = nullptr,
+             const int *kcount = nullptr, int kld = 0);
 
 }  // namespace tr

@@ -284,6 +284,28 @@ void refresh_molecule(tr_ctx *c)
         c->ktiles.count = c->kt_count.p;
         c->ktiles.ld = ntk;
         c->ktiles.active = active;
+        // K blocks of 32 for the tensor-core transforms
+        const int nkb = cdiv(std::max(nao, 1), 32);
+        std::vector<unsigned char> hb((size_t)ntn * nkb, 0);
+        for (int nt = 0; nt < ntn; ++nt)
+            for (int kt = 0; kt < ntk; ++kt)
+                if (hit[(size_t)nt * ntk + kt]) hb[(size_t)nt * nkb + kt / 2] = 1;
+        c->kb_list_h.assign((size_t)ntn * nkb, 0);
+        c->kb_count_h.assign(ntn, 0);
+        for (int nt = 0; nt < ntn; ++nt) {
+            int n = 0;
+            for (int kb = 0; kb < nkb; ++kb)
+                if (hb[(size_t)nt * nkb + kb]) c->kb_list_h[(size_t)nt * nkb + n++] = kb;
+            c->kb_count_h[nt] = n;
+        }
+        c->kb_list.alloc(c->kb_list_h.size(), &c->budget, "integral block sparsity");
+        c->kb_count.alloc(c->kb_count_h.size(), &c->budget, "integral block sparsity");
+        TR_CUDA(cudaMemcpy(c->kb_list.p, c->kb_list_h.data(), sizeof(int) * c->kb_list_h.size(), cudaMemcpyHostToDevice));
+        TR_CUDA(cudaMemcpy(c->kb_count.p, c->kb_count_h.data(), sizeof(int) * c->kb_count_h.size(),
+                           cudaMemcpyHostToDevice));
+        c->kb_mask.alloc(hb.size(), &c->budget, "integral block sparsity");
+        TR_CUDA(cudaMemcpy(c->kb_mask.p, hb.data(), hb.size(), cudaMemcpyHostToDevice));
+        c->kb_ld = nkb;
     }
 }
 
@@ -511,7 +533,10 @@ static void transforms_oz(tr_ctx *c, DevBuf<double> &Iij, DevBuf<double> *Iia, i
     // out[p][r][s] = sum_nu H[p][r][nu] C[nu][s0 + s] for s < ns
     auto pair_transform = [&](int np, int r0, int nr, int s0, int ns, double *out, long long ldo, const char *n1,
                               const char *n2) {
-        oz_gemm(pf, st, n1, Cs, r0, 0, Is, 0, nao, nr, nao, np, H.p, (long long)nr * nao, nao, 1, 1.0, err);
+        // the integrals are block-sparse in mu: each 64-column tile contracts
+        // only the K blocks its kept shell pairs touch
+        oz_gemm(pf, st, n1, Cs, r0, 0, Is, 0, nao, nr, nao, np, H.p, (long long)nr * nao, nao, 1, 1.0, err,
+                c->kb_list.p, c->kb_count.p, c->kb_ld);
         oz_bind(Hs, Hb.p, (long long)np * nr, nao, S);
         oz_split(pf, st, "oz_split_H", H.p, nao, 1, Hs);
         oz_gemm(pf, st, n2, Hs, 0, nr, Cs, s0, 0, nr, ns, np, out, (long long)nr * ldo, ldo, 1, 1.0, err);
@@ -521,7 +546,7 @@ static void transforms_oz(tr_ctx *c, DevBuf<double> &Iij, DevBuf<double> *Iia, i
         const int np = std::min(npcJ, nJt - p0);
         compute_int3c_chunk(c, 0, p0, np, I.p);
         oz_bind(Is, Ib.p, (long long)np * nao, nao, S);
-        oz_split(pf, st, "oz_split_I", I.p, nao, 1, Is);
+        oz_split(pf, st, "oz_split_I", I.p, nao, 1, Is, c->kb_mask.p, nao, c->kb_ld);
         pair_transform(np, 0, nocc, nocc, nvir, c->Y.p + (long long)p0 * nov, nvir, "xform_J1_oz", "xform_J2_oz");
     }
     if (c->k_active) {
@@ -531,7 +556,7 @@ static void transforms_oz(tr_ctx *c, DevBuf<double> &Iij, DevBuf<double> *Iia, i
             const int np = std::min(npc, nK - p0);
             compute_int3c_chunk(c, 1, p0, np, I.p);
             oz_bind(Is, Ib.p, (long long)np * nao, nao, S);
-            oz_split(pf, st, "oz_split_I", I.p, nao, 1, Is);
+            oz_split(pf, st, "oz_split_I", I.p, nao, 1, Is, c->kb_mask.p, nao, c->kb_ld);
             pair_transform(np, o0, oK, o0, oK, Iij.p + (long long)p0 * oK * oK, oK, "xform_K1_oz", "xform_K2_oz");
             pair_transform(np, nocc, vK, nocc, vK, c->Tab.p + (long long)p0 * vK * vK, vK, "xform_K1_oz",
                            "xform_K2_oz");
@@ -544,6 +569,31 @@ static void transforms_oz(tr_ctx *c, DevBuf<double> &Iij, DevBuf<double> *Iia, i
     TR_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     TR_CUDA(cudaStreamSynchronize(st));
     TR_REQUIRE(h == 0, TR_ETIMEOUT, "build: a tensor-core transform pipeline wait ran out (code " + std::to_string(h) + ")");
+}
+
+// T^P_ij = sum_Q (P|Q)^-1 (Q|ij), stored [i][P][j], as an Ozaki product on the
+// tensor cores with the transforms' slice count: A = (P|Q)^-1 (rows P, K = Q),
+// B = (Q|ij) read as rows (i, j) with K = Q, one batch entry per i
+static void apply_metric_oz(tr_ctx *c, const double *Ginv, const double *Iij, int nK, int oK, double *T2, int S)
+{
+    Prof &pf = c->prof;
+    cudaStream_t st = c->st;
+    int *err = c->flag.p + 2;
+    const long long nij = (long long)oK * oK;
+    DevBuf<double> ab, bb;
+    ab.alloc(cdiv(oz_bytes(nK, nK, S), 8), &c->budget, "sliced K metric inverse");
+    bb.alloc(cdiv(oz_bytes(nij, nK, S), 8), &c->budget, "sliced (ij|P)");
+    OzMat As, Bs;
+    oz_bind(As, ab.p, nK, nK, S);
+    oz_split(pf, st, "oz_split_GK", Ginv, nK, 1, As);
+    oz_bind(Bs, bb.p, nij, nK, S);
+    oz_split(pf, st, "oz_split_Iij", Iij, 1, nij, Bs);
+    TR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    oz_gemm(pf, st, "apply_K_metric_oz", As, 0, 0, Bs, 0, oK, nK, oK, oK, T2, (long long)nK * oK, oK, 1, 1.0, err);
+    int h = 0;
+    TR_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TR_CUDA(cudaStreamSynchronize(st));  // the sliced operands are freed on return
+    TR_REQUIRE(h == 0, TR_ETIMEOUT, "build: a tensor-core metric product wait ran out (code " + std::to_string(h) + ")");
 }
 
 void build(tr_ctx *c)
@@ -604,8 +654,13 @@ void build(tr_ctx *c)
             t.n1 = oK;
             t.sB1 = oK;
             t.sC1 = (long long)nK * oK;
-            dgemm(pf, st, "apply_K_metric", false, false, nK, oK, nK, 1.0, c->GinvK.p, nK, Iij.p,
-                  (long long)oK * oK, 0.0, c->T2.p, oK, t, nullptr, 0);
+            // the reduced-precision form keeps T_ij in FP32: its metric product
+            // runs on the tensor cores; the FP64 forms keep it on the FP64 pipe
+            if (S > 0 && mixed)
+                apply_metric_oz(c, c->GinvK.p, Iij.p, nK, oK, c->T2.p, S);
+            else
+                dgemm(pf, st, "apply_K_metric", false, false, nK, oK, nK, 1.0, c->GinvK.p, nK, Iij.p,
+                      (long long)oK * oK, 0.0, c->T2.p, oK, t, nullptr, 0);
         }
         TR_CUDA(cudaStreamSynchronize(st));
     }

@@ -163,6 +163,8 @@ void matvec_b(tr_ctx *c, int m, const double *X, double *BX);
 void matvec_pm(tr_ctx *c, int m, const double *X, double *P, double *M);
 // slices of the tensor-core MO transforms (0: FP64 pipe)
 int xform_slices(const tr_ctx *c);
+// Ozaki slices of the Davidson subspace products on the tensor cores
+int dav_slices(const tr_ctx *c);
 // estimated peak device bytes of tr_build + tr_solve
 size_t footprint(tr_ctx *c);
 // FP64 form on the tensor cores: slice the built tensors; matvec workspaces; A X

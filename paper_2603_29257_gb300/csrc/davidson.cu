@@ -644,9 +644,9 @@ struct Dav {
         ws = c->ws_split.p;
         wsn = c->ws_split.n;
         if ((c->opt.precision == TR_MIXED || c->opt.precision == TR_FP64_TC) && kd == maxsp) {
-            const size_t sv = oz_bytes(maxsp, (int)nov, OZ_SLICES_FP64), stn = oz_bytes(pmax, (int)nov, OZ_SLICES_FP64);
-            const size_t svt = oz_bytes(nov, maxsp, OZ_SLICES_FP64);
-            const size_t ssm = oz_bytes(std::max(n, pmax), maxsp, OZ_SLICES_FP64);
+            const size_t sv = oz_bytes(maxsp, (int)nov, dav_slices(c)), stn = oz_bytes(pmax, (int)nov, dav_slices(c));
+            const size_t svt = oz_bytes(nov, maxsp, dav_slices(c));
+            const size_t ssm = oz_bytes(std::max(n, pmax), maxsp, dav_slices(c));
             const size_t nsl = rpa ? 3 : 2;  // sliced row stores: V, W (and Wm), each by rows and by columns
             if (c->budget.used + nsl * sv + nsl * svt + stn + 2 * ssm + (64u << 20) <= c->budget.limit) {
                 c->dvs_V.alloc(cdiv(sv, 8), &c->budget, "sliced Davidson V");
@@ -656,26 +656,26 @@ struct Dav {
                 c->dvs_Y.alloc(cdiv(ssm, 8), &c->budget, "sliced subspace vectors");
                 c->dvs_C.alloc(cdiv(ssm, 8), &c->budget, "sliced projections");
                 TR_CUDA(cudaMemsetAsync(c->dvs_Vt.p, 0, c->dvs_Vt.n * sizeof(double), st));
-                oz_bind(c->dz_Vt, c->dvs_Vt.p, nov, maxsp, OZ_SLICES_FP64);
+                oz_bind(c->dz_Vt, c->dvs_Vt.p, nov, maxsp, dav_slices(c));
                 oz_set_exponents(st, c->dz_Vt, 1);  // orthonormal rows: every |v| < 2
                 c->dvs_Wt.alloc(cdiv(svt, 8), &c->budget, "sliced Davidson W by columns");
                 c->dz_eW.alloc(1, &c->budget, "exponent");
                 TR_CUDA(cudaMemsetAsync(c->dvs_Wt.p, 0, c->dvs_Wt.n * sizeof(double), st));
-                oz_bind(c->dz_Wt, c->dvs_Wt.p, nov, maxsp, OZ_SLICES_FP64);
+                oz_bind(c->dz_Wt, c->dvs_Wt.p, nov, maxsp, dav_slices(c));
                 // rows not yet sliced read as zero (tiles extend past the live rows)
                 TR_CUDA(cudaMemsetAsync(c->dvs_V.p, 0, c->dvs_V.n * sizeof(double), st));
                 TR_CUDA(cudaMemsetAsync(c->dvs_W.p, 0, c->dvs_W.n * sizeof(double), st));
                 TR_CUDA(cudaMemsetAsync(c->dvs_T.p, 0, c->dvs_T.n * sizeof(double), st));
-                oz_bind(c->dz_V, c->dvs_V.p, maxsp, (int)nov, OZ_SLICES_FP64);
-                oz_bind(c->dz_W, c->dvs_W.p, maxsp, (int)nov, OZ_SLICES_FP64);
+                oz_bind(c->dz_V, c->dvs_V.p, maxsp, (int)nov, dav_slices(c));
+                oz_bind(c->dz_W, c->dvs_W.p, maxsp, (int)nov, dav_slices(c));
                 if (rpa) {
                     c->dvs_Wm.alloc(cdiv(sv, 8), &c->budget, "sliced Davidson (A - B) V");
                     c->dvs_Wmt.alloc(cdiv(svt, 8), &c->budget, "sliced Davidson (A - B) V by columns");
                     c->dz_eWm.alloc(1, &c->budget, "exponent");
                     TR_CUDA(cudaMemsetAsync(c->dvs_Wm.p, 0, c->dvs_Wm.n * sizeof(double), st));
                     TR_CUDA(cudaMemsetAsync(c->dvs_Wmt.p, 0, c->dvs_Wmt.n * sizeof(double), st));
-                    oz_bind(c->dz_Wm, c->dvs_Wm.p, maxsp, (int)nov, OZ_SLICES_FP64);
-                    oz_bind(c->dz_Wmt, c->dvs_Wmt.p, nov, maxsp, OZ_SLICES_FP64);
+                    oz_bind(c->dz_Wm, c->dvs_Wm.p, maxsp, (int)nov, dav_slices(c));
+                    oz_bind(c->dz_Wmt, c->dvs_Wmt.p, nov, maxsp, dav_slices(c));
                 }
                 tcd = true;
             }
@@ -941,7 +941,7 @@ struct Dav {
         if (tcd) {
             // X[i][col] = sum_r V[r][col] Y[r][i]: rows col of V by columns, columns i
             OzMat Ys;
-            oz_bind(Ys, c->dvs_Y.p, n, k, OZ_SLICES_FP64);
+            oz_bind(Ys, c->dvs_Y.p, n, k, dav_slices(c));
             oz_split(pf, st, "oz_split_Yev", c->Yev.p, 1, k, Ys);
             OzOut o;
             o.d = c->Xr.p;
@@ -1003,7 +1003,7 @@ struct Dav {
         if (tcd) {
             // Cs rows i < 2n with K = r: element (i, r) = Cab[r][i]
             OzMat Ys;
-            oz_bind(Ys, c->dvs_Y.p, n2, k, OZ_SLICES_FP64);
+            oz_bind(Ys, c->dvs_Y.p, n2, k, dav_slices(c));
             oz_split(pf, st, "oz_split_Yev", Cab, 1, n2, Ys);
             OzOut o;
             o.d = c->Xr.p;
@@ -1115,7 +1115,7 @@ struct Dav {
             }
             if (tcd) {
                 OzMat Ts;
-                oz_bind(Ts, c->dvs_T.p, pp, (int)nov, OZ_SLICES_FP64);
+                oz_bind(Ts, c->dvs_T.p, pp, (int)nov, dav_slices(c));
                 oz_split(pf, st, "oz_split_T", c->T.p, nov, 1, Ts);
                 tc_reduce("orth_project_tc", c->dz_V, 0, Ts, 0, k, pp, c->Cs.p, pp, 1);  // Cs[r][i] = V_r . T_i
             } else {
@@ -1127,7 +1127,7 @@ struct Dav {
             if (tcd) {
                 // T[i][col] -= sum_r V[r][col] Cs[r][i]
                 OzMat Css;
-                oz_bind(Css, c->dvs_C.p, pp, k, OZ_SLICES_FP64);
+                oz_bind(Css, c->dvs_C.p, pp, k, dav_slices(c));
                 oz_split(pf, st, "oz_split_Cs", c->Cs.p, 1, pp, Css);
                 OzOut o;
                 o.d = c->T.p;

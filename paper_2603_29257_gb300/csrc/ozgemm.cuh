@@ -19,6 +19,10 @@ constexpr int OZ_MAX_SLICES = 7;
 constexpr int OZ_DEFAULT_SLICES_MIXED = 5;
 // slices of every product of the FP64 form on the tensor cores (FP64-level results)
 constexpr int OZ_SLICES_FP64 = 7;
+// slices of the reduced-precision form's Davidson subspace products (V^T T,
+// V C, Y^T V, V^T W): 47 bits below each row's largest element, far beyond
+// what its FP32 block products resolve, stored in 6 slices (7 pad to 8)
+constexpr int OZ_SLICES_DAV_MIXED = 6;
 
 // An FP64 matrix x[rows][K] in sliced form.  Row r has exponent e[r] with
 // |x[r][k]| < 2^e[r] for every k, and integer digits |q_s[r][k]| <= 128 with

@@ -489,6 +489,8 @@ static void transforms_fp64(tr_ctx *c, DevBuf<double> &Iij, DevBuf<double> *Iia)
 
 // Slices of the Ozaki-scheme transforms for this context: 0 when the FP64
 // transforms run on the FP64 pipe
+int dav_slices(const tr_ctx *c) { return c->opt.precision == TR_MIXED ? OZ_SLICES_DAV_MIXED : OZ_SLICES_FP64; }
+
 int xform_slices(const tr_ctx *c)
 {
     const int s = c->opt.xform_slices;
@@ -809,10 +811,10 @@ size_t footprint(tr_ctx *c)
     }
     // sliced V, W and new directions of the Davidson subspace products
     const double dtc = (c->opt.precision == TR_MIXED || c->opt.precision == TR_FP64_TC)
-                           ? 2.0 * (double)oz_bytes(maxsp, (int)nov, OZ_SLICES_FP64) +
-                                 (double)oz_bytes((long long)pmax, (int)nov, OZ_SLICES_FP64) +
-                                 2.0 * (double)oz_bytes((long long)nov, maxsp, OZ_SLICES_FP64) +
-                                 2.0 * (double)oz_bytes((long long)std::max<double>(n, pmax), maxsp, OZ_SLICES_FP64)
+                           ? 2.0 * (double)oz_bytes(maxsp, (int)nov, dav_slices(c)) +
+                                 (double)oz_bytes((long long)pmax, (int)nov, dav_slices(c)) +
+                                 2.0 * (double)oz_bytes((long long)nov, maxsp, dav_slices(c)) +
+                                 2.0 * (double)oz_bytes((long long)std::max<double>(n, pmax), maxsp, dav_slices(c))
                            : 0.0;
     const double jao = c->opt.j_ao ? (double)jao_bytes(c, (int)mb) : 0.0;
     // full TDDFT on the tensor cores: T_ia sliced by rows (P, i) and by rows a

@@ -93,7 +93,7 @@ typedef struct {
     int precision;       /* TR_FP64, TR_MIXED or TR_FP64_TC */
     double screen;       /* primitive-pair screening threshold (0: 1e-22) */
     size_t hbm_budget;   /* bytes of device memory the context may hold (0: 90% of free) */
-    size_t aux_chunk_bytes; /* scratch for AO integral chunks (0: 6 GiB) */
+    size_t aux_chunk_bytes; /* scratch for AO integral chunks (0: 12 GiB) */
     size_t host_budget;  /* pinned host bytes for spilled Davidson vectors (0: unlimited);
                             the subspace is capped so that V and W fit, which triggers
                             restarts earlier (Sec. 3.3) */

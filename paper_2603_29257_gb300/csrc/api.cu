@@ -50,7 +50,7 @@ void fill_defaults(tr_options *o)
 void normalise_options(tr_options *o)
 {
     if (!(o->screen > 0.0)) o->screen = 1e-22;
-    if (o->aux_chunk_bytes == 0) o->aux_chunk_bytes = (size_t)6 << 30;
+    if (o->aux_chunk_bytes == 0) o->aux_chunk_bytes = (size_t)12 << 30;
     if (o->matvec_ws_bytes == 0) o->matvec_ws_bytes = (size_t)4 << 30;
 }
 

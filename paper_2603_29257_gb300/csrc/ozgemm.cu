@@ -542,22 +542,33 @@ __global__ void __launch_bounds__(256)
         for (int w = 1; w < 8; ++w) mx = max(mx, wmax[w]);
         const int er = mx ? mx - 1022 : 0;  // biased exponent field -> frexp exponent; 0 for a zero row
         if (threadIdx.x == 0) e[r] = er;
-        uint16_t *qr = q + r * L;
-        for (int t = threadIdx.x; t < nkb * 32; t += blockDim.x) {
-            const int kb = t >> 5, kl = t & 31;
+        // two neighbouring K values per thread: each slice is one 32-bit store
+        // of two bf16 (row storage is 256-byte aligned, kl even)
+        uint32_t *qr = (uint32_t *)(q + r * L);
+        for (int t = threadIdx.x; t < nkb * 16; t += blockDim.x) {
+            const int kb = t >> 4, kl = (t & 15) * 2, k = kb * 32 + kl;
             if (mk && !mk[kb]) continue;  // a block no product reads
-            int dg[S];
-            if (t < K) {
-                oz_digits<S>(xr[(long long)t * sk], er, dg);
+            int d0[S], d1[S];
+            if (k < K) {
+                oz_digits<S>(xr[(long long)k * sk], er, d0);
             } else {
 #pragma unroll
-                for (int s2 = 0; s2 < S; ++s2) dg[s2] = 0;
+                for (int s2 = 0; s2 < S; ++s2) d0[s2] = 0;
             }
-            uint16_t *o = qr + (long long)kb * SP * 32 + kl;
+            if (k + 1 < K) {
+                oz_digits<S>(xr[(long long)(k + 1) * sk], er, d1);
+            } else {
 #pragma unroll
-            for (int s2 = 0; s2 < S; ++s2)
-                o[s2 * 32] = (uint16_t)(__float_as_uint((float)dg[s2] * __int_as_float((127 - 8 * s2) << 23)) >> 16);
-            for (int s2 = S; s2 < SP; ++s2) o[s2 * 32] = 0;
+                for (int s2 = 0; s2 < S; ++s2) d1[s2] = 0;
+            }
+            uint32_t *o = qr + ((long long)kb * SP * 32 + kl) / 2;
+#pragma unroll
+            for (int s2 = 0; s2 < S; ++s2) {
+                const float w = __int_as_float((127 - 8 * s2) << 23);
+                const uint32_t lo = __float_as_uint((float)d0[s2] * w) >> 16, hi = __float_as_uint((float)d1[s2] * w) >> 16;
+                o[s2 * 16] = lo | (hi << 16);
+            }
+            for (int s2 = S; s2 < SP; ++s2) o[s2 * 16] = 0u;
         }
         __syncthreads();  // wmax is rewritten for the next row
     }

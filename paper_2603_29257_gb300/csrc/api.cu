@@ -382,6 +382,11 @@ int tr_build_batch(tr_ctx **ctxs, int n, int nthreads)
     std::vector<int> rc(n, TR_OK);
     std::atomic<int> next(0);
     std::vector<std::thread> pool;
+    // the build temporaries of each context go back to its block pool rather
+    // than to cudaFree (which waits for the whole device, so concurrent builds
+    // would serialise on each other's frees), and its next batched build takes
+    // them again
+    for (int i = 0; i < n; ++i) ctxs[i]->budget.pool.on = true;
     for (int t = 0; t < nthreads; ++t)
         pool.emplace_back([&]() {
             cudaSetDevice(dev);
@@ -391,6 +396,7 @@ int tr_build_batch(tr_ctx **ctxs, int n, int nthreads)
     int out = TR_OK;
     for (int i = 0; i < n; ++i) {
         cudaStreamSynchronize(own[i]);
+        ctxs[i]->budget.pool.on = false;
         ctxs[i]->st = orig[i];
         cudaStreamDestroy(own[i]);
         if (rc[i] != TR_OK && out == TR_OK) out = rc[i];

@@ -203,8 +203,52 @@ struct Prof {
     } while (0)
 
 // Device allocation accounting against a byte budget.
+// Device blocks of a context kept for reuse by its later allocations of the
+// same size instead of cudaFree, which waits for the whole device: builds of
+// many contexts from several host threads (tr_build_batch) would otherwise
+// serialise on each other's frees.  Blocks are taken only while `on` (the
+// batched build: every use of a block is on the building context's streams,
+// in order); they are freed when an allocation fails, beyond `cap` bytes, and
+// with the context.  Pooled bytes do not count as used.
+struct Pool {
+    bool on = false;
+    size_t cap = (size_t)1 << 30, held = 0;
+    std::vector<std::pair<size_t, void *>> blocks;
+    Pool() = default;
+    Pool(const Pool &) = delete;
+    Pool &operator=(const Pool &) = delete;
+    ~Pool() { flush(); }
+    void *take(size_t bytes)
+    {
+        for (size_t i = 0; i < blocks.size(); ++i)
+            if (blocks[i].first == bytes) {
+                void *q = blocks[i].second;
+                blocks.erase(blocks.begin() + (long)i);
+                held -= bytes;
+                return q;
+            }
+        return nullptr;
+    }
+    bool put(void *q, size_t bytes)
+    {
+        if (!on || held + bytes > cap) return false;
+        blocks.emplace_back(bytes, q);
+        held += bytes;
+        return true;
+    }
+    bool flush()
+    {
+        const bool any = !blocks.empty();
+        for (auto &b : blocks) cudaFree(b.second);
+        blocks.clear();
+        held = 0;
+        return any;
+    }
+};
+
 struct Budget {
     size_t limit = 0, used = 0, peak = 0;
+    Pool pool;
 };
 
 template <typename T>
@@ -218,7 +262,7 @@ struct DevBuf {
     ~DevBuf() { release(); }
     void release() {
         if (p) {
-            cudaFree(p);
+            if (!budget || !budget->pool.put(p, n * sizeof(T))) cudaFree(p);
             if (budget) budget->used -= n * sizeof(T);
         }
         p = nullptr;
@@ -231,7 +275,17 @@ struct DevBuf {
         size_t bytes = count * sizeof(T);
         if (b && b->limit && b->used + bytes > b->limit)
             throw Error(TR_ENOMEM, std::string("device budget exceeded allocating ") + what);
-        cudaError_t e = cudaMalloc(&p, bytes);
+        void *q = b && b->pool.on ? b->pool.take(bytes) : nullptr;
+        cudaError_t e = cudaSuccess;
+        if (q) {
+            p = (T *)q;
+        } else {
+            e = cudaMalloc(&p, bytes);
+            if (e != cudaSuccess && b && b->pool.flush()) {  // blocks kept for reuse go back first
+                cudaGetLastError();
+                e = cudaMalloc(&p, bytes);
+            }
+        }
         if (e != cudaSuccess) {
             cudaGetLastError();
             p = nullptr;
